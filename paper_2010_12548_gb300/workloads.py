@@ -1,0 +1,420 @@
+"""Seeded synthetic inputs shaped like the paper's mobility workloads.
+
+This module is shared by the CUDA path's tests and benchmark and by the CPU
+oracle's tests.  It holds no part of the method's arithmetic (no curve, no
+covering, no lookup): only the polygons and points that the method consumes.
+
+Workloads (stand-ins for the NYC taxi points and the NYC zone / census polygon
+sets used in Sec. 3 and Sec. 5 of the paper, which are not available here):
+
+* star polygons: random star-shaped simple polygons around an integer centre
+  (sorted distinct angles, per-vertex radius), overlaps allowed;
+* Voronoi tilings: the bounded Voronoi diagram of random seeds over the grid
+  square, every shared edge subdivided once with integer jitter, so the
+  polygons tile the square exactly (no gaps, no overlaps);
+* points: uniform, or a mobility-like mix of Gaussian clusters and uniform
+  background, each with a log-normal int32 "fare" attribute.
+
+All randomness comes from numpy's PCG64 seeded per workload.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 2010125480  # workload i uses BASE_SEED + i
+
+
+@dataclass
+class Polygons:
+    """One simple ring per polygon, CSR layout, integer vertices.
+
+    ring_off[j]..ring_off[j+1] index polygon j's vertices in x/y.  Rings are
+    counter-clockwise and carry no closing duplicate vertex.
+    """
+    ring_off: np.ndarray  # uint32 [P+1]
+    x: np.ndarray         # uint32 [V]
+    y: np.ndarray         # uint32 [V]
+    grid_bits: int
+    centres: np.ndarray | None = None  # int64 [P,2] kernel point of star polygons
+
+    @property
+    def n(self) -> int:
+        return len(self.ring_off) - 1
+
+    def ring(self, j: int) -> tuple[np.ndarray, np.ndarray]:
+        a, b = int(self.ring_off[j]), int(self.ring_off[j + 1])
+        return self.x[a:b].astype(np.int64), self.y[a:b].astype(np.int64)
+
+    def subset(self, ids) -> "Polygons":
+        ids = np.asarray(ids, dtype=np.int64)
+        xs, ys, off = [], [], [0]
+        for j in ids:
+            rx, ry = self.ring(int(j))
+            xs.append(rx)
+            ys.append(ry)
+            off.append(off[-1] + len(rx))
+        c = None if self.centres is None else self.centres[ids]
+        return Polygons(np.asarray(off, np.uint32), np.concatenate(xs).astype(np.uint32),
+                        np.concatenate(ys).astype(np.uint32), self.grid_bits, c)
+
+
+@dataclass
+class Points:
+    x: np.ndarray     # uint32 [N]
+    y: np.ndarray     # uint32 [N]
+    attr: np.ndarray  # int32 [N]
+    grid_bits: int
+
+    @property
+    def n(self) -> int:
+        return len(self.x)
+
+    def take(self, idx) -> "Points":
+        return Points(self.x[idx], self.y[idx], self.attr[idx], self.grid_bits)
+
+
+# --------------------------------------------------------------------------
+# polygon simplicity (used to reject and resample jittered rings)
+# --------------------------------------------------------------------------
+
+def _orient(ax, ay, bx, by, cx, cy):
+    return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
+
+
+def ring_is_simple(rx: np.ndarray, ry: np.ndarray) -> bool:
+    """Exact integer check that a closed ring has no self-contact.
+
+    Non-adjacent edges must not meet (closed-segment test); adjacent edges
+    must not fold back onto each other.  O(V^2), vectorised per edge.
+    """
+    rx = np.asarray(rx, np.int64)
+    ry = np.asarray(ry, np.int64)
+    n = len(rx)
+    if n < 3:
+        return False
+    ax, ay = rx, ry
+    bx, by = np.roll(rx, -1), np.roll(ry, -1)
+    if np.any((ax == bx) & (ay == by)):
+        return False
+    # adjacent edges: fold-back = collinear with opposite direction
+    cx, cy = np.roll(rx, -2), np.roll(ry, -2)
+    cr = _orient(ax, ay, bx, by, cx, cy)
+    dot = (bx - ax) * (cx - bx) + (by - ay) * (cy - by)
+    if np.any((cr == 0) & (dot < 0)):
+        return False
+    if n == 3:
+        return _orient(ax[0], ay[0], bx[0], by[0], cx[0], cy[0]) != 0
+    for i in range(n):
+        # edges j not adjacent to i: j in [i+2, i+n-2]
+        js = (i + np.arange(2, n - 1)) % n
+        px, py, qx, qy = ax[i], ay[i], bx[i], by[i]
+        sx, sy, tx, ty = ax[js], ay[js], bx[js], by[js]
+        o1 = np.sign(_orient(px, py, qx, qy, sx, sy))
+        o2 = np.sign(_orient(px, py, qx, qy, tx, ty))
+        o3 = np.sign(_orient(sx, sy, tx, ty, px, py))
+        o4 = np.sign(_orient(sx, sy, tx, ty, qx, qy))
+        proper = (o1 * o2 < 0) & (o3 * o4 < 0)
+        if np.any(proper):
+            return False
+
+        def within(ux, uy, vx, vy, wx, wy):
+            return ((np.minimum(ux, vx) <= wx) & (wx <= np.maximum(ux, vx)) &
+                    (np.minimum(uy, vy) <= wy) & (wy <= np.maximum(uy, vy)))
+        touch = (((o1 == 0) & within(px, py, qx, qy, sx, sy)) |
+                 ((o2 == 0) & within(px, py, qx, qy, tx, ty)) |
+                 ((o3 == 0) & within(sx, sy, tx, ty, px, py)) |
+                 ((o4 == 0) & within(sx, sy, tx, ty, qx, qy)))
+        if np.any(touch):
+            return False
+    return True
+
+
+def _signed_area2(rx, ry):
+    rx = np.asarray(rx, np.int64)
+    ry = np.asarray(ry, np.int64)
+    return int(np.sum(rx * np.roll(ry, -1) - np.roll(rx, -1) * ry))
+
+
+# --------------------------------------------------------------------------
+# star polygons
+# --------------------------------------------------------------------------
+
+def star_polygons(rng: np.random.Generator, n: int, grid_bits: int,
+                  nverts=(8, 32), radius=(2 ** 11, 2 ** 12)) -> Polygons:
+    """Random star-shaped simple polygons with integer vertices.
+
+    Angles are sorted distinct uniform draws, each vertex has its own radius
+    uniform in ``radius``.  The centre is an integer point drawn uniformly
+    from the part of the grid where no vertex needs clamping, so the ring is
+    star-shaped with respect to the centre (checked exactly: every
+    consecutive pair turns counter-clockwise around the centre and the ring
+    winds once).
+    """
+    G = 2 ** grid_bits
+    rmax = int(math.ceil(radius[1])) + 1
+    if 2 * rmax >= G:
+        raise ValueError("radius too large for the grid")
+    xs, ys, off, cs = [], [], [0], []
+    while len(cs) < n:
+        k = int(rng.integers(nverts[0], nverts[1] + 1))
+        c = rng.integers(rmax, G - 1 - rmax, size=2)
+        th = np.sort(rng.uniform(0.0, 2 * math.pi, size=k))
+        r = rng.uniform(radius[0], radius[1], size=k)
+        vx = np.rint(c[0] + r * np.cos(th)).astype(np.int64)
+        vy = np.rint(c[1] + r * np.sin(th)).astype(np.int64)
+        dx, dy = vx - c[0], vy - c[1]
+        cr = dx * np.roll(dy, -1) - np.roll(dx, -1) * dy
+        if np.any(cr <= 0):
+            continue
+        turn = np.sum(np.mod(np.diff(np.append(np.arctan2(dy, dx), np.arctan2(dy[0], dx[0]))),
+                             2 * math.pi))
+        if abs(turn - 2 * math.pi) > 1e-6:
+            continue
+        xs.append(vx)
+        ys.append(vy)
+        off.append(off[-1] + k)
+        cs.append(c.astype(np.int64))
+    return Polygons(np.asarray(off, np.uint32), np.concatenate(xs).astype(np.uint32),
+                    np.concatenate(ys).astype(np.uint32), grid_bits, np.asarray(cs, np.int64))
+
+
+# --------------------------------------------------------------------------
+# Voronoi tilings
+# --------------------------------------------------------------------------
+
+def voronoi_tiling(rng: np.random.Generator, n: int, grid_bits: int,
+                   nverts=(20, 400), jitter: float = 0.125,
+                   min_piece: float = 16.0) -> Polygons:
+    """Exact tiling of the square [0, 2^B - 1]^2 by jittered Voronoi cells.
+
+    The bounded diagram comes from mirroring the seeds across the four sides
+    of the square.  Voronoi vertices are rounded to integers once and shared.
+    Every edge is subdivided once into pieces (both neighbours reuse the same
+    points); interior edges get a perpendicular integer jitter of at most
+    ``jitter`` times the piece length, edges on the square's border stay on
+    it.  Per-polygon vertex targets are drawn uniformly from ``nverts``;
+    a shared edge takes the smaller of its two polygons' per-edge share.
+    Rings that come out non-simple are re-jittered with less amplitude.
+    """
+    from scipy.spatial import Voronoi
+
+    M = float(2 ** grid_bits - 1)
+    for _attempt in range(16):
+        seeds = rng.uniform(0.0, M, size=(n, 2))
+        mir = [seeds,
+               np.c_[-seeds[:, 0], seeds[:, 1]], np.c_[2 * M - seeds[:, 0], seeds[:, 1]],
+               np.c_[seeds[:, 0], -seeds[:, 1]], np.c_[seeds[:, 0], 2 * M - seeds[:, 1]]]
+        vor = Voronoi(np.concatenate(mir))
+        vint = np.clip(np.rint(vor.vertices), 0, M).astype(np.int64)
+        regions = []
+        ok = True
+        for i in range(n):
+            reg = vor.regions[vor.point_region[i]]
+            if len(reg) < 3 or -1 in reg:
+                ok = False
+                break
+            reg = list(reg)
+            # merge vertices that round to the same integer point
+            out = []
+            for v in reg:
+                if out and (vint[v] == vint[out[-1]]).all():
+                    continue
+                out.append(v)
+            while len(out) > 1 and (vint[out[0]] == vint[out[-1]]).all():
+                out.pop()
+            if len(out) < 3:
+                ok = False
+                break
+            if _signed_area2(vint[out, 0], vint[out, 1]) < 0:
+                out = out[::-1]
+            regions.append(out)
+        if not ok:
+            continue
+        polys = _subdivide_tiling(rng, regions, vint, M, nverts, jitter, min_piece)
+        if polys is not None:
+            xs, ys, off = [], [], [0]
+            for rx, ry in polys:
+                xs.append(rx)
+                ys.append(ry)
+                off.append(off[-1] + len(rx))
+            return Polygons(np.asarray(off, np.uint32), np.concatenate(xs).astype(np.uint32),
+                            np.concatenate(ys).astype(np.uint32), grid_bits)
+    raise RuntimeError("could not generate a simple Voronoi tiling")
+
+
+def _subdivide_tiling(rng, regions, vint, M, nverts, jitter, min_piece):
+    n = len(regions)
+    edges_of = []
+    uses: dict[tuple[int, int], list[int]] = {}
+    for i, reg in enumerate(regions):
+        es = []
+        for a, b in zip(reg, reg[1:] + reg[:1]):
+            key = (min(a, b), max(a, b))
+            es.append(key)
+            uses.setdefault(key, []).append(i)
+        edges_of.append(es)
+    target = rng.integers(nverts[0], nverts[1] + 1, size=n)
+    share = target / np.asarray([len(e) for e in edges_of], np.float64)
+    length = {k: float(np.hypot(*(vint[k[1]] - vint[k[0]]))) for k in uses}
+    pieces = {}
+    for k, us in uses.items():
+        p = max(1, int(round(min(share[u] for u in us))))
+        pieces[k] = max(1, min(p, int(length[k] // min_piece)))
+    # top up rings below the minimum on their longest edges
+    for i in range(n):
+        for _ in range(64):
+            tot = sum(pieces[k] for k in edges_of[i])
+            if tot >= nverts[0]:
+                break
+            k = max(edges_of[i], key=lambda e: length[e] / (pieces[e] + 1))
+            if length[k] // min_piece <= pieces[k]:
+                break
+            pieces[k] += 1
+    for amp in (jitter, jitter / 2, jitter / 4, 0.0):
+        sub_rng = np.random.default_rng(int(rng.integers(0, 2 ** 63)))
+        pts = {}
+        for k in sorted(uses):
+            a, b = vint[k[0]].astype(np.float64), vint[k[1]].astype(np.float64)
+            m = pieces[k]
+            t = np.arange(1, m, dtype=np.float64) / m
+            p = a[None, :] + t[:, None] * (b - a)[None, :]
+            border = (a[0] == b[0] and a[0] in (0.0, M)) or (a[1] == b[1] and a[1] in (0.0, M))
+            if m > 1 and not border and amp > 0:
+                d = b - a
+                nrm = np.array([-d[1], d[0]]) / max(np.hypot(*d), 1e-12)
+                off = sub_rng.uniform(-amp, amp, size=m - 1) * (np.hypot(*d) / m)
+                p = p + off[:, None] * nrm[None, :]
+            pts[k] = np.clip(np.rint(p), 0, M).astype(np.int64)
+        out = []
+        good = True
+        for i, reg in enumerate(regions):
+            rx, ry = [], []
+            for a, b in zip(reg, reg[1:] + reg[:1]):
+                k = (min(a, b), max(a, b))
+                inner = pts[k] if a < b else pts[k][::-1]
+                rx.append(vint[a, 0])
+                ry.append(vint[a, 1])
+                rx.extend(inner[:, 0].tolist())
+                ry.extend(inner[:, 1].tolist())
+            rx = np.asarray(rx, np.int64)
+            ry = np.asarray(ry, np.int64)
+            keep = np.ones(len(rx), bool)
+            keep[1:] = (rx[1:] != rx[:-1]) | (ry[1:] != ry[:-1])
+            if len(rx) > 1 and rx[0] == rx[-1] and ry[0] == ry[-1]:
+                keep[-1] = False
+            rx, ry = rx[keep], ry[keep]
+            if not ring_is_simple(rx, ry) or _signed_area2(rx, ry) <= 0:
+                good = False
+                break
+            out.append((rx, ry))
+        if good:
+            return out
+    return None
+
+
+# --------------------------------------------------------------------------
+# points
+# --------------------------------------------------------------------------
+
+def fare_attr(rng: np.random.Generator, n: int) -> np.ndarray:
+    """int32 fare in cents: round(exp(N(7, 0.8)))."""
+    return np.rint(np.exp(rng.normal(7.0, 0.8, size=n))).astype(np.int32)
+
+
+def uniform_points(rng: np.random.Generator, n: int, grid_bits: int) -> Points:
+    G = 2 ** grid_bits
+    x = rng.integers(0, G, size=n, dtype=np.uint32)
+    y = rng.integers(0, G, size=n, dtype=np.uint32)
+    return Points(x, y, fare_attr(rng, n), grid_bits)
+
+
+def mobility_points(seed: int, n: int, grid_bits: int, n_clusters: int,
+                    sigma=(2 ** 16, 2 ** 19), frac_cluster: float = 0.7,
+                    chunk: int = 1 << 22) -> Points:
+    """Cluster/uniform mix: ``frac_cluster`` of the points come from
+    ``n_clusters`` isotropic Gaussians (centre uniform, sigma uniform in
+    ``sigma``, clipped to the grid), the rest are uniform.  Points appear in
+    random order.  Generated in fixed-size chunks, each from its own child
+    seed, so the result does not depend on memory limits."""
+    G = 2 ** grid_bits
+    ss = np.random.SeedSequence(seed)
+    head, body = ss.spawn(2)
+    hr = np.random.default_rng(head)
+    centres = hr.uniform(0, G, size=(n_clusters, 2))
+    sig = hr.uniform(sigma[0], sigma[1], size=n_clusters)
+    x = np.empty(n, np.uint32)
+    y = np.empty(n, np.uint32)
+    attr = np.empty(n, np.int32)
+    nchunks = (n + chunk - 1) // chunk
+    for c, cs in zip(range(nchunks), body.spawn(nchunks)):
+        r = np.random.default_rng(cs)
+        a, b = c * chunk, min(n, (c + 1) * chunk)
+        m = b - a
+        is_c = r.random(m) < frac_cluster
+        which = r.integers(0, n_clusters, size=m)
+        g = r.standard_normal((m, 2))
+        cx = centres[which, 0] + g[:, 0] * sig[which]
+        cy = centres[which, 1] + g[:, 1] * sig[which]
+        ux = r.integers(0, G, size=m)
+        uy = r.integers(0, G, size=m)
+        px = np.where(is_c, np.clip(np.rint(cx), 0, G - 1), ux)
+        py = np.where(is_c, np.clip(np.rint(cy), 0, G - 1), uy)
+        x[a:b] = px.astype(np.uint32)
+        y[a:b] = py.astype(np.uint32)
+        attr[a:b] = fare_attr(r, m)
+    return Points(x, y, attr, grid_bits)
+
+
+# --------------------------------------------------------------------------
+# the benchmark / test workloads
+# --------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    grid_bits: int
+    eps: list
+    polygons: Polygons
+    points: Points
+    extra: dict = field(default_factory=dict)
+
+
+def tiny_stars(n_points: int = 100_000) -> Workload:
+    """100k uniform points on [0,2^16)^2, 16 overlapping star polygons with
+    8-32 vertices and radii in [2^11, 2^12], eps = 64 grid units."""
+    rng = np.random.default_rng(BASE_SEED + 0)
+    polys = star_polygons(rng, 16, 16)
+    pts = uniform_points(rng, n_points, 16)
+    return Workload("stars16_pts100k_g16_eps64", 16, [64], polys, pts)
+
+
+_TILING_CACHE: dict = {}
+
+
+def zones263_tiling() -> Polygons:
+    """263-cell jittered Voronoi tiling of [0,2^24)^2, 20-400 vertices."""
+    if "z263" not in _TILING_CACHE:
+        rng = np.random.default_rng(BASE_SEED + 1)
+        _TILING_CACHE["z263"] = voronoi_tiling(rng, 263, 24, (20, 400))
+    return _TILING_CACHE["z263"]
+
+
+def tracts40k_tiling() -> Polygons:
+    """40,000-cell jittered Voronoi tiling of [0,2^28)^2, 6-60 vertices."""
+    if "t40k" not in _TILING_CACHE:
+        rng = np.random.default_rng(BASE_SEED + 2)
+        _TILING_CACHE["t40k"] = voronoi_tiling(rng, 40_000, 28, (6, 60))
+    return _TILING_CACHE["t40k"]
+
+
+def mobility_zones(n_points: int = 100_000_000) -> Workload:
+    """Mobility-shaped scale-up: n points on [0,2^24)^2 (70% from 32
+    Gaussian clusters, sigma in [2^16, 2^19]; 30% uniform) with fare
+    attributes, the 263-zone tiling, eps sweep {2^12, 2^10, 2^8, 2^6}."""
+    polys = zones263_tiling()
+    pts = mobility_points(BASE_SEED + 101, n_points, 24, 32)
+    return Workload(f"zones263_mobility{n_points}_g24", 24, [2 ** 12, 2 ** 10, 2 ** 8, 2 ** 6],
+                    polys, pts)

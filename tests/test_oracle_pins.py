@@ -1,0 +1,355 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here retypes the oracle's formulas: every expected value comes from a
+hand derivation (tests/golden), from a different formulation (fan
+triangulation + separating axes for star-shaped polygons), from a curve
+property, or from an invariant of the conservative raster (Sec. 2.2, Sec. 6).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2010_12548_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def polys_of(rings, B):
+    off, xs, ys = [0], [], []
+    for r in rings:
+        xs += [p[0] for p in r]
+        ys += [p[1] for p in r]
+        off.append(len(xs))
+    return W.Polygons(np.array(off, np.uint32), np.array(xs, np.uint32), np.array(ys, np.uint32), B)
+
+
+def lattice(B, attr=1):
+    g = np.arange(2 ** B, dtype=np.uint32)
+    gx, gy = np.meshgrid(g, g)
+    return W.Points(gx.ravel(), gy.ravel(), np.full(gx.size, attr, np.int32), B)
+
+
+# ---------------------------------------------------------------- Sec. 2.2 side
+
+def test_finest_side_golden(orc):
+    with open(os.path.join(GOLD, "finest_side.json")) as f:
+        g = json.load(f)
+    for c in g["cases"]:
+        r = orc.finest_k(c["eps"], c["grid_bits"])
+        if c["side"] is None:
+            assert r is None, c
+        else:
+            assert r is not None and 2 ** r[0] == c["side"], (c, r)
+            assert r[1] == c["grid_bits"] - r[0]
+
+
+def test_finest_side_bracket(orc):
+    # s*sqrt(2) <= eps < 2s*sqrt(2) whenever the grid does not cap s
+    rng = np.random.default_rng(7)
+    for eps in list(rng.integers(2, 2 ** 40, 400)) + [2 ** i for i in range(1, 40)]:
+        k, _ = orc.finest_k(int(eps), 30) if int(eps) < 2 ** 31 else orc.finest_k(int(eps), 30)
+        s = 2 ** k
+        assert 2 * s * s <= int(eps) ** 2
+        if k < 30:
+            assert int(eps) ** 2 < 8 * s * s
+
+
+# ---------------------------------------------------------------- Sec. 3 curve
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_curve_bijection_and_prefix(orc, which):
+    for order in range(1, 9):
+        n = 2 ** order
+        gx, gy = np.meshgrid(np.arange(n), np.arange(n))
+        h = orc.curve(order, gx.ravel(), gy.ravel(), which)
+        assert np.array_equal(np.sort(h), np.arange(n * n, dtype=np.uint64))
+        for L in range(order + 1):
+            hl = orc.curve(L, gx.ravel() >> (order - L), gy.ravel() >> (order - L), which)
+            assert np.array_equal(h >> np.uint64(2 * (order - L)), hl)
+
+
+def test_hilbert_adjacency_and_ends(orc):
+    assert list(orc.curve(1, [0, 0, 1, 1], [0, 1, 1, 0])) == [0, 1, 2, 3]
+    for order in range(1, 9):
+        n = 2 ** order
+        gx, gy = np.meshgrid(np.arange(n), np.arange(n))
+        gx, gy = gx.ravel(), gy.ravel()
+        h = orc.curve(order, gx, gy)
+        o = np.argsort(h)
+        step = np.abs(np.diff(gx[o])) + np.abs(np.diff(gy[o]))
+        assert (step == 1).all()  # consecutive ids are 4-neighbours
+        assert (gx[o[0]], gy[o[0]]) == (0, 0)
+        assert (gx[o[-1]], gy[o[-1]]) == (n - 1, 0)
+
+
+# ------------------------------------------------- hand-worked counts (golden)
+
+def test_handworked_square_triangle(orc):
+    with open(os.path.join(GOLD, "handworked_b4.json")) as f:
+        g = json.load(f)
+    B = g["grid_bits"]
+    pts = lattice(B)
+    for name, ring in g["polygons"].items():
+        P = polys_of([ring], B)
+        assert int(orc.join_exact(P, pts)[0][0]) == g["exact"][name]
+        for c in g["cases"]:
+            assert 2 ** orc.finest_k(c["eps"], B)[0] == c["side"]
+            for which in (0, 1):
+                cov = orc.cover(P, c["eps"], which)
+                cnt, sm = cov.join(pts.x, pts.y, pts.attr)
+                assert int(cnt[0]) == c[name] and int(sm[0]) == c[name], (name, c, which)
+            cnt2, sm2, _ = orc.join_o2(P, c["eps"], pts)
+            assert int(cnt2[0]) == c[name]
+
+
+def test_points_outside_grid_ignored(orc):
+    P = polys_of([[(0, 0), (15, 0), (15, 15), (0, 15)]], 4)
+    pts = W.Points(np.array([0, 16, 3, 2 ** 31], np.uint32), np.array([0, 0, 16, 5], np.uint32),
+                   np.array([1, 10, 100, 1000], np.int32), 4)
+    cov = orc.cover(P, 2)
+    assert cov.join(pts.x, pts.y, pts.attr)[0][0] == 1
+    assert orc.join_o2(P, 2, pts)[0][0] == 1
+
+
+# --------------------------------- star polygons: fan triangulation + SAT pin
+
+def _orient(a, b, c):
+    return (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+
+
+def fan(P, j):
+    rx, ry = P.ring(j)
+    c = tuple(int(v) for v in P.centres[j])
+    v = list(zip(rx.tolist(), ry.tolist()))
+    return [(c, v[i], v[(i + 1) % len(v)]) for i in range(len(v))]
+
+
+def tri_meets_square(t, x0, y0, x1, y1):
+    xs = [p[0] for p in t]
+    ys = [p[1] for p in t]
+    if max(xs) < x0 or min(xs) > x1 or max(ys) < y0 or min(ys) > y1:
+        return False
+    corners = [(x0, y0), (x1, y0), (x1, y1), (x0, y1)]
+    for i in range(3):
+        a, b, c = t[i], t[(i + 1) % 3], t[(i + 2) % 3]
+        sc = _orient(a, b, c)
+        if all(_orient(a, b, q) * sc < 0 for q in corners):
+            return False
+    return True
+
+
+def tri_has_point(t, p):
+    a, b, c = t
+    return _orient(a, b, p) >= 0 and _orient(b, c, p) >= 0 and _orient(c, a, p) >= 0
+
+
+def small_stars(seed, B, n=6):
+    rng = np.random.default_rng(seed)
+    G = 2 ** B
+    return W.star_polygons(rng, n, B, nverts=(3, 12), radius=(G / 16, G / 5))
+
+
+@pytest.mark.parametrize("B,eps,seed", [(6, 2, 1), (6, 5, 2), (7, 12, 3), (8, 3, 4), (8, 23, 5)])
+def test_star_cells_vs_fan_sat(orc, B, eps, seed):
+    """O1 and O2 membership equals 'closed cell meets some closed fan triangle'."""
+    P = small_stars(seed, B)
+    pts = lattice(B)
+    k, F = orc.finest_k(eps, B)
+    s = 2 ** k
+    for j in range(P.n):
+        tris = fan(P, j)
+        want = np.zeros(pts.n, bool)
+        cells = {}
+        for i in range(pts.n):
+            cx, cy = int(pts.x[i]) >> k, int(pts.y[i]) >> k
+            if (cx, cy) not in cells:
+                x0, y0 = cx * s, cy * s
+                cells[(cx, cy)] = any(tri_meets_square(t, x0, y0, x0 + s, y0 + s) for t in tris)
+            want[i] = cells[(cx, cy)]
+        _, _, _, mem = orc.join_o2(P, eps, pts, member=True, only=j)
+        assert np.array_equal(mem.astype(bool), want), j
+        one = P.subset([j])
+        cnt, sm = orc.cover(one, eps).join(pts.x, pts.y, pts.attr)
+        assert int(cnt[0]) == int(want.sum())
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_exact_pip_vs_fan(orc, seed):
+    B = 7
+    P = small_stars(seed, B)
+    pts = lattice(B)
+    for j in range(P.n):
+        tris = fan(P, j)
+        want = np.array([any(tri_has_point(t, (int(x), int(y))) for t in tris)
+                         for x, y in zip(pts.x, pts.y)])
+        _, _, mem = orc.join_exact(P, pts, member=True, only=j)
+        assert np.array_equal(mem.astype(bool), want)
+
+
+def test_classify_interior_cells_are_inside(orc):
+    """A cell the oracle calls interior lies inside the fan union and touches
+    no fan edge on the ring; a cell it calls exterior meets no fan triangle."""
+    B = 8
+    P = small_stars(21, B, n=4)
+    rng = np.random.default_rng(5)
+    for j in range(P.n):
+        tris = fan(P, j)
+        for side in (1, 2, 4, 8, 16):
+            x0 = rng.integers(0, 2 ** B - side, 300) // side * side
+            y0 = rng.integers(0, 2 ** B - side, 300) // side * side
+            cls = orc.classify(P, j, x0, y0, side)
+            for a, b, c in zip(x0.tolist(), y0.tolist(), cls.tolist()):
+                meets = any(tri_meets_square(t, a, b, a + side, b + side) for t in tris)
+                if c == 0:
+                    assert not meets
+                else:
+                    assert meets
+                if c == 1:
+                    corners = [(a, b), (a + side, b), (a + side, b + side), (a, b + side)]
+                    assert all(any(tri_has_point(t, q) for t in tris) for q in corners)
+
+
+# ---------------------------------------------------- canonical covering form
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_covering_is_canonical_and_exact_cell_set(orc, which):
+    B = 6
+    P = small_stars(31, B, n=5)
+    for eps in (2, 6, 23):
+        k, F = orc.finest_k(eps, B)
+        cov = orc.cover(P, eps, which)
+        st, lo, ids = cov.start, cov.list_off, cov.list_ids
+        assert st[0] == 0 and st[-1] == 4 ** F
+        assert (np.diff(st.astype(np.int64)) > 0).all()
+        lists = [tuple(ids[lo[r]:lo[r + 1]]) for r in range(cov.R)]
+        for r in range(cov.R):
+            assert list(lists[r]) == sorted(set(lists[r]))
+            if r:
+                assert lists[r] != lists[r - 1]
+        # decode: every finest cell's list equals the set of polygons it meets
+        n = 2 ** F
+        gx, gy = np.meshgrid(np.arange(n), np.arange(n))
+        gx, gy = gx.ravel(), gy.ravel()
+        h = orc.curve(F, gx, gy, which)
+        r_of = np.searchsorted(st, h, side="right") - 1
+        s = 2 ** k
+        for j in range(P.n):
+            cls = orc.classify(P, j, gx * s, gy * s, s)
+            inlist = np.array([j in lists[r] for r in r_of])
+            assert np.array_equal(inlist, cls != 0)
+
+
+# ------------------------------------------------------ invariants (Sec. 2.2, 6)
+
+@pytest.fixture(scope="module")
+def stars_small():
+    w = W.tiny_stars(20_000)
+    return w
+
+
+def test_no_false_negatives_and_eps_bound(orc, stars_small):
+    """I1: exact is contained in the approximation (conservative raster).
+    I2: every false positive lies within eps of the polygon's boundary."""
+    w = stars_small
+    P, pts = w.polygons, w.points
+    for eps in (64, 200, 1000):
+        for j in range(P.n):
+            _, _, _, am = orc.join_o2(P, eps, pts, member=True, only=j)
+            _, _, em = orc.join_exact(P, pts, member=True, only=j)
+            am, em = am.astype(bool), em.astype(bool)
+            assert not np.any(em & ~am)
+            for i in np.nonzero(am & ~em)[0]:
+                assert orc.near_boundary(P, j, int(pts.x[i]), int(pts.y[i]), eps)
+
+
+def test_monotone_in_eps_and_result_range(orc, stars_small):
+    """I3: halving eps never adds a point (finest covered sets nest).
+    I4 (Sec. 6): exact count lies in [alpha - beta, alpha], beta = points in
+    boundary cells."""
+    w = stars_small
+    P, pts = w.polygons, w.points
+    ex, exs = orc.join_exact(P, pts)
+    prev = None
+    for eps in (4096, 2048, 1024, 512, 256, 128, 64, 32, 16, 8, 4, 2):
+        a, s, b = orc.join_o2(P, eps, pts)
+        assert (a - b <= ex).all() and (ex <= a).all()
+        if prev is not None:
+            assert (a <= prev).all()
+        prev = a
+
+
+def test_hilbert_vs_z_same_counts(orc, stars_small):
+    """I6: counts do not depend on the curve; the ranges do."""
+    w = stars_small
+    for eps in (64, 300):
+        ch = orc.cover(w.polygons, eps, 0)
+        cz = orc.cover(w.polygons, eps, 1)
+        a = ch.join(w.points.x, w.points.y, w.points.attr)
+        b = cz.join(w.points.x, w.points.y, w.points.attr)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert not np.array_equal(ch.start[:10], cz.start[:10])
+        o2 = orc.join_o2(w.polygons, eps, w.points)
+        assert np.array_equal(a[0], o2[0]) and np.array_equal(a[1], o2[1])
+
+
+def test_convergence_to_exact(orc):
+    """As the grid is refined around a fixed instance, the s=1 counts fall to
+    the exact counts; once the cell side drops below the smallest nonzero
+    lattice-point distance (vertices < 2^b: m >= b+2) they are equal."""
+    b = 5
+    P0 = small_stars(41, b, n=4)
+    pts0 = lattice(b)
+    ex = orc.join_exact(P0, pts0)[0]
+    prev = None
+    for m in range(0, b + 4):
+        P = W.Polygons(P0.ring_off, P0.x << m, P0.y << m, b + m)
+        pts = W.Points(pts0.x << m, pts0.y << m, pts0.attr, b + m)
+        cnt = orc.cover(P, 2).join(pts.x, pts.y)[0]
+        assert (cnt >= ex).all()
+        if prev is not None:
+            assert (cnt <= prev).all()
+        if m >= b + 2:
+            assert np.array_equal(cnt, ex)
+        prev = cnt
+
+
+def test_tiling_every_point_covered(orc):
+    """I5: a tiling covers every lattice point exactly and approximately, and
+    points strictly inside one tile's interior get exactly one polygon."""
+    rng = np.random.default_rng(3)
+    T = W.voronoi_tiling(rng, 12, 10, nverts=(6, 20), min_piece=4.0)
+    pts = lattice(10)
+    _, _, em = orc.join_exact(T, pts, member=True)
+    assert em.all()
+    cov = orc.cover(T, 8)
+    cnt, _ = cov.join(pts.x, pts.y, pts.attr)
+    ex = orc.join_exact(T, pts)[0]
+    assert cnt.sum() >= pts.n and ex.sum() >= pts.n
+    o2 = orc.join_o2(T, 8, pts)
+    assert np.array_equal(cnt, o2[0])
+
+
+def test_near_boundary_vs_float_distance(orc):
+    """The exact eps-distance test agrees with a float64 point-to-segment
+    distance wherever the two are not within rounding of the threshold."""
+    rng = np.random.default_rng(9)
+    P = small_stars(51, 10, n=3)
+    checked = 0
+    for j in range(P.n):
+        rx, ry = P.ring(j)
+        ax, ay = rx.astype(float), ry.astype(float)
+        bx, by = np.roll(ax, -1), np.roll(ay, -1)
+        for _ in range(300):
+            px, py = rng.integers(0, 2 ** 10, 2)
+            eps = int(rng.integers(1, 200))
+            dx, dy = bx - ax, by - ay
+            t = np.clip(((px - ax) * dx + (py - ay) * dy) / (dx * dx + dy * dy), 0, 1)
+            d = np.min(np.hypot(ax + t * dx - px, ay + t * dy - py))
+            if abs(d - eps) < 1e-6 * max(1.0, eps):
+                continue
+            assert orc.near_boundary(P, j, int(px), int(py), eps) == (d <= eps)
+            checked += 1
+    assert checked > 800
