@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark of the eps-bounded approximate point-in-polygon join + aggregation.
+
+Workload: 100M mobility-shaped points (uint32 coordinates on [0,2^24)^2, 70%
+from 32 Gaussian clusters with sigma in [2^16, 2^19], 30% uniform, int32 fare
+attribute), the 263-zone jittered Voronoi tiling (20-400 vertices), and the
+eps sweep {2^12, 2^10, 2^8, 2^6}.
+
+One step = for every eps of the sweep: build the covering from the polygons
+(host arrays), fit the learned index (2^12 leaves), and join all points with
+the learned lookup into per-polygon COUNT and SUM (device-resident points).
+The metric counts point-joins: points x eps levels per second.
+
+Besides the timed steps the script measures, outside the timed region, the
+join alone per eps for the learned and the binary-search lookups, the
+end-to-end rate through the host-buffer entry point (points copied from pinned
+host memory every step, results read back), and the CPU oracle on a bounded
+sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query latency"
+UNIT = "points/s"
+LEAF_BITS = 12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--points", type=int, default=100_000_000)
+    ap.add_argument("--no-extras", action="store_true", help="skip join-only, e2e and CPU legs")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        def num(s):
+            try:
+                return float(s.split()[0])
+            except Exception:
+                return None
+        sm = [num(r[1]) for r in self.rows if len(r) >= 9 and num(r[1])]
+        mx = [num(r[2]) for r in self.rows if len(r) >= 9 and num(r[2])]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(n_points):
+    from paper_2010_12548_gb300 import workloads as W
+    return W.mobility_zones(n_points)
+
+
+def cpu_oracle_rate(w, seconds: float, threads: int, max_points: int | None = None):
+    """Oracle O2 (definitional per-point test) on a bounded sample of the
+    workload's points, all eps levels; returns (points x eps / s, sample size, secs)."""
+    from oracle import oracle as O
+    O.build()
+    n = 20_000
+    spent = 0.0
+    while True:
+        pts = w.points.take(np.arange(min(n, w.points.n)))
+        t0 = time.perf_counter()
+        for eps in w.eps:
+            O.join_o2(w.polygons, eps, pts, threads=threads)
+        spent = time.perf_counter() - t0
+        if spent >= seconds / 4 or n >= w.points.n or (max_points and n >= max_points):
+            break
+        n = int(n * min(8.0, max(2.0, seconds / max(spent, 1e-3) / 2)))
+        n = min(n, w.points.n)
+    return pts.n * len(w.eps) / spent, pts.n, spent
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init(args) if int(os.environ.get("WORLD_SIZE", "1")) > 1 else (1, 0, 0)
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    w = workload(args.points)
+    rate, sample, _ = cpu_oracle_rate(w, max(2.0, args.cpu_seconds / 2), threads)
+    from oracle import oracle as O
+    pts = w.points.take(np.arange(sample))
+    for _ in range(args.warmup):
+        for eps in w.eps[:1]:
+            O.join_o2(w.polygons, eps, pts.take(np.arange(min(2000, pts.n))), threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for eps in w.eps:
+            O.join_o2(w.polygons, eps, pts, threads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = sample * len(w.eps) / (ms / 1e3)
+    sample_desc = f"first {sample} of the {w.points.n} points, all {len(w.eps)} eps levels per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": config_of(w, args.points),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, n_points):
+    return {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64_learned2^12",
+            "points": n_points, "polygons": w.polygons.n, "grid_bits": 24, "eps": w.eps,
+            "leaf_bits": LEAF_BITS, "lookup": "learned",
+            "l2": "inputs larger than L2 (point arrays 12 B/pt)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_init(args)
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2010_12548_gb300 import build as B
+    B.build()
+    from paper_2010_12548_gb300 import sdb
+
+    w = workload(args.points)
+    N = w.points.n
+    P = w.polygons.n
+    dev = torch.device("cuda", local)
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+
+    x, y, a = to_dev(w.points.x), to_dev(w.points.y), to_dev(w.points.attr)
+    E = len(w.eps)
+    cnt = torch.zeros((E, P), dtype=torch.int64, device=dev)
+    sm = torch.zeros((E, P), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    covs_live = []
+
+    def step(events=None):
+        for i, eps in enumerate(w.eps):
+            if events is not None:
+                events[i][0].record(stream)
+            c = sdb.build_covering(w.polygons, 24, eps, stream)
+            sdb.covering_build_index(c, LEAF_BITS, stream)
+            if events is not None:
+                events[i][1].record(stream)
+            sdb.join_aggregate(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], sm[i], stream)
+            if events is not None:
+                events[i][2].record(stream)
+            covs_live.append(c)
+        while covs_live:
+            covs_live.pop().free()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in w.eps]
+          for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = sdb.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            step(ev[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = sdb.launch_count() - launches0
+    ms = t0.elapsed_time(t1) / args.steps
+    ms = max_over_ranks(ws, ms)
+    value = ws * N * E / (ms / 1e3)
+    build_ms = [statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+                for i in range(E)]
+    join_ms = [statistics.mean(ev[k][i][1].elapsed_time(ev[k][i][2]) for k in range(args.steps))
+               for i in range(E)]
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": config_of(w, N), "clocks": clk.summary(), "gpu_launches": launches}
+    res["phases_ms"] = {"build_and_index": dict(zip([str(e) for e in w.eps], build_ms)),
+                        "join_learned": dict(zip([str(e) for e in w.eps], join_ms))}
+
+    # ---- join alone, learned vs binary search, per eps (not part of the step)
+    peak, peak_kind = peaks()
+    joins = {}
+    if not args.no_extras:
+        reps = 5
+        for i, eps in enumerate(w.eps):
+            c = sdb.build_covering(w.polygons, 24, eps, stream)
+            sdb.covering_build_index(c, LEAF_BITS, stream)
+            inf = c.info()
+            row = {"ranges": inf.n_ranges, "cells": inf.n_cells, "covering_bytes": inf.device_bytes}
+            for name, lk in (("binary", sdb.LOOKUP_BINARY), ("learned", sdb.LOOKUP_LEARNED)):
+                sdb.join_aggregate(x, y, a, c, lk, cnt[i], sm[i], stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(reps):
+                    sdb.join_aggregate(x, y, a, c, lk, cnt[i], sm[i], stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                jm = e0.elapsed_time(e1) / reps
+                row[name + "_ms"] = jm
+                row[name + "_pts_per_s"] = N / (jm / 1e3)
+            row["fallbacks"] = sdb.covering_fallbacks(c, stream)
+            joins[str(eps)] = row
+            c.free()
+        res["join_only"] = joins
+    # ---- roofline of the join kernel of the finest eps inside the timed steps
+    fine = str(w.eps[-1])
+    cov_bytes = joins.get(fine, {}).get("covering_bytes", 0)
+    per_pt = 12 + (64 if cov_bytes > 64e6 else 0)
+    jms = join_ms[-1]
+    achieved = N * per_pt / (jms / 1e3) / 1e9
+    res["roofline"] = {"kernel": "join_kernel<learned> eps=%s" % fine, "bound": "hbm",
+                       "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "peak_kind": peak_kind, "traffic": None,
+                       "algorithmic_bytes_per_point": per_pt}
+    # ---- end to end through the host-buffer entry point
+    if not args.no_extras:
+        hx = torch.from_numpy(w.points.x.view(np.int32)).pin_memory()
+        hy = torch.from_numpy(w.points.y.view(np.int32)).pin_memory()
+        ha = torch.from_numpy(w.points.attr).pin_memory()
+        hc = torch.zeros((E, P), dtype=torch.int64).pin_memory()
+        hs = torch.zeros((E, P), dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            covs = []
+            for eps in w.eps:
+                c = sdb.build_covering(w.polygons, 24, eps, stream)
+                sdb.covering_build_index(c, LEAF_BITS, stream)
+                covs.append(c)
+            sdb.join_aggregate_host_ptrs(hx.data_ptr(), hy.data_ptr(), ha.data_ptr(), N, covs,
+                                         sdb.LOOKUP_LEARNED, hc.data_ptr(), hs.data_ptr(), stream)
+            for c in covs:
+                c.free()
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        tt = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - tt) / args.steps
+        e2e_s = max_over_ranks(ws, e2e_s)
+        res["e2e"] = {"value": ws * N * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * 12,
+                      "d2h_bytes_per_step": E * P * 16, "ms_per_step": e2e_s * 1e3}
+        # the host join must agree with the device join
+        res["e2e"]["matches_device"] = bool(np.array_equal(hc.numpy(), cnt.cpu().numpy()) and
+                                            np.array_equal(hs.numpy(), sm.cpu().numpy()))
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    if rank == 0 and ws == 1 and not args.no_extras:
+        threads = os.cpu_count() or 1
+        rate, sample, secs = cpu_oracle_rate(w, args.cpu_seconds, threads)
+        res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"first {sample} of the {N} points, all {E} eps "
+                                         f"levels, definitional per-point test ({secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

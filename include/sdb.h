@@ -1,0 +1,179 @@
+/*
+ * sdb.h - distance-bounded approximate spatial aggregation on the GPU.
+ *
+ * C ABI of libsdb.so.  The library answers the spatial aggregation query of
+ * Sec. 5 of "The Case for Distance-Bounded Spatial Approximations" (CIDR 2021):
+ *
+ *     SELECT COUNT(*), SUM(a) FROM P, R WHERE P.loc INSIDE R.geometry GROUP BY R.id
+ *
+ * without any exact geometric test.  Each polygon is replaced by a conservative
+ * hierarchical raster (Sec. 2.1, Fig. 1c) whose boundary cells have a diagonal
+ * of at most eps (Sec. 2.2), so every point counted for a polygon it does not
+ * contain lies within eps of that polygon's boundary, and no contained point is
+ * missed.  Cells are linearised with a Hilbert curve and stored as disjoint,
+ * sorted id ranges that each carry a polygon list (Sec. 3, "Polygon
+ * Indexing"); each point is mapped to its finest-level cell id and looked up
+ * (Sec. 3), and the join is fused with the aggregation (Sec. 5.1).
+ *
+ * Conventions shared by every call:
+ *   - Coordinates are unsigned integers on the grid [0, 2^grid_bits)^2,
+ *     1 <= grid_bits <= 30.  eps is in grid units.
+ *   - A cell is a closed square and a polygon a closed region; a cell belongs to
+ *     a polygon's covering when the two intersect (a touch is enough).
+ *   - The finest cell side is s = 2^k, the largest power of two with
+ *     2 s^2 <= eps^2 (diagonal <= eps); k is capped at grid_bits.  The finest
+ *     level is F = grid_bits - k.  A point (x, y) lies in finest cell
+ *     (x >> k, y >> k).
+ *   - "d_" pointers are device memory owned by the caller; "h_" pointers are
+ *     host memory owned by the caller (pinned memory is faster, pageable works).
+ *     Nothing the caller passes is retained after the call returns, except that
+ *     device work enqueued on cuda_stream reads d_ inputs until it completes.
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     work is enqueued on it and the call returns without waiting, unless the
+ *     call's description says it synchronises.
+ *   - Every call returns a status; nothing aborts or throws.  On any status but
+ *     SDB_OK the outputs are unspecified and sdb_last_error() describes the
+ *     failure (thread-local text).
+ *   - Points outside [0, 2^grid_bits)^2 match no polygon.
+ */
+#ifndef SDB_H
+#define SDB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sdb_status {
+  SDB_OK = 0,
+  SDB_EINVAL = 1,   /* invalid argument (message in sdb_last_error) */
+  SDB_ENOMEM = 2,   /* device or host allocation failed */
+  SDB_ECUDA = 3,    /* a CUDA runtime call failed */
+  SDB_ETIMEOUT = 4, /* a bounded wait ran out */
+  SDB_EBUSY = 5     /* the object is in use (e.g. a batch still running) */
+} sdb_status;
+
+enum { SDB_LOOKUP_BINARY = 0, SDB_LOOKUP_LEARNED = 1 };
+
+/* Polygons in host memory, read during the call only.  One simple ring per
+ * polygon (no holes, no self-contact), vertices in [0, 2^grid_bits), either
+ * orientation, no closing duplicate vertex.  Polygon j's vertices are
+ * x[ring_off[j]] .. x[ring_off[j+1]-1]; the output index of polygon j is j.
+ * Simplicity is the caller's responsibility (it is not checked). */
+typedef struct sdb_polygons {
+  uint32_t n_polygons;      /* P, 1 <= P < 2^26 */
+  const uint32_t *ring_off; /* P+1 offsets, ring_off[0] = 0, each ring >= 3 vertices */
+  const uint32_t *x;        /* ring_off[P] vertex x coordinates */
+  const uint32_t *y;        /* ring_off[P] vertex y coordinates */
+} sdb_polygons;
+
+/* Opaque device-resident covering (library-owned device memory). */
+typedef struct sdb_covering sdb_covering;
+
+typedef struct sdb_covering_info {
+  uint32_t grid_bits;      /* B */
+  uint32_t finest_shift;   /* k: finest side 2^k */
+  uint32_t finest_level;   /* F = B - k */
+  uint32_t n_polygons;     /* P */
+  uint64_t n_ranges;       /* R: ranges partition [0, 4^F) */
+  uint64_t n_list_ids;     /* total length of all polygon lists */
+  uint64_t n_cells;        /* raster cells emitted before merging into ranges */
+  uint64_t device_bytes;   /* device memory held by the covering */
+  uint32_t index_leaf_bits;/* leaves = 2^index_leaf_bits, 0 = no learned index */
+  uint32_t reserved;
+} sdb_covering_info;
+
+/* Finest level for (grid_bits, eps), Sec. 2.2 (side eps/sqrt(2), so the
+ * diagonal is eps; the side is rounded down to a power of two so cells nest
+ * in the quadtree).  Host only.  SDB_EINVAL if grid_bits is outside 1..30 or
+ * eps < 2 (no side s >= 1 has diagonal <= eps). */
+sdb_status sdb_finest_level(uint32_t grid_bits, uint64_t eps, uint32_t *shift_out,
+                            uint32_t *level_out);
+
+/* Build the conservative hierarchical raster covering of every polygon
+ * (Sec. 2.1-2.2, Sec. 3 "Polygon Indexing"): per polygon, quadtree cells from
+ * the whole grid down; a cell that meets no edge and lies inside is emitted
+ * whole (interior cell, any level); a cell that meets an edge is split until
+ * the finest level and emitted there (boundary cell); all other cells are
+ * dropped.  Each emitted cell becomes the Hilbert-id range of its finest-level
+ * descendants; the ranges of all polygons are merged into maximal disjoint
+ * ranges partitioning [0, 4^F), each with its ascending, duplicate-free polygon
+ * list (possibly empty).
+ *
+ * Synchronises cuda_stream (the per-level frontier sizes are read on the host).
+ * *out receives a new covering to be released with sdb_covering_free.
+ * SDB_EINVAL: bad grid_bits/eps (see sdb_finest_level), P = 0 or P >= 2^26,
+ * a ring with < 3 vertices, a vertex outside the grid, a null pointer.
+ * SDB_ENOMEM: device memory ran out. */
+sdb_status sdb_build_covering(const sdb_polygons *polys, uint32_t grid_bits, uint64_t eps,
+                              void *cuda_stream, sdb_covering **out);
+
+sdb_status sdb_covering_get_info(const sdb_covering *cov, sdb_covering_info *info);
+
+/* Fit the learned range index (Sec. 3, "Point Indexing": a learned model
+ * predicts a key's position in the sorted array, after RadixSpline): a root
+ * linear model maps a cell id to one of 2^leaf_bits leaves, each leaf a linear
+ * model in FP32 on leaf-relative ids, plus the leaf's maximum prediction error
+ * below and above, measured with the same FP32 arithmetic the lookup uses over
+ * every id the root sends to that leaf.  The fit (least squares per leaf) runs
+ * on the device.  Replaces a previous index.  Synchronises cuda_stream.
+ * SDB_EINVAL: leaf_bits outside 4..20. */
+sdb_status sdb_covering_build_index(sdb_covering *cov, uint32_t leaf_bits, void *cuda_stream);
+
+/* Index-nested-loop join fused with COUNT and SUM (Sec. 5.1): for each point i
+ * with finest cell id h, the range r with start[r] <= h < start[r+1] is found
+ * (lookup = SDB_LOOKUP_BINARY: binary search over the range starts;
+ * SDB_LOOKUP_LEARNED: the learned index's prediction, a search bounded by the
+ * stored error window, verified, with binary search as the fallback; requires
+ * sdb_covering_build_index), and for every polygon j on r's list
+ * d_count[j] += 1 and d_sum[j] += d_attr[i].  Both lookups give identical
+ * results.  d_count and d_sum (P entries each) are zeroed by the call.
+ * d_x, d_y, d_attr: n device values (SoA).  d_attr and d_sum may be NULL
+ * (COUNT only).  n = 0 just zeroes the outputs.  Asynchronous.
+ * SDB_EINVAL: null cov/d_count, n > 0 with null d_x/d_y, d_sum without d_attr,
+ * learned lookup without an index. */
+sdb_status sdb_join_aggregate(const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
+                              uint64_t n, const sdb_covering *cov, int lookup,
+                              uint64_t *d_count, int64_t *d_sum, void *cuda_stream);
+
+/* The same join for points in host memory against n_covs coverings at once
+ * (e.g. the same polygons at several eps).  Points are streamed to the device
+ * in chunks; each chunk is joined against every covering while the next chunk
+ * is copied.  All coverings must have the same n_polygons P.  h_count and h_sum
+ * are host arrays of n_covs * P entries (covering c's results at [c*P, c*P+P)).
+ * Synchronises cuda_stream before returning (results are in host memory).
+ * Device staging buffers are allocated and freed by the call. */
+sdb_status sdb_join_aggregate_host(const uint32_t *h_x, const uint32_t *h_y, const int32_t *h_attr,
+                                   uint64_t n, const sdb_covering *const *covs, uint32_t n_covs,
+                                   int lookup, uint64_t *h_count, int64_t *h_sum,
+                                   void *cuda_stream);
+
+/* Number of learned-index lookups of the covering's most recent learned join
+ * whose bounded search missed and fell back to binary search.  Synchronises
+ * cuda_stream. */
+sdb_status sdb_covering_fallbacks(const sdb_covering *cov, void *cuda_stream, uint64_t *out);
+
+/* Copy the canonical covering to host memory: start[R+1] (start[0] = 0,
+ * start[R] = 4^F, strictly increasing), list_off[R+1], list_ids[n_list_ids];
+ * range r holds finest ids [start[r], start[r+1]) and polygons
+ * list_ids[list_off[r] .. list_off[r+1]-1], ascending.  Adjacent ranges have
+ * different lists.  Synchronous.  Array sizes come from sdb_covering_get_info. */
+sdb_status sdb_covering_export(const sdb_covering *cov, uint64_t *h_start, uint32_t *h_list_off,
+                               uint32_t *h_list_ids);
+
+/* Release a covering (waits for the device to finish with it).  NULL is a no-op. */
+void sdb_covering_free(sdb_covering *cov);
+
+const char *sdb_status_string(sdb_status s);
+const char *sdb_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far (all
+ * devices, all threads).  A diagnostic counter; host only, never fails. */
+uint64_t sdb_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDB_H */

@@ -1,0 +1,412 @@
+// C ABI entry points of libsdb.so (declared in include/sdb.h).  Host-side
+// argument checks, the per-device memory pool, covering lifetime, and the
+// host-buffer join that streams point chunks through the device.
+#include "sdb_internal.cuh"
+
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+namespace sdb {
+
+namespace {
+thread_local char g_err[512] = "";
+std::mutex g_mu;
+cudaMemPool_t g_pool[64];
+bool g_pool_ok[64];
+int g_sms[64];
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+sdb_status cuda_status(cudaError_t e, const char* what, const char* file, int line) {
+  set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  return e == cudaErrorMemoryAllocation ? SDB_ENOMEM : SDB_ECUDA;
+}
+
+static sdb_status get_pool(cudaMemPool_t* pool) {
+  int dev = 0;
+  SDB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device %d out of range", dev);
+    return SDB_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_pool_ok[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    SDB_TRY_CUDA(cudaMemPoolCreate(&g_pool[dev], &props));
+    // keep freed blocks for reuse by later calls of this process
+    uint64_t keep = ~0ull;
+    SDB_TRY_CUDA(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool_ok[dev] = true;
+  }
+  *pool = g_pool[dev];
+  return SDB_OK;
+}
+
+sdb_status dalloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool;
+  SDB_TRY(get_pool(&pool));
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return SDB_ENOMEM;
+  }
+  return SDB_OK;
+}
+
+void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+int num_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 1;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_sms[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_sms[dev] = n > 0 ? n : 1;
+  }
+  return g_sms[dev];
+}
+
+static sdb_status finest(uint32_t B, uint64_t eps, uint32_t* k_out) {
+  if (B < 1 || B > 30) {
+    set_error("grid_bits %u outside 1..30", B);
+    return SDB_EINVAL;
+  }
+  if (eps < 2) {
+    set_error("eps %llu < 2: no cell side >= 1 has a diagonal <= eps", (unsigned long long)eps);
+    return SDB_EINVAL;
+  }
+  // largest k with 2 * (2^k)^2 <= eps^2
+  unsigned __int128 e2 = (unsigned __int128)eps * eps;
+  uint32_t k = 0;
+  while (k < B && ((unsigned __int128)2 << (2 * (k + 1))) <= e2) ++k;
+  *k_out = k;
+  return SDB_OK;
+}
+
+static void free_covering(sdb_covering* c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  void* ps[] = {c->start, c->list_off, c->list_ids, c->pay, c->sample, c->leaves, c->fallbacks};
+  for (void* p : ps)
+    if (p) cudaFreeAsync(p, 0);
+  cudaStreamSynchronize(0);
+  cudaSetDevice(prev);
+  delete c;
+}
+
+static sdb_status check_device(const sdb_covering* cov) {
+  int dev = 0;
+  SDB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev != cov->device) {
+    set_error("covering lives on device %d, current device is %d", cov->device, dev);
+    return SDB_EINVAL;
+  }
+  return SDB_OK;
+}
+
+}  // namespace sdb
+
+using namespace sdb;
+
+extern "C" {
+
+sdb_status sdb_finest_level(uint32_t grid_bits, uint64_t eps, uint32_t* shift_out,
+                            uint32_t* level_out) {
+  uint32_t k = 0;
+  SDB_TRY(finest(grid_bits, eps, &k));
+  if (shift_out) *shift_out = k;
+  if (level_out) *level_out = grid_bits - k;
+  return SDB_OK;
+}
+
+sdb_status sdb_build_covering(const sdb_polygons* polys, uint32_t grid_bits, uint64_t eps,
+                              void* cuda_stream, sdb_covering** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return SDB_EINVAL;
+  }
+  *out = nullptr;
+  uint32_t k = 0;
+  SDB_TRY(finest(grid_bits, eps, &k));
+  if (!polys || !polys->ring_off || !polys->x || !polys->y) {
+    set_error("polygons or one of their arrays is NULL");
+    return SDB_EINVAL;
+  }
+  const uint32_t P = polys->n_polygons;
+  if (P == 0 || P >= (1u << 26)) {
+    set_error("n_polygons %u outside 1..2^26-1", P);
+    return SDB_EINVAL;
+  }
+  if (polys->ring_off[0] != 0) {
+    set_error("ring_off[0] must be 0");
+    return SDB_EINVAL;
+  }
+  for (uint32_t j = 0; j < P; ++j) {
+    if (polys->ring_off[j + 1] < polys->ring_off[j] + 3) {
+      set_error("polygon %u has fewer than 3 vertices", j);
+      return SDB_EINVAL;
+    }
+  }
+  const uint32_t V = polys->ring_off[P];
+  if (V >= 0x7fffffffu) {
+    set_error("too many vertices (%u)", V);
+    return SDB_EINVAL;
+  }
+  const uint32_t G = 1u << grid_bits;
+  for (uint32_t v = 0; v < V; ++v) {
+    if (polys->x[v] >= G || polys->y[v] >= G) {
+      set_error("vertex %u (%u, %u) outside the grid [0, 2^%u)", v, polys->x[v], polys->y[v],
+                grid_bits);
+      return SDB_EINVAL;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  sdb_covering* cov = new (std::nothrow) sdb_covering();
+  if (!cov) {
+    set_error("host allocation failed");
+    return SDB_ENOMEM;
+  }
+  if (cudaGetDevice(&cov->device) != cudaSuccess) {
+    delete cov;
+    set_error("no CUDA device");
+    return SDB_ECUDA;
+  }
+  sdb_status st = build_covering_device(polys, grid_bits, k, s, cov);
+  if (st != SDB_OK) {
+    std::string msg = sdb_last_error();
+    free_covering(cov);
+    set_error("%s", msg.c_str());
+    return st;
+  }
+  *out = cov;
+  return SDB_OK;
+}
+
+sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* info) {
+  if (!cov || !info) {
+    set_error("covering or info is NULL");
+    return SDB_EINVAL;
+  }
+  memset(info, 0, sizeof(*info));
+  info->grid_bits = cov->B;
+  info->finest_shift = cov->k;
+  info->finest_level = cov->F;
+  info->n_polygons = cov->P;
+  info->n_ranges = cov->R;
+  info->n_list_ids = cov->nids;
+  info->n_cells = cov->ncells;
+  info->device_bytes = cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) : 0);
+  info->index_leaf_bits = cov->leaf_bits;
+  return SDB_OK;
+}
+
+sdb_status sdb_covering_build_index(sdb_covering* cov, uint32_t leaf_bits, void* cuda_stream) {
+  if (!cov) {
+    set_error("covering is NULL");
+    return SDB_EINVAL;
+  }
+  if (leaf_bits < 4 || leaf_bits > 20) {
+    set_error("leaf_bits %u outside 4..20", leaf_bits);
+    return SDB_EINVAL;
+  }
+  SDB_TRY(check_device(cov));
+  return build_learned_index(cov, leaf_bits, (cudaStream_t)cuda_stream);
+}
+
+sdb_status sdb_join_aggregate(const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
+                              uint64_t n, const sdb_covering* cov, int lookup, uint64_t* d_count,
+                              int64_t* d_sum, void* cuda_stream) {
+  if (!cov || !d_count) {
+    set_error("covering or d_count is NULL");
+    return SDB_EINVAL;
+  }
+  if (n > 0 && (!d_x || !d_y)) {
+    set_error("n > 0 with NULL coordinates");
+    return SDB_EINVAL;
+  }
+  if (d_sum && !d_attr) {
+    set_error("d_sum requested without d_attr");
+    return SDB_EINVAL;
+  }
+  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED) {
+    set_error("unknown lookup %d", lookup);
+    return SDB_EINVAL;
+  }
+  if (lookup == SDB_LOOKUP_LEARNED && !cov->leaves) {
+    set_error("learned lookup requested but the covering has no index");
+    return SDB_EINVAL;
+  }
+  SDB_TRY(check_device(cov));
+  return launch_join(d_x, d_y, d_attr, n, cov, lookup, d_count, d_sum, (cudaStream_t)cuda_stream,
+                     true);
+}
+
+sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, const int32_t* h_attr,
+                                   uint64_t n, const sdb_covering* const* covs, uint32_t n_covs,
+                                   int lookup, uint64_t* h_count, int64_t* h_sum,
+                                   void* cuda_stream) {
+  if (!covs || n_covs == 0 || !h_count) {
+    set_error("coverings or h_count missing");
+    return SDB_EINVAL;
+  }
+  if (n > 0 && (!h_x || !h_y)) {
+    set_error("n > 0 with NULL coordinates");
+    return SDB_EINVAL;
+  }
+  if (h_sum && !h_attr) {
+    set_error("h_sum requested without h_attr");
+    return SDB_EINVAL;
+  }
+  const uint32_t P = covs[0] ? covs[0]->P : 0;
+  for (uint32_t c = 0; c < n_covs; ++c) {
+    if (!covs[c] || covs[c]->P != P) {
+      set_error("covering %u is NULL or has a different polygon count", c);
+      return SDB_EINVAL;
+    }
+    if (lookup == SDB_LOOKUP_LEARNED && !covs[c]->leaves) {
+      set_error("covering %u has no learned index", c);
+      return SDB_EINVAL;
+    }
+    SDB_TRY(check_device(covs[c]));
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Scratch sc(s);
+  const size_t outn = (size_t)n_covs * P;
+  uint64_t* d_cnt;
+  int64_t* d_sum = nullptr;
+  SDB_TRY(sc.get(&d_cnt, outn));
+  if (h_sum) SDB_TRY(sc.get(&d_sum, outn));
+  SDB_TRY_CUDA(cudaMemsetAsync(d_cnt, 0, outn * 8, s));
+  if (d_sum) SDB_TRY_CUDA(cudaMemsetAsync(d_sum, 0, outn * 8, s));
+  if (lookup == SDB_LOOKUP_LEARNED)
+    for (uint32_t c = 0; c < n_covs; ++c)
+      SDB_TRY_CUDA(cudaMemsetAsync(covs[c]->fallbacks, 0, sizeof(unsigned long long), s));
+  const uint64_t CH = 1ull << 24;  // points per chunk
+  const uint64_t nch = (n + CH - 1) / CH;
+  uint32_t* dx[2];
+  uint32_t* dy[2];
+  int32_t* da[2] = {nullptr, nullptr};
+  for (int b = 0; b < 2; ++b) {
+    SDB_TRY(sc.get(&dx[b], CH));
+    SDB_TRY(sc.get(&dy[b], CH));
+    if (h_sum) SDB_TRY(sc.get(&da[b], CH));
+  }
+  cudaStream_t cs;
+  SDB_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaEvent_t copied[2], done[2];
+  for (int b = 0; b < 2; ++b) {
+    cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
+  }
+  sdb_status st = SDB_OK;
+  for (uint64_t c = 0; c < nch && st == SDB_OK; ++c) {
+    const int b = (int)(c & 1);
+    const uint64_t a0 = c * CH, m = (n - a0 < CH) ? n - a0 : CH;
+    cudaError_t e = cudaSuccess;
+    if (c >= 2) e = cudaStreamWaitEvent(cs, done[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx[b], h_x + a0, m * 4, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy[b], h_y + a0, m * 4, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && h_sum)
+      e = cudaMemcpyAsync(da[b], h_attr + a0, m * 4, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[b], 0);
+    if (e != cudaSuccess) {
+      st = cuda_status(e, "chunk copy", __FILE__, __LINE__);
+      break;
+    }
+    for (uint32_t k = 0; k < n_covs && st == SDB_OK; ++k)
+      st = launch_join(dx[b], dy[b], da[b], m, covs[k], lookup, d_cnt + (size_t)k * P,
+                       d_sum ? d_sum + (size_t)k * P : nullptr, s, false);
+    if (st == SDB_OK && cudaEventRecord(done[b], s) != cudaSuccess)
+      st = cuda_status(cudaGetLastError(), "event record", __FILE__, __LINE__);
+  }
+  if (st == SDB_OK) {
+    cudaError_t e = cudaMemcpyAsync(h_count, d_cnt, outn * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_sum)
+      e = cudaMemcpyAsync(h_sum, d_sum, outn * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "result copy", __FILE__, __LINE__);
+  }
+  cudaStreamSynchronize(cs);
+  for (int b = 0; b < 2; ++b) {
+    cudaEventDestroy(copied[b]);
+    cudaEventDestroy(done[b]);
+  }
+  cudaStreamDestroy(cs);
+  return st;
+}
+
+sdb_status sdb_covering_fallbacks(const sdb_covering* cov, void* cuda_stream, uint64_t* out) {
+  if (!cov || !out) {
+    set_error("covering or out is NULL");
+    return SDB_EINVAL;
+  }
+  *out = 0;
+  if (!cov->fallbacks) return SDB_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned long long v = 0;
+  SDB_TRY_CUDA(cudaMemcpyAsync(&v, cov->fallbacks, sizeof(v), cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  *out = v;
+  return SDB_OK;
+}
+
+sdb_status sdb_covering_export(const sdb_covering* cov, uint64_t* h_start, uint32_t* h_list_off,
+                               uint32_t* h_list_ids) {
+  if (!cov || !h_start || !h_list_off || (cov->nids && !h_list_ids)) {
+    set_error("covering or an output array is NULL");
+    return SDB_EINVAL;
+  }
+  SDB_TRY(check_device(cov));
+  SDB_TRY_CUDA(cudaDeviceSynchronize());
+  SDB_TRY_CUDA(cudaMemcpy(h_start, cov->start, (cov->R + 1) * 8, cudaMemcpyDeviceToHost));
+  SDB_TRY_CUDA(cudaMemcpy(h_list_off, cov->list_off, (cov->R + 1) * 4, cudaMemcpyDeviceToHost));
+  if (cov->nids)
+    SDB_TRY_CUDA(cudaMemcpy(h_list_ids, cov->list_ids, cov->nids * 4, cudaMemcpyDeviceToHost));
+  return SDB_OK;
+}
+
+void sdb_covering_free(sdb_covering* cov) { free_covering(cov); }
+
+const char* sdb_status_string(sdb_status s) {
+  switch (s) {
+    case SDB_OK: return "ok";
+    case SDB_EINVAL: return "invalid argument";
+    case SDB_ENOMEM: return "out of memory";
+    case SDB_ECUDA: return "CUDA error";
+    case SDB_ETIMEOUT: return "timed out";
+    case SDB_EBUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+const char* sdb_last_error(void) { return g_err; }
+
+uint64_t sdb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,615 @@
+// Covering builder: the conservative hierarchical raster of Sec. 2.1-2.2,
+// linearised by the Hilbert curve and merged into disjoint id ranges (Sec. 3,
+// "Polygon Indexing").
+//
+// Level-synchronous quadtree refinement on the device.  A frontier item is a
+// cell of some polygon that meets the polygon's boundary, together with the
+// list of the polygon's edges that meet the (closed) cell, and one parity bit:
+// whether the point c+ = c + (d, d^2) (c the cell's lower-left corner, d an
+// infinitesimal) lies inside the polygon.  Expanding an item tests its four
+// children against the item's edges only (an edge meeting a child meets its
+// parent):
+//   * a child that meets an edge is a boundary cell: emitted at the finest level
+//     F, otherwise pushed to the next frontier with its own edge list;
+//   * a child that meets no edge lies wholly inside or wholly outside; its
+//     corner's parity decides, and is derived from the parent's parity by
+//     counting the parent's edges that cross the segment from the parent's
+//     corner to the child's corner (both shifted by (d, d^2)).
+// The shift makes every test point and test segment avoid every vertex and
+// edge line symbolically, so all predicates are exact integer sign tests
+// (coordinates < 2^30, products < 2^61, int64).  The root parity comes from a
+// rightward ray from (0,0)+.
+//
+// Emitted cells become (lo = h * 4^(F-L), level) records; a sweep over all
+// record endpoints (sort, unique, per-interval polygon lists, merge of equal
+// neighbours) gives the canonical ranges.
+#include "sdb_internal.cuh"
+
+#include <vector>
+
+namespace sdb {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr uint32_t NONE = 0xffffffffu;
+
+struct Edge {
+  int32_t ax, ay, bx, by;
+};
+
+struct Item {
+  uint32_t poly, cx, cy, eoff, ecnt_par;  // ecnt_par: edge count | parity << 31
+};
+
+// Closed segment vs closed axis-aligned square, exact.  Separating axes: the
+// two coordinate axes (bounding boxes) and the segment's normal (the line's
+// signed function f(p) = cross(b - a, p - a) is linear, so its extremes over
+// the square sit at the two corners picked by the signs of the direction).
+__device__ __forceinline__ bool seg_meets_square(const Edge& e, int64_t x0, int64_t y0, int64_t x1,
+                                                 int64_t y1) {
+  int64_t minx = min(e.ax, e.bx), maxx = max(e.ax, e.bx);
+  int64_t miny = min(e.ay, e.by), maxy = max(e.ay, e.by);
+  if (maxx < x0 || minx > x1 || maxy < y0 || miny > y1) return false;
+  int64_t dx = (int64_t)e.bx - e.ax, dy = (int64_t)e.by - e.ay;
+  int64_t fmax = dx * ((dx >= 0 ? y1 : y0) - e.ay) - dy * ((dy >= 0 ? x0 : x1) - e.ax);
+  int64_t fmin = dx * ((dx >= 0 ? y0 : y1) - e.ay) - dy * ((dy >= 0 ? x1 : x0) - e.ax);
+  return fmax >= 0 && fmin <= 0;
+}
+
+// Sign of cross(b - a, q+ - a) with q+ = q + (d, d^2): o - dy*d + dx*d^2.
+// Never zero for a non-degenerate edge.
+__device__ __forceinline__ int pert_side(const Edge& e, int64_t qx, int64_t qy) {
+  int64_t dx = (int64_t)e.bx - e.ax, dy = (int64_t)e.by - e.ay;
+  int64_t o = dx * (qy - e.ay) - dy * (qx - e.ax);
+  if (o != 0) return o > 0 ? 1 : -1;
+  if (dy != 0) return dy < 0 ? 1 : -1;
+  return dx > 0 ? 1 : -1;
+}
+
+// Sign of cross(q+ - r+, p - r+) for the segment r+ -> q+ (same shift on both
+// ends): o + uy*d - ux*d^2 with u = q - r != 0.
+__device__ __forceinline__ int pert_line_side(int64_t rx, int64_t ry, int64_t qx, int64_t qy,
+                                              int64_t px, int64_t py) {
+  int64_t ux = qx - rx, uy = qy - ry;
+  int64_t o = ux * (py - ry) - uy * (px - rx);
+  if (o != 0) return o > 0 ? 1 : -1;
+  if (uy != 0) return uy > 0 ? 1 : -1;
+  return ux > 0 ? -1 : 1;
+}
+
+// Does edge e cross the segment r+ -> q+ ?
+__device__ __forceinline__ uint32_t pert_cross(const Edge& e, int64_t rx, int64_t ry, int64_t qx,
+                                               int64_t qy) {
+  if (e.ax == e.bx && e.ay == e.by) return 0;
+  if (pert_side(e, rx, ry) == pert_side(e, qx, qy)) return 0;
+  return pert_line_side(rx, ry, qx, qy, e.ax, e.ay) != pert_line_side(rx, ry, qx, qy, e.bx, e.by);
+}
+
+// Does edge e cross the rightward ray from q+ ?  (integer endpoints lie above
+// the line y = qy + d^2 iff y > qy)
+__device__ __forceinline__ uint32_t pert_ray_cross(const Edge& e, int64_t qx, int64_t qy) {
+  bool ua = e.ay > qy, ub = e.by > qy;
+  if (ua == ub) return 0;
+  int sd = pert_side(e, qx, qy);
+  return (e.by > e.ay) ? (sd > 0) : (sd < 0);
+}
+
+__device__ __forceinline__ unsigned long long warp_alloc(uint32_t n, unsigned long long* ctr) {
+  int lane = threadIdx.x & 31;
+  uint32_t inc = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += t;
+  }
+  uint32_t total = __shfl_sync(FULL, inc, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(ctr, (unsigned long long)total);
+  base = __shfl_sync(FULL, base, 31);
+  return base + inc - n;
+}
+
+__global__ void build_edges_kernel(const uint32_t* __restrict__ ring_off,
+                                   const uint32_t* __restrict__ vx, const uint32_t* __restrict__ vy,
+                                   const uint32_t* __restrict__ vpoly, uint32_t V,
+                                   Edge* __restrict__ edges, uint32_t* __restrict__ elist) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  uint32_t j = vpoly[v];
+  uint32_t w = (v + 1 < ring_off[j + 1]) ? v + 1 : ring_off[j];
+  edges[v] = Edge{(int32_t)vx[v], (int32_t)vy[v], (int32_t)vx[w], (int32_t)vy[w]};
+  elist[v] = v;
+}
+
+// one warp per polygon: level-0 item (whole grid) with all edges and the
+// parity of (0,0)+
+__global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
+                                  const Edge* __restrict__ edges, uint32_t P,
+                                  Item* __restrict__ items) {
+  uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= P) return;
+  uint32_t a = ring_off[j], b = ring_off[j + 1];
+  uint32_t par = 0;
+  for (uint32_t v = a + lane; v < b; v += 32) par ^= pert_ray_cross(edges[v], 0, 0);
+  par = __popc(__ballot_sync(FULL, par)) & 1u;
+  if (lane == 0) items[j] = Item{j, 0, 0, a, (b - a) | (par << 31)};
+}
+
+__global__ __launch_bounds__(256) void expand_level_kernel(
+    const Item* __restrict__ items, uint32_t n_items, const uint32_t* __restrict__ elist,
+    const Edge* __restrict__ edges, uint32_t B, uint32_t L, uint32_t F,
+    Item* __restrict__ next_items, uint32_t* __restrict__ next_elist,
+    uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val, unsigned long long rec_base,
+    unsigned long long* __restrict__ counters) {
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  bool active = t < n_items;
+  Item it{0, 0, 0, 0, 0};
+  if (active) it = items[t];
+  const uint32_t cl = L + 1;
+  const int64_t side = (int64_t)1 << (B - cl);
+  const int64_t px = (int64_t)it.cx << (B - L), py = (int64_t)it.cy << (B - L);
+  const uint32_t ecnt = it.ecnt_par & 0x7fffffffu;
+  const uint32_t par = it.ecnt_par >> 31;
+  // children c = dy*2 + dx, lower-left corner (px + dx*side, py + dy*side)
+  uint32_t cnt[4] = {0, 0, 0, 0};
+  uint32_t flip = 0;
+  for (uint32_t i = 0; i < ecnt; ++i) {
+    const Edge e = edges[elist[it.eoff + i]];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int64_t x0 = px + (c & 1) * side, y0 = py + (c >> 1) * side;
+      cnt[c] += seg_meets_square(e, x0, y0, x0 + side, y0 + side);
+    }
+    flip ^= pert_cross(e, px, py, px + side, py) << 1;
+    flip ^= pert_cross(e, px, py, px, py + side) << 2;
+    flip ^= pert_cross(e, px, py, px + side, py + side) << 3;
+  }
+  uint32_t n_rec = 0, n_it = 0, n_ed = 0;
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint32_t inside = (par ^ (flip >> c)) & 1u;
+      if (cnt[c] > 0) {
+        if (cl == F) {
+          ++n_rec;
+        } else {
+          ++n_it;
+          n_ed += cnt[c];
+        }
+      } else if (inside) {
+        ++n_rec;
+      }
+    }
+  }
+  unsigned long long ro = warp_alloc(n_rec, &counters[2]);
+  unsigned long long io = warp_alloc(n_it, &counters[0]);
+  unsigned long long eo = warp_alloc(n_ed, &counters[1]);
+  if (!active) return;
+  uint32_t ceoff[4] = {0, 0, 0, 0};
+  const uint32_t shift = 2 * (F - cl);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint32_t ccx = 2 * it.cx + (c & 1), ccy = 2 * it.cy + (c >> 1);
+    uint32_t inside = (par ^ (flip >> c)) & 1u;
+    bool emit = (cnt[c] > 0) ? (cl == F) : (inside != 0);
+    if (emit) {
+      unsigned long long r = rec_base + ro++;
+      rec_key[r] = hilbert_id(ccx, ccy, cl) << shift;
+      rec_val[r] = it.poly | ((F - cl) << 26);
+    } else if (cnt[c] > 0) {
+      ceoff[c] = (uint32_t)eo;
+      next_items[io++] = Item{it.poly, ccx, ccy, (uint32_t)eo, cnt[c] | (inside << 31)};
+      eo += cnt[c];
+    }
+  }
+  if (n_it) {
+    uint32_t fill[4] = {0, 0, 0, 0};
+    for (uint32_t i = 0; i < ecnt; ++i) {
+      uint32_t eid = elist[it.eoff + i];
+      const Edge e = edges[eid];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (cnt[c] == 0) continue;
+        int64_t x0 = px + (c & 1) * side, y0 = py + (c >> 1) * side;
+        if (seg_meets_square(e, x0, y0, x0 + side, y0 + side)) next_elist[ceoff[c] + fill[c]++] = eid;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ range merge
+__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* __restrict__ b, uint32_t m,
+                                                    uint64_t v) {
+  uint32_t lo = 0, len = m;
+  while (len > 0) {
+    uint32_t half = len >> 1;
+    if (b[lo + half] < v) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return lo;
+}
+
+__global__ void breakpoints_kernel(const uint64_t* __restrict__ key, const uint32_t* __restrict__ val,
+                                   uint64_t n, uint64_t top, uint64_t* __restrict__ bp) {
+  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) {
+    uint32_t d = val[r] >> 26;
+    bp[2 * r] = key[r];
+    bp[2 * r + 1] = key[r] + (1ull << (2 * d));
+  } else if (r == n) {
+    bp[2 * n] = 0;
+    bp[2 * n + 1] = top;
+  }
+}
+
+__global__ void spans_kernel(const uint64_t* __restrict__ key, const uint32_t* __restrict__ val,
+                             uint64_t n, const uint64_t* __restrict__ b, uint32_t m,
+                             uint32_t* __restrict__ klo, uint32_t* __restrict__ span) {
+  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  uint32_t d = val[r] >> 26;
+  uint64_t lo = key[r], hi = lo + (1ull << (2 * d));
+  uint32_t a = lower_bound_u64(b, m, lo), c = lower_bound_u64(b, m, hi);
+  klo[r] = a;
+  span[r] = c - a;
+}
+
+// pair i belongs to the record r with poff[r] <= i < poff[r+1]
+__global__ void expand_pairs_kernel(const uint64_t* __restrict__ poff, uint64_t n,
+                                    const uint32_t* __restrict__ klo,
+                                    const uint32_t* __restrict__ val, uint64_t T, uint32_t pbits,
+                                    uint64_t* __restrict__ pairs) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T) return;
+  // last r with poff[r] <= i
+  uint64_t lo = 0, len = n;
+  while (len > 1) {
+    uint64_t half = len >> 1;
+    if (poff[lo + half] <= i) lo += half;
+    len -= half;
+  }
+  uint32_t poly = val[lo] & ((1u << 26) - 1u);
+  uint64_t k = (uint64_t)klo[lo] + (i - poff[lo]);
+  pairs[i] = (k << pbits) | poly;
+}
+
+__global__ void widen_kernel(const uint32_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ out) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i];
+}
+
+__global__ void count_len_kernel(const uint64_t* __restrict__ pairs, uint64_t T, uint32_t pbits,
+                                 uint32_t* __restrict__ len) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < T) atomicAdd(&len[pairs[i] >> pbits], 1u);
+}
+
+__global__ void new_range_kernel(const uint64_t* __restrict__ pairs, const uint32_t* __restrict__ len,
+                                 const uint32_t* __restrict__ eoff, uint32_t nint, uint64_t pmask,
+                                 uint32_t* __restrict__ flag) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nint) return;
+  uint32_t f = 1;
+  if (k > 0 && len[k] == len[k - 1]) {
+    f = 0;
+    for (uint32_t t = 0; t < len[k]; ++t) {
+      if ((pairs[eoff[k] + t] & pmask) != (pairs[eoff[k - 1] + t] & pmask)) {
+        f = 1;
+        break;
+      }
+    }
+  }
+  flag[k] = f;
+}
+
+__global__ void emit_ranges_kernel(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ ridx,
+                                   const uint64_t* __restrict__ b, const uint32_t* __restrict__ len,
+                                   const uint32_t* __restrict__ eoff, uint32_t nint,
+                                   uint64_t* __restrict__ start, uint32_t* __restrict__ rlen,
+                                   uint32_t* __restrict__ rsrc) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nint || !flag[k]) return;
+  uint32_t r = ridx[k];
+  start[r] = b[k];
+  rlen[r] = len[k];
+  rsrc[r] = eoff[k];
+}
+
+__global__ void fill_lists_kernel(const uint64_t* __restrict__ pairs, uint64_t pmask,
+                                  const uint32_t* __restrict__ rlen, const uint32_t* __restrict__ rsrc,
+                                  const uint32_t* __restrict__ list_off, uint64_t R,
+                                  uint32_t* __restrict__ list_ids, uint32_t* __restrict__ pay) {
+  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  uint32_t n = rlen[r], o = list_off[r], s = rsrc[r];
+  for (uint32_t t = 0; t < n; ++t) list_ids[o + t] = (uint32_t)(pairs[s + t] & pmask);
+  pay[r] = n == 0 ? NONE : (n == 1 ? (uint32_t)(pairs[s] & pmask) : (0x80000000u | (uint32_t)r));
+}
+
+__global__ void finish_kernel(uint64_t* start, uint32_t* list_off, uint64_t R, uint64_t top,
+                              uint32_t nids) {
+  start[R] = top;
+  list_off[R] = nids;
+}
+
+__global__ void sample_kernel(const uint64_t* __restrict__ start, uint32_t stride, uint32_t ns,
+                              uint64_t* __restrict__ sample) {
+  uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < ns) sample[j] = start[(uint64_t)j * stride];
+}
+
+__global__ void single_cell_kernel(uint64_t* key, uint32_t* val, uint32_t P) {
+  uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < P) {
+    key[j] = 0;
+    val[j] = j;
+  }
+}
+
+int bits_for(uint64_t v) {  // bits needed to represent v
+  int b = 0;
+  while (b < 64 && (v >> b)) ++b;
+  return b;
+}
+
+sdb_status read_u64(const unsigned long long* d, unsigned long long* h, int n, cudaStream_t s) {
+  SDB_TRY_CUDA(cudaMemcpyAsync(h, d, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  return SDB_OK;
+}
+
+}  // namespace
+
+// records -> canonical ranges (see the file comment)
+static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, uint32_t F, uint32_t P,
+                                cudaStream_t s, sdb_covering* cov) {
+  Scratch sc(s);
+  const uint64_t top = 1ull << (2 * F);
+  const uint64_t nbp = 2 * n + 2;
+  uint64_t *bp, *bptmp, *bps, *b;
+  SDB_TRY(sc.get(&bp, nbp));
+  SDB_TRY(sc.get(&bptmp, nbp));
+  breakpoints_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(key, val, n, top, bp);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(radix_sort_keys(bp, bptmp, nbp, bits_for(top), s, &bps));
+  SDB_TRY(sc.get(&b, nbp));
+  size_t m = 0;
+  SDB_TRY(unique_sorted(bps, nbp, b, &m, s));
+  sc.release(bp);
+  sc.release(bptmp);
+  if (m < 2 || m > 0xfffffff0ull) {
+    set_error("covering: %zu breakpoints out of range", m);
+    return SDB_EINVAL;
+  }
+  const uint32_t nint = (uint32_t)(m - 1);
+  uint32_t *klo, *span;
+  uint64_t *span64, *poff, *dT;
+  SDB_TRY(sc.get(&klo, n));
+  SDB_TRY(sc.get(&span, n));
+  SDB_TRY(sc.get(&span64, n));
+  SDB_TRY(sc.get(&poff, n));
+  SDB_TRY(sc.get(&dT, 1));
+  spans_kernel<<<grid_for(n, 256), 256, 0, s>>>(key, val, n, b, (uint32_t)m, klo, span);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  widen_kernel<<<grid_for(n, 256), 256, 0, s>>>(span, n, span64);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint64_t>(span64, poff, n, dT, s));
+  uint64_t T = 0;
+  SDB_TRY_CUDA(cudaMemcpyAsync(&T, dT, sizeof(T), cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  sc.release(span);
+  sc.release(span64);
+  if (T >= 0xffffffffull) {
+    set_error("covering: %llu (interval, polygon) pairs exceed the 32-bit list range",
+              (unsigned long long)T);
+    return SDB_ENOMEM;
+  }
+  const uint32_t pbits = (uint32_t)(bits_for(P > 1 ? P - 1 : 1));
+  const uint64_t pmask = (1ull << pbits) - 1;
+  uint64_t *pairs, *ptmp, *ps;
+  SDB_TRY(sc.get(&pairs, T));
+  SDB_TRY(sc.get(&ptmp, T));
+  if (T) {
+    expand_pairs_kernel<<<grid_for(T, 256), 256, 0, s>>>(poff, n, klo, val, T, pbits, pairs);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+  }
+  SDB_TRY(radix_sort_keys(pairs, ptmp, T, bits_for((uint64_t)nint) + (int)pbits, s, &ps));
+  uint32_t *len, *eoff, *flag, *ridx, *dR;
+  SDB_TRY(sc.get(&len, nint));
+  SDB_TRY(sc.get(&eoff, nint));
+  SDB_TRY(sc.get(&flag, nint));
+  SDB_TRY(sc.get(&ridx, nint));
+  SDB_TRY(sc.get(&dR, 1));
+  SDB_TRY_CUDA(cudaMemsetAsync(len, 0, (size_t)nint * sizeof(uint32_t), s));
+  if (T) {
+    count_len_kernel<<<grid_for(T, 256), 256, 0, s>>>(ps, T, pbits, len);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+  }
+  SDB_TRY(exclusive_scan<uint32_t>(len, eoff, nint, nullptr, s));
+  new_range_kernel<<<grid_for(nint, 256), 256, 0, s>>>(ps, len, eoff, nint, pmask, flag);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint32_t>(flag, ridx, nint, dR, s));
+  uint32_t R = 0;
+  SDB_TRY_CUDA(cudaMemcpyAsync(&R, dR, sizeof(R), cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+
+  // persistent arrays
+  SDB_TRY(dalloc_n(&cov->start, (size_t)R + 1, s));
+  SDB_TRY(dalloc_n(&cov->list_off, (size_t)R + 1, s));
+  SDB_TRY(dalloc_n(&cov->pay, (size_t)R, s));
+  uint32_t *rlen, *rsrc, *dN;
+  SDB_TRY(sc.get(&rlen, R));
+  SDB_TRY(sc.get(&rsrc, R));
+  SDB_TRY(sc.get(&dN, 1));
+  emit_ranges_kernel<<<grid_for(nint, 256), 256, 0, s>>>(flag, ridx, b, len, eoff, nint, cov->start,
+                                                         rlen, rsrc);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint32_t>(rlen, cov->list_off, R, dN, s));
+  uint32_t nids = 0;
+  SDB_TRY_CUDA(cudaMemcpyAsync(&nids, dN, sizeof(nids), cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  SDB_TRY(dalloc_n(&cov->list_ids, (size_t)nids, s));
+  fill_lists_kernel<<<grid_for(R, 256), 256, 0, s>>>(ps, pmask, rlen, rsrc, cov->list_off, R,
+                                                      cov->list_ids, cov->pay);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  finish_kernel<<<1, 1, 0, s>>>(cov->start, cov->list_off, R, top, nids);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  // shared-memory sample of the starts for the top of the binary search
+  const uint32_t SAMPLE_MAX = 2048;
+  uint64_t keys = (uint64_t)R + 1;
+  uint32_t stride = (uint32_t)((keys + SAMPLE_MAX - 1) / SAMPLE_MAX);
+  if (stride < 1) stride = 1;
+  uint32_t ns = (uint32_t)((keys + stride - 1) / stride);
+  SDB_TRY(dalloc_n(&cov->sample, ns, s));
+  sample_kernel<<<grid_for(ns, 256), 256, 0, s>>>(cov->start, stride, ns, cov->sample);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  cov->R = R;
+  cov->nids = nids;
+  cov->sample_n = ns;
+  cov->sample_stride = stride;
+  cov->bytes = ((size_t)R + 1) * 12 + (size_t)R * 4 + (size_t)nids * 4 + (size_t)ns * 8;
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  return SDB_OK;
+}
+
+sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,
+                                 sdb_covering* cov) {
+  const uint32_t P = polys->n_polygons;
+  const uint32_t V = polys->ring_off[P];
+  const uint32_t F = B - k;
+  cov->B = B;
+  cov->k = k;
+  cov->F = F;
+  cov->P = P;
+  Scratch sc(s);
+  // polygons -> device edges
+  std::vector<uint32_t> vpoly(V);
+  for (uint32_t j = 0; j < P; ++j)
+    for (uint32_t v = polys->ring_off[j]; v < polys->ring_off[j + 1]; ++v) vpoly[v] = j;
+  uint32_t *d_off, *d_x, *d_y, *d_vp, *elist;
+  Edge* edges;
+  SDB_TRY(sc.get(&d_off, P + 1));
+  SDB_TRY(sc.get(&d_x, V));
+  SDB_TRY(sc.get(&d_y, V));
+  SDB_TRY(sc.get(&d_vp, V));
+  SDB_TRY(sc.get(&edges, V));
+  SDB_TRY(sc.get(&elist, V));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_off, polys->ring_off, (P + 1) * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_x, polys->x, V * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_y, polys->y, V * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_vp, vpoly.data(), V * 4ull, cudaMemcpyHostToDevice, s));
+  build_edges_kernel<<<grid_for(V, 256), 256, 0, s>>>(d_off, d_x, d_y, d_vp, V, edges, elist);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+
+  // record buffer, grown on demand
+  uint64_t rec_cap = 1 << 20, n_rec = 0;
+  if (rec_cap < 8ull * P) rec_cap = 8ull * P;
+  uint64_t* rkey;
+  uint32_t* rval;
+  SDB_TRY(dalloc_n(&rkey, rec_cap, s));
+  SDB_TRY(dalloc_n(&rval, rec_cap, s));
+  struct Free {
+    uint64_t** k;
+    uint32_t** v;
+    cudaStream_t s;
+    ~Free() {
+      dfree(*k, s);
+      dfree(*v, s);
+    }
+  } free_recs{&rkey, &rval, s};
+
+  unsigned long long* ctr;
+  SDB_TRY(sc.get(&ctr, 3));
+  if (F == 0) {
+    single_cell_kernel<<<grid_for(P, 256), 256, 0, s>>>(rkey, rval, P);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    n_rec = P;
+  } else {
+    Item* items;
+    SDB_TRY(dalloc_n(&items, P, s));
+    root_items_kernel<<<grid_for((size_t)P * 32, 256), 256, 0, s>>>(d_off, edges, P, items);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    uint32_t* cur_el = elist;
+    bool own_el = false;
+    uint64_t n_items = P, n_edges = V;
+    for (uint32_t L = 0; L < F && n_items > 0; ++L) {
+      const bool last = (L + 1 == F);
+      // capacity: every record and every child item comes from one of 4
+      // children; every child edge entry from one (edge, child) pair
+      if (n_rec + 4 * n_items > rec_cap) {
+        uint64_t nc = rec_cap;
+        while (nc < n_rec + 4 * n_items) nc *= 2;
+        uint64_t* k2;
+        uint32_t* v2;
+        SDB_TRY(dalloc_n(&k2, nc, s));
+        SDB_TRY(dalloc_n(&v2, nc, s));
+        SDB_TRY_CUDA(cudaMemcpyAsync(k2, rkey, n_rec * 8, cudaMemcpyDeviceToDevice, s));
+        SDB_TRY_CUDA(cudaMemcpyAsync(v2, rval, n_rec * 4, cudaMemcpyDeviceToDevice, s));
+        dfree(rkey, s);
+        dfree(rval, s);
+        rkey = k2;
+        rval = v2;
+        rec_cap = nc;
+      }
+      if (4 * n_items > 0xffffffffull || 4 * n_edges > 0xffffffffull) {
+        set_error("covering: level %u frontier too large (%llu cells, %llu edge entries)", L,
+                  (unsigned long long)n_items, (unsigned long long)n_edges);
+        dfree(items, s);
+        if (own_el) dfree(cur_el, s);
+        return SDB_ENOMEM;
+      }
+      Item* nitems = nullptr;
+      uint32_t* nel = nullptr;
+      if (!last) {
+        sdb_status st = dalloc_n(&nitems, 4 * n_items, s);
+        if (st == SDB_OK) st = dalloc_n(&nel, 4 * n_edges, s);
+        if (st != SDB_OK) {
+          dfree(items, s);
+          if (own_el) dfree(cur_el, s);
+          if (nitems) dfree(nitems, s);
+          return st;
+        }
+      }
+      SDB_TRY_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
+      expand_level_kernel<<<grid_for(n_items, 256), 256, 0, s>>>(
+          items, (uint32_t)n_items, cur_el, edges, B, L, F, nitems, nel, rkey, rval, n_rec, ctr);
+      note_launch();
+      SDB_TRY_CUDA(cudaGetLastError());
+      unsigned long long h[3];
+      SDB_TRY(read_u64(ctr, h, 3, s));
+      dfree(items, s);
+      if (own_el) dfree(cur_el, s);
+      items = nitems;
+      cur_el = nel;
+      own_el = true;
+      n_items = last ? 0 : h[0];
+      n_edges = h[1];
+      n_rec += h[2];
+    }
+    if (items) dfree(items, s);
+    if (own_el && cur_el) dfree(cur_el, s);
+  }
+  cov->ncells = n_rec;
+  return merge_records(rkey, rval, n_rec, F, P, s, cov);
+}
+
+}  // namespace sdb

@@ -1,0 +1,186 @@
+// Internal definitions shared by the libsdb.so translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "sdb.h"
+
+namespace sdb {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+sdb_status cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
+#define SDB_TRY_CUDA(call)                                                     \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) return ::sdb::cuda_status(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define SDB_TRY(call)                   \
+  do {                                  \
+    sdb_status s_ = (call);             \
+    if (s_ != SDB_OK) return s_;        \
+  } while (0)
+
+// ---------------------------------------------------------------- memory
+// Stream-ordered allocations from a library-owned pool (one per device) that
+// keeps freed blocks cached, so repeated builds do not pay for cudaMalloc.
+sdb_status dalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+template <class T>
+sdb_status dalloc_n(T** p, size_t n, cudaStream_t s) {
+  return dalloc(reinterpret_cast<void**>(p), (n ? n : 1) * sizeof(T), s);
+}
+
+// RAII holder for temporaries of one call (freed on the call's stream).
+struct Scratch {
+  cudaStream_t s;
+  void* ptrs[64];
+  int n = 0;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (int i = 0; i < n; ++i) dfree(ptrs[i], s);
+  }
+  template <class T>
+  sdb_status get(T** p, size_t count) {
+    if (n >= 64) {
+      set_error("internal: scratch slots exhausted");
+      return SDB_ENOMEM;
+    }
+    SDB_TRY(dalloc_n(p, count, s));
+    ptrs[n++] = *p;
+    return SDB_OK;
+  }
+  // release one early (must have come from this scratch)
+  void release(void* p) {
+    for (int i = 0; i < n; ++i)
+      if (ptrs[i] == p) {
+        dfree(p, s);
+        ptrs[i] = ptrs[--n];
+        return;
+      }
+  }
+};
+
+int num_sms();
+
+// count of kernels this library has launched in the process (all devices)
+void note_launch();
+
+// ---------------------------------------------------------------- Hilbert curve
+// Quadrant-digit Hilbert curve whose order-1 visit order is (0,0), (0,1), (1,1),
+// (1,0).  Scanning levels from the top, the orientation inherited by the lower
+// levels is one of four symmetries of the square: identity, transpose,
+// anti-transpose, rotation by 180 degrees.  They form a Klein four-group, so the
+// orientation is two bits (swap, complement) and composing orientations is XOR.
+// Under orientation (sw, cm) the raw bits (xb, yb) of a level read as
+//   xt = (sw ? yb : xb) ^ cm,  yt = (sw ? xb : yb) ^ cm,
+// the level's digit is 2*xt + (xt ^ yt), and quadrant (0,0) contributes a
+// transpose (sw ^= 1) while quadrant (1,0) contributes an anti-transpose
+// (sw ^= 1, cm ^= 1).
+__host__ __device__ inline uint64_t hilbert_id(uint32_t x, uint32_t y, uint32_t order) {
+  uint64_t d = 0;
+  uint32_t sw = 0, cm = 0;
+  for (int lev = (int)order - 1; lev >= 0; --lev) {
+    uint32_t xb = (x >> lev) & 1u, yb = (y >> lev) & 1u;
+    uint32_t xt = (sw ? yb : xb) ^ cm, yt = (sw ? xb : yb) ^ cm;
+    d = (d << 2) | ((xt << 1) | (xt ^ yt));
+    if (!yt) {
+      sw ^= 1u;
+      cm ^= xt;
+    }
+  }
+  return d;
+}
+
+// Four levels per step: entry [state*256 + xnib*16 + ynib] = 8 digit bits in
+// bits 0..7 (first level highest) and the next state (sw*2 + cm) in bits 8..9.
+struct HilbertLut {
+  uint16_t e[1024];
+};
+void make_hilbert_lut(HilbertLut* t);
+
+// ---------------------------------------------------------------- covering
+// One leaf of the learned range index, 32 bytes (one DRAM sector).  The leaf
+// receives the ids h in [base, next leaf's base); its ranges are first..last.
+// Prediction: first + floor(fma(a, float(h - base), b)) in FP32; the true range
+// lies in [pred - errlo, pred + errhi] for every id the leaf receives.
+struct LeafRec {
+  uint64_t base;
+  float a, b;
+  uint32_t first, last;
+  int32_t errlo, errhi;
+};
+
+__device__ __forceinline__ int64_t leaf_predict(const LeafRec& l, uint64_t h) {
+  float x = __ull2float_rn(h - l.base);
+  float pos = __fmaf_rn(l.a, x, l.b);
+  return (int64_t)l.first + (int64_t)__float2ll_rd(pos);
+}
+
+__device__ __forceinline__ uint32_t root_leaf(float ra, float rb, uint32_t nleaves, uint64_t h) {
+  int v = __float2int_rd(__fmaf_rn(ra, __ull2float_rn(h), rb));
+  v = v < 0 ? 0 : v;
+  return (uint32_t)v >= nleaves ? nleaves - 1 : (uint32_t)v;
+}
+
+}  // namespace sdb
+
+struct sdb_covering {
+  int device = 0;
+  uint32_t B = 0, k = 0, F = 0, P = 0;
+  uint64_t R = 0, nids = 0, ncells = 0;
+  // canonical form
+  uint64_t* start = nullptr;     // R+1
+  uint32_t* list_off = nullptr;  // R+1
+  uint32_t* list_ids = nullptr;  // nids
+  // lookup acceleration
+  uint32_t* pay = nullptr;       // R: 0xFFFFFFFF empty, <2^31 single polygon, else 2^31|r
+  uint64_t* sample = nullptr;    // sample_n keys start[j * sample_stride]
+  uint32_t sample_n = 0, sample_stride = 1;
+  // learned index
+  uint32_t leaf_bits = 0;
+  float root_a = 0.f, root_b = 0.f;        // leaf = clamp(floor(root_a * float(h) + root_b))
+  sdb::LeafRec* leaves = nullptr;          // 2^leaf_bits
+  unsigned long long* fallbacks = nullptr; // device counter
+  size_t bytes = 0;
+};
+
+namespace sdb {
+
+// cover.cu
+sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,
+                                 sdb_covering* cov);
+// learned.cu
+sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream_t s);
+// join.cu
+// zero = true: outputs (and the fallback counter) are cleared first;
+// zero = false: the launch adds into them (chunked joins)
+sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr, uint64_t n,
+                       const sdb_covering* cov, int lookup, uint64_t* count, int64_t* sum,
+                       cudaStream_t s, bool zero);
+
+// sort.cu: device-wide primitives
+template <class T>
+sdb_status exclusive_scan(const T* in, T* out, size_t n, T* d_total, cudaStream_t s);
+sdb_status radix_sort_keys(uint64_t* keys, uint64_t* tmp, size_t n, int bits, cudaStream_t s,
+                           uint64_t** result);
+sdb_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp,
+                            size_t n, int bits, cudaStream_t s, uint64_t** kres, uint32_t** vres);
+// unique of a sorted array: writes out[0..m), returns m via host sync
+sdb_status unique_sorted(const uint64_t* in, size_t n, uint64_t* out, size_t* m, cudaStream_t s);
+
+inline unsigned grid_for(size_t n, unsigned block) {
+  size_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 0x7fffffffu) g = 0x7fffffffu;
+  return (unsigned)g;
+}
+
+}  // namespace sdb

@@ -1,0 +1,286 @@
+// Device-wide primitives used by the covering builder: exclusive scan,
+// stable LSD radix sort of uint64 keys (optionally carrying uint32 values),
+// and unique of a sorted array.  Hand-written; no library sort.
+#include "sdb_internal.cuh"
+
+namespace sdb {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------------ scan
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <class T>
+__device__ T block_exclusive_scan(T v, T* s_warp, T* total) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    T ws = lane < (SCAN_THREADS / 32) ? s_warp[lane] : T(0);
+    T wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T t = __shfl_up_sync(FULL, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < (SCAN_THREADS / 32)) s_warp[lane] = wi - ws;
+    if (lane == (SCAN_THREADS / 32) - 1) s_warp[SCAN_THREADS / 32] = wi;
+  }
+  __syncthreads();
+  T r = s_warp[w] + inc - v;
+  *total = s_warp[SCAN_THREADS / 32];
+  __syncthreads();
+  return r;
+}
+
+template <class T>
+__global__ __launch_bounds__(SCAN_THREADS) void scan_reduce_kernel(const T* in, size_t n, T* sums) {
+  __shared__ T s_warp[SCAN_THREADS / 32 + 1];
+  size_t base = (size_t)blockIdx.x * SCAN_TILE;
+  T acc = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    size_t g = base + (size_t)i * SCAN_THREADS + threadIdx.x;
+    if (g < n) acc += in[g];
+  }
+  T tot;
+  block_exclusive_scan<T>(acc, s_warp, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ __launch_bounds__(SCAN_THREADS) void scan_tile_kernel(const T* in, T* out, size_t n,
+                                                                 const T* block_off, T* d_total) {
+  __shared__ T s_warp[SCAN_THREADS / 32 + 1];
+  size_t base = (size_t)blockIdx.x * SCAN_TILE + (size_t)threadIdx.x * SCAN_ITEMS;
+  T v[SCAN_ITEMS];
+  T acc = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    size_t g = base + i;
+    v[i] = g < n ? in[g] : T(0);
+    acc += v[i];
+  }
+  T tot;
+  T pre = block_exclusive_scan<T>(acc, s_warp, &tot);
+  T off = (block_off ? block_off[blockIdx.x] : T(0)) + pre;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    size_t g = base + i;
+    if (g < n) out[g] = off;
+    off += v[i];
+  }
+  if (d_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) {
+    *d_total = off;  // last thread holds the grand total after its items
+  }
+}
+
+// ------------------------------------------------------------------ radix sort
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;  // per lane
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+__global__ __launch_bounds__(RS_THREADS) void radix_hist_kernel(const uint64_t* __restrict__ keys,
+                                                                size_t n, int shift,
+                                                                uint32_t* __restrict__ hist,
+                                                                uint32_t nblocks) {
+  __shared__ uint32_t h[RS_WARPS][256];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&h[0][0])[i] = 0;
+  __syncthreads();
+  size_t base = (size_t)blockIdx.x * RS_TILE + (size_t)w * (32 * RS_ITEMS);
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    size_t g = base + (size_t)it * 32 + lane;
+    uint32_t d = g < n ? (uint32_t)((keys[g] >> shift) & 255u) : 256u;
+    unsigned peers = __match_any_sync(FULL, d);
+    if (d < 256u && lane == __ffs(peers) - 1) h[w][d] += __popc(peers);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+    uint32_t t = 0;
+    for (int ww = 0; ww < RS_WARPS; ++ww) t += h[ww][d];
+    hist[(size_t)d * nblocks + blockIdx.x] = t;
+  }
+}
+
+template <bool VALS>
+__global__ __launch_bounds__(RS_THREADS) void radix_scatter_kernel(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ offs,
+    uint32_t nblocks) {
+  __shared__ uint32_t cnt[RS_WARPS][256];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
+  __syncthreads();
+  size_t base = (size_t)blockIdx.x * RS_TILE + (size_t)w * (32 * RS_ITEMS);
+  unsigned lt = (1u << lane) - 1u;
+  uint64_t k[RS_ITEMS];
+  uint32_t v[RS_ITEMS];
+  uint32_t rank[RS_ITEMS];
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    size_t g = base + (size_t)it * 32 + lane;
+    bool ok = g < n;
+    k[it] = ok ? kin[g] : 0ull;
+    if (VALS) v[it] = ok ? vin[g] : 0u;
+    uint32_t d = ok ? (uint32_t)((k[it] >> shift) & 255u) : 256u;
+    unsigned peers = __match_any_sync(FULL, d);
+    uint32_t before = ok ? cnt[w][d] : 0u;
+    __syncwarp();
+    if (ok && lane == __ffs(peers) - 1) cnt[w][d] = before + __popc(peers);
+    __syncwarp();
+    rank[it] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+    uint32_t run = offs[(size_t)d * nblocks + blockIdx.x];
+    for (int ww = 0; ww < RS_WARPS; ++ww) {
+      uint32_t t = cnt[ww][d];
+      cnt[ww][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    size_t g = base + (size_t)it * 32 + lane;
+    if (g < n) {
+      uint32_t d = (uint32_t)((k[it] >> shift) & 255u);
+      uint32_t pos = cnt[w][d] + rank[it];
+      kout[pos] = k[it];
+      if (VALS) vout[pos] = v[it];
+    }
+  }
+}
+
+template <bool VALS>
+sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp, size_t n,
+                           int bits, cudaStream_t s, uint64_t** kres, uint32_t** vres) {
+  *kres = keys;
+  if (VALS) *vres = vals;
+  if (n <= 1 || bits <= 0) return SDB_OK;
+  if (n >= 0xffffffffull) {
+    set_error("radix sort: %zu elements exceeds the 32-bit rank range", n);
+    return SDB_EINVAL;
+  }
+  uint32_t nblocks = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
+  Scratch sc(s);
+  uint32_t *hist, *offs;
+  SDB_TRY(sc.get(&hist, (size_t)256 * nblocks));
+  SDB_TRY(sc.get(&offs, (size_t)256 * nblocks));
+  uint64_t *ka = keys, *kb = ktmp;
+  uint32_t *va = vals, *vb = vtmp;
+  for (int shift = 0; shift < bits; shift += 8) {
+    radix_hist_kernel<<<nblocks, RS_THREADS, 0, s>>>(ka, n, shift, hist, nblocks);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    SDB_TRY(exclusive_scan<uint32_t>(hist, offs, (size_t)256 * nblocks, nullptr, s));
+    radix_scatter_kernel<VALS><<<nblocks, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, offs, nblocks);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    uint64_t* t = ka;
+    ka = kb;
+    kb = t;
+    uint32_t* u = va;
+    va = vb;
+    vb = u;
+  }
+  *kres = ka;
+  if (VALS) *vres = va;
+  return SDB_OK;
+}
+
+__global__ void flag_new_kernel(const uint64_t* in, size_t n, uint32_t* flags) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flags[i] = (i == 0 || in[i] != in[i - 1]) ? 1u : 0u;
+}
+
+__global__ void compact_flagged_kernel(const uint64_t* in, size_t n, const uint32_t* flags,
+                                       const uint32_t* pos, uint64_t* out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flags[i]) out[pos[i]] = in[i];
+}
+
+}  // namespace
+
+template <class T>
+sdb_status exclusive_scan(const T* in, T* out, size_t n, T* d_total, cudaStream_t s) {
+  if (n == 0) {
+    if (d_total) SDB_TRY_CUDA(cudaMemsetAsync(d_total, 0, sizeof(T), s));
+    return SDB_OK;
+  }
+  size_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nb == 1) {
+    scan_tile_kernel<T><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, d_total);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    return SDB_OK;
+  }
+  Scratch sc(s);
+  T *sums, *soff;
+  SDB_TRY(sc.get(&sums, nb));
+  SDB_TRY(sc.get(&soff, nb));
+  scan_reduce_kernel<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<T>(sums, soff, nb, nullptr, s));
+  scan_tile_kernel<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, soff, d_total);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  return SDB_OK;
+}
+
+template sdb_status exclusive_scan<uint32_t>(const uint32_t*, uint32_t*, size_t, uint32_t*, cudaStream_t);
+template sdb_status exclusive_scan<uint64_t>(const uint64_t*, uint64_t*, size_t, uint64_t*, cudaStream_t);
+
+sdb_status radix_sort_keys(uint64_t* keys, uint64_t* tmp, size_t n, int bits, cudaStream_t s,
+                           uint64_t** result) {
+  uint32_t* dummy = nullptr;
+  return radix_sort_impl<false>(keys, nullptr, tmp, nullptr, n, bits, s, result, &dummy);
+}
+
+sdb_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp, size_t n,
+                            int bits, cudaStream_t s, uint64_t** kres, uint32_t** vres) {
+  return radix_sort_impl<true>(keys, vals, ktmp, vtmp, n, bits, s, kres, vres);
+}
+
+sdb_status unique_sorted(const uint64_t* in, size_t n, uint64_t* out, size_t* m, cudaStream_t s) {
+  if (n == 0) {
+    *m = 0;
+    return SDB_OK;
+  }
+  if (n >= 0xffffffffull) {
+    set_error("unique: %zu elements exceeds the 32-bit index range", n);
+    return SDB_EINVAL;
+  }
+  Scratch sc(s);
+  uint32_t *flags, *pos, *tot;
+  SDB_TRY(sc.get(&flags, n));
+  SDB_TRY(sc.get(&pos, n));
+  SDB_TRY(sc.get(&tot, 1));
+  flag_new_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, n, flags);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint32_t>(flags, pos, n, tot, s));
+  compact_flagged_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, n, flags, pos, out);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  uint32_t h = 0;
+  SDB_TRY_CUDA(cudaMemcpyAsync(&h, tot, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  *m = h;
+  return SDB_OK;
+}
+
+}  // namespace sdb

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libsdb.so (C ABI in include/sdb.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Device arrays are passed as torch CUDA tensors (their data
+pointers), streams as torch streams; PyTorch provides device memory and
+streams, nothing else.  If libsdb.so is missing the import fails: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsdb.so")
+
+SDB_OK, SDB_EINVAL, SDB_ENOMEM, SDB_ECUDA, SDB_ETIMEOUT, SDB_EBUSY = range(6)
+LOOKUP_BINARY, LOOKUP_LEARNED = 0, 1
+
+
+class SdbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sdb status {status}: {msg}")
+        self.status = status
+
+
+class _Polys(C.Structure):
+    _fields_ = [("n_polygons", C.c_uint32), ("ring_off", C.c_void_p), ("x", C.c_void_p),
+                ("y", C.c_void_p)]
+
+
+class CoveringInfo(C.Structure):
+    _fields_ = [("grid_bits", C.c_uint32), ("finest_shift", C.c_uint32),
+                ("finest_level", C.c_uint32), ("n_polygons", C.c_uint32),
+                ("n_ranges", C.c_uint64), ("n_list_ids", C.c_uint64), ("n_cells", C.c_uint64),
+                ("device_bytes", C.c_uint64), ("index_leaf_bits", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, U32, U64, I = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+        sig = {
+            "sdb_finest_level": ([U32, U64, P, P], I),
+            "sdb_build_covering": ([P, U32, U64, P, P], I),
+            "sdb_covering_get_info": ([P, P], I),
+            "sdb_covering_build_index": ([P, U32, P], I),
+            "sdb_join_aggregate": ([P, P, P, U64, P, I, P, P, P], I),
+            "sdb_join_aggregate_host": ([P, P, P, U64, P, U32, I, P, P, P], I),
+            "sdb_covering_fallbacks": ([P, P, P], I),
+            "sdb_covering_export": ([P, P, P, P], I),
+            "sdb_covering_free": ([P], None),
+            "sdb_status_string": ([I], C.c_char_p),
+            "sdb_last_error": ([], C.c_char_p),
+            "sdb_launch_count": ([], U64),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != SDB_OK:
+        raise SdbError(st, lib().sdb_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, itemsize: int):
+    """Device pointer of a contiguous CUDA tensor with the given element size
+    (uint32/int32 point arrays: 4; uint64/int64 outputs: 8)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous CUDA tensors")
+    if t.element_size() != itemsize:
+        raise ValueError(f"expected {itemsize}-byte elements, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def finest_level(grid_bits: int, eps: int) -> tuple[int, int]:
+    """(k, F): finest side 2^k, finest level F (Sec. 2.2)."""
+    k, F = C.c_uint32(), C.c_uint32()
+    _check(lib().sdb_finest_level(grid_bits, int(eps), C.byref(k), C.byref(F)))
+    return k.value, F.value
+
+
+class Covering:
+    """Device-resident covering (owns the library handle)."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> CoveringInfo:
+        inf = CoveringInfo()
+        _check(lib().sdb_covering_get_info(self._h, C.byref(inf)))
+        return inf
+
+    def free(self):
+        if self._h and self._h.value:
+            lib().sdb_covering_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_covering(polys, grid_bits: int, eps: int, stream=None) -> Covering:
+    """sdb_build_covering: polys has ring_off/x/y uint32 numpy arrays."""
+    off = np.ascontiguousarray(polys.ring_off, np.uint32)
+    x = np.ascontiguousarray(polys.x, np.uint32)
+    y = np.ascontiguousarray(polys.y, np.uint32)
+    sp = _Polys(len(off) - 1, _np_ptr(off), _np_ptr(x), _np_ptr(y))
+    out = C.c_void_p()
+    _check(lib().sdb_build_covering(C.byref(sp), grid_bits, int(eps), _stream(stream), C.byref(out)))
+    return Covering(out.value)
+
+
+def covering_build_index(cov: Covering, leaf_bits: int, stream=None):
+    _check(lib().sdb_covering_build_index(cov.handle, leaf_bits, _stream(stream)))
+
+
+def join_aggregate(x, y, attr, cov: Covering, lookup: int, count, sum_=None, stream=None):
+    """sdb_join_aggregate on device tensors (uint32 x/y, int32 attr, int64 outputs)."""
+    n = x.numel() if x is not None else 0
+    _check(lib().sdb_join_aggregate(_dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), n, cov.handle,
+                                    lookup, _dptr(count, 8), _dptr(sum_, 8), _stream(stream)))
+
+
+def join_aggregate_host(x, y, attr, covs, lookup: int, stream=None):
+    """sdb_join_aggregate_host on numpy arrays; returns (count, sum) of shape
+    (len(covs), P) as uint64 / int64 numpy arrays."""
+    x = np.ascontiguousarray(x, np.uint32)
+    y = np.ascontiguousarray(y, np.uint32)
+    a = None if attr is None else np.ascontiguousarray(attr, np.int32)
+    P = covs[0].info().n_polygons
+    arr = (C.c_void_p * len(covs))(*[c.handle.value for c in covs])
+    cnt = np.zeros((len(covs), P), np.uint64)
+    sm = None if a is None else np.zeros((len(covs), P), np.int64)
+    _check(lib().sdb_join_aggregate_host(_np_ptr(x), _np_ptr(y), _np_ptr(a), len(x), arr,
+                                         len(covs), lookup, _np_ptr(cnt), _np_ptr(sm),
+                                         _stream(stream)))
+    return cnt, sm
+
+
+def join_aggregate_host_ptrs(x_ptr: int, y_ptr: int, attr_ptr: int | None, n: int, covs,
+                             lookup: int, count_ptr: int, sum_ptr: int | None, stream=None):
+    """sdb_join_aggregate_host on raw host pointers (e.g. pinned torch tensors)."""
+    arr = (C.c_void_p * len(covs))(*[c.handle.value for c in covs])
+    _check(lib().sdb_join_aggregate_host(C.c_void_p(x_ptr), C.c_void_p(y_ptr),
+                                         C.c_void_p(attr_ptr) if attr_ptr else None, n, arr,
+                                         len(covs), lookup, C.c_void_p(count_ptr),
+                                         C.c_void_p(sum_ptr) if sum_ptr else None,
+                                         _stream(stream)))
+
+
+def covering_fallbacks(cov: Covering, stream=None) -> int:
+    v = C.c_uint64()
+    _check(lib().sdb_covering_fallbacks(cov.handle, _stream(stream), C.byref(v)))
+    return v.value
+
+
+def covering_export(cov: Covering):
+    """(start uint64[R+1], list_off uint32[R+1], list_ids uint32[nids])."""
+    inf = cov.info()
+    start = np.empty(inf.n_ranges + 1, np.uint64)
+    loff = np.empty(inf.n_ranges + 1, np.uint32)
+    ids = np.empty(max(inf.n_list_ids, 1), np.uint32)
+    _check(lib().sdb_covering_export(cov.handle, _np_ptr(start), _np_ptr(loff), _np_ptr(ids)))
+    return start, loff, ids[:inf.n_list_ids]
+
+
+def launch_count() -> int:
+    """Kernels launched by libsdb.so in this process so far."""
+    return int(lib().sdb_launch_count())
+
+
+def status_string(st: int) -> str:
+    return lib().sdb_status_string(st).decode()

@@ -18,3 +18,21 @@ def orc():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def sdblib():
+    """The CUDA library (built in-tree if missing)."""
+    from paper_2010_12548_gb300 import build, sdb
+    if not os.path.exists(sdb.LIB_PATH):
+        build.build()
+    sdb.lib()
+    return sdb
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test collected without a CUDA device")
+    return torch
