@@ -131,8 +131,8 @@ sdb_status sdb_covering_build_index(sdb_covering *cov, uint32_t leaf_bits, void 
  * results.  d_count and d_sum (P entries each) are zeroed by the call.
  * d_x, d_y, d_attr: n device values (SoA).  d_attr and d_sum may be NULL
  * (COUNT only).  n = 0 just zeroes the outputs.  Asynchronous.
- * SDB_EINVAL: null cov/d_count, n > 0 with null d_x/d_y, d_sum without d_attr,
- * learned lookup without an index. */
+ * SDB_EINVAL: null cov/d_count, n > 0 with null d_x/d_y, n > 0 with d_sum but no
+ * d_attr, learned lookup without an index. */
 sdb_status sdb_join_aggregate(const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
                               uint64_t n, const sdb_covering *cov, int lookup,
                               uint64_t *d_count, int64_t *d_sum, void *cuda_stream);

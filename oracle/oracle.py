@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 from dataclasses import dataclass
 
@@ -24,11 +25,17 @@ HILBERT, ZORDER = 0, 1
 
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (g++, plain C++17)."""
+    stamp = LIB + ".arch"
+    arch = platform.machine()
+    if not os.path.exists(stamp) or open(stamp).read().strip() != arch:
+        force = True
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
                                SRC, "-o", tmp])
         os.replace(tmp, LIB)
+        with open(stamp, "w") as f:
+            f.write(arch)
     return LIB
 
 

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -40,6 +41,10 @@ def _stale(obj: str, src: str) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "ARCH")
+    arch = platform.machine()
+    if not os.path.exists(stamp) or open(stamp).read().strip() != arch:
+        force = True  # objects from another host architecture
     nv = nvcc()
     objs, jobs = [], []
     for src in SOURCES:
@@ -60,6 +65,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         tmp = OUT + f".tmp{os.getpid()}"
         run([nv, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
         os.replace(tmp, OUT)
+    with open(stamp, "w") as f:
+        f.write(arch)
     return OUT
 
 

@@ -249,7 +249,7 @@ sdb_status sdb_join_aggregate(const uint32_t* d_x, const uint32_t* d_y, const in
     set_error("n > 0 with NULL coordinates");
     return SDB_EINVAL;
   }
-  if (d_sum && !d_attr) {
+  if (d_sum && !d_attr && n > 0) {
     set_error("d_sum requested without d_attr");
     return SDB_EINVAL;
   }
@@ -278,7 +278,7 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
     set_error("n > 0 with NULL coordinates");
     return SDB_EINVAL;
   }
-  if (h_sum && !h_attr) {
+  if (h_sum && !h_attr && n > 0) {
     set_error("h_sum requested without h_attr");
     return SDB_EINVAL;
   }
