@@ -149,6 +149,32 @@ sdb_status sdb_join_aggregate_host(const uint32_t *h_x, const uint32_t *h_y, con
                                    int lookup, uint64_t *h_count, int64_t *h_sum,
                                    void *cuda_stream);
 
+/* Allocation-free variant of sdb_join_aggregate_host for one covering.  The paper
+ * has no counterpart: this serves callers that cannot allocate device memory
+ * while they call in -- code running while a CUDA stream capture is active
+ * (allocation is not permitted during capture), services that reserve their
+ * whole device-memory budget up front and forbid later allocations, and plugins
+ * inside a process whose own allocator owns the device.
+ *
+ * Staging buffers and per-polygon accumulators live in one file-scope device
+ * array of SDB_NOALLOC_CHUNK * 12 + SDB_NOALLOC_MAX_POLYGONS * 16 bytes (13 MiB)
+ * that every GPU which loads the library holds until the process exits.  The
+ * call makes no cudaMalloc/cudaFree or other allocating call; it streams the
+ * points SDB_NOALLOC_CHUNK at a time on cuda_stream alone and synchronises it
+ * before returning (results in h_count/h_sum, P entries each).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every
+ * call shares the array and clears the accumulators itself; calls whose GPU work
+ * overlaps (other streams or threads) race on it.
+ * SDB_EINVAL: more than SDB_NOALLOC_MAX_POLYGONS polygons, and the argument
+ * errors of sdb_join_aggregate_host. */
+#define SDB_NOALLOC_CHUNK (1u << 20)
+#define SDB_NOALLOC_MAX_POLYGONS (1u << 16)
+sdb_status sdb_join_aggregate_host_noalloc(const uint32_t *h_x, const uint32_t *h_y,
+                                           const int32_t *h_attr, uint64_t n,
+                                           const sdb_covering *cov, int lookup, uint64_t *h_count,
+                                           int64_t *h_sum, void *cuda_stream);
+
 /* Number of learned-index lookups of the covering's most recent learned join
  * whose bounded search missed and fell back to binary search.  Synchronises
  * cuda_stream. */

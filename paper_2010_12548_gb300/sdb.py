@@ -62,6 +62,7 @@ def lib():
             "sdb_status_string": ([I], C.c_char_p),
             "sdb_last_error": ([], C.c_char_p),
             "sdb_launch_count": ([], U64),
+            "sdb_join_aggregate_host_noalloc": ([P, P, P, U64, P, I, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -182,6 +183,22 @@ def join_aggregate_host_ptrs(x_ptr: int, y_ptr: int, attr_ptr: int | None, n: in
                                          len(covs), lookup, C.c_void_p(count_ptr),
                                          C.c_void_p(sum_ptr) if sum_ptr else None,
                                          _stream(stream)))
+
+
+def join_aggregate_host_noalloc(x, y, attr, cov: Covering, lookup: int, stream=None):
+    """sdb_join_aggregate_host_noalloc on numpy arrays: the host-buffer join for
+    callers that cannot allocate device memory (see include/sdb.h); returns
+    (count, sum) of shape (P,) as uint64 / int64 numpy arrays."""
+    x = np.ascontiguousarray(x, np.uint32)
+    y = np.ascontiguousarray(y, np.uint32)
+    a = None if attr is None else np.ascontiguousarray(attr, np.int32)
+    P = cov.info().n_polygons
+    cnt = np.zeros(P, np.uint64)
+    sm = None if a is None else np.zeros(P, np.int64)
+    _check(lib().sdb_join_aggregate_host_noalloc(_np_ptr(x), _np_ptr(y), _np_ptr(a), len(x),
+                                                 cov.handle, lookup, _np_ptr(cnt), _np_ptr(sm),
+                                                 _stream(stream)))
+    return cnt, sm
 
 
 def covering_fallbacks(cov: Covering, stream=None) -> int:
