@@ -7,8 +7,9 @@ attribute), the 263-zone jittered Voronoi tiling (20-400 vertices), and the
 eps sweep {2^12, 2^10, 2^8, 2^6}.
 
 One step = for every eps of the sweep: build the covering from the polygons
-(host arrays), fit the learned index (2^12 leaves), and join all points with
-the learned lookup into per-polygon COUNT and SUM (device-resident points).
+(host arrays), fit the learned index (leaves for ~16 ranges each within
+2^12..2^16), and join all points with the learned lookup into per-polygon COUNT
+and SUM (device-resident points).
 The metric counts point-joins: points x eps levels per second.
 
 Besides the timed steps the script measures, outside the timed region, the
@@ -38,7 +39,13 @@ if ROOT not in sys.path:
 
 METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query latency"
 UNIT = "points/s"
-LEAF_BITS = 12
+LEAF_BITS_RANGE = (12, 16)
+
+
+def leaf_bits_for(n_ranges: int) -> int:
+    """Leaves for about 16 ranges each, within 2^12..2^16."""
+    b = max(1, int(n_ranges) // 16).bit_length()
+    return min(LEAF_BITS_RANGE[1], max(LEAF_BITS_RANGE[0], b))
 
 
 def parse():
@@ -206,9 +213,9 @@ def run_reference(args):
 
 
 def config_of(w, n_points):
-    return {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64_learned2^12",
+    return {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64_learned",
             "points": n_points, "polygons": w.polygons.n, "grid_bits": 24, "eps": w.eps,
-            "leaf_bits": LEAF_BITS, "lookup": "learned",
+            "leaf_bits": "ranges/16 within 2^12..2^16", "lookup": "learned",
             "l2": "inputs larger than L2 (point arrays 12 B/pt)"}
 
 
@@ -244,7 +251,7 @@ def main():
             if events is not None:
                 events[i][0].record(stream)
             c = sdb.build_covering(w.polygons, 24, eps, stream)
-            sdb.covering_build_index(c, LEAF_BITS, stream)
+            sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
             if events is not None:
                 events[i][1].record(stream)
             sdb.join_aggregate(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], sm[i], stream)
@@ -292,10 +299,18 @@ def main():
         reps = 5
         for i, eps in enumerate(w.eps):
             c = sdb.build_covering(w.polygons, 24, eps, stream)
-            sdb.covering_build_index(c, LEAF_BITS, stream)
             inf = c.info()
             row = {"ranges": inf.n_ranges, "cells": inf.n_cells, "covering_bytes": inf.device_bytes}
-            for name, lk in (("binary", sdb.LOOKUP_BINARY), ("learned", sdb.LOOKUP_LEARNED)):
+            variants = [("binary", sdb.LOOKUP_BINARY, None)]
+            lb = leaf_bits_for(inf.n_ranges)
+            for bits in sorted({12, lb}):
+                variants.append((f"learned{bits}", sdb.LOOKUP_LEARNED, bits))
+            for name, lk, bits in variants:
+                if bits is not None:
+                    sdb.covering_build_index(c, bits, stream)
+                    mw, xw = sdb.covering_index_stats(c)
+                    row[name + "_window_mean"] = mw
+                    row[name + "_window_max"] = xw
                 sdb.join_aggregate(x, y, a, c, lk, cnt[i], sm[i], stream)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
@@ -307,7 +322,11 @@ def main():
                 jm = e0.elapsed_time(e1) / reps
                 row[name + "_ms"] = jm
                 row[name + "_pts_per_s"] = N / (jm / 1e3)
-            row["fallbacks"] = sdb.covering_fallbacks(c, stream)
+                if bits is not None:
+                    row[name + "_fallbacks"] = sdb.covering_fallbacks(c, stream)
+            row["learned_ms"] = row[f"learned{lb}_ms"]
+            row["learned_pts_per_s"] = row[f"learned{lb}_pts_per_s"]
+            row["leaf_bits"] = lb
             joins[str(eps)] = row
             c.free()
         res["join_only"] = joins
@@ -333,7 +352,7 @@ def main():
             covs = []
             for eps in w.eps:
                 c = sdb.build_covering(w.polygons, 24, eps, stream)
-                sdb.covering_build_index(c, LEAF_BITS, stream)
+                sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
                 covs.append(c)
             sdb.join_aggregate_host_ptrs(hx.data_ptr(), hy.data_ptr(), ha.data_ptr(), N, covs,
                                          sdb.LOOKUP_LEARNED, hc.data_ptr(), hs.data_ptr(), stream)

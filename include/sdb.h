@@ -180,6 +180,11 @@ sdb_status sdb_join_aggregate_host_noalloc(const uint32_t *h_x, const uint32_t *
  * cuda_stream. */
 sdb_status sdb_covering_fallbacks(const sdb_covering *cov, void *cuda_stream, uint64_t *out);
 
+/* Learned-index window sizes (errlo + errhi + 1 per leaf): mean weighted by the
+ * ranges each leaf spans, and maximum.  Zeros without an index.  Synchronous. */
+sdb_status sdb_covering_index_stats(const sdb_covering *cov, double *mean_window,
+                                    uint32_t *max_window);
+
 /* Copy the canonical covering to host memory: start[R+1] (start[0] = 0,
  * start[R] = 4^F, strictly increasing), list_off[R+1], list_ids[n_list_ids];
  * range r holds finest ids [start[r], start[r+1]) and polygons

@@ -111,7 +111,8 @@ static void free_covering(sdb_covering* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
-  void* ps[] = {c->start, c->list_off, c->list_ids, c->pay, c->sample, c->leaves, c->fallbacks};
+  void* ps[] = {c->start,  c->list_off, c->list_ids, c->pay,
+                c->sample, c->leaves,   c->knots,    c->fallbacks};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, 0);
   cudaStreamSynchronize(0);
@@ -220,7 +221,8 @@ sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* inf
   info->n_ranges = cov->R;
   info->n_list_ids = cov->nids;
   info->n_cells = cov->ncells;
-  info->device_bytes = cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) : 0);
+  info->device_bytes =
+      cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) + (4ull << cov->knot_bits) + 4 : 0);
   info->index_leaf_bits = cov->leaf_bits;
   return SDB_OK;
 }
@@ -373,6 +375,43 @@ sdb_status sdb_covering_fallbacks(const sdb_covering* cov, void* cuda_stream, ui
   SDB_TRY_CUDA(cudaMemcpyAsync(&v, cov->fallbacks, sizeof(v), cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   *out = v;
+  return SDB_OK;
+}
+
+sdb_status sdb_covering_index_stats(const sdb_covering* cov, double* mean_window,
+                                    uint32_t* max_window) {
+  if (!cov || !mean_window || !max_window) {
+    set_error("covering or an output is NULL");
+    return SDB_EINVAL;
+  }
+  *mean_window = 0;
+  *max_window = 0;
+  if (!cov->leaves) return SDB_OK;
+  SDB_TRY(check_device(cov));
+  const size_t L = (size_t)1 << cov->leaf_bits;
+  LeafRec* h = new (std::nothrow) LeafRec[L];
+  if (!h) {
+    set_error("host allocation failed");
+    return SDB_ENOMEM;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h, cov->leaves, L * sizeof(LeafRec), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    delete[] h;
+    return cuda_status(e, "leaf copy", __FILE__, __LINE__);
+  }
+  double wsum = 0, rsum = 0;
+  uint32_t wmax = 0;
+  for (size_t l = 0; l < L; ++l) {
+    const double w = (double)h[l].errlo + (double)h[l].errhi + 1.0;
+    const double r = (double)h[l].last - (double)h[l].first + 1.0;
+    wsum += w * r;
+    rsum += r;
+    if (w > wmax) wmax = (uint32_t)w;
+  }
+  delete[] h;
+  *mean_window = rsum > 0 ? wsum / rsum : 0;
+  *max_window = wmax;
   return SDB_OK;
 }
 

@@ -67,7 +67,9 @@ struct JoinArgs {
   uint32_t B, k, nsteps, st0, P;
   // learned index
   const LeafRec* leaves;
-  float root_a, root_b;
+  const float* knots;
+  uint32_t nknots, wshift;
+  float inv_w;
   uint32_t nleaves;
   unsigned long long* fallbacks;
 };
@@ -152,14 +154,15 @@ __device__ __forceinline__ void find_bs(const uint64_t (&h)[G], uint32_t (&r)[G]
 
 template <int G>
 __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&r)[G],
-                                             const JoinArgs& A) {
-  uint64_t lo[G], wlo[G], whi[G];
+                                             const float* s_knots, const JoinArgs& A) {
+  uint64_t lo[G];
   uint32_t len[G];
+  uint32_t maxlen = 1;
 #pragma unroll
   for (int q = 0; q < G; ++q) {
-    uint32_t l = root_leaf(A.root_a, A.root_b, A.nleaves, h[q]);
+    const uint32_t l = root_leaf(s_knots, A.wshift, A.inv_w, A.nleaves, h[q]);
     const uint4* p = reinterpret_cast<const uint4*>(A.leaves + l);
-    uint4 u0 = __ldg(p), u1 = __ldg(p + 1);
+    const uint4 u0 = __ldg(p), u1 = __ldg(p + 1);
     LeafRec lr;
     lr.base = (uint64_t)u0.x | ((uint64_t)u0.y << 32);
     lr.a = __uint_as_float(u0.z);
@@ -168,26 +171,19 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
     lr.last = u1.y;
     lr.errlo = (int32_t)u1.z;
     lr.errhi = (int32_t)u1.w;
-    int64_t pr = leaf_predict(lr, h[q]);
+    const int64_t pr = leaf_predict(lr, h[q]);
     int64_t a = pr - lr.errlo, b = pr + lr.errhi;
     if (a < (int64_t)lr.first) a = lr.first;
     if (b > (int64_t)lr.last) b = lr.last;
     if (b < a) b = a;
-    wlo[q] = (uint64_t)a;
-    whi[q] = (uint64_t)b;
-    lo[q] = wlo[q];
+    lo[q] = (uint64_t)a;
     len[q] = (uint32_t)(b - a + 1);
+    maxlen = max(maxlen, len[q]);
   }
-  // bracket checks issued with the search: start[wlo] <= h < start[whi + 1]
-  uint64_t c0[G], c1[G];
-#pragma unroll
-  for (int q = 0; q < G; ++q) {
-    c0[q] = __ldg(A.start + wlo[q]);
-    c1[q] = __ldg(A.start + whi[q] + 1);
-  }
-  bool more = true;
-  while (more) {
-    more = false;
+  // the same number of halving steps for the whole warp; finished lanes idle
+  maxlen = __reduce_max_sync(FULL, maxlen);
+  const int steps = 32 - __clz(maxlen - 1);
+  for (int st = 0; st < steps; ++st) {
     uint64_t v[G];
 #pragma unroll
     for (int q = 0; q < G; ++q)
@@ -195,16 +191,17 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
 #pragma unroll
     for (int q = 0; q < G; ++q) {
       if (len[q] > 1) {
-        uint32_t half = len[q] >> 1;
+        const uint32_t half = len[q] >> 1;
         if (v[q] <= h[q]) lo[q] += half;
         len[q] -= half;
-        more |= len[q] > 1;
       }
     }
   }
+  // judge: the result must bracket h; otherwise plain binary search decides
 #pragma unroll
   for (int q = 0; q < G; ++q) {
-    if (c0[q] <= h[q] && h[q] < c1[q]) {
+    const uint64_t s0 = __ldg(A.start + lo[q]), s1 = __ldg(A.start + lo[q] + 1);
+    if (s0 <= h[q] && h[q] < s1) {
       r[q] = (uint32_t)lo[q];
     } else {
       atomicAdd(A.fallbacks, 1ull);
@@ -213,69 +210,102 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
   }
 }
 
+// Per-block accumulators in shared memory (P <= SMEM_POLYS): a 32-bit count and
+// the attribute sum split exactly into its low 16 bits (unsigned) and the rest
+// (signed), each in a 32-bit counter.  A block flushes them into the global
+// 64-bit outputs at least every FLUSH_POINTS points, so none can wrap:
+// FLUSH_POINTS * 65535 < 2^32 and FLUSH_POINTS * 32768 < 2^31.
+constexpr uint32_t FLUSH_TILES = 32;
+constexpr uint32_t FLUSH_POINTS = FLUSH_TILES * THREADS * 4;
+static_assert((uint64_t)FLUSH_POINTS * 65535u < (1ull << 32), "low-half counter could wrap");
+
+struct Acc {
+  uint32_t* cnt;
+  uint32_t* lo;
+  int32_t* hi;
+};
+
 template <bool SMEM, bool SUM>
-__device__ __forceinline__ void agg_warp(uint32_t p, int32_t a, uint32_t* s_cnt,
-                                         unsigned long long* s_sum, const JoinArgs& A) {
-  unsigned peers = __match_any_sync(FULL, p);
-  if (p == NONE) return;
-  unsigned c = __popc(peers);
-  long long tot = 0;
-  if (SUM) {
-    int lo = __reduce_add_sync(peers, a & 0xffff);
-    int hi = __reduce_add_sync(peers, a >> 16);
-    tot = (long long)hi * 65536 + lo;
+__device__ __forceinline__ void add_one(uint32_t p, int32_t a, const Acc& s, const JoinArgs& A) {
+  if (SMEM) {
+    atomicAdd(&s.cnt[p], 1u);
+    if (SUM) {
+      atomicAdd(&s.lo[p], (uint32_t)a & 0xffffu);
+      atomicAdd(&s.hi[p], a >> 16);
+    }
+  } else {
+    atomicAdd(&A.count[p], 1ull);
+    if (SUM) atomicAdd(&A.sum[p], (unsigned long long)(long long)a);
   }
-  if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) {
-    if (SMEM) {
-      atomicAdd(&s_cnt[p], c);
-      if (SUM) atomicAdd(&s_sum[p], (unsigned long long)tot);
-    } else {
-      atomicAdd(&A.count[p], (unsigned long long)c);
-      if (SUM) atomicAdd(&A.sum[p], (unsigned long long)tot);
+}
+
+template <bool SUM>
+__device__ void flush_acc(const Acc& s, const JoinArgs& A) {
+  for (uint32_t i = threadIdx.x; i < A.P; i += THREADS) {
+    const uint32_t c = s.cnt[i];
+    if (c) {
+      atomicAdd(&A.count[i], (unsigned long long)c);
+      s.cnt[i] = 0;
+      if (SUM) {
+        const long long tot = (long long)s.hi[i] * 65536 + (long long)s.lo[i];
+        atomicAdd(&A.sum[i], (unsigned long long)tot);
+        s.lo[i] = 0;
+        s.hi[i] = 0;
+      }
     }
   }
 }
 
 template <int LOOKUP, bool SMEM, bool SUM>
-__global__ __launch_bounds__(THREADS) void join_kernel(JoinArgs A) {
+__global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned long long* s_sum = reinterpret_cast<unsigned long long*>(smem);
-  size_t off = (SMEM && SUM) ? (size_t)A.P * 8 : 0;
-  uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem + off);
-  off += (LOOKUP == SDB_LOOKUP_BINARY) ? (size_t)A.sample_n * 8 : 0;
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + off);
+  // lookup staging: the binary search's sample of range starts, or the learned
+  // index's root knots
+  uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem);
+  float* s_knots = reinterpret_cast<float*>(smem);
+  size_t off = (LOOKUP == SDB_LOOKUP_BINARY) ? (size_t)A.sample_n * 8
+                                               : (((size_t)A.nknots * 4 + 7) & ~(size_t)7);
+  Acc acc;
+  acc.cnt = reinterpret_cast<uint32_t*>(smem + off);
   off += SMEM ? (size_t)A.P * 4 : 0;
+  acc.lo = reinterpret_cast<uint32_t*>(smem + off);
+  acc.hi = reinterpret_cast<int32_t*>(smem + off + ((SMEM && SUM) ? (size_t)A.P * 4 : 0));
+  off += (SMEM && SUM) ? (size_t)A.P * 8 : 0;
   uint16_t* s_lut = reinterpret_cast<uint16_t*>(smem + off);
 
   for (uint32_t i = threadIdx.x; i < 1024; i += THREADS) s_lut[i] = lut_entry(i);
   if (LOOKUP == SDB_LOOKUP_BINARY)
     for (uint32_t i = threadIdx.x; i < A.sample_n; i += THREADS) s_sample[i] = A.sample[i];
+  else
+    for (uint32_t i = threadIdx.x; i < A.nknots; i += THREADS) s_knots[i] = A.knots[i];
   if (SMEM)
     for (uint32_t i = threadIdx.x; i < A.P; i += THREADS) {
-      s_cnt[i] = 0;
-      if (SUM) s_sum[i] = 0;
+      acc.cnt[i] = 0;
+      if (SUM) {
+        acc.lo[i] = 0;
+        acc.hi[i] = 0;
+      }
     }
   __syncthreads();
 
-  const int lane = threadIdx.x & 31;
-  const uint64_t ngroups = (A.n + 3) >> 2;
-  const uint64_t warp = ((uint64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * THREADS) >> 5;
-  const uint32_t gmask = (A.B >= 32) ? 0u : ~((1u << A.B) - 1u);
-
-  for (uint64_t gb = warp * 32; gb < ngroups; gb += nwarps * 32) {
-    const uint64_t g = gb + lane;
+  const uint32_t gmask = ~((1u << A.B) - 1u);
+  const uint64_t per_tile = (uint64_t)THREADS * 4;
+  const uint64_t ntiles = (A.n + per_tile - 1) / per_tile;
+  uint32_t since_flush = 0;
+  // block-uniform loop over tiles of 1024 consecutive points; thread t takes
+  // points 4t..4t+3 of the tile (a warp reads 512 contiguous bytes per array)
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t e0 = t * per_tile + (uint64_t)threadIdx.x * 4;
     uint32_t xs[4], ys[4];
     int32_t as[4];
     bool ok[4];
-    const uint64_t e0 = g * 4;
     if (A.vec && e0 + 3 < A.n) {
-      uint4 xv = __ldcs(reinterpret_cast<const uint4*>(A.x) + g);
-      uint4 yv = __ldcs(reinterpret_cast<const uint4*>(A.y) + g);
+      const uint4 xv = __ldcs(reinterpret_cast<const uint4*>(A.x + e0));
+      const uint4 yv = __ldcs(reinterpret_cast<const uint4*>(A.y + e0));
       xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
       ys[0] = yv.x; ys[1] = yv.y; ys[2] = yv.z; ys[3] = yv.w;
       if (SUM) {
-        int4 av = __ldcs(reinterpret_cast<const int4*>(A.attr) + g);
+        const int4 av = __ldcs(reinterpret_cast<const int4*>(A.attr + e0));
         as[0] = av.x; as[1] = av.y; as[2] = av.z; as[3] = av.w;
       }
 #pragma unroll
@@ -299,36 +329,31 @@ __global__ __launch_bounds__(THREADS) void join_kernel(JoinArgs A) {
     if (LOOKUP == SDB_LOOKUP_BINARY)
       find_bs<4>(h, r, s_sample, A);
     else
-      find_learned<4>(h, r, A);
+      find_learned<4>(h, r, s_knots, A);
     uint32_t pay[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) pay[q] = ok[q] ? __ldg(A.pay + r[q]) : NONE;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const bool multi = pay[q] != NONE && (pay[q] & 0x80000000u);
-      agg_warp<SMEM, SUM>(multi ? NONE : pay[q], SUM ? as[q] : 0, s_cnt, s_sum, A);
-      if (__any_sync(FULL, multi)) {
-        uint32_t lo = 0, n = 0;
-        if (multi) {
-          uint32_t rr = pay[q] & 0x7fffffffu;
-          lo = __ldg(A.list_off + rr);
-          n = __ldg(A.list_off + rr + 1) - lo;
-        }
-        for (uint32_t t = 0; __any_sync(FULL, t < n); ++t)
-          agg_warp<SMEM, SUM>(t < n ? __ldg(A.list_ids + lo + t) : NONE, SUM ? as[q] : 0, s_cnt,
-                              s_sum, A);
+      const int32_t a = SUM ? as[q] : 0;
+      if (pay[q] < 0x80000000u) {
+        add_one<SMEM, SUM>(pay[q], a, acc, A);
+      } else if (pay[q] != NONE) {  // several polygons share the range
+        const uint32_t rr = pay[q] & 0x7fffffffu;
+        const uint32_t b = __ldg(A.list_off + rr), e = __ldg(A.list_off + rr + 1);
+        for (uint32_t i = b; i < e; ++i) add_one<SMEM, SUM>(__ldg(A.list_ids + i), a, acc, A);
       }
+    }
+    if (SMEM && ++since_flush == FLUSH_TILES) {
+      since_flush = 0;
+      __syncthreads();
+      flush_acc<SUM>(acc, A);
+      __syncthreads();
     }
   }
-
   if (SMEM) {
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < A.P; i += THREADS) {
-      if (s_cnt[i]) {
-        atomicAdd(&A.count[i], (unsigned long long)s_cnt[i]);
-        if (SUM) atomicAdd(&A.sum[i], s_sum[i]);
-      }
-    }
+    flush_acc<SUM>(acc, A);
   }
 }
 
@@ -336,7 +361,11 @@ template <int LOOKUP, bool SMEM, bool SUM>
 sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
   size_t smem = 2048;  // table
   if (SMEM) smem += (size_t)A.P * (SUM ? 12 : 4);
-  if (LOOKUP == SDB_LOOKUP_BINARY) smem += (size_t)A.sample_n * 8;
+  if (LOOKUP == SDB_LOOKUP_BINARY)
+    smem += (size_t)A.sample_n * 8;
+  else
+    smem += ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
+  smem = (smem + 15) & ~(size_t)15;
   auto kern = join_kernel<LOOKUP, SMEM, SUM>;
   if (smem > 48 * 1024)
     SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -344,11 +373,8 @@ sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
   SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   uint64_t blocks = (uint64_t)num_sms() * per_sm;
-  // shared counters are 32-bit: keep each block under 2^31 points
-  uint64_t min_blocks = A.n / (1ull << 31) + 1;
-  if (blocks < min_blocks) blocks = min_blocks;
-  uint64_t need = (A.n + 4 * THREADS - 1) / (4 * THREADS);
-  if (blocks > need && need >= min_blocks) blocks = need > 0 ? need : 1;
+  const uint64_t need = (A.n + 4 * THREADS - 1) / (4 * THREADS);  // tiles
+  if (blocks > need) blocks = need > 0 ? need : 1;
   kern<<<(unsigned)blocks, THREADS, smem, s>>>(A);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
@@ -390,8 +416,10 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.st0 = (pad & 1u) ? 2u : 0u;  // swap bit set when the padding is odd
   A.P = cov->P;
   A.leaves = cov->leaves;
-  A.root_a = cov->root_a;
-  A.root_b = cov->root_b;
+  A.knots = cov->knots;
+  A.nknots = cov->leaf_bits ? (1u << cov->knot_bits) + 1 : 0;
+  A.wshift = cov->knot_wshift;
+  A.inv_w = 1.0f / (float)(1ull << cov->knot_wshift);
   A.nleaves = cov->leaf_bits ? (1u << cov->leaf_bits) : 0u;
   A.fallbacks = cov->fallbacks;
   const bool smem = cov->P <= SMEM_POLYS;

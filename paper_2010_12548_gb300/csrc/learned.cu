@@ -3,11 +3,16 @@
 // search; RadixSpline is the paper's model, a two-level piecewise-linear model
 // is used here).
 //
-//   root:  leaf(h) = clamp(floor(fma(ra, float(h), rb)), 0, L-1)       (FP32)
+//   root:  leaf(h) = clamp(floor(knot_j + (knot_{j+1} - knot_j) * frac), 0, L-1)  (FP32)
+//          with j = h >> wshift, frac = (h - (j << wshift)) / 2^wshift and
+//          knot_j = L * #{i : start_i < j << wshift} / R  (2^12 uniform knots)
 //   leaf:  pred(h) = first + floor(fma(a, float(h - base), b))         (FP32)
 //
-// Both maps are monotone in h.  The root is a least-squares line through
-// (start_i, i * L / R).  Leaf l receives exactly the ids h in
+// Both maps are monotone in h.  The root is the piecewise-linear interpolant of
+// the range starts' cumulative distribution, so leaves receive roughly equal
+// numbers of ranges even where ranges crowd along polygon boundaries (a single
+// line through (start_i, i) routes most ranges to a few leaves: the covering's
+// id -> index map is a staircase at every scale).  Leaf l receives exactly the ids h in
 // [base_l, base_{l+1}), where base_l is the smallest id the root sends to a
 // leaf >= l; it is found by binary search on the root function itself, with the
 // same instructions the lookup uses, so routing at fit time and lookup time
@@ -24,33 +29,6 @@ namespace sdb {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int RB = 256;  // root reduction block
-
-__global__ __launch_bounds__(RB) void root_partial_kernel(const uint64_t* __restrict__ start,
-                                                          uint64_t R, double inv_top, double inv_R,
-                                                          double* __restrict__ part) {
-  __shared__ double sh[4][RB];
-  double sx = 0, sy = 0, sxx = 0, sxy = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * RB + threadIdx.x; i < R; i += (uint64_t)gridDim.x * RB) {
-    double x = (double)start[i] * inv_top, y = (double)i * inv_R;
-    sx += x;
-    sy += y;
-    sxx += x * x;
-    sxy += x * y;
-  }
-  sh[0][threadIdx.x] = sx;
-  sh[1][threadIdx.x] = sy;
-  sh[2][threadIdx.x] = sxx;
-  sh[3][threadIdx.x] = sxy;
-  __syncthreads();
-  for (int o = RB / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
-      for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
-}
-
 __device__ __forceinline__ uint64_t upper_bound_idx(const uint64_t* __restrict__ start, uint64_t R,
                                                     uint64_t h) {
   // last r in [0, R) with start[r] <= h (start[0] = 0 <= h < start[R])
@@ -63,9 +41,28 @@ __device__ __forceinline__ uint64_t upper_bound_idx(const uint64_t* __restrict__
   return lo;
 }
 
+// knot j: L * (number of range starts below j << wshift) / R
+__global__ void knots_kernel(const uint64_t* __restrict__ start, uint64_t R, uint32_t K,
+                             uint32_t wshift, uint32_t L, float* __restrict__ knot) {
+  uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > K) return;
+  const uint64_t key = (uint64_t)j << wshift;
+  uint64_t lo = 0, len = R;  // first i with start[i] >= key
+  while (len > 0) {
+    uint64_t half = len >> 1;
+    if (start[lo + half] < key) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  knot[j] = (float)((double)L * (double)lo / (double)R);
+}
+
 // base of every leaf l in [0, L]: smallest h in [0, top] with leaf(h) >= l
-__global__ void leaf_base_kernel(float ra, float rb, uint32_t L, uint64_t top,
-                                 uint64_t* __restrict__ base) {
+__global__ void leaf_base_kernel(const float* __restrict__ knot, uint32_t wshift, float inv_w,
+                                 uint32_t L, uint64_t top, uint64_t* __restrict__ base) {
   uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l > L) return;
   if (l == 0) {
@@ -79,7 +76,7 @@ __global__ void leaf_base_kernel(float ra, float rb, uint32_t L, uint64_t top,
   uint64_t lo = 0, hi = top;
   while (lo < hi) {
     uint64_t mid = lo + ((hi - lo) >> 1);
-    if (root_leaf(ra, rb, L, mid) >= l)
+    if (root_leaf(knot, wshift, inv_w, L, mid) >= l)
       hi = mid;
     else
       lo = mid + 1;
@@ -175,43 +172,27 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
   const uint32_t L = 1u << leaf_bits;
   const uint64_t R = cov->R;
   const uint64_t top = 1ull << (2 * cov->F);
+  const uint32_t kbits = 2 * cov->F < 12 ? 2 * cov->F : 12;
+  const uint32_t K = 1u << kbits;
+  const uint32_t wshift = 2 * cov->F - kbits;
+  const float inv_w = 1.0f / (float)(1ull << wshift);  // exact: a power of two
   Scratch sc(s);
-  // root: least squares of i*L/R on start_i (both scaled to [0, 1))
-  const int nb = 256;
-  double* part;
-  SDB_TRY(sc.get(&part, (size_t)nb * 4));
-  root_partial_kernel<<<nb, RB, 0, s>>>(cov->start, R, 1.0 / (double)top, 1.0 / (double)R, part);
-  note_launch();
-  SDB_TRY_CUDA(cudaGetLastError());
-  double hp[nb * 4];
-  SDB_TRY_CUDA(cudaMemcpyAsync(hp, part, sizeof(hp), cudaMemcpyDeviceToHost, s));
-  SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  double sx = 0, sy = 0, sxx = 0, sxy = 0;
-  for (int b = 0; b < nb; ++b) {
-    sx += hp[4 * b];
-    sy += hp[4 * b + 1];
-    sxx += hp[4 * b + 2];
-    sxy += hp[4 * b + 3];
-  }
-  const double n = (double)R;
-  double den = n * sxx - sx * sx, slope = den > 0 ? (n * sxy - sx * sy) / den : 1.0;
-  if (!(slope > 0)) slope = 1.0;
-  double icpt = (sy - slope * sx) / n;
-  // leaf = L * (slope * h / top + icpt)
-  cov->root_a = (float)((double)L * slope / (double)top);
-  cov->root_b = (float)((double)L * icpt);
-  if (!(cov->root_a > 0.f)) cov->root_a = (float)((double)L / (double)top);
-
   if (cov->leaves) dfree(cov->leaves, s);
+  if (cov->knots) dfree(cov->knots, s);
   cov->leaves = nullptr;
+  cov->knots = nullptr;
   SDB_TRY(dalloc_n(&cov->leaves, L, s));
+  SDB_TRY(dalloc_n(&cov->knots, (size_t)K + 1, s));
   if (!cov->fallbacks) {
     SDB_TRY(dalloc_n(&cov->fallbacks, 1, s));
     SDB_TRY_CUDA(cudaMemsetAsync(cov->fallbacks, 0, sizeof(unsigned long long), s));
   }
+  knots_kernel<<<grid_for((size_t)K + 1, 256), 256, 0, s>>>(cov->start, R, K, wshift, L, cov->knots);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
   uint64_t* base;
   SDB_TRY(sc.get(&base, (size_t)L + 1));
-  leaf_base_kernel<<<grid_for((size_t)L + 1, 256), 256, 0, s>>>(cov->root_a, cov->root_b, L, top,
+  leaf_base_kernel<<<grid_for((size_t)L + 1, 256), 256, 0, s>>>(cov->knots, wshift, inv_w, L, top,
                                                                  base);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
@@ -221,6 +202,8 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
   SDB_TRY_CUDA(cudaGetLastError());
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   cov->leaf_bits = leaf_bits;
+  cov->knot_bits = kbits;
+  cov->knot_wshift = wshift;
   return SDB_OK;
 }
 

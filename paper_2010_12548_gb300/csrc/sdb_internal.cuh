@@ -124,8 +124,19 @@ __device__ __forceinline__ int64_t leaf_predict(const LeafRec& l, uint64_t h) {
   return (int64_t)l.first + (int64_t)__float2ll_rd(pos);
 }
 
-__device__ __forceinline__ uint32_t root_leaf(float ra, float rb, uint32_t nleaves, uint64_t h) {
-  int v = __float2int_rd(__fmaf_rn(ra, __ull2float_rn(h), rb));
+// Root of the learned index: a piecewise-linear approximation of the ranges'
+// cumulative distribution over the id space, in leaf units.  Knot j sits at
+// id j << wshift and holds knot[j] = L * (#range starts below it) / R; between
+// knots the value is interpolated in FP32.  The map is monotone in h (each
+// piece is non-decreasing and ends at the next knot's value), so every leaf
+// receives one contiguous interval of ids.
+__device__ __forceinline__ uint32_t root_leaf(const float* knot, uint32_t wshift, float inv_w,
+                                              uint32_t nleaves, uint64_t h) {
+  const uint32_t j = (uint32_t)(h >> wshift);
+  const uint64_t rem = h - ((uint64_t)j << wshift);
+  const float k0 = knot[j], k1 = knot[j + 1];
+  const float pos = __fmaf_rn(k1 - k0, __fmul_rn(__ull2float_rn(rem), inv_w), k0);
+  int v = __float2int_rd(pos);
   v = v < 0 ? 0 : v;
   return (uint32_t)v >= nleaves ? nleaves - 1 : (uint32_t)v;
 }
@@ -146,7 +157,8 @@ struct sdb_covering {
   uint32_t sample_n = 0, sample_stride = 1;
   // learned index
   uint32_t leaf_bits = 0;
-  float root_a = 0.f, root_b = 0.f;        // leaf = clamp(floor(root_a * float(h) + root_b))
+  uint32_t knot_bits = 0, knot_wshift = 0; // root: 2^knot_bits + 1 knots, spacing 2^knot_wshift ids
+  float* knots = nullptr;                  // root knots (leaf units)
   sdb::LeafRec* leaves = nullptr;          // 2^leaf_bits
   unsigned long long* fallbacks = nullptr; // device counter
   size_t bytes = 0;

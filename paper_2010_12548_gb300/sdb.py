@@ -62,6 +62,7 @@ def lib():
             "sdb_status_string": ([I], C.c_char_p),
             "sdb_last_error": ([], C.c_char_p),
             "sdb_launch_count": ([], U64),
+            "sdb_covering_index_stats": ([P, P, P], I),
             "sdb_join_aggregate_host_noalloc": ([P, P, P, U64, P, I, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -205,6 +206,13 @@ def covering_fallbacks(cov: Covering, stream=None) -> int:
     v = C.c_uint64()
     _check(lib().sdb_covering_fallbacks(cov.handle, _stream(stream), C.byref(v)))
     return v.value
+
+
+def covering_index_stats(cov: Covering) -> tuple[float, int]:
+    """(range-weighted mean window, max window) of the learned index."""
+    m, x = C.c_double(), C.c_uint32()
+    _check(lib().sdb_covering_index_stats(cov.handle, C.byref(m), C.byref(x)))
+    return m.value, x.value
 
 
 def covering_export(cov: Covering):
