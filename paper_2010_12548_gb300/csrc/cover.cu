@@ -42,21 +42,6 @@ struct Item {
   uint32_t poly, cx, cy, eoff, ecnt_par;  // ecnt_par: edge count | parity << 31
 };
 
-// Closed segment vs closed axis-aligned square, exact.  Separating axes: the
-// two coordinate axes (bounding boxes) and the segment's normal (the line's
-// signed function f(p) = cross(b - a, p - a) is linear, so its extremes over
-// the square sit at the two corners picked by the signs of the direction).
-__device__ __forceinline__ bool seg_meets_square(const Edge& e, int64_t x0, int64_t y0, int64_t x1,
-                                                 int64_t y1) {
-  int64_t minx = min(e.ax, e.bx), maxx = max(e.ax, e.bx);
-  int64_t miny = min(e.ay, e.by), maxy = max(e.ay, e.by);
-  if (maxx < x0 || minx > x1 || maxy < y0 || miny > y1) return false;
-  int64_t dx = (int64_t)e.bx - e.ax, dy = (int64_t)e.by - e.ay;
-  int64_t fmax = dx * ((dx >= 0 ? y1 : y0) - e.ay) - dy * ((dy >= 0 ? x0 : x1) - e.ax);
-  int64_t fmin = dx * ((dx >= 0 ? y0 : y1) - e.ay) - dy * ((dy >= 0 ? x1 : x0) - e.ax);
-  return fmax >= 0 && fmin <= 0;
-}
-
 // Sign of cross(b - a, q+ - a) with q+ = q + (d, d^2): o - dy*d + dx*d^2.
 // Never zero for a non-degenerate edge.
 __device__ __forceinline__ int pert_side(const Edge& e, int64_t qx, int64_t qy) {
@@ -65,25 +50,6 @@ __device__ __forceinline__ int pert_side(const Edge& e, int64_t qx, int64_t qy) 
   if (o != 0) return o > 0 ? 1 : -1;
   if (dy != 0) return dy < 0 ? 1 : -1;
   return dx > 0 ? 1 : -1;
-}
-
-// Sign of cross(q+ - r+, p - r+) for the segment r+ -> q+ (same shift on both
-// ends): o + uy*d - ux*d^2 with u = q - r != 0.
-__device__ __forceinline__ int pert_line_side(int64_t rx, int64_t ry, int64_t qx, int64_t qy,
-                                              int64_t px, int64_t py) {
-  int64_t ux = qx - rx, uy = qy - ry;
-  int64_t o = ux * (py - ry) - uy * (px - rx);
-  if (o != 0) return o > 0 ? 1 : -1;
-  if (uy != 0) return uy > 0 ? 1 : -1;
-  return ux > 0 ? -1 : 1;
-}
-
-// Does edge e cross the segment r+ -> q+ ?
-__device__ __forceinline__ uint32_t pert_cross(const Edge& e, int64_t rx, int64_t ry, int64_t qx,
-                                               int64_t qy) {
-  if (e.ax == e.bx && e.ay == e.by) return 0;
-  if (pert_side(e, rx, ry) == pert_side(e, qx, qy)) return 0;
-  return pert_line_side(rx, ry, qx, qy, e.ax, e.ay) != pert_line_side(rx, ry, qx, qy, e.bx, e.by);
 }
 
 // Does edge e cross the rightward ray from q+ ?  (integer endpoints lie above
@@ -137,6 +103,59 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
   if (lane == 0) items[j] = Item{j, 0, 0, a, (b - a) | (par << 31)};
 }
 
+// One edge against the 2x2 children of a parent square with lower-left corner
+// (px, py) and child side 2^sh.  The line function f(p) = cross(b - a, p - a)
+// is linear, so its values on the 3x3 lattice of child corners follow from one
+// evaluation and shifted steps: f(px + u*side, py + v*side) = f00 + u*stepx +
+// v*stepy.  Bits 0..3 of the result: the closed edge meets closed child c
+// (c = dy*2 + dx); separating axes: the bounding boxes, and the edge's line
+// (f takes both signs, or zero, over the child's corners; its extremes sit at
+// the corners picked by the signs of the steps).  Bits 5..7: parity flips from
+// the parent's corner to the corner of child 1 (via the rightward ray along the
+// bottom row), child 2
+// (upward ray along the left column) and child 3 (child 1's corner plus the
+// upward ray along the middle column), all for corners shifted by (d, d^2);
+// a segment's crossing parity is the XOR of the two rays that contain it.
+__device__ __forceinline__ uint32_t edge_vs_children(const Edge& e, int64_t px, int64_t py,
+                                                     uint32_t sh) {
+  const int64_t side = (int64_t)1 << sh;
+  const int64_t dx = (int64_t)e.bx - e.ax, dy = (int64_t)e.by - e.ay;
+  const int64_t f00 = dx * (py - e.ay) - dy * (px - e.ax);
+  const int64_t stepx = -(dy << sh), stepy = dx << sh;
+  const int32_t minx = min(e.ax, e.bx), maxx = max(e.ax, e.bx);
+  const int32_t miny = min(e.ay, e.by), maxy = max(e.ay, e.by);
+  uint32_t out = 0;
+  const int64_t ux = stepx >= 0 ? 1 : 0, uy = stepy >= 0 ? 1 : 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int64_t cu = c & 1, cv = c >> 1;
+    const int64_t x0 = px + cu * side, y0 = py + cv * side;
+    const bool box = !(maxx < x0 || minx > x0 + side || maxy < y0 || miny > y0 + side);
+    const int64_t fmax = f00 + (cu + ux) * stepx + (cv + uy) * stepy;
+    const int64_t fmin = f00 + (cu + 1 - ux) * stepx + (cv + 1 - uy) * stepy;
+    out |= (uint32_t)(box && fmax >= 0 && fmin <= 0) << c;
+  }
+  if (dx == 0 && dy == 0) return out;
+  // perturbed sign of f at lattice point (u, v): f, else -dy, else dx
+  const int tie = dy != 0 ? (dy < 0 ? 1 : -1) : (dx > 0 ? 1 : -1);
+  auto sg = [&](int64_t f) { return f != 0 ? (f > 0 ? 1 : -1) : tie; };
+  const int s00 = sg(f00), s10 = sg(f00 + stepx), s01 = sg(f00 + stepy),
+            s11 = sg(f00 + stepx + stepy);
+  // rightward ray from (u, 0)+: the edge straddles y = py + d^2 and lies to its right
+  uint32_t flip1 = 0, flip2 = 0, flipm = 0;
+  if ((e.ay > py) != (e.by > py)) {
+    const bool up = e.by > e.ay;
+    flip1 = (up ? s00 > 0 : s00 < 0) ^ (up ? s10 > 0 : s10 < 0);
+  }
+  // upward ray from (0, v)+ / (1, v)+: the edge straddles x = px (+ side) + d
+  // and lies above the point
+  const bool right = e.bx > e.ax;
+  if ((e.ax > px) != (e.bx > px)) flip2 = (right ? s00 < 0 : s00 > 0) ^ (right ? s01 < 0 : s01 > 0);
+  if ((e.ax > px + side) != (e.bx > px + side))
+    flipm = (right ? s10 < 0 : s10 > 0) ^ (right ? s11 < 0 : s11 > 0);
+  return out | (flip1 << 5) | (flip2 << 6) | ((flip1 ^ flipm) << 7);
+}
+
 __global__ __launch_bounds__(256) void expand_level_kernel(
     const Item* __restrict__ items, uint32_t n_items, const uint32_t* __restrict__ elist,
     const Edge* __restrict__ edges, uint32_t B, uint32_t L, uint32_t F,
@@ -148,23 +167,18 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   Item it{0, 0, 0, 0, 0};
   if (active) it = items[t];
   const uint32_t cl = L + 1;
-  const int64_t side = (int64_t)1 << (B - cl);
+  const uint32_t sh = B - cl;
   const int64_t px = (int64_t)it.cx << (B - L), py = (int64_t)it.cy << (B - L);
   const uint32_t ecnt = it.ecnt_par & 0x7fffffffu;
   const uint32_t par = it.ecnt_par >> 31;
   // children c = dy*2 + dx, lower-left corner (px + dx*side, py + dy*side)
   uint32_t cnt[4] = {0, 0, 0, 0};
-  uint32_t flip = 0;
+  uint32_t flip = 0;  // bit c: parity flip from the parent's corner to child c's
   for (uint32_t i = 0; i < ecnt; ++i) {
-    const Edge e = edges[elist[it.eoff + i]];
+    const uint32_t m = edge_vs_children(edges[elist[it.eoff + i]], px, py, sh);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      int64_t x0 = px + (c & 1) * side, y0 = py + (c >> 1) * side;
-      cnt[c] += seg_meets_square(e, x0, y0, x0 + side, y0 + side);
-    }
-    flip ^= pert_cross(e, px, py, px + side, py) << 1;
-    flip ^= pert_cross(e, px, py, px, py + side) << 2;
-    flip ^= pert_cross(e, px, py, px + side, py + side) << 3;
+    for (int c = 0; c < 4; ++c) cnt[c] += (m >> c) & 1u;
+    flip ^= m >> 4;
   }
   uint32_t n_rec = 0, n_it = 0, n_ed = 0;
   if (active) {
@@ -207,14 +221,11 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   if (n_it) {
     uint32_t fill[4] = {0, 0, 0, 0};
     for (uint32_t i = 0; i < ecnt; ++i) {
-      uint32_t eid = elist[it.eoff + i];
-      const Edge e = edges[eid];
+      const uint32_t eid = elist[it.eoff + i];
+      const uint32_t m = edge_vs_children(edges[eid], px, py, sh);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (cnt[c] == 0) continue;
-        int64_t x0 = px + (c & 1) * side, y0 = py + (c >> 1) * side;
-        if (seg_meets_square(e, x0, y0, x0 + side, y0 + side)) next_elist[ceoff[c] + fill[c]++] = eid;
-      }
+      for (int c = 0; c < 4; ++c)
+        if (cnt[c] > 0 && ((m >> c) & 1u)) next_elist[ceoff[c] + fill[c]++] = eid;
     }
   }
 }
@@ -352,6 +363,140 @@ __global__ void single_cell_kernel(uint64_t* key, uint32_t* val, uint32_t P) {
   }
 }
 
+// ---- merge without nesting: one sort of the records by id
+// Quadtree cells are either nested or disjoint.  When no record strictly
+// contains another record's start (true for tilings: cells of different
+// polygons are then identical or disjoint), each group of records with the
+// same start is one elementary interval, the gaps between groups are empty
+// intervals, and the canonical ranges follow by merging equal neighbours.
+
+// groups of equal start; nesting makes the covering take the general path
+__global__ void group_flags_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                                   uint64_t n, uint32_t* __restrict__ flag,
+                                   unsigned int* __restrict__ nested) {
+  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint64_t lo = sk[r];
+  const uint32_t d = sv[r] >> 26;
+  flag[r] = (r == 0 || sk[r - 1] != lo) ? 1u : 0u;
+  if (r + 1 < n) {
+    const uint64_t lo2 = sk[r + 1];
+    if (lo2 == lo ? ((sv[r + 1] >> 26) != d) : (lo2 < lo + (1ull << (2 * d)))) *nested = 1u;
+  }
+}
+
+__global__ void group_heads_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ flag,
+                                   const uint32_t* __restrict__ gidx, uint64_t n,
+                                   uint32_t* __restrict__ gfirst) {
+  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n && flag[r]) gfirst[gidx[r]] = (uint32_t)r;
+}
+
+// per group: its size, and its polygon ids sorted ascending (groups are small:
+// the polygons sharing one cell)
+__global__ void group_sort_kernel(uint32_t* __restrict__ sv, const uint32_t* __restrict__ gfirst,
+                                  uint32_t G, uint64_t n, uint32_t* __restrict__ gsize) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const uint32_t a = gfirst[g], b = (g + 1 < G) ? gfirst[g + 1] : (uint32_t)n;
+  const uint32_t PM = (1u << 26) - 1u;
+  for (uint32_t i = a + 1; i < b; ++i) {
+    const uint32_t v = sv[i];
+    uint32_t j = i;
+    while (j > a && (sv[j - 1] & PM) > (v & PM)) {
+      sv[j] = sv[j - 1];
+      --j;
+    }
+    sv[j] = v;
+  }
+  gsize[g] = b - a;
+}
+
+// Ranges opened by group g, in id order: an empty gap before it (bit 0, with
+// its start in *gap_lo), the group itself unless it continues the previous
+// group with the same list (bit 1), and after the last group the empty tail
+// up to the top of the id space (bit 2).
+__device__ __forceinline__ uint32_t group_opens(const uint64_t* __restrict__ sk,
+                                                const uint32_t* __restrict__ sv,
+                                                const uint32_t* __restrict__ gfirst,
+                                                const uint32_t* __restrict__ gsize, uint32_t g,
+                                                uint32_t G, uint64_t top, uint64_t* gap_lo,
+                                                uint64_t* hi_out) {
+  const uint32_t a = gfirst[g];
+  const uint64_t lo = sk[a], hi = lo + (1ull << (2 * (sv[a] >> 26)));
+  uint32_t gap, fresh;
+  if (g == 0) {
+    *gap_lo = 0;
+    gap = lo > 0;
+    fresh = 1;
+  } else {
+    const uint32_t pa = gfirst[g - 1];
+    const uint64_t phi = sk[pa] + (1ull << (2 * (sv[pa] >> 26)));
+    *gap_lo = phi;
+    gap = lo > phi;
+    fresh = gap || gsize[g] != gsize[g - 1];
+    const uint32_t PM = (1u << 26) - 1u;
+    for (uint32_t t = 0; !fresh && t < gsize[g]; ++t) fresh = (sv[a + t] & PM) != (sv[pa + t] & PM);
+  }
+  *hi_out = hi;
+  const uint32_t tail = (g == G - 1) && hi < top;
+  return gap | (fresh << 1) | (tail << 2);
+}
+
+__global__ void group_count_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                                   const uint32_t* __restrict__ gfirst,
+                                   const uint32_t* __restrict__ gsize, uint32_t G, uint64_t top,
+                                   uint32_t* __restrict__ nopen) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  uint64_t gl, hi;
+  const uint32_t o = group_opens(sk, sv, gfirst, gsize, g, G, top, &gl, &hi);
+  nopen[g] = __popc(o);
+}
+
+__global__ void group_emit_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                                  const uint32_t* __restrict__ gfirst,
+                                  const uint32_t* __restrict__ gsize,
+                                  const uint32_t* __restrict__ roff, uint32_t G, uint64_t top,
+                                  uint64_t* __restrict__ start, uint32_t* __restrict__ rlen,
+                                  uint32_t* __restrict__ rsrc) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  uint64_t gl, hi;
+  const uint32_t o = group_opens(sk, sv, gfirst, gsize, g, G, top, &gl, &hi);
+  uint32_t r = roff[g];
+  if (o & 1u) {
+    start[r] = gl;
+    rlen[r] = 0;
+    rsrc[r] = 0;
+    ++r;
+  }
+  if (o & 2u) {
+    start[r] = sk[gfirst[g]];
+    rlen[r] = gsize[g];
+    rsrc[r] = gfirst[g];
+    ++r;
+  }
+  if (o & 4u) {
+    start[r] = hi;
+    rlen[r] = 0;
+    rsrc[r] = 0;
+  }
+}
+
+__global__ void fill_lists_sv_kernel(const uint32_t* __restrict__ sv,
+                                     const uint32_t* __restrict__ rlen,
+                                     const uint32_t* __restrict__ rsrc,
+                                     const uint32_t* __restrict__ list_off, uint64_t R,
+                                     uint32_t* __restrict__ list_ids, uint32_t* __restrict__ pay) {
+  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const uint32_t PM = (1u << 26) - 1u;
+  const uint32_t n = rlen[r], o = list_off[r], s = rsrc[r];
+  for (uint32_t t = 0; t < n; ++t) list_ids[o + t] = sv[s + t] & PM;
+  pay[r] = n == 0 ? NONE : (n == 1 ? (sv[s] & PM) : (0x80000000u | (uint32_t)r));
+}
+
 int bits_for(uint64_t v) {  // bits needed to represent v
   int b = 0;
   while (b < 64 && (v >> b)) ++b;
@@ -366,8 +511,12 @@ sdb_status read_u64(const unsigned long long* d, unsigned long long* h, int n, c
 
 }  // namespace
 
-// records -> canonical ranges (see the file comment)
-static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, uint32_t F, uint32_t P,
+static sdb_status finish_ranges(sdb_covering* cov, uint64_t R, uint32_t nids, uint64_t top,
+                                cudaStream_t s);
+
+// records -> canonical ranges, general path (nested records allowed): sweep
+// over all record endpoints (see the file comment)
+static sdb_status merge_general(uint64_t* key, uint32_t* val, uint64_t n, uint32_t F, uint32_t P,
                                 cudaStream_t s, sdb_covering* cov) {
   Scratch sc(s);
   const uint64_t top = 1ull << (2 * F);
@@ -466,10 +615,15 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, uint32
                                                       cov->list_ids, cov->pay);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
+  return finish_ranges(cov, R, nids, top, s);
+}
+
+// sentinel entries, the shared-memory sample of the starts, sizes
+static sdb_status finish_ranges(sdb_covering* cov, uint64_t R, uint32_t nids, uint64_t top,
+                                cudaStream_t s) {
   finish_kernel<<<1, 1, 0, s>>>(cov->start, cov->list_off, R, top, nids);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  // shared-memory sample of the starts for the top of the binary search
   const uint32_t SAMPLE_MAX = 2048;
   uint64_t keys = (uint64_t)R + 1;
   uint32_t stride = (uint32_t)((keys + SAMPLE_MAX - 1) / SAMPLE_MAX);
@@ -486,6 +640,84 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, uint32
   cov->bytes = ((size_t)R + 1) * 12 + (size_t)R * 4 + (size_t)nids * 4 + (size_t)ns * 8;
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   return SDB_OK;
+}
+
+// records -> canonical ranges: sort by start once; without nesting (see
+// above) the groups give the ranges directly, otherwise the general sweep runs
+static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, uint32_t F, uint32_t P,
+                                cudaStream_t s, sdb_covering* cov) {
+  Scratch sc(s);
+  const uint64_t top = 1ull << (2 * F);
+  if (n >= 0xffffffffull) {
+    set_error("covering: %llu cells exceed the 32-bit index range", (unsigned long long)n);
+    return SDB_ENOMEM;
+  }
+  uint64_t *ktmp, *sk;
+  uint32_t *vtmp, *sv;
+  SDB_TRY(sc.get(&ktmp, n));
+  SDB_TRY(sc.get(&vtmp, n));
+  SDB_TRY(radix_sort_pairs(key, val, ktmp, vtmp, n, bits_for(top), s, &sk, &sv));
+  uint32_t *flag, *gidx, *dG;
+  unsigned int* nested;
+  SDB_TRY(sc.get(&flag, n));
+  SDB_TRY(sc.get(&gidx, n));
+  SDB_TRY(sc.get(&dG, 1));
+  SDB_TRY(sc.get(&nested, 1));
+  SDB_TRY_CUDA(cudaMemsetAsync(nested, 0, sizeof(unsigned int), s));
+  group_flags_kernel<<<grid_for(n, 256), 256, 0, s>>>(sk, sv, n, flag, nested);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint32_t>(flag, gidx, n, dG, s));
+  uint32_t hG[2] = {0, 0};
+  SDB_TRY_CUDA(cudaMemcpyAsync(&hG[0], dG, 4, cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(&hG[1], nested, 4, cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  if (hG[1]) {
+    sc.release(flag);
+    sc.release(gidx);
+    return merge_general(sk, sv, n, F, P, s, cov);
+  }
+  const uint32_t G = hG[0];
+  uint32_t *gfirst, *gsize, *nopen, *roff, *dR;
+  SDB_TRY(sc.get(&gfirst, G));
+  SDB_TRY(sc.get(&gsize, G));
+  SDB_TRY(sc.get(&nopen, G));
+  SDB_TRY(sc.get(&roff, G));
+  SDB_TRY(sc.get(&dR, 1));
+  group_heads_kernel<<<grid_for(n, 256), 256, 0, s>>>(sk, flag, gidx, n, gfirst);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  group_sort_kernel<<<grid_for(G, 256), 256, 0, s>>>(sv, gfirst, G, n, gsize);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  group_count_kernel<<<grid_for(G, 256), 256, 0, s>>>(sk, sv, gfirst, gsize, G, top, nopen);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint32_t>(nopen, roff, G, dR, s));
+  uint32_t R = 0;
+  SDB_TRY_CUDA(cudaMemcpyAsync(&R, dR, sizeof(R), cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  SDB_TRY(dalloc_n(&cov->start, (size_t)R + 1, s));
+  SDB_TRY(dalloc_n(&cov->list_off, (size_t)R + 1, s));
+  SDB_TRY(dalloc_n(&cov->pay, (size_t)R, s));
+  uint32_t *rlen, *rsrc, *dN;
+  SDB_TRY(sc.get(&rlen, R));
+  SDB_TRY(sc.get(&rsrc, R));
+  SDB_TRY(sc.get(&dN, 1));
+  group_emit_kernel<<<grid_for(G, 256), 256, 0, s>>>(sk, sv, gfirst, gsize, roff, G, top,
+                                                      cov->start, rlen, rsrc);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint32_t>(rlen, cov->list_off, R, dN, s));
+  uint32_t nids = 0;
+  SDB_TRY_CUDA(cudaMemcpyAsync(&nids, dN, sizeof(nids), cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  SDB_TRY(dalloc_n(&cov->list_ids, (size_t)nids, s));
+  fill_lists_sv_kernel<<<grid_for(R, 256), 256, 0, s>>>(sv, rlen, rsrc, cov->list_off, R,
+                                                         cov->list_ids, cov->pay);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  return finish_ranges(cov, R, nids, top, s);
 }
 
 sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,

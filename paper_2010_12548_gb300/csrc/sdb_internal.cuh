@@ -109,8 +109,9 @@ void make_hilbert_lut(HilbertLut* t);
 // ---------------------------------------------------------------- covering
 // One leaf of the learned range index, 32 bytes (one DRAM sector).  The leaf
 // receives the ids h in [base, next leaf's base); its ranges are first..last.
-// Prediction: first + floor(fma(a, float(h - base), b)) in FP32; the true range
-// lies in [pred - errlo, pred + errhi] for every id the leaf receives.
+// Prediction: first + floor(fma(a, float(h - base), b)) in FP32, clamped into
+// [first, last] (monotone, and no extrapolation across a long last range); the
+// true range lies in [pred - errlo, pred + errhi] for every id the leaf receives.
 struct LeafRec {
   uint64_t base;
   float a, b;
@@ -119,9 +120,11 @@ struct LeafRec {
 };
 
 __device__ __forceinline__ int64_t leaf_predict(const LeafRec& l, uint64_t h) {
-  float x = __ull2float_rn(h - l.base);
-  float pos = __fmaf_rn(l.a, x, l.b);
-  return (int64_t)l.first + (int64_t)__float2ll_rd(pos);
+  const float x = __ull2float_rn(h - l.base);
+  const float pos = __fmaf_rn(l.a, x, l.b);
+  int64_t p = (int64_t)l.first + (int64_t)__float2ll_rd(pos);
+  p = p < (int64_t)l.first ? (int64_t)l.first : p;
+  return p > (int64_t)l.last ? (int64_t)l.last : p;
 }
 
 // Root of the learned index: a piecewise-linear approximation of the ranges'
