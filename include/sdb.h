@@ -175,6 +175,88 @@ sdb_status sdb_join_aggregate_host_noalloc(const uint32_t *h_x, const uint32_t *
                                            const sdb_covering *cov, int lookup, uint64_t *h_count,
                                            int64_t *h_sum, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched level-of-detail queries (Sec. 1: users explore at several levels of
+ * detail, an overview first, then zooms into regions of interest).  A query is
+ * an axis-aligned viewport [x0, x1) x [y0, y1), a subset of the polygons and a
+ * distance bound eps; it asks, for each polygon of the subset, COUNT and SUM of
+ * the points inside the viewport whose finest cell (at the query's eps) meets
+ * the polygon -- the eps-bounded join of sdb_join_aggregate restricted to the
+ * viewport and the subset.
+ * ------------------------------------------------------------------------- */
+
+/* A resident point set on the device, ordered by full-resolution Hilbert id so
+ * a viewport is a few contiguous index ranges.  Library-owned copy. */
+typedef struct sdb_points sdb_points;
+
+/* Copy n device points (SoA; d_attr may be NULL = zeros) into a resident set.
+ * Synchronises cuda_stream.  SDB_EINVAL: grid_bits outside 1..30, n = 0 or
+ * n >= 2^32, NULL coordinates, a point outside the grid. */
+sdb_status sdb_points_create(const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
+                             uint64_t n, uint32_t grid_bits, void *cuda_stream, sdb_points **out);
+void sdb_points_free(sdb_points *pts);
+
+typedef struct sdb_query {
+  uint32_t x0, y0, x1, y1; /* viewport, half-open, inside the grid, non-empty */
+  uint64_t eps;            /* distance bound in grid units (>= 2) */
+  uint32_t poly_off;       /* the subset is subset_ids[poly_off .. poly_off + poly_cnt) */
+  uint32_t poly_cnt;       /* its output slot i holds polygon subset_ids[poly_off + i] */
+} sdb_query;
+
+typedef struct sdb_batch sdb_batch;
+
+typedef struct sdb_batch_info {
+  uint32_t n_queries;
+  uint32_t n_pairs;        /* (query, polygon) pairs that can reach their viewport */
+  uint64_t out_len;        /* sum of poly_cnt: length of the output arrays */
+  uint64_t n_ranges;       /* covering ranges over all queries */
+  uint64_t max_ranges;     /* largest covering of one query */
+  uint64_t n_cells;        /* raster cells emitted before merging */
+  uint64_t candidates;     /* points in the viewports' candidate index ranges */
+  uint64_t n_tiles;        /* work items of the persistent launch */
+  uint32_t tile;           /* points per work item */
+  uint32_t points_per_thread;
+} sdb_batch_info;
+
+enum { SDB_BATCH_PERSISTENT = 0, SDB_BATCH_PER_QUERY = 1, SDB_BATCH_GRAPH = 2 };
+
+/* Prepare a batch: every query's covering (the conservative raster of its
+ * subset at its eps, cells restricted to those holding viewport points; all
+ * queries in one level-synchronous pass), the viewport's candidate point
+ * ranges, and the work list.  polygons/queries/subset_ids are host arrays read
+ * during the call; pts must outlive the batch.  Output slices: query q's
+ * results are entries [off_q, off_q + poly_cnt_q) of the output arrays, off_q
+ * the sum of the preceding queries' poly_cnt.  Synchronises cuda_stream.
+ * SDB_EINVAL: bad viewport/eps/subset, polygons that overlap inside one query
+ * (batched coverings assume disjoint polygons, e.g. a tiling). */
+sdb_status sdb_batch_create(const sdb_points *pts, const sdb_polygons *polys,
+                            const sdb_query *queries, uint32_t n_queries,
+                            const uint32_t *subset_ids, uint64_t n_subset_ids, void *cuda_stream,
+                            sdb_batch **out);
+sdb_status sdb_batch_get_info(const sdb_batch *b, sdb_batch_info *info);
+/* Covering ranges of every query (host array of n_queries). */
+sdb_status sdb_batch_query_ranges(const sdb_batch *b, uint32_t *h_ranges);
+
+/* Run all queries into d_count / d_sum (out_len device entries each, zeroed by
+ * the call; d_sum may be NULL).  mode SDB_BATCH_PERSISTENT: one persistent
+ * launch whose blocks pull (query, point tile) work items from a device
+ * counter; SDB_BATCH_PER_QUERY: one launch per query; SDB_BATCH_GRAPH: the
+ * persistent launch captured once into a CUDA graph (per output pointers) and
+ * replayed -- needs a created stream, not the legacy default stream.  All modes
+ * give identical results.  Asynchronous. */
+sdb_status sdb_batch_run(sdb_batch *b, int mode, uint64_t *d_count, int64_t *d_sum,
+                         void *cuda_stream);
+
+/* Autotuner: times the persistent launch on this batch for tiles of 1024,
+ * 4096, 16384 points and 1, 2, 4 points per thread, keeps the fastest.
+ * Synchronises cuda_stream. */
+sdb_status sdb_batch_autotune(sdb_batch *b, void *cuda_stream, uint32_t *tile_out,
+                              uint32_t *ppt_out);
+/* Set the tile size (>= 1) and points per thread (1, 2 or 4) directly. */
+sdb_status sdb_batch_set_tuning(sdb_batch *b, uint32_t tile, uint32_t points_per_thread,
+                                void *cuda_stream);
+void sdb_batch_free(sdb_batch *b);
+
 /* Number of learned-index lookups of the covering's most recent learned join
  * whose bounded search missed and fell back to binary search.  Synchronises
  * cuda_stream. */

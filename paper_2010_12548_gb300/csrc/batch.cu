@@ -1,0 +1,838 @@
+// Batched level-of-detail queries over a resident point set.
+//
+// Users explore data at several levels of detail: an overview first, then
+// zooms into regions of interest (Sec. 1, "Motivating Application").  A query
+// here is an axis-aligned viewport, a subset of the polygons and a distance
+// bound eps; it asks for COUNT and SUM per polygon of the subset over the
+// points inside the viewport, answered from the eps-bounded covering (Sec. 2.2,
+// Sec. 5.1).
+//
+//  * Points are made resident once, ordered by their full-resolution Hilbert
+//    id, so a viewport is a handful of contiguous index ranges: the viewport is
+//    cut into at most 9 x 9 aligned quadtree cells (side <= a quarter of the
+//    viewport), each a contiguous id range, found by binary search.
+//  * All queries' coverings are built in one level-synchronous pass over the
+//    (query, polygon) pairs whose polygon can reach the viewport, cells clipped
+//    to the viewport (cover.cu), which keeps them small at fine eps.
+//  * The join is one persistent launch: blocks pull (query, point-tile) work
+//    items from a device counter; per point the viewport test, the cell id at
+//    the query's finest level, binary search in the query's ranges, and
+//    per-slot COUNT/SUM in the query's output slice.  Alternatively one launch
+//    per query, or the persistent launch replayed as a captured CUDA graph.
+//  * An autotuner picks the tile size and points per thread by timing the
+//    candidates on the batch itself.
+#include "sdb_internal.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace sdb {
+namespace {
+
+constexpr uint32_t NONE = 0xffffffffu;
+constexpr int THREADS = 256;
+constexpr int MAXC = 81;  // candidate index ranges per query (9 x 9 cells)
+
+struct QueryDev {
+  uint64_t sbase;  // first entry of the query's covering slice
+  uint32_t R;      // ranges in the slice (the sentinel follows)
+  uint32_t k, nsteps, st0;
+  uint32_t x0, y0, x1, y1;
+  uint32_t out_off;
+  uint32_t pad;
+};
+
+struct TileRec {
+  uint32_t q, begin, end, pad;
+};
+
+__device__ __forceinline__ uint16_t lut_entry(uint32_t idx) {
+  uint32_t sw = (idx >> 9) & 1u, cm = (idx >> 8) & 1u;
+  uint32_t xn = (idx >> 4) & 15u, yn = idx & 15u, out = 0;
+#pragma unroll
+  for (int lev = 3; lev >= 0; --lev) {
+    uint32_t xb = (xn >> lev) & 1u, yb = (yn >> lev) & 1u;
+    uint32_t xt = (sw ? yb : xb) ^ cm, yt = (sw ? xb : yb) ^ cm;
+    out = (out << 2) | (xt << 1) | (xt ^ yt);
+    if (!yt) {
+      sw ^= 1u;
+      cm ^= xt;
+    }
+  }
+  return (uint16_t)(out | (((sw << 1) | cm) << 8));
+}
+
+__device__ __forceinline__ uint64_t encode_cell(uint32_t cx, uint32_t cy, uint32_t nsteps,
+                                                uint32_t st0, const uint16_t* lut) {
+  uint64_t h = 0;
+  uint32_t st = st0;
+  for (int s = (int)nsteps - 1; s >= 0; --s) {
+    uint32_t idx = (st << 8) | (((cx >> (4 * s)) & 15u) << 4) | ((cy >> (4 * s)) & 15u);
+    uint32_t e = lut[idx];
+    h = (h << 8) | (e & 255u);
+    st = e >> 8;
+  }
+  return h;
+}
+
+// ---------------------------------------------------------------- points
+__global__ void point_keys_kernel(const uint32_t* __restrict__ x, const uint32_t* __restrict__ y,
+                                  uint64_t n, uint32_t B, uint32_t nsteps, uint32_t st0,
+                                  uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
+                                  unsigned int* __restrict__ bad) {
+  __shared__ uint16_t lut[1024];
+  for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) lut[i] = lut_entry(i);
+  __syncthreads();
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t xi = x[i], yi = y[i];
+    if (B < 32 && ((xi >> B) | (yi >> B))) *bad = 1u;
+    key[i] = encode_cell(xi, yi, nsteps, st0, lut);
+    idx[i] = (uint32_t)i;
+  }
+}
+
+__global__ void gather_points_kernel(const uint32_t* __restrict__ idx, uint64_t n,
+                                     const uint32_t* __restrict__ x, const uint32_t* __restrict__ y,
+                                     const int32_t* __restrict__ a, uint32_t* __restrict__ xs,
+                                     uint32_t* __restrict__ ys, int32_t* __restrict__ as) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t j = idx[i];
+  xs[i] = x[j];
+  ys[i] = y[j];
+  as[i] = a ? a[j] : 0;
+}
+
+// ---------------------------------------------------------------- candidates
+// one thread per query: the viewport cut into aligned cells at most a quarter
+// of its side, each cell a contiguous id range, turned into point index ranges
+__global__ void candidates_kernel(const QueryDev* __restrict__ qd, uint32_t Q,
+                                  const uint64_t* __restrict__ key, uint64_t n, uint32_t B,
+                                  uint32_t* __restrict__ cand, uint32_t* __restrict__ ncand) {
+  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const QueryDev Qd = qd[q];
+  const uint32_t side = max(Qd.x1 - Qd.x0, Qd.y1 - Qd.y0);
+  uint32_t lc = 0;  // log2 of the cell side
+  while (lc < B && (2u << lc) <= max(1u, side / 4)) ++lc;
+  const uint32_t L = B - lc;  // cell level
+  uint32_t a[MAXC], b[MAXC];
+  int m = 0;
+  for (uint32_t cy = Qd.y0 >> lc; cy <= (Qd.y1 - 1) >> lc; ++cy)
+    for (uint32_t cx = Qd.x0 >> lc; cx <= (Qd.x1 - 1) >> lc; ++cx) {
+      const uint64_t h = hilbert_id(cx, cy, L);
+      const uint64_t k0 = h << (2 * lc), k1 = (h + 1) << (2 * lc);
+      uint64_t lo = 0, len = n;  // first index with key >= k0
+      while (len > 0) {
+        uint64_t half = len >> 1;
+        if (key[lo + half] < k0) {
+          lo += half + 1;
+          len -= half + 1;
+        } else {
+          len = half;
+        }
+      }
+      uint64_t hi = lo, len2 = n - lo;  // first index with key >= k1
+      while (len2 > 0) {
+        uint64_t half = len2 >> 1;
+        if (key[hi + half] < k1) {
+          hi += half + 1;
+          len2 -= half + 1;
+        } else {
+          len2 = half;
+        }
+      }
+      if (hi > lo && m < MAXC) {
+        a[m] = (uint32_t)lo;
+        b[m] = (uint32_t)hi;
+        ++m;
+      }
+    }
+  // sort by start, merge touching ranges
+  for (int i = 1; i < m; ++i) {
+    uint32_t va = a[i], vb = b[i];
+    int j = i;
+    while (j > 0 && a[j - 1] > va) {
+      a[j] = a[j - 1];
+      b[j] = b[j - 1];
+      --j;
+    }
+    a[j] = va;
+    b[j] = vb;
+  }
+  int w = 0;
+  for (int i = 0; i < m; ++i) {
+    if (w > 0 && a[i] <= b[w - 1]) {
+      b[w - 1] = max(b[w - 1], b[i]);
+    } else {
+      a[w] = a[i];
+      b[w] = b[i];
+      ++w;
+    }
+  }
+  for (int i = 0; i < w; ++i) {
+    cand[(size_t)q * MAXC * 2 + 2 * i] = a[i];
+    cand[(size_t)q * MAXC * 2 + 2 * i + 1] = b[i];
+  }
+  ncand[q] = (uint32_t)w;
+}
+
+__global__ void tile_count_kernel(const uint32_t* __restrict__ cand,
+                                  const uint32_t* __restrict__ ncand, uint32_t Q, uint32_t T,
+                                  uint64_t* __restrict__ ntile) {
+  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  uint64_t t = 0;
+  for (uint32_t i = 0; i < ncand[q]; ++i) {
+    const uint32_t a = cand[(size_t)q * MAXC * 2 + 2 * i], b = cand[(size_t)q * MAXC * 2 + 2 * i + 1];
+    t += ((uint64_t)b - a + T - 1) / T;
+  }
+  ntile[q] = t;
+}
+
+__global__ void tile_fill_kernel(const uint32_t* __restrict__ cand,
+                                 const uint32_t* __restrict__ ncand, uint32_t Q, uint32_t T,
+                                 const uint64_t* __restrict__ toff, TileRec* __restrict__ tiles) {
+  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  uint64_t t = toff[q];
+  for (uint32_t i = 0; i < ncand[q]; ++i) {
+    const uint32_t a = cand[(size_t)q * MAXC * 2 + 2 * i], b = cand[(size_t)q * MAXC * 2 + 2 * i + 1];
+    for (uint64_t s = a; s < b; s += T)
+      tiles[t++] = TileRec{q, (uint32_t)s, (uint32_t)min((uint64_t)b, s + T), 0};
+  }
+}
+
+// ---------------------------------------------------------------- join
+struct BatchArgs {
+  const uint32_t* x;
+  const uint32_t* y;
+  const int32_t* attr;
+  const QueryDev* q;
+  const TileRec* tiles;
+  const uint64_t* start;
+  const uint32_t* pay;
+  const uint32_t* list_off;
+  const uint32_t* list_ids;
+  unsigned long long* count;
+  unsigned long long* sum;
+};
+
+__device__ __forceinline__ void add_slot(const BatchArgs& A, uint32_t out, uint32_t p, int32_t a,
+                                         bool sum) {
+  atomicAdd(&A.count[out + p], 1ull);
+  if (sum) atomicAdd(&A.sum[out + p], (unsigned long long)(long long)a);
+}
+
+template <int G, bool SUM>
+__global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t tile_lo,
+                                                        uint32_t tile_hi,
+                                                        unsigned long long* head) {
+  __shared__ uint16_t lut[1024];
+  __shared__ uint32_t s_tile;
+  for (uint32_t i = threadIdx.x; i < 1024; i += THREADS) lut[i] = lut_entry(i);
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = tile_lo + (uint32_t)atomicAdd(head, 1ull);
+    __syncthreads();
+    const uint32_t t = s_tile;
+    __syncthreads();
+    if (t >= tile_hi) break;
+    const TileRec tr = A.tiles[t];
+    const QueryDev Q = A.q[tr.q];
+    for (uint32_t i0 = tr.begin + threadIdx.x * G; i0 < tr.end; i0 += THREADS * G) {
+      uint64_t h[G];
+      bool ok[G];
+      int32_t av[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const uint32_t i = i0 + g;
+        ok[g] = i < tr.end;
+        const uint32_t x = ok[g] ? A.x[i] : 0u, y = ok[g] ? A.y[i] : 0u;
+        av[g] = (SUM && ok[g]) ? A.attr[i] : 0;
+        ok[g] = ok[g] && x >= Q.x0 && x < Q.x1 && y >= Q.y0 && y < Q.y1;
+        h[g] = ok[g] ? encode_cell(x >> Q.k, y >> Q.k, Q.nsteps, Q.st0, lut) : 0ull;
+      }
+      // last entry r in [0, R) of the slice with start <= h (sentinel above)
+      uint32_t lo[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) lo[g] = 0;
+      for (uint32_t len = Q.R + 1; len > 1;) {
+        const uint32_t half = len >> 1;
+        uint64_t v[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) v[g] = __ldg(A.start + Q.sbase + lo[g] + half);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (v[g] <= h[g]) lo[g] += half;
+        len -= half;
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        if (!ok[g]) continue;
+        const uint64_t e = Q.sbase + lo[g];
+        const uint32_t p = __ldg(A.pay + e);
+        if (p < 0x80000000u) {
+          add_slot(A, Q.out_off, p, av[g], SUM);
+        } else if (p != NONE) {
+          const uint32_t rr = p & 0x7fffffffu;
+          const uint32_t b = __ldg(A.list_off + rr), en = __ldg(A.list_off + rr + 1);
+          for (uint32_t j = b; j < en; ++j) add_slot(A, Q.out_off, __ldg(A.list_ids + j), av[g], SUM);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+}  // namespace sdb
+
+struct sdb_points {
+  int device = 0;
+  uint32_t B = 0;
+  uint64_t n = 0;
+  uint64_t* key = nullptr;
+  uint32_t* x = nullptr;
+  uint32_t* y = nullptr;
+  int32_t* attr = nullptr;
+};
+
+struct sdb_batch {
+  int device = 0;
+  const sdb_points* pts = nullptr;
+  uint32_t Q = 0, NP = 0;
+  sdb::CoverSet cs;
+  sdb::QueryDev* dq = nullptr;
+  std::vector<sdb::QueryDev> hq;
+  uint64_t out_len = 0, max_ranges = 0, candidates = 0;
+  uint32_t* cand = nullptr;
+  uint32_t* ncand = nullptr;
+  uint32_t tile = 4096, ppt = 2;
+  sdb::TileRec* tiles = nullptr;
+  uint64_t ntiles = 0;
+  std::vector<uint64_t> qtile;  // host, Q + 1
+  unsigned long long* heads = nullptr;  // Q + 1 work counters
+  cudaGraphExec_t graph = nullptr;
+  void* g_count = nullptr;
+  void* g_sum = nullptr;
+};
+
+namespace sdb {
+namespace {
+
+sdb_status build_tiles(sdb_batch* b, uint32_t T, cudaStream_t s) {
+  Scratch sc(s);
+  uint64_t *nt, *toff, *dtot;
+  SDB_TRY(sc.get(&nt, b->Q));
+  SDB_TRY(sc.get(&toff, (size_t)b->Q + 1));
+  SDB_TRY(sc.get(&dtot, 1));
+  tile_count_kernel<<<grid_for(b->Q, 128), 128, 0, s>>>(b->cand, b->ncand, b->Q, T, nt);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint64_t>(nt, toff, b->Q, dtot, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(toff + b->Q, dtot, 8, cudaMemcpyDeviceToDevice, s));
+  b->qtile.assign((size_t)b->Q + 1, 0);
+  SDB_TRY_CUDA(cudaMemcpyAsync(b->qtile.data(), toff, ((size_t)b->Q + 1) * 8,
+                               cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  const uint64_t total = b->qtile[b->Q];
+  if (total >= 0xffffffffull) {
+    set_error("batch: %llu tiles exceed the 32-bit range", (unsigned long long)total);
+    return SDB_EINVAL;
+  }
+  if (b->tiles) dfree(b->tiles, s);
+  b->tiles = nullptr;
+  SDB_TRY(dalloc_n(&b->tiles, total, s));
+  tile_fill_kernel<<<grid_for(b->Q, 128), 128, 0, s>>>(b->cand, b->ncand, b->Q, T, toff, b->tiles);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  b->ntiles = total;
+  b->tile = T;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return SDB_OK;
+}
+
+template <int G, bool SUM>
+sdb_status launch_batch_t(const BatchArgs& A, uint32_t lo, uint32_t hi,
+                          unsigned long long* head, cudaStream_t s) {
+  auto kern = batch_kernel<G, SUM>;
+  int per_sm = 0;
+  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0));
+  uint64_t blocks = (uint64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+  if (blocks > hi - lo) blocks = hi - lo;
+  if (blocks == 0) return SDB_OK;
+  kern<<<(unsigned)blocks, THREADS, 0, s>>>(A, lo, hi, head);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  return SDB_OK;
+}
+
+sdb_status launch_batch(const BatchArgs& A, uint32_t ppt, bool sum, uint32_t lo, uint32_t hi,
+                        unsigned long long* head, cudaStream_t s) {
+  if (ppt == 1) return sum ? launch_batch_t<1, true>(A, lo, hi, head, s)
+                           : launch_batch_t<1, false>(A, lo, hi, head, s);
+  if (ppt == 2) return sum ? launch_batch_t<2, true>(A, lo, hi, head, s)
+                           : launch_batch_t<2, false>(A, lo, hi, head, s);
+  return sum ? launch_batch_t<4, true>(A, lo, hi, head, s)
+             : launch_batch_t<4, false>(A, lo, hi, head, s);
+}
+
+BatchArgs batch_args(const sdb_batch* b, uint64_t* count, int64_t* sum) {
+  BatchArgs A;
+  A.x = b->pts->x;
+  A.y = b->pts->y;
+  A.attr = b->pts->attr;
+  A.q = b->dq;
+  A.tiles = b->tiles;
+  A.start = b->cs.start;
+  A.pay = b->cs.pay;
+  A.list_off = b->cs.list_off;
+  A.list_ids = b->cs.list_ids;
+  A.count = reinterpret_cast<unsigned long long*>(count);
+  A.sum = reinterpret_cast<unsigned long long*>(sum);
+  return A;
+}
+
+// the persistent form: clear outputs and the work counter, one launch
+sdb_status run_persistent(sdb_batch* b, uint64_t* count, int64_t* sum, cudaStream_t s) {
+  SDB_TRY_CUDA(cudaMemsetAsync(count, 0, b->out_len * 8, s));
+  if (sum) SDB_TRY_CUDA(cudaMemsetAsync(sum, 0, b->out_len * 8, s));
+  SDB_TRY_CUDA(cudaMemsetAsync(b->heads + b->Q, 0, sizeof(unsigned long long), s));
+  return launch_batch(batch_args(b, count, sum), b->ppt, sum != nullptr, 0, (uint32_t)b->ntiles,
+                      b->heads + b->Q, s);
+}
+
+bool valid_device(int dev) {
+  int cur = -1;
+  return cudaGetDevice(&cur) == cudaSuccess && cur == dev;
+}
+
+}  // namespace
+}  // namespace sdb
+
+using namespace sdb;
+
+extern "C" {
+
+sdb_status sdb_points_create(const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
+                             uint64_t n, uint32_t grid_bits, void* cuda_stream, sdb_points** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return SDB_EINVAL;
+  }
+  *out = nullptr;
+  if (grid_bits < 1 || grid_bits > 30) {
+    set_error("grid_bits %u outside 1..30", grid_bits);
+    return SDB_EINVAL;
+  }
+  if (n == 0 || n >= 0xffffffffull || !d_x || !d_y) {
+    set_error("need 1 <= n < 2^32 points with coordinates");
+    return SDB_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  sdb_points* p = new (std::nothrow) sdb_points();
+  if (!p) {
+    set_error("host allocation failed");
+    return SDB_ENOMEM;
+  }
+  cudaGetDevice(&p->device);
+  p->B = grid_bits;
+  p->n = n;
+  sdb_status st = SDB_OK;
+  {
+    Scratch sc(s);
+    uint64_t* ktmp = nullptr;
+    uint32_t *idx = nullptr, *itmp = nullptr;
+    unsigned int* bad = nullptr;
+    uint64_t* ks = nullptr;
+    uint32_t* is = nullptr;
+    st = dalloc_n(&p->key, n, s);
+    if (st == SDB_OK) st = dalloc_n(&p->x, n, s);
+    if (st == SDB_OK) st = dalloc_n(&p->y, n, s);
+    if (st == SDB_OK) st = dalloc_n(&p->attr, n, s);
+    if (st == SDB_OK) st = sc.get(&ktmp, n);
+    if (st == SDB_OK) st = sc.get(&idx, n);
+    if (st == SDB_OK) st = sc.get(&itmp, n);
+    if (st == SDB_OK) st = sc.get(&bad, 1);
+    if (st == SDB_OK) {
+      cudaMemsetAsync(bad, 0, 4, s);
+      const uint32_t nsteps = (grid_bits + 3) / 4, pad = 4 * nsteps - grid_bits;
+      point_keys_kernel<<<num_sms() * 8, 256, 0, s>>>(d_x, d_y, n, grid_bits, nsteps,
+                                                      (pad & 1u) ? 2u : 0u, p->key, idx, bad);
+      note_launch();
+      if (cudaGetLastError() != cudaSuccess) st = cuda_status(cudaErrorLaunchFailure, "point keys", __FILE__, __LINE__);
+    }
+    if (st == SDB_OK) st = radix_sort_pairs(p->key, idx, ktmp, itmp, n, 2 * grid_bits, s, &ks, &is);
+    if (st == SDB_OK && ks != p->key)
+      st = cudaMemcpyAsync(p->key, ks, n * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+               ? SDB_OK
+               : cuda_status(cudaErrorUnknown, "key copy", __FILE__, __LINE__);
+    if (st == SDB_OK) {
+      gather_points_kernel<<<grid_for(n, 256), 256, 0, s>>>(is, n, d_x, d_y, d_attr, p->x, p->y,
+                                                            p->attr);
+      note_launch();
+      unsigned int hb = 0;
+      cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s);
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = cuda_status(e, "points create", __FILE__, __LINE__);
+      else if (hb) {
+        set_error("a point lies outside the grid [0, 2^%u)", grid_bits);
+        st = SDB_EINVAL;
+      }
+    }
+  }
+  if (st != SDB_OK) {
+    sdb_points_free(p);
+    return st;
+  }
+  *out = p;
+  return SDB_OK;
+}
+
+void sdb_points_free(sdb_points* p) {
+  if (!p) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  void* ps[] = {p->key, p->x, p->y, p->attr};
+  for (void* q : ps)
+    if (q) cudaFreeAsync(q, 0);
+  cudaStreamSynchronize(0);
+  cudaSetDevice(prev);
+  delete p;
+}
+
+sdb_status sdb_batch_create(const sdb_points* pts, const sdb_polygons* polys,
+                            const sdb_query* queries, uint32_t n_queries,
+                            const uint32_t* subset_ids, uint64_t n_subset_ids, void* cuda_stream,
+                            sdb_batch** out) {
+  if (!out || !pts || !polys || !queries || n_queries == 0 || !polys->ring_off || !polys->x ||
+      !polys->y) {
+    set_error("points, polygons, queries and out are required");
+    return SDB_EINVAL;
+  }
+  *out = nullptr;
+  if (!valid_device(pts->device)) {
+    set_error("points live on another device");
+    return SDB_EINVAL;
+  }
+  const uint32_t B = pts->B, P = polys->n_polygons;
+  if (P == 0 || P >= (1u << 26) || polys->ring_off[0] != 0) {
+    set_error("bad polygon set");
+    return SDB_EINVAL;
+  }
+  const uint32_t G = 1u << B;
+  // polygon bounding boxes (and vertex checks)
+  std::vector<uint32_t> bb(4ull * P);
+  for (uint32_t j = 0; j < P; ++j) {
+    if (polys->ring_off[j + 1] < polys->ring_off[j] + 3) {
+      set_error("polygon %u has fewer than 3 vertices", j);
+      return SDB_EINVAL;
+    }
+    uint32_t mnx = ~0u, mny = ~0u, mxx = 0, mxy = 0;
+    for (uint32_t v = polys->ring_off[j]; v < polys->ring_off[j + 1]; ++v) {
+      if (polys->x[v] >= G || polys->y[v] >= G) {
+        set_error("vertex %u outside the grid", v);
+        return SDB_EINVAL;
+      }
+      mnx = std::min(mnx, polys->x[v]);
+      mxx = std::max(mxx, polys->x[v]);
+      mny = std::min(mny, polys->y[v]);
+      mxy = std::max(mxy, polys->y[v]);
+    }
+    bb[4 * j] = mnx;
+    bb[4 * j + 1] = mny;
+    bb[4 * j + 2] = mxx;
+    bb[4 * j + 3] = mxy;
+  }
+  std::vector<CoverQuery> cq(n_queries);
+  std::vector<QueryDev> hq(n_queries);
+  std::vector<uint32_t> pp, pq, ps;
+  uint64_t out_off = 0;
+  for (uint32_t q = 0; q < n_queries; ++q) {
+    const sdb_query& Qu = queries[q];
+    uint32_t k = 0, F = 0;
+    SDB_TRY(sdb_finest_level(B, Qu.eps, &k, &F));
+    if (!(Qu.x0 < Qu.x1 && Qu.y0 < Qu.y1 && Qu.x1 <= G && Qu.y1 <= G)) {
+      set_error("query %u: viewport must be non-empty and inside the grid", q);
+      return SDB_EINVAL;
+    }
+    if ((uint64_t)Qu.poly_off + Qu.poly_cnt > n_subset_ids || (Qu.poly_cnt && !subset_ids)) {
+      set_error("query %u: polygon subset outside the id array", q);
+      return SDB_EINVAL;
+    }
+    if (out_off + Qu.poly_cnt >= 0xffffffffull) {
+      set_error("batch output exceeds 2^32 entries");
+      return SDB_EINVAL;
+    }
+    cq[q] = CoverQuery{F, Qu.x0, Qu.y0, Qu.x1, Qu.y1};
+    QueryDev& d = hq[q];
+    memset(&d, 0, sizeof(d));
+    d.k = k;
+    d.nsteps = (F + 3) / 4;
+    d.st0 = ((4 * d.nsteps - F) & 1u) ? 2u : 0u;
+    d.x0 = Qu.x0;
+    d.y0 = Qu.y0;
+    d.x1 = Qu.x1;
+    d.y1 = Qu.y1;
+    d.out_off = (uint32_t)out_off;
+    // pairs whose polygon's cells can hold viewport points: bounding box grown
+    // by one finest cell
+    const int64_t sgrow = (int64_t)1 << k;
+    for (uint32_t t = 0; t < Qu.poly_cnt; ++t) {
+      const uint32_t j = subset_ids[Qu.poly_off + t];
+      if (j >= P) {
+        set_error("query %u: polygon id %u out of range", q, j);
+        return SDB_EINVAL;
+      }
+      if ((int64_t)bb[4 * j] - sgrow < (int64_t)Qu.x1 && (int64_t)bb[4 * j + 2] + sgrow >= Qu.x0 &&
+          (int64_t)bb[4 * j + 1] - sgrow < (int64_t)Qu.y1 &&
+          (int64_t)bb[4 * j + 3] + sgrow >= Qu.y0) {
+        pp.push_back(j);
+        pq.push_back(q);
+        ps.push_back(t);
+      }
+    }
+    out_off += Qu.poly_cnt;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  sdb_batch* b = new (std::nothrow) sdb_batch();
+  if (!b) {
+    set_error("host allocation failed");
+    return SDB_ENOMEM;
+  }
+  b->device = pts->device;
+  b->pts = pts;
+  b->Q = n_queries;
+  b->NP = (uint32_t)pp.size();
+  b->out_len = out_off;
+  CoverSpec spec;
+  spec.B = B;
+  spec.Q = n_queries;
+  spec.q = cq.data();
+  spec.NP = b->NP;
+  spec.pair_poly = pp.data();
+  spec.pair_query = pq.data();
+  spec.pair_slot = ps.data();
+  sdb_status st = build_coverings(polys, spec, s, &b->cs);
+  if (st == SDB_OK) {
+    for (uint32_t q = 0; q < n_queries; ++q) {
+      hq[q].sbase = b->cs.qoff[q];
+      hq[q].R = (uint32_t)(b->cs.qoff[q + 1] - b->cs.qoff[q] - 1);
+      b->max_ranges = std::max<uint64_t>(b->max_ranges, hq[q].R);
+    }
+    b->hq = hq;
+    st = dalloc_n(&b->dq, n_queries, s);
+  }
+  if (st == SDB_OK)
+    st = cudaMemcpyAsync(b->dq, hq.data(), n_queries * sizeof(QueryDev), cudaMemcpyHostToDevice,
+                         s) == cudaSuccess
+             ? SDB_OK
+             : cuda_status(cudaErrorUnknown, "query copy", __FILE__, __LINE__);
+  if (st == SDB_OK) st = dalloc_n(&b->cand, (size_t)n_queries * MAXC * 2, s);
+  if (st == SDB_OK) st = dalloc_n(&b->ncand, n_queries, s);
+  if (st == SDB_OK) st = dalloc_n(&b->heads, (size_t)n_queries + 1, s);
+  if (st == SDB_OK) {
+    candidates_kernel<<<grid_for(n_queries, 64), 64, 0, s>>>(b->dq, n_queries, pts->key, pts->n, B,
+                                                             b->cand, b->ncand);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) st = cuda_status(cudaErrorLaunchFailure, "candidates", __FILE__, __LINE__);
+  }
+  if (st == SDB_OK) st = build_tiles(b, b->tile, s);
+  if (st == SDB_OK) {
+    // candidate points (for reporting)
+    std::vector<uint32_t> hc((size_t)n_queries * MAXC * 2), hn(n_queries);
+    cudaMemcpy(hc.data(), b->cand, hc.size() * 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(hn.data(), b->ncand, hn.size() * 4, cudaMemcpyDeviceToHost);
+    for (uint32_t q = 0; q < n_queries; ++q)
+      for (uint32_t i = 0; i < hn[q]; ++i)
+        b->candidates += hc[(size_t)q * MAXC * 2 + 2 * i + 1] - hc[(size_t)q * MAXC * 2 + 2 * i];
+  }
+  if (st != SDB_OK) {
+    std::string msg = sdb_last_error();
+    sdb_batch_free(b);
+    set_error("%s", msg.c_str());
+    return st;
+  }
+  *out = b;
+  return SDB_OK;
+}
+
+sdb_status sdb_batch_get_info(const sdb_batch* b, sdb_batch_info* info) {
+  if (!b || !info) {
+    set_error("batch or info is NULL");
+    return SDB_EINVAL;
+  }
+  memset(info, 0, sizeof(*info));
+  info->n_queries = b->Q;
+  info->n_pairs = b->NP;
+  info->out_len = b->out_len;
+  info->n_ranges = b->cs.E - b->Q;
+  info->max_ranges = b->max_ranges;
+  info->n_cells = b->cs.ncells;
+  info->candidates = b->candidates;
+  info->n_tiles = b->ntiles;
+  info->tile = b->tile;
+  info->points_per_thread = b->ppt;
+  return SDB_OK;
+}
+
+sdb_status sdb_batch_run(sdb_batch* b, int mode, uint64_t* d_count, int64_t* d_sum,
+                         void* cuda_stream) {
+  if (!b || !d_count) {
+    set_error("batch or d_count is NULL");
+    return SDB_EINVAL;
+  }
+  if (!valid_device(b->device)) {
+    set_error("batch lives on another device");
+    return SDB_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (mode == SDB_BATCH_PERSISTENT) return run_persistent(b, d_count, d_sum, s);
+  if (mode == SDB_BATCH_PER_QUERY) {
+    SDB_TRY_CUDA(cudaMemsetAsync(d_count, 0, b->out_len * 8, s));
+    if (d_sum) SDB_TRY_CUDA(cudaMemsetAsync(d_sum, 0, b->out_len * 8, s));
+    SDB_TRY_CUDA(cudaMemsetAsync(b->heads, 0, (size_t)b->Q * sizeof(unsigned long long), s));
+    const BatchArgs A = batch_args(b, d_count, d_sum);
+    for (uint32_t q = 0; q < b->Q; ++q)
+      if (b->qtile[q + 1] > b->qtile[q])
+        SDB_TRY(launch_batch(A, b->ppt, d_sum != nullptr, (uint32_t)b->qtile[q],
+                             (uint32_t)b->qtile[q + 1], b->heads + q, s));
+    return SDB_OK;
+  }
+  if (mode == SDB_BATCH_GRAPH) {
+    if (s == nullptr) {
+      set_error("graph mode needs a created stream (the legacy stream cannot be captured)");
+      return SDB_EINVAL;
+    }
+    if (!b->graph || b->g_count != d_count || b->g_sum != d_sum) {
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      SDB_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      sdb_status st = run_persistent(b, d_count, d_sum, s);
+      cudaError_t e = cudaStreamEndCapture(s, &g);
+      if (st != SDB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return cuda_status(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+      }
+      b->g_count = d_count;
+      b->g_sum = d_sum;
+    }
+    SDB_TRY_CUDA(cudaGraphLaunch(b->graph, s));
+    return SDB_OK;
+  }
+  set_error("unknown batch mode %d", mode);
+  return SDB_EINVAL;
+}
+
+sdb_status sdb_batch_autotune(sdb_batch* b, void* cuda_stream, uint32_t* tile_out,
+                              uint32_t* ppt_out) {
+  if (!b) {
+    set_error("batch is NULL");
+    return SDB_EINVAL;
+  }
+  if (!valid_device(b->device)) {
+    set_error("batch lives on another device");
+    return SDB_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Scratch sc(s);
+  uint64_t* cnt;
+  int64_t* sm;
+  SDB_TRY(sc.get(&cnt, b->out_len));
+  SDB_TRY(sc.get(&sm, b->out_len));
+  cudaEvent_t e0, e1;
+  SDB_TRY_CUDA(cudaEventCreate(&e0));
+  SDB_TRY_CUDA(cudaEventCreate(&e1));
+  const uint32_t tiles[] = {1024, 4096, 16384};
+  const uint32_t ppts[] = {1, 2, 4};
+  float best = 1e30f;
+  uint32_t bt = b->tile, bp = b->ppt;
+  sdb_status st = SDB_OK;
+  for (uint32_t T : tiles) {
+    if ((st = build_tiles(b, T, s)) != SDB_OK) break;
+    for (uint32_t G : ppts) {
+      b->ppt = G;
+      float ms = 0;
+      for (int rep = 0; rep < 2 && st == SDB_OK; ++rep) {  // first run warms up
+        cudaEventRecord(e0, s);
+        st = run_persistent(b, cnt, sm, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = SDB_ECUDA;
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (st != SDB_OK) break;
+      if (ms < best) {
+        best = ms;
+        bt = T;
+        bp = G;
+      }
+    }
+    if (st != SDB_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->ppt = bp;
+  if (st == SDB_OK) st = build_tiles(b, bt, s);
+  if (st == SDB_OK) {
+    if (tile_out) *tile_out = bt;
+    if (ppt_out) *ppt_out = bp;
+  }
+  return st;
+}
+
+sdb_status sdb_batch_set_tuning(sdb_batch* b, uint32_t tile, uint32_t points_per_thread,
+                                void* cuda_stream) {
+  if (!b || tile == 0 || !(points_per_thread == 1 || points_per_thread == 2 ||
+                           points_per_thread == 4)) {
+    set_error("batch NULL, tile 0, or points per thread not 1, 2 or 4");
+    return SDB_EINVAL;
+  }
+  b->ppt = points_per_thread;
+  return build_tiles(b, tile, (cudaStream_t)cuda_stream);
+}
+
+sdb_status sdb_batch_query_ranges(const sdb_batch* b, uint32_t* h_ranges) {
+  if (!b || !h_ranges) {
+    set_error("batch or output is NULL");
+    return SDB_EINVAL;
+  }
+  for (uint32_t q = 0; q < b->Q; ++q) h_ranges[q] = b->hq[q].R;
+  return SDB_OK;
+}
+
+void sdb_batch_free(sdb_batch* b) {
+  if (!b) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->cs.release(0);
+  void* ps[] = {b->dq, b->cand, b->ncand, b->tiles, b->heads};
+  for (void* q : ps)
+    if (q) cudaFreeAsync(q, 0);
+  cudaStreamSynchronize(0);
+  cudaSetDevice(prev);
+  delete b;
+}
+
+}  // extern "C"

@@ -39,8 +39,12 @@ struct Edge {
 };
 
 struct Item {
-  uint32_t poly, cx, cy, eoff, ecnt_par;  // ecnt_par: edge count | parity << 31
+  uint32_t pair, cx, cy, eoff, ecnt_par;  // ecnt_par: edge count | parity << 31
 };
+
+__device__ __forceinline__ uint64_t qof(uint64_t key, uint32_t qshift) {
+  return qshift >= 64 ? 0ull : key >> qshift;
+}
 
 // Sign of cross(b - a, q+ - a) with q+ = q + (d, d^2): o - dy*d + dx*d^2.
 // Never zero for a non-degenerate edge.
@@ -88,19 +92,38 @@ __global__ void build_edges_kernel(const uint32_t* __restrict__ ring_off,
   elist[v] = v;
 }
 
-// one warp per polygon: level-0 item (whole grid) with all edges and the
-// parity of (0,0)+
+// one warp per (query, polygon) pair: the level-0 item (whole grid) with all of
+// the polygon's edges and the parity of (0,0)+; a query whose finest level is 0
+// gets the whole grid as one boundary cell instead
 __global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
-                                  const Edge* __restrict__ edges, uint32_t P,
-                                  Item* __restrict__ items) {
-  uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                  const Edge* __restrict__ edges,
+                                  const uint32_t* __restrict__ pair_poly,
+                                  const uint32_t* __restrict__ pair_query,
+                                  const uint32_t* __restrict__ pair_slot,
+                                  const CoverQuery* __restrict__ qs, uint32_t NP, uint32_t qshift,
+                                  Item* __restrict__ items, uint64_t* __restrict__ rec_key,
+                                  uint32_t* __restrict__ rec_val,
+                                  unsigned long long* __restrict__ counters) {
+  uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (j >= P) return;
+  if (p >= NP) return;
+  const uint32_t j = pair_poly[p], qi = pair_query[p];
+  if (qs[qi].F == 0) {
+    if (lane == 0) {
+      unsigned long long r = atomicAdd(&counters[2], 1ull);
+      rec_key[r] = qshift >= 64 ? 0ull : ((uint64_t)qi << qshift);
+      rec_val[r] = pair_slot[p];
+    }
+    return;
+  }
   uint32_t a = ring_off[j], b = ring_off[j + 1];
   uint32_t par = 0;
   for (uint32_t v = a + lane; v < b; v += 32) par ^= pert_ray_cross(edges[v], 0, 0);
   par = __popc(__ballot_sync(FULL, par)) & 1u;
-  if (lane == 0) items[j] = Item{j, 0, 0, a, (b - a) | (par << 31)};
+  if (lane == 0) {
+    unsigned long long i = atomicAdd(&counters[0], 1ull);
+    items[i] = Item{p, 0, 0, a, (b - a) | (par << 31)};
+  }
 }
 
 // One edge against the 2x2 children of a parent square with lower-left corner
@@ -119,7 +142,7 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
 __device__ __forceinline__ uint32_t edge_vs_children(const Edge& e, int64_t px, int64_t py,
                                                      uint32_t sh) {
   const int64_t side = (int64_t)1 << sh;
-  const int64_t dx = (int64_t)e.bx - e.ax, dy = (int64_t)e.by - e.ay;
+  const int64_t dx = (int64_t)e.bx - e.ax, dy = (int64_t)e.by - e.ay;  // (edge direction)
   const int64_t f00 = dx * (py - e.ay) - dy * (px - e.ax);
   const int64_t stepx = -(dy << sh), stepy = dx << sh;
   const int32_t minx = min(e.ax, e.bx), maxx = max(e.ax, e.bx);
@@ -158,17 +181,32 @@ __device__ __forceinline__ uint32_t edge_vs_children(const Edge& e, int64_t px, 
 
 __global__ __launch_bounds__(256) void expand_level_kernel(
     const Item* __restrict__ items, uint32_t n_items, const uint32_t* __restrict__ elist,
-    const Edge* __restrict__ edges, uint32_t B, uint32_t L, uint32_t F,
-    Item* __restrict__ next_items, uint32_t* __restrict__ next_elist,
+    const Edge* __restrict__ edges, const uint32_t* __restrict__ pair_query,
+    const uint32_t* __restrict__ pair_slot, const CoverQuery* __restrict__ qs, uint32_t qshift,
+    uint32_t B, uint32_t L, Item* __restrict__ next_items, uint32_t* __restrict__ next_elist,
     uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val, unsigned long long rec_base,
     unsigned long long* __restrict__ counters) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   bool active = t < n_items;
   Item it{0, 0, 0, 0, 0};
   if (active) it = items[t];
+  const uint32_t qi = active ? pair_query[it.pair] : 0u;
+  CoverQuery Q{0, 0, 0, 0, 0};
+  if (active) Q = qs[qi];
+  const uint32_t F = Q.F;
   const uint32_t cl = L + 1;
   const uint32_t sh = B - cl;
+  const int64_t side = (int64_t)1 << sh;
   const int64_t px = (int64_t)it.cx << (B - L), py = (int64_t)it.cy << (B - L);
+  // children holding lattice points of the query's box [x0, x1) x [y0, y1)
+  uint32_t keep = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int64_t x0 = px + (c & 1) * side, y0 = py + (c >> 1) * side;
+    keep |= (uint32_t)(x0 < (int64_t)Q.x1 && x0 + side > (int64_t)Q.x0 && y0 < (int64_t)Q.y1 &&
+                       y0 + side > (int64_t)Q.y0)
+            << c;
+  }
   const uint32_t ecnt = it.ecnt_par & 0x7fffffffu;
   const uint32_t par = it.ecnt_par >> 31;
   // children c = dy*2 + dx, lower-left corner (px + dx*side, py + dy*side)
@@ -185,6 +223,7 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       uint32_t inside = (par ^ (flip >> c)) & 1u;
+      if (!((keep >> c) & 1u)) continue;
       if (cnt[c] > 0) {
         if (cl == F) {
           ++n_rec;
@@ -203,18 +242,25 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   if (!active) return;
   uint32_t ceoff[4] = {0, 0, 0, 0};
   const uint32_t shift = 2 * (F - cl);
+  const uint64_t qbits = qshift >= 64 ? 0ull : ((uint64_t)qi << qshift);
+  const uint32_t slot = pair_slot[it.pair];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
+    if (!((keep >> c) & 1u)) {
+      cnt[c] = 0;  // dropped: no record, no child item, no edge list
+      continue;
+    }
     uint32_t ccx = 2 * it.cx + (c & 1), ccy = 2 * it.cy + (c >> 1);
     uint32_t inside = (par ^ (flip >> c)) & 1u;
     bool emit = (cnt[c] > 0) ? (cl == F) : (inside != 0);
     if (emit) {
       unsigned long long r = rec_base + ro++;
-      rec_key[r] = hilbert_id(ccx, ccy, cl) << shift;
-      rec_val[r] = it.poly | ((F - cl) << 26);
+      rec_key[r] = qbits | (hilbert_id(ccx, ccy, cl) << shift);
+      rec_val[r] = slot | ((F - cl) << 26);
+      cnt[c] = 0;  // a finest boundary cell needs no edge list
     } else if (cnt[c] > 0) {
       ceoff[c] = (uint32_t)eo;
-      next_items[io++] = Item{it.poly, ccx, ccy, (uint32_t)eo, cnt[c] | (inside << 31)};
+      next_items[io++] = Item{it.pair, ccx, ccy, (uint32_t)eo, cnt[c] | (inside << 31)};
       eo += cnt[c];
     }
   }
@@ -355,44 +401,39 @@ __global__ void sample_kernel(const uint64_t* __restrict__ start, uint32_t strid
   if (j < ns) sample[j] = start[(uint64_t)j * stride];
 }
 
-__global__ void single_cell_kernel(uint64_t* key, uint32_t* val, uint32_t P) {
-  uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < P) {
-    key[j] = 0;
-    val[j] = j;
-  }
-}
 
-// ---- merge without nesting: one sort of the records by id
-// Quadtree cells are either nested or disjoint.  When no record strictly
-// contains another record's start (true for tilings: cells of different
-// polygons are then identical or disjoint), each group of records with the
-// same start is one elementary interval, the gaps between groups are empty
-// intervals, and the canonical ranges follow by merging equal neighbours.
+// ---- merge without nesting: one sort of the records by (query, id)
+// Quadtree cells are either nested or disjoint.  When, within every query, no
+// record strictly contains another record's start (true for tilings and their
+// subsets: cells of different polygons are then identical or disjoint), each
+// group of records with the same key is one elementary interval, the gaps
+// between groups are empty intervals, and the canonical ranges follow by merging
+// equal neighbours.  Keys are (query << qshift) | start.
 
-// groups of equal start; nesting makes the covering take the general path
 __global__ void group_flags_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-                                   uint64_t n, uint32_t* __restrict__ flag,
+                                   uint64_t n, uint32_t qshift, uint32_t* __restrict__ flag,
                                    unsigned int* __restrict__ nested) {
   uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  const uint64_t lo = sk[r];
+  const uint64_t k = sk[r];
   const uint32_t d = sv[r] >> 26;
-  flag[r] = (r == 0 || sk[r - 1] != lo) ? 1u : 0u;
+  flag[r] = (r == 0 || sk[r - 1] != k) ? 1u : 0u;
   if (r + 1 < n) {
-    const uint64_t lo2 = sk[r + 1];
-    if (lo2 == lo ? ((sv[r + 1] >> 26) != d) : (lo2 < lo + (1ull << (2 * d)))) *nested = 1u;
+    const uint64_t k2 = sk[r + 1];
+    if (k2 == k ? ((sv[r + 1] >> 26) != d)
+                : (qof(k2, qshift) == qof(k, qshift) && k2 < k + (1ull << (2 * d))))
+      *nested = 1u;
   }
 }
 
-__global__ void group_heads_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ flag,
+__global__ void group_heads_kernel(const uint32_t* __restrict__ flag,
                                    const uint32_t* __restrict__ gidx, uint64_t n,
                                    uint32_t* __restrict__ gfirst) {
   uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n && flag[r]) gfirst[gidx[r]] = (uint32_t)r;
 }
 
-// per group: its size, and its polygon ids sorted ascending (groups are small:
+// per group: its size, and its slot ids sorted ascending (groups are small:
 // the polygons sharing one cell)
 __global__ void group_sort_kernel(uint32_t* __restrict__ sv, const uint32_t* __restrict__ gfirst,
                                   uint32_t G, uint64_t n, uint32_t* __restrict__ gsize) {
@@ -412,59 +453,86 @@ __global__ void group_sort_kernel(uint32_t* __restrict__ sv, const uint32_t* __r
   gsize[g] = b - a;
 }
 
-// Ranges opened by group g, in id order: an empty gap before it (bit 0, with
-// its start in *gap_lo), the group itself unless it continues the previous
-// group with the same list (bit 1), and after the last group the empty tail
-// up to the top of the id space (bit 2).
-__device__ __forceinline__ uint32_t group_opens(const uint64_t* __restrict__ sk,
-                                                const uint32_t* __restrict__ sv,
-                                                const uint32_t* __restrict__ gfirst,
-                                                const uint32_t* __restrict__ gsize, uint32_t g,
-                                                uint32_t G, uint64_t top, uint64_t* gap_lo,
-                                                uint64_t* hi_out) {
-  const uint32_t a = gfirst[g];
-  const uint64_t lo = sk[a], hi = lo + (1ull << (2 * (sv[a] >> 26)));
+struct GroupCtx {
+  const uint64_t* sk;
+  const uint32_t* sv;
+  const uint32_t* gfirst;
+  const uint32_t* gsize;
+  const CoverQuery* qs;
+  uint32_t G, qshift;
+  uint64_t lomask;
+};
+
+// Ranges opened by group g in its query's id order: an empty gap before it
+// (bit 0, starting at *gap_lo), the group itself unless it continues the
+// previous group of the same query with the same list (bit 1), and after the
+// query's last group the empty tail up to 4^F (bit 2).
+__device__ __forceinline__ uint32_t group_opens(const GroupCtx& c, uint32_t g, uint32_t* q_out,
+                                                uint64_t* lo_out, uint64_t* gap_lo,
+                                                uint64_t* hi_out, bool* first_out) {
+  const uint32_t a = c.gfirst[g];
+  const uint64_t key = c.sk[a];
+  const uint32_t q = (uint32_t)qof(key, c.qshift);
+  const uint64_t lo = key & c.lomask, hi = lo + (1ull << (2 * (c.sv[a] >> 26)));
+  const uint64_t top = 1ull << (2 * c.qs[q].F);
+  const bool first = g == 0 || qof(c.sk[c.gfirst[g - 1]], c.qshift) != q;
   uint32_t gap, fresh;
-  if (g == 0) {
+  if (first) {
     *gap_lo = 0;
     gap = lo > 0;
     fresh = 1;
   } else {
-    const uint32_t pa = gfirst[g - 1];
-    const uint64_t phi = sk[pa] + (1ull << (2 * (sv[pa] >> 26)));
+    const uint32_t pa = c.gfirst[g - 1];
+    const uint64_t phi = (c.sk[pa] & c.lomask) + (1ull << (2 * (c.sv[pa] >> 26)));
     *gap_lo = phi;
     gap = lo > phi;
-    fresh = gap || gsize[g] != gsize[g - 1];
+    fresh = gap || c.gsize[g] != c.gsize[g - 1];
     const uint32_t PM = (1u << 26) - 1u;
-    for (uint32_t t = 0; !fresh && t < gsize[g]; ++t) fresh = (sv[a + t] & PM) != (sv[pa + t] & PM);
+    for (uint32_t t = 0; !fresh && t < c.gsize[g]; ++t)
+      fresh = (c.sv[a + t] & PM) != (c.sv[pa + t] & PM);
   }
+  const bool last = g + 1 == c.G || qof(c.sk[c.gfirst[g + 1]], c.qshift) != q;
+  const uint32_t tail = last && hi < top;
+  *q_out = q;
+  *lo_out = lo;
   *hi_out = hi;
-  const uint32_t tail = (g == G - 1) && hi < top;
+  *first_out = first;
   return gap | (fresh << 1) | (tail << 2);
 }
 
-__global__ void group_count_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-                                   const uint32_t* __restrict__ gfirst,
-                                   const uint32_t* __restrict__ gsize, uint32_t G, uint64_t top,
-                                   uint32_t* __restrict__ nopen) {
+__global__ void group_count_kernel(GroupCtx c, uint32_t* __restrict__ nopen,
+                                   uint32_t* __restrict__ qcount, uint32_t* __restrict__ qfirst) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
-  uint64_t gl, hi;
-  const uint32_t o = group_opens(sk, sv, gfirst, gsize, g, G, top, &gl, &hi);
+  if (g >= c.G) return;
+  uint32_t q;
+  uint64_t lo, gl, hi;
+  bool first;
+  const uint32_t o = group_opens(c, g, &q, &lo, &gl, &hi, &first);
   nopen[g] = __popc(o);
+  atomicAdd(&qcount[q], (uint32_t)__popc(o));
+  if (first) qfirst[q] = g;
 }
 
-__global__ void group_emit_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-                                  const uint32_t* __restrict__ gfirst,
-                                  const uint32_t* __restrict__ gsize,
-                                  const uint32_t* __restrict__ roff, uint32_t G, uint64_t top,
-                                  uint64_t* __restrict__ start, uint32_t* __restrict__ rlen,
-                                  uint32_t* __restrict__ rsrc) {
+// entries of query q: its ranges plus the sentinel (a query without cells has
+// one empty range)
+__global__ void query_sizes_kernel(const uint32_t* __restrict__ qcount,
+                                   const uint32_t* __restrict__ qfirst, uint32_t Q,
+                                   uint64_t* __restrict__ qsize) {
+  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < Q) qsize[q] = (qfirst[q] == NONE ? 1ull : (uint64_t)qcount[q]) + 1ull;
+}
+
+__global__ void group_emit_kernel(GroupCtx c, const uint32_t* __restrict__ gscan,
+                                  const uint32_t* __restrict__ qfirst,
+                                  const uint64_t* __restrict__ qoff, uint64_t* __restrict__ start,
+                                  uint32_t* __restrict__ rlen, uint32_t* __restrict__ rsrc) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
-  uint64_t gl, hi;
-  const uint32_t o = group_opens(sk, sv, gfirst, gsize, g, G, top, &gl, &hi);
-  uint32_t r = roff[g];
+  if (g >= c.G) return;
+  uint32_t q;
+  uint64_t lo, gl, hi;
+  bool first;
+  const uint32_t o = group_opens(c, g, &q, &lo, &gl, &hi, &first);
+  uint64_t r = qoff[q] + (gscan[g] - gscan[qfirst[q]]);
   if (o & 1u) {
     start[r] = gl;
     rlen[r] = 0;
@@ -472,9 +540,9 @@ __global__ void group_emit_kernel(const uint64_t* __restrict__ sk, const uint32_
     ++r;
   }
   if (o & 2u) {
-    start[r] = sk[gfirst[g]];
-    rlen[r] = gsize[g];
-    rsrc[r] = gfirst[g];
+    start[r] = lo;
+    rlen[r] = c.gsize[g];
+    rsrc[r] = c.gfirst[g];
     ++r;
   }
   if (o & 4u) {
@@ -484,17 +552,41 @@ __global__ void group_emit_kernel(const uint64_t* __restrict__ sk, const uint32_
   }
 }
 
+// per query: the sentinel, and the single empty range of a query without cells
+__global__ void query_emit_kernel(const uint32_t* __restrict__ qfirst,
+                                  const uint64_t* __restrict__ qoff,
+                                  const CoverQuery* __restrict__ qs, uint32_t Q,
+                                  uint64_t* __restrict__ start, uint32_t* __restrict__ rlen,
+                                  uint32_t* __restrict__ rsrc) {
+  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  if (qfirst[q] == NONE) {
+    start[qoff[q]] = 0;
+    rlen[qoff[q]] = 0;
+    rsrc[qoff[q]] = 0;
+  }
+  const uint64_t e = qoff[q + 1] - 1;
+  start[e] = 1ull << (2 * qs[q].F);
+  rlen[e] = 0;
+  rsrc[e] = 0;
+}
+
 __global__ void fill_lists_sv_kernel(const uint32_t* __restrict__ sv,
                                      const uint32_t* __restrict__ rlen,
                                      const uint32_t* __restrict__ rsrc,
-                                     const uint32_t* __restrict__ list_off, uint64_t R,
+                                     const uint32_t* __restrict__ list_off, uint64_t E,
                                      uint32_t* __restrict__ list_ids, uint32_t* __restrict__ pay) {
   uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
+  if (r >= E) return;
   const uint32_t PM = (1u << 26) - 1u;
   const uint32_t n = rlen[r], o = list_off[r], s = rsrc[r];
   for (uint32_t t = 0; t < n; ++t) list_ids[o + t] = sv[s + t] & PM;
   pay[r] = n == 0 ? NONE : (n == 1 ? (sv[s] & PM) : (0x80000000u | (uint32_t)r));
+}
+
+__global__ void set_u32_kernel(uint32_t* p, uint64_t n, uint32_t v) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
 }
 
 int bits_for(uint64_t v) {  // bits needed to represent v
@@ -511,13 +603,10 @@ sdb_status read_u64(const unsigned long long* d, unsigned long long* h, int n, c
 
 }  // namespace
 
-static sdb_status finish_ranges(sdb_covering* cov, uint64_t R, uint32_t nids, uint64_t top,
-                                cudaStream_t s);
-
-// records -> canonical ranges, general path (nested records allowed): sweep
-// over all record endpoints (see the file comment)
+// records -> canonical ranges, general path (one query, nested cells allowed):
+// sweep over all record endpoints (see the file comment)
 static sdb_status merge_general(uint64_t* key, uint32_t* val, uint64_t n, uint32_t F, uint32_t P,
-                                cudaStream_t s, sdb_covering* cov) {
+                                cudaStream_t s, CoverSet* out) {
   Scratch sc(s);
   const uint64_t top = 1ull << (2 * F);
   const uint64_t nbp = 2 * n + 2;
@@ -595,59 +684,47 @@ static sdb_status merge_general(uint64_t* key, uint32_t* val, uint64_t n, uint32
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
 
   // persistent arrays
-  SDB_TRY(dalloc_n(&cov->start, (size_t)R + 1, s));
-  SDB_TRY(dalloc_n(&cov->list_off, (size_t)R + 1, s));
-  SDB_TRY(dalloc_n(&cov->pay, (size_t)R, s));
+  SDB_TRY(dalloc_n(&out->start, (size_t)R + 1, s));
+  SDB_TRY(dalloc_n(&out->list_off, (size_t)R + 1, s));
+  SDB_TRY(dalloc_n(&out->pay, (size_t)R + 1, s));  // + sentinel entry
   uint32_t *rlen, *rsrc, *dN;
   SDB_TRY(sc.get(&rlen, R));
   SDB_TRY(sc.get(&rsrc, R));
   SDB_TRY(sc.get(&dN, 1));
-  emit_ranges_kernel<<<grid_for(nint, 256), 256, 0, s>>>(flag, ridx, b, len, eoff, nint, cov->start,
+  emit_ranges_kernel<<<grid_for(nint, 256), 256, 0, s>>>(flag, ridx, b, len, eoff, nint, out->start,
                                                          rlen, rsrc);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  SDB_TRY(exclusive_scan<uint32_t>(rlen, cov->list_off, R, dN, s));
+  SDB_TRY(exclusive_scan<uint32_t>(rlen, out->list_off, R, dN, s));
   uint32_t nids = 0;
   SDB_TRY_CUDA(cudaMemcpyAsync(&nids, dN, sizeof(nids), cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  SDB_TRY(dalloc_n(&cov->list_ids, (size_t)nids, s));
-  fill_lists_kernel<<<grid_for(R, 256), 256, 0, s>>>(ps, pmask, rlen, rsrc, cov->list_off, R,
-                                                      cov->list_ids, cov->pay);
+  SDB_TRY(dalloc_n(&out->list_ids, (size_t)nids, s));
+  fill_lists_kernel<<<grid_for(R, 256), 256, 0, s>>>(ps, pmask, rlen, rsrc, out->list_off, R,
+                                                      out->list_ids, out->pay);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  return finish_ranges(cov, R, nids, top, s);
-}
-
-// sentinel entries, the shared-memory sample of the starts, sizes
-static sdb_status finish_ranges(sdb_covering* cov, uint64_t R, uint32_t nids, uint64_t top,
-                                cudaStream_t s) {
-  finish_kernel<<<1, 1, 0, s>>>(cov->start, cov->list_off, R, top, nids);
+  finish_kernel<<<1, 1, 0, s>>>(out->start, out->list_off, R, top, nids);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  const uint32_t SAMPLE_MAX = 2048;
-  uint64_t keys = (uint64_t)R + 1;
-  uint32_t stride = (uint32_t)((keys + SAMPLE_MAX - 1) / SAMPLE_MAX);
-  if (stride < 1) stride = 1;
-  uint32_t ns = (uint32_t)((keys + stride - 1) / stride);
-  SDB_TRY(dalloc_n(&cov->sample, ns, s));
-  sample_kernel<<<grid_for(ns, 256), 256, 0, s>>>(cov->start, stride, ns, cov->sample);
+  set_u32_kernel<<<1, 1, 0, s>>>(out->pay + R, 1, NONE);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  cov->R = R;
-  cov->nids = nids;
-  cov->sample_n = ns;
-  cov->sample_stride = stride;
-  cov->bytes = ((size_t)R + 1) * 12 + (size_t)R * 4 + (size_t)nids * 4 + (size_t)ns * 8;
+  out->E = (uint64_t)R + 1;
+  out->nids = nids;
+  out->qoff = {0, out->E};
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   return SDB_OK;
 }
 
-// records -> canonical ranges: sort by start once; without nesting (see
-// above) the groups give the ranges directly, otherwise the general sweep runs
-static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, uint32_t F, uint32_t P,
-                                cudaStream_t s, sdb_covering* cov) {
+// records -> canonical ranges: sort by (query, start) once; without nesting
+// (see above) the groups give the ranges directly, otherwise (one query only)
+// the general sweep runs
+static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const CoverSpec& spec,
+                                const CoverQuery* d_qs, uint32_t qshift, int key_bits,
+                                cudaStream_t s, CoverSet* out) {
   Scratch sc(s);
-  const uint64_t top = 1ull << (2 * F);
+  const uint32_t Q = spec.Q;
   if (n >= 0xffffffffull) {
     set_error("covering: %llu cells exceed the 32-bit index range", (unsigned long long)n);
     return SDB_ENOMEM;
@@ -656,7 +733,7 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, uint32
   uint32_t *vtmp, *sv;
   SDB_TRY(sc.get(&ktmp, n));
   SDB_TRY(sc.get(&vtmp, n));
-  SDB_TRY(radix_sort_pairs(key, val, ktmp, vtmp, n, bits_for(top), s, &sk, &sv));
+  SDB_TRY(radix_sort_pairs(key, val, ktmp, vtmp, n, key_bits, s, &sk, &sv));
   uint32_t *flag, *gidx, *dG;
   unsigned int* nested;
   SDB_TRY(sc.get(&flag, n));
@@ -664,77 +741,138 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, uint32
   SDB_TRY(sc.get(&dG, 1));
   SDB_TRY(sc.get(&nested, 1));
   SDB_TRY_CUDA(cudaMemsetAsync(nested, 0, sizeof(unsigned int), s));
-  group_flags_kernel<<<grid_for(n, 256), 256, 0, s>>>(sk, sv, n, flag, nested);
-  note_launch();
-  SDB_TRY_CUDA(cudaGetLastError());
+  if (n) {
+    group_flags_kernel<<<grid_for(n, 256), 256, 0, s>>>(sk, sv, n, qshift, flag, nested);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+  }
   SDB_TRY(exclusive_scan<uint32_t>(flag, gidx, n, dG, s));
   uint32_t hG[2] = {0, 0};
   SDB_TRY_CUDA(cudaMemcpyAsync(&hG[0], dG, 4, cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaMemcpyAsync(&hG[1], nested, 4, cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   if (hG[1]) {
+    if (Q != 1) {
+      set_error("batched coverings need polygons that do not overlap within a query");
+      return SDB_EINVAL;
+    }
     sc.release(flag);
     sc.release(gidx);
-    return merge_general(sk, sv, n, F, P, s, cov);
+    uint32_t P = 0;
+    for (uint32_t i = 0; i < spec.NP; ++i) P = spec.pair_slot[i] + 1 > P ? spec.pair_slot[i] + 1 : P;
+    return merge_general(sk, sv, n, spec.q[0].F, P, s, out);
   }
   const uint32_t G = hG[0];
-  uint32_t *gfirst, *gsize, *nopen, *roff, *dR;
+  uint32_t *gfirst, *gsize, *nopen, *gscan, *qcount, *qfirst;
+  uint64_t *qsize, *qoff, *dE;
   SDB_TRY(sc.get(&gfirst, G));
   SDB_TRY(sc.get(&gsize, G));
   SDB_TRY(sc.get(&nopen, G));
-  SDB_TRY(sc.get(&roff, G));
-  SDB_TRY(sc.get(&dR, 1));
-  group_heads_kernel<<<grid_for(n, 256), 256, 0, s>>>(sk, flag, gidx, n, gfirst);
+  SDB_TRY(sc.get(&gscan, G));
+  SDB_TRY(sc.get(&qcount, Q));
+  SDB_TRY(sc.get(&qfirst, Q));
+  SDB_TRY(sc.get(&qsize, Q));
+  SDB_TRY(sc.get(&qoff, (size_t)Q + 1));
+  SDB_TRY(sc.get(&dE, 1));
+  SDB_TRY_CUDA(cudaMemsetAsync(qcount, 0, (size_t)Q * 4, s));
+  set_u32_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, Q, NONE);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  group_sort_kernel<<<grid_for(G, 256), 256, 0, s>>>(sv, gfirst, G, n, gsize);
+  GroupCtx gc{sk, sv, gfirst, gsize, d_qs, G, qshift,
+              qshift >= 64 ? ~0ull : ((1ull << qshift) - 1ull)};
+  if (G) {
+    group_heads_kernel<<<grid_for(n, 256), 256, 0, s>>>(flag, gidx, n, gfirst);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    group_sort_kernel<<<grid_for(G, 256), 256, 0, s>>>(sv, gfirst, G, n, gsize);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    group_count_kernel<<<grid_for(G, 256), 256, 0, s>>>(gc, nopen, qcount, qfirst);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+  }
+  SDB_TRY(exclusive_scan<uint32_t>(nopen, gscan, G, nullptr, s));
+  query_sizes_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qcount, qfirst, Q, qsize);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  group_count_kernel<<<grid_for(G, 256), 256, 0, s>>>(sk, sv, gfirst, gsize, G, top, nopen);
-  note_launch();
-  SDB_TRY_CUDA(cudaGetLastError());
-  SDB_TRY(exclusive_scan<uint32_t>(nopen, roff, G, dR, s));
-  uint32_t R = 0;
-  SDB_TRY_CUDA(cudaMemcpyAsync(&R, dR, sizeof(R), cudaMemcpyDeviceToHost, s));
+  SDB_TRY(exclusive_scan<uint64_t>(qsize, qoff, Q, dE, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(qoff + Q, dE, 8, cudaMemcpyDeviceToDevice, s));
+  out->qoff.assign((size_t)Q + 1, 0);
+  SDB_TRY_CUDA(cudaMemcpyAsync(out->qoff.data(), qoff, ((size_t)Q + 1) * 8, cudaMemcpyDeviceToHost,
+                               s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  SDB_TRY(dalloc_n(&cov->start, (size_t)R + 1, s));
-  SDB_TRY(dalloc_n(&cov->list_off, (size_t)R + 1, s));
-  SDB_TRY(dalloc_n(&cov->pay, (size_t)R, s));
+  const uint64_t E = out->qoff[Q];
+  if (E >= 0x7fffffffull) {  // entry indices travel in 31 bits of the packed payload
+    set_error("covering: %llu ranges exceed the 32-bit index range", (unsigned long long)E);
+    return SDB_ENOMEM;
+  }
+  SDB_TRY(dalloc_n(&out->start, E, s));
+  SDB_TRY(dalloc_n(&out->list_off, E, s));
+  SDB_TRY(dalloc_n(&out->pay, E, s));
   uint32_t *rlen, *rsrc, *dN;
-  SDB_TRY(sc.get(&rlen, R));
-  SDB_TRY(sc.get(&rsrc, R));
+  SDB_TRY(sc.get(&rlen, E));
+  SDB_TRY(sc.get(&rsrc, E));
   SDB_TRY(sc.get(&dN, 1));
-  group_emit_kernel<<<grid_for(G, 256), 256, 0, s>>>(sk, sv, gfirst, gsize, roff, G, top,
-                                                      cov->start, rlen, rsrc);
+  if (G) {
+    group_emit_kernel<<<grid_for(G, 256), 256, 0, s>>>(gc, gscan, qfirst, qoff, out->start, rlen,
+                                                        rsrc);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+  }
+  query_emit_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, qoff, d_qs, Q, out->start, rlen, rsrc);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  SDB_TRY(exclusive_scan<uint32_t>(rlen, cov->list_off, R, dN, s));
+  SDB_TRY(exclusive_scan<uint32_t>(rlen, out->list_off, E, dN, s));
   uint32_t nids = 0;
   SDB_TRY_CUDA(cudaMemcpyAsync(&nids, dN, sizeof(nids), cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  SDB_TRY(dalloc_n(&cov->list_ids, (size_t)nids, s));
-  fill_lists_sv_kernel<<<grid_for(R, 256), 256, 0, s>>>(sv, rlen, rsrc, cov->list_off, R,
-                                                         cov->list_ids, cov->pay);
+  SDB_TRY(dalloc_n(&out->list_ids, (size_t)nids, s));
+  fill_lists_sv_kernel<<<grid_for(E, 256), 256, 0, s>>>(sv, rlen, rsrc, out->list_off, E,
+                                                         out->list_ids, out->pay);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  return finish_ranges(cov, R, nids, top, s);
+  out->E = E;
+  out->nids = nids;
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  return SDB_OK;
 }
 
-sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,
-                                 sdb_covering* cov) {
+void CoverSet::release(cudaStream_t s) {
+  dfree(start, s);
+  dfree(list_off, s);
+  dfree(list_ids, s);
+  dfree(pay, s);
+  start = nullptr;
+  list_off = nullptr;
+  list_ids = nullptr;
+  pay = nullptr;
+}
+
+sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cudaStream_t s,
+                           CoverSet* out) {
   const uint32_t P = polys->n_polygons;
   const uint32_t V = polys->ring_off[P];
-  const uint32_t F = B - k;
-  cov->B = B;
-  cov->k = k;
-  cov->F = F;
-  cov->P = P;
+  const uint32_t B = spec.B, Q = spec.Q, NP = spec.NP;
+  uint32_t Fmax = 0;
+  for (uint32_t q = 0; q < Q; ++q) Fmax = spec.q[q].F > Fmax ? spec.q[q].F : Fmax;
+  // record keys: (query << qshift) | start; one query needs no query bits
+  uint32_t qshift = 64;
+  int key_bits = bits_for(1ull << (2 * Fmax));
+  if (Q > 1) {
+    qshift = 2 * Fmax + 1;
+    key_bits = (int)qshift + bits_for(Q - 1);
+    if (key_bits > 64) {
+      set_error("batched coverings: %u queries at finest level %u do not fit 64-bit keys", Q, Fmax);
+      return SDB_EINVAL;
+    }
+  }
   Scratch sc(s);
   // polygons -> device edges
   std::vector<uint32_t> vpoly(V);
   for (uint32_t j = 0; j < P; ++j)
     for (uint32_t v = polys->ring_off[j]; v < polys->ring_off[j + 1]; ++v) vpoly[v] = j;
-  uint32_t *d_off, *d_x, *d_y, *d_vp, *elist;
+  uint32_t *d_off, *d_x, *d_y, *d_vp, *elist, *d_pp, *d_pq, *d_ps;
+  CoverQuery* d_qs;
   Edge* edges;
   SDB_TRY(sc.get(&d_off, P + 1));
   SDB_TRY(sc.get(&d_x, V));
@@ -742,17 +880,27 @@ sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t
   SDB_TRY(sc.get(&d_vp, V));
   SDB_TRY(sc.get(&edges, V));
   SDB_TRY(sc.get(&elist, V));
+  SDB_TRY(sc.get(&d_pp, NP));
+  SDB_TRY(sc.get(&d_pq, NP));
+  SDB_TRY(sc.get(&d_ps, NP));
+  SDB_TRY(sc.get(&d_qs, Q));
   SDB_TRY_CUDA(cudaMemcpyAsync(d_off, polys->ring_off, (P + 1) * 4ull, cudaMemcpyHostToDevice, s));
   SDB_TRY_CUDA(cudaMemcpyAsync(d_x, polys->x, V * 4ull, cudaMemcpyHostToDevice, s));
   SDB_TRY_CUDA(cudaMemcpyAsync(d_y, polys->y, V * 4ull, cudaMemcpyHostToDevice, s));
   SDB_TRY_CUDA(cudaMemcpyAsync(d_vp, vpoly.data(), V * 4ull, cudaMemcpyHostToDevice, s));
+  if (NP) {
+    SDB_TRY_CUDA(cudaMemcpyAsync(d_pp, spec.pair_poly, NP * 4ull, cudaMemcpyHostToDevice, s));
+    SDB_TRY_CUDA(cudaMemcpyAsync(d_pq, spec.pair_query, NP * 4ull, cudaMemcpyHostToDevice, s));
+    SDB_TRY_CUDA(cudaMemcpyAsync(d_ps, spec.pair_slot, NP * 4ull, cudaMemcpyHostToDevice, s));
+  }
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_qs, spec.q, Q * sizeof(CoverQuery), cudaMemcpyHostToDevice, s));
   build_edges_kernel<<<grid_for(V, 256), 256, 0, s>>>(d_off, d_x, d_y, d_vp, V, edges, elist);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
 
   // record buffer, grown on demand
   uint64_t rec_cap = 1 << 20, n_rec = 0;
-  if (rec_cap < 8ull * P) rec_cap = 8ull * P;
+  if (rec_cap < 8ull * NP) rec_cap = 8ull * NP;
   uint64_t* rkey;
   uint32_t* rval;
   SDB_TRY(dalloc_n(&rkey, rec_cap, s));
@@ -769,79 +917,132 @@ sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t
 
   unsigned long long* ctr;
   SDB_TRY(sc.get(&ctr, 3));
-  if (F == 0) {
-    single_cell_kernel<<<grid_for(P, 256), 256, 0, s>>>(rkey, rval, P);
+  SDB_TRY_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
+  Item* items = nullptr;
+  SDB_TRY(dalloc_n(&items, NP, s));
+  if (NP) {
+    root_items_kernel<<<grid_for((size_t)NP * 32, 256), 256, 0, s>>>(
+        d_off, edges, d_pp, d_pq, d_ps, d_qs, NP, qshift, items, rkey, rval, ctr);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
-    n_rec = P;
-  } else {
-    Item* items;
-    SDB_TRY(dalloc_n(&items, P, s));
-    root_items_kernel<<<grid_for((size_t)P * 32, 256), 256, 0, s>>>(d_off, edges, P, items);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
-    uint32_t* cur_el = elist;
-    bool own_el = false;
-    uint64_t n_items = P, n_edges = V;
-    for (uint32_t L = 0; L < F && n_items > 0; ++L) {
-      const bool last = (L + 1 == F);
-      // capacity: every record and every child item comes from one of 4
-      // children; every child edge entry from one (edge, child) pair
-      if (n_rec + 4 * n_items > rec_cap) {
-        uint64_t nc = rec_cap;
-        while (nc < n_rec + 4 * n_items) nc *= 2;
-        uint64_t* k2;
-        uint32_t* v2;
-        SDB_TRY(dalloc_n(&k2, nc, s));
-        SDB_TRY(dalloc_n(&v2, nc, s));
-        SDB_TRY_CUDA(cudaMemcpyAsync(k2, rkey, n_rec * 8, cudaMemcpyDeviceToDevice, s));
-        SDB_TRY_CUDA(cudaMemcpyAsync(v2, rval, n_rec * 4, cudaMemcpyDeviceToDevice, s));
-        dfree(rkey, s);
-        dfree(rval, s);
-        rkey = k2;
-        rval = v2;
-        rec_cap = nc;
-      }
-      if (4 * n_items > 0xffffffffull || 4 * n_edges > 0xffffffffull) {
-        set_error("covering: level %u frontier too large (%llu cells, %llu edge entries)", L,
-                  (unsigned long long)n_items, (unsigned long long)n_edges);
-        dfree(items, s);
-        if (own_el) dfree(cur_el, s);
-        return SDB_ENOMEM;
-      }
-      Item* nitems = nullptr;
-      uint32_t* nel = nullptr;
-      if (!last) {
-        sdb_status st = dalloc_n(&nitems, 4 * n_items, s);
-        if (st == SDB_OK) st = dalloc_n(&nel, 4 * n_edges, s);
-        if (st != SDB_OK) {
-          dfree(items, s);
-          if (own_el) dfree(cur_el, s);
-          if (nitems) dfree(nitems, s);
-          return st;
-        }
-      }
-      SDB_TRY_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
-      expand_level_kernel<<<grid_for(n_items, 256), 256, 0, s>>>(
-          items, (uint32_t)n_items, cur_el, edges, B, L, F, nitems, nel, rkey, rval, n_rec, ctr);
-      note_launch();
-      SDB_TRY_CUDA(cudaGetLastError());
-      unsigned long long h[3];
-      SDB_TRY(read_u64(ctr, h, 3, s));
+  }
+  unsigned long long h0[3];
+  SDB_TRY(read_u64(ctr, h0, 3, s));
+  uint64_t n_items = h0[0], n_edges = 0;
+  n_rec = h0[2];
+  for (uint32_t i = 0; i < NP; ++i)
+    if (spec.q[spec.pair_query[i]].F > 0)
+      n_edges += polys->ring_off[spec.pair_poly[i] + 1] - polys->ring_off[spec.pair_poly[i]];
+  uint32_t* cur_el = elist;
+  bool own_el = false;
+  for (uint32_t L = 0; L < Fmax && n_items > 0; ++L) {
+    const bool last = (L + 1 == Fmax);
+    // capacity: every record and every child item comes from one of 4
+    // children; every child edge entry from one (edge, child) pair
+    if (n_rec + 4 * n_items > rec_cap) {
+      uint64_t nc = rec_cap;
+      while (nc < n_rec + 4 * n_items) nc *= 2;
+      uint64_t* k2;
+      uint32_t* v2;
+      SDB_TRY(dalloc_n(&k2, nc, s));
+      SDB_TRY(dalloc_n(&v2, nc, s));
+      SDB_TRY_CUDA(cudaMemcpyAsync(k2, rkey, n_rec * 8, cudaMemcpyDeviceToDevice, s));
+      SDB_TRY_CUDA(cudaMemcpyAsync(v2, rval, n_rec * 4, cudaMemcpyDeviceToDevice, s));
+      dfree(rkey, s);
+      dfree(rval, s);
+      rkey = k2;
+      rval = v2;
+      rec_cap = nc;
+    }
+    if (4 * n_items > 0xffffffffull || 4 * n_edges > 0xffffffffull) {
+      set_error("covering: level %u frontier too large (%llu cells, %llu edge entries)", L,
+                (unsigned long long)n_items, (unsigned long long)n_edges);
       dfree(items, s);
       if (own_el) dfree(cur_el, s);
-      items = nitems;
-      cur_el = nel;
-      own_el = true;
-      n_items = last ? 0 : h[0];
-      n_edges = h[1];
-      n_rec += h[2];
+      return SDB_ENOMEM;
     }
-    if (items) dfree(items, s);
-    if (own_el && cur_el) dfree(cur_el, s);
+    Item* nitems = nullptr;
+    uint32_t* nel = nullptr;
+    if (!last) {
+      sdb_status st = dalloc_n(&nitems, 4 * n_items, s);
+      if (st == SDB_OK) st = dalloc_n(&nel, 4 * n_edges, s);
+      if (st != SDB_OK) {
+        dfree(items, s);
+        if (own_el) dfree(cur_el, s);
+        if (nitems) dfree(nitems, s);
+        return st;
+      }
+    }
+    SDB_TRY_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
+    expand_level_kernel<<<grid_for(n_items, 256), 256, 0, s>>>(
+        items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift, B, L, nitems, nel, rkey,
+        rval, n_rec, ctr);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    unsigned long long h[3];
+    SDB_TRY(read_u64(ctr, h, 3, s));
+    dfree(items, s);
+    if (own_el) dfree(cur_el, s);
+    items = nitems;
+    cur_el = nel;
+    own_el = true;
+    n_items = last ? 0 : h[0];
+    n_edges = h[1];
+    n_rec += h[2];
   }
-  cov->ncells = n_rec;
-  return merge_records(rkey, rval, n_rec, F, P, s, cov);
+  if (items) dfree(items, s);
+  if (own_el && cur_el) dfree(cur_el, s);
+  out->ncells = n_rec;
+  return merge_records(rkey, rval, n_rec, spec, d_qs, qshift, key_bits, s, out);
+}
+
+sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,
+                                 sdb_covering* cov) {
+  const uint32_t P = polys->n_polygons;
+  const uint32_t F = B - k;
+  cov->B = B;
+  cov->k = k;
+  cov->F = F;
+  cov->P = P;
+  std::vector<uint32_t> pp(P), pq(P, 0);
+  for (uint32_t j = 0; j < P; ++j) pp[j] = j;
+  CoverQuery q{F, 0, 0, 1u << B, 1u << B};
+  CoverSpec spec;
+  spec.B = B;
+  spec.Q = 1;
+  spec.q = &q;
+  spec.NP = P;
+  spec.pair_poly = pp.data();
+  spec.pair_query = pq.data();
+  spec.pair_slot = pp.data();
+  CoverSet cs;
+  sdb_status st = build_coverings(polys, spec, s, &cs);
+  if (st != SDB_OK) {
+    cs.release(s);
+    return st;
+  }
+  cov->start = cs.start;
+  cov->list_off = cs.list_off;
+  cov->list_ids = cs.list_ids;
+  cov->pay = cs.pay;
+  cov->R = cs.E - 1;
+  cov->nids = cs.nids;
+  cov->ncells = cs.ncells;
+  // shared-memory sample of the starts for the top of the binary search
+  const uint32_t SAMPLE_MAX = 2048;
+  const uint64_t keys = cov->R + 1;
+  uint32_t stride = (uint32_t)((keys + SAMPLE_MAX - 1) / SAMPLE_MAX);
+  if (stride < 1) stride = 1;
+  const uint32_t ns = (uint32_t)((keys + stride - 1) / stride);
+  SDB_TRY(dalloc_n(&cov->sample, ns, s));
+  sample_kernel<<<grid_for(ns, 256), 256, 0, s>>>(cov->start, stride, ns, cov->sample);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  cov->sample_n = ns;
+  cov->sample_stride = stride;
+  cov->bytes = (size_t)keys * 16 + (size_t)cov->nids * 4 + (size_t)ns * 8;
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  return SDB_OK;
 }
 
 }  // namespace sdb

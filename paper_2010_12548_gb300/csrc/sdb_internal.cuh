@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "sdb.h"
 
@@ -169,7 +170,39 @@ struct sdb_covering {
 
 namespace sdb {
 
-// cover.cu
+// cover.cu -------------------------------------------------------------------
+// Several coverings can be built in one level-synchronous pass.  Query q covers
+// the polygons of its (query, polygon) pairs at finest level F, keeping only
+// cells that hold lattice points of its box [x0, x1) x [y0, y1); each pair's
+// polygon is reported under the pair's slot id.  A single covering is one
+// query over the whole grid whose slots are the polygon ids.
+struct CoverQuery {
+  uint32_t F, x0, y0, x1, y1;
+};
+struct CoverSpec {
+  uint32_t B = 0;
+  uint32_t Q = 0;
+  const CoverQuery* q = nullptr;        // host, Q entries
+  uint32_t NP = 0;                      // pairs
+  const uint32_t* pair_poly = nullptr;  // host, NP entries each
+  const uint32_t* pair_query = nullptr;
+  const uint32_t* pair_slot = nullptr;
+};
+// Result, device arrays from the library pool.  Query q's ranges are entries
+// [qoff[q], qoff[q+1] - 1) of start/list_off/pay; entry qoff[q+1] - 1 is a
+// sentinel with start 4^F and an empty list, so list_off[i+1] - list_off[i] is
+// the length of range i's list for every range.
+struct CoverSet {
+  uint64_t* start = nullptr;     // E
+  uint32_t* list_off = nullptr;  // E
+  uint32_t* list_ids = nullptr;  // nids (slot ids)
+  uint32_t* pay = nullptr;       // E: empty / single slot / 2^31 | entry index
+  uint64_t E = 0, nids = 0, ncells = 0;
+  std::vector<uint64_t> qoff;    // host, Q + 1
+  void release(cudaStream_t s);
+};
+sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cudaStream_t s,
+                           CoverSet* out);
 sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,
                                  sdb_covering* cov);
 // learned.cu

@@ -39,6 +39,20 @@ class CoveringInfo(C.Structure):
                 ("reserved", C.c_uint32)]
 
 
+class Query(C.Structure):
+    _fields_ = [("x0", C.c_uint32), ("y0", C.c_uint32), ("x1", C.c_uint32), ("y1", C.c_uint32),
+                ("eps", C.c_uint64), ("poly_off", C.c_uint32), ("poly_cnt", C.c_uint32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_queries", C.c_uint32), ("n_pairs", C.c_uint32), ("out_len", C.c_uint64),
+                ("n_ranges", C.c_uint64), ("max_ranges", C.c_uint64), ("n_cells", C.c_uint64),
+                ("candidates", C.c_uint64), ("n_tiles", C.c_uint64), ("tile", C.c_uint32),
+                ("points_per_thread", C.c_uint32)]
+
+
+BATCH_PERSISTENT, BATCH_PER_QUERY, BATCH_GRAPH = 0, 1, 2
+
 _lib = None
 
 
@@ -63,6 +77,15 @@ def lib():
             "sdb_last_error": ([], C.c_char_p),
             "sdb_launch_count": ([], U64),
             "sdb_covering_index_stats": ([P, P, P], I),
+            "sdb_points_create": ([P, P, P, U64, U32, P, P], I),
+            "sdb_points_free": ([P], None),
+            "sdb_batch_create": ([P, P, P, U32, P, U64, P, P], I),
+            "sdb_batch_get_info": ([P, P], I),
+            "sdb_batch_query_ranges": ([P, P], I),
+            "sdb_batch_run": ([P, I, P, P, P], I),
+            "sdb_batch_autotune": ([P, P, P, P], I),
+            "sdb_batch_set_tuning": ([P, U32, U32, P], I),
+            "sdb_batch_free": ([P], None),
             "sdb_join_aggregate_host_noalloc": ([P, P, P, U64, P, I, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -228,6 +251,100 @@ def covering_export(cov: Covering):
 def launch_count() -> int:
     """Kernels launched by libsdb.so in this process so far."""
     return int(lib().sdb_launch_count())
+
+
+class Points:
+    """Resident, Hilbert-ordered point set (owns the library handle)."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h and self._h.value:
+            lib().sdb_points_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def points_create(x, y, attr, grid_bits: int, stream=None) -> Points:
+    """sdb_points_create from device tensors (4-byte elements)."""
+    out = C.c_void_p()
+    _check(lib().sdb_points_create(_dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), x.numel(), grid_bits,
+                                   _stream(stream), C.byref(out)))
+    return Points(out.value)
+
+
+class Batch:
+    """Prepared batch of viewport queries (owns the library handle; keeps the
+    point set it was built on alive)."""
+
+    def __init__(self, handle: int, points: Points):
+        self._h = C.c_void_p(handle)
+        self.points = points
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> BatchInfo:
+        inf = BatchInfo()
+        _check(lib().sdb_batch_get_info(self._h, C.byref(inf)))
+        return inf
+
+    def query_ranges(self) -> np.ndarray:
+        r = np.zeros(self.info().n_queries, np.uint32)
+        _check(lib().sdb_batch_query_ranges(self._h, _np_ptr(r)))
+        return r
+
+    def free(self):
+        if self._h and self._h.value:
+            lib().sdb_batch_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def batch_create(points: Points, polys, queries, subset_ids, stream=None) -> Batch:
+    """sdb_batch_create.  queries: a sequence of (x0, y0, x1, y1, eps, poly_off,
+    poly_cnt) tuples or a numpy structured/2-D array with those columns."""
+    off = np.ascontiguousarray(polys.ring_off, np.uint32)
+    x = np.ascontiguousarray(polys.x, np.uint32)
+    y = np.ascontiguousarray(polys.y, np.uint32)
+    sp = _Polys(len(off) - 1, _np_ptr(off), _np_ptr(x), _np_ptr(y))
+    qs = (Query * len(queries))(*[Query(*[int(v) for v in q]) for q in queries])
+    ids = np.ascontiguousarray(subset_ids, np.uint32)
+    out = C.c_void_p()
+    _check(lib().sdb_batch_create(points.handle, C.byref(sp), qs, len(queries), _np_ptr(ids),
+                                  len(ids), _stream(stream), C.byref(out)))
+    return Batch(out.value, points)
+
+
+def batch_run(batch: Batch, mode: int, count, sum_=None, stream=None):
+    _check(lib().sdb_batch_run(batch.handle, mode, _dptr(count, 8), _dptr(sum_, 8),
+                               _stream(stream)))
+
+
+def batch_autotune(batch: Batch, stream=None) -> tuple[int, int]:
+    t, p = C.c_uint32(), C.c_uint32()
+    _check(lib().sdb_batch_autotune(batch.handle, _stream(stream), C.byref(t), C.byref(p)))
+    return t.value, p.value
+
+
+def batch_set_tuning(batch: Batch, tile: int, points_per_thread: int, stream=None):
+    _check(lib().sdb_batch_set_tuning(batch.handle, tile, points_per_thread, _stream(stream)))
 
 
 def status_string(st: int) -> str:

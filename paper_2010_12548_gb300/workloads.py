@@ -20,6 +20,7 @@ All randomness comes from numpy's PCG64 seeded per workload.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -84,11 +85,16 @@ def _orient(ax, ay, bx, by, cx, cy):
     return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
 
 
+def _shift(a, k):
+    """a rotated left by k (a cheaper np.roll(a, -k) for 1-D arrays)."""
+    return np.concatenate((a[k:], a[:k]))
+
+
 def ring_is_simple(rx: np.ndarray, ry: np.ndarray) -> bool:
     """Exact integer check that a closed ring has no self-contact.
 
     Non-adjacent edges must not meet (closed-segment test); adjacent edges
-    must not fold back onto each other.  O(V^2), vectorised per edge.
+    must not fold back onto each other.  O(V^2), one pairwise pass.
     """
     rx = np.asarray(rx, np.int64)
     ry = np.asarray(ry, np.int64)
@@ -96,46 +102,44 @@ def ring_is_simple(rx: np.ndarray, ry: np.ndarray) -> bool:
     if n < 3:
         return False
     ax, ay = rx, ry
-    bx, by = np.roll(rx, -1), np.roll(ry, -1)
+    bx, by = _shift(rx, 1), _shift(ry, 1)
     if np.any((ax == bx) & (ay == by)):
         return False
     # adjacent edges: fold-back = collinear with opposite direction
-    cx, cy = np.roll(rx, -2), np.roll(ry, -2)
+    cx, cy = _shift(rx, 2), _shift(ry, 2)
     cr = _orient(ax, ay, bx, by, cx, cy)
     dot = (bx - ax) * (cx - bx) + (by - ay) * (cy - by)
     if np.any((cr == 0) & (dot < 0)):
         return False
     if n == 3:
         return _orient(ax[0], ay[0], bx[0], by[0], cx[0], cy[0]) != 0
-    for i in range(n):
-        # edges j not adjacent to i: j in [i+2, i+n-2]
-        js = (i + np.arange(2, n - 1)) % n
-        px, py, qx, qy = ax[i], ay[i], bx[i], by[i]
-        sx, sy, tx, ty = ax[js], ay[js], bx[js], by[js]
-        o1 = np.sign(_orient(px, py, qx, qy, sx, sy))
-        o2 = np.sign(_orient(px, py, qx, qy, tx, ty))
-        o3 = np.sign(_orient(sx, sy, tx, ty, px, py))
-        o4 = np.sign(_orient(sx, sy, tx, ty, qx, qy))
-        proper = (o1 * o2 < 0) & (o3 * o4 < 0)
-        if np.any(proper):
-            return False
+    # all pairs (i, j) of non-adjacent edges, i < j
+    i, j = np.triu_indices(n, 2)
+    keep = ~((i == 0) & (j == n - 1))
+    i, j = i[keep], j[keep]
+    px, py, qx, qy = ax[i], ay[i], bx[i], by[i]
+    sx, sy, tx, ty = ax[j], ay[j], bx[j], by[j]
+    o1 = np.sign(_orient(px, py, qx, qy, sx, sy))
+    o2 = np.sign(_orient(px, py, qx, qy, tx, ty))
+    o3 = np.sign(_orient(sx, sy, tx, ty, px, py))
+    o4 = np.sign(_orient(sx, sy, tx, ty, qx, qy))
+    if np.any((o1 * o2 < 0) & (o3 * o4 < 0)):
+        return False
 
-        def within(ux, uy, vx, vy, wx, wy):
-            return ((np.minimum(ux, vx) <= wx) & (wx <= np.maximum(ux, vx)) &
-                    (np.minimum(uy, vy) <= wy) & (wy <= np.maximum(uy, vy)))
-        touch = (((o1 == 0) & within(px, py, qx, qy, sx, sy)) |
-                 ((o2 == 0) & within(px, py, qx, qy, tx, ty)) |
-                 ((o3 == 0) & within(sx, sy, tx, ty, px, py)) |
-                 ((o4 == 0) & within(sx, sy, tx, ty, qx, qy)))
-        if np.any(touch):
-            return False
-    return True
+    def within(ux, uy, vx, vy, wx, wy):
+        return ((np.minimum(ux, vx) <= wx) & (wx <= np.maximum(ux, vx)) &
+                (np.minimum(uy, vy) <= wy) & (wy <= np.maximum(uy, vy)))
+    touch = (((o1 == 0) & within(px, py, qx, qy, sx, sy)) |
+             ((o2 == 0) & within(px, py, qx, qy, tx, ty)) |
+             ((o3 == 0) & within(sx, sy, tx, ty, px, py)) |
+             ((o4 == 0) & within(sx, sy, tx, ty, qx, qy)))
+    return not np.any(touch)
 
 
 def _signed_area2(rx, ry):
     rx = np.asarray(rx, np.int64)
     ry = np.asarray(ry, np.int64)
-    return int(np.sum(rx * np.roll(ry, -1) - np.roll(rx, -1) * ry))
+    return int(np.sum(rx * _shift(ry, 1) - _shift(rx, 1) * ry))
 
 
 # --------------------------------------------------------------------------
@@ -394,20 +398,41 @@ def tiny_stars(n_points: int = 100_000) -> Workload:
 _TILING_CACHE: dict = {}
 
 
+def _cached_tiling(key: str, make) -> Polygons:
+    """Memory and disk cache of a generated tiling (generation is deterministic;
+    the directory comes from SDB_WORKLOAD_CACHE, default a temp folder)."""
+    if key in _TILING_CACHE:
+        return _TILING_CACHE[key]
+    import tempfile
+    d = os.environ.get("SDB_WORKLOAD_CACHE", os.path.join(tempfile.gettempdir(), "sdb_workloads"))
+    path = os.path.join(d, key + ".npz")
+    T = None
+    try:
+        with np.load(path) as z:
+            T = Polygons(z["ring_off"], z["x"], z["y"], int(z["grid_bits"]))
+    except Exception:
+        T = make()
+        try:
+            os.makedirs(d, exist_ok=True)
+            tmp = path + f".{os.getpid()}.npz"
+            np.savez(tmp, ring_off=T.ring_off, x=T.x, y=T.y, grid_bits=T.grid_bits)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    _TILING_CACHE[key] = T
+    return T
+
+
 def zones263_tiling() -> Polygons:
     """263-cell jittered Voronoi tiling of [0,2^24)^2, 20-400 vertices."""
-    if "z263" not in _TILING_CACHE:
-        rng = np.random.default_rng(BASE_SEED + 1)
-        _TILING_CACHE["z263"] = voronoi_tiling(rng, 263, 24, (20, 400))
-    return _TILING_CACHE["z263"]
+    return _cached_tiling("zones263_g24_v1", lambda: voronoi_tiling(
+        np.random.default_rng(BASE_SEED + 1), 263, 24, (20, 400)))
 
 
 def tracts40k_tiling() -> Polygons:
     """40,000-cell jittered Voronoi tiling of [0,2^28)^2, 6-60 vertices."""
-    if "t40k" not in _TILING_CACHE:
-        rng = np.random.default_rng(BASE_SEED + 2)
-        _TILING_CACHE["t40k"] = voronoi_tiling(rng, 40_000, 28, (6, 60))
-    return _TILING_CACHE["t40k"]
+    return _cached_tiling("tracts40k_g28_v1", lambda: voronoi_tiling(
+        np.random.default_rng(BASE_SEED + 2), 40_000, 28, (6, 60)))
 
 
 def mobility_zones(n_points: int = 100_000_000) -> Workload:
@@ -418,3 +443,73 @@ def mobility_zones(n_points: int = 100_000_000) -> Workload:
     pts = mobility_points(BASE_SEED + 101, n_points, 24, 32)
     return Workload(f"zones263_mobility{n_points}_g24", 24, [2 ** 12, 2 ** 10, 2 ** 8, 2 ** 6],
                     polys, pts)
+
+
+# --------------------------------------------------------------------------
+# level-of-detail query batches
+# --------------------------------------------------------------------------
+
+@dataclass
+class QueryBatch:
+    """Viewport queries: rows (x0, y0, x1, y1, eps, poly_off, poly_cnt) and the
+    concatenated polygon subsets."""
+    queries: np.ndarray     # int64 [Q, 7]
+    subset_ids: np.ndarray  # uint32
+
+
+def polygon_bboxes(P: Polygons) -> np.ndarray:
+    """[P, 4] (minx, miny, maxx, maxy) per polygon."""
+    off = P.ring_off.astype(np.int64)
+    seg = np.repeat(np.arange(P.n), np.diff(off))
+    out = np.empty((P.n, 4), np.int64)
+    for c, (arr, fn) in enumerate(((P.x, np.minimum), (P.y, np.minimum), (P.x, np.maximum),
+                                   (P.y, np.maximum))):
+        init = np.iinfo(np.int64).max if fn is np.minimum else -1
+        acc = np.full(P.n, init, np.int64)
+        fn.at(acc, seg, arr.astype(np.int64))
+        out[:, c] = acc
+    return out
+
+
+def lod_queries(seed: int, n: int, polys: Polygons, side=(2 ** 14, 2 ** 24),
+                subset=(1, 5000), eps_levels=tuple(2 ** e for e in range(14, 5, -1))) -> QueryBatch:
+    """Level-of-detail queries: viewport side log-uniform in ``side`` (square,
+    uniform position inside the grid), eps uniform over ``eps_levels``, and a
+    polygon subset of size uniform in ``subset``: a random choice among the
+    polygons whose bounding box meets the viewport, filled up with random other
+    polygons when fewer meet it (a view's layer of regions plus unrelated
+    ones)."""
+    rng = np.random.default_rng(seed)
+    G = 2 ** polys.grid_bits
+    bb = polygon_bboxes(polys)
+    rows, ids = [], []
+    for _ in range(n):
+        s = int(np.exp(rng.uniform(np.log(side[0]), np.log(side[1]))))
+        s = max(1, min(s, G))
+        x0 = int(rng.integers(0, G - s + 1))
+        y0 = int(rng.integers(0, G - s + 1))
+        eps = int(eps_levels[rng.integers(0, len(eps_levels))])
+        k = int(rng.integers(subset[0], subset[1] + 1))
+        k = min(k, polys.n)
+        meet = np.nonzero((bb[:, 0] < x0 + s) & (bb[:, 2] >= x0) &
+                          (bb[:, 1] < y0 + s) & (bb[:, 3] >= y0))[0]
+        if len(meet) >= k:
+            sub = rng.choice(meet, size=k, replace=False)
+        else:
+            rest = np.setdiff1d(np.arange(polys.n), meet)
+            sub = np.concatenate([meet, rng.choice(rest, size=k - len(meet), replace=False)])
+            rng.shuffle(sub)
+        rows.append((x0, y0, x0 + s, y0 + s, eps, sum(len(i) for i in ids), k))
+        ids.append(sub.astype(np.uint32))
+    return QueryBatch(np.asarray(rows, np.int64),
+                      np.concatenate(ids) if ids else np.zeros(0, np.uint32))
+
+
+def lod_workload(n_points: int = 200_000_000, n_queries: int = 4096) -> tuple:
+    """4,096 level-of-detail queries over 200M resident points on [0,2^28)^2
+    (70% from 64 Gaussian clusters with sigma in [2^20, 2^23], 30% uniform) and
+    the 40,000-polygon tiling; eps from {2^14 .. 2^6}."""
+    T = tracts40k_tiling()
+    pts = mobility_points(BASE_SEED + 104, n_points, 28, 64, sigma=(2 ** 20, 2 ** 23))
+    qb = lod_queries(BASE_SEED + 4, n_queries, T)
+    return T, pts, qb
