@@ -35,13 +35,21 @@ constexpr uint32_t NONE = 0xffffffffu;
 constexpr int THREADS = 256;
 constexpr int MAXC = 81;  // candidate index ranges per query (9 x 9 cells)
 
+// covering arrays of one chunk of queries
+struct ChunkDev {
+  const uint64_t* start;
+  const uint32_t* pay;
+  const uint32_t* list_off;
+  const uint32_t* list_ids;
+};
+
 struct QueryDev {
-  uint64_t sbase;  // first entry of the query's covering slice
+  uint64_t sbase;  // first entry of the query's covering slice in its chunk
   uint32_t R;      // ranges in the slice (the sentinel follows)
+  uint32_t chunk;
   uint32_t k, nsteps, st0;
   uint32_t x0, y0, x1, y1;
   uint32_t out_off;
-  uint32_t pad;
 };
 
 struct TileRec {
@@ -213,10 +221,7 @@ struct BatchArgs {
   const int32_t* attr;
   const QueryDev* q;
   const TileRec* tiles;
-  const uint64_t* start;
-  const uint32_t* pay;
-  const uint32_t* list_off;
-  const uint32_t* list_ids;
+  const ChunkDev* chunks;
   unsigned long long* count;
   unsigned long long* sum;
 };
@@ -243,6 +248,7 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
     if (t >= tile_hi) break;
     const TileRec tr = A.tiles[t];
     const QueryDev Q = A.q[tr.q];
+    const ChunkDev C = A.chunks[Q.chunk];
     for (uint32_t i0 = tr.begin + threadIdx.x * G; i0 < tr.end; i0 += THREADS * G) {
       uint64_t h[G];
       bool ok[G];
@@ -264,7 +270,7 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
         const uint32_t half = len >> 1;
         uint64_t v[G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) v[g] = __ldg(A.start + Q.sbase + lo[g] + half);
+        for (int g = 0; g < G; ++g) v[g] = __ldg(C.start + Q.sbase + lo[g] + half);
 #pragma unroll
         for (int g = 0; g < G; ++g)
           if (v[g] <= h[g]) lo[g] += half;
@@ -274,13 +280,13 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
       for (int g = 0; g < G; ++g) {
         if (!ok[g]) continue;
         const uint64_t e = Q.sbase + lo[g];
-        const uint32_t p = __ldg(A.pay + e);
+        const uint32_t p = __ldg(C.pay + e);
         if (p < 0x80000000u) {
           add_slot(A, Q.out_off, p, av[g], SUM);
         } else if (p != NONE) {
           const uint32_t rr = p & 0x7fffffffu;
-          const uint32_t b = __ldg(A.list_off + rr), en = __ldg(A.list_off + rr + 1);
-          for (uint32_t j = b; j < en; ++j) add_slot(A, Q.out_off, __ldg(A.list_ids + j), av[g], SUM);
+          const uint32_t b = __ldg(C.list_off + rr), en = __ldg(C.list_off + rr + 1);
+          for (uint32_t j = b; j < en; ++j) add_slot(A, Q.out_off, __ldg(C.list_ids + j), av[g], SUM);
         }
       }
     }
@@ -304,7 +310,9 @@ struct sdb_batch {
   int device = 0;
   const sdb_points* pts = nullptr;
   uint32_t Q = 0, NP = 0;
-  sdb::CoverSet cs;
+  std::vector<sdb::CoverSet> cs;  // one per chunk of queries
+  sdb::ChunkDev* dchunks = nullptr;
+  uint64_t n_ranges = 0, n_cells = 0;
   sdb::QueryDev* dq = nullptr;
   std::vector<sdb::QueryDev> hq;
   uint64_t out_len = 0, max_ranges = 0, candidates = 0;
@@ -391,10 +399,7 @@ BatchArgs batch_args(const sdb_batch* b, uint64_t* count, int64_t* sum) {
   A.attr = b->pts->attr;
   A.q = b->dq;
   A.tiles = b->tiles;
-  A.start = b->cs.start;
-  A.pay = b->cs.pay;
-  A.list_off = b->cs.list_off;
-  A.list_ids = b->cs.list_ids;
+  A.chunks = b->dchunks;
   A.count = reinterpret_cast<unsigned long long*>(count);
   A.sum = reinterpret_cast<unsigned long long*>(sum);
   return A;
@@ -614,24 +619,67 @@ sdb_status sdb_batch_create(const sdb_points* pts, const sdb_polygons* polys,
   b->Q = n_queries;
   b->NP = (uint32_t)pp.size();
   b->out_len = out_off;
-  CoverSpec spec;
-  spec.B = B;
-  spec.Q = n_queries;
-  spec.q = cq.data();
-  spec.NP = b->NP;
-  spec.pair_poly = pp.data();
-  spec.pair_query = pq.data();
-  spec.pair_slot = ps.data();
-  sdb_status st = build_coverings(polys, spec, s, &b->cs);
-  if (st == SDB_OK) {
-    for (uint32_t q = 0; q < n_queries; ++q) {
-      hq[q].sbase = b->cs.qoff[q];
-      hq[q].R = (uint32_t)(b->cs.qoff[q + 1] - b->cs.qoff[q] - 1);
-      b->max_ranges = std::max<uint64_t>(b->max_ranges, hq[q].R);
-    }
-    b->hq = hq;
-    st = dalloc_n(&b->dq, n_queries, s);
+  // coverings in chunks of queries; a chunk that overflows the builder's
+  // 32-bit ranges (or memory) is halved and retried
+  std::vector<uint64_t> pfirst(n_queries + 1, 0);  // pairs are in query order
+  for (uint32_t i = 0, q = 0; q <= n_queries; ++q) {
+    while (i < pq.size() && pq[i] < q) ++i;
+    pfirst[q] = i;
   }
+  sdb_status st = SDB_OK;
+  uint32_t chunk_q = 512;
+  std::vector<uint32_t> pq_local;
+  for (uint32_t q0 = 0; q0 < n_queries && st == SDB_OK;) {
+    const uint32_t nq = std::min(chunk_q, n_queries - q0);
+    const uint64_t pa = pfirst[q0], pb = pfirst[q0 + nq];
+    pq_local.assign(pq.begin() + pa, pq.begin() + pb);
+    for (auto& v : pq_local) v -= q0;
+    CoverSpec spec;
+    spec.B = B;
+    spec.Q = nq;
+    spec.q = cq.data() + q0;
+    spec.NP = (uint32_t)(pb - pa);
+    spec.pair_poly = pp.data() + pa;
+    spec.pair_query = pq_local.data();
+    spec.pair_slot = ps.data() + pa;
+    CoverSet set;
+    st = build_coverings(polys, spec, s, &set);
+    if (st == SDB_ENOMEM && nq > 1) {
+      set.release(s);
+      cudaStreamSynchronize(s);
+      cudaGetLastError();
+      chunk_q = nq / 2;
+      st = SDB_OK;
+      continue;
+    }
+    if (st != SDB_OK) {
+      set.release(s);
+      break;
+    }
+    for (uint32_t q = 0; q < nq; ++q) {
+      QueryDev& d = hq[q0 + q];
+      d.sbase = set.qoff[q];
+      d.R = (uint32_t)(set.qoff[q + 1] - set.qoff[q] - 1);
+      d.chunk = (uint32_t)b->cs.size();
+      b->max_ranges = std::max<uint64_t>(b->max_ranges, d.R);
+    }
+    b->n_ranges += set.E - nq;
+    b->n_cells += set.ncells;
+    b->cs.push_back(set);
+    q0 += nq;
+  }
+  if (st == SDB_OK) {
+    b->hq = hq;
+    std::vector<ChunkDev> hc;
+    for (auto& c : b->cs) hc.push_back(ChunkDev{c.start, c.pay, c.list_off, c.list_ids});
+    st = dalloc_n(&b->dchunks, hc.size(), s);
+    if (st == SDB_OK)
+      st = cudaMemcpyAsync(b->dchunks, hc.data(), hc.size() * sizeof(ChunkDev),
+                           cudaMemcpyHostToDevice, s) == cudaSuccess
+               ? SDB_OK
+               : cuda_status(cudaErrorUnknown, "chunk copy", __FILE__, __LINE__);
+  }
+  if (st == SDB_OK) st = dalloc_n(&b->dq, n_queries, s);
   if (st == SDB_OK)
     st = cudaMemcpyAsync(b->dq, hq.data(), n_queries * sizeof(QueryDev), cudaMemcpyHostToDevice,
                          s) == cudaSuccess
@@ -675,9 +723,9 @@ sdb_status sdb_batch_get_info(const sdb_batch* b, sdb_batch_info* info) {
   info->n_queries = b->Q;
   info->n_pairs = b->NP;
   info->out_len = b->out_len;
-  info->n_ranges = b->cs.E - b->Q;
+  info->n_ranges = b->n_ranges;
   info->max_ranges = b->max_ranges;
-  info->n_cells = b->cs.ncells;
+  info->n_cells = b->n_cells;
   info->candidates = b->candidates;
   info->n_tiles = b->ntiles;
   info->tile = b->tile;
@@ -826,8 +874,8 @@ void sdb_batch_free(sdb_batch* b) {
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  b->cs.release(0);
-  void* ps[] = {b->dq, b->cand, b->ncand, b->tiles, b->heads};
+  for (auto& c : b->cs) c.release(0);
+  void* ps[] = {b->dq, b->cand, b->ncand, b->tiles, b->heads, b->dchunks};
   for (void* q : ps)
     if (q) cudaFreeAsync(q, 0);
   cudaStreamSynchronize(0);

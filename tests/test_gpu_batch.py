@@ -113,7 +113,9 @@ def test_query_alone_equals_in_mix(cuda, sdblib, small):
         assert np.array_equal(s1, sm[offs[q]:offs[q + 1]])
 
 
-def test_overlapping_polygons_rejected(cuda, sdblib):
+def test_overlapping_polygons(cuda, sdblib, orc):
+    """One query over nested polygons takes the general merge and is exact;
+    several queries require polygons that do not overlap within a query."""
     torch = cuda
     rng = np.random.default_rng(3)
     # a square inside another square
@@ -122,8 +124,13 @@ def test_overlapping_polygons_rejected(cuda, sdblib):
                    np.array([100, 100, 5000, 5000, 2000, 2000, 3000, 3000], np.uint32), 14)
     pts = W.uniform_points(rng, 10_000, 14)
     p = sdblib.points_create(dev(torch, pts.x), dev(torch, pts.y), dev(torch, pts.attr), 14)
+    row = (50, 60, 9000, 8000, 16, 0, 2)
+    b = sdblib.batch_create(p, S, [row], np.arange(2))
+    cnt, sm = run_batch(torch, sdblib, b, sdblib.BATCH_PERSISTENT)
+    c, s_ = oracle_slice(orc, S, pts, row, np.arange(2))
+    assert np.array_equal(cnt, c) and np.array_equal(sm, s_)
     with pytest.raises(sdblib.SdbError) as e:
-        sdblib.batch_create(p, S, [(0, 0, 2 ** 14, 2 ** 14, 16, 0, 2)], np.arange(2))
+        sdblib.batch_create(p, S, [row, row], np.arange(2))
     assert e.value.status == sdblib.SDB_EINVAL
 
 
