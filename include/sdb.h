@@ -257,6 +257,66 @@ sdb_status sdb_batch_set_tuning(sdb_batch *b, uint32_t tile, uint32_t points_per
                                 void *cuda_stream);
 void sdb_batch_free(sdb_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Serving (Sec. 1: interactive exploration needs fast answers while users zoom):
+ * points stay resident; queries arrive at any time and are answered by
+ * continuous batching.  A pool of workers, each with its own CUDA stream, takes
+ * every pending query (up to max_batch) as one batch whenever a worker is free,
+ * so queries arriving while other batches run join the next free slot and the
+ * batches overlap on the device.  Per query a viewport-clipped covering comes
+ * from a device-memory cache (LRU under cache_bytes; coverings of running
+ * batches are pinned) or is built with the batch's other missing queries in one
+ * pass; a worker takes new work only while the coverings of running batches fit
+ * cache_bytes.  Each batch's join is one persistent launch, or one launch per
+ * query in the plain form (per_query = 1).  Results are the same as the batch
+ * API's for the same query, alone or in any mix.
+ * ------------------------------------------------------------------------- */
+typedef struct sdb_server sdb_server;
+
+typedef struct sdb_server_config {
+  uint32_t workers;           /* batches in flight, one stream each, 1..64 */
+  uint32_t max_batch;         /* queries per batch, >= 1 */
+  uint64_t cache_bytes;       /* device-memory budget for coverings */
+  uint32_t use_cache;         /* 0: every query's covering is built afresh */
+  uint32_t per_query;         /* 1: one launch per query instead of one per batch */
+  uint32_t tile;              /* points per work item, 0 = default */
+  uint32_t points_per_thread; /* 1, 2, 4, or 0 = default */
+} sdb_server_config;
+
+typedef struct sdb_ticket_info {
+  double latency_ms;  /* submit until the result is in host memory */
+  double queue_ms;    /* submit until a worker took the query */
+  uint32_t batch_size;
+  uint32_t cache_hit; /* the covering came from the cache */
+  uint64_t ranges;    /* covering ranges of the query */
+} sdb_ticket_info;
+
+typedef struct sdb_server_stats {
+  uint64_t submitted, completed, batches;
+  uint64_t cache_hits, cache_misses, evictions;
+  uint64_t cache_bytes, cache_entries, peak_bytes;
+} sdb_server_stats;
+
+/* Start the workers.  pts must outlive the server; polygons are copied.
+ * SDB_EINVAL: bad config or polygons, points on another device. */
+sdb_status sdb_server_create(const sdb_points *pts, const sdb_polygons *polys,
+                             const sdb_server_config *cfg, sdb_server **out);
+/* Queue one query (q->poly_off is ignored: subset_ids holds its q->poly_cnt
+ * polygon ids; both are copied).  Returns at once with a ticket.
+ * SDB_EINVAL: bad viewport, eps or polygon id; SDB_EBUSY: shutting down. */
+sdb_status sdb_server_submit(sdb_server *srv, const sdb_query *q, const uint32_t *subset_ids,
+                             uint64_t *ticket);
+/* Wait up to timeout_ms for a ticket; on success copy its poly_cnt counts and
+ * sums to host arrays (either may be NULL) and the timing to info (nullable),
+ * and retire the ticket.  SDB_ETIMEOUT: not done yet (the ticket stays valid);
+ * SDB_EINVAL: unknown or retired ticket; otherwise the batch's own status. */
+sdb_status sdb_server_wait(sdb_server *srv, uint64_t ticket, uint32_t timeout_ms,
+                           uint64_t *h_count, int64_t *h_sum, sdb_ticket_info *info);
+sdb_status sdb_server_get_stats(sdb_server *srv, sdb_server_stats *stats);
+/* Finish every queued query, stop the workers, free the cache.  Tickets not
+ * yet waited for are discarded. */
+void sdb_server_destroy(sdb_server *srv);
+
 /* Number of learned-index lookups of the covering's most recent learned join
  * whose bounded search missed and fell back to binary search.  Synchronises
  * cuda_stream. */

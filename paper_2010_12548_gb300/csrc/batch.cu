@@ -35,26 +35,9 @@ constexpr uint32_t NONE = 0xffffffffu;
 constexpr int THREADS = 256;
 constexpr int MAXC = 81;  // candidate index ranges per query (9 x 9 cells)
 
-// covering arrays of one chunk of queries
-struct ChunkDev {
-  const uint64_t* start;
-  const uint32_t* pay;
-  const uint32_t* list_off;
-  const uint32_t* list_ids;
-};
-
-struct QueryDev {
-  uint64_t sbase;  // first entry of the query's covering slice in its chunk
-  uint32_t R;      // ranges in the slice (the sentinel follows)
-  uint32_t chunk;
-  uint32_t k, nsteps, st0;
-  uint32_t x0, y0, x1, y1;
-  uint32_t out_off;
-};
-
-struct TileRec {
-  uint32_t q, begin, end, pad;
-};
+using QueryDev = BatchQueryDev;
+using ChunkDev = BatchChunkDev;
+using TileRec = BatchTile;
 
 __device__ __forceinline__ uint16_t lut_entry(uint32_t idx) {
   uint32_t sw = (idx >> 9) & 1u, cm = (idx >> 8) & 1u;
@@ -296,33 +279,12 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
 }  // namespace
 }  // namespace sdb
 
-struct sdb_points {
-  int device = 0;
-  uint32_t B = 0;
-  uint64_t n = 0;
-  uint64_t* key = nullptr;
-  uint32_t* x = nullptr;
-  uint32_t* y = nullptr;
-  int32_t* attr = nullptr;
-};
-
 struct sdb_batch {
   int device = 0;
-  const sdb_points* pts = nullptr;
-  uint32_t Q = 0, NP = 0;
+  uint32_t NP = 0;
+  sdb::BatchCore core;
   std::vector<sdb::CoverSet> cs;  // one per chunk of queries
-  sdb::ChunkDev* dchunks = nullptr;
-  uint64_t n_ranges = 0, n_cells = 0;
-  sdb::QueryDev* dq = nullptr;
-  std::vector<sdb::QueryDev> hq;
-  uint64_t out_len = 0, max_ranges = 0, candidates = 0;
-  uint32_t* cand = nullptr;
-  uint32_t* ncand = nullptr;
-  uint32_t tile = 4096, ppt = 2;
-  sdb::TileRec* tiles = nullptr;
-  uint64_t ntiles = 0;
-  std::vector<uint64_t> qtile;  // host, Q + 1
-  unsigned long long* heads = nullptr;  // Q + 1 work counters
+  uint64_t n_ranges = 0, n_cells = 0, max_ranges = 0;
   cudaGraphExec_t graph = nullptr;
   void* g_count = nullptr;
   void* g_sum = nullptr;
@@ -330,42 +292,6 @@ struct sdb_batch {
 
 namespace sdb {
 namespace {
-
-sdb_status build_tiles(sdb_batch* b, uint32_t T, cudaStream_t s) {
-  Scratch sc(s);
-  uint64_t *nt, *toff, *dtot;
-  SDB_TRY(sc.get(&nt, b->Q));
-  SDB_TRY(sc.get(&toff, (size_t)b->Q + 1));
-  SDB_TRY(sc.get(&dtot, 1));
-  tile_count_kernel<<<grid_for(b->Q, 128), 128, 0, s>>>(b->cand, b->ncand, b->Q, T, nt);
-  note_launch();
-  SDB_TRY_CUDA(cudaGetLastError());
-  SDB_TRY(exclusive_scan<uint64_t>(nt, toff, b->Q, dtot, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(toff + b->Q, dtot, 8, cudaMemcpyDeviceToDevice, s));
-  b->qtile.assign((size_t)b->Q + 1, 0);
-  SDB_TRY_CUDA(cudaMemcpyAsync(b->qtile.data(), toff, ((size_t)b->Q + 1) * 8,
-                               cudaMemcpyDeviceToHost, s));
-  SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  const uint64_t total = b->qtile[b->Q];
-  if (total >= 0xffffffffull) {
-    set_error("batch: %llu tiles exceed the 32-bit range", (unsigned long long)total);
-    return SDB_EINVAL;
-  }
-  if (b->tiles) dfree(b->tiles, s);
-  b->tiles = nullptr;
-  SDB_TRY(dalloc_n(&b->tiles, total, s));
-  tile_fill_kernel<<<grid_for(b->Q, 128), 128, 0, s>>>(b->cand, b->ncand, b->Q, T, toff, b->tiles);
-  note_launch();
-  SDB_TRY_CUDA(cudaGetLastError());
-  SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  b->ntiles = total;
-  b->tile = T;
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
-  return SDB_OK;
-}
 
 template <int G, bool SUM>
 sdb_status launch_batch_t(const BatchArgs& A, uint32_t lo, uint32_t hi,
@@ -392,34 +318,249 @@ sdb_status launch_batch(const BatchArgs& A, uint32_t ppt, bool sum, uint32_t lo,
              : launch_batch_t<4, false>(A, lo, hi, head, s);
 }
 
-BatchArgs batch_args(const sdb_batch* b, uint64_t* count, int64_t* sum) {
-  BatchArgs A;
-  A.x = b->pts->x;
-  A.y = b->pts->y;
-  A.attr = b->pts->attr;
-  A.q = b->dq;
-  A.tiles = b->tiles;
-  A.chunks = b->dchunks;
-  A.count = reinterpret_cast<unsigned long long*>(count);
-  A.sum = reinterpret_cast<unsigned long long*>(sum);
-  return A;
-}
-
-// the persistent form: clear outputs and the work counter, one launch
-sdb_status run_persistent(sdb_batch* b, uint64_t* count, int64_t* sum, cudaStream_t s) {
-  SDB_TRY_CUDA(cudaMemsetAsync(count, 0, b->out_len * 8, s));
-  if (sum) SDB_TRY_CUDA(cudaMemsetAsync(sum, 0, b->out_len * 8, s));
-  SDB_TRY_CUDA(cudaMemsetAsync(b->heads + b->Q, 0, sizeof(unsigned long long), s));
-  return launch_batch(batch_args(b, count, sum), b->ppt, sum != nullptr, 0, (uint32_t)b->ntiles,
-                      b->heads + b->Q, s);
-}
-
 bool valid_device(int dev) {
   int cur = -1;
   return cudaGetDevice(&cur) == cudaSuccess && cur == dev;
 }
 
+sdb_status status_of(cudaError_t e, const char* what) {
+  return e == cudaSuccess ? SDB_OK : cuda_status(e, what, __FILE__, __LINE__);
+}
+
 }  // namespace
+
+void BatchCore::release(cudaStream_t s) {
+  dfree(dq, s);
+  dfree(dchunks, s);
+  dfree(cand, s);
+  dfree(ncand, s);
+  dfree(tiles, s);
+  dfree(heads, s);
+  dq = nullptr;
+  dchunks = nullptr;
+  cand = nullptr;
+  ncand = nullptr;
+  tiles = nullptr;
+  heads = nullptr;
+}
+
+sdb_status batch_query_dev(uint32_t B, const sdb_query& Qu, uint64_t out_off, BatchQueryDev* d,
+                           uint32_t* F_out) {
+  uint32_t k = 0, F = 0;
+  SDB_TRY(sdb_finest_level(B, Qu.eps, &k, &F));
+  const uint32_t G = 1u << B;
+  if (!(Qu.x0 < Qu.x1 && Qu.y0 < Qu.y1 && Qu.x1 <= G && Qu.y1 <= G)) {
+    set_error("viewport must be non-empty and inside the grid");
+    return SDB_EINVAL;
+  }
+  memset(d, 0, sizeof(*d));
+  d->k = k;
+  d->nsteps = (F + 3) / 4;
+  d->st0 = ((4 * d->nsteps - F) & 1u) ? 2u : 0u;
+  d->x0 = Qu.x0;
+  d->y0 = Qu.y0;
+  d->x1 = Qu.x1;
+  d->y1 = Qu.y1;
+  d->out_off = (uint32_t)out_off;
+  *F_out = F;
+  return SDB_OK;
+}
+
+sdb_status batch_core_tiles(BatchCore* c, uint32_t T, cudaStream_t s) {
+  Scratch sc(s);
+  uint64_t *nt, *toff, *dtot;
+  SDB_TRY(sc.get(&nt, c->Q));
+  SDB_TRY(sc.get(&toff, (size_t)c->Q + 1));
+  SDB_TRY(sc.get(&dtot, 1));
+  tile_count_kernel<<<grid_for(c->Q, 128), 128, 0, s>>>(c->cand, c->ncand, c->Q, T, nt);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(exclusive_scan<uint64_t>(nt, toff, c->Q, dtot, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(toff + c->Q, dtot, 8, cudaMemcpyDeviceToDevice, s));
+  c->qtile.assign((size_t)c->Q + 1, 0);
+  SDB_TRY_CUDA(cudaMemcpyAsync(c->qtile.data(), toff, ((size_t)c->Q + 1) * 8,
+                               cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  const uint64_t total = c->qtile[c->Q];
+  if (total >= 0xffffffffull) {
+    set_error("batch: %llu tiles exceed the 32-bit range", (unsigned long long)total);
+    return SDB_EINVAL;
+  }
+  if (c->tiles) dfree(c->tiles, s);
+  c->tiles = nullptr;
+  SDB_TRY(dalloc_n(&c->tiles, total, s));
+  tile_fill_kernel<<<grid_for(c->Q, 128), 128, 0, s>>>(c->cand, c->ncand, c->Q, T, toff, c->tiles);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  c->ntiles = total;
+  c->tile = T;
+  return SDB_OK;
+}
+
+sdb_status batch_core_prepare(BatchCore* c, cudaStream_t s) {
+  const uint32_t Q = c->Q;
+  SDB_TRY(dalloc_n(&c->dq, Q, s));
+  SDB_TRY(dalloc_n(&c->dchunks, c->hchunks.size(), s));
+  SDB_TRY(dalloc_n(&c->cand, (size_t)Q * MAXC * 2, s));
+  SDB_TRY(dalloc_n(&c->ncand, Q, s));
+  SDB_TRY(dalloc_n(&c->heads, (size_t)Q + 1, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(c->dq, c->hq.data(), Q * sizeof(BatchQueryDev),
+                               cudaMemcpyHostToDevice, s));
+  if (!c->hchunks.empty())
+    SDB_TRY_CUDA(cudaMemcpyAsync(c->dchunks, c->hchunks.data(),
+                                 c->hchunks.size() * sizeof(BatchChunkDev), cudaMemcpyHostToDevice,
+                                 s));
+  candidates_kernel<<<grid_for(Q, 64), 64, 0, s>>>(c->dq, Q, c->pts->key, c->pts->n, c->pts->B,
+                                                   c->cand, c->ncand);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  SDB_TRY(batch_core_tiles(c, c->tile, s));
+  // candidate points (for reporting)
+  std::vector<uint32_t> hc((size_t)Q * MAXC * 2), hn(Q);
+  SDB_TRY_CUDA(cudaMemcpyAsync(hc.data(), c->cand, hc.size() * 4, cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(hn.data(), c->ncand, hn.size() * 4, cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  c->candidates = 0;
+  for (uint32_t q = 0; q < Q; ++q)
+    for (uint32_t i = 0; i < hn[q]; ++i)
+      c->candidates += hc[(size_t)q * MAXC * 2 + 2 * i + 1] - hc[(size_t)q * MAXC * 2 + 2 * i];
+  return SDB_OK;
+}
+
+sdb_status batch_core_run(BatchCore* c, int mode, uint64_t* count, int64_t* sum, cudaStream_t s) {
+  BatchArgs A;
+  A.x = c->pts->x;
+  A.y = c->pts->y;
+  A.attr = c->pts->attr;
+  A.q = c->dq;
+  A.tiles = c->tiles;
+  A.chunks = c->dchunks;
+  A.count = reinterpret_cast<unsigned long long*>(count);
+  A.sum = reinterpret_cast<unsigned long long*>(sum);
+  if (c->out_len) {
+    SDB_TRY_CUDA(cudaMemsetAsync(count, 0, c->out_len * 8, s));
+    if (sum) SDB_TRY_CUDA(cudaMemsetAsync(sum, 0, c->out_len * 8, s));
+  }
+  if (mode == SDB_BATCH_PER_QUERY) {
+    SDB_TRY_CUDA(cudaMemsetAsync(c->heads, 0, (size_t)c->Q * sizeof(unsigned long long), s));
+    for (uint32_t q = 0; q < c->Q; ++q)
+      if (c->qtile[q + 1] > c->qtile[q])
+        SDB_TRY(launch_batch(A, c->ppt, sum != nullptr, (uint32_t)c->qtile[q],
+                             (uint32_t)c->qtile[q + 1], c->heads + q, s));
+    return SDB_OK;
+  }
+  SDB_TRY_CUDA(cudaMemsetAsync(c->heads + c->Q, 0, sizeof(unsigned long long), s));
+  return launch_batch(A, c->ppt, sum != nullptr, 0, (uint32_t)c->ntiles, c->heads + c->Q, s);
+}
+
+// Coverings of queries [q0, q0 + nq) of a pair list, built in chunks that are
+// halved and retried when they overflow the builder's 32-bit ranges or memory.
+// Appends CoverSets to *sets and fills sbase/R/chunk of hq.
+sdb_status build_query_coverings(const sdb_polygons* polys, uint32_t B,
+                                 const std::vector<CoverQuery>& cq,
+                                 const std::vector<uint32_t>& pp, const std::vector<uint32_t>& pq,
+                                 const std::vector<uint32_t>& ps, std::vector<BatchQueryDev>& hq,
+                                 std::vector<CoverSet>* sets, uint32_t chunk_base,
+                                 cudaStream_t s, uint64_t* n_ranges, uint64_t* n_cells,
+                                 uint64_t* max_ranges) {
+  const uint32_t Q = (uint32_t)cq.size();
+  std::vector<uint64_t> pfirst((size_t)Q + 1, 0);  // pairs are in query order
+  for (uint64_t i = 0, q = 0; q <= Q; ++q) {
+    while (i < pq.size() && pq[i] < q) ++i;
+    pfirst[q] = i;
+  }
+  uint32_t chunk_q = 512;
+  std::vector<uint32_t> pq_local;
+  for (uint32_t q0 = 0; q0 < Q;) {
+    const uint32_t nq = std::min(chunk_q, Q - q0);
+    const uint64_t pa = pfirst[q0], pb = pfirst[q0 + nq];
+    pq_local.assign(pq.begin() + pa, pq.begin() + pb);
+    for (auto& v : pq_local) v -= q0;
+    CoverSpec spec;
+    spec.B = B;
+    spec.Q = nq;
+    spec.q = cq.data() + q0;
+    spec.NP = (uint32_t)(pb - pa);
+    spec.pair_poly = pp.data() + pa;
+    spec.pair_query = pq_local.data();
+    spec.pair_slot = ps.data() + pa;
+    CoverSet set;
+    sdb_status st = build_coverings(polys, spec, s, &set);
+    if (st == SDB_ENOMEM && nq > 1) {
+      set.release(s);
+      cudaStreamSynchronize(s);
+      cudaGetLastError();
+      chunk_q = nq / 2;
+      continue;
+    }
+    if (st != SDB_OK) {
+      set.release(s);
+      return st;
+    }
+    for (uint32_t q = 0; q < nq; ++q) {
+      BatchQueryDev& d = hq[q0 + q];
+      d.sbase = set.qoff[q];
+      d.R = (uint32_t)(set.qoff[q + 1] - set.qoff[q] - 1);
+      d.chunk = chunk_base + (uint32_t)sets->size();
+      *max_ranges = std::max<uint64_t>(*max_ranges, d.R);
+    }
+    *n_ranges += set.E - nq;
+    *n_cells += set.ncells;
+    sets->push_back(set);
+    q0 += nq;
+  }
+  return SDB_OK;
+}
+
+// (query, polygon) pairs whose polygon's cells can hold viewport points: the
+// polygon's bounding box grown by one finest cell meets the viewport
+void viewport_pairs(const std::vector<uint32_t>& bb, uint32_t q, const sdb_query& Qu, uint32_t k,
+                    const uint32_t* ids, std::vector<uint32_t>& pp, std::vector<uint32_t>& pq,
+                    std::vector<uint32_t>& ps) {
+  const int64_t g = (int64_t)1 << k;
+  for (uint32_t t = 0; t < Qu.poly_cnt; ++t) {
+    const uint32_t j = ids[t];
+    if ((int64_t)bb[4 * j] - g < (int64_t)Qu.x1 && (int64_t)bb[4 * j + 2] + g >= Qu.x0 &&
+        (int64_t)bb[4 * j + 1] - g < (int64_t)Qu.y1 && (int64_t)bb[4 * j + 3] + g >= Qu.y0) {
+      pp.push_back(j);
+      pq.push_back(q);
+      ps.push_back(t);
+    }
+  }
+}
+
+sdb_status polygon_bboxes(const sdb_polygons* polys, uint32_t B, std::vector<uint32_t>* bb) {
+  const uint32_t P = polys->n_polygons, G = 1u << B;
+  if (P == 0 || P >= (1u << 26) || polys->ring_off[0] != 0) {
+    set_error("bad polygon set");
+    return SDB_EINVAL;
+  }
+  bb->assign(4ull * P, 0);
+  for (uint32_t j = 0; j < P; ++j) {
+    if (polys->ring_off[j + 1] < polys->ring_off[j] + 3) {
+      set_error("polygon %u has fewer than 3 vertices", j);
+      return SDB_EINVAL;
+    }
+    uint32_t mnx = ~0u, mny = ~0u, mxx = 0, mxy = 0;
+    for (uint32_t v = polys->ring_off[j]; v < polys->ring_off[j + 1]; ++v) {
+      if (polys->x[v] >= G || polys->y[v] >= G) {
+        set_error("vertex %u outside the grid", v);
+        return SDB_EINVAL;
+      }
+      mnx = std::min(mnx, polys->x[v]);
+      mxx = std::max(mxx, polys->x[v]);
+      mny = std::min(mny, polys->y[v]);
+      mxy = std::max(mxy, polys->y[v]);
+    }
+    (*bb)[4 * j] = mnx;
+    (*bb)[4 * j + 1] = mny;
+    (*bb)[4 * j + 2] = mxx;
+    (*bb)[4 * j + 3] = mxy;
+  }
+  return SDB_OK;
+}
+
 }  // namespace sdb
 
 using namespace sdb;
@@ -466,28 +607,25 @@ sdb_status sdb_points_create(const uint32_t* d_x, const uint32_t* d_y, const int
     if (st == SDB_OK) st = sc.get(&idx, n);
     if (st == SDB_OK) st = sc.get(&itmp, n);
     if (st == SDB_OK) st = sc.get(&bad, 1);
+    if (st == SDB_OK) st = status_of(cudaMemsetAsync(bad, 0, 4, s), "memset");
     if (st == SDB_OK) {
-      cudaMemsetAsync(bad, 0, 4, s);
       const uint32_t nsteps = (grid_bits + 3) / 4, pad = 4 * nsteps - grid_bits;
       point_keys_kernel<<<num_sms() * 8, 256, 0, s>>>(d_x, d_y, n, grid_bits, nsteps,
                                                       (pad & 1u) ? 2u : 0u, p->key, idx, bad);
       note_launch();
-      if (cudaGetLastError() != cudaSuccess) st = cuda_status(cudaErrorLaunchFailure, "point keys", __FILE__, __LINE__);
+      st = status_of(cudaGetLastError(), "point keys");
     }
     if (st == SDB_OK) st = radix_sort_pairs(p->key, idx, ktmp, itmp, n, 2 * grid_bits, s, &ks, &is);
     if (st == SDB_OK && ks != p->key)
-      st = cudaMemcpyAsync(p->key, ks, n * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess
-               ? SDB_OK
-               : cuda_status(cudaErrorUnknown, "key copy", __FILE__, __LINE__);
+      st = status_of(cudaMemcpyAsync(p->key, ks, n * 8, cudaMemcpyDeviceToDevice, s), "key copy");
     if (st == SDB_OK) {
       gather_points_kernel<<<grid_for(n, 256), 256, 0, s>>>(is, n, d_x, d_y, d_attr, p->x, p->y,
                                                             p->attr);
       note_launch();
       unsigned int hb = 0;
-      cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s);
-      cudaError_t e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) st = cuda_status(e, "points create", __FILE__, __LINE__);
-      else if (hb) {
+      st = status_of(cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s), "flag copy");
+      if (st == SDB_OK) st = status_of(cudaStreamSynchronize(s), "points create");
+      if (st == SDB_OK && hb) {
         set_error("a point lies outside the grid [0, 2^%u)", grid_bits);
         st = SDB_EINVAL;
       }
@@ -530,82 +668,36 @@ sdb_status sdb_batch_create(const sdb_points* pts, const sdb_polygons* polys,
     return SDB_EINVAL;
   }
   const uint32_t B = pts->B, P = polys->n_polygons;
-  if (P == 0 || P >= (1u << 26) || polys->ring_off[0] != 0) {
-    set_error("bad polygon set");
-    return SDB_EINVAL;
-  }
-  const uint32_t G = 1u << B;
-  // polygon bounding boxes (and vertex checks)
-  std::vector<uint32_t> bb(4ull * P);
-  for (uint32_t j = 0; j < P; ++j) {
-    if (polys->ring_off[j + 1] < polys->ring_off[j] + 3) {
-      set_error("polygon %u has fewer than 3 vertices", j);
-      return SDB_EINVAL;
-    }
-    uint32_t mnx = ~0u, mny = ~0u, mxx = 0, mxy = 0;
-    for (uint32_t v = polys->ring_off[j]; v < polys->ring_off[j + 1]; ++v) {
-      if (polys->x[v] >= G || polys->y[v] >= G) {
-        set_error("vertex %u outside the grid", v);
-        return SDB_EINVAL;
-      }
-      mnx = std::min(mnx, polys->x[v]);
-      mxx = std::max(mxx, polys->x[v]);
-      mny = std::min(mny, polys->y[v]);
-      mxy = std::max(mxy, polys->y[v]);
-    }
-    bb[4 * j] = mnx;
-    bb[4 * j + 1] = mny;
-    bb[4 * j + 2] = mxx;
-    bb[4 * j + 3] = mxy;
-  }
+  std::vector<uint32_t> bb;
+  SDB_TRY(polygon_bboxes(polys, B, &bb));
   std::vector<CoverQuery> cq(n_queries);
-  std::vector<QueryDev> hq(n_queries);
+  std::vector<BatchQueryDev> hq(n_queries);
   std::vector<uint32_t> pp, pq, ps;
   uint64_t out_off = 0;
   for (uint32_t q = 0; q < n_queries; ++q) {
     const sdb_query& Qu = queries[q];
-    uint32_t k = 0, F = 0;
-    SDB_TRY(sdb_finest_level(B, Qu.eps, &k, &F));
-    if (!(Qu.x0 < Qu.x1 && Qu.y0 < Qu.y1 && Qu.x1 <= G && Qu.y1 <= G)) {
-      set_error("query %u: viewport must be non-empty and inside the grid", q);
-      return SDB_EINVAL;
+    uint32_t F = 0;
+    sdb_status st = batch_query_dev(B, Qu, out_off, &hq[q], &F);
+    if (st != SDB_OK) {
+      set_error("query %u: %s", q, std::string(sdb_last_error()).c_str());
+      return st;
     }
     if ((uint64_t)Qu.poly_off + Qu.poly_cnt > n_subset_ids || (Qu.poly_cnt && !subset_ids)) {
       set_error("query %u: polygon subset outside the id array", q);
       return SDB_EINVAL;
     }
+    for (uint32_t t = 0; t < Qu.poly_cnt; ++t)
+      if (subset_ids[Qu.poly_off + t] >= P) {
+        set_error("query %u: polygon id %u out of range", q, subset_ids[Qu.poly_off + t]);
+        return SDB_EINVAL;
+      }
     if (out_off + Qu.poly_cnt >= 0xffffffffull) {
       set_error("batch output exceeds 2^32 entries");
       return SDB_EINVAL;
     }
     cq[q] = CoverQuery{F, Qu.x0, Qu.y0, Qu.x1, Qu.y1};
-    QueryDev& d = hq[q];
-    memset(&d, 0, sizeof(d));
-    d.k = k;
-    d.nsteps = (F + 3) / 4;
-    d.st0 = ((4 * d.nsteps - F) & 1u) ? 2u : 0u;
-    d.x0 = Qu.x0;
-    d.y0 = Qu.y0;
-    d.x1 = Qu.x1;
-    d.y1 = Qu.y1;
-    d.out_off = (uint32_t)out_off;
-    // pairs whose polygon's cells can hold viewport points: bounding box grown
-    // by one finest cell
-    const int64_t sgrow = (int64_t)1 << k;
-    for (uint32_t t = 0; t < Qu.poly_cnt; ++t) {
-      const uint32_t j = subset_ids[Qu.poly_off + t];
-      if (j >= P) {
-        set_error("query %u: polygon id %u out of range", q, j);
-        return SDB_EINVAL;
-      }
-      if ((int64_t)bb[4 * j] - sgrow < (int64_t)Qu.x1 && (int64_t)bb[4 * j + 2] + sgrow >= Qu.x0 &&
-          (int64_t)bb[4 * j + 1] - sgrow < (int64_t)Qu.y1 &&
-          (int64_t)bb[4 * j + 3] + sgrow >= Qu.y0) {
-        pp.push_back(j);
-        pq.push_back(q);
-        ps.push_back(t);
-      }
-    }
+    viewport_pairs(bb, q, Qu, hq[q].k, subset_ids ? subset_ids + Qu.poly_off : nullptr, pp, pq,
+                   ps);
     out_off += Qu.poly_cnt;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -615,94 +707,17 @@ sdb_status sdb_batch_create(const sdb_points* pts, const sdb_polygons* polys,
     return SDB_ENOMEM;
   }
   b->device = pts->device;
-  b->pts = pts;
-  b->Q = n_queries;
   b->NP = (uint32_t)pp.size();
-  b->out_len = out_off;
-  // coverings in chunks of queries; a chunk that overflows the builder's
-  // 32-bit ranges (or memory) is halved and retried
-  std::vector<uint64_t> pfirst(n_queries + 1, 0);  // pairs are in query order
-  for (uint32_t i = 0, q = 0; q <= n_queries; ++q) {
-    while (i < pq.size() && pq[i] < q) ++i;
-    pfirst[q] = i;
-  }
-  sdb_status st = SDB_OK;
-  uint32_t chunk_q = 512;
-  std::vector<uint32_t> pq_local;
-  for (uint32_t q0 = 0; q0 < n_queries && st == SDB_OK;) {
-    const uint32_t nq = std::min(chunk_q, n_queries - q0);
-    const uint64_t pa = pfirst[q0], pb = pfirst[q0 + nq];
-    pq_local.assign(pq.begin() + pa, pq.begin() + pb);
-    for (auto& v : pq_local) v -= q0;
-    CoverSpec spec;
-    spec.B = B;
-    spec.Q = nq;
-    spec.q = cq.data() + q0;
-    spec.NP = (uint32_t)(pb - pa);
-    spec.pair_poly = pp.data() + pa;
-    spec.pair_query = pq_local.data();
-    spec.pair_slot = ps.data() + pa;
-    CoverSet set;
-    st = build_coverings(polys, spec, s, &set);
-    if (st == SDB_ENOMEM && nq > 1) {
-      set.release(s);
-      cudaStreamSynchronize(s);
-      cudaGetLastError();
-      chunk_q = nq / 2;
-      st = SDB_OK;
-      continue;
-    }
-    if (st != SDB_OK) {
-      set.release(s);
-      break;
-    }
-    for (uint32_t q = 0; q < nq; ++q) {
-      QueryDev& d = hq[q0 + q];
-      d.sbase = set.qoff[q];
-      d.R = (uint32_t)(set.qoff[q + 1] - set.qoff[q] - 1);
-      d.chunk = (uint32_t)b->cs.size();
-      b->max_ranges = std::max<uint64_t>(b->max_ranges, d.R);
-    }
-    b->n_ranges += set.E - nq;
-    b->n_cells += set.ncells;
-    b->cs.push_back(set);
-    q0 += nq;
-  }
+  b->core.pts = pts;
+  b->core.Q = n_queries;
+  b->core.out_len = out_off;
+  sdb_status st = build_query_coverings(polys, B, cq, pp, pq, ps, hq, &b->cs, 0, s, &b->n_ranges,
+                                        &b->n_cells, &b->max_ranges);
   if (st == SDB_OK) {
-    b->hq = hq;
-    std::vector<ChunkDev> hc;
-    for (auto& c : b->cs) hc.push_back(ChunkDev{c.start, c.pay, c.list_off, c.list_ids});
-    st = dalloc_n(&b->dchunks, hc.size(), s);
-    if (st == SDB_OK)
-      st = cudaMemcpyAsync(b->dchunks, hc.data(), hc.size() * sizeof(ChunkDev),
-                           cudaMemcpyHostToDevice, s) == cudaSuccess
-               ? SDB_OK
-               : cuda_status(cudaErrorUnknown, "chunk copy", __FILE__, __LINE__);
-  }
-  if (st == SDB_OK) st = dalloc_n(&b->dq, n_queries, s);
-  if (st == SDB_OK)
-    st = cudaMemcpyAsync(b->dq, hq.data(), n_queries * sizeof(QueryDev), cudaMemcpyHostToDevice,
-                         s) == cudaSuccess
-             ? SDB_OK
-             : cuda_status(cudaErrorUnknown, "query copy", __FILE__, __LINE__);
-  if (st == SDB_OK) st = dalloc_n(&b->cand, (size_t)n_queries * MAXC * 2, s);
-  if (st == SDB_OK) st = dalloc_n(&b->ncand, n_queries, s);
-  if (st == SDB_OK) st = dalloc_n(&b->heads, (size_t)n_queries + 1, s);
-  if (st == SDB_OK) {
-    candidates_kernel<<<grid_for(n_queries, 64), 64, 0, s>>>(b->dq, n_queries, pts->key, pts->n, B,
-                                                             b->cand, b->ncand);
-    note_launch();
-    if (cudaGetLastError() != cudaSuccess) st = cuda_status(cudaErrorLaunchFailure, "candidates", __FILE__, __LINE__);
-  }
-  if (st == SDB_OK) st = build_tiles(b, b->tile, s);
-  if (st == SDB_OK) {
-    // candidate points (for reporting)
-    std::vector<uint32_t> hc((size_t)n_queries * MAXC * 2), hn(n_queries);
-    cudaMemcpy(hc.data(), b->cand, hc.size() * 4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(hn.data(), b->ncand, hn.size() * 4, cudaMemcpyDeviceToHost);
-    for (uint32_t q = 0; q < n_queries; ++q)
-      for (uint32_t i = 0; i < hn[q]; ++i)
-        b->candidates += hc[(size_t)q * MAXC * 2 + 2 * i + 1] - hc[(size_t)q * MAXC * 2 + 2 * i];
+    b->core.hq = hq;
+    for (auto& c : b->cs)
+      b->core.hchunks.push_back(BatchChunkDev{c.start, c.pay, c.list_off, c.list_ids});
+    st = batch_core_prepare(&b->core, s);
   }
   if (st != SDB_OK) {
     std::string msg = sdb_last_error();
@@ -720,16 +735,16 @@ sdb_status sdb_batch_get_info(const sdb_batch* b, sdb_batch_info* info) {
     return SDB_EINVAL;
   }
   memset(info, 0, sizeof(*info));
-  info->n_queries = b->Q;
+  info->n_queries = b->core.Q;
   info->n_pairs = b->NP;
-  info->out_len = b->out_len;
+  info->out_len = b->core.out_len;
   info->n_ranges = b->n_ranges;
   info->max_ranges = b->max_ranges;
   info->n_cells = b->n_cells;
-  info->candidates = b->candidates;
-  info->n_tiles = b->ntiles;
-  info->tile = b->tile;
-  info->points_per_thread = b->ppt;
+  info->candidates = b->core.candidates;
+  info->n_tiles = b->core.ntiles;
+  info->tile = b->core.tile;
+  info->points_per_thread = b->core.ppt;
   return SDB_OK;
 }
 
@@ -744,18 +759,8 @@ sdb_status sdb_batch_run(sdb_batch* b, int mode, uint64_t* d_count, int64_t* d_s
     return SDB_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  if (mode == SDB_BATCH_PERSISTENT) return run_persistent(b, d_count, d_sum, s);
-  if (mode == SDB_BATCH_PER_QUERY) {
-    SDB_TRY_CUDA(cudaMemsetAsync(d_count, 0, b->out_len * 8, s));
-    if (d_sum) SDB_TRY_CUDA(cudaMemsetAsync(d_sum, 0, b->out_len * 8, s));
-    SDB_TRY_CUDA(cudaMemsetAsync(b->heads, 0, (size_t)b->Q * sizeof(unsigned long long), s));
-    const BatchArgs A = batch_args(b, d_count, d_sum);
-    for (uint32_t q = 0; q < b->Q; ++q)
-      if (b->qtile[q + 1] > b->qtile[q])
-        SDB_TRY(launch_batch(A, b->ppt, d_sum != nullptr, (uint32_t)b->qtile[q],
-                             (uint32_t)b->qtile[q + 1], b->heads + q, s));
-    return SDB_OK;
-  }
+  if (mode == SDB_BATCH_PERSISTENT || mode == SDB_BATCH_PER_QUERY)
+    return batch_core_run(&b->core, mode, d_count, d_sum, s);
   if (mode == SDB_BATCH_GRAPH) {
     if (s == nullptr) {
       set_error("graph mode needs a created stream (the legacy stream cannot be captured)");
@@ -768,7 +773,7 @@ sdb_status sdb_batch_run(sdb_batch* b, int mode, uint64_t* d_count, int64_t* d_s
       }
       cudaGraph_t g = nullptr;
       SDB_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      sdb_status st = run_persistent(b, d_count, d_sum, s);
+      sdb_status st = batch_core_run(&b->core, SDB_BATCH_PERSISTENT, d_count, d_sum, s);
       cudaError_t e = cudaStreamEndCapture(s, &g);
       if (st != SDB_OK) {
         if (g) cudaGraphDestroy(g);
@@ -791,6 +796,15 @@ sdb_status sdb_batch_run(sdb_batch* b, int mode, uint64_t* d_count, int64_t* d_s
   return SDB_EINVAL;
 }
 
+static sdb_status set_tiles(sdb_batch* b, uint32_t T, cudaStream_t s) {
+  SDB_TRY(batch_core_tiles(&b->core, T, s));
+  if (b->graph) {  // the captured launch refers to the old work list
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return SDB_OK;
+}
+
 sdb_status sdb_batch_autotune(sdb_batch* b, void* cuda_stream, uint32_t* tile_out,
                               uint32_t* ppt_out) {
   if (!b) {
@@ -805,24 +819,24 @@ sdb_status sdb_batch_autotune(sdb_batch* b, void* cuda_stream, uint32_t* tile_ou
   Scratch sc(s);
   uint64_t* cnt;
   int64_t* sm;
-  SDB_TRY(sc.get(&cnt, b->out_len));
-  SDB_TRY(sc.get(&sm, b->out_len));
+  SDB_TRY(sc.get(&cnt, b->core.out_len));
+  SDB_TRY(sc.get(&sm, b->core.out_len));
   cudaEvent_t e0, e1;
   SDB_TRY_CUDA(cudaEventCreate(&e0));
   SDB_TRY_CUDA(cudaEventCreate(&e1));
   const uint32_t tiles[] = {1024, 4096, 16384};
   const uint32_t ppts[] = {1, 2, 4};
   float best = 1e30f;
-  uint32_t bt = b->tile, bp = b->ppt;
+  uint32_t bt = b->core.tile, bp = b->core.ppt;
   sdb_status st = SDB_OK;
   for (uint32_t T : tiles) {
-    if ((st = build_tiles(b, T, s)) != SDB_OK) break;
+    if ((st = set_tiles(b, T, s)) != SDB_OK) break;
     for (uint32_t G : ppts) {
-      b->ppt = G;
+      b->core.ppt = G;
       float ms = 0;
-      for (int rep = 0; rep < 2 && st == SDB_OK; ++rep) {  // first run warms up
+      for (int rep = 0; rep < 2 && st == SDB_OK; ++rep) {  // the first run warms up
         cudaEventRecord(e0, s);
-        st = run_persistent(b, cnt, sm, s);
+        st = batch_core_run(&b->core, SDB_BATCH_PERSISTENT, cnt, sm, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) st = SDB_ECUDA;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -838,8 +852,8 @@ sdb_status sdb_batch_autotune(sdb_batch* b, void* cuda_stream, uint32_t* tile_ou
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->ppt = bp;
-  if (st == SDB_OK) st = build_tiles(b, bt, s);
+  b->core.ppt = bp;
+  if (st == SDB_OK) st = set_tiles(b, bt, s);
   if (st == SDB_OK) {
     if (tile_out) *tile_out = bt;
     if (ppt_out) *ppt_out = bp;
@@ -854,8 +868,8 @@ sdb_status sdb_batch_set_tuning(sdb_batch* b, uint32_t tile, uint32_t points_per
     set_error("batch NULL, tile 0, or points per thread not 1, 2 or 4");
     return SDB_EINVAL;
   }
-  b->ppt = points_per_thread;
-  return build_tiles(b, tile, (cudaStream_t)cuda_stream);
+  b->core.ppt = points_per_thread;
+  return set_tiles(b, tile, (cudaStream_t)cuda_stream);
 }
 
 sdb_status sdb_batch_query_ranges(const sdb_batch* b, uint32_t* h_ranges) {
@@ -863,7 +877,7 @@ sdb_status sdb_batch_query_ranges(const sdb_batch* b, uint32_t* h_ranges) {
     set_error("batch or output is NULL");
     return SDB_EINVAL;
   }
-  for (uint32_t q = 0; q < b->Q; ++q) h_ranges[q] = b->hq[q].R;
+  for (uint32_t q = 0; q < b->core.Q; ++q) h_ranges[q] = b->core.hq[q].R;
   return SDB_OK;
 }
 
@@ -875,9 +889,7 @@ void sdb_batch_free(sdb_batch* b) {
   cudaDeviceSynchronize();
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto& c : b->cs) c.release(0);
-  void* ps[] = {b->dq, b->cand, b->ncand, b->tiles, b->heads, b->dchunks};
-  for (void* q : ps)
-    if (q) cudaFreeAsync(q, 0);
+  b->core.release(0);
   cudaStreamSynchronize(0);
   cudaSetDevice(prev);
   delete b;

@@ -168,6 +168,17 @@ struct sdb_covering {
   size_t bytes = 0;
 };
 
+// resident point set ordered by full-resolution Hilbert id (batch.cu)
+struct sdb_points {
+  int device = 0;
+  uint32_t B = 0;
+  uint64_t n = 0;
+  uint64_t* key = nullptr;
+  uint32_t* x = nullptr;
+  uint32_t* y = nullptr;
+  int32_t* attr = nullptr;
+};
+
 namespace sdb {
 
 // cover.cu -------------------------------------------------------------------
@@ -205,6 +216,68 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
                            CoverSet* out);
 sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,
                                  sdb_covering* cov);
+// batch.cu ------------------------------------------------------------------
+// Per-query parameters of a batched join, and the covering arrays a query's
+// slice lives in (one chunk may serve many queries).
+struct BatchQueryDev {
+  uint64_t sbase;  // first entry of the query's covering slice in its chunk
+  uint32_t R;      // ranges in the slice (the sentinel follows)
+  uint32_t chunk;
+  uint32_t k, nsteps, st0;
+  uint32_t x0, y0, x1, y1;
+  uint32_t out_off;
+};
+struct BatchChunkDev {
+  const uint64_t* start;
+  const uint32_t* pay;
+  const uint32_t* list_off;
+  const uint32_t* list_ids;
+};
+struct BatchTile {
+  uint32_t q, begin, end, pad;
+};
+// Everything a batched join needs besides the coverings themselves.
+struct BatchCore {
+  const sdb_points* pts = nullptr;
+  uint32_t Q = 0;
+  uint64_t out_len = 0, candidates = 0;
+  std::vector<BatchQueryDev> hq;
+  std::vector<BatchChunkDev> hchunks;
+  BatchQueryDev* dq = nullptr;
+  BatchChunkDev* dchunks = nullptr;
+  uint32_t* cand = nullptr;   // per query up to 81 candidate point index ranges
+  uint32_t* ncand = nullptr;
+  uint32_t tile = 4096, ppt = 2;
+  BatchTile* tiles = nullptr;
+  uint64_t ntiles = 0;
+  std::vector<uint64_t> qtile;  // host, Q + 1: tiles of query q
+  unsigned long long* heads = nullptr;  // Q + 1 work counters
+  void release(cudaStream_t s);
+};
+// viewport, level and output slot of one query (sbase/R/chunk left to the caller)
+sdb_status batch_query_dev(uint32_t B, const sdb_query& q, uint64_t out_off, BatchQueryDev* d,
+                           uint32_t* F_out);
+// upload hq/hchunks, candidate ranges, work list (candidate counts computed)
+sdb_status batch_core_prepare(BatchCore* c, cudaStream_t s);
+sdb_status batch_core_tiles(BatchCore* c, uint32_t T, cudaStream_t s);
+// mode SDB_BATCH_PERSISTENT or SDB_BATCH_PER_QUERY; outputs cleared first
+sdb_status batch_core_run(BatchCore* c, int mode, uint64_t* count, int64_t* sum, cudaStream_t s);
+// coverings for queries cq (pairs in query order), chunked; fills sbase/R/chunk
+// of hq with chunk indices starting at chunk_base
+sdb_status build_query_coverings(const sdb_polygons* polys, uint32_t B,
+                                 const std::vector<CoverQuery>& cq,
+                                 const std::vector<uint32_t>& pp, const std::vector<uint32_t>& pq,
+                                 const std::vector<uint32_t>& ps, std::vector<BatchQueryDev>& hq,
+                                 std::vector<CoverSet>* sets, uint32_t chunk_base,
+                                 cudaStream_t s, uint64_t* n_ranges, uint64_t* n_cells,
+                                 uint64_t* max_ranges);
+// pairs of query q whose polygon (bounding boxes bb, 4 per polygon) can reach
+// its viewport at finest shift k; ids = the query's subset
+void viewport_pairs(const std::vector<uint32_t>& bb, uint32_t q, const sdb_query& Qu, uint32_t k,
+                    const uint32_t* ids, std::vector<uint32_t>& pp, std::vector<uint32_t>& pq,
+                    std::vector<uint32_t>& ps);
+sdb_status polygon_bboxes(const sdb_polygons* polys, uint32_t B, std::vector<uint32_t>* bb);
+
 // learned.cu
 sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream_t s);
 // join.cu

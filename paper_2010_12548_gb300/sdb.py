@@ -53,6 +53,23 @@ class BatchInfo(C.Structure):
 
 BATCH_PERSISTENT, BATCH_PER_QUERY, BATCH_GRAPH = 0, 1, 2
 
+
+class ServerConfig(C.Structure):
+    _fields_ = [("workers", C.c_uint32), ("max_batch", C.c_uint32), ("cache_bytes", C.c_uint64),
+                ("use_cache", C.c_uint32), ("per_query", C.c_uint32), ("tile", C.c_uint32),
+                ("points_per_thread", C.c_uint32)]
+
+
+class TicketInfo(C.Structure):
+    _fields_ = [("latency_ms", C.c_double), ("queue_ms", C.c_double), ("batch_size", C.c_uint32),
+                ("cache_hit", C.c_uint32), ("ranges", C.c_uint64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "batches", "cache_hits",
+                                          "cache_misses", "evictions", "cache_bytes",
+                                          "cache_entries", "peak_bytes")]
+
 _lib = None
 
 
@@ -86,6 +103,11 @@ def lib():
             "sdb_batch_autotune": ([P, P, P, P], I),
             "sdb_batch_set_tuning": ([P, U32, U32, P], I),
             "sdb_batch_free": ([P], None),
+            "sdb_server_create": ([P, P, P, P], I),
+            "sdb_server_submit": ([P, P, P, P], I),
+            "sdb_server_wait": ([P, U64, U32, P, P, P], I),
+            "sdb_server_get_stats": ([P, P], I),
+            "sdb_server_destroy": ([P], None),
             "sdb_join_aggregate_host_noalloc": ([P, P, P, U64, P, I, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -345,6 +367,63 @@ def batch_autotune(batch: Batch, stream=None) -> tuple[int, int]:
 
 def batch_set_tuning(batch: Batch, tile: int, points_per_thread: int, stream=None):
     _check(lib().sdb_batch_set_tuning(batch.handle, tile, points_per_thread, _stream(stream)))
+
+
+class Server:
+    """Continuous-batching query server (owns the library handle)."""
+
+    def __init__(self, handle: int, points: Points, P: int):
+        self._h = C.c_void_p(handle)
+        self.points = points
+        self.n_polygons = P
+
+    def submit(self, query, subset_ids) -> int:
+        """Queue (x0, y0, x1, y1, eps, _, poly_cnt) with its subset ids; returns a ticket."""
+        ids = np.ascontiguousarray(subset_ids, np.uint32)
+        q = Query(*[int(v) for v in query])
+        q.poly_off = 0
+        q.poly_cnt = len(ids)
+        t = C.c_uint64()
+        _check(lib().sdb_server_submit(self._h, C.byref(q), _np_ptr(ids), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, poly_cnt: int, timeout_ms: int = 60_000):
+        """(count, sum, TicketInfo) of a ticket; raises SdbError(SDB_ETIMEOUT) on timeout."""
+        cnt = np.zeros(max(poly_cnt, 1), np.uint64)
+        sm = np.zeros(max(poly_cnt, 1), np.int64)
+        info = TicketInfo()
+        _check(lib().sdb_server_wait(self._h, ticket, timeout_ms, _np_ptr(cnt), _np_ptr(sm),
+                                     C.byref(info)))
+        return cnt[:poly_cnt], sm[:poly_cnt], info
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(lib().sdb_server_get_stats(self._h, C.byref(st)))
+        return st
+
+    def destroy(self):
+        if self._h and self._h.value:
+            lib().sdb_server_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def server_create(points: Points, polys, *, workers=4, max_batch=256, cache_bytes=40 << 30,
+                  use_cache=True, per_query=False, tile=0, points_per_thread=0) -> Server:
+    off = np.ascontiguousarray(polys.ring_off, np.uint32)
+    x = np.ascontiguousarray(polys.x, np.uint32)
+    y = np.ascontiguousarray(polys.y, np.uint32)
+    sp = _Polys(len(off) - 1, _np_ptr(off), _np_ptr(x), _np_ptr(y))
+    cfg = ServerConfig(workers, max_batch, cache_bytes, int(use_cache), int(per_query), tile,
+                       points_per_thread)
+    out = C.c_void_p()
+    _check(lib().sdb_server_create(points.handle, C.byref(sp), C.byref(cfg), C.byref(out)))
+    return Server(out.value, points, len(off) - 1)
 
 
 def status_string(st: int) -> str:

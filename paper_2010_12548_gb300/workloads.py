@@ -513,3 +513,48 @@ def lod_workload(n_points: int = 200_000_000, n_queries: int = 4096) -> tuple:
     pts = mobility_points(BASE_SEED + 104, n_points, 28, 64, sigma=(2 ** 20, 2 ** 23))
     qb = lod_queries(BASE_SEED + 4, n_queries, T)
     return T, pts, qb
+
+
+def zoom_sessions(seed: int, n_sessions: int, polys: Polygons, start_side: int = 2 ** 24,
+                  start_eps: int = 2 ** 14, zooms=(5, 20), max_polys: int = 5000) -> list:
+    """Zoom sessions: from a square viewport of side ``start_side`` at a
+    uniform position, each step halves the side (around a point uniform in the
+    middle half of the current view) and halves eps, for a number of steps
+    uniform in ``zooms``; eps stops at 2, the side at 1.  Each query asks for
+    the polygons whose bounding box meets its viewport (at most ``max_polys``,
+    in id order).  Returns a list of sessions, each a list of (query row, ids)
+    with rows (x0, y0, x1, y1, eps, 0, n)."""
+    rng = np.random.default_rng(seed)
+    G = 2 ** polys.grid_bits
+    bb = polygon_bboxes(polys)
+    out = []
+    for _ in range(n_sessions):
+        side = min(start_side, G)
+        x0 = int(rng.integers(0, G - side + 1))
+        y0 = int(rng.integers(0, G - side + 1))
+        eps = start_eps
+        steps = int(rng.integers(zooms[0], zooms[1] + 1))
+        sess = []
+        for _ in range(steps):
+            meet = np.nonzero((bb[:, 0] < x0 + side) & (bb[:, 2] >= x0) &
+                              (bb[:, 1] < y0 + side) & (bb[:, 3] >= y0))[0][:max_polys]
+            sess.append(((x0, y0, x0 + side, y0 + side, eps, 0, len(meet)),
+                         meet.astype(np.uint32)))
+            # zoom in around a point of the middle half of the view
+            cx = x0 + side // 4 + int(rng.integers(0, max(1, side // 2)))
+            cy = y0 + side // 4 + int(rng.integers(0, max(1, side // 2)))
+            side = max(1, side // 2)
+            x0 = min(max(0, cx - side // 2), G - side)
+            y0 = min(max(0, cy - side // 2), G - side)
+            eps = max(2, eps // 2)
+        out.append(sess)
+    return out
+
+
+def serving_workload(n_points: int = 500_000_000, n_sessions: int = 512) -> tuple:
+    """500M resident points on [0,2^28)^2 (cluster/uniform mix as the
+    level-of-detail workload) and zoom sessions over the 40,000-polygon
+    tiling."""
+    T = tracts40k_tiling()
+    pts = mobility_points(BASE_SEED + 105, n_points, 28, 64, sigma=(2 ** 20, 2 ** 23))
+    return T, pts, zoom_sessions(BASE_SEED + 5, n_sessions, T)
