@@ -55,8 +55,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--points", type=int, default=100_000_000)
-    ap.add_argument("--no-extras", action="store_true", help="skip join-only, e2e and CPU legs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed steps (no join-only, e2e, CPU, batch or serving legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--legs", default="join,e2e,cpu,batch,serve",
+                    help="extra legs: join (lookups alone), e2e, cpu, batch, serve")
+    ap.add_argument("--lod-points", type=int, default=200_000_000)
+    ap.add_argument("--lod-queries", type=int, default=4096)
+    ap.add_argument("--serve-points", type=int, default=500_000_000)
+    ap.add_argument("--serve-rates", default="1000,10000,50000")
     return ap.parse_args()
 
 
@@ -292,10 +299,11 @@ def main():
     res["phases_ms"] = {"build_and_index": dict(zip([str(e) for e in w.eps], build_ms)),
                         "join_learned": dict(zip([str(e) for e in w.eps], join_ms))}
 
+    legs = set() if args.no_extras else set(args.legs.split(","))
     # ---- join alone, learned vs binary search, per eps (not part of the step)
     peak, peak_kind = peaks()
     joins = {}
-    if not args.no_extras:
+    if "join" in legs:
         reps = 5
         for i, eps in enumerate(w.eps):
             c = sdb.build_covering(w.polygons, 24, eps, stream)
@@ -341,7 +349,7 @@ def main():
                        "peak_kind": peak_kind, "traffic": None,
                        "algorithmic_bytes_per_point": per_pt}
     # ---- end to end through the host-buffer entry point
-    if not args.no_extras:
+    if "e2e" in legs:
         hx = torch.from_numpy(w.points.x.view(np.int32)).pin_memory()
         hy = torch.from_numpy(w.points.y.view(np.int32)).pin_memory()
         ha = torch.from_numpy(w.points.attr).pin_memory()
@@ -373,17 +381,148 @@ def main():
         res["e2e"]["matches_device"] = bool(np.array_equal(hc.numpy(), cnt.cpu().numpy()) and
                                             np.array_equal(hs.numpy(), sm.cpu().numpy()))
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
-    if rank == 0 and ws == 1 and not args.no_extras:
+    if rank == 0 and ws == 1 and "cpu" in legs:
         threads = os.cpu_count() or 1
         rate, sample, secs = cpu_oracle_rate(w, args.cpu_seconds, threads)
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": f"first {sample} of the {N} points, all {E} eps "
                                          f"levels, definitional per-point test ({secs:.1f} s)"}
+    # ---- batched level-of-detail queries and serving (resident points)
+    del x, y, a
+    torch.cuda.empty_cache()
+    if "batch" in legs or "serve" in legs:
+        res.update(resident_legs(args, legs, sdb, torch, dev, stream))
+    if "serving" in res and res["serving"].get("batched"):
+        nominal = [r for r in res["serving"]["batched"] if r["rate"] == 10000] or \
+            res["serving"]["batched"]
+        res["p50_ms"] = nominal[0]["p50_ms"]
+        res["p99_ms"] = nominal[0]["p99_ms"]
     if rank == 0:
         print(json.dumps(res), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def timed(torch, stream, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def poisson_serve(sdb, srv, queries, rate, n, seed):
+    """Submit n queries at Poisson arrival times (rate per second) from a
+    submitter thread; returns per-query latencies and the wall time."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    order = rng.integers(0, len(queries), size=n)
+    tickets = [None] * n
+    t0 = time.perf_counter()
+    due = t0 + np.cumsum(gaps)
+
+    def submitter():
+        for k in range(n):
+            while True:
+                now = time.perf_counter()
+                if now >= due[k]:
+                    break
+                if due[k] - now > 2e-4:
+                    time.sleep(min(1e-3, due[k] - now - 1e-4))
+            row, ids = queries[order[k]]
+            tickets[k] = srv.submit(row, ids)
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, batch, hits = [], [], 0
+    th.join()
+    for k in range(n):
+        _, _, info = srv.wait(tickets[k], len(queries[order[k]][1]), timeout_ms=600_000)
+        lat.append(info.latency_ms)
+        batch.append(info.batch_size)
+        hits += info.cache_hit
+    wall = time.perf_counter() - t0
+    return np.asarray(lat), np.asarray(batch), hits, wall
+
+
+def resident_legs(args, legs, sdb, torch, dev, stream):
+    """Batched level-of-detail queries (4,096 queries over 200M resident points)
+    and serving (Poisson arrivals of zoom-session queries over 500M points)."""
+    from paper_2010_12548_gb300 import workloads as W
+    out = {}
+    T = W.tracts40k_tiling()
+    n_all = max(args.lod_points if "batch" in legs else 0,
+                args.serve_points if "serve" in legs else 0)
+    pts = W.resident_points(n_all)
+
+    def resident(n):
+        xs = torch.from_numpy(pts.x[:n].view(np.int32)).to(dev)
+        ys = torch.from_numpy(pts.y[:n].view(np.int32)).to(dev)
+        at = torch.from_numpy(pts.attr[:n]).to(dev)
+        p = sdb.points_create(xs, ys, at, 28, stream)
+        del xs, ys, at
+        torch.cuda.empty_cache()
+        return p
+
+    if "batch" in legs:
+        qb = W.lod_queries(W.BASE_SEED + 4, args.lod_queries, T)
+        rows = [tuple(r) for r in qb.queries]
+        p = resident(args.lod_points)
+        t = time.perf_counter()
+        b = sdb.batch_create(p, T, rows, qb.subset_ids, stream)
+        build_s = time.perf_counter() - t
+        tile, ppt = sdb.batch_autotune(b, stream)
+        inf = b.info()
+        cnt = torch.zeros(inf.out_len, dtype=torch.int64, device=dev)
+        sm = torch.zeros(inf.out_len, dtype=torch.int64, device=dev)
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            ms = {m: timed(torch, side, lambda m=m: sdb.batch_run(b, m, cnt, sm, side), 5)
+                  for m in (sdb.BATCH_PERSISTENT, sdb.BATCH_GRAPH, sdb.BATCH_PER_QUERY)}
+        out["batched"] = {
+            "workload": f"lod{args.lod_queries}_tracts40k_pts{args.lod_points // 1_000_000}M_g28",
+            "queries": inf.n_queries, "pairs": inf.n_pairs, "ranges": inf.n_ranges,
+            "max_ranges": inf.max_ranges, "cells": inf.n_cells, "candidate_points": inf.candidates,
+            "covering_build_s": build_s, "tile": tile, "points_per_thread": ppt,
+            "persistent_ms": ms[sdb.BATCH_PERSISTENT], "graph_ms": ms[sdb.BATCH_GRAPH],
+            "per_query_launches_ms": ms[sdb.BATCH_PER_QUERY],
+            "queries_per_s_graph": inf.n_queries / (ms[sdb.BATCH_GRAPH] / 1e3),
+            "candidate_points_per_s_graph": inf.candidates / (ms[sdb.BATCH_GRAPH] / 1e3)}
+        b.free()
+        p.free()
+        del cnt, sm
+        torch.cuda.empty_cache()
+    if "serve" in legs:
+        sessions = W.zoom_sessions(W.BASE_SEED + 5, 512, T)
+        queries = [q for ss in sessions for q in ss]
+        p = resident(args.serve_points)
+        rates = [int(r) for r in args.serve_rates.split(",") if r]
+        serving = {"workload": f"zoom512sessions_tracts40k_pts{args.serve_points // 1_000_000}M_g28",
+                   "queries_in_pool": len(queries), "batched": [], "plain": []}
+        for kind, cfg in (("batched", dict(workers=4, max_batch=256, cache_bytes=40 << 30)),
+                          ("plain", dict(workers=1, max_batch=1, use_cache=False,
+                                         per_query=True))):
+            for rate in (rates if kind == "batched" else rates[:1]):
+                srv = sdb.server_create(p, T, **cfg)
+                n = int(min(4000, max(400, rate * 2)))
+                if kind == "plain":
+                    n = min(n, 600)
+                lat, bs, hits, wall = poisson_serve(sdb, srv, queries, rate, n, seed=rate)
+                st = srv.stats()
+                srv.destroy()
+                serving[kind].append({
+                    "rate": rate, "queries": n, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                    "throughput_qps": n / wall, "mean_batch": float(bs.mean()),
+                    "cache_hit_rate": hits / n, "batches": int(st.batches),
+                    "cache_bytes": int(st.peak_bytes)})
+        out["serving"] = serving
+        p.free()
+    return out
 
 
 if __name__ == "__main__":

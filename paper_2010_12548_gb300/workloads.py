@@ -337,12 +337,14 @@ def uniform_points(rng: np.random.Generator, n: int, grid_bits: int) -> Points:
 
 def mobility_points(seed: int, n: int, grid_bits: int, n_clusters: int,
                     sigma=(2 ** 16, 2 ** 19), frac_cluster: float = 0.7,
-                    chunk: int = 1 << 22) -> Points:
+                    chunk: int = 1 << 22, threads: int | None = None) -> Points:
     """Cluster/uniform mix: ``frac_cluster`` of the points come from
     ``n_clusters`` isotropic Gaussians (centre uniform, sigma uniform in
     ``sigma``, clipped to the grid), the rest are uniform.  Points appear in
     random order.  Generated in fixed-size chunks, each from its own child
-    seed, so the result does not depend on memory limits."""
+    seed (so the result does not depend on memory limits or on the number of
+    threads filling the chunks)."""
+    import concurrent.futures as cf
     G = 2 ** grid_bits
     ss = np.random.SeedSequence(seed)
     head, body = ss.spawn(2)
@@ -353,7 +355,8 @@ def mobility_points(seed: int, n: int, grid_bits: int, n_clusters: int,
     y = np.empty(n, np.uint32)
     attr = np.empty(n, np.int32)
     nchunks = (n + chunk - 1) // chunk
-    for c, cs in zip(range(nchunks), body.spawn(nchunks)):
+
+    def fill(c, cs):
         r = np.random.default_rng(cs)
         a, b = c * chunk, min(n, (c + 1) * chunk)
         m = b - a
@@ -369,6 +372,15 @@ def mobility_points(seed: int, n: int, grid_bits: int, n_clusters: int,
         x[a:b] = px.astype(np.uint32)
         y[a:b] = py.astype(np.uint32)
         attr[a:b] = fare_attr(r, m)
+
+    seeds = body.spawn(nchunks)
+    workers = threads or min(16, os.cpu_count() or 1)
+    if nchunks <= 1 or workers <= 1:
+        for c, cs in enumerate(seeds):
+            fill(c, cs)
+    else:
+        with cf.ThreadPoolExecutor(workers) as ex:
+            list(ex.map(fill, range(nchunks), seeds))
     return Points(x, y, attr, grid_bits)
 
 
@@ -505,14 +517,19 @@ def lod_queries(seed: int, n: int, polys: Polygons, side=(2 ** 14, 2 ** 24),
                       np.concatenate(ids) if ids else np.zeros(0, np.uint32))
 
 
+def resident_points(n_points: int) -> Points:
+    """Points on [0,2^28)^2 for the level-of-detail and serving workloads: 70%
+    from 64 Gaussian clusters (sigma in [2^20, 2^23], clipped), 30% uniform.
+    A shorter set is a prefix of a longer one (same chunks)."""
+    return mobility_points(BASE_SEED + 104, n_points, 28, 64, sigma=(2 ** 20, 2 ** 23))
+
+
 def lod_workload(n_points: int = 200_000_000, n_queries: int = 4096) -> tuple:
     """4,096 level-of-detail queries over 200M resident points on [0,2^28)^2
-    (70% from 64 Gaussian clusters with sigma in [2^20, 2^23], 30% uniform) and
-    the 40,000-polygon tiling; eps from {2^14 .. 2^6}."""
+    and the 40,000-polygon tiling; eps from {2^14 .. 2^6}."""
     T = tracts40k_tiling()
-    pts = mobility_points(BASE_SEED + 104, n_points, 28, 64, sigma=(2 ** 20, 2 ** 23))
     qb = lod_queries(BASE_SEED + 4, n_queries, T)
-    return T, pts, qb
+    return T, resident_points(n_points), qb
 
 
 def zoom_sessions(seed: int, n_sessions: int, polys: Polygons, start_side: int = 2 ** 24,
@@ -556,5 +573,4 @@ def serving_workload(n_points: int = 500_000_000, n_sessions: int = 512) -> tupl
     level-of-detail workload) and zoom sessions over the 40,000-polygon
     tiling."""
     T = tracts40k_tiling()
-    pts = mobility_points(BASE_SEED + 105, n_points, 28, 64, sigma=(2 ** 20, 2 ** 23))
-    return T, pts, zoom_sessions(BASE_SEED + 5, n_sessions, T)
+    return T, resident_points(n_points), zoom_sessions(BASE_SEED + 5, n_sessions, T)
