@@ -473,7 +473,15 @@ sdb_status build_query_coverings(const sdb_polygons* polys, uint32_t B,
   uint32_t chunk_q = 512;
   std::vector<uint32_t> pq_local;
   for (uint32_t q0 = 0; q0 < Q;) {
-    const uint32_t nq = std::min(chunk_q, Q - q0);
+    // queries of a chunk share 64-bit keys: query bits above 2 * (finest level)
+    uint32_t nq = std::min(chunk_q, Q - q0);
+    for (;;) {
+      uint32_t Fm = 0;
+      for (uint32_t q = q0; q < q0 + nq; ++q) Fm = std::max(Fm, cq[q].F);
+      const uint32_t room = 64 - 2 * Fm;  // F <= 30
+      if (nq == 1 || room >= 32 || nq <= (1u << room)) break;
+      nq = 1u << room;
+    }
     const uint64_t pa = pfirst[q0], pb = pfirst[q0 + nq];
     pq_local.assign(pq.begin() + pa, pq.begin() + pb);
     for (auto& v : pq_local) v -= q0;

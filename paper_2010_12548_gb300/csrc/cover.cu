@@ -859,7 +859,9 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
   uint32_t qshift = 64;
   int key_bits = bits_for(1ull << (2 * Fmax));
   if (Q > 1) {
-    qshift = 2 * Fmax + 1;
+    // ids are below 4^F; a range end may reach 4^F and carry into the query
+    // field, which the merge never compares across queries
+    qshift = 2 * Fmax;
     key_bits = (int)qshift + bits_for(Q - 1);
     if (key_bits > 64) {
       set_error("batched coverings: %u queries at finest level %u do not fit 64-bit keys", Q, Fmax);

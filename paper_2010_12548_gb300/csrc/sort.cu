@@ -90,6 +90,7 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 16;  // per lane
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+static_assert(RS_THREADS == 256, "one thread per digit in the scatter's digit scans");
 
 __global__ __launch_bounds__(RS_THREADS) void radix_hist_kernel(const uint64_t* __restrict__ keys,
                                                                 size_t n, int shift,
@@ -114,53 +115,92 @@ __global__ __launch_bounds__(RS_THREADS) void radix_hist_kernel(const uint64_t* 
   }
 }
 
+// Stable scatter of one 8-bit digit.  Each warp ranks its 512 keys (in order)
+// by digit with a warp match; the block then lays its tile out in shared memory
+// sorted by digit (stable), and writes it back so that consecutive threads
+// write consecutive slots of the same digit's output run (coalesced), starting
+// at the block's global offset for that digit.
 template <bool VALS>
 __global__ __launch_bounds__(RS_THREADS) void radix_scatter_kernel(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ offs,
     uint32_t nblocks) {
-  __shared__ uint32_t cnt[RS_WARPS][256];
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(dyn);                 // RS_TILE keys
+  uint32_t* sv = reinterpret_cast<uint32_t*>(dyn + RS_TILE * 8);   // RS_TILE values
+  __shared__ uint32_t cnt[RS_WARPS][256];  // per warp and digit: count, then warp prefix
+  __shared__ uint32_t dstart[256];         // digit's first slot in the tile
+  __shared__ uint32_t gbase[256];          // digit's first global slot for this block
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  size_t base = (size_t)blockIdx.x * RS_TILE + (size_t)w * (32 * RS_ITEMS);
-  unsigned lt = (1u << lane) - 1u;
+  const size_t tile0 = (size_t)blockIdx.x * RS_TILE;
+  const size_t base = tile0 + (size_t)w * (32 * RS_ITEMS);
+  const unsigned lt = (1u << lane) - 1u;
   uint64_t k[RS_ITEMS];
   uint32_t v[RS_ITEMS];
   uint32_t rank[RS_ITEMS];
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
-    size_t g = base + (size_t)it * 32 + lane;
-    bool ok = g < n;
+    const size_t g = base + (size_t)it * 32 + lane;
+    const bool ok = g < n;
     k[it] = ok ? kin[g] : 0ull;
     if (VALS) v[it] = ok ? vin[g] : 0u;
-    uint32_t d = ok ? (uint32_t)((k[it] >> shift) & 255u) : 256u;
-    unsigned peers = __match_any_sync(FULL, d);
-    uint32_t before = ok ? cnt[w][d] : 0u;
+    const uint32_t d = ok ? (uint32_t)((k[it] >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(FULL, d);
+    const uint32_t before = ok ? cnt[w][d] : 0u;
     __syncwarp();
     if (ok && lane == __ffs(peers) - 1) cnt[w][d] = before + __popc(peers);
     __syncwarp();
     rank[it] = before + __popc(peers & lt);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
-    uint32_t run = offs[(size_t)d * nblocks + blockIdx.x];
+  // digit totals of the tile -> warp prefixes; thread d owns digit d
+  uint32_t total = 0;
+  {
+    const int d = threadIdx.x;  // RS_THREADS == 256
     for (int ww = 0; ww < RS_WARPS; ++ww) {
-      uint32_t t = cnt[ww][d];
-      cnt[ww][d] = run;
-      run += t;
+      const uint32_t t = cnt[ww][d];
+      cnt[ww][d] = total;
+      total += t;
+    }
+    gbase[d] = offs[(size_t)d * nblocks + blockIdx.x];
+  }
+  // exclusive scan of the 256 digit totals (block-wide, two levels of warps)
+  {
+    __shared__ uint32_t wsum[RS_WARPS];
+    uint32_t inc = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int ww = 0; ww < w; ++ww) wpre += wsum[ww];
+    dstart[threadIdx.x] = wpre + inc - total;
+  }
+  __syncthreads();
+  // stable layout of the tile by digit in shared memory
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    const size_t g = base + (size_t)it * 32 + lane;
+    if (g < n) {
+      const uint32_t d = (uint32_t)((k[it] >> shift) & 255u);
+      const uint32_t slot = dstart[d] + cnt[w][d] + rank[it];
+      sk[slot] = k[it];
+      if (VALS) sv[slot] = v[it];
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int it = 0; it < RS_ITEMS; ++it) {
-    size_t g = base + (size_t)it * 32 + lane;
-    if (g < n) {
-      uint32_t d = (uint32_t)((k[it] >> shift) & 255u);
-      uint32_t pos = cnt[w][d] + rank[it];
-      kout[pos] = k[it];
-      if (VALS) vout[pos] = v[it];
-    }
+  const uint32_t tile_n = (uint32_t)min((size_t)RS_TILE, n - tile0);
+  for (uint32_t i = threadIdx.x; i < tile_n; i += RS_THREADS) {
+    const uint64_t key = sk[i];
+    const uint32_t d = (uint32_t)((key >> shift) & 255u);
+    const uint32_t pos = gbase[d] + (i - dstart[d]);
+    kout[pos] = key;
+    if (VALS) vout[pos] = sv[i];
   }
 }
 
@@ -175,6 +215,10 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
     return SDB_EINVAL;
   }
   uint32_t nblocks = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
+  constexpr size_t SCATTER_SMEM = (size_t)RS_TILE * 12;
+  SDB_TRY_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<VALS>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SCATTER_SMEM));
   Scratch sc(s);
   uint32_t *hist, *offs;
   SDB_TRY(sc.get(&hist, (size_t)256 * nblocks));
@@ -186,7 +230,8 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
     SDB_TRY(exclusive_scan<uint32_t>(hist, offs, (size_t)256 * nblocks, nullptr, s));
-    radix_scatter_kernel<VALS><<<nblocks, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, offs, nblocks);
+    radix_scatter_kernel<VALS><<<nblocks, RS_THREADS, SCATTER_SMEM, s>>>(ka, va, kb, vb, n, shift,
+                                                                          offs, nblocks);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
     uint64_t* t = ka;
