@@ -179,6 +179,14 @@ __device__ __forceinline__ uint32_t edge_vs_children(const Edge& e, int64_t px, 
   return out | (flip1 << 5) | (flip2 << 6) | ((flip1 ^ flipm) << 7);
 }
 
+// One level of the refinement: each frontier item (a boundary cell of one
+// pair) is split into its 4 children.  G lanes share an item (G a power of two
+// up to 32, chosen from the level's mean edge count): each lane tests every
+// G-th edge, the group combines meet counts and parity flips with shuffles, and
+// its first lane writes the records and child items.  Child edge lists keep
+// the parent's edge order (a ballot per child and chunk of G edges); the meet
+// masks of the first 8 chunks are kept in a register for that second pass.
+template <int G>
 __global__ __launch_bounds__(256) void expand_level_kernel(
     const Item* __restrict__ items, uint32_t n_items, const uint32_t* __restrict__ elist,
     const Edge* __restrict__ edges, const uint32_t* __restrict__ pair_query,
@@ -186,8 +194,12 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
     uint32_t B, uint32_t L, Item* __restrict__ next_items, uint32_t* __restrict__ next_elist,
     uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val, unsigned long long rec_base,
     unsigned long long* __restrict__ counters) {
-  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  bool active = t < n_items;
+  const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = gt / G < n_items;
+  const uint32_t t = (uint32_t)(gt / G);  // item of this lane's group
+  const uint32_t gl = (uint32_t)(gt % G); // lane within the group
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t gmask = G == 32 ? FULL : (((1u << G) - 1u) << (lane & ~(uint32_t)(G - 1)));
   Item it{0, 0, 0, 0, 0};
   if (active) it = items[t];
   const uint32_t qi = active ? pair_query[it.pair] : 0u;
@@ -211,15 +223,25 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   const uint32_t par = it.ecnt_par >> 31;
   // children c = dy*2 + dx, lower-left corner (px + dx*side, py + dy*side)
   uint32_t cnt[4] = {0, 0, 0, 0};
-  uint32_t flip = 0;  // bit c: parity flip from the parent's corner to child c's
-  for (uint32_t i = 0; i < ecnt; ++i) {
+  uint32_t flip = 0;   // bit c: parity flip from the parent's corner to child c's
+  uint32_t mcache = 0; // meet bits of this lane's edges in chunks 0..7
+  for (uint32_t i = gl, j = 0; i < ecnt; i += G, ++j) {
     const uint32_t m = edge_vs_children(edges[elist[it.eoff + i]], px, py, sh);
 #pragma unroll
     for (int c = 0; c < 4; ++c) cnt[c] += (m >> c) & 1u;
     flip ^= m >> 4;
+    if (j < 8) mcache |= (m & 15u) << (4 * j);
+  }
+  if (G > 1) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cnt[c] += __shfl_xor_sync(gmask, cnt[c], o);
+      flip ^= __shfl_xor_sync(gmask, flip, o);
+    }
   }
   uint32_t n_rec = 0, n_it = 0, n_ed = 0;
-  if (active) {
+  if (active && gl == 0) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       uint32_t inside = (par ^ (flip >> c)) & 1u;
@@ -240,6 +262,11 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   unsigned long long io = warp_alloc(n_it, &counters[0]);
   unsigned long long eo = warp_alloc(n_ed, &counters[1]);
   if (!active) return;
+  const uint32_t leader = lane & ~(uint32_t)(G - 1);
+  if (G > 1) {
+    n_it = __shfl_sync(gmask, n_it, leader);
+    eo = __shfl_sync(gmask, eo, leader);
+  }
   uint32_t ceoff[4] = {0, 0, 0, 0};
   const uint32_t shift = 2 * (F - cl);
   const uint64_t qbits = qshift >= 64 ? 0ull : ((uint64_t)qi << qshift);
@@ -254,24 +281,36 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
     uint32_t inside = (par ^ (flip >> c)) & 1u;
     bool emit = (cnt[c] > 0) ? (cl == F) : (inside != 0);
     if (emit) {
-      unsigned long long r = rec_base + ro++;
-      rec_key[r] = qbits | (hilbert_id(ccx, ccy, cl) << shift);
-      rec_val[r] = slot | ((F - cl) << 26);
+      if (gl == 0) {
+        unsigned long long r = rec_base + ro++;
+        rec_key[r] = qbits | (hilbert_id(ccx, ccy, cl) << shift);
+        rec_val[r] = slot | ((F - cl) << 26);
+      }
       cnt[c] = 0;  // a finest boundary cell needs no edge list
     } else if (cnt[c] > 0) {
       ceoff[c] = (uint32_t)eo;
-      next_items[io++] = Item{it.pair, ccx, ccy, (uint32_t)eo, cnt[c] | (inside << 31)};
+      if (gl == 0) next_items[io++] = Item{it.pair, ccx, ccy, (uint32_t)eo, cnt[c] | (inside << 31)};
       eo += cnt[c];
     }
   }
   if (n_it) {
     uint32_t fill[4] = {0, 0, 0, 0};
-    for (uint32_t i = 0; i < ecnt; ++i) {
-      const uint32_t eid = elist[it.eoff + i];
-      const uint32_t m = edge_vs_children(edges[eid], px, py, sh);
+    const uint32_t below = (1u << (lane - leader)) - 1u;
+    for (uint32_t base = 0, j = 0; base < ecnt; base += G, ++j) {
+      const uint32_t i = base + gl;
+      uint32_t m = 0, eid = 0;
+      if (i < ecnt) {
+        eid = elist[it.eoff + i];
+        m = j < 8 ? (mcache >> (4 * j)) & 15u : edge_vs_children(edges[eid], px, py, sh) & 15u;
+      }
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (cnt[c] > 0 && ((m >> c) & 1u)) next_elist[ceoff[c] + fill[c]++] = eid;
+      for (int c = 0; c < 4; ++c) {
+        if (cnt[c] == 0) continue;
+        const bool hit = (m >> c) & 1u;
+        const uint32_t bal = G > 1 ? ((__ballot_sync(gmask, hit) & gmask) >> leader) : (uint32_t)hit;
+        if (hit) next_elist[ceoff[c] + fill[c] + __popc(bal & below)] = eid;
+        fill[c] += __popc(bal);
+      }
     }
   }
 }
@@ -500,8 +539,10 @@ __device__ __forceinline__ uint32_t group_opens(const GroupCtx& c, uint32_t g, u
   return gap | (fresh << 1) | (tail << 2);
 }
 
+// ranges each group opens, and each query's first and last group (one writer
+// each, since groups are sorted by query: no contended counter)
 __global__ void group_count_kernel(GroupCtx c, uint32_t* __restrict__ nopen,
-                                   uint32_t* __restrict__ qcount, uint32_t* __restrict__ qfirst) {
+                                   uint32_t* __restrict__ qfirst, uint32_t* __restrict__ qlast) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= c.G) return;
   uint32_t q;
@@ -509,17 +550,21 @@ __global__ void group_count_kernel(GroupCtx c, uint32_t* __restrict__ nopen,
   bool first;
   const uint32_t o = group_opens(c, g, &q, &lo, &gl, &hi, &first);
   nopen[g] = __popc(o);
-  atomicAdd(&qcount[q], (uint32_t)__popc(o));
   if (first) qfirst[q] = g;
+  if (g + 1 == c.G || qof(c.sk[c.gfirst[g + 1]], c.qshift) != q) qlast[q] = g;
 }
 
-// entries of query q: its ranges plus the sentinel (a query without cells has
-// one empty range)
-__global__ void query_sizes_kernel(const uint32_t* __restrict__ qcount,
-                                   const uint32_t* __restrict__ qfirst, uint32_t Q,
+// entries of query q: the ranges its groups open plus the sentinel (a query
+// without cells has one empty range)
+__global__ void query_sizes_kernel(const uint32_t* __restrict__ qfirst,
+                                   const uint32_t* __restrict__ qlast,
+                                   const uint32_t* __restrict__ gscan,
+                                   const uint32_t* __restrict__ nopen, uint32_t Q,
                                    uint64_t* __restrict__ qsize) {
   uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < Q) qsize[q] = (qfirst[q] == NONE ? 1ull : (uint64_t)qcount[q]) + 1ull;
+  if (q >= Q) return;
+  const uint32_t a = qfirst[q], b = qlast[q];
+  qsize[q] = a == NONE ? 2ull : (uint64_t)(gscan[b] + nopen[b] - gscan[a]) + 1ull;
 }
 
 __global__ void group_emit_kernel(GroupCtx c, const uint32_t* __restrict__ gscan,
@@ -763,18 +808,17 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
     return merge_general(sk, sv, n, spec.q[0].F, P, s, out);
   }
   const uint32_t G = hG[0];
-  uint32_t *gfirst, *gsize, *nopen, *gscan, *qcount, *qfirst;
+  uint32_t *gfirst, *gsize, *nopen, *gscan, *qlast, *qfirst;
   uint64_t *qsize, *qoff, *dE;
   SDB_TRY(sc.get(&gfirst, G));
   SDB_TRY(sc.get(&gsize, G));
   SDB_TRY(sc.get(&nopen, G));
   SDB_TRY(sc.get(&gscan, G));
-  SDB_TRY(sc.get(&qcount, Q));
+  SDB_TRY(sc.get(&qlast, Q));
   SDB_TRY(sc.get(&qfirst, Q));
   SDB_TRY(sc.get(&qsize, Q));
   SDB_TRY(sc.get(&qoff, (size_t)Q + 1));
   SDB_TRY(sc.get(&dE, 1));
-  SDB_TRY_CUDA(cudaMemsetAsync(qcount, 0, (size_t)Q * 4, s));
   set_u32_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, Q, NONE);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
@@ -787,12 +831,12 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
     group_sort_kernel<<<grid_for(G, 256), 256, 0, s>>>(sv, gfirst, G, n, gsize);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
-    group_count_kernel<<<grid_for(G, 256), 256, 0, s>>>(gc, nopen, qcount, qfirst);
+    group_count_kernel<<<grid_for(G, 256), 256, 0, s>>>(gc, nopen, qfirst, qlast);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
   }
   SDB_TRY(exclusive_scan<uint32_t>(nopen, gscan, G, nullptr, s));
-  query_sizes_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qcount, qfirst, Q, qsize);
+  query_sizes_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, qlast, gscan, nopen, Q, qsize);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
   SDB_TRY(exclusive_scan<uint64_t>(qsize, qoff, Q, dE, s));
@@ -846,6 +890,35 @@ void CoverSet::release(cudaStream_t s) {
   list_off = nullptr;
   list_ids = nullptr;
   pay = nullptr;
+}
+
+static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items, const uint32_t* elist,
+                         const Edge* edges, const uint32_t* pq, const uint32_t* ps,
+                         const CoverQuery* qs, uint32_t qshift, uint32_t B, uint32_t L,
+                         Item* nitems, uint32_t* nel, uint64_t* rkey, uint32_t* rval,
+                         unsigned long long rec_base, unsigned long long* ctr, cudaStream_t s) {
+  const size_t threads = (size_t)n_items * G;
+#define SDB_EXPAND(g)                                                                          \
+  case g:                                                                                      \
+    expand_level_kernel<g><<<grid_for(threads, 256), 256, 0, s>>>(                             \
+        items, n_items, elist, edges, pq, ps, qs, qshift, B, L, nitems, nel, rkey, rval,        \
+        rec_base, ctr);                                                                        \
+    break;
+  switch (G) {
+    SDB_EXPAND(1)
+    SDB_EXPAND(2)
+    SDB_EXPAND(4)
+    SDB_EXPAND(8)
+    SDB_EXPAND(16)
+    SDB_EXPAND(32)
+    default:
+      set_error("expand: bad lane count %u", G);
+      return SDB_EINVAL;
+  }
+#undef SDB_EXPAND
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  return SDB_OK;
 }
 
 sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cudaStream_t s,
@@ -976,10 +1049,13 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
       }
     }
     SDB_TRY_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
-    expand_level_kernel<<<grid_for(n_items, 256), 256, 0, s>>>(
-        items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift, B, L, nitems, nel, rkey,
-        rval, n_rec, ctr);
-    note_launch();
+    // lanes per item: about the level's mean edge count, a power of two <= 32
+    const uint64_t mean = (n_edges + n_items - 1) / n_items;
+    uint32_t G = 1;
+    if (mean >= 4)
+      while (G < 32 && G < mean) G <<= 1;
+    SDB_TRY(launch_expand(G, items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift, B,
+                          L, nitems, nel, rkey, rval, n_rec, ctr, s));
     SDB_TRY_CUDA(cudaGetLastError());
     unsigned long long h[3];
     SDB_TRY(read_u64(ctr, h, 3, s));

@@ -92,20 +92,31 @@ constexpr int RS_ITEMS = 16;  // per lane
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 static_assert(RS_THREADS == 256, "one thread per digit in the scatter's digit scans");
 
+// Per-block digit histogram of one 8-bit digit.  A full tile is read with
+// 16-byte loads, all issued before any counting; counts go to per-warp
+// shared-memory histograms with shared atomics.
 __global__ __launch_bounds__(RS_THREADS) void radix_hist_kernel(const uint64_t* __restrict__ keys,
-                                                                size_t n, int shift,
-                                                                uint32_t* __restrict__ hist,
-                                                                uint32_t nblocks) {
+                                                               size_t n, int shift,
+                                                               uint32_t* __restrict__ hist,
+                                                               uint32_t nblocks) {
   __shared__ uint32_t h[RS_WARPS][256];
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&h[0][0])[i] = 0;
   __syncthreads();
-  size_t base = (size_t)blockIdx.x * RS_TILE + (size_t)w * (32 * RS_ITEMS);
-  for (int it = 0; it < RS_ITEMS; ++it) {
-    size_t g = base + (size_t)it * 32 + lane;
-    uint32_t d = g < n ? (uint32_t)((keys[g] >> shift) & 255u) : 256u;
-    unsigned peers = __match_any_sync(FULL, d);
-    if (d < 256u && lane == __ffs(peers) - 1) h[w][d] += __popc(peers);
+  const size_t tile0 = (size_t)blockIdx.x * RS_TILE;
+  if (tile0 + RS_TILE <= n && (reinterpret_cast<uintptr_t>(keys) & 15u) == 0) {
+    const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys + tile0);
+    ulonglong2 r[RS_ITEMS / 2];
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS / 2; ++it) r[it] = k2[it * RS_THREADS + threadIdx.x];
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS / 2; ++it) {
+      atomicAdd(&h[w][(uint32_t)(r[it].x >> shift) & 255u], 1u);
+      atomicAdd(&h[w][(uint32_t)(r[it].y >> shift) & 255u], 1u);
+    }
+  } else {
+    for (size_t g = tile0 + threadIdx.x; g < n; g += RS_THREADS)
+      atomicAdd(&h[w][(uint32_t)(keys[g] >> shift) & 255u], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
@@ -141,11 +152,16 @@ __global__ __launch_bounds__(RS_THREADS) void radix_scatter_kernel(
   uint32_t v[RS_ITEMS];
   uint32_t rank[RS_ITEMS];
 #pragma unroll
-  for (int it = 0; it < RS_ITEMS; ++it) {
+  for (int it = 0; it < RS_ITEMS; ++it) {  // all loads in flight before the ranking
     const size_t g = base + (size_t)it * 32 + lane;
     const bool ok = g < n;
     k[it] = ok ? kin[g] : 0ull;
     if (VALS) v[it] = ok ? vin[g] : 0u;
+  }
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    const size_t g = base + (size_t)it * 32 + lane;
+    const bool ok = g < n;
     const uint32_t d = ok ? (uint32_t)((k[it] >> shift) & 255u) : 256u;
     const unsigned peers = __match_any_sync(FULL, d);
     const uint32_t before = ok ? cnt[w][d] : 0u;
