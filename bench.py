@@ -8,7 +8,7 @@ eps sweep {2^12, 2^10, 2^8, 2^6}.
 
 One step = for every eps of the sweep: build the covering from the polygons
 (host arrays), fit the learned index (leaves for ~16 ranges each within
-2^12..2^16), and join all points with the learned lookup into per-polygon COUNT
+2^12..2^20), and join all points with the learned lookup into per-polygon COUNT
 and SUM (device-resident points).
 The metric counts point-joins: points x eps levels per second.
 
@@ -39,11 +39,11 @@ if ROOT not in sys.path:
 
 METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query latency"
 UNIT = "points/s"
-LEAF_BITS_RANGE = (12, 16)
+LEAF_BITS_RANGE = (12, 20)
 
 
 def leaf_bits_for(n_ranges: int) -> int:
-    """Leaves for about 16 ranges each, within 2^12..2^16."""
+    """Leaves for about 16 ranges each, within 2^12..2^20."""
     b = max(1, int(n_ranges) // 16).bit_length()
     return min(LEAF_BITS_RANGE[1], max(LEAF_BITS_RANGE[0], b))
 
@@ -222,7 +222,7 @@ def run_reference(args):
 def config_of(w, n_points):
     return {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64_learned",
             "points": n_points, "polygons": w.polygons.n, "grid_bits": 24, "eps": w.eps,
-            "leaf_bits": "ranges/16 within 2^12..2^16", "lookup": "learned",
+            "leaf_bits": "ranges/16 within 2^12..2^20", "lookup": "learned",
             "l2": "inputs larger than L2 (point arrays 12 B/pt)"}
 
 
@@ -252,6 +252,7 @@ def main():
     sm = torch.zeros((E, P), dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
     covs_live = []
+    cov_bytes = [0] * E
 
     def step(events=None):
         for i, eps in enumerate(w.eps):
@@ -259,6 +260,7 @@ def main():
                 events[i][0].record(stream)
             c = sdb.build_covering(w.polygons, 24, eps, stream)
             sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
+            cov_bytes[i] = c.info().device_bytes  # covering + index
             if events is not None:
                 events[i][1].record(stream)
             sdb.join_aggregate(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], sm[i], stream)
@@ -339,9 +341,10 @@ def main():
             c.free()
         res["join_only"] = joins
     # ---- roofline of the join kernel of the finest eps inside the timed steps
+    # algorithmic bytes: the point stream (x, y, attr) plus one read of the
+    # covering and its index
     fine = str(w.eps[-1])
-    cov_bytes = joins.get(fine, {}).get("covering_bytes", 0)
-    per_pt = 12 + (64 if cov_bytes > 64e6 else 0)
+    per_pt = 12 + cov_bytes[-1] / N
     jms = join_ms[-1]
     achieved = N * per_pt / (jms / 1e3) / 1e9
     res["roofline"] = {"kernel": "join_kernel<learned> eps=%s" % fine, "bound": "hbm",

@@ -21,6 +21,7 @@
 //    per query, or the persistent launch replayed as a captured CUDA graph.
 //  * An autotuner picks the tile size and points per thread by timing the
 //    candidates on the batch itself.
+#include "hilbert.cuh"
 #include "sdb_internal.cuh"
 
 #include <algorithm>
@@ -39,48 +40,19 @@ using QueryDev = BatchQueryDev;
 using ChunkDev = BatchChunkDev;
 using TileRec = BatchTile;
 
-__device__ __forceinline__ uint16_t lut_entry(uint32_t idx) {
-  uint32_t sw = (idx >> 9) & 1u, cm = (idx >> 8) & 1u;
-  uint32_t xn = (idx >> 4) & 15u, yn = idx & 15u, out = 0;
-#pragma unroll
-  for (int lev = 3; lev >= 0; --lev) {
-    uint32_t xb = (xn >> lev) & 1u, yb = (yn >> lev) & 1u;
-    uint32_t xt = (sw ? yb : xb) ^ cm, yt = (sw ? xb : yb) ^ cm;
-    out = (out << 2) | (xt << 1) | (xt ^ yt);
-    if (!yt) {
-      sw ^= 1u;
-      cm ^= xt;
-    }
-  }
-  return (uint16_t)(out | (((sw << 1) | cm) << 8));
-}
-
-__device__ __forceinline__ uint64_t encode_cell(uint32_t cx, uint32_t cy, uint32_t nsteps,
-                                                uint32_t st0, const uint16_t* lut) {
-  uint64_t h = 0;
-  uint32_t st = st0;
-  for (int s = (int)nsteps - 1; s >= 0; --s) {
-    uint32_t idx = (st << 8) | (((cx >> (4 * s)) & 15u) << 4) | ((cy >> (4 * s)) & 15u);
-    uint32_t e = lut[idx];
-    h = (h << 8) | (e & 255u);
-    st = e >> 8;
-  }
-  return h;
-}
-
 // ---------------------------------------------------------------- points
 __global__ void point_keys_kernel(const uint32_t* __restrict__ x, const uint32_t* __restrict__ y,
                                   uint64_t n, uint32_t B, uint32_t nsteps, uint32_t st0,
                                   uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
                                   unsigned int* __restrict__ bad) {
-  __shared__ uint16_t lut[1024];
-  for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) lut[i] = lut_entry(i);
+  __shared__ uint32_t tab[HILBERT3_SMEM_WORDS];
+  hilbert3_fill(tab);
   __syncthreads();
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t xi = x[i], yi = y[i];
     if (B < 32 && ((xi >> B) | (yi >> B))) *bad = 1u;
-    key[i] = encode_cell(xi, yi, nsteps, st0, lut);
+    key[i] = hilbert3_encode(xi, yi, nsteps, st0, tab);
     idx[i] = (uint32_t)i;
   }
 }
@@ -219,9 +191,9 @@ template <int G, bool SUM>
 __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t tile_lo,
                                                         uint32_t tile_hi,
                                                         unsigned long long* head) {
-  __shared__ uint16_t lut[1024];
+  __shared__ uint32_t tab[HILBERT3_SMEM_WORDS];
   __shared__ uint32_t s_tile;
-  for (uint32_t i = threadIdx.x; i < 1024; i += THREADS) lut[i] = lut_entry(i);
+  hilbert3_fill(tab);
   __syncthreads();
   for (;;) {
     if (threadIdx.x == 0) s_tile = tile_lo + (uint32_t)atomicAdd(head, 1ull);
@@ -243,7 +215,7 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
         const uint32_t x = ok[g] ? A.x[i] : 0u, y = ok[g] ? A.y[i] : 0u;
         av[g] = (SUM && ok[g]) ? A.attr[i] : 0;
         ok[g] = ok[g] && x >= Q.x0 && x < Q.x1 && y >= Q.y0 && y < Q.y1;
-        h[g] = ok[g] ? encode_cell(x >> Q.k, y >> Q.k, Q.nsteps, Q.st0, lut) : 0ull;
+        h[g] = ok[g] ? hilbert3_encode(x >> Q.k, y >> Q.k, Q.nsteps, Q.st0, tab) : 0ull;
       }
       // last entry r in [0, R) of the slice with start <= h (sentinel above)
       uint32_t lo[G];
@@ -355,8 +327,7 @@ sdb_status batch_query_dev(uint32_t B, const sdb_query& Qu, uint64_t out_off, Ba
   }
   memset(d, 0, sizeof(*d));
   d->k = k;
-  d->nsteps = (F + 3) / 4;
-  d->st0 = ((4 * d->nsteps - F) & 1u) ? 2u : 0u;
+  hilbert3_params(F, &d->nsteps, &d->st0);
   d->x0 = Qu.x0;
   d->y0 = Qu.y0;
   d->x1 = Qu.x1;
@@ -617,9 +588,10 @@ sdb_status sdb_points_create(const uint32_t* d_x, const uint32_t* d_y, const int
     if (st == SDB_OK) st = sc.get(&bad, 1);
     if (st == SDB_OK) st = status_of(cudaMemsetAsync(bad, 0, 4, s), "memset");
     if (st == SDB_OK) {
-      const uint32_t nsteps = (grid_bits + 3) / 4, pad = 4 * nsteps - grid_bits;
-      point_keys_kernel<<<num_sms() * 8, 256, 0, s>>>(d_x, d_y, n, grid_bits, nsteps,
-                                                      (pad & 1u) ? 2u : 0u, p->key, idx, bad);
+      uint32_t nsteps, st0;
+      hilbert3_params(grid_bits, &nsteps, &st0);
+      point_keys_kernel<<<num_sms() * 8, 256, 0, s>>>(d_x, d_y, n, grid_bits, nsteps, st0, p->key,
+                                                      idx, bad);
       note_launch();
       st = status_of(cudaGetLastError(), "point keys");
     }

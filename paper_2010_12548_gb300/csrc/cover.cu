@@ -65,19 +65,42 @@ __device__ __forceinline__ uint32_t pert_ray_cross(const Edge& e, int64_t qx, in
   return (e.by > e.ay) ? (sd > 0) : (sd < 0);
 }
 
-__device__ __forceinline__ unsigned long long warp_alloc(uint32_t n, unsigned long long* ctr) {
-  int lane = threadIdx.x & 31;
-  uint32_t inc = n;
+// Offsets for three per-thread counts, with one atomic per counter and block
+// (blockDim.x == 256): warp scans, then warp prefixes in shared memory.  Every
+// thread of the block must call it.
+__device__ __forceinline__ void block_alloc3(const uint32_t (&n)[3],
+                                             unsigned long long* __restrict__ ctr,
+                                             unsigned long long (&off)[3]) {
+  __shared__ uint32_t wsum[3][8];
+  __shared__ unsigned long long base[3];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc[3] = {n[0], n[1], n[2]};
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(FULL, inc, o);
-    if (lane >= o) inc += t;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const uint32_t t = __shfl_up_sync(FULL, inc[j], o);
+      if (lane >= o) inc[j] += t;
+    }
   }
-  uint32_t total = __shfl_sync(FULL, inc, 31);
-  unsigned long long base = 0;
-  if (lane == 31 && total) base = atomicAdd(ctr, (unsigned long long)total);
-  base = __shfl_sync(FULL, base, 31);
-  return base + inc - n;
+  if (lane == 31) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) wsum[j][w] = inc[j];
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    const int j = threadIdx.x;
+    uint32_t t = 0;
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t v = wsum[j][k];
+      wsum[j][k] = t;
+      t += v;
+    }
+    base[j] = t ? atomicAdd(&ctr[j], (unsigned long long)t) : 0ull;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 3; ++j) off[j] = base[j] + wsum[j][w] + inc[j] - n[j];
 }
 
 __global__ void build_edges_kernel(const uint32_t* __restrict__ ring_off,
@@ -258,9 +281,10 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
       }
     }
   }
-  unsigned long long ro = warp_alloc(n_rec, &counters[2]);
-  unsigned long long io = warp_alloc(n_it, &counters[0]);
-  unsigned long long eo = warp_alloc(n_ed, &counters[1]);
+  // counters: 0 child items, 1 child edge entries, 2 records
+  unsigned long long off[3];
+  block_alloc3({n_it, n_ed, n_rec}, counters, off);
+  unsigned long long io = off[0], eo = off[1], ro = off[2];
   if (!active) return;
   const uint32_t leader = lane & ~(uint32_t)(G - 1);
   if (G > 1) {

@@ -7,39 +7,24 @@
 //  * points are SoA uint32 x[], y[], int32 attr[]; each lane takes 4 consecutive
 //    points per step (one 16-byte load per array, streaming cache hint), a warp
 //    covers 128 consecutive points, all warps stride over the array;
-//  * the cell id is computed 4 levels at a time from a 1024-entry table in
-//    shared memory (each block builds it at start);
+//  * the cell id is computed 3 levels at a time from a 256-entry table that
+//    each block stores in shared memory once per bank (conflict-free lookups);
 //  * binary search: the top ~11 levels come from a sample of the range starts
 //    staged in shared memory, the rest from global memory with a fixed number
 //    of steps, the 4 points of a lane searched in lockstep so their loads
 //    overlap;
-//  * learned search: root model -> 32-byte leaf record -> FP32 prediction ->
-//    search inside the leaf's error window -> bracket verified, binary search
-//    as the fallback (counted);
-//  * aggregation: lanes holding the same polygon are grouped with a warp match,
-//    the group's count and (split 16/16-bit, exact) attribute sum are reduced
-//    in registers and added once by the group leader, into shared memory
-//    (P <= SMEM_POLYS, flushed once per block) or straight into global memory.
+//  * learned search: root model -> 32-byte leaf record (one load) -> FP32
+//    prediction -> search inside the leaf's error window -> bracket verified
+//    (only the ends no probe has proven are read), binary search as the
+//    fallback (counted);
+//  * aggregation: per point, its count and (split 16/16-bit, exact) attribute
+//    sum are added with shared-memory atomics to per-block accumulators
+//    (P <= SMEM_POLYS, flushed into the 64-bit outputs every few tiles), or
+//    with global atomics straight into the outputs.
+#include "hilbert.cuh"
 #include "sdb_internal.cuh"
 
 namespace sdb {
-
-void make_hilbert_lut(HilbertLut* t) {
-  for (uint32_t idx = 0; idx < 1024; ++idx) {
-    uint32_t sw = (idx >> 9) & 1u, cm = (idx >> 8) & 1u;
-    uint32_t xn = (idx >> 4) & 15u, yn = idx & 15u, out = 0;
-    for (int lev = 3; lev >= 0; --lev) {
-      uint32_t xb = (xn >> lev) & 1u, yb = (yn >> lev) & 1u;
-      uint32_t xt = (sw ? yb : xb) ^ cm, yt = (sw ? xb : yb) ^ cm;
-      out = (out << 2) | (xt << 1) | (xt ^ yt);
-      if (!yt) {
-        sw ^= 1u;
-        cm ^= xt;
-      }
-    }
-    t->e[idx] = (uint16_t)(out | (((sw << 1) | cm) << 8));
-  }
-}
 
 namespace {
 
@@ -73,39 +58,6 @@ struct JoinArgs {
   uint32_t nleaves;
   unsigned long long* fallbacks;
 };
-
-__device__ __forceinline__ uint16_t lut_entry(uint32_t idx) {
-  uint32_t sw = (idx >> 9) & 1u, cm = (idx >> 8) & 1u;
-  uint32_t xn = (idx >> 4) & 15u, yn = idx & 15u, out = 0;
-#pragma unroll
-  for (int lev = 3; lev >= 0; --lev) {
-    uint32_t xb = (xn >> lev) & 1u, yb = (yn >> lev) & 1u;
-    uint32_t xt = (sw ? yb : xb) ^ cm, yt = (sw ? xb : yb) ^ cm;
-    out = (out << 2) | (xt << 1) | (xt ^ yt);
-    if (!yt) {
-      sw ^= 1u;
-      cm ^= xt;
-    }
-  }
-  return (uint16_t)(out | (((sw << 1) | cm) << 8));
-}
-
-// Finest cell id of cell (cx, cy): nsteps table steps of 4 levels each, the
-// top step padded with zero levels; st0 cancels the padding's orientation
-// changes (each zero level transposes), so the result equals the plain
-// F-level id.
-__device__ __forceinline__ uint64_t encode_cell(uint32_t cx, uint32_t cy, uint32_t nsteps,
-                                                uint32_t st0, const uint16_t* lut) {
-  uint64_t h = 0;
-  uint32_t st = st0;
-  for (int s = (int)nsteps - 1; s >= 0; --s) {
-    uint32_t idx = (st << 8) | (((cx >> (4 * s)) & 15u) << 4) | ((cy >> (4 * s)) & 15u);
-    uint32_t e = lut[idx];
-    h = (h << 8) | (e & 255u);
-    st = e >> 8;
-  }
-  return h;
-}
 
 // last r in [0, R) with start[r] <= h, global memory only (fallback path)
 __device__ __noinline__ uint32_t bs_global(const uint64_t* __restrict__ start, uint64_t R,
@@ -161,16 +113,19 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
 #pragma unroll
   for (int q = 0; q < G; ++q) {
     const uint32_t l = root_leaf(s_knots, A.wshift, A.inv_w, A.nleaves, h[q]);
-    const uint4* p = reinterpret_cast<const uint4*>(A.leaves + l);
-    const uint4 u0 = __ldg(p), u1 = __ldg(p + 1);
+    // the 32-byte record in one load (records are 32-byte aligned)
+    uint64_t w0, w1, w2, w3;
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+        : "l"(A.leaves + l));
     LeafRec lr;
-    lr.base = (uint64_t)u0.x | ((uint64_t)u0.y << 32);
-    lr.a = __uint_as_float(u0.z);
-    lr.b = __uint_as_float(u0.w);
-    lr.first = u1.x;
-    lr.last = u1.y;
-    lr.errlo = (int32_t)u1.z;
-    lr.errhi = (int32_t)u1.w;
+    lr.base = w0;
+    lr.a = __uint_as_float((uint32_t)w1);
+    lr.b = __uint_as_float((uint32_t)(w1 >> 32));
+    lr.first = (uint32_t)w2;
+    lr.last = (uint32_t)(w2 >> 32);
+    lr.errlo = (int32_t)(uint32_t)w3;
+    lr.errhi = (int32_t)(uint32_t)(w3 >> 32);
     const int64_t pr = leaf_predict(lr, h[q]);
     int64_t a = pr - lr.errlo, b = pr + lr.errhi;
     if (a < (int64_t)lr.first) a = lr.first;
@@ -180,9 +135,14 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
     len[q] = (uint32_t)(b - a + 1);
     maxlen = max(maxlen, len[q]);
   }
-  // the same number of halving steps for the whole warp; finished lanes idle
+  // the same number of halving steps for the whole warp; finished lanes idle.
+  // A probe <= h proves start[lo] <= h for the final lo (bit 0), a probe > h
+  // proves start[lo + 1] > h (bit 1: the result is the window's last start <= h)
   maxlen = __reduce_max_sync(FULL, maxlen);
   const int steps = 32 - __clz(maxlen - 1);
+  uint32_t known[G];
+#pragma unroll
+  for (int q = 0; q < G; ++q) known[q] = 0;
   for (int st = 0; st < steps; ++st) {
     uint64_t v[G];
 #pragma unroll
@@ -192,15 +152,22 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
     for (int q = 0; q < G; ++q) {
       if (len[q] > 1) {
         const uint32_t half = len[q] >> 1;
-        if (v[q] <= h[q]) lo[q] += half;
+        if (v[q] <= h[q]) {
+          lo[q] += half;
+          known[q] |= 1u;
+        } else {
+          known[q] |= 2u;
+        }
         len[q] -= half;
       }
     }
   }
-  // judge: the result must bracket h; otherwise plain binary search decides
+  // judge: the result must bracket h (ends not proven by a probe are read);
+  // otherwise plain binary search decides
 #pragma unroll
   for (int q = 0; q < G; ++q) {
-    const uint64_t s0 = __ldg(A.start + lo[q]), s1 = __ldg(A.start + lo[q] + 1);
+    const uint64_t s0 = (known[q] & 1u) ? 0ull : __ldg(A.start + lo[q]);
+    const uint64_t s1 = (known[q] & 2u) ? ~0ull : __ldg(A.start + lo[q] + 1);
     if (s0 <= h[q] && h[q] < s1) {
       r[q] = (uint32_t)lo[q];
     } else {
@@ -259,21 +226,21 @@ __device__ void flush_acc(const Acc& s, const JoinArgs& A) {
 template <int LOOKUP, bool SMEM, bool SUM>
 __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // lookup staging: the binary search's sample of range starts, or the learned
-  // index's root knots
-  uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem);
-  float* s_knots = reinterpret_cast<float*>(smem);
-  size_t off = (LOOKUP == SDB_LOOKUP_BINARY) ? (size_t)A.sample_n * 8
-                                               : (((size_t)A.nknots * 4 + 7) & ~(size_t)7);
+  // the cell-id table, then the lookup staging (the binary search's sample of
+  // range starts, or the learned index's root knots), then the accumulators
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem + HILBERT3_SMEM_BYTES);
+  float* s_knots = reinterpret_cast<float*>(smem + HILBERT3_SMEM_BYTES);
+  size_t off = HILBERT3_SMEM_BYTES + ((LOOKUP == SDB_LOOKUP_BINARY)
+                                          ? (size_t)A.sample_n * 8
+                                          : (((size_t)A.nknots * 4 + 7) & ~(size_t)7));
   Acc acc;
   acc.cnt = reinterpret_cast<uint32_t*>(smem + off);
   off += SMEM ? (size_t)A.P * 4 : 0;
   acc.lo = reinterpret_cast<uint32_t*>(smem + off);
   acc.hi = reinterpret_cast<int32_t*>(smem + off + ((SMEM && SUM) ? (size_t)A.P * 4 : 0));
-  off += (SMEM && SUM) ? (size_t)A.P * 8 : 0;
-  uint16_t* s_lut = reinterpret_cast<uint16_t*>(smem + off);
 
-  for (uint32_t i = threadIdx.x; i < 1024; i += THREADS) s_lut[i] = lut_entry(i);
+  hilbert3_fill(s_tab);
   if (LOOKUP == SDB_LOOKUP_BINARY)
     for (uint32_t i = threadIdx.x; i < A.sample_n; i += THREADS) s_sample[i] = A.sample[i];
   else
@@ -323,7 +290,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       ok[q] = ok[q] && !((xs[q] | ys[q]) & gmask);
-      h[q] = ok[q] ? encode_cell(xs[q] >> A.k, ys[q] >> A.k, A.nsteps, A.st0, s_lut) : 0ull;
+      h[q] = ok[q] ? hilbert3_encode(xs[q] >> A.k, ys[q] >> A.k, A.nsteps, A.st0, s_tab) : 0ull;
     }
     uint32_t r[4];
     if (LOOKUP == SDB_LOOKUP_BINARY)
@@ -359,7 +326,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
 
 template <int LOOKUP, bool SMEM, bool SUM>
 sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
-  size_t smem = 2048;  // table
+  size_t smem = HILBERT3_SMEM_BYTES;
   if (SMEM) smem += (size_t)A.P * (SUM ? 12 : 4);
   if (LOOKUP == SDB_LOOKUP_BINARY)
     smem += (size_t)A.sample_n * 8;
@@ -411,9 +378,7 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.stride = cov->sample_stride;
   A.B = cov->B;
   A.k = cov->k;
-  A.nsteps = (cov->F + 3) / 4;
-  uint32_t pad = 4 * A.nsteps - cov->F;
-  A.st0 = (pad & 1u) ? 2u : 0u;  // swap bit set when the padding is odd
+  hilbert3_params(cov->F, &A.nsteps, &A.st0);
   A.P = cov->P;
   A.leaves = cov->leaves;
   A.knots = cov->knots;

@@ -16,7 +16,9 @@
 // [base_l, base_{l+1}), where base_l is the smallest id the root sends to a
 // leaf >= l; it is found by binary search on the root function itself, with the
 // same instructions the lookup uses, so routing at fit time and lookup time
-// agree bit for bit.  The leaf line is a least-squares fit of the range index
+// agree bit for bit.  By monotonicity start_i < base_l exactly when the root
+// sends start_i to a leaf below l, so one pass over the ranges counts the
+// starts below every leaf's base, which fixes each leaf's first and last range.  The leaf line is a least-squares fit of the range index
 // (relative to the leaf's first range) on the leaf-relative id.  Its error
 // window covers, for every range i the leaf can see, every id of
 // [start_i, start_{i+1}) that the leaf receives: by monotonicity it is enough to
@@ -29,18 +31,6 @@ namespace sdb {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-__device__ __forceinline__ uint64_t upper_bound_idx(const uint64_t* __restrict__ start, uint64_t R,
-                                                    uint64_t h) {
-  // last r in [0, R) with start[r] <= h (start[0] = 0 <= h < start[R])
-  uint64_t lo = 0, len = R + 1;
-  while (len > 1) {
-    uint64_t half = len >> 1;
-    if (start[lo + half] <= h) lo += half;
-    len -= half;
-  }
-  return lo;
-}
-
 // knot j: L * (number of range starts below j << wshift) / R
 __global__ void knots_kernel(const uint64_t* __restrict__ start, uint64_t R, uint32_t K,
                              uint32_t wshift, uint32_t L, float* __restrict__ knot) {
@@ -84,7 +74,7 @@ __global__ void leaf_base_kernel(const float* __restrict__ knot, uint32_t wshift
   base[l] = lo;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
@@ -99,14 +89,32 @@ __device__ __forceinline__ long long warp_max(long long v) {
   return v;
 }
 
-// one warp per leaf: range span, centred least squares, error window
+// below[l] = #{i < R : start_i < base_l} for l in [0, L].  Range i's start
+// goes to leaf lam_i; the leaves lam_{i-1} < l <= lam_i have exactly i starts
+// below their base (lam_{-1} = -1, and start_R = 4^F stands for leaf L).
+__global__ void leaf_below_kernel(const uint64_t* __restrict__ start, uint64_t R,
+                                  const float* __restrict__ knot, uint32_t wshift, float inv_w,
+                                  uint32_t L, uint32_t* __restrict__ below) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > R) return;
+  const uint32_t lam = i < R ? root_leaf(knot, wshift, inv_w, L, start[i]) : L;
+  const uint32_t from = i == 0 ? 0u : root_leaf(knot, wshift, inv_w, L, start[i - 1]) + 1u;
+  for (uint32_t l = from; l <= lam; ++l) below[l] = (uint32_t)i;
+}
+
+// one warp per leaf: centred least squares (FP32), error window
 __global__ void leaf_fit_kernel(const uint64_t* __restrict__ start, uint64_t R,
-                                const uint64_t* __restrict__ base, uint32_t L,
+                                const uint64_t* __restrict__ base,
+                                const uint32_t* __restrict__ below, uint32_t L,
                                 LeafRec* __restrict__ leaves) {
   uint32_t l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (l >= L) return;
   const uint64_t b0 = base[l], b1 = base[l + 1];
+  // range holding b0: the last start <= b0 (b0 < 4^F = start[R] for l < L)
+  const uint32_t c0 = below[l];
+  uint64_t first = (c0 < R && start[c0] == b0) ? c0 : (uint64_t)c0 - 1;
+  first = first < R ? first : R - 1;
   LeafRec lr;
   lr.base = b0;
   lr.a = 0.f;
@@ -114,39 +122,37 @@ __global__ void leaf_fit_kernel(const uint64_t* __restrict__ start, uint64_t R,
   lr.errlo = 0;
   lr.errhi = 0;
   if (b0 >= b1) {  // no id is routed here
-    uint64_t f = b0 < start[R] ? upper_bound_idx(start, R, b0) : R - 1;
-    lr.first = lr.last = (uint32_t)f;
+    lr.first = lr.last = (uint32_t)first;
     if (lane == 0) leaves[l] = lr;
     return;
   }
-  const uint64_t first = upper_bound_idx(start, R, b0);
-  const uint64_t last = upper_bound_idx(start, R, b1 - 1);
+  uint64_t last = (uint64_t)below[l + 1] - 1;  // range holding b1 - 1
+  last = last < first ? first : (last < R ? last : R - 1);
   lr.first = (uint32_t)first;
   lr.last = (uint32_t)last;
   const uint64_t n = last - first + 1;
-  // pass 1: means
-  double sx = 0, sy = 0;
+  // pass 1: means; pass 2: centred moments (FP32: the fit only shapes the
+  // windows, which come from the lookup's own arithmetic in pass 3)
+  float sx = 0.f, sy = 0.f;
   for (uint64_t i = first + lane; i <= last; i += 32) {
-    uint64_t s = start[i] > b0 ? start[i] : b0;
-    sx += (double)(s - b0);
-    sy += (double)(i - first);
+    const uint64_t s = start[i] > b0 ? start[i] : b0;
+    sx += __ull2float_rn(s - b0);
+    sy += (float)(i - first);
   }
-  sx = warp_sum(sx);
-  sy = warp_sum(sy);
-  const double mx = sx / (double)n, my = sy / (double)n;
-  // pass 2: centred moments
-  double sxx = 0, sxy = 0;
+  const float inv_n = 1.0f / (float)n;
+  const float mx = warp_sum(sx) * inv_n, my = warp_sum(sy) * inv_n;
+  float sxx = 0.f, sxy = 0.f;
   for (uint64_t i = first + lane; i <= last; i += 32) {
-    uint64_t s = start[i] > b0 ? start[i] : b0;
-    double dx = (double)(s - b0) - mx, dy = (double)(i - first) - my;
-    sxx += dx * dx;
-    sxy += dx * dy;
+    const uint64_t s = start[i] > b0 ? start[i] : b0;
+    const float dx = __ull2float_rn(s - b0) - mx, dy = (float)(i - first) - my;
+    sxx = fmaf(dx, dx, sxx);
+    sxy = fmaf(dx, dy, sxy);
   }
   sxx = warp_sum(sxx);
   sxy = warp_sum(sxy);
-  double slope = (sxx > 0 && sxy > 0) ? sxy / sxx : 0.0;
-  lr.a = (float)slope;
-  lr.b = (float)(my - slope * mx);
+  const float slope = (sxx > 0.f && sxy > 0.f) ? sxy / sxx : 0.f;
+  lr.a = slope;
+  lr.b = my - slope * mx;
   // pass 3: error window with the lookup's own FP32 arithmetic
   long long ehi = 0, elo = 0;
   for (uint64_t i = first + lane; i <= last; i += 32) {
@@ -182,6 +188,10 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
   cov->leaves = nullptr;
   cov->knots = nullptr;
   SDB_TRY(dalloc_n(&cov->leaves, L, s));
+  if (reinterpret_cast<uintptr_t>(cov->leaves) & 31u) {  // the lookup reads 32 bytes at once
+    set_error("learned index: leaf records not 32-byte aligned");
+    return SDB_ECUDA;
+  }
   SDB_TRY(dalloc_n(&cov->knots, (size_t)K + 1, s));
   if (!cov->fallbacks) {
     SDB_TRY(dalloc_n(&cov->fallbacks, 1, s));
@@ -191,12 +201,18 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
   uint64_t* base;
+  uint32_t* below;
   SDB_TRY(sc.get(&base, (size_t)L + 1));
+  SDB_TRY(sc.get(&below, (size_t)L + 1));
   leaf_base_kernel<<<grid_for((size_t)L + 1, 256), 256, 0, s>>>(cov->knots, wshift, inv_w, L, top,
                                                                  base);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  leaf_fit_kernel<<<grid_for((size_t)L * 32, 256), 256, 0, s>>>(cov->start, R, base, L,
+  leaf_below_kernel<<<grid_for((size_t)R + 1, 256), 256, 0, s>>>(cov->start, R, cov->knots, wshift,
+                                                                   inv_w, L, below);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  leaf_fit_kernel<<<grid_for((size_t)L * 32, 256), 256, 0, s>>>(cov->start, R, base, below, L,
                                                                   cov->leaves);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());

@@ -100,13 +100,6 @@ __host__ __device__ inline uint64_t hilbert_id(uint32_t x, uint32_t y, uint32_t 
   return d;
 }
 
-// Four levels per step: entry [state*256 + xnib*16 + ynib] = 8 digit bits in
-// bits 0..7 (first level highest) and the next state (sw*2 + cm) in bits 8..9.
-struct HilbertLut {
-  uint16_t e[1024];
-};
-void make_hilbert_lut(HilbertLut* t);
-
 // ---------------------------------------------------------------- covering
 // One leaf of the learned range index, 32 bytes (one DRAM sector).  The leaf
 // receives the ids h in [base, next leaf's base); its ranges are first..last.
@@ -119,6 +112,7 @@ struct LeafRec {
   uint32_t first, last;
   int32_t errlo, errhi;
 };
+static_assert(sizeof(LeafRec) == 32, "leaf records are read as one 32-byte load");
 
 __device__ __forceinline__ int64_t leaf_predict(const LeafRec& l, uint64_t h) {
   const float x = __ull2float_rn(h - l.base);
@@ -139,7 +133,10 @@ __device__ __forceinline__ uint32_t root_leaf(const float* knot, uint32_t wshift
   const uint32_t j = (uint32_t)(h >> wshift);
   const uint64_t rem = h - ((uint64_t)j << wshift);
   const float k0 = knot[j], k1 = knot[j + 1];
-  const float pos = __fmaf_rn(k1 - k0, __fmul_rn(__ull2float_rn(rem), inv_w), k0);
+  // k0 <= pos <= k1 by construction (the min guards one-ulp overshoot of the
+  // rounded slope), so the map is monotone across knots as well
+  const float pos =
+      fminf(__fmaf_rn(k1 - k0, __fmul_rn(__ull2float_rn(rem), inv_w), k0), k1);
   int v = __float2int_rd(pos);
   v = v < 0 ? 0 : v;
   return (uint32_t)v >= nleaves ? nleaves - 1 : (uint32_t)v;
