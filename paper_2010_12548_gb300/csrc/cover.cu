@@ -38,9 +38,17 @@ struct Edge {
   int32_t ax, ay, bx, by;
 };
 
-struct Item {
-  uint32_t pair, cx, cy, eoff, ecnt_par;  // ecnt_par: edge count | parity << 31
+// A frontier cell of one (query, polygon) pair at level L: cell (cx, cy), its
+// Hilbert id at level L and the curve's orientation (sw << 1 | cm) below it,
+// so a child's id is one more digit; its edge list elist[eoff, eoff + ecnt)
+// and the perturbed parity of its lower-left corner.
+struct __align__(16) Item {
+  uint64_t hid;
+  uint32_t pair, cx, cy, eoff;
+  uint32_t ecnt_par;  // edge count | parity << 31
+  uint32_t orient;
 };
+static_assert(sizeof(Item) == 32, "two 16-byte loads per item");
 
 __device__ __forceinline__ uint64_t qof(uint64_t key, uint32_t qshift) {
   return qshift >= 64 ? 0ull : key >> qshift;
@@ -145,60 +153,68 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
   par = __popc(__ballot_sync(FULL, par)) & 1u;
   if (lane == 0) {
     unsigned long long i = atomicAdd(&counters[0], 1ull);
-    items[i] = Item{p, 0, 0, a, (b - a) | (par << 31)};
+    items[i] = Item{0ull, p, 0, 0, a, (b - a) | (par << 31), 0u};
   }
 }
 
 // One edge against the 2x2 children of a parent square with lower-left corner
-// (px, py) and child side 2^sh.  The line function f(p) = cross(b - a, p - a)
-// is linear, so its values on the 3x3 lattice of child corners follow from one
-// evaluation and shifted steps: f(px + u*side, py + v*side) = f00 + u*stepx +
-// v*stepy.  Bits 0..3 of the result: the closed edge meets closed child c
+// (px, py) and child side 2^sh (grid bits <= 30, so corners and edge ends fit
+// in int32 and the line function below in int64).  The line function
+// f(p) = cross(b - a, p - a) is linear, so its values on the 3x3 lattice of
+// child corners follow from one evaluation and shifted steps:
+// f(px + u*side, py + v*side) = f00 + u*stepx + v*stepy.  Only their strict
+// signs are kept, as 9-bit masks (bit u + 3v).
+// Bits 0..3 of the result: the closed edge meets closed child c
 // (c = dy*2 + dx); separating axes: the bounding boxes, and the edge's line
-// (f takes both signs, or zero, over the child's corners; its extremes sit at
-// the corners picked by the signs of the steps).  Bits 5..7: parity flips from
-// the parent's corner to the corner of child 1 (via the rightward ray along the
-// bottom row), child 2
-// (upward ray along the left column) and child 3 (child 1's corner plus the
-// upward ray along the middle column), all for corners shifted by (d, d^2);
-// a segment's crossing parity is the XOR of the two rays that contain it.
-__device__ __forceinline__ uint32_t edge_vs_children(const Edge& e, int64_t px, int64_t py,
+// (f is not of one strict sign over the child's four corners).
+// Bits 5..7: parity flips from the parent's corner to the corner of child 1
+// (rightward ray along the bottom row), child 2 (upward ray along the left
+// column) and child 3 (child 1's corner plus the upward ray along the middle
+// column), all for corners shifted by (d, d^2).  A ray from q+ crosses the
+// edge iff the edge straddles the ray's line and the perturbed sign of f at
+// q+ has the side that faces the edge, so the crossing parity of the segment
+// between two lattice points is the XOR of their perturbed signs, taken when
+// the edge straddles the segment's line.
+__device__ __forceinline__ uint32_t edge_vs_children(const Edge& e, int32_t px, int32_t py,
                                                      uint32_t sh) {
-  const int64_t side = (int64_t)1 << sh;
+  const int32_t side = 1 << sh;
   const int64_t dx = (int64_t)e.bx - e.ax, dy = (int64_t)e.by - e.ay;  // (edge direction)
-  const int64_t f00 = dx * (py - e.ay) - dy * (px - e.ax);
+  const int64_t f00 = dx * ((int64_t)py - e.ay) - dy * ((int64_t)px - e.ax);
   const int64_t stepx = -(dy << sh), stepy = dx << sh;
+  uint32_t pos = 0, neg = 0;
+  int64_t row = f00;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    int64_t f = row;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      pos |= (uint32_t)(f > 0) << (u + 3 * v);
+      neg |= (uint32_t)(f < 0) << (u + 3 * v);
+      f += stepx;
+    }
+    row += stepy;
+  }
   const int32_t minx = min(e.ax, e.bx), maxx = max(e.ax, e.bx);
   const int32_t miny = min(e.ay, e.by), maxy = max(e.ay, e.by);
   uint32_t out = 0;
-  const int64_t ux = stepx >= 0 ? 1 : 0, uy = stepy >= 0 ? 1 : 0;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const int64_t cu = c & 1, cv = c >> 1;
-    const int64_t x0 = px + cu * side, y0 = py + cv * side;
-    const bool box = !(maxx < x0 || minx > x0 + side || maxy < y0 || miny > y0 + side);
-    const int64_t fmax = f00 + (cu + ux) * stepx + (cv + uy) * stepy;
-    const int64_t fmin = f00 + (cu + 1 - ux) * stepx + (cv + 1 - uy) * stepy;
-    out |= (uint32_t)(box && fmax >= 0 && fmin <= 0) << c;
+    const int cu = c & 1, cv = c >> 1;
+    const int32_t x0 = px + cu * side, y0 = py + cv * side;
+    const bool box = !(maxx < x0 || minx - side > x0 || maxy < y0 || miny - side > y0);
+    const uint32_t corners = 0x1bu << (cu + 3 * cv);  // (u,v), (u+1,v), (u,v+1), (u+1,v+1)
+    out |= (uint32_t)(box && (corners & ~pos) && (corners & ~neg)) << c;
   }
   if (dx == 0 && dy == 0) return out;
-  // perturbed sign of f at lattice point (u, v): f, else -dy, else dx
-  const int tie = dy != 0 ? (dy < 0 ? 1 : -1) : (dx > 0 ? 1 : -1);
-  auto sg = [&](int64_t f) { return f != 0 ? (f > 0 ? 1 : -1) : tie; };
-  const int s00 = sg(f00), s10 = sg(f00 + stepx), s01 = sg(f00 + stepy),
-            s11 = sg(f00 + stepx + stepy);
-  // rightward ray from (u, 0)+: the edge straddles y = py + d^2 and lies to its right
-  uint32_t flip1 = 0, flip2 = 0, flipm = 0;
-  if ((e.ay > py) != (e.by > py)) {
-    const bool up = e.by > e.ay;
-    flip1 = (up ? s00 > 0 : s00 < 0) ^ (up ? s10 > 0 : s10 < 0);
-  }
-  // upward ray from (0, v)+ / (1, v)+: the edge straddles x = px (+ side) + d
-  // and lies above the point
-  const bool right = e.bx > e.ax;
-  if ((e.ax > px) != (e.bx > px)) flip2 = (right ? s00 < 0 : s00 > 0) ^ (right ? s01 < 0 : s01 > 0);
-  if ((e.ax > px + side) != (e.bx > px + side))
-    flipm = (right ? s10 < 0 : s10 > 0) ^ (right ? s11 < 0 : s11 > 0);
+  // perturbed sign at lattice point (u, v): that of f, else of -dy, else of dx
+  const bool tie_pos = dy != 0 ? dy < 0 : dx > 0;
+  const uint32_t ppos = pos | (tie_pos ? (~(pos | neg) & 0x1ffu) : 0u);
+  const uint32_t p00 = ppos & 1u, p10 = (ppos >> 1) & 1u, p01 = (ppos >> 3) & 1u,
+                 p11 = (ppos >> 4) & 1u;
+  // rightward ray along y = py + d^2; upward rays along x = px + d, px + side + d
+  const uint32_t flip1 = ((e.ay > py) != (e.by > py)) ? (p00 ^ p10) : 0u;
+  const uint32_t flip2 = ((e.ax > px) != (e.bx > px)) ? (p00 ^ p01) : 0u;
+  const uint32_t flipm = ((e.ax > px + side) != (e.bx > px + side)) ? (p10 ^ p11) : 0u;
   return out | (flip1 << 5) | (flip2 << 6) | ((flip1 ^ flipm) << 7);
 }
 
@@ -223,7 +239,7 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   const uint32_t gl = (uint32_t)(gt % G); // lane within the group
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t gmask = G == 32 ? FULL : (((1u << G) - 1u) << (lane & ~(uint32_t)(G - 1)));
-  Item it{0, 0, 0, 0, 0};
+  Item it{0ull, 0, 0, 0, 0, 0, 0};
   if (active) it = items[t];
   const uint32_t qi = active ? pair_query[it.pair] : 0u;
   CoverQuery Q{0, 0, 0, 0, 0};
@@ -233,6 +249,7 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   const uint32_t sh = B - cl;
   const int64_t side = (int64_t)1 << sh;
   const int64_t px = (int64_t)it.cx << (B - L), py = (int64_t)it.cy << (B - L);
+  const int32_t px32 = (int32_t)px, py32 = (int32_t)py;  // < 2^30
   // children holding lattice points of the query's box [x0, x1) x [y0, y1)
   uint32_t keep = 0;
 #pragma unroll
@@ -249,7 +266,7 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   uint32_t flip = 0;   // bit c: parity flip from the parent's corner to child c's
   uint32_t mcache = 0; // meet bits of this lane's edges in chunks 0..7
   for (uint32_t i = gl, j = 0; i < ecnt; i += G, ++j) {
-    const uint32_t m = edge_vs_children(edges[elist[it.eoff + i]], px, py, sh);
+    const uint32_t m = edge_vs_children(edges[elist[it.eoff + i]], px32, py32, sh);
 #pragma unroll
     for (int c = 0; c < 4; ++c) cnt[c] += (m >> c) & 1u;
     flip ^= m >> 4;
@@ -301,19 +318,27 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
       cnt[c] = 0;  // dropped: no record, no child item, no edge list
       continue;
     }
-    uint32_t ccx = 2 * it.cx + (c & 1), ccy = 2 * it.cy + (c >> 1);
+    const uint32_t ccx = 2 * it.cx + (c & 1), ccy = 2 * it.cy + (c >> 1);
+    // child's digit and orientation under the parent's orientation (sw, cm)
+    const uint32_t sw = it.orient >> 1, cm = it.orient & 1u;
+    const uint32_t xt = (sw ? (uint32_t)(c >> 1) : (uint32_t)(c & 1)) ^ cm;
+    const uint32_t yt = (sw ? (uint32_t)(c & 1) : (uint32_t)(c >> 1)) ^ cm;
+    const uint64_t chid = (it.hid << 2) | ((xt << 1) | (xt ^ yt));
+    const uint32_t corient = yt ? it.orient : (it.orient ^ 2u ^ xt);
     uint32_t inside = (par ^ (flip >> c)) & 1u;
     bool emit = (cnt[c] > 0) ? (cl == F) : (inside != 0);
     if (emit) {
       if (gl == 0) {
         unsigned long long r = rec_base + ro++;
-        rec_key[r] = qbits | (hilbert_id(ccx, ccy, cl) << shift);
+        rec_key[r] = qbits | (chid << shift);
         rec_val[r] = slot | ((F - cl) << 26);
       }
       cnt[c] = 0;  // a finest boundary cell needs no edge list
     } else if (cnt[c] > 0) {
       ceoff[c] = (uint32_t)eo;
-      if (gl == 0) next_items[io++] = Item{it.pair, ccx, ccy, (uint32_t)eo, cnt[c] | (inside << 31)};
+      if (gl == 0)
+        next_items[io++] =
+            Item{chid, it.pair, ccx, ccy, (uint32_t)eo, cnt[c] | (inside << 31), corient};
       eo += cnt[c];
     }
   }
@@ -325,7 +350,7 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
       uint32_t m = 0, eid = 0;
       if (i < ecnt) {
         eid = elist[it.eoff + i];
-        m = j < 8 ? (mcache >> (4 * j)) & 15u : edge_vs_children(edges[eid], px, py, sh) & 15u;
+        m = j < 8 ? (mcache >> (4 * j)) & 15u : edge_vs_children(edges[eid], px32, py32, sh) & 15u;
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
