@@ -132,7 +132,7 @@ __global__ __launch_bounds__(RS_THREADS) void radix_hist_kernel(const uint64_t* 
 // write consecutive slots of the same digit's output run (coalesced), starting
 // at the block's global offset for that digit.
 template <bool VALS>
-__global__ __launch_bounds__(RS_THREADS) void radix_scatter_kernel(
+__global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ offs,
     uint32_t nblocks) {
@@ -148,15 +148,14 @@ __global__ __launch_bounds__(RS_THREADS) void radix_scatter_kernel(
   const size_t tile0 = (size_t)blockIdx.x * RS_TILE;
   const size_t base = tile0 + (size_t)w * (32 * RS_ITEMS);
   const unsigned lt = (1u << lane) - 1u;
+  // keys stay in registers through the ranking; values are read only when
+  // the tile's layout is known (fewer live registers, more resident warps)
   uint64_t k[RS_ITEMS];
-  uint32_t v[RS_ITEMS];
   uint32_t rank[RS_ITEMS];
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {  // all loads in flight before the ranking
     const size_t g = base + (size_t)it * 32 + lane;
-    const bool ok = g < n;
-    k[it] = ok ? kin[g] : 0ull;
-    if (VALS) v[it] = ok ? vin[g] : 0u;
+    k[it] = g < n ? kin[g] : 0ull;
   }
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
@@ -198,16 +197,26 @@ __global__ __launch_bounds__(RS_THREADS) void radix_scatter_kernel(
     dstart[threadIdx.x] = wpre + inc - total;
   }
   __syncthreads();
-  // stable layout of the tile by digit in shared memory
+  // stable layout of the tile by digit in shared memory (rank becomes the slot)
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
     const size_t g = base + (size_t)it * 32 + lane;
     if (g < n) {
       const uint32_t d = (uint32_t)((k[it] >> shift) & 255u);
-      const uint32_t slot = dstart[d] + cnt[w][d] + rank[it];
-      sk[slot] = k[it];
-      if (VALS) sv[slot] = v[it];
+      rank[it] += dstart[d] + cnt[w][d];
+      sk[rank[it]] = k[it];
     }
+  }
+  if (VALS) {
+    uint32_t v[RS_ITEMS];
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+      const size_t g = base + (size_t)it * 32 + lane;
+      v[it] = g < n ? vin[g] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it)
+      if (base + (size_t)it * 32 + lane < n) sv[rank[it]] = v[it];
   }
   __syncthreads();
   const uint32_t tile_n = (uint32_t)min((size_t)RS_TILE, n - tile0);
