@@ -40,6 +40,10 @@ if ROOT not in sys.path:
 METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query latency"
 UNIT = "points/s"
 LEAF_BITS_RANGE = (12, 20)
+# DRAM bytes (read + write) of one join_kernel<learned> launch at eps = 2^6 on
+# the default workload (100M points, 2^20 leaves), from one ncu capture of this
+# script's step: profiles/join_kernel_learned_eps64_zones263_mobility100M.txt
+JOIN_FINEST_TRAFFIC = {"points": 100_000_000, "eps": 64, "leaf_bits": 20, "bytes": 1.74864e9}
 
 
 def leaf_bits_for(n_ranges: int) -> int:
@@ -253,14 +257,18 @@ def main():
     stream = torch.cuda.current_stream()
     covs_live = []
     cov_bytes = [0] * E
+    fine_leaf_bits = [0]
 
     def step(events=None):
         for i, eps in enumerate(w.eps):
             if events is not None:
                 events[i][0].record(stream)
             c = sdb.build_covering(w.polygons, 24, eps, stream)
-            sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
+            lb = leaf_bits_for(c.info().n_ranges)
+            sdb.covering_build_index(c, lb, stream)
             cov_bytes[i] = c.info().device_bytes  # covering + index
+            if i == E - 1:
+                fine_leaf_bits[0] = lb
             if events is not None:
                 events[i][1].record(stream)
             sdb.join_aggregate(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], sm[i], stream)
@@ -347,10 +355,14 @@ def main():
     per_pt = 12 + cov_bytes[-1] / N
     jms = join_ms[-1]
     achieved = N * per_pt / (jms / 1e3) / 1e9
+    T = JOIN_FINEST_TRAFFIC
+    traffic = (T["bytes"] if (N == T["points"] and w.eps[-1] == T["eps"]
+                              and fine_leaf_bits[0] == T["leaf_bits"]) else None)
     res["roofline"] = {"kernel": "join_kernel<learned> eps=%s" % fine, "bound": "hbm",
                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                       "peak_kind": peak_kind, "traffic": None,
-                       "algorithmic_bytes_per_point": per_pt}
+                       "peak_kind": peak_kind, "traffic": traffic,
+                       "algorithmic_bytes_per_point": per_pt,
+                       "algorithmic_bytes_per_launch": per_pt * N}
     # ---- end to end through the host-buffer entry point
     if "e2e" in legs:
         hx = torch.from_numpy(w.points.x.view(np.int32)).pin_memory()
