@@ -52,13 +52,14 @@ def lib():
         L.orc_finest_k.restype = I32
         L.orc_curve_many.argtypes = [I32, U32, U64, P, P, P]
         L.orc_classify_many.argtypes = [P, P, P, U32, U64, P, P, I64, P]
-        L.orc_cover.argtypes = [U32, P, P, P, U32, U64, I32]
+        L.orc_cover.argtypes = [U32, P, P, P, U32, U64, I32, I32]
         L.orc_cover.restype = P
         L.orc_cover_sizes.argtypes = [P, P, P, P, P, P]
         L.orc_cover_export.argtypes = [P, P, P, P]
         L.orc_cover_free.argtypes = [P]
-        L.orc_join_o1.argtypes = [P, U64, P, P, P, P, P, I32]
-        L.orc_join_o2.argtypes = [U32, P, P, P, U32, U64, U64, P, P, P, P, P, P, P, I64, I32]
+        L.orc_join_o1.argtypes = [P, U64, P, P, P, P, P, P, P, P, I32]
+        L.orc_join_o2.argtypes = [U32, P, P, P, U32, U64, U64, P, P, P, P, P, P, P, P, P, I64,
+                                  I32]
         L.orc_join_o2.restype = I32
         L.orc_join_exact.argtypes = [U32, P, P, P, U32, U64, P, P, P, P, P, P, I64, I32]
         L.orc_near_boundary.argtypes = [P, P, P, U32, U32, U32, U64]
@@ -111,6 +112,7 @@ class Covering:
     grid_bits: int
     n_polygons: int
     which: int
+    flagged: bool = False
     _h: int = 0
 
     @property
@@ -134,15 +136,28 @@ class Covering:
         a = None if attr is None else np.ascontiguousarray(attr, np.int32)
         cnt = np.zeros(self.n_polygons, np.uint64)
         sm = np.zeros(self.n_polygons, np.int64)
-        lib().orc_join_o1(self._h, len(x), _p(x), _p(y), _p(a), _p(cnt), _p(sm), self.which)
+        lib().orc_join_o1(self._h, len(x), _p(x), _p(y), _p(a), _p(cnt), _p(sm), None, None,
+                          None, self.which)
         return cnt, sm
 
+    def join_range(self, x, y, attr=None):
+        """O1 on a flagged covering (Sec. 6): (count, sum, bcount, bsum, babs)."""
+        x, y = _u32(x), _u32(y)
+        a = None if attr is None else np.ascontiguousarray(attr, np.int32)
+        P = self.n_polygons
+        out = [np.zeros(P, np.uint64), np.zeros(P, np.int64), np.zeros(P, np.uint64),
+               np.zeros(P, np.int64), np.zeros(P, np.uint64)]
+        lib().orc_join_o1(self._h, len(x), _p(x), _p(y), _p(a), *[_p(o) for o in out], self.which)
+        return tuple(out)
 
-def cover(polys, eps: int, which: int = HILBERT, grid_bits: int | None = None) -> Covering:
-    """O1: recursive quadtree covering of every polygon, swept into canonical ranges."""
+
+def cover(polys, eps: int, which: int = HILBERT, grid_bits: int | None = None,
+          flagged: bool = False) -> Covering:
+    """O1: recursive quadtree covering of every polygon, swept into canonical ranges
+    (flagged: list entries carry bit 31 on boundary cells, Sec. 6)."""
     B = polys.grid_bits if grid_bits is None else grid_bits
     off, vx, vy = _u32(polys.ring_off), _u32(polys.x), _u32(polys.y)
-    h = lib().orc_cover(len(off) - 1, _p(off), _p(vx), _p(vy), B, int(eps), which)
+    h = lib().orc_cover(len(off) - 1, _p(off), _p(vx), _p(vy), B, int(eps), which, int(flagged))
     if not h:
         raise ValueError("invalid covering arguments")
     R, nids, nrec = C.c_uint64(), C.c_uint64(), C.c_uint64()
@@ -152,14 +167,15 @@ def cover(polys, eps: int, which: int = HILBERT, grid_bits: int | None = None) -
     loff = np.empty(R.value + 1, np.uint32)
     ids = np.empty(nids.value, np.uint32)
     lib().orc_cover_export(h, _p(start), _p(loff), _p(ids))
-    return Covering(start, loff, ids, nrec.value, F.value, k.value, B, len(off) - 1, which, h)
+    return Covering(start, loff, ids, nrec.value, F.value, k.value, B, len(off) - 1, which,
+                    bool(flagged), h)
 
 
 def join_o2(polys, eps: int, pts, *, threads: int = 1, member: bool = False, only: int = -1,
-            grid_bits: int | None = None):
+            grid_bits: int | None = None, boundary_sums: bool = False):
     """O2: per point, the definitional test 'closed finest cell meets closed polygon'.
 
-    Returns (count, sum, boundary_count[, member])."""
+    Returns (count, sum, boundary_count[, boundary_sum, boundary_abs][, member])."""
     B = polys.grid_bits if grid_bits is None else grid_bits
     P = polys.n
     x, y = _u32(pts.x), _u32(pts.y)
@@ -167,13 +183,29 @@ def join_o2(polys, eps: int, pts, *, threads: int = 1, member: bool = False, onl
     cnt = np.zeros(P, np.uint64)
     sm = np.zeros(P, np.int64)
     bnd = np.zeros(P, np.uint64)
+    bs = np.zeros(P, np.int64) if boundary_sums else None
+    ba = np.zeros(P, np.uint64) if boundary_sums else None
     mem = np.zeros(len(x), np.uint8) if member else None
     rc = lib().orc_join_o2(P, _p(_u32(polys.ring_off)), _p(_u32(polys.x)), _p(_u32(polys.y)), B,
                            int(eps), len(x), _p(x), _p(y), _p(a), _p(cnt), _p(sm), _p(bnd),
-                           _p(mem), only, threads)
+                           _p(bs), _p(ba), _p(mem), only, threads)
     if rc != 0:
         raise ValueError("invalid O2 arguments")
-    return (cnt, sm, bnd, mem) if member else (cnt, sm, bnd)
+    out = (cnt, sm, bnd) + ((bs, ba) if boundary_sums else ())
+    return out + (mem,) if member else out
+
+
+def range_bounds(count, sm, bcount, bsum, babs):
+    """Sec. 6 on a conservative covering: the exact COUNT lies in
+    [count - bcount, count]; the exact SUM is sum minus the attribute sum of the
+    false positives, a subset of the boundary points, so it lies in
+    [sum - pos, sum - neg] with pos = (babs + bsum) / 2 >= 0 and
+    neg = (bsum - babs) / 2 <= 0 (the boundary points' positive and negative parts)."""
+    count, sm = np.asarray(count, np.int64), np.asarray(sm, np.int64)
+    bcount, bsum, babs = (np.asarray(bcount, np.int64), np.asarray(bsum, np.int64),
+                          np.asarray(babs, np.int64))
+    pos, neg = (babs + bsum) // 2, (bsum - babs) // 2
+    return count - bcount, count, sm - pos, sm - neg
 
 
 def join_exact(polys, pts, *, threads: int = 1, member: bool = False, only: int = -1):

@@ -217,6 +217,7 @@ int classify(const Ring& r, i64 x0, i64 y0, i64 side) {
 struct Rec {
   uint64_t lo, hi;  // finest-level ids [lo, hi)
   uint32_t poly;
+  bool boundary;    // a boundary cell at the finest level (else an interior cell)
 };
 
 void cover_rec(const Ring& r, uint32_t j, uint32_t B, uint32_t F, uint32_t L, uint64_t cx,
@@ -230,7 +231,7 @@ void cover_rec(const Ring& r, uint32_t j, uint32_t B, uint32_t F, uint32_t L, ui
     // contiguous ids [h * 4^(F-L), (h+1) * 4^(F-L))
     uint64_t h = curve(which, L, cx, cy);
     uint32_t shift = 2 * (F - L);
-    out.push_back(Rec{h << shift, (h + 1) << shift, j});
+    out.push_back(Rec{h << shift, (h + 1) << shift, j, c == BOUNDARY});
     return;
   }
   for (uint64_t dy = 0; dy < 2; ++dy)
@@ -249,18 +250,26 @@ struct Covering {
 // Sweep over all record endpoints in id order: each elementary interval gets
 // the ascending set of polygons whose records contain it; a new range starts
 // only where that set changes (maximal ranges, canonical form).
-Covering* build_covering(const std::vector<Ring>& rings, uint32_t B, uint32_t F, uint32_t k, int which) {
+// flagged (Sec. 6, result range estimation): a list entry is poly | 1 << 31
+// when the interval lies in a boundary cell of that polygon, and ranges split
+// where the flags change as well.
+Covering* build_covering(const std::vector<Ring>& rings, uint32_t B, uint32_t F, uint32_t k, int which,
+                         bool flagged) {
   std::vector<Rec> recs;
   for (uint32_t j = 0; j < rings.size(); ++j) cover_rec(rings[j], j, B, F, 0, 0, 0, which, recs);
   uint64_t top = (uint64_t)1 << (2 * F);
-  std::map<uint64_t, std::vector<std::pair<uint32_t, int>>> ev;  // position -> (poly, +1/-1)
+  // position -> (poly | boundary << 31, +1 / -1)
+  std::map<uint64_t, std::vector<std::pair<uint32_t, int>>> ev;
   ev[0];
   ev[top];
   for (const Rec& r : recs) {
-    ev[r.lo].push_back({r.poly, +1});
-    ev[r.hi].push_back({r.poly, -1});
+    const uint32_t e = r.poly | ((flagged && r.boundary) ? 0x80000000u : 0u);
+    ev[r.lo].push_back({e, +1});
+    ev[r.hi].push_back({e, -1});
   }
-  std::map<uint32_t, int> active;  // poly -> number of open records
+  // (poly, flag) -> number of open records; one polygon's cells are disjoint,
+  // so a polygon is open with at most one flag at any position
+  std::map<uint32_t, int> active;
   Covering* cov = new Covering();
   cov->B = B; cov->F = F; cov->k = k; cov->P = (uint32_t)rings.size();
   cov->nrec = recs.size();
@@ -272,8 +281,10 @@ Covering* build_covering(const std::vector<Ring>& rings, uint32_t B, uint32_t F,
       active[e.first] += e.second;
       if (active[e.first] == 0) active.erase(e.first);
     }
-    std::vector<uint32_t> cur;
+    std::vector<uint32_t> cur;  // ascending by polygon (the flag is bit 31)
     for (auto& a : active) cur.push_back(a.first);
+    std::sort(cur.begin(), cur.end(),
+              [](uint32_t a, uint32_t b) { return (a & 0x7fffffffu) < (b & 0x7fffffffu); });
     if (have_prev && cur == prev) continue;
     cov->start.push_back(it->first);
     cov->list_off.push_back((uint32_t)cov->list_ids.size());
@@ -363,11 +374,11 @@ void orc_classify_many(const uint32_t* off, const uint32_t* vx, const uint32_t* 
 }
 
 void* orc_cover(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint32_t* vy,
-                uint32_t B, uint64_t eps, int which) {
+                uint32_t B, uint64_t eps, int which, int flagged) {
   uint32_t k;
   if (B < 1 || B > 30 || finest_k(eps, B, &k) != 0) return nullptr;
   std::vector<Ring> rs = load_rings(P, off, vx, vy);
-  return build_covering(rs, B, B - k, k, which);
+  return build_covering(rs, B, B - k, k, which, flagged != 0);
 }
 
 void orc_cover_sizes(void* h, uint64_t* R, uint64_t* nids, uint64_t* nrec, uint32_t* F, uint32_t* k) {
@@ -390,20 +401,34 @@ void orc_cover_free(void* h) { delete (Covering*)h; }
 
 // O1 join: per point, its finest cell id, then the last range whose start is <= id
 // (std::upper_bound on the sorted starts), then every polygon on that range's list.
+// On a flagged covering (Sec. 6) the boundary partials are kept as well, all
+// nullable: bcount[p] = counted points in boundary cells of p, bsum[p] = their
+// attribute sum, babs[p] = the sum of their attributes' magnitudes.
 void orc_join_o1(void* h, uint64_t n, const uint32_t* x, const uint32_t* y, const int32_t* attr,
-                 uint64_t* count, int64_t* sum, int which) {
+                 uint64_t* count, int64_t* sum, uint64_t* bcount, int64_t* bsum, uint64_t* babs,
+                 int which) {
   Covering* c = (Covering*)h;
   std::fill(count, count + c->P, 0);
   if (sum) std::fill(sum, sum + c->P, 0);
+  if (bcount) std::fill(bcount, bcount + c->P, 0);
+  if (bsum) std::fill(bsum, bsum + c->P, 0);
+  if (babs) std::fill(babs, babs + c->P, 0);
   for (uint64_t i = 0; i < n; ++i) {
     uint64_t cx, cy;
     if (!point_cell(c->B, c->k, x[i], y[i], &cx, &cy)) continue;
     uint64_t id = curve(which, c->F, cx, cy);
     size_t r = (size_t)(std::upper_bound(c->start.begin(), c->start.end(), id) - c->start.begin()) - 1;
+    const int64_t a = attr ? attr[i] : 0;
     for (uint32_t e = c->list_off[r]; e < c->list_off[r + 1]; ++e) {
-      uint32_t p = c->list_ids[e];
+      const uint32_t p = c->list_ids[e] & 0x7fffffffu;
+      const bool boundary = (c->list_ids[e] >> 31) != 0;
       count[p] += 1;
-      if (sum) sum[p] += attr ? attr[i] : 0;
+      if (sum) sum[p] += a;
+      if (boundary) {
+        if (bcount) bcount[p] += 1;
+        if (bsum) bsum[p] += a;
+        if (babs) babs[p] += (uint64_t)(a < 0 ? -a : a);
+      }
     }
   }
 }
@@ -412,13 +437,14 @@ void orc_join_o1(void* h, uint64_t n, const uint32_t* x, const uint32_t* y, cons
 // closed finest cell of p meets closed polygon j.  No covering, no curve.
 // bnd_count (nullable): per polygon, the counted points whose cell meets the
 // polygon's boundary (Sec. 6, result range: exact count lies in
-// [count - bnd_count, count] for a conservative raster).
+// [count - bnd_count, count] for a conservative raster); bnd_sum / bnd_abs
+// (nullable): those points' attribute sum and sum of magnitudes.
 // member (nullable, n bytes): per point, 1 if it counts for polygon `only`
 // (only >= 0) or for any polygon (only < 0).
 int orc_join_o2(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint32_t* vy, uint32_t B,
                 uint64_t eps, uint64_t n, const uint32_t* x, const uint32_t* y, const int32_t* attr,
-                uint64_t* count, int64_t* sum, uint64_t* bnd_count, uint8_t* member, int64_t only,
-                int threads) {
+                uint64_t* count, int64_t* sum, uint64_t* bnd_count, int64_t* bnd_sum,
+                uint64_t* bnd_abs, uint8_t* member, int64_t only, int threads) {
   uint32_t k;
   if (B < 1 || B > 30 || finest_k(eps, B, &k) != 0) return -1;
   std::vector<Ring> rs = load_rings(P, off, vx, vy);
@@ -428,6 +454,8 @@ int orc_join_o2(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint3
   std::vector<std::vector<uint64_t>> tc(threads, std::vector<uint64_t>(P, 0));
   std::vector<std::vector<int64_t>> ts(threads, std::vector<int64_t>(P, 0));
   std::vector<std::vector<uint64_t>> tb(threads, std::vector<uint64_t>(P, 0));
+  std::vector<std::vector<int64_t>> tbs(threads, std::vector<int64_t>(P, 0));
+  std::vector<std::vector<uint64_t>> tba(threads, std::vector<uint64_t>(P, 0));
   parallel_for(n, threads, [&](uint64_t a, uint64_t b, int t) {
     std::vector<uint32_t> cand;
     for (uint64_t i = a; i < b; ++i) {
@@ -439,9 +467,14 @@ int orc_join_o2(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint3
         for (uint32_t j : cand) {
           int c = classify(rs[j], x0, y0, s);
           if (c == EXTERIOR) continue;
+          const int64_t av = attr ? attr[i] : 0;
           tc[t][j] += 1;
-          ts[t][j] += attr ? attr[i] : 0;
-          if (c == BOUNDARY) tb[t][j] += 1;
+          ts[t][j] += av;
+          if (c == BOUNDARY) {
+            tb[t][j] += 1;
+            tbs[t][j] += av;
+            tba[t][j] += (uint64_t)(av < 0 ? -av : av);
+          }
           if (only < 0 || (int64_t)j == only) hit = true;
         }
       }
@@ -452,10 +485,14 @@ int orc_join_o2(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint3
     count[j] = 0;
     if (sum) sum[j] = 0;
     if (bnd_count) bnd_count[j] = 0;
+    if (bnd_sum) bnd_sum[j] = 0;
+    if (bnd_abs) bnd_abs[j] = 0;
     for (int t = 0; t < threads; ++t) {
       count[j] += tc[t][j];
       if (sum) sum[j] += ts[t][j];
       if (bnd_count) bnd_count[j] += tb[t][j];
+      if (bnd_sum) bnd_sum[j] += tbs[t][j];
+      if (bnd_abs) bnd_abs[j] += tba[t][j];
     }
   }
   return 0;

@@ -242,6 +242,101 @@ def test_covering_is_canonical_and_exact_cell_set(orc, which):
             assert np.array_equal(inlist, cls != 0)
 
 
+# ------------------------------------------- result range estimation (Sec. 6)
+
+def test_handworked_boundary_counts(orc):
+    """Boundary-cell point counts derived by hand (tests/golden/handworked_b4.json):
+    the flagged covering's O1 join and the definitional O2 test both match."""
+    with open(os.path.join(GOLD, "handworked_b4.json")) as f:
+        g = json.load(f)
+    B = g["grid_bits"]
+    pts = lattice(B)
+    for name, ring in g["polygons"].items():
+        P = polys_of([ring], B)
+        for c in g["cases"]:
+            want = c["boundary"][name]
+            for which in (0, 1):
+                cov = orc.cover(P, c["eps"], which, flagged=True)
+                cnt, sm, bc, bs, ba = cov.join_range(pts.x, pts.y, pts.attr)
+                assert int(cnt[0]) == c[name] and int(bc[0]) == want, (name, c, which)
+                assert int(bs[0]) == want and int(ba[0]) == want
+            assert int(orc.join_o2(P, c["eps"], pts)[2][0]) == want
+
+
+def _merge_plain(cov):
+    """Strip the boundary flags and merge equal neighbours."""
+    st, lo, ids = cov.start, cov.list_off, cov.list_ids
+    starts, lists = [], []
+    for r in range(cov.R):
+        lst = tuple(int(e) & 0x7FFFFFFF for e in ids[lo[r]:lo[r + 1]])
+        if lists and lists[-1] == lst:
+            continue
+        starts.append(int(st[r]))
+        lists.append(lst)
+    return starts + [int(st[-1])], lists
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_flagged_covering_cell_by_cell(orc, which):
+    """Every finest cell of the flagged covering: polygon j is on its list iff the
+    cell meets j, and flagged iff the cell meets j's boundary (classify, a
+    separate predicate from the sweep); without flags it is the plain covering."""
+    B = 6
+    P = small_stars(31, B, n=5)
+    for eps in (2, 6, 23):
+        k, F = orc.finest_k(eps, B)
+        cf = orc.cover(P, eps, which, flagged=True)
+        cp = orc.cover(P, eps, which)
+        st, lo, ids = cf.start, cf.list_off, cf.list_ids
+        lists = [tuple(int(e) for e in ids[lo[r]:lo[r + 1]]) for r in range(cf.R)]
+        assert st[0] == 0 and st[-1] == 4 ** F
+        for r in range(cf.R):
+            polys = [e & 0x7FFFFFFF for e in lists[r]]
+            assert polys == sorted(set(polys))
+            if r:
+                assert lists[r] != lists[r - 1]
+        n = 2 ** F
+        gx, gy = np.meshgrid(np.arange(n), np.arange(n))
+        gx, gy = gx.ravel(), gy.ravel()
+        h = orc.curve(F, gx, gy, which)
+        r_of = np.searchsorted(st, h, side="right") - 1
+        s = 2 ** k
+        for j in range(P.n):
+            cls = orc.classify(P, j, gx * s, gy * s, s)
+            inlist = np.array([j in [e & 0x7FFFFFFF for e in lists[r]] for r in r_of])
+            flagged = np.array([(j | 0x80000000) in lists[r] for r in r_of])
+            assert np.array_equal(inlist, cls != 0)
+            assert np.array_equal(flagged, cls == 2)
+        ps, pl = _merge_plain(cf)
+        assert ps == [int(v) for v in cp.start]
+        assert pl == [tuple(int(e) for e in cp.list_ids[cp.list_off[r]:cp.list_off[r + 1]])
+                      for r in range(cp.R)]
+
+
+def test_range_bounds_signed_attributes(orc):
+    """Sec. 6 with signed attributes: the flagged O1 partials equal the
+    definitional O2 ones, and the exact COUNT and SUM (exact point-in-polygon
+    join) lie in the intervals, whose widths are bcount and babs."""
+    w = W.tiny_stars(20_000)
+    rng = np.random.default_rng(5)
+    attr = rng.integers(-2 ** 31, 2 ** 31, size=w.points.n, dtype=np.int64).astype(np.int32)
+    attr[:4] = [-2 ** 31, 2 ** 31 - 1, 0, -1]
+    pts = W.Points(w.points.x, w.points.y, attr, w.points.grid_bits)
+    P = w.polygons
+    ex, exs = orc.join_exact(P, pts)
+    for eps in (4096, 512, 64, 8):
+        cov = orc.cover(P, eps, flagged=True)
+        c, s, bc, bs, ba = cov.join_range(pts.x, pts.y, pts.attr)
+        c2, s2, b2, bs2, ba2 = orc.join_o2(P, eps, pts, boundary_sums=True)
+        for u, v in ((c, c2), (s, s2), (bc, b2), (bs, bs2), (ba, ba2)):
+            assert np.array_equal(u, v), eps
+        lo_c, hi_c, lo_s, hi_s = orc.range_bounds(c, s, bc, bs, ba)
+        assert ((lo_c <= ex) & (ex <= hi_c)).all()
+        assert ((lo_s <= exs) & (exs <= hi_s)).all()
+        assert np.array_equal(hi_c - lo_c, bc.astype(np.int64))
+        assert np.array_equal(hi_s - lo_s, ba.astype(np.int64))
+
+
 # ------------------------------------------------------ invariants (Sec. 2.2, 6)
 
 @pytest.fixture(scope="module")
