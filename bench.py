@@ -13,7 +13,8 @@ and SUM (device-resident points).
 The metric counts point-joins: points x eps levels per second.
 
 Besides the timed steps the script measures, outside the timed region, the
-join alone per eps for the learned and the binary-search lookups, the
+join alone per eps for the learned and the binary-search lookups, result
+range estimation (boundary-flagged coverings and the range join), the
 end-to-end rate through the host-buffer entry point (points copied from pinned
 host memory every step, results read back), and the CPU oracle on a bounded
 sample.
@@ -62,8 +63,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps (no join-only, e2e, CPU, batch or serving legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--legs", default="join,e2e,cpu,batch,serve",
-                    help="extra legs: join (lookups alone), e2e, cpu, batch, serve")
+    ap.add_argument("--legs", default="join,range,e2e,cpu,batch,serve",
+                    help="extra legs: join (lookups alone), range (result range estimation), "
+                         "e2e, cpu, batch, serve")
     ap.add_argument("--lod-points", type=int, default=200_000_000)
     ap.add_argument("--lod-queries", type=int, default=4096)
     ap.add_argument("--serve-points", type=int, default=500_000_000)
@@ -348,6 +350,43 @@ def main():
             joins[str(eps)] = row
             c.free()
         res["join_only"] = joins
+    # ---- result range estimation (Sec. 6): flagged coverings and the range join
+    if "range" in legs:
+        reps = 5
+        rng_rows = {}
+        P_ = w.polygons.n
+        bc, bs_, ba = (torch.zeros(P_, dtype=torch.int64, device=dev) for _ in range(3))
+        for i, eps in enumerate(w.eps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            c = sdb.build_covering(w.polygons, 24, eps, stream, flags=sdb.COVER_BOUNDARY_FLAGS)
+            inf = c.info()
+            lb = leaf_bits_for(inf.n_ranges)
+            sdb.covering_build_index(c, lb, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row = {"build_and_index_ms": e0.elapsed_time(e1), "ranges": inf.n_ranges,
+                   "plain_ranges": joins.get(str(eps), {}).get("ranges"), "leaf_bits": lb}
+            sdb.join_aggregate_range(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], bc, sm[i], bs_, ba,
+                                     stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                sdb.join_aggregate_range(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], bc, sm[i], bs_,
+                                         ba, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row["range_join_ms"] = e0.elapsed_time(e1) / reps
+            row["plain_join_ms"] = joins.get(str(eps), {}).get("learned_ms")
+            c_np = cnt[i].cpu().numpy()
+            b_np = bc.cpu().numpy()
+            live = c_np > 0
+            row["boundary_fraction"] = float(b_np.sum() / max(1, c_np.sum()))
+            row["mean_relative_count_interval"] = float((b_np[live] / c_np[live]).mean())
+            rng_rows[str(eps)] = row
+            c.free()
+        res["range_estimation"] = rng_rows
     # ---- roofline of the join kernel of the finest eps inside the timed steps
     # algorithmic bytes: the point stream (x, y, attr) plus one read of the
     # covering and its index

@@ -81,7 +81,7 @@ typedef struct sdb_covering_info {
   uint64_t n_cells;        /* raster cells emitted before merging into ranges */
   uint64_t device_bytes;   /* device memory held by the covering */
   uint32_t index_leaf_bits;/* leaves = 2^index_leaf_bits, 0 = no learned index */
-  uint32_t reserved;
+  uint32_t boundary_flags; /* 1 if built with SDB_COVER_BOUNDARY_FLAGS */
 } sdb_covering_info;
 
 /* Finest level for (grid_bits, eps), Sec. 2.2 (side eps/sqrt(2), so the
@@ -108,6 +108,22 @@ sdb_status sdb_finest_level(uint32_t grid_bits, uint64_t eps, uint32_t *shift_ou
  * SDB_ENOMEM: device memory ran out. */
 sdb_status sdb_build_covering(const sdb_polygons *polys, uint32_t grid_bits, uint64_t eps,
                               void *cuda_stream, sdb_covering **out);
+
+/* Result range estimation (Sec. 6): errors of a conservative raster occur only
+ * in boundary cells, so counting the points that fall in a polygon's boundary
+ * cells bounds the exact answer.  With SDB_COVER_BOUNDARY_FLAGS every list
+ * entry is polygon | 1 << 31 when the range lies in boundary cells of that
+ * polygon (finest-level cells meeting its boundary) and polygon otherwise
+ * (interior cells); ranges are maximal for the flagged lists, so a covering has
+ * at least as many ranges as the plain one.  Stripping the flags and merging
+ * equal neighbours gives exactly the plain covering.  Every join accepts a
+ * flagged covering; sdb_join_aggregate_range requires one. */
+#define SDB_COVER_BOUNDARY_FLAGS 1u
+
+/* sdb_build_covering with options: flags = 0 or SDB_COVER_BOUNDARY_FLAGS.
+ * SDB_EINVAL as sdb_build_covering, or an unknown flag bit. */
+sdb_status sdb_build_covering_ex(const sdb_polygons *polys, uint32_t grid_bits, uint64_t eps,
+                                 uint32_t flags, void *cuda_stream, sdb_covering **out);
 
 sdb_status sdb_covering_get_info(const sdb_covering *cov, sdb_covering_info *info);
 
@@ -136,6 +152,24 @@ sdb_status sdb_covering_build_index(sdb_covering *cov, uint32_t leaf_bits, void 
 sdb_status sdb_join_aggregate(const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
                               uint64_t n, const sdb_covering *cov, int lookup,
                               uint64_t *d_count, int64_t *d_sum, void *cuda_stream);
+
+/* sdb_join_aggregate plus the result-range partials of Sec. 6, on a covering
+ * built with SDB_COVER_BOUNDARY_FLAGS: for every polygon j on the range of
+ * point i where j is flagged, d_bcount[j] += 1, d_bsum[j] += d_attr[i] and
+ * d_babs[j] += |d_attr[i]|.  With a conservative raster the exact answers lie in
+ *   COUNT: [d_count - d_bcount, d_count]
+ *   SUM:   [d_sum - (d_babs + d_bsum) / 2, d_sum + (d_babs - d_bsum) / 2]
+ * (the false positives are a subset of the boundary points; (d_babs + d_bsum)/2
+ * and (d_bsum - d_babs)/2 are their positive and negative parts).  All output
+ * arrays have P entries, are zeroed by the call and are device memory;
+ * d_sum, d_bsum and d_babs are given together or all NULL (COUNT only).
+ * Asynchronous.  SDB_EINVAL: as sdb_join_aggregate, a null d_bcount, a covering
+ * without boundary flags, or only some of d_sum / d_bsum / d_babs. */
+sdb_status sdb_join_aggregate_range(const uint32_t *d_x, const uint32_t *d_y,
+                                    const int32_t *d_attr, uint64_t n, const sdb_covering *cov,
+                                    int lookup, uint64_t *d_count, int64_t *d_sum,
+                                    uint64_t *d_bcount, int64_t *d_bsum, uint64_t *d_babs,
+                                    void *cuda_stream);
 
 /* The same join for points in host memory against n_covs coverings at once
  * (e.g. the same polygons at several eps).  Points are streamed to the device

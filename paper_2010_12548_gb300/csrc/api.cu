@@ -147,11 +147,20 @@ sdb_status sdb_finest_level(uint32_t grid_bits, uint64_t eps, uint32_t* shift_ou
 
 sdb_status sdb_build_covering(const sdb_polygons* polys, uint32_t grid_bits, uint64_t eps,
                               void* cuda_stream, sdb_covering** out) {
+  return sdb_build_covering_ex(polys, grid_bits, eps, 0u, cuda_stream, out);
+}
+
+sdb_status sdb_build_covering_ex(const sdb_polygons* polys, uint32_t grid_bits, uint64_t eps,
+                                 uint32_t flags, void* cuda_stream, sdb_covering** out) {
   if (!out) {
     set_error("out is NULL");
     return SDB_EINVAL;
   }
   *out = nullptr;
+  if (flags & ~SDB_COVER_BOUNDARY_FLAGS) {
+    set_error("unknown covering flags 0x%x", flags);
+    return SDB_EINVAL;
+  }
   uint32_t k = 0;
   SDB_TRY(finest(grid_bits, eps, &k));
   if (!polys || !polys->ring_off || !polys->x || !polys->y) {
@@ -197,7 +206,8 @@ sdb_status sdb_build_covering(const sdb_polygons* polys, uint32_t grid_bits, uin
     set_error("no CUDA device");
     return SDB_ECUDA;
   }
-  sdb_status st = build_covering_device(polys, grid_bits, k, s, cov);
+  sdb_status st = build_covering_device(polys, grid_bits, k,
+                                        (flags & SDB_COVER_BOUNDARY_FLAGS) != 0, s, cov);
   if (st != SDB_OK) {
     std::string msg = sdb_last_error();
     free_covering(cov);
@@ -224,6 +234,7 @@ sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* inf
   info->device_bytes =
       cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) + (4ull << cov->knot_bits) + 4 : 0);
   info->index_leaf_bits = cov->leaf_bits;
+  info->boundary_flags = cov->flagged ? 1u : 0u;
   return SDB_OK;
 }
 
@@ -266,6 +277,43 @@ sdb_status sdb_join_aggregate(const uint32_t* d_x, const uint32_t* d_y, const in
   SDB_TRY(check_device(cov));
   return launch_join(d_x, d_y, d_attr, n, cov, lookup, d_count, d_sum, (cudaStream_t)cuda_stream,
                      true);
+}
+
+sdb_status sdb_join_aggregate_range(const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
+                                    uint64_t n, const sdb_covering* cov, int lookup,
+                                    uint64_t* d_count, int64_t* d_sum, uint64_t* d_bcount,
+                                    int64_t* d_bsum, uint64_t* d_babs, void* cuda_stream) {
+  if (!cov || !d_count || !d_bcount) {
+    set_error("covering, d_count or d_bcount is NULL");
+    return SDB_EINVAL;
+  }
+  if (!cov->flagged) {
+    set_error("covering was built without boundary flags (SDB_COVER_BOUNDARY_FLAGS)");
+    return SDB_EINVAL;
+  }
+  if (n > 0 && (!d_x || !d_y)) {
+    set_error("n > 0 with NULL coordinates");
+    return SDB_EINVAL;
+  }
+  if ((d_sum != nullptr) != (d_bsum != nullptr) || (d_sum != nullptr) != (d_babs != nullptr)) {
+    set_error("d_sum, d_bsum and d_babs must be given together");
+    return SDB_EINVAL;
+  }
+  if (d_sum && !d_attr && n > 0) {
+    set_error("d_sum requested without d_attr");
+    return SDB_EINVAL;
+  }
+  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED) {
+    set_error("unknown lookup %d", lookup);
+    return SDB_EINVAL;
+  }
+  if (lookup == SDB_LOOKUP_LEARNED && !cov->leaves) {
+    set_error("learned lookup requested but the covering has no index");
+    return SDB_EINVAL;
+  }
+  SDB_TRY(check_device(cov));
+  return launch_join(d_x, d_y, d_attr, n, cov, lookup, d_count, d_sum, (cudaStream_t)cuda_stream,
+                     true, d_bcount, d_bsum, d_babs);
 }
 
 sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, const int32_t* h_attr,

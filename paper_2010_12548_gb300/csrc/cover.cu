@@ -33,6 +33,16 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t NONE = 0xffffffffu;
+// A record's value: slot (bits 0..25), level above the finest (26..30), and
+// bit 31 set for a boundary cell of a flagged covering (Sec. 6).
+constexpr uint32_t VAL_SLOT = (1u << 26) - 1u;
+constexpr uint32_t VAL_FLAG = 0x80000000u;
+__device__ __forceinline__ uint32_t val_level(uint32_t v) { return (v >> 26) & 31u; }
+// list entry / single-polygon payload of a slot with its boundary flag
+__device__ __forceinline__ uint32_t list_entry(uint32_t v) { return v & (VAL_SLOT | VAL_FLAG); }
+__device__ __forceinline__ uint32_t single_pay(uint32_t v) {
+  return (v & VAL_SLOT) | ((v >> 31) << 30);
+}
 
 struct Edge {
   int32_t ax, ay, bx, by;
@@ -132,8 +142,8 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
                                   const uint32_t* __restrict__ pair_query,
                                   const uint32_t* __restrict__ pair_slot,
                                   const CoverQuery* __restrict__ qs, uint32_t NP, uint32_t qshift,
-                                  Item* __restrict__ items, uint64_t* __restrict__ rec_key,
-                                  uint32_t* __restrict__ rec_val,
+                                  uint32_t bflag, Item* __restrict__ items,
+                                  uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val,
                                   unsigned long long* __restrict__ counters) {
   uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
@@ -143,7 +153,7 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
     if (lane == 0) {
       unsigned long long r = atomicAdd(&counters[2], 1ull);
       rec_key[r] = qshift >= 64 ? 0ull : ((uint64_t)qi << qshift);
-      rec_val[r] = pair_slot[p];
+      rec_val[r] = pair_slot[p] | bflag;  // the whole grid as one boundary cell
     }
     return;
   }
@@ -230,7 +240,8 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
     const Item* __restrict__ items, uint32_t n_items, const uint32_t* __restrict__ elist,
     const Edge* __restrict__ edges, const uint32_t* __restrict__ pair_query,
     const uint32_t* __restrict__ pair_slot, const CoverQuery* __restrict__ qs, uint32_t qshift,
-    uint32_t B, uint32_t L, Item* __restrict__ next_items, uint32_t* __restrict__ next_elist,
+    uint32_t bflag, uint32_t B, uint32_t L, Item* __restrict__ next_items,
+    uint32_t* __restrict__ next_elist,
     uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val, unsigned long long rec_base,
     unsigned long long* __restrict__ counters) {
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -331,7 +342,7 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
       if (gl == 0) {
         unsigned long long r = rec_base + ro++;
         rec_key[r] = qbits | (chid << shift);
-        rec_val[r] = slot | ((F - cl) << 26);
+        rec_val[r] = slot | ((F - cl) << 26) | (cnt[c] > 0 ? bflag : 0u);
       }
       cnt[c] = 0;  // a finest boundary cell needs no edge list
     } else if (cnt[c] > 0) {
@@ -384,7 +395,7 @@ __global__ void breakpoints_kernel(const uint64_t* __restrict__ key, const uint3
                                    uint64_t n, uint64_t top, uint64_t* __restrict__ bp) {
   uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) {
-    uint32_t d = val[r] >> 26;
+    uint32_t d = val_level(val[r]);
     bp[2 * r] = key[r];
     bp[2 * r + 1] = key[r] + (1ull << (2 * d));
   } else if (r == n) {
@@ -398,7 +409,7 @@ __global__ void spans_kernel(const uint64_t* __restrict__ key, const uint32_t* _
                              uint32_t* __restrict__ klo, uint32_t* __restrict__ span) {
   uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  uint32_t d = val[r] >> 26;
+  uint32_t d = val_level(val[r]);
   uint64_t lo = key[r], hi = lo + (1ull << (2 * d));
   uint32_t a = lower_bound_u64(b, m, lo), c = lower_bound_u64(b, m, hi);
   klo[r] = a;
@@ -409,7 +420,7 @@ __global__ void spans_kernel(const uint64_t* __restrict__ key, const uint32_t* _
 __global__ void expand_pairs_kernel(const uint64_t* __restrict__ poff, uint64_t n,
                                     const uint32_t* __restrict__ klo,
                                     const uint32_t* __restrict__ val, uint64_t T, uint32_t pbits,
-                                    uint64_t* __restrict__ pairs) {
+                                    uint32_t fl, uint64_t* __restrict__ pairs) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= T) return;
   // last r with poff[r] <= i
@@ -419,7 +430,9 @@ __global__ void expand_pairs_kernel(const uint64_t* __restrict__ poff, uint64_t 
     if (poff[lo + half] <= i) lo += half;
     len -= half;
   }
-  uint32_t poly = val[lo] & ((1u << 26) - 1u);
+  // the pair's polygon field: slot, then its boundary flag when flagged (fl = 1)
+  const uint32_t v = val[lo];
+  const uint32_t poly = fl ? (((v & VAL_SLOT) << 1) | (v >> 31)) : (v & VAL_SLOT);
   uint64_t k = (uint64_t)klo[lo] + (i - poff[lo]);
   pairs[i] = (k << pbits) | poly;
 }
@@ -466,15 +479,24 @@ __global__ void emit_ranges_kernel(const uint32_t* __restrict__ flag, const uint
   rsrc[r] = eoff[k];
 }
 
-__global__ void fill_lists_kernel(const uint64_t* __restrict__ pairs, uint64_t pmask,
+__global__ void fill_lists_kernel(const uint64_t* __restrict__ pairs, uint64_t pmask, uint32_t fl,
                                   const uint32_t* __restrict__ rlen, const uint32_t* __restrict__ rsrc,
                                   const uint32_t* __restrict__ list_off, uint64_t R,
                                   uint32_t* __restrict__ list_ids, uint32_t* __restrict__ pay) {
   uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   uint32_t n = rlen[r], o = list_off[r], s = rsrc[r];
-  for (uint32_t t = 0; t < n; ++t) list_ids[o + t] = (uint32_t)(pairs[s + t] & pmask);
-  pay[r] = n == 0 ? NONE : (n == 1 ? (uint32_t)(pairs[s] & pmask) : (0x80000000u | (uint32_t)r));
+  auto entry = [&](uint64_t pr) {  // polygon field -> slot | flag << 31
+    const uint32_t f = (uint32_t)(pr & pmask);
+    return fl ? ((f >> 1) | ((f & 1u) << 31)) : f;
+  };
+  for (uint32_t t = 0; t < n; ++t) list_ids[o + t] = entry(pairs[s + t]);
+  if (n == 1) {
+    const uint32_t e = entry(pairs[s]);
+    pay[r] = (e & VAL_SLOT) | ((e >> 31) << 30);
+  } else {
+    pay[r] = n == 0 ? NONE : (0x80000000u | (uint32_t)r);
+  }
 }
 
 __global__ void finish_kernel(uint64_t* start, uint32_t* list_off, uint64_t R, uint64_t top,
@@ -504,11 +526,11 @@ __global__ void group_flags_kernel(const uint64_t* __restrict__ sk, const uint32
   uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const uint64_t k = sk[r];
-  const uint32_t d = sv[r] >> 26;
+  const uint32_t d = val_level(sv[r]);
   flag[r] = (r == 0 || sk[r - 1] != k) ? 1u : 0u;
   if (r + 1 < n) {
     const uint64_t k2 = sk[r + 1];
-    if (k2 == k ? ((sv[r + 1] >> 26) != d)
+    if (k2 == k ? (val_level(sv[r + 1]) != d)
                 : (qof(k2, qshift) == qof(k, qshift) && k2 < k + (1ull << (2 * d))))
       *nested = 1u;
   }
@@ -561,7 +583,7 @@ __device__ __forceinline__ uint32_t group_opens(const GroupCtx& c, uint32_t g, u
   const uint32_t a = c.gfirst[g];
   const uint64_t key = c.sk[a];
   const uint32_t q = (uint32_t)qof(key, c.qshift);
-  const uint64_t lo = key & c.lomask, hi = lo + (1ull << (2 * (c.sv[a] >> 26)));
+  const uint64_t lo = key & c.lomask, hi = lo + (1ull << (2 * val_level(c.sv[a])));
   const uint64_t top = 1ull << (2 * c.qs[q].F);
   const bool first = g == 0 || qof(c.sk[c.gfirst[g - 1]], c.qshift) != q;
   uint32_t gap, fresh;
@@ -571,13 +593,12 @@ __device__ __forceinline__ uint32_t group_opens(const GroupCtx& c, uint32_t g, u
     fresh = 1;
   } else {
     const uint32_t pa = c.gfirst[g - 1];
-    const uint64_t phi = (c.sk[pa] & c.lomask) + (1ull << (2 * (c.sv[pa] >> 26)));
+    const uint64_t phi = (c.sk[pa] & c.lomask) + (1ull << (2 * val_level(c.sv[pa])));
     *gap_lo = phi;
     gap = lo > phi;
     fresh = gap || c.gsize[g] != c.gsize[g - 1];
-    const uint32_t PM = (1u << 26) - 1u;
     for (uint32_t t = 0; !fresh && t < c.gsize[g]; ++t)
-      fresh = (c.sv[a + t] & PM) != (c.sv[pa + t] & PM);
+      fresh = list_entry(c.sv[a + t]) != list_entry(c.sv[pa + t]);
   }
   const bool last = g + 1 == c.G || qof(c.sk[c.gfirst[g + 1]], c.qshift) != q;
   const uint32_t tail = last && hi < top;
@@ -672,10 +693,9 @@ __global__ void fill_lists_sv_kernel(const uint32_t* __restrict__ sv,
                                      uint32_t* __restrict__ list_ids, uint32_t* __restrict__ pay) {
   uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= E) return;
-  const uint32_t PM = (1u << 26) - 1u;
   const uint32_t n = rlen[r], o = list_off[r], s = rsrc[r];
-  for (uint32_t t = 0; t < n; ++t) list_ids[o + t] = sv[s + t] & PM;
-  pay[r] = n == 0 ? NONE : (n == 1 ? (sv[s] & PM) : (0x80000000u | (uint32_t)r));
+  for (uint32_t t = 0; t < n; ++t) list_ids[o + t] = list_entry(sv[s + t]);
+  pay[r] = n == 0 ? NONE : (n == 1 ? single_pay(sv[s]) : (0x80000000u | (uint32_t)r));
 }
 
 __global__ void set_u32_kernel(uint32_t* p, uint64_t n, uint32_t v) {
@@ -700,7 +720,8 @@ sdb_status read_u64(const unsigned long long* d, unsigned long long* h, int n, c
 // records -> canonical ranges, general path (one query, nested cells allowed):
 // sweep over all record endpoints (see the file comment)
 static sdb_status merge_general(uint64_t* key, uint32_t* val, uint64_t n, uint32_t F, uint32_t P,
-                                cudaStream_t s, CoverSet* out) {
+                                bool flags, cudaStream_t s, CoverSet* out) {
+  const uint32_t fl = flags ? 1u : 0u;  // the pairs' polygon field carries the flag
   Scratch sc(s);
   const uint64_t top = 1ull << (2 * F);
   const uint64_t nbp = 2 * n + 2;
@@ -745,13 +766,13 @@ static sdb_status merge_general(uint64_t* key, uint32_t* val, uint64_t n, uint32
               (unsigned long long)T);
     return SDB_ENOMEM;
   }
-  const uint32_t pbits = (uint32_t)(bits_for(P > 1 ? P - 1 : 1));
+  const uint32_t pbits = (uint32_t)(bits_for(P > 1 ? P - 1 : 1)) + fl;
   const uint64_t pmask = (1ull << pbits) - 1;
   uint64_t *pairs, *ptmp, *ps;
   SDB_TRY(sc.get(&pairs, T));
   SDB_TRY(sc.get(&ptmp, T));
   if (T) {
-    expand_pairs_kernel<<<grid_for(T, 256), 256, 0, s>>>(poff, n, klo, val, T, pbits, pairs);
+    expand_pairs_kernel<<<grid_for(T, 256), 256, 0, s>>>(poff, n, klo, val, T, pbits, fl, pairs);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
   }
@@ -794,7 +815,7 @@ static sdb_status merge_general(uint64_t* key, uint32_t* val, uint64_t n, uint32
   SDB_TRY_CUDA(cudaMemcpyAsync(&nids, dN, sizeof(nids), cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   SDB_TRY(dalloc_n(&out->list_ids, (size_t)nids, s));
-  fill_lists_kernel<<<grid_for(R, 256), 256, 0, s>>>(ps, pmask, rlen, rsrc, out->list_off, R,
+  fill_lists_kernel<<<grid_for(R, 256), 256, 0, s>>>(ps, pmask, fl, rlen, rsrc, out->list_off, R,
                                                       out->list_ids, out->pay);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
@@ -854,7 +875,7 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
     sc.release(gidx);
     uint32_t P = 0;
     for (uint32_t i = 0; i < spec.NP; ++i) P = spec.pair_slot[i] + 1 > P ? spec.pair_slot[i] + 1 : P;
-    return merge_general(sk, sv, n, spec.q[0].F, P, s, out);
+    return merge_general(sk, sv, n, spec.q[0].F, P, spec.flags, s, out);
   }
   const uint32_t G = hG[0];
   uint32_t *gfirst, *gsize, *nopen, *gscan, *qlast, *qfirst;
@@ -943,14 +964,14 @@ void CoverSet::release(cudaStream_t s) {
 
 static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items, const uint32_t* elist,
                          const Edge* edges, const uint32_t* pq, const uint32_t* ps,
-                         const CoverQuery* qs, uint32_t qshift, uint32_t B, uint32_t L,
+                         const CoverQuery* qs, uint32_t qshift, uint32_t bflag, uint32_t B, uint32_t L,
                          Item* nitems, uint32_t* nel, uint64_t* rkey, uint32_t* rval,
                          unsigned long long rec_base, unsigned long long* ctr, cudaStream_t s) {
   const size_t threads = (size_t)n_items * G;
 #define SDB_EXPAND(g)                                                                          \
   case g:                                                                                      \
     expand_level_kernel<g><<<grid_for(threads, 256), 256, 0, s>>>(                             \
-        items, n_items, elist, edges, pq, ps, qs, qshift, B, L, nitems, nel, rkey, rval,        \
+        items, n_items, elist, edges, pq, ps, qs, qshift, bflag, B, L, nitems, nel, rkey, rval, \
         rec_base, ctr);                                                                        \
     break;
   switch (G) {
@@ -1039,6 +1060,7 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
     }
   } free_recs{&rkey, &rval, s};
 
+  const uint32_t bflag = spec.flags ? VAL_FLAG : 0u;  // boundary records' flag
   unsigned long long* ctr;
   SDB_TRY(sc.get(&ctr, 3));
   SDB_TRY_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
@@ -1046,7 +1068,7 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
   SDB_TRY(dalloc_n(&items, NP, s));
   if (NP) {
     root_items_kernel<<<grid_for((size_t)NP * 32, 256), 256, 0, s>>>(
-        d_off, edges, d_pp, d_pq, d_ps, d_qs, NP, qshift, items, rkey, rval, ctr);
+        d_off, edges, d_pp, d_pq, d_ps, d_qs, NP, qshift, bflag, items, rkey, rval, ctr);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
   }
@@ -1103,7 +1125,7 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
     uint32_t G = 1;
     if (mean >= 4)
       while (G < 32 && G < mean) G <<= 1;
-    SDB_TRY(launch_expand(G, items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift, B,
+    SDB_TRY(launch_expand(G, items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift, bflag, B,
                           L, nitems, nel, rkey, rval, n_rec, ctr, s));
     SDB_TRY_CUDA(cudaGetLastError());
     unsigned long long h[3];
@@ -1123,8 +1145,8 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
   return merge_records(rkey, rval, n_rec, spec, d_qs, qshift, key_bits, s, out);
 }
 
-sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,
-                                 sdb_covering* cov) {
+sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, bool flags,
+                                 cudaStream_t s, sdb_covering* cov) {
   const uint32_t P = polys->n_polygons;
   const uint32_t F = B - k;
   cov->B = B;
@@ -1142,6 +1164,8 @@ sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t
   spec.pair_poly = pp.data();
   spec.pair_query = pq.data();
   spec.pair_slot = pp.data();
+  spec.flags = flags;
+  cov->flagged = flags;
   CoverSet cs;
   sdb_status st = build_coverings(polys, spec, s, &cs);
   if (st != SDB_OK) {

@@ -32,6 +32,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t NONE = 0xffffffffu;
 constexpr int THREADS = 256;
 constexpr uint32_t SMEM_POLYS = 2048;
+constexpr uint32_t SMEM_POLYS_RANGE = 1024;  // 32 bytes of accumulators per polygon
 
 struct JoinArgs {
   const uint32_t* x;
@@ -40,6 +41,11 @@ struct JoinArgs {
   uint64_t n;
   unsigned long long* count;
   unsigned long long* sum;
+  // result-range partials (Sec. 6): boundary count, boundary attribute sum
+  // and sum of magnitudes
+  unsigned long long* bcount;
+  unsigned long long* bsum;
+  unsigned long long* babs;
   int vec;
   // covering
   const uint64_t* start;
@@ -186,27 +192,53 @@ constexpr uint32_t FLUSH_TILES = 32;
 constexpr uint32_t FLUSH_POINTS = FLUSH_TILES * THREADS * 4;
 static_assert((uint64_t)FLUSH_POINTS * 65535u < (1ull << 32), "low-half counter could wrap");
 
+// With result-range partials, boundary points add to a second set of the same
+// counters and to a magnitude sum, split the same way (|a| <= 2^31, so its high
+// half is at most 2^15 per point).
 struct Acc {
   uint32_t* cnt;
   uint32_t* lo;
   int32_t* hi;
+  uint32_t* bcnt;
+  uint32_t* blo;
+  int32_t* bhi;
+  uint32_t* alo;
+  uint32_t* ahi;
 };
 
-template <bool SMEM, bool SUM>
-__device__ __forceinline__ void add_one(uint32_t p, int32_t a, const Acc& s, const JoinArgs& A) {
+template <bool SMEM, bool SUM, bool RANGE>
+__device__ __forceinline__ void add_one(uint32_t p, int32_t a, uint32_t bnd, const Acc& s,
+                                        const JoinArgs& A) {
+  const uint32_t m = a < 0 ? 0u - (uint32_t)a : (uint32_t)a;  // |a|
   if (SMEM) {
     atomicAdd(&s.cnt[p], 1u);
     if (SUM) {
       atomicAdd(&s.lo[p], (uint32_t)a & 0xffffu);
       atomicAdd(&s.hi[p], a >> 16);
     }
+    if (RANGE && bnd) {
+      atomicAdd(&s.bcnt[p], 1u);
+      if (SUM) {
+        atomicAdd(&s.blo[p], (uint32_t)a & 0xffffu);
+        atomicAdd(&s.bhi[p], a >> 16);
+        atomicAdd(&s.alo[p], m & 0xffffu);
+        atomicAdd(&s.ahi[p], m >> 16);
+      }
+    }
   } else {
     atomicAdd(&A.count[p], 1ull);
     if (SUM) atomicAdd(&A.sum[p], (unsigned long long)(long long)a);
+    if (RANGE && bnd) {
+      atomicAdd(&A.bcount[p], 1ull);
+      if (SUM) {
+        atomicAdd(&A.bsum[p], (unsigned long long)(long long)a);
+        atomicAdd(&A.babs[p], (unsigned long long)m);
+      }
+    }
   }
 }
 
-template <bool SUM>
+template <bool SUM, bool RANGE>
 __device__ void flush_acc(const Acc& s, const JoinArgs& A) {
   for (uint32_t i = threadIdx.x; i < A.P; i += THREADS) {
     const uint32_t c = s.cnt[i];
@@ -220,10 +252,28 @@ __device__ void flush_acc(const Acc& s, const JoinArgs& A) {
         s.hi[i] = 0;
       }
     }
+    if (RANGE) {
+      const uint32_t bc = s.bcnt[i];
+      if (bc) {
+        atomicAdd(&A.bcount[i], (unsigned long long)bc);
+        s.bcnt[i] = 0;
+        if (SUM) {
+          const long long bt = (long long)s.bhi[i] * 65536 + (long long)s.blo[i];
+          const unsigned long long at =
+              (unsigned long long)s.ahi[i] * 65536ull + (unsigned long long)s.alo[i];
+          atomicAdd(&A.bsum[i], (unsigned long long)bt);
+          atomicAdd(&A.babs[i], at);
+          s.blo[i] = 0;
+          s.bhi[i] = 0;
+          s.alo[i] = 0;
+          s.ahi[i] = 0;
+        }
+      }
+    }
   }
 }
 
-template <int LOOKUP, bool SMEM, bool SUM>
+template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
 __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   // the cell-id table, then the lookup staging (the binary search's sample of
@@ -234,11 +284,23 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   size_t off = HILBERT3_SMEM_BYTES + ((LOOKUP == SDB_LOOKUP_BINARY)
                                           ? (size_t)A.sample_n * 8
                                           : (((size_t)A.nknots * 4 + 7) & ~(size_t)7));
+  // accumulators: P words each of cnt [, lo, hi] [, bcnt [, blo, bhi, alo, ahi]]
   Acc acc;
-  acc.cnt = reinterpret_cast<uint32_t*>(smem + off);
-  off += SMEM ? (size_t)A.P * 4 : 0;
-  acc.lo = reinterpret_cast<uint32_t*>(smem + off);
-  acc.hi = reinterpret_cast<int32_t*>(smem + off + ((SMEM && SUM) ? (size_t)A.P * 4 : 0));
+  {
+    uint32_t* w = reinterpret_cast<uint32_t*>(smem + off);
+    const size_t P = SMEM ? A.P : 0;
+    acc.cnt = w;
+    w += P;
+    acc.lo = w;
+    acc.hi = reinterpret_cast<int32_t*>(w + (SUM ? P : 0));
+    w += SUM ? 2 * P : 0;
+    acc.bcnt = w;
+    w += RANGE ? P : 0;
+    acc.blo = w;
+    acc.bhi = reinterpret_cast<int32_t*>(w + ((RANGE && SUM) ? P : 0));
+    acc.alo = w + ((RANGE && SUM) ? 2 * P : 0);
+    acc.ahi = w + ((RANGE && SUM) ? 3 * P : 0);
+  }
 
   hilbert3_fill(s_tab);
   if (LOOKUP == SDB_LOOKUP_BINARY)
@@ -251,6 +313,15 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
       if (SUM) {
         acc.lo[i] = 0;
         acc.hi[i] = 0;
+      }
+      if (RANGE) {
+        acc.bcnt[i] = 0;
+        if (SUM) {
+          acc.blo[i] = 0;
+          acc.bhi[i] = 0;
+          acc.alo[i] = 0;
+          acc.ahi[i] = 0;
+        }
       }
     }
   __syncthreads();
@@ -303,37 +374,41 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int32_t a = SUM ? as[q] : 0;
+      // single polygon: slot | boundary << 30; list entries: slot | boundary << 31
       if (pay[q] < 0x80000000u) {
-        add_one<SMEM, SUM>(pay[q], a, acc, A);
+        add_one<SMEM, SUM, RANGE>(pay[q] & 0x3fffffffu, a, (pay[q] >> 30) & 1u, acc, A);
       } else if (pay[q] != NONE) {  // several polygons share the range
         const uint32_t rr = pay[q] & 0x7fffffffu;
         const uint32_t b = __ldg(A.list_off + rr), e = __ldg(A.list_off + rr + 1);
-        for (uint32_t i = b; i < e; ++i) add_one<SMEM, SUM>(__ldg(A.list_ids + i), a, acc, A);
+        for (uint32_t i = b; i < e; ++i) {
+          const uint32_t id = __ldg(A.list_ids + i);
+          add_one<SMEM, SUM, RANGE>(id & 0x7fffffffu, a, id >> 31, acc, A);
+        }
       }
     }
     if (SMEM && ++since_flush == FLUSH_TILES) {
       since_flush = 0;
       __syncthreads();
-      flush_acc<SUM>(acc, A);
+      flush_acc<SUM, RANGE>(acc, A);
       __syncthreads();
     }
   }
   if (SMEM) {
     __syncthreads();
-    flush_acc<SUM>(acc, A);
+    flush_acc<SUM, RANGE>(acc, A);
   }
 }
 
-template <int LOOKUP, bool SMEM, bool SUM>
+template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
 sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
   size_t smem = HILBERT3_SMEM_BYTES;
-  if (SMEM) smem += (size_t)A.P * (SUM ? 12 : 4);
+  if (SMEM) smem += (size_t)A.P * ((SUM ? 12 : 4) + (RANGE ? (SUM ? 20 : 4) : 0));
   if (LOOKUP == SDB_LOOKUP_BINARY)
     smem += (size_t)A.sample_n * 8;
   else
     smem += ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
   smem = (smem + 15) & ~(size_t)15;
-  auto kern = join_kernel<LOOKUP, SMEM, SUM>;
+  auto kern = join_kernel<LOOKUP, SMEM, SUM, RANGE>;
   if (smem > 48 * 1024)
     SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -348,14 +423,32 @@ sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
   return SDB_OK;
 }
 
+
+template <bool RANGE>
+sdb_status launch_pick(const JoinArgs& A, int lookup, bool has_sum, cudaStream_t s) {
+  const bool smem = A.P <= (RANGE ? SMEM_POLYS_RANGE : SMEM_POLYS);
+  if (lookup == SDB_LOOKUP_BINARY) {
+    if (smem)
+      return has_sum ? launch_t<0, true, true, RANGE>(A, s) : launch_t<0, true, false, RANGE>(A, s);
+    return has_sum ? launch_t<0, false, true, RANGE>(A, s) : launch_t<0, false, false, RANGE>(A, s);
+  }
+  if (smem)
+    return has_sum ? launch_t<1, true, true, RANGE>(A, s) : launch_t<1, true, false, RANGE>(A, s);
+  return has_sum ? launch_t<1, false, true, RANGE>(A, s) : launch_t<1, false, false, RANGE>(A, s);
+}
+
 }  // namespace
 
 sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr, uint64_t n,
                        const sdb_covering* cov, int lookup, uint64_t* count, int64_t* sum,
-                       cudaStream_t s, bool zero) {
+                       cudaStream_t s, bool zero, uint64_t* bcount, int64_t* bsum,
+                       uint64_t* babs) {
   if (zero) {
     SDB_TRY_CUDA(cudaMemsetAsync(count, 0, (size_t)cov->P * 8, s));
     if (sum) SDB_TRY_CUDA(cudaMemsetAsync(sum, 0, (size_t)cov->P * 8, s));
+    if (bcount) SDB_TRY_CUDA(cudaMemsetAsync(bcount, 0, (size_t)cov->P * 8, s));
+    if (bsum) SDB_TRY_CUDA(cudaMemsetAsync(bsum, 0, (size_t)cov->P * 8, s));
+    if (babs) SDB_TRY_CUDA(cudaMemsetAsync(babs, 0, (size_t)cov->P * 8, s));
     if (lookup == SDB_LOOKUP_LEARNED)
       SDB_TRY_CUDA(cudaMemsetAsync(cov->fallbacks, 0, sizeof(unsigned long long), s));
   }
@@ -387,14 +480,11 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.inv_w = 1.0f / (float)(1ull << cov->knot_wshift);
   A.nleaves = cov->leaf_bits ? (1u << cov->leaf_bits) : 0u;
   A.fallbacks = cov->fallbacks;
-  const bool smem = cov->P <= SMEM_POLYS;
+  A.bcount = reinterpret_cast<unsigned long long*>(bcount);
+  A.bsum = reinterpret_cast<unsigned long long*>(bsum);
+  A.babs = reinterpret_cast<unsigned long long*>(babs);
   const bool has_sum = sum != nullptr;
-  if (lookup == SDB_LOOKUP_BINARY) {
-    if (smem) return has_sum ? launch_t<0, true, true>(A, s) : launch_t<0, true, false>(A, s);
-    return has_sum ? launch_t<0, false, true>(A, s) : launch_t<0, false, false>(A, s);
-  }
-  if (smem) return has_sum ? launch_t<1, true, true>(A, s) : launch_t<1, true, false>(A, s);
-  return has_sum ? launch_t<1, false, true>(A, s) : launch_t<1, false, false>(A, s);
+  return bcount ? launch_pick<true>(A, lookup, has_sum, s) : launch_pick<false>(A, lookup, has_sum, s);
 }
 
 }  // namespace sdb

@@ -147,6 +147,7 @@ __device__ __forceinline__ uint32_t root_leaf(const float* knot, uint32_t wshift
 struct sdb_covering {
   int device = 0;
   uint32_t B = 0, k = 0, F = 0, P = 0;
+  bool flagged = false;  // list entries and pay carry boundary flags
   uint64_t R = 0, nids = 0, ncells = 0;
   // canonical form
   uint64_t* start = nullptr;     // R+1
@@ -195,6 +196,7 @@ struct CoverSpec {
   const uint32_t* pair_poly = nullptr;  // host, NP entries each
   const uint32_t* pair_query = nullptr;
   const uint32_t* pair_slot = nullptr;
+  bool flags = false;  // boundary flags on list entries (result range, Sec. 6)
 };
 // Result, device arrays from the library pool.  Query q's ranges are entries
 // [qoff[q], qoff[q+1] - 1) of start/list_off/pay; entry qoff[q+1] - 1 is a
@@ -211,8 +213,8 @@ struct CoverSet {
 };
 sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cudaStream_t s,
                            CoverSet* out);
-sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, cudaStream_t s,
-                                 sdb_covering* cov);
+sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, bool flags,
+                                 cudaStream_t s, sdb_covering* cov);
 // batch.cu ------------------------------------------------------------------
 // Per-query parameters of a batched join, and the covering arrays a query's
 // slice lives in (one chunk may serve many queries).
@@ -280,9 +282,12 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
 // join.cu
 // zero = true: outputs (and the fallback counter) are cleared first;
 // zero = false: the launch adds into them (chunked joins)
+// bcount / bsum / babs (nullable; the covering must be flagged): result-range
+// partials of Sec. 6 (boundary count, boundary attribute sum, sum of magnitudes)
 sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr, uint64_t n,
                        const sdb_covering* cov, int lookup, uint64_t* count, int64_t* sum,
-                       cudaStream_t s, bool zero);
+                       cudaStream_t s, bool zero, uint64_t* bcount = nullptr,
+                       int64_t* bsum = nullptr, uint64_t* babs = nullptr);
 
 // sort.cu: device-wide primitives
 template <class T>

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsdb.so")
 
 SDB_OK, SDB_EINVAL, SDB_ENOMEM, SDB_ECUDA, SDB_ETIMEOUT, SDB_EBUSY = range(6)
 LOOKUP_BINARY, LOOKUP_LEARNED = 0, 1
+COVER_BOUNDARY_FLAGS = 1
 
 
 class SdbError(RuntimeError):
@@ -36,7 +37,7 @@ class CoveringInfo(C.Structure):
                 ("finest_level", C.c_uint32), ("n_polygons", C.c_uint32),
                 ("n_ranges", C.c_uint64), ("n_list_ids", C.c_uint64), ("n_cells", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("index_leaf_bits", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("boundary_flags", C.c_uint32)]
 
 
 class Query(C.Structure):
@@ -83,6 +84,8 @@ def lib():
         sig = {
             "sdb_finest_level": ([U32, U64, P, P], I),
             "sdb_build_covering": ([P, U32, U64, P, P], I),
+            "sdb_build_covering_ex": ([P, U32, U64, U32, P, P], I),
+            "sdb_join_aggregate_range": ([P, P, P, U64, P, I, P, P, P, P, P, P], I),
             "sdb_covering_get_info": ([P, P], I),
             "sdb_covering_build_index": ([P, U32, P], I),
             "sdb_join_aggregate": ([P, P, P, U64, P, I, P, P, P], I),
@@ -182,14 +185,16 @@ class Covering:
             pass
 
 
-def build_covering(polys, grid_bits: int, eps: int, stream=None) -> Covering:
-    """sdb_build_covering: polys has ring_off/x/y uint32 numpy arrays."""
+def build_covering(polys, grid_bits: int, eps: int, stream=None, flags: int = 0) -> Covering:
+    """sdb_build_covering_ex: polys has ring_off/x/y uint32 numpy arrays; flags 0
+    or COVER_BOUNDARY_FLAGS (boundary-flagged lists for result ranges)."""
     off = np.ascontiguousarray(polys.ring_off, np.uint32)
     x = np.ascontiguousarray(polys.x, np.uint32)
     y = np.ascontiguousarray(polys.y, np.uint32)
     sp = _Polys(len(off) - 1, _np_ptr(off), _np_ptr(x), _np_ptr(y))
     out = C.c_void_p()
-    _check(lib().sdb_build_covering(C.byref(sp), grid_bits, int(eps), _stream(stream), C.byref(out)))
+    _check(lib().sdb_build_covering_ex(C.byref(sp), grid_bits, int(eps), int(flags),
+                                       _stream(stream), C.byref(out)))
     return Covering(out.value)
 
 
@@ -202,6 +207,25 @@ def join_aggregate(x, y, attr, cov: Covering, lookup: int, count, sum_=None, str
     n = x.numel() if x is not None else 0
     _check(lib().sdb_join_aggregate(_dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), n, cov.handle,
                                     lookup, _dptr(count, 8), _dptr(sum_, 8), _stream(stream)))
+
+
+def join_aggregate_range(x, y, attr, cov: Covering, lookup: int, count, bcount, sum_=None,
+                         bsum=None, babs=None, stream=None):
+    """sdb_join_aggregate_range on device tensors (int64 outputs of P entries):
+    COUNT/SUM plus the boundary partials bounding the exact answers."""
+    n = x.numel() if x is not None else 0
+    _check(lib().sdb_join_aggregate_range(_dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), n, cov.handle,
+                                          lookup, _dptr(count, 8), _dptr(sum_, 8),
+                                          _dptr(bcount, 8), _dptr(bsum, 8), _dptr(babs, 8),
+                                          _stream(stream)))
+
+
+def range_bounds(count, sum_, bcount, bsum, babs):
+    """Intervals holding the exact COUNT and SUM (numpy int64 arrays in, out):
+    [count - bcount, count] and [sum - (babs + bsum) / 2, sum + (babs - bsum) / 2]."""
+    count, sum_, bcount = (np.asarray(v, np.int64) for v in (count, sum_, bcount))
+    bsum, babs = np.asarray(bsum, np.int64), np.asarray(babs, np.int64)
+    return count - bcount, count, sum_ - (babs + bsum) // 2, sum_ + (babs - bsum) // 2
 
 
 def join_aggregate_host(x, y, attr, covs, lookup: int, stream=None):

@@ -340,10 +340,12 @@ def mobility_points(seed: int, n: int, grid_bits: int, n_clusters: int,
                     chunk: int = 1 << 22, threads: int | None = None) -> Points:
     """Cluster/uniform mix: ``frac_cluster`` of the points come from
     ``n_clusters`` isotropic Gaussians (centre uniform, sigma uniform in
-    ``sigma``, clipped to the grid), the rest are uniform.  Points appear in
-    random order.  Generated in fixed-size chunks, each from its own child
-    seed (so the result does not depend on memory limits or on the number of
-    threads filling the chunks)."""
+    ``sigma``, truncated to the grid: a sample that rounds outside the grid
+    is drawn again from its cluster, so no mass piles up on the grid's
+    border), the rest are uniform.  Points appear in random order.  Generated
+    in fixed-size chunks, each from its own child seed (so the result does
+    not depend on memory limits or on the number of threads filling the
+    chunks)."""
     import concurrent.futures as cf
     G = 2 ** grid_bits
     ss = np.random.SeedSequence(seed)
@@ -365,6 +367,17 @@ def mobility_points(seed: int, n: int, grid_bits: int, n_clusters: int,
         g = r.standard_normal((m, 2))
         cx = centres[which, 0] + g[:, 0] * sig[which]
         cy = centres[which, 1] + g[:, 1] * sig[which]
+
+        def outside(u, v):  # rounds to a coordinate outside [0, G)
+            return (u < -0.5) | (u >= G - 0.5) | (v < -0.5) | (v >= G - 0.5)
+        out = np.nonzero(is_c & outside(cx, cy))[0]
+        for _ in range(64):
+            if out.size == 0:
+                break
+            g = r.standard_normal((out.size, 2))
+            cx[out] = centres[which[out], 0] + g[:, 0] * sig[which[out]]
+            cy[out] = centres[which[out], 1] + g[:, 1] * sig[which[out]]
+            out = out[outside(cx[out], cy[out])]
         ux = r.integers(0, G, size=m)
         uy = r.integers(0, G, size=m)
         px = np.where(is_c, np.clip(np.rint(cx), 0, G - 1), ux)
