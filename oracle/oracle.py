@@ -61,6 +61,7 @@ def lib():
         L.orc_join_o2.argtypes = [U32, P, P, P, U32, U64, U64, P, P, P, P, P, P, P, P, P, I64,
                                   I32]
         L.orc_join_o2.restype = I32
+        L.orc_point_index_aggregate.argtypes = [P, U64, P, P, P, P, P, I32]
         L.orc_join_exact.argtypes = [U32, P, P, P, U32, U64, P, P, P, P, P, P, I64, I32]
         L.orc_near_boundary.argtypes = [P, P, P, U32, U32, U32, U64]
         L.orc_near_boundary.restype = I32
@@ -138,6 +139,17 @@ class Covering:
         sm = np.zeros(self.n_polygons, np.int64)
         lib().orc_join_o1(self._h, len(x), _p(x), _p(y), _p(a), _p(cnt), _p(sm), None, None,
                           None, self.which)
+        return cnt, sm
+
+    def point_index_aggregate(self, x, y, attr=None):
+        """Sec. 3 point indexing: sorted full-resolution keys + prefix sums,
+        two lower bounds per covering range.  Equals join() exactly."""
+        x, y = _u32(x), _u32(y)
+        a = None if attr is None else np.ascontiguousarray(attr, np.int32)
+        cnt = np.zeros(self.n_polygons, np.uint64)
+        sm = np.zeros(self.n_polygons, np.int64)
+        lib().orc_point_index_aggregate(self._h, len(x), _p(x), _p(y), _p(a), _p(cnt), _p(sm),
+                                        self.which)
         return cnt, sm
 
     def join_range(self, x, y, attr=None):

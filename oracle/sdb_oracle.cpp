@@ -498,6 +498,47 @@ int orc_join_o2(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint3
   return 0;
 }
 
+// Point-indexed aggregation (Sec. 3, "Point Indexing"): the points' cells are
+// linearised by the same curve at full resolution (level B, so a finest-level
+// id h at level F covers the full-resolution ids [h << 2k, (h + 1) << 2k)),
+// stored as a sorted array with prefix sums of the attribute; per covering
+// range [start_r, start_r+1) the qualifying points are
+// [lower_bound(start_r << 2k), lower_bound(start_r+1 << 2k)), their COUNT the
+// difference of the two positions and their SUM the difference of the prefix
+// sums, added to every polygon on the range's list.  Plain std::sort and
+// std::lower_bound.
+void orc_point_index_aggregate(void* h, uint64_t n, const uint32_t* x, const uint32_t* y,
+                               const int32_t* attr, uint64_t* count, int64_t* sum, int which) {
+  Covering* c = (Covering*)h;
+  std::vector<std::pair<uint64_t, int64_t>> kv;
+  kv.reserve(n);
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t cx, cy;
+    if (!point_cell(c->B, 0, x[i], y[i], &cx, &cy)) continue;
+    kv.push_back({curve(which, c->B, cx, cy), attr ? (int64_t)attr[i] : 0});
+  }
+  std::sort(kv.begin(), kv.end());
+  std::vector<uint64_t> keys(kv.size());
+  std::vector<int64_t> prefix(kv.size() + 1, 0);
+  for (size_t i = 0; i < kv.size(); ++i) {
+    keys[i] = kv[i].first;
+    prefix[i + 1] = prefix[i] + kv[i].second;
+  }
+  std::fill(count, count + c->P, 0);
+  if (sum) std::fill(sum, sum + c->P, 0);
+  const uint32_t sh = 2 * c->k;
+  for (size_t r = 0; r + 1 < c->start.size(); ++r) {
+    if (c->list_off[r] == c->list_off[r + 1]) continue;
+    const size_t a = std::lower_bound(keys.begin(), keys.end(), c->start[r] << sh) - keys.begin();
+    const size_t b = std::lower_bound(keys.begin(), keys.end(), c->start[r + 1] << sh) - keys.begin();
+    for (uint32_t e = c->list_off[r]; e < c->list_off[r + 1]; ++e) {
+      const uint32_t p = c->list_ids[e] & 0x7fffffffu;
+      count[p] += b - a;
+      if (sum) sum[p] += prefix[b] - prefix[a];
+    }
+  }
+}
+
 // exact closed point-in-polygon join (the answer the approximation bounds)
 void orc_join_exact(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint32_t* vy,
                     uint32_t B, uint64_t n, const uint32_t* x, const uint32_t* y, const int32_t* attr,

@@ -337,6 +337,43 @@ def test_range_bounds_signed_attributes(orc):
         assert np.array_equal(hi_s - lo_s, ba.astype(np.int64))
 
 
+# ----------------------------------------------- point indexing (Sec. 3)
+
+def test_point_index_handworked(orc):
+    """Sorted keys + prefix sums over the covering's ranges give the hand-derived
+    counts (tests/golden/handworked_b4.json)."""
+    with open(os.path.join(GOLD, "handworked_b4.json")) as f:
+        g = json.load(f)
+    B = g["grid_bits"]
+    pts = lattice(B)
+    for name, ring in g["polygons"].items():
+        P = polys_of([ring], B)
+        for c in g["cases"]:
+            for which in (0, 1):
+                cnt, sm = orc.cover(P, c["eps"], which).point_index_aggregate(pts.x, pts.y,
+                                                                              pts.attr)
+                assert int(cnt[0]) == c[name] and int(sm[0]) == c[name], (name, c, which)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_point_index_equals_point_stream(orc, which):
+    """Range counting over sorted points (two lower bounds per range) equals the
+    per-point lookup join exactly: overlapping stars, duplicated points, points
+    outside the grid, signed attributes, several eps (F = 0 included)."""
+    w = W.tiny_stars(30_000)
+    rng = np.random.default_rng(8)
+    x = np.concatenate([w.points.x, w.points.x[:500], [2 ** 16, 3]]).astype(np.uint32)
+    y = np.concatenate([w.points.y, w.points.y[:500], [5, 2 ** 20]]).astype(np.uint32)
+    a = rng.integers(-2 ** 31, 2 ** 31, len(x), dtype=np.int64).astype(np.int32)
+    for eps in (2 ** 17, 4096, 300, 64, 5):
+        cov = orc.cover(w.polygons, eps, which)
+        want = cov.join(x, y, a)
+        got = cov.point_index_aggregate(x, y, a)
+        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1]), eps
+        fl = orc.cover(w.polygons, eps, which, flagged=True).point_index_aggregate(x, y, a)
+        assert np.array_equal(fl[0], want[0]) and np.array_equal(fl[1], want[1]), eps
+
+
 # ------------------------------------------------------ invariants (Sec. 2.2, 6)
 
 @pytest.fixture(scope="module")
