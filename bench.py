@@ -14,7 +14,8 @@ The metric counts point-joins: points x eps levels per second.
 
 Besides the timed steps the script measures, outside the timed region, the
 join alone per eps for the learned and the binary-search lookups, result
-range estimation (boundary-flagged coverings and the range join), the
+range estimation (boundary-flagged coverings and the range join), point-indexed
+aggregation (sorted points, prefix sums, binary search vs RadixSpline), the
 end-to-end rate through the host-buffer entry point (points copied from pinned
 host memory every step, results read back), and the CPU oracle on a bounded
 sample.
@@ -63,9 +64,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps (no join-only, e2e, CPU, batch or serving legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--legs", default="join,range,e2e,cpu,batch,serve",
+    ap.add_argument("--legs", default="join,range,e2e,cpu,batch,pointindex,serve",
                     help="extra legs: join (lookups alone), range (result range estimation), "
-                         "e2e, cpu, batch, serve")
+                         "e2e, cpu, batch, pointindex (range counting over sorted points), serve")
+    ap.add_argument("--pi-points", type=int, default=500_000_000)
     ap.add_argument("--lod-points", type=int, default=200_000_000)
     ap.add_argument("--lod-queries", type=int, default=4096)
     ap.add_argument("--serve-points", type=int, default=500_000_000)
@@ -444,7 +446,7 @@ def main():
     # ---- batched level-of-detail queries and serving (resident points)
     del x, y, a
     torch.cuda.empty_cache()
-    if "batch" in legs or "serve" in legs:
+    if "batch" in legs or "serve" in legs or "pointindex" in legs:
         res.update(resident_legs(args, legs, sdb, torch, dev, stream))
     if "serving" in res and res["serving"].get("batched"):
         nominal = [r for r in res["serving"]["batched"] if r["rate"] == 10000] or \
@@ -503,6 +505,54 @@ def poisson_serve(sdb, srv, queries, rate, n, seed):
     return np.asarray(lat), np.asarray(batch), hits, wall
 
 
+def point_index_leg(args, sdb, torch, dev, stream, T, pts, resident):
+    """Sec. 3 point indexing (the paper's Fig. 4a setting: ~40k tract polygons
+    over resident points, 32..800 covering cells per polygon): range counting
+    over Hilbert-sorted points with prefix sums, binary search vs RadixSpline
+    (radix bits 25, spline error 32), beside the per-point join over the same
+    points; results must be equal."""
+    n = args.pi_points
+    p = resident(n)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sdb.points_build_index(p, 25, 32, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ns, err, _ = sdb.points_index_stats(p, stream)
+    out = {"workload": f"tracts40k_pts{n // 1_000_000}M_g28", "points": n,
+           "index_build_ms": e0.elapsed_time(e1), "spline_points": ns, "spline_max_error": err,
+           "radix_bits": 25, "spline_error": 32, "levels": {}}
+    xs = torch.from_numpy(pts.x[:n].view(np.int32)).to(dev)
+    ys = torch.from_numpy(pts.y[:n].view(np.int32)).to(dev)
+    at = torch.from_numpy(pts.attr[:n]).to(dev)
+    P = T.n
+    c1, s1, c2, s2 = (torch.zeros(P, dtype=torch.int64, device=dev) for _ in range(4))
+    for eps in (2 ** 19, 2 ** 18, 2 ** 17, 2 ** 16, 2 ** 15):
+        cov = sdb.build_covering(T, 28, eps, stream)
+        inf = cov.info()
+        sdb.covering_build_index(cov, leaf_bits_for(inf.n_ranges), stream)
+        bs = timed(torch, stream, lambda: sdb.points_aggregate(p, cov, sdb.LOOKUP_BINARY, c1, s1,
+                                                               stream), 5)
+        rs = timed(torch, stream, lambda: sdb.points_aggregate(p, cov, sdb.LOOKUP_RADIX_SPLINE, c1,
+                                                               s1, stream), 5)
+        js = timed(torch, stream, lambda: sdb.join_aggregate(xs, ys, at, cov, sdb.LOOKUP_LEARNED,
+                                                             c2, s2, stream), 3)
+        lookups = inf.n_ranges + 1
+        out["levels"][str(eps)] = {
+            "cells_per_polygon": inf.n_cells / P, "ranges": inf.n_ranges,
+            "binary_ms": bs, "radix_spline_ms": rs, "point_stream_join_ms": js,
+            "radix_spline_lookups_per_s": lookups / (rs / 1e3),
+            "binary_lookups_per_s": lookups / (bs / 1e3),
+            "matches_point_stream": bool(torch.equal(c1, c2) and torch.equal(s1, s2)),
+            "fallbacks": sdb.points_index_stats(p, stream)[2]}
+        cov.free()
+    del xs, ys, at
+    p.free()
+    torch.cuda.empty_cache()
+    return out
+
+
 def resident_legs(args, legs, sdb, torch, dev, stream):
     """Batched level-of-detail queries (4,096 queries over 200M resident points)
     and serving (Poisson arrivals of zoom-session queries over 500M points)."""
@@ -510,7 +560,8 @@ def resident_legs(args, legs, sdb, torch, dev, stream):
     out = {}
     T = W.tracts40k_tiling()
     n_all = max(args.lod_points if "batch" in legs else 0,
-                args.serve_points if "serve" in legs else 0)
+                args.serve_points if "serve" in legs else 0,
+                args.pi_points if "pointindex" in legs else 0)
     pts = W.resident_points(n_all)
 
     def resident(n):
@@ -550,6 +601,8 @@ def resident_legs(args, legs, sdb, torch, dev, stream):
         p.free()
         del cnt, sm
         torch.cuda.empty_cache()
+    if "pointindex" in legs:
+        out["point_index"] = point_index_leg(args, sdb, torch, dev, stream, T, pts, resident)
     if "serve" in legs:
         sessions = W.zoom_sessions(W.BASE_SEED + 5, 512, T)
         queries = [q for ss in sessions for q in ss]

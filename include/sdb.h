@@ -54,7 +54,7 @@ typedef enum sdb_status {
   SDB_EBUSY = 5     /* the object is in use (e.g. a batch still running) */
 } sdb_status;
 
-enum { SDB_LOOKUP_BINARY = 0, SDB_LOOKUP_LEARNED = 1 };
+enum { SDB_LOOKUP_BINARY = 0, SDB_LOOKUP_LEARNED = 1, SDB_LOOKUP_RADIX_SPLINE = 2 };
 
 /* Polygons in host memory, read during the call only.  One simple ring per
  * polygon (no holes, no self-contact), vertices in [0, 2^grid_bits), either
@@ -229,6 +229,49 @@ typedef struct sdb_points sdb_points;
 sdb_status sdb_points_create(const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
                              uint64_t n, uint32_t grid_bits, void *cuda_stream, sdb_points **out);
 void sdb_points_free(sdb_points *pts);
+
+/* ---------------------------------------------------------------------------
+ * Point-indexed aggregation (Sec. 3, "Point Indexing"): the points' cells are
+ * linearised by the same curve at full resolution and kept as a sorted array
+ * (the resident set above); a polygon's covering ranges select contiguous
+ * slices of it, so per covering range COUNT = ub - lb and SUM = prefix[ub] -
+ * prefix[lb] with lb / ub the lower bounds of the range's first id and of the
+ * next range's first id, both scaled to full resolution (<< 2 * finest_shift).
+ * The results equal sdb_join_aggregate on the same points exactly.
+ * ------------------------------------------------------------------------- */
+
+/* Build the point index: int64 prefix sums of the attribute in key order and
+ * a RadixSpline over the distinct keys (the paper's learned index, with radix
+ * bits 25 and spline error 32 in its experiments): spline points such that
+ * linear interpolation between consecutive ones is within spline_error of every
+ * key's first position (greedy spline corridor, exact integer slopes, built in
+ * independent chunks of 4096 keys), and a table of 2^radix_bits + 1 entries
+ * giving, per prefix of the key range, the first spline point at or above it.
+ * Replaces a previous index.  Synchronises cuda_stream.
+ * SDB_EINVAL: NULL pts, radix_bits outside 1..30, spline_error outside
+ * 1..2^20, another current device.  SDB_ENOMEM: device memory ran out. */
+sdb_status sdb_points_build_index(sdb_points *pts, uint32_t radix_bits, uint32_t spline_error,
+                                  void *cuda_stream);
+
+/* COUNT and SUM per polygon of cov over the resident points by range counting:
+ * one lower-bound lookup per range boundary (lookup = SDB_LOOKUP_BINARY: binary
+ * search over the keys; SDB_LOOKUP_RADIX_SPLINE: radix table -> spline segment
+ * -> exact integer interpolation -> search within +-(spline_error + 1), the
+ * bracket verified, binary search as the counted fallback), then the slice's
+ * length and prefix-sum difference added to every polygon on the range's list.
+ * d_count, d_sum (P device entries; d_sum may be NULL) are zeroed by the call.
+ * Asynchronous.  SDB_EINVAL: NULL pts/cov/d_count, another lookup, grid bits of
+ * cov and pts differ, SUM or the spline requested before sdb_points_build_index,
+ * objects on another device. */
+sdb_status sdb_points_aggregate(const sdb_points *pts, const sdb_covering *cov, int lookup,
+                                uint64_t *d_count, int64_t *d_sum, void *cuda_stream);
+
+/* Spline diagnostics: number of spline points, the largest interpolation error
+ * over all distinct keys (measured on the device; <= spline_error by
+ * construction) and the fallbacks of the last spline aggregation.
+ * Synchronises cuda_stream.  SDB_EINVAL: NULL arguments, no index. */
+sdb_status sdb_points_index_stats(const sdb_points *pts, uint64_t *n_spline, uint64_t *max_error,
+                                  uint64_t *fallbacks, void *cuda_stream);
 
 typedef struct sdb_query {
   uint32_t x0, y0, x1, y1; /* viewport, half-open, inside the grid, non-empty */

@@ -625,6 +625,7 @@ void sdb_points_free(sdb_points* p) {
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
+  sdb::release_point_index(p, 0);
   void* ps[] = {p->key, p->x, p->y, p->attr};
   for (void* q : ps)
     if (q) cudaFreeAsync(q, 0);

@@ -175,9 +175,26 @@ struct sdb_points {
   uint32_t* x = nullptr;
   uint32_t* y = nullptr;
   int32_t* attr = nullptr;
+  // point index (sdb_points_build_index): prefix sums and a RadixSpline
+  int64_t* prefix = nullptr;  // n + 1
+  uint64_t* rs_key = nullptr;
+  uint32_t* rs_pos = nullptr;
+  uint32_t* rs_table = nullptr;  // 2^rs_radix_bits + 1
+  unsigned long long* rs_fallbacks = nullptr;
+  uint64_t rs_n = 0, rs_min = 0, rs_max = 0;
+  uint32_t rs_radix_bits = 0, rs_error = 0, rs_shift = 0;
 };
 
 namespace sdb {
+
+// pointindex.cu --------------------------------------------------------------
+sdb_status build_point_index(sdb_points* p, uint32_t radix_bits, uint32_t spline_error,
+                             cudaStream_t s);
+void release_point_index(sdb_points* p, cudaStream_t s);
+sdb_status point_index_aggregate(const sdb_points* p, const sdb_covering* cov, int lookup,
+                                 uint64_t* count, int64_t* sum, cudaStream_t s);
+sdb_status point_index_stats(const sdb_points* p, uint64_t* n_spline, uint64_t* max_error,
+                             uint64_t* fallbacks, cudaStream_t s);
 
 // cover.cu -------------------------------------------------------------------
 // Several coverings can be built in one level-synchronous pass.  Query q covers

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsdb.so")
 
 SDB_OK, SDB_EINVAL, SDB_ENOMEM, SDB_ECUDA, SDB_ETIMEOUT, SDB_EBUSY = range(6)
-LOOKUP_BINARY, LOOKUP_LEARNED = 0, 1
+LOOKUP_BINARY, LOOKUP_LEARNED, LOOKUP_RADIX_SPLINE = 0, 1, 2
 COVER_BOUNDARY_FLAGS = 1
 
 
@@ -99,6 +99,9 @@ def lib():
             "sdb_covering_index_stats": ([P, P, P], I),
             "sdb_points_create": ([P, P, P, U64, U32, P, P], I),
             "sdb_points_free": ([P], None),
+            "sdb_points_build_index": ([P, U32, U32, P], I),
+            "sdb_points_aggregate": ([P, P, I, P, P, P], I),
+            "sdb_points_index_stats": ([P, P, P, P, P], I),
             "sdb_batch_create": ([P, P, P, U32, P, U64, P, P], I),
             "sdb_batch_get_info": ([P, P], I),
             "sdb_batch_query_ranges": ([P, P], I),
@@ -327,6 +330,25 @@ def points_create(x, y, attr, grid_bits: int, stream=None) -> Points:
     _check(lib().sdb_points_create(_dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), x.numel(), grid_bits,
                                    _stream(stream), C.byref(out)))
     return Points(out.value)
+
+
+def points_build_index(pts: Points, radix_bits: int = 25, spline_error: int = 32, stream=None):
+    """sdb_points_build_index: prefix sums + RadixSpline over the resident keys."""
+    _check(lib().sdb_points_build_index(pts.handle, radix_bits, spline_error, _stream(stream)))
+
+
+def points_aggregate(pts: Points, cov: Covering, lookup: int, count, sum_=None, stream=None):
+    """sdb_points_aggregate into int64 device tensors of P entries."""
+    _check(lib().sdb_points_aggregate(pts.handle, cov.handle, lookup, _dptr(count, 8),
+                                      _dptr(sum_, 8), _stream(stream)))
+
+
+def points_index_stats(pts: Points, stream=None):
+    """(spline points, largest interpolation error, fallbacks of the last spline run)."""
+    a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    _check(lib().sdb_points_index_stats(pts.handle, C.byref(a), C.byref(b), C.byref(c),
+                                        _stream(stream)))
+    return a.value, b.value, c.value
 
 
 class Batch:
