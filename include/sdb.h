@@ -209,6 +209,29 @@ sdb_status sdb_join_aggregate_host_noalloc(const uint32_t *h_x, const uint32_t *
                                            const sdb_covering *cov, int lookup, uint64_t *h_count,
                                            int64_t *h_sum, void *cuda_stream);
 
+/* Bounded Raster Join (Sec. 5.2), restated on device buffers without a
+ * graphics API: the points are blended into a uniform canvas whose pixels are
+ * the finest cells of eps (each pixel keeps the COUNT and SUM of its points),
+ * every polygon is rasterised conservatively onto the same pixels (a pixel is
+ * masked in when the closed pixel meets the closed polygon; exact integer
+ * scanline rasterisation), and the masked pixels' aggregates are summed per
+ * polygon.  No covering and no precomputation; the result equals
+ * sdb_join_aggregate with a covering of the same polygons and eps.  The canvas
+ * of 4^F pixels is processed in tiles of 2^tile_bits x 2^tile_bits pixels
+ * (0 = 2^13), as many at a time as fit in 8 GiB (16 bytes per pixel), so the
+ * cost grows with the canvas: quadratically as eps shrinks.
+ * polys: host arrays as for sdb_build_covering; d_x, d_y, d_attr: n device
+ * points (d_attr and d_sum may be NULL); d_count, d_sum: P device entries,
+ * zeroed by the call.  Synchronises cuda_stream.
+ * SDB_EINVAL: as sdb_build_covering, NULL outputs or coordinates, n >= 2^32,
+ * tile_bits > 14, more than 2^16 tiles (finest level - tile_bits > 8), or a
+ * polygon row whose rasterisation needs more than 128 spans or crossings.
+ * SDB_ENOMEM: device memory ran out. */
+sdb_status sdb_raster_join(const sdb_polygons *polys, uint32_t grid_bits, uint64_t eps,
+                           const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
+                           uint64_t n, uint32_t tile_bits, uint64_t *d_count, int64_t *d_sum,
+                           void *cuda_stream);
+
 /* ---------------------------------------------------------------------------
  * Batched level-of-detail queries (Sec. 1: users explore at several levels of
  * detail, an overview first, then zooms into regions of interest).  A query is

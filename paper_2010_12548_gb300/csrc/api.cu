@@ -163,6 +163,34 @@ sdb_status sdb_build_covering_ex(const sdb_polygons* polys, uint32_t grid_bits, 
   }
   uint32_t k = 0;
   SDB_TRY(finest(grid_bits, eps, &k));
+  SDB_TRY(validate_polygons(polys, grid_bits));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  sdb_covering* cov = new (std::nothrow) sdb_covering();
+  if (!cov) {
+    set_error("host allocation failed");
+    return SDB_ENOMEM;
+  }
+  if (cudaGetDevice(&cov->device) != cudaSuccess) {
+    delete cov;
+    set_error("no CUDA device");
+    return SDB_ECUDA;
+  }
+  sdb_status st = build_covering_device(polys, grid_bits, k,
+                                        (flags & SDB_COVER_BOUNDARY_FLAGS) != 0, s, cov);
+  if (st != SDB_OK) {
+    std::string msg = sdb_last_error();
+    free_covering(cov);
+    set_error("%s", msg.c_str());
+    return st;
+  }
+  *out = cov;
+  return SDB_OK;
+}
+
+}  // extern "C"
+
+namespace sdb {
+sdb_status validate_polygons(const sdb_polygons* polys, uint32_t grid_bits) {
   if (!polys || !polys->ring_off || !polys->x || !polys->y) {
     set_error("polygons or one of their arrays is NULL");
     return SDB_EINVAL;
@@ -195,27 +223,38 @@ sdb_status sdb_build_covering_ex(const sdb_polygons* polys, uint32_t grid_bits, 
       return SDB_EINVAL;
     }
   }
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  sdb_covering* cov = new (std::nothrow) sdb_covering();
-  if (!cov) {
-    set_error("host allocation failed");
-    return SDB_ENOMEM;
-  }
-  if (cudaGetDevice(&cov->device) != cudaSuccess) {
-    delete cov;
-    set_error("no CUDA device");
-    return SDB_ECUDA;
-  }
-  sdb_status st = build_covering_device(polys, grid_bits, k,
-                                        (flags & SDB_COVER_BOUNDARY_FLAGS) != 0, s, cov);
-  if (st != SDB_OK) {
-    std::string msg = sdb_last_error();
-    free_covering(cov);
-    set_error("%s", msg.c_str());
-    return st;
-  }
-  *out = cov;
   return SDB_OK;
+}
+}  // namespace sdb
+
+extern "C" {
+
+sdb_status sdb_raster_join(const sdb_polygons* polys, uint32_t grid_bits, uint64_t eps,
+                           const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
+                           uint64_t n, uint32_t tile_bits, uint64_t* d_count, int64_t* d_sum,
+                           void* cuda_stream) {
+  uint32_t k = 0;
+  SDB_TRY(finest(grid_bits, eps, &k));
+  SDB_TRY(validate_polygons(polys, grid_bits));
+  if (!d_count || (n > 0 && (!d_x || !d_y))) {
+    set_error("d_count is NULL, or n > 0 with NULL coordinates");
+    return SDB_EINVAL;
+  }
+  if (d_sum && !d_attr && n > 0) {
+    set_error("d_sum requested without d_attr");
+    return SDB_EINVAL;
+  }
+  if (n >= (1ull << 32)) {
+    set_error("n = %llu points: at most 2^32 - 1 per call", (unsigned long long)n);
+    return SDB_EINVAL;
+  }
+  if (tile_bits == 0) tile_bits = 13;
+  if (tile_bits > 14) {
+    set_error("tile_bits %u outside 1..14 (0 = default 13)", tile_bits);
+    return SDB_EINVAL;
+  }
+  return raster_join(polys, grid_bits, k, d_x, d_y, d_attr, n, tile_bits, 8ull << 30, d_count,
+                     d_sum, (cudaStream_t)cuda_stream);
 }
 
 sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* info) {

@@ -187,6 +187,17 @@ struct sdb_points {
 
 namespace sdb {
 
+// api.cu ---------------------------------------------------------------------
+sdb_status validate_polygons(const sdb_polygons* polys, uint32_t grid_bits);
+
+// raster.cu ------------------------------------------------------------------
+// Bounded Raster Join: counts (and sums, when sum != nullptr) per polygon over
+// a canvas of 2^(B-k) x 2^(B-k) pixels, cut into tiles of 2^tile_bits pixels a
+// side, as many tiles at once as fit in budget_bytes (16 bytes per pixel).
+sdb_status raster_join(const sdb_polygons* polys, uint32_t B, uint32_t k, const uint32_t* x,
+                       const uint32_t* y, const int32_t* attr, uint64_t n, uint32_t tile_bits,
+                       uint64_t budget_bytes, uint64_t* count, int64_t* sum, cudaStream_t s);
+
 // pointindex.cu --------------------------------------------------------------
 sdb_status build_point_index(sdb_points* p, uint32_t radix_bits, uint32_t spline_error,
                              cudaStream_t s);

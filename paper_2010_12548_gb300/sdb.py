@@ -100,6 +100,7 @@ def lib():
             "sdb_points_create": ([P, P, P, U64, U32, P, P], I),
             "sdb_points_free": ([P], None),
             "sdb_points_build_index": ([P, U32, U32, P], I),
+            "sdb_raster_join": ([P, U32, U64, P, P, P, U64, U32, P, P, P], I),
             "sdb_points_aggregate": ([P, P, I, P, P, P], I),
             "sdb_points_index_stats": ([P, P, P, P, P], I),
             "sdb_batch_create": ([P, P, P, U32, P, U64, P, P], I),
@@ -199,6 +200,20 @@ def build_covering(polys, grid_bits: int, eps: int, stream=None, flags: int = 0)
     _check(lib().sdb_build_covering_ex(C.byref(sp), grid_bits, int(eps), int(flags),
                                        _stream(stream), C.byref(out)))
     return Covering(out.value)
+
+
+def raster_join(polys, grid_bits: int, eps: int, x, y, attr, count, sum_=None, tile_bits: int = 0,
+                stream=None):
+    """sdb_raster_join (Bounded Raster Join) on device tensors; polys as for
+    build_covering."""
+    off = np.ascontiguousarray(polys.ring_off, np.uint32)
+    px = np.ascontiguousarray(polys.x, np.uint32)
+    py = np.ascontiguousarray(polys.y, np.uint32)
+    sp = _Polys(len(off) - 1, _np_ptr(off), _np_ptr(px), _np_ptr(py))
+    n = x.numel() if x is not None else 0
+    _check(lib().sdb_raster_join(C.byref(sp), grid_bits, int(eps), _dptr(x, 4), _dptr(y, 4),
+                                 _dptr(attr, 4), n, tile_bits, _dptr(count, 8), _dptr(sum_, 8),
+                                 _stream(stream)))
 
 
 def covering_build_index(cov: Covering, leaf_bits: int, stream=None):
