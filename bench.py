@@ -13,7 +13,8 @@ and SUM (device-resident points).
 The metric counts point-joins: points x eps levels per second.
 
 Besides the timed steps the script measures, outside the timed region, the
-join alone per eps for the learned and the binary-search lookups, result
+join alone per eps for the learned and the binary-search lookups, the
+Bounded Raster Join (canvas blend + conservative rasterisation), result
 range estimation (boundary-flagged coverings and the range join), point-indexed
 aggregation (sorted points, prefix sums, binary search vs RadixSpline), the
 end-to-end rate through the host-buffer entry point (points copied from pinned
@@ -64,9 +65,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps (no join-only, e2e, CPU, batch or serving legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--legs", default="join,range,e2e,cpu,batch,pointindex,serve",
-                    help="extra legs: join (lookups alone), range (result range estimation), "
-                         "e2e, cpu, batch, pointindex (range counting over sorted points), serve")
+    ap.add_argument("--legs", default="join,raster,range,e2e,cpu,batch,pointindex,serve",
+                    help="extra legs: join (lookups alone), raster (Bounded Raster Join), range "
+                         "(result range estimation), e2e, cpu, batch, pointindex (range "
+                         "counting over sorted points), serve")
     ap.add_argument("--pi-points", type=int, default=500_000_000)
     ap.add_argument("--lod-points", type=int, default=200_000_000)
     ap.add_argument("--lod-queries", type=int, default=4096)
@@ -352,6 +354,22 @@ def main():
             joins[str(eps)] = row
             c.free()
         res["join_only"] = joins
+    # ---- Bounded Raster Join (Sec. 5.2): canvas blend + conservative raster mask
+    if "raster" in legs:
+        rows = {}
+        P_ = w.polygons.n
+        rc, rs_ = (torch.zeros(P_, dtype=torch.int64, device=dev) for _ in range(2))
+        for i, eps in enumerate(w.eps):
+            reps = 3 if eps >= 1024 else 1
+            ms = timed(torch, stream, lambda: sdb.raster_join(w.polygons, 24, eps, x, y, a, rc, rs_,
+                                                              0, stream), reps)
+            F = 24 - int(np.log2(eps)) + 1
+            rows[str(eps)] = {"raster_join_ms": ms, "canvas_pixels": 4 ** F,
+                              "tiles": max(1, 4 ** (F - 13)),
+                              "covering_build_index_plus_join_ms": build_ms[i] + join_ms[i],
+                              "matches_covering_join": bool(torch.equal(rc, cnt[i])
+                                                            and torch.equal(rs_, sm[i]))}
+        res["raster_join"] = rows
     # ---- result range estimation (Sec. 6): flagged coverings and the range join
     if "range" in legs:
         reps = 5
