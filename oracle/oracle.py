@@ -51,19 +51,19 @@ def lib():
         L.orc_finest_k.argtypes = [U64, U32, C.POINTER(C.c_uint32)]
         L.orc_finest_k.restype = I32
         L.orc_curve_many.argtypes = [I32, U32, U64, P, P, P]
-        L.orc_classify_many.argtypes = [P, P, P, U32, U64, P, P, I64, P]
-        L.orc_cover.argtypes = [U32, P, P, P, U32, U64, I32, I32]
+        L.orc_classify_many.argtypes = [P, P, P, P, U32, U64, P, P, I64, P]
+        L.orc_cover.argtypes = [U32, P, P, P, P, U32, U64, I32, I32]
         L.orc_cover.restype = P
         L.orc_cover_sizes.argtypes = [P, P, P, P, P, P]
         L.orc_cover_export.argtypes = [P, P, P, P]
         L.orc_cover_free.argtypes = [P]
         L.orc_join_o1.argtypes = [P, U64, P, P, P, P, P, P, P, P, I32]
-        L.orc_join_o2.argtypes = [U32, P, P, P, U32, U64, U64, P, P, P, P, P, P, P, P, P, I64,
-                                  I32]
+        L.orc_join_o2.argtypes = [U32, P, P, P, P, U32, U64, U64, P, P, P, P, P, P, P, P, P,
+                                  I64, I32, I32]
         L.orc_join_o2.restype = I32
         L.orc_point_index_aggregate.argtypes = [P, U64, P, P, P, P, P, I32]
-        L.orc_join_exact.argtypes = [U32, P, P, P, U32, U64, P, P, P, P, P, P, I64, I32]
-        L.orc_near_boundary.argtypes = [P, P, P, U32, U32, U32, U64]
+        L.orc_join_exact.argtypes = [U32, P, P, P, P, U32, U64, P, P, P, P, P, P, I64, I32]
+        L.orc_near_boundary.argtypes = [P, P, P, P, U32, U32, U32, U64]
         L.orc_near_boundary.restype = I32
         _lib = L
     return _lib
@@ -75,6 +75,15 @@ def _p(a):
 
 def _u32(a):
     return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def _shape(polys):
+    """(n_polygons, poly_ring_off or None, ring_off, x, y) of a polygon set; a set
+    with poly_ring_off holds polygons of several rings (outer rings and holes,
+    even-odd region)."""
+    pro = getattr(polys, "poly_ring_off", None)
+    pro = None if pro is None else _u32(pro)
+    return polys.n, pro, _u32(polys.ring_off), _u32(polys.x), _u32(polys.y)
 
 
 def finest_k(eps: int, grid_bits: int):
@@ -97,8 +106,9 @@ def classify(polys, j: int, x0, y0, side: int) -> np.ndarray:
     x0 = np.ascontiguousarray(x0, np.int64)
     y0 = np.ascontiguousarray(y0, np.int64)
     out = np.empty(len(x0), np.uint8)
-    lib().orc_classify_many(_p(_u32(polys.ring_off)), _p(_u32(polys.x)), _p(_u32(polys.y)), j,
-                            len(x0), _p(x0), _p(y0), side, _p(out))
+    _, pro, off, vx, vy = _shape(polys)
+    lib().orc_classify_many(_p(pro), _p(off), _p(vx), _p(vy), j, len(x0), _p(x0), _p(y0), side,
+                            _p(out))
     return out
 
 
@@ -164,12 +174,14 @@ class Covering:
 
 
 def cover(polys, eps: int, which: int = HILBERT, grid_bits: int | None = None,
-          flagged: bool = False) -> Covering:
+          flagged: bool = False, noncons: bool = False) -> Covering:
     """O1: recursive quadtree covering of every polygon, swept into canonical ranges
-    (flagged: list entries carry bit 31 on boundary cells, Sec. 6)."""
+    (flagged: list entries carry bit 31 on boundary cells, Sec. 6; noncons: a
+    finest boundary cell is kept only when its centre is in the polygon, Sec. 2.2)."""
     B = polys.grid_bits if grid_bits is None else grid_bits
-    off, vx, vy = _u32(polys.ring_off), _u32(polys.x), _u32(polys.y)
-    h = lib().orc_cover(len(off) - 1, _p(off), _p(vx), _p(vy), B, int(eps), which, int(flagged))
+    P, pro, off, vx, vy = _shape(polys)
+    h = lib().orc_cover(P, _p(pro), _p(off), _p(vx), _p(vy), B, int(eps), which,
+                        int(flagged) | (2 if noncons else 0))
     if not h:
         raise ValueError("invalid covering arguments")
     R, nids, nrec = C.c_uint64(), C.c_uint64(), C.c_uint64()
@@ -179,12 +191,12 @@ def cover(polys, eps: int, which: int = HILBERT, grid_bits: int | None = None,
     loff = np.empty(R.value + 1, np.uint32)
     ids = np.empty(nids.value, np.uint32)
     lib().orc_cover_export(h, _p(start), _p(loff), _p(ids))
-    return Covering(start, loff, ids, nrec.value, F.value, k.value, B, len(off) - 1, which,
+    return Covering(start, loff, ids, nrec.value, F.value, k.value, B, P, which,
                     bool(flagged), h)
 
 
 def join_o2(polys, eps: int, pts, *, threads: int = 1, member: bool = False, only: int = -1,
-            grid_bits: int | None = None, boundary_sums: bool = False):
+            grid_bits: int | None = None, boundary_sums: bool = False, noncons: bool = False):
     """O2: per point, the definitional test 'closed finest cell meets closed polygon'.
 
     Returns (count, sum, boundary_count[, boundary_sum, boundary_abs][, member])."""
@@ -198,9 +210,10 @@ def join_o2(polys, eps: int, pts, *, threads: int = 1, member: bool = False, onl
     bs = np.zeros(P, np.int64) if boundary_sums else None
     ba = np.zeros(P, np.uint64) if boundary_sums else None
     mem = np.zeros(len(x), np.uint8) if member else None
-    rc = lib().orc_join_o2(P, _p(_u32(polys.ring_off)), _p(_u32(polys.x)), _p(_u32(polys.y)), B,
+    _, pro, off, vx, vy = _shape(polys)
+    rc = lib().orc_join_o2(P, _p(pro), _p(off), _p(vx), _p(vy), B,
                            int(eps), len(x), _p(x), _p(y), _p(a), _p(cnt), _p(sm), _p(bnd),
-                           _p(bs), _p(ba), _p(mem), only, threads)
+                           _p(bs), _p(ba), _p(mem), only, threads, 2 if noncons else 0)
     if rc != 0:
         raise ValueError("invalid O2 arguments")
     out = (cnt, sm, bnd) + ((bs, ba) if boundary_sums else ())
@@ -228,7 +241,8 @@ def join_exact(polys, pts, *, threads: int = 1, member: bool = False, only: int 
     cnt = np.zeros(P, np.uint64)
     sm = np.zeros(P, np.int64)
     mem = np.zeros(len(x), np.uint8) if member else None
-    lib().orc_join_exact(P, _p(_u32(polys.ring_off)), _p(_u32(polys.x)), _p(_u32(polys.y)),
+    _, pro, off, vx, vy = _shape(polys)
+    lib().orc_join_exact(P, _p(pro), _p(off), _p(vx), _p(vy),
                          polys.grid_bits, len(x), _p(x), _p(y), _p(a), _p(cnt), _p(sm), _p(mem),
                          only, threads)
     return (cnt, sm, mem) if member else (cnt, sm)
@@ -236,5 +250,6 @@ def join_exact(polys, pts, *, threads: int = 1, member: bool = False, only: int 
 
 def near_boundary(polys, j: int, px: int, py: int, eps: int) -> bool:
     """Exact: is (px, py) within distance eps of polygon j's boundary?"""
-    return bool(lib().orc_near_boundary(_p(_u32(polys.ring_off)), _p(_u32(polys.x)),
-                                        _p(_u32(polys.y)), j, int(px), int(py), int(eps)))
+    _, pro, off, vx, vy = _shape(polys)
+    return bool(lib().orc_near_boundary(_p(pro), _p(off), _p(vx), _p(vy), j, int(px), int(py),
+                                        int(eps)))

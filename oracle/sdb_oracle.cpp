@@ -46,23 +46,50 @@ typedef int64_t i64;
 typedef unsigned __int128 u128;
 typedef __int128 i128;
 
+// One polygon: one or more closed rings (outer boundaries and holes); the
+// region is the set of points with an odd crossing number over all rings, plus
+// the rings themselves (closed).  Edge i runs from vertex i to vertex nxt[i],
+// the next vertex of the same ring.
 struct Ring {
   std::vector<i64> x, y;
+  std::vector<size_t> nxt;
   i64 minx, miny, maxx, maxy;
 };
+
+void finish_ring(Ring& r) {
+  r.minx = *std::min_element(r.x.begin(), r.x.end());
+  r.maxx = *std::max_element(r.x.begin(), r.x.end());
+  r.miny = *std::min_element(r.y.begin(), r.y.end());
+  r.maxy = *std::max_element(r.y.begin(), r.y.end());
+}
+
+void add_ring(Ring& r, const uint32_t* vx, const uint32_t* vy, uint32_t a, uint32_t b) {
+  const size_t base = r.x.size();
+  for (uint32_t v = a; v < b; ++v) {
+    r.x.push_back(vx[v]);
+    r.y.push_back(vy[v]);
+    r.nxt.push_back(v + 1 < b ? base + (v - a) + 1 : base);
+  }
+}
 
 std::vector<Ring> load_rings(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint32_t* vy) {
   std::vector<Ring> rs(P);
   for (uint32_t j = 0; j < P; ++j) {
-    Ring& r = rs[j];
-    for (uint32_t v = off[j]; v < off[j + 1]; ++v) {
-      r.x.push_back(vx[v]);
-      r.y.push_back(vy[v]);
-    }
-    r.minx = *std::min_element(r.x.begin(), r.x.end());
-    r.maxx = *std::max_element(r.x.begin(), r.x.end());
-    r.miny = *std::min_element(r.y.begin(), r.y.end());
-    r.maxy = *std::max_element(r.y.begin(), r.y.end());
+    add_ring(rs[j], vx, vy, off[j], off[j + 1]);
+    finish_ring(rs[j]);
+  }
+  return rs;
+}
+
+// polygon j = rings [poly_ring_off[j], poly_ring_off[j+1]), ring r = vertices
+// [ring_off[r], ring_off[r+1])
+std::vector<Ring> load_multi(uint32_t P, const uint32_t* poly_ring_off, const uint32_t* ring_off,
+                             const uint32_t* vx, const uint32_t* vy) {
+  std::vector<Ring> rs(P);
+  for (uint32_t j = 0; j < P; ++j) {
+    for (uint32_t r = poly_ring_off[j]; r < poly_ring_off[j + 1]; ++r)
+      add_ring(rs[j], vx, vy, ring_off[r], ring_off[r + 1]);
+    finish_ring(rs[j]);
   }
   return rs;
 }
@@ -174,18 +201,20 @@ bool segment_meets_square(i64 ax, i64 ay, i64 bx, i64 by, i64 x0, i64 y0, i64 x1
 // point (px, py) in the closed polygon: on an edge, or odd crossing number of
 // the rightward horizontal ray (an edge counts when one endpoint is strictly
 // above py and the other is not, and the edge's x at height py exceeds px).
-bool inside_closed(const Ring& r, i64 px, i64 py) {
+// The point is given in units of 1/m (m = 1 or 2: half-integer points such as
+// cell centres); the ring is scaled by m on the fly.
+bool inside_closed_scaled(const Ring& r, i64 px, i64 py, i64 m) {
   size_t n = r.x.size();
   for (size_t i = 0; i < n; ++i) {
-    size_t k = (i + 1) % n;
-    if (orient(r.x[i], r.y[i], r.x[k], r.y[k], px, py) == 0 &&
-        between(r.x[i], r.y[i], r.x[k], r.y[k], px, py))
+    size_t k = r.nxt[i];
+    if (orient(m * r.x[i], m * r.y[i], m * r.x[k], m * r.y[k], px, py) == 0 &&
+        between(m * r.x[i], m * r.y[i], m * r.x[k], m * r.y[k], px, py))
       return true;
   }
   bool odd = false;
   for (size_t i = 0; i < n; ++i) {
-    size_t k = (i + 1) % n;
-    i64 ax = r.x[i], ay = r.y[i], bx = r.x[k], by = r.y[k];
+    size_t k = r.nxt[i];
+    i64 ax = m * r.x[i], ay = m * r.y[i], bx = m * r.x[k], by = m * r.y[k];
     if ((ay > py) != (by > py)) {
       // x_cross = ax + (py - ay) (bx - ax) / (by - ay)  >  px, multiplied out
       i64 num = (ax - px) * (by - ay) + (py - ay) * (bx - ax);
@@ -196,6 +225,8 @@ bool inside_closed(const Ring& r, i64 px, i64 py) {
   return odd;
 }
 
+bool inside_closed(const Ring& r, i64 px, i64 py) { return inside_closed_scaled(r, px, py, 1); }
+
 enum { EXTERIOR = 0, INTERIOR = 1, BOUNDARY = 2 };
 
 // Sec. 2.2 classification of the closed square [x0, x0+side] x [y0, y0+side]
@@ -205,7 +236,7 @@ int classify(const Ring& r, i64 x0, i64 y0, i64 side) {
   if (r.maxx < x0 || r.minx > x1 || r.maxy < y0 || r.miny > y1) return EXTERIOR;
   size_t n = r.x.size();
   for (size_t i = 0; i < n; ++i) {
-    size_t k = (i + 1) % n;
+    size_t k = r.nxt[i];
     if (segment_meets_square(r.x[i], r.y[i], r.x[k], r.y[k], x0, y0, x1, y1)) return BOUNDARY;
   }
   // no boundary point in the square: the whole square lies on one side, and its
@@ -220,11 +251,17 @@ struct Rec {
   bool boundary;    // a boundary cell at the finest level (else an interior cell)
 };
 
+// noncons (Sec. 2.2, non-conservative raster): a finest boundary cell is kept
+// only when its centre lies in the closed polygon (centres are half-integers
+// when the side is 1, so the test runs in doubled coordinates).
 void cover_rec(const Ring& r, uint32_t j, uint32_t B, uint32_t F, uint32_t L, uint64_t cx,
-               uint64_t cy, int which, std::vector<Rec>& out) {
+               uint64_t cy, int which, bool noncons, std::vector<Rec>& out) {
   i64 side = (i64)1 << (B - L);
   int c = classify(r, (i64)cx * side, (i64)cy * side, side);
   if (c == EXTERIOR) return;
+  if (L == F && c == BOUNDARY && noncons &&
+      !inside_closed_scaled(r, 2 * (i64)cx * side + side, 2 * (i64)cy * side + side, 2))
+    return;
   if (c == INTERIOR || L == F) {
     // interior cell (any level) or boundary cell at the finest level: all of its
     // finest-level descendants, which by the curve's prefix property are the
@@ -236,7 +273,7 @@ void cover_rec(const Ring& r, uint32_t j, uint32_t B, uint32_t F, uint32_t L, ui
   }
   for (uint64_t dy = 0; dy < 2; ++dy)
     for (uint64_t dx = 0; dx < 2; ++dx)
-      cover_rec(r, j, B, F, L + 1, 2 * cx + dx, 2 * cy + dy, which, out);
+      cover_rec(r, j, B, F, L + 1, 2 * cx + dx, 2 * cy + dy, which, noncons, out);
 }
 
 struct Covering {
@@ -254,9 +291,10 @@ struct Covering {
 // when the interval lies in a boundary cell of that polygon, and ranges split
 // where the flags change as well.
 Covering* build_covering(const std::vector<Ring>& rings, uint32_t B, uint32_t F, uint32_t k, int which,
-                         bool flagged) {
+                         bool flagged, bool noncons) {
   std::vector<Rec> recs;
-  for (uint32_t j = 0; j < rings.size(); ++j) cover_rec(rings[j], j, B, F, 0, 0, 0, which, recs);
+  for (uint32_t j = 0; j < rings.size(); ++j)
+    cover_rec(rings[j], j, B, F, 0, 0, 0, which, noncons, recs);
   uint64_t top = (uint64_t)1 << (2 * F);
   // position -> (poly | boundary << 31, +1 / -1)
   std::map<uint64_t, std::vector<std::pair<uint32_t, int>>> ev;
@@ -366,19 +404,28 @@ void orc_curve_many(int which, uint32_t order, uint64_t n, const uint32_t* x, co
 
 // 0 = exterior, 1 = interior, 2 = boundary, for n closed squares of one side
 // against polygon j
-void orc_classify_many(const uint32_t* off, const uint32_t* vx, const uint32_t* vy, uint32_t j,
-                       uint64_t n, const int64_t* x0, const int64_t* y0, int64_t side, uint8_t* out) {
-  uint32_t sub[2] = {0, off[j + 1] - off[j]};
-  std::vector<Ring> one = load_rings(1, sub, vx + off[j], vy + off[j]);
-  for (uint64_t i = 0; i < n; ++i) out[i] = (uint8_t)classify(one[0], x0[i], y0[i], side);
+// poly_ring_off as for orc_cover (NULL: one ring per polygon)
+void orc_classify_many(const uint32_t* poly_ring_off, const uint32_t* off, const uint32_t* vx,
+                       const uint32_t* vy, uint32_t j, uint64_t n, const int64_t* x0,
+                       const int64_t* y0, int64_t side, uint8_t* out) {
+  Ring one;
+  const uint32_t r0 = poly_ring_off ? poly_ring_off[j] : j;
+  const uint32_t r1 = poly_ring_off ? poly_ring_off[j + 1] : j + 1;
+  for (uint32_t r = r0; r < r1; ++r) add_ring(one, vx, vy, off[r], off[r + 1]);
+  finish_ring(one);
+  for (uint64_t i = 0; i < n; ++i) out[i] = (uint8_t)classify(one, x0[i], y0[i], side);
 }
 
-void* orc_cover(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint32_t* vy,
-                uint32_t B, uint64_t eps, int which, int flagged) {
+// mode: bit 0 boundary flags (Sec. 6), bit 1 non-conservative (Sec. 2.2).
+// poly_ring_off == NULL: one ring per polygon (ring_off indexed by polygon).
+void* orc_cover(uint32_t P, const uint32_t* poly_ring_off, const uint32_t* ring_off,
+                const uint32_t* vx, const uint32_t* vy, uint32_t B, uint64_t eps, int which,
+                int mode) {
   uint32_t k;
   if (B < 1 || B > 30 || finest_k(eps, B, &k) != 0) return nullptr;
-  std::vector<Ring> rs = load_rings(P, off, vx, vy);
-  return build_covering(rs, B, B - k, k, which, flagged != 0);
+  std::vector<Ring> rs = poly_ring_off ? load_multi(P, poly_ring_off, ring_off, vx, vy)
+                                       : load_rings(P, ring_off, vx, vy);
+  return build_covering(rs, B, B - k, k, which, (mode & 1) != 0, (mode & 2) != 0);
 }
 
 void orc_cover_sizes(void* h, uint64_t* R, uint64_t* nids, uint64_t* nrec, uint32_t* F, uint32_t* k) {
@@ -441,13 +488,18 @@ void orc_join_o1(void* h, uint64_t n, const uint32_t* x, const uint32_t* y, cons
 // (nullable): those points' attribute sum and sum of magnitudes.
 // member (nullable, n bytes): per point, 1 if it counts for polygon `only`
 // (only >= 0) or for any polygon (only < 0).
-int orc_join_o2(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint32_t* vy, uint32_t B,
-                uint64_t eps, uint64_t n, const uint32_t* x, const uint32_t* y, const int32_t* attr,
-                uint64_t* count, int64_t* sum, uint64_t* bnd_count, int64_t* bnd_sum,
-                uint64_t* bnd_abs, uint8_t* member, int64_t only, int threads) {
+// mode bit 1: non-conservative (a boundary cell counts only when its centre
+// lies in the closed polygon).  poly_ring_off as for orc_cover.
+int orc_join_o2(uint32_t P, const uint32_t* poly_ring_off, const uint32_t* off, const uint32_t* vx,
+                const uint32_t* vy, uint32_t B, uint64_t eps, uint64_t n, const uint32_t* x,
+                const uint32_t* y, const int32_t* attr, uint64_t* count, int64_t* sum,
+                uint64_t* bnd_count, int64_t* bnd_sum, uint64_t* bnd_abs, uint8_t* member,
+                int64_t only, int threads, int mode) {
   uint32_t k;
   if (B < 1 || B > 30 || finest_k(eps, B, &k) != 0) return -1;
-  std::vector<Ring> rs = load_rings(P, off, vx, vy);
+  std::vector<Ring> rs = poly_ring_off ? load_multi(P, poly_ring_off, off, vx, vy)
+                                       : load_rings(P, off, vx, vy);
+  const bool noncons = (mode & 2) != 0;
   BucketGrid bg(rs, B);
   i64 s = (i64)1 << k;
   if (threads < 1) threads = 1;
@@ -467,6 +519,8 @@ int orc_join_o2(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint3
         for (uint32_t j : cand) {
           int c = classify(rs[j], x0, y0, s);
           if (c == EXTERIOR) continue;
+          if (c == BOUNDARY && noncons && !inside_closed_scaled(rs[j], 2 * x0 + s, 2 * y0 + s, 2))
+            continue;
           const int64_t av = attr ? attr[i] : 0;
           tc[t][j] += 1;
           ts[t][j] += av;
@@ -540,10 +594,12 @@ void orc_point_index_aggregate(void* h, uint64_t n, const uint32_t* x, const uin
 }
 
 // exact closed point-in-polygon join (the answer the approximation bounds)
-void orc_join_exact(uint32_t P, const uint32_t* off, const uint32_t* vx, const uint32_t* vy,
-                    uint32_t B, uint64_t n, const uint32_t* x, const uint32_t* y, const int32_t* attr,
-                    uint64_t* count, int64_t* sum, uint8_t* member, int64_t only, int threads) {
-  std::vector<Ring> rs = load_rings(P, off, vx, vy);
+void orc_join_exact(uint32_t P, const uint32_t* poly_ring_off, const uint32_t* off,
+                    const uint32_t* vx, const uint32_t* vy, uint32_t B, uint64_t n,
+                    const uint32_t* x, const uint32_t* y, const int32_t* attr, uint64_t* count,
+                    int64_t* sum, uint8_t* member, int64_t only, int threads) {
+  std::vector<Ring> rs = poly_ring_off ? load_multi(P, poly_ring_off, off, vx, vy)
+                                       : load_rings(P, off, vx, vy);
   BucketGrid bg(rs, B);
   if (threads < 1) threads = 1;
   std::vector<std::vector<uint64_t>> tc(threads, std::vector<uint64_t>(P, 0));
@@ -576,11 +632,15 @@ void orc_join_exact(uint32_t P, const uint32_t* off, const uint32_t* vx, const u
 
 // Sec. 2.2 distance bound: is the point within distance eps of polygon j's
 // boundary?  Exact: squared distances compared in 128-bit integers.
-int orc_near_boundary(const uint32_t* off, const uint32_t* vx, const uint32_t* vy, uint32_t j,
-                      uint32_t px, uint32_t py, uint64_t eps) {
+int orc_near_boundary(const uint32_t* poly_ring_off, const uint32_t* off, const uint32_t* vx,
+                      const uint32_t* vy, uint32_t j, uint32_t px, uint32_t py, uint64_t eps) {
   i128 e2 = (i128)eps * (i128)eps;
-  for (uint32_t v = off[j]; v < off[j + 1]; ++v) {
-    uint32_t w = (v + 1 < off[j + 1]) ? v + 1 : off[j];
+  // rings of polygon j (one ring when poly_ring_off is NULL)
+  const uint32_t r0 = poly_ring_off ? poly_ring_off[j] : j;
+  const uint32_t r1 = poly_ring_off ? poly_ring_off[j + 1] : j + 1;
+  for (uint32_t rr = r0; rr < r1; ++rr)
+  for (uint32_t v = off[rr]; v < off[rr + 1]; ++v) {
+    uint32_t w = (v + 1 < off[rr + 1]) ? v + 1 : off[rr];
     i64 ax = vx[v], ay = vy[v], bx = vx[w], by = vy[w];
     i64 dx = bx - ax, dy = by - ay;
     i64 qx = (i64)px - ax, qy = (i64)py - ay;

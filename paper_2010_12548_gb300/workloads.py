@@ -63,6 +63,24 @@ class Polygons:
 
 
 @dataclass
+class MultiPolygons:
+    """Polygons of one or more rings (outer boundaries and holes), CSR layout:
+    polygon j owns rings poly_ring_off[j]..poly_ring_off[j+1], ring r the
+    vertices ring_off[r]..ring_off[r+1] of x/y (no closing duplicate).  A
+    polygon's region is the set of points with an odd crossing number over all
+    of its rings, together with the rings themselves."""
+    poly_ring_off: np.ndarray  # uint32 [P+1]
+    ring_off: np.ndarray       # uint32 [R+1]
+    x: np.ndarray              # uint32 [V]
+    y: np.ndarray              # uint32 [V]
+    grid_bits: int
+
+    @property
+    def n(self) -> int:
+        return len(self.poly_ring_off) - 1
+
+
+@dataclass
 class Points:
     x: np.ndarray     # uint32 [N]
     y: np.ndarray     # uint32 [N]
@@ -183,6 +201,59 @@ def star_polygons(rng: np.random.Generator, n: int, grid_bits: int,
         cs.append(c.astype(np.int64))
     return Polygons(np.asarray(off, np.uint32), np.concatenate(xs).astype(np.uint32),
                     np.concatenate(ys).astype(np.uint32), grid_bits, np.asarray(cs, np.int64))
+
+
+def _ring_around(rng, c, k, rlo, rhi):
+    """k vertices at evenly spaced angles (jitter up to a quarter of the
+    spacing, so consecutive angles differ by at most 1.5 spacings) with radii
+    uniform in [rlo, rhi] around integer centre c."""
+    step = 2 * math.pi / k
+    th = np.arange(k) * step + rng.uniform(-0.25, 0.25, size=k) * step + rng.uniform(0, step)
+    r = rng.uniform(rlo, rhi, size=k)
+    return (np.rint(c[0] + r * np.cos(th)).astype(np.int64),
+            np.rint(c[1] + r * np.sin(th)).astype(np.int64))
+
+
+def holed_stars(rng: np.random.Generator, n: int, grid_bits: int, nverts=(6, 24),
+                radius=(2 ** 10, 2 ** 11), p_hole: float = 0.5,
+                p_part: float = 0.35) -> MultiPolygons:
+    """Star polygons with holes and second parts (multi-polygons).
+
+    The outer ring has k >= 6 vertices at jittered even angles, so no gap
+    exceeds 90 degrees and every edge stays at least cos(45 deg) * r_min - 1
+    from the centre; a hole (probability p_hole) is a ring around the same
+    centre with radii at most r_min / 2, strictly inside.  A second part
+    (probability p_part) is a smaller ring whose centre lies more than the
+    sum of both circumradii away, so the parts are disjoint.  Polygons of the
+    set may overlap each other."""
+    G = 2 ** grid_bits
+    r_hi = radius[1]
+    margin = int(3 * r_hi) + 2
+    if 2 * margin >= G:
+        raise ValueError("radius too large for the grid")
+    xs, ys, roff, poff = [], [], [0], [0]
+
+    def add(vx, vy):
+        xs.append(vx)
+        ys.append(vy)
+        roff.append(roff[-1] + len(vx))
+
+    for _ in range(n):
+        k = int(rng.integers(max(6, nverts[0]), nverts[1] + 1))
+        c = rng.integers(margin, G - 1 - margin, size=2)
+        rlo = rng.uniform(radius[0], r_hi)
+        add(*_ring_around(rng, c, k, rlo, r_hi))
+        if rng.random() < p_hole:
+            add(*_ring_around(rng, c, int(rng.integers(3, 9)), rlo / 8, rlo / 2))
+        if rng.random() < p_part:
+            ang = rng.uniform(0, 2 * math.pi)
+            d = r_hi + r_hi / 2 + 4
+            c2 = np.rint(c + d * np.array([math.cos(ang), math.sin(ang)])).astype(np.int64)
+            add(*_ring_around(rng, c2, int(rng.integers(3, 9)), r_hi / 6, r_hi / 2))
+        poff.append(len(roff) - 1)
+    return MultiPolygons(np.asarray(poff, np.uint32), np.asarray(roff, np.uint32),
+                         np.concatenate(xs).astype(np.uint32), np.concatenate(ys).astype(np.uint32),
+                         grid_bits)
 
 
 # --------------------------------------------------------------------------

@@ -374,6 +374,127 @@ def test_point_index_equals_point_stream(orc, which):
         assert np.array_equal(fl[0], want[0]) and np.array_equal(fl[1], want[1]), eps
 
 
+# ------------------------------------- non-conservative raster (Sec. 2.2)
+
+def multi_of(polys, B):
+    """MultiPolygons from a list of polygons, each a list of rings."""
+    pro, roff, xs, ys = [0], [0], [], []
+    for rings in polys:
+        for r in rings:
+            xs += [p[0] for p in r]
+            ys += [p[1] for p in r]
+            roff.append(len(xs))
+        pro.append(len(roff) - 1)
+    return W.MultiPolygons(np.array(pro, np.uint32), np.array(roff, np.uint32),
+                           np.array(xs, np.uint32), np.array(ys, np.uint32), B)
+
+
+def test_noncons_handworked(orc):
+    """Hand-derived non-conservative counts (centre rule) of both golden files."""
+    for fname, make in (("handworked_b4.json", lambda ring, B: polys_of([ring], B)),
+                        ("handworked_holes_b4.json", lambda rings, B: multi_of([rings], B))):
+        with open(os.path.join(GOLD, fname)) as f:
+            g = json.load(f)
+        B = g["grid_bits"]
+        pts = lattice(B)
+        for name, shape in g["polygons"].items():
+            P = make(shape, B)
+            for c in g["cases"]:
+                want = c["noncons"][name]
+                for which in (0, 1):
+                    cnt, sm = orc.cover(P, c["eps"], which, noncons=True).join(pts.x, pts.y,
+                                                                               pts.attr)
+                    assert int(cnt[0]) == want and int(sm[0]) == want, (name, c, which)
+                assert int(orc.join_o2(P, c["eps"], pts, noncons=True)[0][0]) == want
+
+
+def test_noncons_o1_o2_and_eps_bound(orc, stars_small):
+    """Non-conservative covering join = definitional test; every false negative
+    and false positive lies within eps of the boundary; never more than the
+    conservative count."""
+    w = stars_small
+    P, pts = w.polygons, w.points
+    for eps in (64, 200, 1000):
+        cons = orc.join_o2(P, eps, pts)[0]
+        want = orc.join_o2(P, eps, pts, noncons=True)
+        assert (want[0] <= cons).all()
+        for which in (0, 1):
+            got = orc.cover(P, eps, which, noncons=True).join(pts.x, pts.y, pts.attr)
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+        for j in range(P.n):
+            _, _, _, am = orc.join_o2(P, eps, pts, member=True, only=j, noncons=True)
+            _, _, em = orc.join_exact(P, pts, member=True, only=j)
+            for i in np.nonzero(am.astype(bool) != em.astype(bool))[0]:
+                assert orc.near_boundary(P, j, int(pts.x[i]), int(pts.y[i]), eps)
+
+
+# ----------------------------------- multi-polygons and holes (Sec. 5.2)
+
+def test_holes_handworked(orc):
+    with open(os.path.join(GOLD, "handworked_holes_b4.json")) as f:
+        g = json.load(f)
+    B = g["grid_bits"]
+    pts = lattice(B)
+    for name, rings in g["polygons"].items():
+        P = multi_of([rings], B)
+        assert int(orc.join_exact(P, pts)[0][0]) == g["exact"][name]
+        for c in g["cases"]:
+            for which in (0, 1):
+                cnt, sm = orc.cover(P, c["eps"], which).join(pts.x, pts.y, pts.attr)
+                assert int(cnt[0]) == c[name] and int(sm[0]) == c[name], (name, c, which)
+            assert int(orc.join_o2(P, c["eps"], pts)[0][0]) == c[name]
+
+
+def test_multi_classify_is_ring_combination(orc):
+    """A polygon of several rings classifies a cell as: boundary when any ring
+    does; otherwise interior when an odd number of its rings contain the cell
+    (even-odd region), else exterior -- checked against the single-ring
+    classification of each ring."""
+    B = 12
+    M = W.holed_stars(np.random.default_rng(21), 12, B, radius=(2 ** 7, 2 ** 8))
+    rings = W.Polygons(M.ring_off, M.x, M.y, B)
+    rng = np.random.default_rng(22)
+    for side in (1, 8, 64, 512):
+        x0 = rng.integers(0, 2 ** B - side, 3000) // side * side
+        y0 = rng.integers(0, 2 ** B - side, 3000) // side * side
+        for j in range(M.n):
+            got = orc.classify(M, j, x0, y0, side)
+            cls = [orc.classify(rings, r, x0, y0, side)
+                   for r in range(M.poly_ring_off[j], M.poly_ring_off[j + 1])]
+            bnd = np.any([c == 2 for c in cls], axis=0)
+            odd = (np.sum([c == 1 for c in cls], axis=0) % 2) == 1
+            want = np.where(bnd, 2, np.where(odd, 1, 0))
+            assert np.array_equal(got, want), (side, j)
+
+
+def test_multi_o1_o2_exact(orc):
+    """Holed and multi-part stars: covering join = definitional test (both
+    curves, conservative and non-conservative); the exact join never exceeds
+    the conservative one, and its misses are within eps."""
+    B = 14
+    M = W.holed_stars(np.random.default_rng(31), 10, B, radius=(2 ** 8, 2 ** 9))
+    rng = np.random.default_rng(32)
+    pts = W.Points(rng.integers(0, 2 ** B, 40_000, dtype=np.uint32),
+                   rng.integers(0, 2 ** B, 40_000, dtype=np.uint32),
+                   rng.integers(-1000, 1000, 40_000).astype(np.int32), B)
+    ex = orc.join_exact(M, pts)
+    for eps in (3, 40, 300):
+        for nc in (False, True):
+            want = orc.join_o2(M, eps, pts, noncons=nc)
+            for which in (0, 1):
+                got = orc.cover(M, eps, which, noncons=nc).join(pts.x, pts.y, pts.attr)
+                assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+            if not nc:
+                assert (ex[0] <= want[0]).all()
+        for j in range(M.n):
+            _, _, _, am = orc.join_o2(M, eps, pts, member=True, only=j)
+            _, _, em = orc.join_exact(M, pts, member=True, only=j)
+            am, em = am.astype(bool), em.astype(bool)
+            assert not np.any(em & ~am)
+            for i in np.nonzero(am & ~em)[0][:50]:
+                assert orc.near_boundary(M, j, int(pts.x[i]), int(pts.y[i]), eps)
+
+
 # ------------------------------------------------------ invariants (Sec. 2.2, 6)
 
 @pytest.fixture(scope="module")
