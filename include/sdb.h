@@ -68,6 +68,25 @@ typedef struct sdb_polygons {
   const uint32_t *y;        /* ring_off[P] vertex y coordinates */
 } sdb_polygons;
 
+/* Polygons of one or more rings in host memory, read during the call only:
+ * multi-polygons and polygons with holes (the paper's neighbourhood regions
+ * include multi-polygons, Sec. 5.2).  Polygon j owns rings
+ * poly_ring_off[j] .. poly_ring_off[j+1]-1; ring r owns vertices
+ * x[ring_off[r]] .. x[ring_off[r+1]-1] (no closing duplicate, either
+ * orientation).  The polygon's region is the set of points with an odd
+ * crossing number over all of its rings, together with the rings (closed):
+ * outer boundaries and holes need no orientation or order.  Rings of one
+ * polygon must not cross each other (not checked). */
+typedef struct sdb_multipolygons {
+  uint32_t n_polygons;           /* P, 1 <= P < 2^26 */
+  uint32_t n_rings;              /* >= P */
+  const uint32_t *poly_ring_off; /* P+1, poly_ring_off[0] = 0, each polygon >= 1 ring,
+                                    poly_ring_off[P] = n_rings */
+  const uint32_t *ring_off;      /* n_rings+1, ring_off[0] = 0, each ring >= 3 vertices */
+  const uint32_t *x;             /* ring_off[n_rings] vertex coordinates */
+  const uint32_t *y;
+} sdb_multipolygons;
+
 /* Opaque device-resident covering (library-owned device memory). */
 typedef struct sdb_covering sdb_covering;
 
@@ -120,10 +139,28 @@ sdb_status sdb_build_covering(const sdb_polygons *polys, uint32_t grid_bits, uin
  * flagged covering; sdb_join_aggregate_range requires one. */
 #define SDB_COVER_BOUNDARY_FLAGS 1u
 
-/* sdb_build_covering with options: flags = 0 or SDB_COVER_BOUNDARY_FLAGS.
- * SDB_EINVAL as sdb_build_covering, or an unknown flag bit. */
+/* Non-conservative raster (Sec. 2.2: boundary cells with a small overlap may
+ * be omitted, trading false positives for false negatives): a finest-level
+ * boundary cell is kept only when its centre lies in the closed polygon;
+ * interior cells are kept as always.  Every answer error still lies within
+ * eps of the boundary.  Not combinable with SDB_COVER_BOUNDARY_FLAGS (the
+ * result-range interval assumes a conservative raster). */
+#define SDB_COVER_NONCONSERVATIVE 2u
+
+/* sdb_build_covering with options: flags = 0, SDB_COVER_BOUNDARY_FLAGS or
+ * SDB_COVER_NONCONSERVATIVE.  SDB_EINVAL as sdb_build_covering, an unknown flag
+ * bit, or both flags together. */
 sdb_status sdb_build_covering_ex(const sdb_polygons *polys, uint32_t grid_bits, uint64_t eps,
                                  uint32_t flags, void *cuda_stream, sdb_covering **out);
+
+/* sdb_build_covering_ex for polygons of several rings (holes, multi-polygons):
+ * a cell is a boundary cell of polygon j when it meets any of j's rings, an
+ * interior cell when it meets none and lies in j's even-odd region.  The
+ * covering is used like any other.  SDB_EINVAL as sdb_build_covering_ex, a
+ * polygon without rings, a ring with < 3 vertices, inconsistent offsets. */
+sdb_status sdb_build_covering_multi(const sdb_multipolygons *polys, uint32_t grid_bits,
+                                    uint64_t eps, uint32_t flags, void *cuda_stream,
+                                    sdb_covering **out);
 
 sdb_status sdb_covering_get_info(const sdb_covering *cov, sdb_covering_info *info);
 
@@ -231,6 +268,13 @@ sdb_status sdb_raster_join(const sdb_polygons *polys, uint32_t grid_bits, uint64
                            const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
                            uint64_t n, uint32_t tile_bits, uint64_t *d_count, int64_t *d_sum,
                            void *cuda_stream);
+
+/* sdb_raster_join for polygons of several rings (the crossings of all rings
+ * decide the interior; every ring's edges mark boundary pixels). */
+sdb_status sdb_raster_join_multi(const sdb_multipolygons *polys, uint32_t grid_bits, uint64_t eps,
+                                 const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
+                                 uint64_t n, uint32_t tile_bits, uint64_t *d_count,
+                                 int64_t *d_sum, void *cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * Batched level-of-detail queries (Sec. 1: users explore at several levels of

@@ -130,6 +130,133 @@ static sdb_status check_device(const sdb_covering* cov) {
   return SDB_OK;
 }
 
+sdb_status check_cover_flags(uint32_t flags) {
+  if (flags & ~(SDB_COVER_BOUNDARY_FLAGS | SDB_COVER_NONCONSERVATIVE)) {
+    set_error("unknown covering flags 0x%x", flags);
+    return SDB_EINVAL;
+  }
+  if ((flags & SDB_COVER_BOUNDARY_FLAGS) && (flags & SDB_COVER_NONCONSERVATIVE)) {
+    set_error("boundary flags need a conservative covering");
+    return SDB_EINVAL;
+  }
+  return SDB_OK;
+}
+
+sdb_status new_covering(const PolyEdges& pe, uint32_t grid_bits, uint32_t k, uint32_t flags,
+                        cudaStream_t s, sdb_covering** out) {
+  sdb_covering* cov = new (std::nothrow) sdb_covering();
+  if (!cov) {
+    set_error("host allocation failed");
+    return SDB_ENOMEM;
+  }
+  if (cudaGetDevice(&cov->device) != cudaSuccess) {
+    delete cov;
+    set_error("no CUDA device");
+    return SDB_ECUDA;
+  }
+  sdb_status st = build_covering_device(pe, grid_bits, k, flags, s, cov);
+  if (st != SDB_OK) {
+    std::string msg = sdb_last_error();
+    free_covering(cov);
+    set_error("%s", msg.c_str());
+    return st;
+  }
+  *out = cov;
+  return SDB_OK;
+}
+
+PolyEdges poly_edges(const sdb_polygons* p) {
+  PolyEdges e;
+  e.P = p->n_polygons;
+  e.V = p->ring_off[e.P];
+  e.x = p->x;
+  e.y = p->y;
+  e.edge_off.assign(p->ring_off, p->ring_off + e.P + 1);
+  e.next.resize(e.V);
+  for (uint32_t j = 0; j < e.P; ++j)
+    for (uint32_t v = p->ring_off[j]; v < p->ring_off[j + 1]; ++v)
+      e.next[v] = v + 1 < p->ring_off[j + 1] ? v + 1 : p->ring_off[j];
+  return e;
+}
+
+PolyEdges poly_edges(const sdb_multipolygons* p) {
+  PolyEdges e;
+  e.P = p->n_polygons;
+  e.V = p->ring_off[p->n_rings];
+  e.x = p->x;
+  e.y = p->y;
+  e.edge_off.resize(e.P + 1);
+  for (uint32_t j = 0; j <= e.P; ++j) e.edge_off[j] = p->ring_off[p->poly_ring_off[j]];
+  e.next.resize(e.V);
+  for (uint32_t r = 0; r < p->n_rings; ++r)
+    for (uint32_t v = p->ring_off[r]; v < p->ring_off[r + 1]; ++v)
+      e.next[v] = v + 1 < p->ring_off[r + 1] ? v + 1 : p->ring_off[r];
+  return e;
+}
+
+sdb_status validate_multipolygons(const sdb_multipolygons* p, uint32_t grid_bits) {
+  if (!p || !p->poly_ring_off || !p->ring_off || !p->x || !p->y) {
+    set_error("polygons or one of their arrays is NULL");
+    return SDB_EINVAL;
+  }
+  const uint32_t P = p->n_polygons, R = p->n_rings;
+  if (P == 0 || P >= (1u << 26) || R < P) {
+    set_error("n_polygons %u outside 1..2^26-1 or fewer rings (%u)", P, R);
+    return SDB_EINVAL;
+  }
+  if (p->poly_ring_off[0] != 0 || p->poly_ring_off[P] != R || p->ring_off[0] != 0) {
+    set_error("offsets must start at 0 and poly_ring_off[P] must equal n_rings");
+    return SDB_EINVAL;
+  }
+  for (uint32_t j = 0; j < P; ++j)
+    if (p->poly_ring_off[j + 1] <= p->poly_ring_off[j]) {
+      set_error("polygon %u has no ring", j);
+      return SDB_EINVAL;
+    }
+  for (uint32_t r = 0; r < R; ++r)
+    if (p->ring_off[r + 1] < p->ring_off[r] + 3) {
+      set_error("ring %u has fewer than 3 vertices", r);
+      return SDB_EINVAL;
+    }
+  const uint32_t V = p->ring_off[R];
+  if (V >= 0x7fffffffu) {
+    set_error("too many vertices (%u)", V);
+    return SDB_EINVAL;
+  }
+  const uint32_t G = 1u << grid_bits;
+  for (uint32_t v = 0; v < V; ++v)
+    if (p->x[v] >= G || p->y[v] >= G) {
+      set_error("vertex %u (%u, %u) outside the grid [0, 2^%u)", v, p->x[v], p->y[v], grid_bits);
+      return SDB_EINVAL;
+    }
+  return SDB_OK;
+}
+
+sdb_status raster_common(const PolyEdges& pe, uint32_t grid_bits, uint32_t k,
+                                const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
+                                uint64_t n, uint32_t tile_bits, uint64_t* d_count, int64_t* d_sum,
+                                void* cuda_stream) {
+  if (!d_count || (n > 0 && (!d_x || !d_y))) {
+    set_error("d_count is NULL, or n > 0 with NULL coordinates");
+    return SDB_EINVAL;
+  }
+  if (d_sum && !d_attr && n > 0) {
+    set_error("d_sum requested without d_attr");
+    return SDB_EINVAL;
+  }
+  if (n >= (1ull << 32)) {
+    set_error("n = %llu points: at most 2^32 - 1 per call", (unsigned long long)n);
+    return SDB_EINVAL;
+  }
+  if (tile_bits == 0) tile_bits = 13;
+  if (tile_bits > 14) {
+    set_error("tile_bits %u outside 1..14 (0 = default 13)", tile_bits);
+    return SDB_EINVAL;
+  }
+  return raster_join(pe, grid_bits, k, d_x, d_y, d_attr, n, tile_bits, 8ull << 30, d_count, d_sum,
+                     (cudaStream_t)cuda_stream);
+}
+
 }  // namespace sdb
 
 using namespace sdb;
@@ -157,34 +284,26 @@ sdb_status sdb_build_covering_ex(const sdb_polygons* polys, uint32_t grid_bits, 
     return SDB_EINVAL;
   }
   *out = nullptr;
-  if (flags & ~SDB_COVER_BOUNDARY_FLAGS) {
-    set_error("unknown covering flags 0x%x", flags);
-    return SDB_EINVAL;
-  }
+  SDB_TRY(check_cover_flags(flags));
   uint32_t k = 0;
   SDB_TRY(finest(grid_bits, eps, &k));
   SDB_TRY(validate_polygons(polys, grid_bits));
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  sdb_covering* cov = new (std::nothrow) sdb_covering();
-  if (!cov) {
-    set_error("host allocation failed");
-    return SDB_ENOMEM;
+  return new_covering(poly_edges(polys), grid_bits, k, flags, (cudaStream_t)cuda_stream, out);
+}
+
+sdb_status sdb_build_covering_multi(const sdb_multipolygons* polys, uint32_t grid_bits,
+                                    uint64_t eps, uint32_t flags, void* cuda_stream,
+                                    sdb_covering** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return SDB_EINVAL;
   }
-  if (cudaGetDevice(&cov->device) != cudaSuccess) {
-    delete cov;
-    set_error("no CUDA device");
-    return SDB_ECUDA;
-  }
-  sdb_status st = build_covering_device(polys, grid_bits, k,
-                                        (flags & SDB_COVER_BOUNDARY_FLAGS) != 0, s, cov);
-  if (st != SDB_OK) {
-    std::string msg = sdb_last_error();
-    free_covering(cov);
-    set_error("%s", msg.c_str());
-    return st;
-  }
-  *out = cov;
-  return SDB_OK;
+  *out = nullptr;
+  SDB_TRY(check_cover_flags(flags));
+  uint32_t k = 0;
+  SDB_TRY(finest(grid_bits, eps, &k));
+  SDB_TRY(validate_multipolygons(polys, grid_bits));
+  return new_covering(poly_edges(polys), grid_bits, k, flags, (cudaStream_t)cuda_stream, out);
 }
 
 }  // extern "C"
@@ -236,26 +355,21 @@ sdb_status sdb_raster_join(const sdb_polygons* polys, uint32_t grid_bits, uint64
   uint32_t k = 0;
   SDB_TRY(finest(grid_bits, eps, &k));
   SDB_TRY(validate_polygons(polys, grid_bits));
-  if (!d_count || (n > 0 && (!d_x || !d_y))) {
-    set_error("d_count is NULL, or n > 0 with NULL coordinates");
-    return SDB_EINVAL;
-  }
-  if (d_sum && !d_attr && n > 0) {
-    set_error("d_sum requested without d_attr");
-    return SDB_EINVAL;
-  }
-  if (n >= (1ull << 32)) {
-    set_error("n = %llu points: at most 2^32 - 1 per call", (unsigned long long)n);
-    return SDB_EINVAL;
-  }
-  if (tile_bits == 0) tile_bits = 13;
-  if (tile_bits > 14) {
-    set_error("tile_bits %u outside 1..14 (0 = default 13)", tile_bits);
-    return SDB_EINVAL;
-  }
-  return raster_join(polys, grid_bits, k, d_x, d_y, d_attr, n, tile_bits, 8ull << 30, d_count,
-                     d_sum, (cudaStream_t)cuda_stream);
+  return raster_common(poly_edges(polys), grid_bits, k, d_x, d_y, d_attr, n, tile_bits, d_count,
+                       d_sum, cuda_stream);
 }
+
+sdb_status sdb_raster_join_multi(const sdb_multipolygons* polys, uint32_t grid_bits, uint64_t eps,
+                                 const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
+                                 uint64_t n, uint32_t tile_bits, uint64_t* d_count,
+                                 int64_t* d_sum, void* cuda_stream) {
+  uint32_t k = 0;
+  SDB_TRY(finest(grid_bits, eps, &k));
+  SDB_TRY(validate_multipolygons(polys, grid_bits));
+  return raster_common(poly_edges(polys), grid_bits, k, d_x, d_y, d_attr, n, tile_bits, d_count,
+                       d_sum, cuda_stream);
+}
+
 
 sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* info) {
   if (!cov || !info) {

@@ -428,7 +428,7 @@ sdb_status batch_core_run(BatchCore* c, int mode, uint64_t* count, int64_t* sum,
 // Coverings of queries [q0, q0 + nq) of a pair list, built in chunks that are
 // halved and retried when they overflow the builder's 32-bit ranges or memory.
 // Appends CoverSets to *sets and fills sbase/R/chunk of hq.
-sdb_status build_query_coverings(const sdb_polygons* polys, uint32_t B,
+sdb_status build_query_coverings(const PolyEdges& pe, uint32_t B,
                                  const std::vector<CoverQuery>& cq,
                                  const std::vector<uint32_t>& pp, const std::vector<uint32_t>& pq,
                                  const std::vector<uint32_t>& ps, std::vector<BatchQueryDev>& hq,
@@ -465,7 +465,7 @@ sdb_status build_query_coverings(const sdb_polygons* polys, uint32_t B,
     spec.pair_query = pq_local.data();
     spec.pair_slot = ps.data() + pa;
     CoverSet set;
-    sdb_status st = build_coverings(polys, spec, s, &set);
+    sdb_status st = build_coverings(pe, spec, s, &set);
     if (st == SDB_ENOMEM && nq > 1) {
       set.release(s);
       cudaStreamSynchronize(s);
@@ -692,8 +692,8 @@ sdb_status sdb_batch_create(const sdb_points* pts, const sdb_polygons* polys,
   b->core.pts = pts;
   b->core.Q = n_queries;
   b->core.out_len = out_off;
-  sdb_status st = build_query_coverings(polys, B, cq, pp, pq, ps, hq, &b->cs, 0, s, &b->n_ranges,
-                                        &b->n_cells, &b->max_ranges);
+  sdb_status st = build_query_coverings(poly_edges(polys), B, cq, pp, pq, ps, hq, &b->cs, 0, s,
+                                        &b->n_ranges, &b->n_cells, &b->max_ranges);
   if (st == SDB_OK) {
     b->core.hq = hq;
     for (auto& c : b->cs)

@@ -121,28 +121,78 @@ __device__ __forceinline__ void block_alloc3(const uint32_t (&n)[3],
   for (int j = 0; j < 3; ++j) off[j] = base[j] + wsum[j][w] + inc[j] - n[j];
 }
 
-__global__ void build_edges_kernel(const uint32_t* __restrict__ ring_off,
-                                   const uint32_t* __restrict__ vx, const uint32_t* __restrict__ vy,
-                                   const uint32_t* __restrict__ vpoly, uint32_t V,
+__global__ void build_edges_kernel(const uint32_t* __restrict__ vx, const uint32_t* __restrict__ vy,
+                                   const uint32_t* __restrict__ next, uint32_t V,
                                    Edge* __restrict__ edges, uint32_t* __restrict__ elist) {
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
-  uint32_t j = vpoly[v];
-  uint32_t w = (v + 1 < ring_off[j + 1]) ? v + 1 : ring_off[j];
+  const uint32_t w = next[v];  // the following vertex of v's ring
   edges[v] = Edge{(int32_t)vx[v], (int32_t)vy[v], (int32_t)vx[w], (int32_t)vy[w]};
   elist[v] = v;
+}
+
+// Non-conservative raster (Sec. 2.2): centre tests in doubled coordinates
+// (centres of unit cells are then integers; perturbation as for the corners).
+// Perturbed side of (x, y)+ against edge (a, b): sign of cross(b - a, q - a),
+// ties by -dy, then dx.
+__device__ __forceinline__ int dbl_side(int64_t ax, int64_t ay, int64_t dx, int64_t dy, int64_t x,
+                                        int64_t y) {
+  const int64_t o = dx * (y - ay) - dy * (x - ax);
+  if (o != 0) return o > 0 ? 1 : -1;
+  if (dy != 0) return dy < 0 ? 1 : -1;
+  return dx > 0 ? 1 : -1;
+}
+// the rightward ray from (x, y)+ crosses the edge
+__device__ __forceinline__ uint32_t dbl_ray_right(int64_t ax, int64_t ay, int64_t bx, int64_t by,
+                                                  int64_t x, int64_t y) {
+  if ((ay > y) == (by > y)) return 0;
+  const int sd = dbl_side(ax, ay, bx - ax, by - ay, x, y);
+  return (by > ay) ? (sd > 0) : (sd < 0);
+}
+// the upward ray from (x, y)+ crosses the edge
+__device__ __forceinline__ uint32_t dbl_ray_up(int64_t ax, int64_t ay, int64_t bx, int64_t by,
+                                               int64_t x, int64_t y) {
+  if ((ax > x) == (bx > x)) return 0;
+  const int sd = dbl_side(ax, ay, bx - ax, by - ay, x, y);
+  return (bx > ax) ? (sd < 0) : (sd > 0);
+}
+__device__ __forceinline__ uint32_t dbl_on_edge(int64_t ax, int64_t ay, int64_t bx, int64_t by,
+                                                int64_t x, int64_t y) {
+  const int64_t o = (bx - ax) * (y - ay) - (by - ay) * (x - ax);
+  return o == 0 && min(ax, bx) <= x && x <= max(ax, bx) && min(ay, by) <= y && y <= max(ay, by);
+}
+
+// One edge against the centres of the 2x2 children of the parent with corner
+// (px, py) and child side `side`: bits 0..3 the parity flip from the parent's
+// corner+ to child c's centre+ along the path right to the centre's x, then up
+// (segment parities as XORs of rays); bits 4..7 the centre lies on the edge.
+__device__ __forceinline__ uint32_t edge_vs_centres(const Edge& e, int64_t px, int64_t py,
+                                                    int64_t side) {
+  const int64_t ax = 2 * (int64_t)e.ax, ay = 2 * (int64_t)e.ay;
+  const int64_t bx = 2 * (int64_t)e.bx, by = 2 * (int64_t)e.by;
+  const int64_t X0 = 2 * px, Y0 = 2 * py;
+  const uint32_t r0 = dbl_ray_right(ax, ay, bx, by, X0, Y0);
+  uint32_t out = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int64_t cx = X0 + (2 * (c & 1) + 1) * side, cy = Y0 + (2 * (c >> 1) + 1) * side;
+    const uint32_t f = r0 ^ dbl_ray_right(ax, ay, bx, by, cx, Y0) ^
+                       dbl_ray_up(ax, ay, bx, by, cx, Y0) ^ dbl_ray_up(ax, ay, bx, by, cx, cy);
+    out |= (f << c) | (dbl_on_edge(ax, ay, bx, by, cx, cy) << (4 + c));
+  }
+  return out;
 }
 
 // one warp per (query, polygon) pair: the level-0 item (whole grid) with all of
 // the polygon's edges and the parity of (0,0)+; a query whose finest level is 0
 // gets the whole grid as one boundary cell instead
-__global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
+__global__ void root_items_kernel(const uint32_t* __restrict__ edge_off,
                                   const Edge* __restrict__ edges,
                                   const uint32_t* __restrict__ pair_poly,
                                   const uint32_t* __restrict__ pair_query,
                                   const uint32_t* __restrict__ pair_slot,
                                   const CoverQuery* __restrict__ qs, uint32_t NP, uint32_t qshift,
-                                  uint32_t bflag, Item* __restrict__ items,
+                                  uint32_t bflag, bool noncons, uint32_t B, Item* __restrict__ items,
                                   uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val,
                                   unsigned long long* __restrict__ counters) {
   uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -150,6 +200,19 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
   if (p >= NP) return;
   const uint32_t j = pair_poly[p], qi = pair_query[p];
   if (qs[qi].F == 0) {
+    if (noncons) {  // the whole grid is kept only when its centre is in the polygon
+      const int64_t c = (int64_t)1 << B;  // the centre, doubled
+      uint32_t par = 0, on = 0;
+      for (uint32_t v = edge_off[j] + lane; v < edge_off[j + 1]; v += 32) {
+        const Edge e = edges[v];
+        const int64_t ax = 2 * (int64_t)e.ax, ay = 2 * (int64_t)e.ay;
+        const int64_t bx = 2 * (int64_t)e.bx, by = 2 * (int64_t)e.by;
+        par ^= dbl_ray_right(ax, ay, bx, by, c, c);
+        on |= dbl_on_edge(ax, ay, bx, by, c, c);
+      }
+      const bool keep = __any_sync(FULL, on) || (__popc(__ballot_sync(FULL, par)) & 1u);
+      if (!keep) return;
+    }
     if (lane == 0) {
       unsigned long long r = atomicAdd(&counters[2], 1ull);
       rec_key[r] = qshift >= 64 ? 0ull : ((uint64_t)qi << qshift);
@@ -157,7 +220,7 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ ring_off,
     }
     return;
   }
-  uint32_t a = ring_off[j], b = ring_off[j + 1];
+  uint32_t a = edge_off[j], b = edge_off[j + 1];
   uint32_t par = 0;
   for (uint32_t v = a + lane; v < b; v += 32) par ^= pert_ray_cross(edges[v], 0, 0);
   par = __popc(__ballot_sync(FULL, par)) & 1u;
@@ -235,7 +298,7 @@ __device__ __forceinline__ uint32_t edge_vs_children(const Edge& e, int32_t px, 
 // its first lane writes the records and child items.  Child edge lists keep
 // the parent's edge order (a ballot per child and chunk of G edges); the meet
 // masks of the first 8 chunks are kept in a register for that second pass.
-template <int G>
+template <int G, bool NC>
 __global__ __launch_bounds__(256) void expand_level_kernel(
     const Item* __restrict__ items, uint32_t n_items, const uint32_t* __restrict__ elist,
     const Edge* __restrict__ edges, const uint32_t* __restrict__ pair_query,
@@ -276,12 +339,21 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
   uint32_t cnt[4] = {0, 0, 0, 0};
   uint32_t flip = 0;   // bit c: parity flip from the parent's corner to child c's
   uint32_t mcache = 0; // meet bits of this lane's edges in chunks 0..7
+  // non-conservative, last level: bits 0..3 parity flips to the children's
+  // centres, bits 4..7 a centre lies on an edge
+  const bool nc = NC && cl == F;
+  uint32_t cen = 0;
   for (uint32_t i = gl, j = 0; i < ecnt; i += G, ++j) {
-    const uint32_t m = edge_vs_children(edges[elist[it.eoff + i]], px32, py32, sh);
+    const Edge e = edges[elist[it.eoff + i]];
+    const uint32_t m = edge_vs_children(e, px32, py32, sh);
 #pragma unroll
     for (int c = 0; c < 4; ++c) cnt[c] += (m >> c) & 1u;
     flip ^= m >> 4;
     if (j < 8) mcache |= (m & 15u) << (4 * j);
+    if (nc) {
+      const uint32_t b = edge_vs_centres(e, px, py, side);
+      cen = (cen ^ (b & 15u)) | (b & 0xf0u);
+    }
   }
   if (G > 1) {
 #pragma unroll
@@ -289,8 +361,13 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
 #pragma unroll
       for (int c = 0; c < 4; ++c) cnt[c] += __shfl_xor_sync(gmask, cnt[c], o);
       flip ^= __shfl_xor_sync(gmask, flip, o);
+      const uint32_t oc = __shfl_xor_sync(gmask, cen, o);
+      cen = ((cen ^ oc) & 15u) | ((cen | oc) & 0xf0u);
     }
   }
+  // boundary children kept at the last level: all, or (non-conservative) those
+  // whose centre is on an edge or inside (the corner's parity plus the flip)
+  const uint32_t bkeep = nc ? (((cen >> 4) | ((par ? 15u : 0u) ^ (cen & 15u))) & 15u) : 15u;
   uint32_t n_rec = 0, n_it = 0, n_ed = 0;
   if (active && gl == 0) {
 #pragma unroll
@@ -299,7 +376,7 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
       if (!((keep >> c) & 1u)) continue;
       if (cnt[c] > 0) {
         if (cl == F) {
-          ++n_rec;
+          n_rec += (bkeep >> c) & 1u;
         } else {
           ++n_it;
           n_ed += cnt[c];
@@ -337,6 +414,10 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
     const uint64_t chid = (it.hid << 2) | ((xt << 1) | (xt ^ yt));
     const uint32_t corient = yt ? it.orient : (it.orient ^ 2u ^ xt);
     uint32_t inside = (par ^ (flip >> c)) & 1u;
+    if (cnt[c] > 0 && cl == F && !((bkeep >> c) & 1u)) {
+      cnt[c] = 0;  // non-conservative: a boundary cell whose centre lies outside
+      continue;
+    }
     bool emit = (cnt[c] > 0) ? (cl == F) : (inside != 0);
     if (emit) {
       if (gl == 0) {
@@ -964,15 +1045,21 @@ void CoverSet::release(cudaStream_t s) {
 
 static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items, const uint32_t* elist,
                          const Edge* edges, const uint32_t* pq, const uint32_t* ps,
-                         const CoverQuery* qs, uint32_t qshift, uint32_t bflag, uint32_t B, uint32_t L,
+                         const CoverQuery* qs, uint32_t qshift, uint32_t bflag, bool noncons,
+                         uint32_t B, uint32_t L,
                          Item* nitems, uint32_t* nel, uint64_t* rkey, uint32_t* rval,
                          unsigned long long rec_base, unsigned long long* ctr, cudaStream_t s) {
   const size_t threads = (size_t)n_items * G;
 #define SDB_EXPAND(g)                                                                          \
   case g:                                                                                      \
-    expand_level_kernel<g><<<grid_for(threads, 256), 256, 0, s>>>(                             \
-        items, n_items, elist, edges, pq, ps, qs, qshift, bflag, B, L, nitems, nel, rkey, rval, \
-        rec_base, ctr);                                                                        \
+    if (noncons)                                                                               \
+      expand_level_kernel<g, true><<<grid_for(threads, 256), 256, 0, s>>>(                     \
+          items, n_items, elist, edges, pq, ps, qs, qshift, bflag, B, L, nitems, nel, rkey,     \
+          rval, rec_base, ctr);                                                                \
+    else                                                                                       \
+      expand_level_kernel<g, false><<<grid_for(threads, 256), 256, 0, s>>>(                    \
+          items, n_items, elist, edges, pq, ps, qs, qshift, bflag, B, L, nitems, nel, rkey,     \
+          rval, rec_base, ctr);                                                                \
     break;
   switch (G) {
     SDB_EXPAND(1)
@@ -991,10 +1078,10 @@ static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items,
   return SDB_OK;
 }
 
-sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cudaStream_t s,
+sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStream_t s,
                            CoverSet* out) {
-  const uint32_t P = polys->n_polygons;
-  const uint32_t V = polys->ring_off[P];
+  const uint32_t P = pe.P;
+  const uint32_t V = pe.V;
   const uint32_t B = spec.B, Q = spec.Q, NP = spec.NP;
   uint32_t Fmax = 0;
   for (uint32_t q = 0; q < Q; ++q) Fmax = spec.q[q].F > Fmax ? spec.q[q].F : Fmax;
@@ -1013,9 +1100,6 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
   }
   Scratch sc(s);
   // polygons -> device edges
-  std::vector<uint32_t> vpoly(V);
-  for (uint32_t j = 0; j < P; ++j)
-    for (uint32_t v = polys->ring_off[j]; v < polys->ring_off[j + 1]; ++v) vpoly[v] = j;
   uint32_t *d_off, *d_x, *d_y, *d_vp, *elist, *d_pp, *d_pq, *d_ps;
   CoverQuery* d_qs;
   Edge* edges;
@@ -1029,17 +1113,17 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
   SDB_TRY(sc.get(&d_pq, NP));
   SDB_TRY(sc.get(&d_ps, NP));
   SDB_TRY(sc.get(&d_qs, Q));
-  SDB_TRY_CUDA(cudaMemcpyAsync(d_off, polys->ring_off, (P + 1) * 4ull, cudaMemcpyHostToDevice, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(d_x, polys->x, V * 4ull, cudaMemcpyHostToDevice, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(d_y, polys->y, V * 4ull, cudaMemcpyHostToDevice, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(d_vp, vpoly.data(), V * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_off, pe.edge_off.data(), (P + 1) * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_x, pe.x, V * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_y, pe.y, V * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_vp, pe.next.data(), V * 4ull, cudaMemcpyHostToDevice, s));
   if (NP) {
     SDB_TRY_CUDA(cudaMemcpyAsync(d_pp, spec.pair_poly, NP * 4ull, cudaMemcpyHostToDevice, s));
     SDB_TRY_CUDA(cudaMemcpyAsync(d_pq, spec.pair_query, NP * 4ull, cudaMemcpyHostToDevice, s));
     SDB_TRY_CUDA(cudaMemcpyAsync(d_ps, spec.pair_slot, NP * 4ull, cudaMemcpyHostToDevice, s));
   }
   SDB_TRY_CUDA(cudaMemcpyAsync(d_qs, spec.q, Q * sizeof(CoverQuery), cudaMemcpyHostToDevice, s));
-  build_edges_kernel<<<grid_for(V, 256), 256, 0, s>>>(d_off, d_x, d_y, d_vp, V, edges, elist);
+  build_edges_kernel<<<grid_for(V, 256), 256, 0, s>>>(d_x, d_y, d_vp, V, edges, elist);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
 
@@ -1068,7 +1152,8 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
   SDB_TRY(dalloc_n(&items, NP, s));
   if (NP) {
     root_items_kernel<<<grid_for((size_t)NP * 32, 256), 256, 0, s>>>(
-        d_off, edges, d_pp, d_pq, d_ps, d_qs, NP, qshift, bflag, items, rkey, rval, ctr);
+        d_off, edges, d_pp, d_pq, d_ps, d_qs, NP, qshift, bflag, spec.noncons, B, items, rkey, rval,
+        ctr);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
   }
@@ -1078,7 +1163,7 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
   n_rec = h0[2];
   for (uint32_t i = 0; i < NP; ++i)
     if (spec.q[spec.pair_query[i]].F > 0)
-      n_edges += polys->ring_off[spec.pair_poly[i] + 1] - polys->ring_off[spec.pair_poly[i]];
+      n_edges += pe.edge_off[spec.pair_poly[i] + 1] - pe.edge_off[spec.pair_poly[i]];
   uint32_t* cur_el = elist;
   bool own_el = false;
   for (uint32_t L = 0; L < Fmax && n_items > 0; ++L) {
@@ -1125,7 +1210,8 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
     uint32_t G = 1;
     if (mean >= 4)
       while (G < 32 && G < mean) G <<= 1;
-    SDB_TRY(launch_expand(G, items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift, bflag, B,
+    SDB_TRY(launch_expand(G, items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift, bflag,
+                          spec.noncons, B,
                           L, nitems, nel, rkey, rval, n_rec, ctr, s));
     SDB_TRY_CUDA(cudaGetLastError());
     unsigned long long h[3];
@@ -1145,9 +1231,10 @@ sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cud
   return merge_records(rkey, rval, n_rec, spec, d_qs, qshift, key_bits, s, out);
 }
 
-sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, bool flags,
+sdb_status build_covering_device(const PolyEdges& pe, uint32_t B, uint32_t k, uint32_t options,
                                  cudaStream_t s, sdb_covering* cov) {
-  const uint32_t P = polys->n_polygons;
+  const uint32_t P = pe.P;
+  const bool flags = (options & SDB_COVER_BOUNDARY_FLAGS) != 0;
   const uint32_t F = B - k;
   cov->B = B;
   cov->k = k;
@@ -1165,9 +1252,10 @@ sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t
   spec.pair_query = pq.data();
   spec.pair_slot = pp.data();
   spec.flags = flags;
+  spec.noncons = (options & SDB_COVER_NONCONSERVATIVE) != 0;
   cov->flagged = flags;
   CoverSet cs;
-  sdb_status st = build_coverings(polys, spec, s, &cs);
+  sdb_status st = build_coverings(pe, spec, s, &cs);
   if (st != SDB_OK) {
     cs.release(s);
     return st;

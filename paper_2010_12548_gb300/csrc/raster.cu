@@ -334,23 +334,22 @@ __global__ __launch_bounds__(THREADS) void polygon_rows_kernel(
   }
 }
 
-__global__ void raster_edges_kernel(const uint32_t* __restrict__ ring_off,
-                                    const uint32_t* __restrict__ vx, const uint32_t* __restrict__ vy,
-                                    const uint32_t* __restrict__ vpoly, uint32_t V,
+__global__ void raster_edges_kernel(const uint32_t* __restrict__ vx,
+                                    const uint32_t* __restrict__ vy,
+                                    const uint32_t* __restrict__ next, uint32_t V,
                                     REdge* __restrict__ edges) {
   const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
-  const uint32_t j = vpoly[v];
-  const uint32_t w = (v + 1 < ring_off[j + 1]) ? v + 1 : ring_off[j];
+  const uint32_t w = next[v];  // the following vertex of v's ring
   edges[v] = REdge{(int32_t)vx[v], (int32_t)vy[v], (int32_t)vx[w], (int32_t)vy[w]};
 }
 
 }  // namespace
 
-sdb_status raster_join(const sdb_polygons* polys, uint32_t B, uint32_t k, const uint32_t* x,
+sdb_status raster_join(const PolyEdges& pe, uint32_t B, uint32_t k, const uint32_t* x,
                        const uint32_t* y, const int32_t* attr, uint64_t n, uint32_t tile_bits,
                        uint64_t budget_bytes, uint64_t* count, int64_t* sum, cudaStream_t s) {
-  const uint32_t P = polys->n_polygons, V = polys->ring_off[P];
+  const uint32_t P = pe.P, V = pe.V;
   const uint32_t F = B - k;
   const uint32_t t = F < tile_bits ? F : tile_bits;
   if (F - t > 8) {
@@ -370,16 +369,14 @@ sdb_status raster_join(const sdb_polygons* polys, uint32_t B, uint32_t k, const 
   SDB_TRY_CUDA(cudaMemsetAsync(count, 0, (size_t)P * 8, s));
   if (sum) SDB_TRY_CUDA(cudaMemsetAsync(sum, 0, (size_t)P * 8, s));
   // polygons: edges and bounding boxes
-  std::vector<uint32_t> vpoly(V);
   std::vector<int32_t> hb(4 * (size_t)P);
-  for (uint32_t j = 0; j < P; ++j) {
+  for (uint32_t j = 0; j < P; ++j) {  // bounding box over all of j's rings
     int32_t x0 = INT32_MAX, y0 = INT32_MAX, x1 = 0, y1 = 0;
-    for (uint32_t v = polys->ring_off[j]; v < polys->ring_off[j + 1]; ++v) {
-      vpoly[v] = j;
-      x0 = std::min<int32_t>(x0, (int32_t)polys->x[v]);
-      y0 = std::min<int32_t>(y0, (int32_t)polys->y[v]);
-      x1 = std::max<int32_t>(x1, (int32_t)polys->x[v]);
-      y1 = std::max<int32_t>(y1, (int32_t)polys->y[v]);
+    for (uint32_t v = pe.edge_off[j]; v < pe.edge_off[j + 1]; ++v) {
+      x0 = std::min<int32_t>(x0, (int32_t)pe.x[v]);
+      y0 = std::min<int32_t>(y0, (int32_t)pe.y[v]);
+      x1 = std::max<int32_t>(x1, (int32_t)pe.x[v]);
+      y1 = std::max<int32_t>(y1, (int32_t)pe.y[v]);
     }
     hb[4 * j] = x0;
     hb[4 * j + 1] = y0;
@@ -397,13 +394,13 @@ sdb_status raster_join(const sdb_polygons* polys, uint32_t B, uint32_t k, const 
   SDB_TRY(sc.get(&d_bb, 4 * (size_t)P));
   SDB_TRY(sc.get(&d_e, V));
   SDB_TRY(sc.get(&d_over, 1));
-  SDB_TRY_CUDA(cudaMemcpyAsync(d_off, polys->ring_off, (P + 1) * 4ull, cudaMemcpyHostToDevice, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(d_x, polys->x, V * 4ull, cudaMemcpyHostToDevice, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(d_y, polys->y, V * 4ull, cudaMemcpyHostToDevice, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(d_vp, vpoly.data(), V * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_off, pe.edge_off.data(), (P + 1) * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_x, pe.x, V * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_y, pe.y, V * 4ull, cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(d_vp, pe.next.data(), V * 4ull, cudaMemcpyHostToDevice, s));
   SDB_TRY_CUDA(cudaMemcpyAsync(d_bb, hb.data(), hb.size() * 4, cudaMemcpyHostToDevice, s));
   SDB_TRY_CUDA(cudaMemsetAsync(d_over, 0, 4, s));
-  raster_edges_kernel<<<grid_for(V, 256), 256, 0, s>>>(d_off, d_x, d_y, d_vp, V, d_e);
+  raster_edges_kernel<<<grid_for(V, 256), 256, 0, s>>>(d_x, d_y, d_vp, V, d_e);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
   // points bucketed by tile (one tile: no bucketing)

@@ -188,13 +188,27 @@ struct sdb_points {
 namespace sdb {
 
 // api.cu ---------------------------------------------------------------------
+// Polygons as edge sets: polygon j owns edges [edge_off[j], edge_off[j+1]) and
+// edge v runs from vertex v to vertex next[v], the following vertex of its
+// ring.  A polygon of several rings (outer boundaries and holes) is the
+// even-odd region of all its edges.
+struct PolyEdges {
+  uint32_t P = 0, V = 0;
+  const uint32_t* x = nullptr;  // caller-owned vertex arrays
+  const uint32_t* y = nullptr;
+  std::vector<uint32_t> edge_off;
+  std::vector<uint32_t> next;
+};
+PolyEdges poly_edges(const sdb_polygons* p);
+PolyEdges poly_edges(const sdb_multipolygons* p);
 sdb_status validate_polygons(const sdb_polygons* polys, uint32_t grid_bits);
+sdb_status validate_multipolygons(const sdb_multipolygons* polys, uint32_t grid_bits);
 
 // raster.cu ------------------------------------------------------------------
 // Bounded Raster Join: counts (and sums, when sum != nullptr) per polygon over
 // a canvas of 2^(B-k) x 2^(B-k) pixels, cut into tiles of 2^tile_bits pixels a
 // side, as many tiles at once as fit in budget_bytes (16 bytes per pixel).
-sdb_status raster_join(const sdb_polygons* polys, uint32_t B, uint32_t k, const uint32_t* x,
+sdb_status raster_join(const PolyEdges& pe, uint32_t B, uint32_t k, const uint32_t* x,
                        const uint32_t* y, const int32_t* attr, uint64_t n, uint32_t tile_bits,
                        uint64_t budget_bytes, uint64_t* count, int64_t* sum, cudaStream_t s);
 
@@ -224,7 +238,8 @@ struct CoverSpec {
   const uint32_t* pair_poly = nullptr;  // host, NP entries each
   const uint32_t* pair_query = nullptr;
   const uint32_t* pair_slot = nullptr;
-  bool flags = false;  // boundary flags on list entries (result range, Sec. 6)
+  bool flags = false;    // boundary flags on list entries (result range, Sec. 6)
+  bool noncons = false;  // finest boundary cells kept only when their centre is inside
 };
 // Result, device arrays from the library pool.  Query q's ranges are entries
 // [qoff[q], qoff[q+1] - 1) of start/list_off/pay; entry qoff[q+1] - 1 is a
@@ -239,9 +254,10 @@ struct CoverSet {
   std::vector<uint64_t> qoff;    // host, Q + 1
   void release(cudaStream_t s);
 };
-sdb_status build_coverings(const sdb_polygons* polys, const CoverSpec& spec, cudaStream_t s,
+sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStream_t s,
                            CoverSet* out);
-sdb_status build_covering_device(const sdb_polygons* polys, uint32_t B, uint32_t k, bool flags,
+// options: SDB_COVER_BOUNDARY_FLAGS, SDB_COVER_NONCONSERVATIVE
+sdb_status build_covering_device(const PolyEdges& pe, uint32_t B, uint32_t k, uint32_t options,
                                  cudaStream_t s, sdb_covering* cov);
 // batch.cu ------------------------------------------------------------------
 // Per-query parameters of a batched join, and the covering arrays a query's
@@ -291,7 +307,7 @@ sdb_status batch_core_tiles(BatchCore* c, uint32_t T, cudaStream_t s);
 sdb_status batch_core_run(BatchCore* c, int mode, uint64_t* count, int64_t* sum, cudaStream_t s);
 // coverings for queries cq (pairs in query order), chunked; fills sbase/R/chunk
 // of hq with chunk indices starting at chunk_base
-sdb_status build_query_coverings(const sdb_polygons* polys, uint32_t B,
+sdb_status build_query_coverings(const PolyEdges& pe, uint32_t B,
                                  const std::vector<CoverQuery>& cq,
                                  const std::vector<uint32_t>& pp, const std::vector<uint32_t>& pq,
                                  const std::vector<uint32_t>& ps, std::vector<BatchQueryDev>& hq,

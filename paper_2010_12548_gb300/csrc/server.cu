@@ -117,6 +117,7 @@ struct sdb_server {
   uint32_t B = 0, P = 0;
   std::vector<uint32_t> ring_off, vx, vy, bb;
   sdb_polygons polys{};
+  sdb::PolyEdges pe;  // the polygons as edge sets, converted once
   // queue and tickets
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -211,7 +212,7 @@ sdb_status process(sdb_server* S, std::vector<std::shared_ptr<Ticket>>& batch, c
     }
     std::vector<CoverSet> sets;
     uint64_t nr = 0, nc = 0, mr = 0;
-    rc = sdb::build_query_coverings(&S->polys, S->B, cq, pp, pq, ps, mq, &sets,
+    rc = sdb::build_query_coverings(S->pe, S->B, cq, pp, pq, ps, mq, &sets,
                                     (uint32_t)chunks.size(), s, &nr, &nc, &mr);
     for (auto& set : sets) {
       auto c = std::make_shared<Chunk>();
@@ -403,6 +404,7 @@ sdb_status sdb_server_create(const sdb_points* pts, const sdb_polygons* polys,
   S->vx.assign(polys->x, polys->x + V);
   S->vy.assign(polys->y, polys->y + V);
   S->polys = sdb_polygons{S->P, S->ring_off.data(), S->vx.data(), S->vy.data()};
+  S->pe = sdb::poly_edges(&S->polys);
   for (uint32_t w = 0; w < cfg->workers; ++w) S->workers.emplace_back(worker, S);
   *out = S;
   return SDB_OK;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsdb.so")
 
 SDB_OK, SDB_EINVAL, SDB_ENOMEM, SDB_ECUDA, SDB_ETIMEOUT, SDB_EBUSY = range(6)
 LOOKUP_BINARY, LOOKUP_LEARNED, LOOKUP_RADIX_SPLINE = 0, 1, 2
-COVER_BOUNDARY_FLAGS = 1
+COVER_BOUNDARY_FLAGS, COVER_NONCONSERVATIVE = 1, 2
 
 
 class SdbError(RuntimeError):
@@ -30,6 +30,26 @@ class SdbError(RuntimeError):
 class _Polys(C.Structure):
     _fields_ = [("n_polygons", C.c_uint32), ("ring_off", C.c_void_p), ("x", C.c_void_p),
                 ("y", C.c_void_p)]
+
+
+class _MultiPolys(C.Structure):
+    _fields_ = [("n_polygons", C.c_uint32), ("n_rings", C.c_uint32),
+                ("poly_ring_off", C.c_void_p), ("ring_off", C.c_void_p), ("x", C.c_void_p),
+                ("y", C.c_void_p)]
+
+
+def _polys_arg(polys, keep):
+    """(struct, is_multi) for a polygon set; numpy arrays kept alive in keep.
+    A set with poly_ring_off holds polygons of several rings."""
+    arrs = [np.ascontiguousarray(a, np.uint32) for a in (polys.ring_off, polys.x, polys.y)]
+    keep.extend(arrs)
+    pro = getattr(polys, "poly_ring_off", None)
+    if pro is None:
+        return _Polys(len(arrs[0]) - 1, _np_ptr(arrs[0]), _np_ptr(arrs[1]), _np_ptr(arrs[2])), False
+    pro = np.ascontiguousarray(pro, np.uint32)
+    keep.append(pro)
+    return _MultiPolys(len(pro) - 1, len(arrs[0]) - 1, _np_ptr(pro), _np_ptr(arrs[0]),
+                       _np_ptr(arrs[1]), _np_ptr(arrs[2])), True
 
 
 class CoveringInfo(C.Structure):
@@ -85,6 +105,8 @@ def lib():
             "sdb_finest_level": ([U32, U64, P, P], I),
             "sdb_build_covering": ([P, U32, U64, P, P], I),
             "sdb_build_covering_ex": ([P, U32, U64, U32, P, P], I),
+            "sdb_build_covering_multi": ([P, U32, U64, U32, P, P], I),
+            "sdb_raster_join_multi": ([P, U32, U64, P, P, P, U64, U32, P, P, P], I),
             "sdb_join_aggregate_range": ([P, P, P, U64, P, I, P, P, P, P, P, P], I),
             "sdb_covering_get_info": ([P, P], I),
             "sdb_covering_build_index": ([P, U32, P], I),
@@ -190,15 +212,14 @@ class Covering:
 
 
 def build_covering(polys, grid_bits: int, eps: int, stream=None, flags: int = 0) -> Covering:
-    """sdb_build_covering_ex: polys has ring_off/x/y uint32 numpy arrays; flags 0
-    or COVER_BOUNDARY_FLAGS (boundary-flagged lists for result ranges)."""
-    off = np.ascontiguousarray(polys.ring_off, np.uint32)
-    x = np.ascontiguousarray(polys.x, np.uint32)
-    y = np.ascontiguousarray(polys.y, np.uint32)
-    sp = _Polys(len(off) - 1, _np_ptr(off), _np_ptr(x), _np_ptr(y))
+    """sdb_build_covering_ex (or _multi for polygons of several rings): polys has
+    ring_off/x/y (and poly_ring_off) uint32 numpy arrays; flags 0,
+    COVER_BOUNDARY_FLAGS (result ranges) or COVER_NONCONSERVATIVE."""
+    keep = []
+    sp, multi = _polys_arg(polys, keep)
     out = C.c_void_p()
-    _check(lib().sdb_build_covering_ex(C.byref(sp), grid_bits, int(eps), int(flags),
-                                       _stream(stream), C.byref(out)))
+    fn = lib().sdb_build_covering_multi if multi else lib().sdb_build_covering_ex
+    _check(fn(C.byref(sp), grid_bits, int(eps), int(flags), _stream(stream), C.byref(out)))
     return Covering(out.value)
 
 
@@ -206,14 +227,12 @@ def raster_join(polys, grid_bits: int, eps: int, x, y, attr, count, sum_=None, t
                 stream=None):
     """sdb_raster_join (Bounded Raster Join) on device tensors; polys as for
     build_covering."""
-    off = np.ascontiguousarray(polys.ring_off, np.uint32)
-    px = np.ascontiguousarray(polys.x, np.uint32)
-    py = np.ascontiguousarray(polys.y, np.uint32)
-    sp = _Polys(len(off) - 1, _np_ptr(off), _np_ptr(px), _np_ptr(py))
+    keep = []
+    sp, multi = _polys_arg(polys, keep)
     n = x.numel() if x is not None else 0
-    _check(lib().sdb_raster_join(C.byref(sp), grid_bits, int(eps), _dptr(x, 4), _dptr(y, 4),
-                                 _dptr(attr, 4), n, tile_bits, _dptr(count, 8), _dptr(sum_, 8),
-                                 _stream(stream)))
+    fn = lib().sdb_raster_join_multi if multi else lib().sdb_raster_join
+    _check(fn(C.byref(sp), grid_bits, int(eps), _dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), n,
+              tile_bits, _dptr(count, 8), _dptr(sum_, 8), _stream(stream)))
 
 
 def covering_build_index(cov: Covering, leaf_bits: int, stream=None):

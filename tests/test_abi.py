@@ -70,8 +70,11 @@ def test_invalid_arguments_rejected_on_host(sdblib):
     assert st == sdblib.SDB_EINVAL
     assert L.sdb_build_covering(None, 8, 4, None, None) == sdblib.SDB_EINVAL
     out = C.c_void_p()
-    assert L.sdb_build_covering_ex(None, 8, 4, 2, None, C.byref(out)) == sdblib.SDB_EINVAL
+    assert L.sdb_build_covering_ex(None, 8, 4, 4, None, C.byref(out)) == sdblib.SDB_EINVAL
     assert b"flags" in L.sdb_last_error()
+    assert L.sdb_build_covering_ex(None, 8, 4, 3, None, C.byref(out)) == sdblib.SDB_EINVAL
+    assert b"conservative" in L.sdb_last_error()
+    assert L.sdb_build_covering_multi(None, 8, 4, 0, None, C.byref(out)) == sdblib.SDB_EINVAL
     assert L.sdb_join_aggregate_range(None, None, None, 0, None, 0, None, None, None, None, None,
                                       None) == sdblib.SDB_EINVAL
     assert L.sdb_join_aggregate(None, None, None, 0, None, 0, None, None, None) == sdblib.SDB_EINVAL

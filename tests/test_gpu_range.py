@@ -142,7 +142,7 @@ def test_range_edge_cases(cuda, sdblib, orc):
         sdblib.join_aggregate_range(x, x, dev(torch, base.attr), cov, 0, z, z, z, None, z)
     assert e.value.status == sdblib.SDB_EINVAL
     with pytest.raises(sdblib.SdbError) as e:
-        sdblib.build_covering(P, B, 9, flags=2)
+        sdblib.build_covering(P, B, 9, flags=4)
     assert e.value.status == sdblib.SDB_EINVAL
 
 
