@@ -404,6 +404,21 @@ def main():
             live = c_np > 0
             row["boundary_fraction"] = float(b_np.sum() / max(1, c_np.sum()))
             row["mean_relative_count_interval"] = float((b_np[live] / c_np[live]).mean())
+            c.free()
+            # the non-conservative covering (Sec. 2.2): build, join, and the share
+            # of the boundary count it drops
+            e0.record(stream)
+            c = sdb.build_covering(w.polygons, 24, eps, stream, flags=sdb.COVER_NONCONSERVATIVE)
+            sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row["noncons_build_and_index_ms"] = e0.elapsed_time(e1)
+            row["noncons_ranges"] = c.info().n_ranges
+            row["noncons_join_ms"] = timed(torch, stream, lambda: sdb.join_aggregate(
+                x, y, a, c, sdb.LOOKUP_LEARNED, bs_, ba, stream), 5)
+            nc_np = bs_.cpu().numpy()
+            row["noncons_dropped_fraction_of_boundary"] = float(
+                (c_np - nc_np).sum() / max(1, b_np.sum()))
             rng_rows[str(eps)] = row
             c.free()
         res["range_estimation"] = rng_rows
