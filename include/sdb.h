@@ -153,6 +153,18 @@ sdb_status sdb_build_covering(const sdb_polygons *polys, uint32_t grid_bits, uin
 sdb_status sdb_build_covering_ex(const sdb_polygons *polys, uint32_t grid_bits, uint64_t eps,
                                  uint32_t flags, void *cuda_stream, sdb_covering **out);
 
+/* The coverings of the same polygons at n_eps distance bounds, built together
+ * in one level-synchronous pass (an eps sweep, as in the paper's experiments):
+ * out[i] receives the covering for eps[i], identical to what
+ * sdb_build_covering_ex(polys, grid_bits, eps[i], flags) returns, each to be
+ * released with sdb_covering_free.  Polygons that overlap one another are
+ * built one eps at a time.  Synchronises cuda_stream.  SDB_EINVAL: as
+ * sdb_build_covering_ex, NULL eps/out, n_eps outside 1..64.  On failure no
+ * covering is returned. */
+sdb_status sdb_build_coverings(const sdb_polygons *polys, uint32_t grid_bits, const uint64_t *eps,
+                               uint32_t n_eps, uint32_t flags, void *cuda_stream,
+                               sdb_covering **out);
+
 /* sdb_build_covering_ex for polygons of several rings (holes, multi-polygons):
  * a cell is a boundary cell of polygon j when it meets any of j's rings, an
  * interior cell when it meets none and lies in j's even-odd region.  The

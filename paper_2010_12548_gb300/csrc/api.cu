@@ -291,6 +291,45 @@ sdb_status sdb_build_covering_ex(const sdb_polygons* polys, uint32_t grid_bits, 
   return new_covering(poly_edges(polys), grid_bits, k, flags, (cudaStream_t)cuda_stream, out);
 }
 
+sdb_status sdb_build_coverings(const sdb_polygons* polys, uint32_t grid_bits, const uint64_t* eps,
+                               uint32_t n_eps, uint32_t flags, void* cuda_stream,
+                               sdb_covering** out) {
+  if (!out || !eps || n_eps == 0 || n_eps > 64) {
+    set_error("out or eps is NULL, or n_eps outside 1..64");
+    return SDB_EINVAL;
+  }
+  for (uint32_t i = 0; i < n_eps; ++i) out[i] = nullptr;
+  SDB_TRY(check_cover_flags(flags));
+  std::vector<uint32_t> ks(n_eps);
+  for (uint32_t i = 0; i < n_eps; ++i) SDB_TRY(finest(grid_bits, eps[i], &ks[i]));
+  SDB_TRY(validate_polygons(polys, grid_bits));
+  std::vector<sdb_covering*> covs(n_eps, nullptr);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_error("no CUDA device");
+    return SDB_ECUDA;
+  }
+  for (uint32_t i = 0; i < n_eps; ++i) {
+    covs[i] = new (std::nothrow) sdb_covering();
+    if (!covs[i]) {
+      for (auto* c : covs) delete c;
+      set_error("host allocation failed");
+      return SDB_ENOMEM;
+    }
+    covs[i]->device = dev;
+  }
+  sdb_status st = build_coverings_multi(poly_edges(polys), grid_bits, ks.data(), n_eps, flags,
+                                        (cudaStream_t)cuda_stream, covs.data());
+  if (st != SDB_OK) {
+    std::string msg = sdb_last_error();
+    for (auto* c : covs) free_covering(c);
+    set_error("%s", msg.c_str());
+    return st;
+  }
+  for (uint32_t i = 0; i < n_eps; ++i) out[i] = covs[i];
+  return SDB_OK;
+}
+
 sdb_status sdb_build_covering_multi(const sdb_multipolygons* polys, uint32_t grid_bits,
                                     uint64_t eps, uint32_t flags, void* cuda_stream,
                                     sdb_covering** out) {

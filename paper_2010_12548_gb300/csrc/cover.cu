@@ -710,12 +710,16 @@ __global__ void group_count_kernel(GroupCtx c, uint32_t* __restrict__ nopen,
 __global__ void query_sizes_kernel(const uint32_t* __restrict__ qfirst,
                                    const uint32_t* __restrict__ qlast,
                                    const uint32_t* __restrict__ gscan,
-                                   const uint32_t* __restrict__ nopen, uint32_t Q,
-                                   uint64_t* __restrict__ qsize) {
+                                   const uint32_t* __restrict__ nopen,
+                                   const uint32_t* __restrict__ gfirst, uint32_t G, uint64_t n,
+                                   uint32_t Q, uint64_t* __restrict__ qsize,
+                                   uint64_t* __restrict__ qcells) {
   uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= Q) return;
   const uint32_t a = qfirst[q], b = qlast[q];
   qsize[q] = a == NONE ? 2ull : (uint64_t)(gscan[b] + nopen[b] - gscan[a]) + 1ull;
+  // the query's records: from its first group's head to the next query's
+  qcells[q] = a == NONE ? 0ull : (b + 1 < G ? (uint64_t)gfirst[b + 1] : n) - gfirst[a];
 }
 
 __global__ void group_emit_kernel(GroupCtx c, const uint32_t* __restrict__ gscan,
@@ -909,6 +913,7 @@ static sdb_status merge_general(uint64_t* key, uint32_t* val, uint64_t n, uint32
   out->E = (uint64_t)R + 1;
   out->nids = nids;
   out->qoff = {0, out->E};
+  out->qcells = {n};
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   return SDB_OK;
 }
@@ -987,13 +992,19 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
     SDB_TRY_CUDA(cudaGetLastError());
   }
   SDB_TRY(exclusive_scan<uint32_t>(nopen, gscan, G, nullptr, s));
-  query_sizes_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, qlast, gscan, nopen, Q, qsize);
+  uint64_t* qcells;
+  SDB_TRY(sc.get(&qcells, Q));
+  query_sizes_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, qlast, gscan, nopen, gfirst, G, n, Q,
+                                                      qsize, qcells);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
   SDB_TRY(exclusive_scan<uint64_t>(qsize, qoff, Q, dE, s));
   SDB_TRY_CUDA(cudaMemcpyAsync(qoff + Q, dE, 8, cudaMemcpyDeviceToDevice, s));
   out->qoff.assign((size_t)Q + 1, 0);
+  out->qcells.assign(Q, 0);
   SDB_TRY_CUDA(cudaMemcpyAsync(out->qoff.data(), qoff, ((size_t)Q + 1) * 8, cudaMemcpyDeviceToHost,
+                               s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(out->qcells.data(), qcells, (size_t)Q * 8, cudaMemcpyDeviceToHost,
                                s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   const uint64_t E = out->qoff[Q];
@@ -1231,6 +1242,8 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   return merge_records(rkey, rval, n_rec, spec, d_qs, qshift, key_bits, s, out);
 }
 
+sdb_status finish_covering(sdb_covering* cov, cudaStream_t s);
+
 sdb_status build_covering_device(const PolyEdges& pe, uint32_t B, uint32_t k, uint32_t options,
                                  cudaStream_t s, sdb_covering* cov) {
   const uint32_t P = pe.P;
@@ -1267,7 +1280,11 @@ sdb_status build_covering_device(const PolyEdges& pe, uint32_t B, uint32_t k, ui
   cov->R = cs.E - 1;
   cov->nids = cs.nids;
   cov->ncells = cs.ncells;
-  // shared-memory sample of the starts for the top of the binary search
+  return finish_covering(cov, s);
+}
+
+// the binary search's shared-memory sample of the starts, and the size
+sdb_status finish_covering(sdb_covering* cov, cudaStream_t s) {
   const uint32_t SAMPLE_MAX = 2048;
   const uint64_t keys = cov->R + 1;
   uint32_t stride = (uint32_t)((keys + SAMPLE_MAX - 1) / SAMPLE_MAX);
@@ -1282,6 +1299,101 @@ sdb_status build_covering_device(const PolyEdges& pe, uint32_t B, uint32_t k, ui
   cov->bytes = (size_t)keys * 16 + (size_t)cov->nids * 4 + (size_t)ns * 8;
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   return SDB_OK;
+}
+
+namespace {
+// list offsets of a slice rebased to its first entry
+__global__ void rebase_u32_kernel(const uint32_t* __restrict__ in, uint64_t n,
+                                  uint32_t* __restrict__ out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i] - in[0];
+}
+// payloads of a slice: list references rebased by the slice's first entry
+__global__ void rebase_pay_kernel(const uint32_t* __restrict__ in, uint64_t n, uint32_t base,
+                                  uint32_t* __restrict__ out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t v = in[i];
+  out[i] = (v != NONE && (v & 0x80000000u)) ? (0x80000000u | ((v & 0x7fffffffu) - base)) : v;
+}
+}  // namespace
+
+sdb_status build_coverings_multi(const PolyEdges& pe, uint32_t B, const uint32_t* ks, uint32_t nq,
+                                 uint32_t options, cudaStream_t s, sdb_covering* const* covs) {
+  const uint32_t P = pe.P;
+  std::vector<CoverQuery> q(nq);
+  std::vector<uint32_t> pp((size_t)P * nq), pq((size_t)P * nq), ps((size_t)P * nq);
+  for (uint32_t i = 0; i < nq; ++i) {
+    q[i] = CoverQuery{B - ks[i], 0, 0, 1u << B, 1u << B};
+    for (uint32_t j = 0; j < P; ++j) {
+      pp[(size_t)i * P + j] = j;
+      pq[(size_t)i * P + j] = i;
+      ps[(size_t)i * P + j] = j;
+    }
+  }
+  CoverSpec spec;
+  spec.B = B;
+  spec.Q = nq;
+  spec.q = q.data();
+  spec.NP = P * nq;
+  spec.pair_poly = pp.data();
+  spec.pair_query = pq.data();
+  spec.pair_slot = ps.data();
+  spec.flags = (options & SDB_COVER_BOUNDARY_FLAGS) != 0;
+  spec.noncons = (options & SDB_COVER_NONCONSERVATIVE) != 0;
+  CoverSet cs;
+  sdb_status st = nq > 1 ? build_coverings(pe, spec, s, &cs) : SDB_EINVAL;
+  if (st != SDB_OK) {
+    // overlapping polygons (the joint merge needs disjoint cells per query),
+    // a key that does not fit, or one shift: one pass per shift
+    cs.release(s);
+    cudaStreamSynchronize(s);
+    for (uint32_t i = 0; i < nq; ++i) {
+      covs[i]->B = B;
+      SDB_TRY(build_covering_device(pe, B, ks[i], options, s, covs[i]));
+    }
+    return SDB_OK;
+  }
+  // each query's slice [qoff[i], qoff[i+1]) (its last entry the sentinel)
+  std::vector<uint32_t> lo(nq + 1, 0);
+  for (uint32_t i = 0; i < nq; ++i)
+    SDB_TRY_CUDA(cudaMemcpyAsync(&lo[i], cs.list_off + cs.qoff[i], 4, cudaMemcpyDeviceToHost, s));
+  lo[nq] = (uint32_t)cs.nids;
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  sdb_status rc = SDB_OK;
+  auto ck = [](cudaError_t e) {
+    return e == cudaSuccess ? SDB_OK : cuda_status(e, "covering slice", __FILE__, __LINE__);
+  };
+  for (uint32_t i = 0; i < nq && rc == SDB_OK; ++i) {
+    sdb_covering* c = covs[i];
+    const uint64_t a = cs.qoff[i], e = cs.qoff[i + 1] - a;
+    c->B = B;
+    c->k = ks[i];
+    c->F = B - ks[i];
+    c->P = P;
+    c->flagged = spec.flags;
+    c->R = e - 1;
+    c->nids = lo[i + 1] - lo[i];
+    c->ncells = cs.qcells[i];
+    rc = dalloc_n(&c->start, e, s);
+    if (rc == SDB_OK) rc = dalloc_n(&c->list_off, e, s);
+    if (rc == SDB_OK) rc = dalloc_n(&c->pay, e, s);
+    if (rc == SDB_OK) rc = dalloc_n(&c->list_ids, c->nids, s);
+    if (rc != SDB_OK) break;
+    rc = ck(cudaMemcpyAsync(c->start, cs.start + a, e * 8, cudaMemcpyDeviceToDevice, s));
+    if (rc == SDB_OK && c->nids)
+      rc = ck(cudaMemcpyAsync(c->list_ids, cs.list_ids + lo[i], (size_t)c->nids * 4,
+                              cudaMemcpyDeviceToDevice, s));
+    if (rc != SDB_OK) break;
+    rebase_u32_kernel<<<grid_for(e, 256), 256, 0, s>>>(cs.list_off + a, e, c->list_off);
+    note_launch();
+    rebase_pay_kernel<<<grid_for(e, 256), 256, 0, s>>>(cs.pay + a, e, (uint32_t)a, c->pay);
+    note_launch();
+    rc = ck(cudaGetLastError());
+    if (rc == SDB_OK) rc = finish_covering(c, s);
+  }
+  cs.release(s);
+  return rc;
 }
 
 }  // namespace sdb

@@ -252,6 +252,7 @@ struct CoverSet {
   uint32_t* pay = nullptr;       // E: empty / single slot / 2^31 | entry index
   uint64_t E = 0, nids = 0, ncells = 0;
   std::vector<uint64_t> qoff;    // host, Q + 1
+  std::vector<uint64_t> qcells;  // host, raster cells (records) of each query
   void release(cudaStream_t s);
 };
 sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStream_t s,
@@ -259,6 +260,11 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
 // options: SDB_COVER_BOUNDARY_FLAGS, SDB_COVER_NONCONSERVATIVE
 sdb_status build_covering_device(const PolyEdges& pe, uint32_t B, uint32_t k, uint32_t options,
                                  cudaStream_t s, sdb_covering* cov);
+// several finest shifts ks[0..nq) of the same polygons in one level-synchronous
+// pass (one covering per shift, as build_covering_device would make it);
+// polygons that overlap fall back to one pass per shift
+sdb_status build_coverings_multi(const PolyEdges& pe, uint32_t B, const uint32_t* ks, uint32_t nq,
+                                 uint32_t options, cudaStream_t s, sdb_covering* const* covs);
 // batch.cu ------------------------------------------------------------------
 // Per-query parameters of a batched join, and the covering arrays a query's
 // slice lives in (one chunk may serve many queries).

@@ -106,6 +106,7 @@ def lib():
             "sdb_build_covering": ([P, U32, U64, P, P], I),
             "sdb_build_covering_ex": ([P, U32, U64, U32, P, P], I),
             "sdb_build_covering_multi": ([P, U32, U64, U32, P, P], I),
+            "sdb_build_coverings": ([P, U32, P, U32, U32, P, P], I),
             "sdb_raster_join_multi": ([P, U32, U64, P, P, P, U64, U32, P, P, P], I),
             "sdb_join_aggregate_range": ([P, P, P, U64, P, I, P, P, P, P, P, P], I),
             "sdb_covering_get_info": ([P, P], I),
@@ -233,6 +234,19 @@ def raster_join(polys, grid_bits: int, eps: int, x, y, attr, count, sum_=None, t
     fn = lib().sdb_raster_join_multi if multi else lib().sdb_raster_join
     _check(fn(C.byref(sp), grid_bits, int(eps), _dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), n,
               tile_bits, _dptr(count, 8), _dptr(sum_, 8), _stream(stream)))
+
+
+def build_coverings(polys, grid_bits: int, eps_list, stream=None, flags: int = 0):
+    """sdb_build_coverings: one covering per eps, built in one pass."""
+    keep = []
+    sp, multi = _polys_arg(polys, keep)
+    if multi:
+        return [build_covering(polys, grid_bits, e, stream, flags) for e in eps_list]
+    eps = np.ascontiguousarray(eps_list, np.uint64)
+    outs = (C.c_void_p * len(eps))()
+    _check(lib().sdb_build_coverings(C.byref(sp), grid_bits, _np_ptr(eps), len(eps), int(flags),
+                                     _stream(stream), outs))
+    return [Covering(o) for o in outs]
 
 
 def covering_build_index(cov: Covering, leaf_bits: int, stream=None):

@@ -207,3 +207,23 @@ def test_deterministic(cuda, sdblib):
     r = [gpu_join(cuda, sdblib, c1, pts, lk) for lk in (0, 1, 0, 1)]
     for a, b in r[1:]:
         assert np.array_equal(a, r[0][0]) and np.array_equal(b, r[0][1])
+
+
+def test_build_coverings_eps_sweep(cuda, sdblib, orc):
+    """Coverings of an eps sweep built in one pass equal the ones built one at
+    a time, entry for entry (zone tiling: the joint pass; overlapping stars:
+    the per-eps fallback), with boundary flags and non-conservative too."""
+    T = W.zones263_tiling()
+    for flags in (0, 1, 2):
+        covs = sdblib.build_coverings(T, 24, [4096, 1024, 256], flags=flags)
+        for c, eps in zip(covs, (4096, 1024, 256)):
+            one = sdblib.build_covering(T, 24, eps, flags=flags)
+            for a, b in zip(sdblib.covering_export(c), sdblib.covering_export(one)):
+                assert np.array_equal(a, b), (flags, eps)
+            ia, ib = c.info(), one.info()
+            assert (ia.n_ranges, ia.n_list_ids, ia.n_cells) == (ib.n_ranges, ib.n_list_ids,
+                                                                ib.n_cells)
+    w = W.tiny_stars(10_000)
+    covs = sdblib.build_coverings(w.polygons, 16, [2048, 64, 5])
+    for c, eps in zip(covs, (2048, 64, 5)):
+        assert_same_covering(sdblib, c, orc.cover(w.polygons, eps))
