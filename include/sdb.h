@@ -220,6 +220,19 @@ sdb_status sdb_join_aggregate_range(const uint32_t *d_x, const uint32_t *d_y,
                                     uint64_t *d_bcount, int64_t *d_bsum, uint64_t *d_babs,
                                     void *cuda_stream);
 
+/* sdb_join_aggregate for n_covs coverings of the same polygons on the same grid
+ * (an eps sweep) in one pass over the points: each point is read and its cell
+ * id computed once, at the finest level among the coverings (a coarser id is
+ * its prefix), then looked up in every covering.  d_count and d_sum hold
+ * n_covs rows of P entries (row c for covs[c]), zeroed by the call; results
+ * equal n_covs separate sdb_join_aggregate calls.  Asynchronous.
+ * SDB_EINVAL: as sdb_join_aggregate, a NULL covering, coverings that differ in
+ * polygon count or grid bits, n_covs = 0. */
+sdb_status sdb_join_aggregate_multi(const uint32_t *d_x, const uint32_t *d_y,
+                                    const int32_t *d_attr, uint64_t n,
+                                    const sdb_covering *const *covs, uint32_t n_covs, int lookup,
+                                    uint64_t *d_count, int64_t *d_sum, void *cuda_stream);
+
 /* The same join for points in host memory against n_covs coverings at once
  * (e.g. the same polygons at several eps).  Points are streamed to the device
  * in chunks; each chunk is joined against every covering while the next chunk

@@ -508,6 +508,41 @@ sdb_status sdb_join_aggregate_range(const uint32_t* d_x, const uint32_t* d_y, co
                      true, d_bcount, d_bsum, d_babs);
 }
 
+sdb_status sdb_join_aggregate_multi(const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
+                                    uint64_t n, const sdb_covering* const* covs, uint32_t n_covs,
+                                    int lookup, uint64_t* d_count, int64_t* d_sum,
+                                    void* cuda_stream) {
+  if (!covs || n_covs == 0 || !d_count) {
+    set_error("covs or d_count is NULL, or n_covs = 0");
+    return SDB_EINVAL;
+  }
+  if (n > 0 && (!d_x || !d_y)) {
+    set_error("n > 0 with NULL coordinates");
+    return SDB_EINVAL;
+  }
+  if (d_sum && !d_attr && n > 0) {
+    set_error("d_sum requested without d_attr");
+    return SDB_EINVAL;
+  }
+  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED) {
+    set_error("unknown lookup %d", lookup);
+    return SDB_EINVAL;
+  }
+  for (uint32_t c = 0; c < n_covs; ++c) {
+    if (!covs[c] || covs[c]->P != covs[0]->P || covs[c]->B != covs[0]->B) {
+      set_error("covering %u is NULL or differs in polygon count or grid bits", c);
+      return SDB_EINVAL;
+    }
+    if (lookup == SDB_LOOKUP_LEARNED && !covs[c]->leaves) {
+      set_error("learned lookup requested but covering %u has no index", c);
+      return SDB_EINVAL;
+    }
+    SDB_TRY(check_device(covs[c]));
+  }
+  return launch_join_multi(d_x, d_y, d_attr, n, covs, n_covs, lookup, d_count, d_sum,
+                           (cudaStream_t)cuda_stream, true);
+}
+
 sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, const int32_t* h_attr,
                                    uint64_t n, const sdb_covering* const* covs, uint32_t n_covs,
                                    int lookup, uint64_t* h_count, int64_t* h_sum,
@@ -525,7 +560,9 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
     return SDB_EINVAL;
   }
   const uint32_t P = covs[0] ? covs[0]->P : 0;
+  bool same_grid = true;
   for (uint32_t c = 0; c < n_covs; ++c) {
+    if (covs[c] && covs[c]->B != covs[0]->B) same_grid = false;
     if (!covs[c] || covs[c]->P != P) {
       set_error("covering %u is NULL or has a different polygon count", c);
       return SDB_EINVAL;
@@ -581,9 +618,12 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
       st = cuda_status(e, "chunk copy", __FILE__, __LINE__);
       break;
     }
-    for (uint32_t k = 0; k < n_covs && st == SDB_OK; ++k)
-      st = launch_join(dx[b], dy[b], da[b], m, covs[k], lookup, d_cnt + (size_t)k * P,
-                       d_sum ? d_sum + (size_t)k * P : nullptr, s, false);
+    if (same_grid)  // one pass over the chunk for all coverings
+      st = launch_join_multi(dx[b], dy[b], da[b], m, covs, n_covs, lookup, d_cnt, d_sum, s, false);
+    else
+      for (uint32_t k = 0; k < n_covs && st == SDB_OK; ++k)
+        st = launch_join(dx[b], dy[b], da[b], m, covs[k], lookup, d_cnt + (size_t)k * P,
+                         d_sum ? d_sum + (size_t)k * P : nullptr, s, false);
     if (st == SDB_OK && cudaEventRecord(done[b], s) != cudaSuccess)
       st = cuda_status(cudaGetLastError(), "event record", __FILE__, __LINE__);
   }

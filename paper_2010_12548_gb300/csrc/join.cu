@@ -424,6 +424,142 @@ sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
 }
 
 
+// ------------------------------------------------ several coverings at once
+// One pass over the points for up to MULTI coverings of the same polygons (an
+// eps sweep): each point is loaded and its cell id computed once, at the
+// finest level of the set; a coarser covering's id is a prefix of it (the
+// curve's prefix property: drop 2 * (F - F') low bits).  Lookups and
+// accumulators are per covering; the coverings' root knots and samples are
+// read through the L1 cache.
+constexpr int MULTI = 4;
+struct MultiArgs {
+  JoinArgs c[MULTI];       // points, grid and the finest level's encoding in c[0]
+  uint32_t shift[MULTI];   // id of covering e = finest id >> shift[e]
+  uint32_t E;
+};
+
+template <int LOOKUP, bool SMEM, bool SUM>
+__global__ __launch_bounds__(THREADS, 4) void join_multi_kernel(MultiArgs M) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  const JoinArgs& A0 = M.c[0];
+  const size_t P = SMEM ? A0.P : 0;
+  const size_t per = SUM ? 3 * P : P;  // words of accumulators per covering
+  uint32_t* accw = reinterpret_cast<uint32_t*>(smem + HILBERT3_SMEM_BYTES);
+  Acc acc[MULTI];
+#pragma unroll
+  for (int e = 0; e < MULTI; ++e) {
+    acc[e].cnt = accw + e * per;
+    acc[e].lo = accw + e * per + P;
+    acc[e].hi = reinterpret_cast<int32_t*>(accw + e * per + 2 * P);
+    acc[e].bcnt = acc[e].blo = acc[e].alo = acc[e].ahi = nullptr;
+    acc[e].bhi = nullptr;
+  }
+  hilbert3_fill(s_tab);
+  if (SMEM)
+    for (uint32_t i = threadIdx.x; i < M.E * per; i += THREADS) accw[i] = 0;
+  __syncthreads();
+
+  const uint32_t gmask = ~((1u << A0.B) - 1u);
+  const uint64_t per_tile = (uint64_t)THREADS * 4;
+  const uint64_t ntiles = (A0.n + per_tile - 1) / per_tile;
+  uint32_t since_flush = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t e0 = t * per_tile + (uint64_t)threadIdx.x * 4;
+    uint32_t xs[4], ys[4];
+    int32_t as[4];
+    bool ok[4];
+    if (A0.vec && e0 + 3 < A0.n) {
+      const uint4 xv = __ldcs(reinterpret_cast<const uint4*>(A0.x + e0));
+      const uint4 yv = __ldcs(reinterpret_cast<const uint4*>(A0.y + e0));
+      xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
+      ys[0] = yv.x; ys[1] = yv.y; ys[2] = yv.z; ys[3] = yv.w;
+      if (SUM) {
+        const int4 av = __ldcs(reinterpret_cast<const int4*>(A0.attr + e0));
+        as[0] = av.x; as[1] = av.y; as[2] = av.z; as[3] = av.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ok[q] = true;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ok[q] = e0 + q < A0.n;
+        xs[q] = ok[q] ? A0.x[e0 + q] : 0u;
+        ys[q] = ok[q] ? A0.y[e0 + q] : 0u;
+        if (SUM) as[q] = ok[q] ? A0.attr[e0 + q] : 0;
+      }
+    }
+    uint64_t h[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ok[q] = ok[q] && !((xs[q] | ys[q]) & gmask);
+      h[q] = ok[q] ? hilbert3_encode(xs[q] >> A0.k, ys[q] >> A0.k, A0.nsteps, A0.st0, s_tab) : 0ull;
+    }
+#pragma unroll
+    for (int e = 0; e < MULTI; ++e) {
+      if (e >= (int)M.E) break;
+      const JoinArgs& A = M.c[e];
+      uint64_t he[4];
+      uint32_t r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) he[q] = h[q] >> M.shift[e];
+      if (LOOKUP == SDB_LOOKUP_BINARY)
+        find_bs<4>(he, r, A.sample, A);
+      else
+        find_learned<4>(he, r, A.knots, A);
+      uint32_t pay[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) pay[q] = ok[q] ? __ldg(A.pay + r[q]) : NONE;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t a = SUM ? as[q] : 0;
+        if (pay[q] < 0x80000000u) {
+          add_one<SMEM, SUM, false>(pay[q] & 0x3fffffffu, a, 0u, acc[e], A);
+        } else if (pay[q] != NONE) {
+          const uint32_t rr = pay[q] & 0x7fffffffu;
+          const uint32_t b = __ldg(A.list_off + rr), en = __ldg(A.list_off + rr + 1);
+          for (uint32_t i = b; i < en; ++i)
+            add_one<SMEM, SUM, false>(__ldg(A.list_ids + i) & 0x7fffffffu, a, 0u, acc[e], A);
+        }
+      }
+    }
+    if (SMEM && ++since_flush == FLUSH_TILES) {
+      since_flush = 0;
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < MULTI; ++e)
+        if (e < (int)M.E) flush_acc<SUM, false>(acc[e], M.c[e]);
+      __syncthreads();
+    }
+  }
+  if (SMEM) {
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < MULTI; ++e)
+      if (e < (int)M.E) flush_acc<SUM, false>(acc[e], M.c[e]);
+  }
+}
+
+template <int LOOKUP, bool SMEM, bool SUM>
+sdb_status launch_multi_t(const MultiArgs& M, cudaStream_t s) {
+  size_t smem = HILBERT3_SMEM_BYTES;
+  if (SMEM) smem += (size_t)M.E * M.c[0].P * (SUM ? 12 : 4);
+  smem = (smem + 15) & ~(size_t)15;
+  auto kern = join_multi_kernel<LOOKUP, SMEM, SUM>;
+  if (smem > 48 * 1024)
+    SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
+  if (per_sm < 1) per_sm = 1;
+  uint64_t blocks = (uint64_t)num_sms() * per_sm;
+  const uint64_t need = (M.c[0].n + 4 * THREADS - 1) / (4 * THREADS);
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  kern<<<(unsigned)blocks, THREADS, smem, s>>>(M);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  return SDB_OK;
+}
+
 template <bool RANGE>
 sdb_status launch_pick(const JoinArgs& A, int lookup, bool has_sum, cudaStream_t s) {
   const bool smem = A.P <= (RANGE ? SMEM_POLYS_RANGE : SMEM_POLYS);
@@ -485,6 +621,83 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.babs = reinterpret_cast<unsigned long long*>(babs);
   const bool has_sum = sum != nullptr;
   return bcount ? launch_pick<true>(A, lookup, has_sum, s) : launch_pick<false>(A, lookup, has_sum, s);
+}
+
+namespace {
+JoinArgs join_args(const uint32_t* x, const uint32_t* y, const int32_t* attr, uint64_t n,
+                   const sdb_covering* cov, uint64_t* count, int64_t* sum) {
+  JoinArgs A{};
+  A.x = x;
+  A.y = y;
+  A.attr = attr;
+  A.n = n;
+  A.count = reinterpret_cast<unsigned long long*>(count);
+  A.sum = reinterpret_cast<unsigned long long*>(sum);
+  A.vec = ((((uintptr_t)x) | ((uintptr_t)y) | (attr ? (uintptr_t)attr : 0)) & 15u) == 0;
+  A.start = cov->start;
+  A.pay = cov->pay;
+  A.list_off = cov->list_off;
+  A.list_ids = cov->list_ids;
+  A.sample = cov->sample;
+  A.R = cov->R;
+  A.sample_n = cov->sample_n;
+  A.stride = cov->sample_stride;
+  A.B = cov->B;
+  A.k = cov->k;
+  hilbert3_params(cov->F, &A.nsteps, &A.st0);
+  A.P = cov->P;
+  A.leaves = cov->leaves;
+  A.knots = cov->knots;
+  A.nknots = cov->leaf_bits ? (1u << cov->knot_bits) + 1 : 0;
+  A.wshift = cov->knot_wshift;
+  A.inv_w = 1.0f / (float)(1ull << cov->knot_wshift);
+  A.nleaves = cov->leaf_bits ? (1u << cov->leaf_bits) : 0u;
+  A.fallbacks = cov->fallbacks;
+  return A;
+}
+}  // namespace
+
+sdb_status launch_join_multi(const uint32_t* x, const uint32_t* y, const int32_t* attr,
+                             uint64_t n, const sdb_covering* const* covs, uint32_t E, int lookup,
+                             uint64_t* count, int64_t* sum, cudaStream_t s, bool zero) {
+  const uint32_t P = covs[0]->P;
+  for (uint32_t e0 = 0; e0 < E; e0 += MULTI) {
+    const uint32_t m = std::min<uint32_t>(MULTI, E - e0);
+    uint32_t finest = 0;  // the covering with the largest finest level encodes the ids
+    for (uint32_t e = 1; e < m; ++e)
+      if (covs[e0 + e]->F > covs[e0 + finest]->F) finest = e;
+    MultiArgs M{};
+    M.E = m;
+    for (uint32_t e = 0; e < m; ++e) {
+      const sdb_covering* c = covs[e0 + e];
+      if (zero) {
+        SDB_TRY_CUDA(cudaMemsetAsync(count + (size_t)(e0 + e) * P, 0, (size_t)P * 8, s));
+        if (sum) SDB_TRY_CUDA(cudaMemsetAsync(sum + (size_t)(e0 + e) * P, 0, (size_t)P * 8, s));
+        if (lookup == SDB_LOOKUP_LEARNED)
+          SDB_TRY_CUDA(cudaMemsetAsync(c->fallbacks, 0, sizeof(unsigned long long), s));
+      }
+      M.c[e] = join_args(x, y, attr, n, c, count + (size_t)(e0 + e) * P,
+                         sum ? sum + (size_t)(e0 + e) * P : nullptr);
+      M.shift[e] = 2 * (covs[e0 + finest]->F - c->F);
+    }
+    // the encoding parameters of the finest covering go with c[0]
+    const JoinArgs& Af = M.c[finest];
+    M.c[0].k = Af.k;
+    M.c[0].nsteps = Af.nsteps;
+    M.c[0].st0 = Af.st0;
+    if (n == 0) continue;
+    const bool smem = (uint64_t)m * P <= SMEM_POLYS;
+    const bool has_sum = sum != nullptr;
+    sdb_status st;
+    if (lookup == SDB_LOOKUP_BINARY)
+      st = smem ? (has_sum ? launch_multi_t<0, true, true>(M, s) : launch_multi_t<0, true, false>(M, s))
+                : (has_sum ? launch_multi_t<0, false, true>(M, s) : launch_multi_t<0, false, false>(M, s));
+    else
+      st = smem ? (has_sum ? launch_multi_t<1, true, true>(M, s) : launch_multi_t<1, true, false>(M, s))
+                : (has_sum ? launch_multi_t<1, false, true>(M, s) : launch_multi_t<1, false, false>(M, s));
+    SDB_TRY(st);
+  }
+  return SDB_OK;
 }
 
 }  // namespace sdb

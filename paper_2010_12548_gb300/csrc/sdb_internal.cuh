@@ -332,6 +332,11 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
 // join.cu
 // zero = true: outputs (and the fallback counter) are cleared first;
 // zero = false: the launch adds into them (chunked joins)
+// one pass over the points for E coverings of the same polygons and grid;
+// count / sum hold E rows of P entries (row e for covs[e])
+sdb_status launch_join_multi(const uint32_t* x, const uint32_t* y, const int32_t* attr,
+                             uint64_t n, const sdb_covering* const* covs, uint32_t E, int lookup,
+                             uint64_t* count, int64_t* sum, cudaStream_t s, bool zero);
 // bcount / bsum / babs (nullable; the covering must be flagged): result-range
 // partials of Sec. 6 (boundary count, boundary attribute sum, sum of magnitudes)
 sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr, uint64_t n,

@@ -107,6 +107,7 @@ def lib():
             "sdb_build_covering_ex": ([P, U32, U64, U32, P, P], I),
             "sdb_build_covering_multi": ([P, U32, U64, U32, P, P], I),
             "sdb_build_coverings": ([P, U32, P, U32, U32, P, P], I),
+            "sdb_join_aggregate_multi": ([P, P, P, U64, P, U32, I, P, P, P], I),
             "sdb_raster_join_multi": ([P, U32, U64, P, P, P, U64, U32, P, P, P], I),
             "sdb_join_aggregate_range": ([P, P, P, U64, P, I, P, P, P, P, P, P], I),
             "sdb_covering_get_info": ([P, P], I),
@@ -258,6 +259,16 @@ def join_aggregate(x, y, attr, cov: Covering, lookup: int, count, sum_=None, str
     n = x.numel() if x is not None else 0
     _check(lib().sdb_join_aggregate(_dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), n, cov.handle,
                                     lookup, _dptr(count, 8), _dptr(sum_, 8), _stream(stream)))
+
+
+def join_aggregate_multi(x, y, attr, covs, lookup: int, count, sum_=None, stream=None):
+    """sdb_join_aggregate_multi: one pass over the points for several coverings;
+    count / sum_ are int64 device tensors of shape (len(covs), P)."""
+    n = x.numel() if x is not None else 0
+    arr = (C.c_void_p * len(covs))(*[c.handle.value for c in covs])
+    _check(lib().sdb_join_aggregate_multi(_dptr(x, 4), _dptr(y, 4), _dptr(attr, 4), n, arr,
+                                          len(covs), lookup, _dptr(count, 8), _dptr(sum_, 8),
+                                          _stream(stream)))
 
 
 def join_aggregate_range(x, y, attr, cov: Covering, lookup: int, count, bcount, sum_=None,

@@ -227,3 +227,50 @@ def test_build_coverings_eps_sweep(cuda, sdblib, orc):
     covs = sdblib.build_coverings(w.polygons, 16, [2048, 64, 5])
     for c, eps in zip(covs, (2048, 64, 5)):
         assert_same_covering(sdblib, c, orc.cover(w.polygons, eps))
+
+
+def test_join_multi_equals_separate_joins(cuda, sdblib, orc):
+    """One pass over the points for several coverings (an eps sweep, more than
+    one group of four, unordered) equals one join per covering; the finest
+    covering need not come first; many polygons take global accumulators."""
+    torch = cuda
+    T = W.zones263_tiling()
+    pts = W.mobility_points(W.BASE_SEED + 12, 300_007, 24, 32)
+    eps_list = [1024, 2 ** 14, 64, 4096, 256, 2 ** 17]
+    covs = [sdblib.build_covering(T, 24, e) for e in eps_list]
+    for c in covs:
+        sdblib.covering_build_index(c, 14)
+    x, y, a = dev(torch, pts.x), dev(torch, pts.y), dev(torch, pts.attr)
+    E, P = len(covs), T.n
+    for lookup in (0, 1):
+        for n in (pts.n, 1, 1001):
+            cnt = torch.full((E, P), 7, dtype=torch.int64, device="cuda")
+            sm = torch.full((E, P), 7, dtype=torch.int64, device="cuda")
+            sdblib.join_aggregate_multi(x[:n], y[:n], a[:n], covs, lookup, cnt, sm)
+            torch.cuda.synchronize()
+            for e, c in enumerate(covs):
+                want = gpu_join(torch, sdblib, c, pts, lookup, x=x[:n], y=y[:n], a=a[:n])
+                assert np.array_equal(cnt[e].cpu().numpy().view(np.uint64), want[0]), (lookup, e)
+                assert np.array_equal(sm[e].cpu().numpy(), want[1]), (lookup, e)
+    # the oracle on one covering, and unaligned pointers
+    want = orc.cover(T, 64).join(pts.x[1:], pts.y[1:], pts.attr[1:])
+    cnt = torch.zeros((E, P), dtype=torch.int64, device="cuda")
+    sm = torch.zeros((E, P), dtype=torch.int64, device="cuda")
+    sdblib.join_aggregate_multi(x[1:], y[1:], a[1:], covs, 1, cnt, sm)
+    torch.cuda.synchronize()
+    assert np.array_equal(cnt[2].cpu().numpy().view(np.uint64), want[0])
+    assert np.array_equal(sm[2].cpu().numpy(), want[1])
+    # 3000 polygons x 2 coverings > 2048 accumulators: global atomics
+    rng = np.random.default_rng(5)
+    S = W.star_polygons(rng, 3000, 16, nverts=(3, 8), radius=(200, 900))
+    sp = W.uniform_points(rng, 100_000, 16)
+    sc = [sdblib.build_covering(S, 16, e) for e in (40, 300)]
+    cnt = torch.zeros((2, S.n), dtype=torch.int64, device="cuda")
+    sm = torch.zeros((2, S.n), dtype=torch.int64, device="cuda")
+    sdblib.join_aggregate_multi(dev(torch, sp.x), dev(torch, sp.y), dev(torch, sp.attr), sc, 0,
+                                cnt, sm)
+    torch.cuda.synchronize()
+    for e, eps in enumerate((40, 300)):
+        want = orc.cover(S, eps).join(sp.x, sp.y, sp.attr)
+        assert np.array_equal(cnt[e].cpu().numpy().view(np.uint64), want[0])
+        assert np.array_equal(sm[e].cpu().numpy(), want[1])
