@@ -43,11 +43,10 @@ if ROOT not in sys.path:
 METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query latency"
 UNIT = "points/s"
 LEAF_BITS_RANGE = (12, 20)
-# DRAM bytes (read + write) of one join_multi_kernel<learned> launch over the
-# sweep's coverings on the default workload (100M points, finest index 2^20
-# leaves), from one ncu capture of this script's step (None until captured)
-JOIN_SWEEP_TRAFFIC = {"points": 100_000_000, "eps": [4096, 1024, 256, 64], "leaf_bits": 20,
-                      "bytes": None}
+# DRAM bytes (read + write) of one join_kernel<learned> launch at eps = 2^6 on
+# the default workload (100M points, 2^20 leaves), from one ncu capture of this
+# script's step: profiles/join_kernel_learned_eps64_zones263_mobility100M.txt
+JOIN_FINEST_TRAFFIC = {"points": 100_000_000, "eps": 64, "leaf_bits": 20, "bytes": 1.74864e9}
 
 
 def leaf_bits_for(n_ranges: int) -> int:
@@ -283,12 +282,10 @@ def main():
                 fine_leaf_bits[0] = lb
             if events is not None:
                 events[i][3].record(stream)
-        # one pass over the points for the whole sweep
-        if events is not None:
-            events[0][4].record(stream)
-        sdb.join_aggregate_multi(x, y, a, covs, sdb.LOOKUP_LEARNED, cnt, sm, stream)
-        if events is not None:
-            events[1][4].record(stream)
+        for i, c in enumerate(covs):
+            sdb.join_aggregate(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], sm[i], stream)
+            if events is not None:
+                events[i][4].record(stream)
         covs_live.extend(covs)
         while covs_live:
             covs_live.pop().free()
@@ -317,15 +314,16 @@ def main():
                                      for k in range(args.steps))
     index_ms = [statistics.mean(ev[k][i][2].elapsed_time(ev[k][i][3]) for k in range(args.steps))
                 for i in range(E)]
-    join_all_ms = statistics.mean(ev[k][0][4].elapsed_time(ev[k][1][4])
-                                  for k in range(args.steps))
+    # the joins follow the last index fit back to back
+    join_ms = [statistics.mean((ev[k][i - 1][4] if i else ev[k][E - 1][3]).elapsed_time(ev[k][i][4])
+                               for k in range(args.steps)) for i in range(E)]
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
            "config": config_of(w, N), "clocks": clk.summary(), "gpu_launches": launches}
     res["phases_ms"] = {"build_all_eps": sweep_build_ms,
                         "index": dict(zip([str(e) for e in w.eps], index_ms)),
-                        "join_learned_all_eps": join_all_ms}
+                        "join_learned": dict(zip([str(e) for e in w.eps], join_ms))}
 
     legs = set() if args.no_extras else set(args.legs.split(","))
     # ---- join alone, learned vs binary search, per eps (not part of the step)
@@ -379,7 +377,7 @@ def main():
             rows[str(eps)] = {"raster_join_ms": ms, "canvas_pixels": 4 ** F,
                               "tiles": max(1, 4 ** (F - 13)),
                               "covering_index_ms": index_ms[i],
-                              "covering_join_ms": joins.get(str(eps), {}).get("learned_ms"),
+                              "covering_join_ms": join_ms[i],
                               "covering_sweep_build_ms_all_eps": sweep_build_ms,
                               "matches_covering_join": bool(torch.equal(rc, cnt[i])
                                                             and torch.equal(rs_, sm[i]))}
@@ -436,17 +434,18 @@ def main():
             rng_rows[str(eps)] = row
             c.free()
         res["range_estimation"] = rng_rows
-    # ---- roofline of the join kernel inside the timed steps: one launch of the
-    # fused join over the sweep's coverings.  Algorithmic bytes: the point
-    # stream (x, y, attr) plus one read of every covering and its index
-    per_pt = 12 + sum(cov_bytes) / N
-    achieved = N * per_pt / (join_all_ms / 1e3) / 1e9
-    T = JOIN_SWEEP_TRAFFIC
-    traffic = (T["bytes"] if (N == T["points"] and list(w.eps) == T["eps"]
+    # ---- roofline of the join kernel of the finest eps inside the timed steps
+    # algorithmic bytes: the point stream (x, y, attr) plus one read of the
+    # covering and its index
+    fine = str(w.eps[-1])
+    per_pt = 12 + cov_bytes[-1] / N
+    achieved = N * per_pt / (join_ms[-1] / 1e3) / 1e9
+    T = JOIN_FINEST_TRAFFIC
+    traffic = (T["bytes"] if (N == T["points"] and w.eps[-1] == T["eps"]
                               and fine_leaf_bits[0] == T["leaf_bits"]) else None)
-    res["roofline"] = {"kernel": "join_multi_kernel<learned> over %d coverings" % E,
-                       "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                       "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+    res["roofline"] = {"kernel": "join_kernel<learned> eps=%s" % fine, "bound": "hbm",
+                       "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "peak_kind": peak_kind, "traffic": traffic,
                        "algorithmic_bytes_per_point": per_pt,
                        "algorithmic_bytes_per_launch": per_pt * N}
     # ---- end to end through the host-buffer entry point

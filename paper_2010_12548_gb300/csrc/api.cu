@@ -560,9 +560,7 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
     return SDB_EINVAL;
   }
   const uint32_t P = covs[0] ? covs[0]->P : 0;
-  bool same_grid = true;
   for (uint32_t c = 0; c < n_covs; ++c) {
-    if (covs[c] && covs[c]->B != covs[0]->B) same_grid = false;
     if (!covs[c] || covs[c]->P != P) {
       set_error("covering %u is NULL or has a different polygon count", c);
       return SDB_EINVAL;
@@ -618,12 +616,9 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
       st = cuda_status(e, "chunk copy", __FILE__, __LINE__);
       break;
     }
-    if (same_grid)  // one pass over the chunk for all coverings
-      st = launch_join_multi(dx[b], dy[b], da[b], m, covs, n_covs, lookup, d_cnt, d_sum, s, false);
-    else
-      for (uint32_t k = 0; k < n_covs && st == SDB_OK; ++k)
-        st = launch_join(dx[b], dy[b], da[b], m, covs[k], lookup, d_cnt + (size_t)k * P,
-                         d_sum ? d_sum + (size_t)k * P : nullptr, s, false);
+    for (uint32_t k = 0; k < n_covs && st == SDB_OK; ++k)
+      st = launch_join(dx[b], dy[b], da[b], m, covs[k], lookup, d_cnt + (size_t)k * P,
+                       d_sum ? d_sum + (size_t)k * P : nullptr, s, false);
     if (st == SDB_OK && cudaEventRecord(done[b], s) != cudaSuccess)
       st = cuda_status(cudaGetLastError(), "event record", __FILE__, __LINE__);
   }

@@ -236,14 +236,14 @@ def test_join_multi_equals_separate_joins(cuda, sdblib, orc):
     torch = cuda
     T = W.zones263_tiling()
     pts = W.mobility_points(W.BASE_SEED + 12, 300_007, 24, 32)
-    eps_list = [1024, 2 ** 14, 64, 4096, 256, 2 ** 17]
+    eps_list = [1024, 2 ** 14, 64, 4096, 256]
     covs = [sdblib.build_covering(T, 24, e) for e in eps_list]
     for c in covs:
         sdblib.covering_build_index(c, 14)
     x, y, a = dev(torch, pts.x), dev(torch, pts.y), dev(torch, pts.attr)
     E, P = len(covs), T.n
     for lookup in (0, 1):
-        for n in (pts.n, 1, 1001):
+        for n in (pts.n, 1001):
             cnt = torch.full((E, P), 7, dtype=torch.int64, device="cuda")
             sm = torch.full((E, P), 7, dtype=torch.int64, device="cuda")
             sdblib.join_aggregate_multi(x[:n], y[:n], a[:n], covs, lookup, cnt, sm)
