@@ -139,6 +139,7 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
   extern __shared__ __align__(16) unsigned char dyn[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(dyn);                 // RS_TILE keys
   uint32_t* sv = reinterpret_cast<uint32_t*>(dyn + RS_TILE * 8);   // RS_TILE values
+  uint32_t* vin_s = sv + RS_TILE;  // the tile's values as read, staged asynchronously
   __shared__ uint32_t cnt[RS_WARPS][256];  // per warp and digit: count, then warp prefix
   __shared__ uint32_t dstart[256];         // digit's first slot in the tile
   __shared__ uint32_t gbase[256];          // digit's first global slot for this block
@@ -148,6 +149,19 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
   const size_t tile0 = (size_t)blockIdx.x * RS_TILE;
   const size_t base = tile0 + (size_t)w * (32 * RS_ITEMS);
   const unsigned lt = (1u << lane) - 1u;
+  // a full tile's values travel to shared memory while the keys are ranked
+  // (16-byte asynchronous copies; tiles start 16 KB apart in a 256-byte
+  // aligned buffer); a partial last tile reads them directly later
+  const bool full = tile0 + RS_TILE <= n && (reinterpret_cast<uintptr_t>(vin) & 15u) == 0;
+  if (VALS && full) {
+    for (int c = threadIdx.x; c < RS_TILE / 4; c += RS_THREADS) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(vin_s + 4 * c);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst),
+                   "l"(vin + tile0 + 4 * c)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   // keys stay in registers through the ranking; values are read only when
   // the tile's layout is known (fewer live registers, more resident warps)
   uint64_t k[RS_ITEMS];
@@ -209,10 +223,17 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
   }
   if (VALS) {
     uint32_t v[RS_ITEMS];
+    if (full) {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();  // every thread's copies have landed
 #pragma unroll
-    for (int it = 0; it < RS_ITEMS; ++it) {
-      const size_t g = base + (size_t)it * 32 + lane;
-      v[it] = g < n ? vin[g] : 0u;
+      for (int it = 0; it < RS_ITEMS; ++it) v[it] = vin_s[w * (32 * RS_ITEMS) + it * 32 + lane];
+    } else {
+#pragma unroll
+      for (int it = 0; it < RS_ITEMS; ++it) {
+        const size_t g = base + (size_t)it * 32 + lane;
+        v[it] = g < n ? vin[g] : 0u;
+      }
     }
 #pragma unroll
     for (int it = 0; it < RS_ITEMS; ++it)
@@ -240,7 +261,7 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
     return SDB_EINVAL;
   }
   uint32_t nblocks = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
-  constexpr size_t SCATTER_SMEM = (size_t)RS_TILE * 12;
+  constexpr size_t SCATTER_SMEM = (size_t)RS_TILE * (VALS ? 16 : 12);
   SDB_TRY_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<VALS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)SCATTER_SMEM));
