@@ -46,7 +46,7 @@ LEAF_BITS_RANGE = (12, 20)
 # DRAM bytes (read + write) of one join_kernel<learned> launch at eps = 2^6 on
 # the default workload (100M points, 2^20 leaves), from one ncu capture of this
 # script's step: profiles/join_kernel_learned_eps64_zones263_mobility100M.txt
-JOIN_FINEST_TRAFFIC = {"points": 100_000_000, "eps": 64, "leaf_bits": 20, "bytes": 1.74864e9}
+JOIN_FINEST_TRAFFIC = {"points": 100_000_000, "eps": 64, "leaf_bits": 20, "bytes": 1.76935e9}
 
 
 def leaf_bits_for(n_ranges: int) -> int:
