@@ -6,14 +6,15 @@ from 32 Gaussian clusters with sigma in [2^16, 2^19], 30% uniform, int32 fare
 attribute), the 263-zone jittered Voronoi tiling (20-400 vertices), and the
 eps sweep {2^12, 2^10, 2^8, 2^6}.
 
-One step = for every eps of the sweep: build the covering from the polygons
-(host arrays), fit the learned index (leaves for ~16 ranges each within
-2^12..2^20), and join all points with the learned lookup into per-polygon COUNT
-and SUM (device-resident points).
+One step = the coverings of the whole sweep built from the polygons (host
+arrays) in one pass, then for every eps the lookup structure (by default the
+cell table of 2^22 buckets; --lookup learned: the learned index with leaves
+for ~16 ranges each within 2^12..2^20) and the join of all points into
+per-polygon COUNT and SUM (device-resident points).
 The metric counts point-joins: points x eps levels per second.
 
 Besides the timed steps the script measures, outside the timed region, the
-join alone per eps for the learned and the binary-search lookups, the
+join alone per eps for the binary-search, learned and cell-table lookups, the
 Bounded Raster Join (canvas blend + conservative rasterisation), result
 range estimation (boundary-flagged coverings and the range join), point-indexed
 aggregation (sorted points, prefix sums, binary search vs RadixSpline), the
@@ -43,10 +44,13 @@ if ROOT not in sys.path:
 METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query latency"
 UNIT = "points/s"
 LEAF_BITS_RANGE = (12, 20)
-# DRAM bytes (read + write) of one join_kernel<learned> launch at eps = 2^6 on
-# the default workload (100M points, 2^20 leaves), from one ncu capture of this
-# script's step: profiles/join_kernel_learned_eps64_zones263_mobility100M.txt
-JOIN_FINEST_TRAFFIC = {"points": 100_000_000, "eps": 64, "leaf_bits": 20, "bytes": 1.76935e9}
+TABLE_BITS = 22  # cell table: 2^22 buckets (16 MB), fewer when 2F < 22
+# DRAM bytes (read + write) of one join_kernel launch at eps = 2^6 on the
+# default workload (100M points; 2^20 leaves or 2^22 table buckets), from one ncu
+# capture of this script's step: profiles/join_kernel_<lookup>_eps64_*.txt
+JOIN_FINEST_TRAFFIC = {
+    "learned": {"points": 100_000_000, "eps": 64, "bits": 20, "bytes": 1.76935e9},
+}
 
 
 def leaf_bits_for(n_ranges: int) -> int:
@@ -69,6 +73,9 @@ def parse():
                     help="extra legs: join (lookups alone), raster (Bounded Raster Join), range "
                          "(result range estimation), e2e, cpu, batch, pointindex (range "
                          "counting over sorted points), serve")
+    ap.add_argument("--lookup", default="table", choices=["table", "learned", "binary"],
+                    help="lookup of the timed step's joins")
+    ap.add_argument("--table-bits", type=int, default=TABLE_BITS)
     ap.add_argument("--pi-points", type=int, default=500_000_000)
     ap.add_argument("--lod-points", type=int, default=200_000_000)
     ap.add_argument("--lod-queries", type=int, default=4096)
@@ -221,7 +228,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": config_of(w, args.points),
+        "config": config_of(w, args.points, args.lookup, args.table_bits),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -229,11 +236,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def config_of(w, n_points):
-    return {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64_learned",
-            "points": n_points, "polygons": w.polygons.n, "grid_bits": 24, "eps": w.eps,
-            "leaf_bits": "ranges/16 within 2^12..2^20", "lookup": "learned",
-            "l2": "inputs larger than L2 (point arrays 12 B/pt)"}
+def config_of(w, n_points, lookup="table", table_bits=TABLE_BITS):
+    c = {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64_{lookup}",
+         "points": n_points, "polygons": w.polygons.n, "grid_bits": 24, "eps": w.eps,
+         "lookup": lookup, "l2": "inputs larger than L2 (point arrays 12 B/pt)"}
+    if lookup == "learned":
+        c["leaf_bits"] = "ranges/16 within 2^12..2^20"
+    if lookup == "table":
+        c["table_bits"] = f"min({table_bits}, 2F)"
+    return c
 
 
 def main():
@@ -263,7 +274,18 @@ def main():
     stream = torch.cuda.current_stream()
     covs_live = []
     cov_bytes = [0] * E
+    table_mixed = [0] * E
+    table_bytes_fine = [0]
     fine_leaf_bits = [0]
+    lookup = {"table": sdb.LOOKUP_TABLE, "learned": sdb.LOOKUP_LEARNED,
+              "binary": sdb.LOOKUP_BINARY}[args.lookup]
+
+    def prepare(c):
+        """The lookup structure of the step's lookup on covering c."""
+        if lookup == sdb.LOOKUP_LEARNED:
+            sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
+        elif lookup == sdb.LOOKUP_TABLE:
+            sdb.covering_build_table(c, args.table_bits, stream)
 
     def step(events=None):
         # the sweep's coverings in one pass, then per eps the index and the join
@@ -275,15 +297,18 @@ def main():
         for i, c in enumerate(covs):
             if events is not None:
                 events[i][2].record(stream)
-            lb = leaf_bits_for(c.info().n_ranges)
-            sdb.covering_build_index(c, lb, stream)
-            cov_bytes[i] = c.info().device_bytes  # covering + index
+            prepare(c)
+            inf = c.info()
             if i == E - 1:
-                fine_leaf_bits[0] = lb
+                fine_leaf_bits[0] = inf.index_leaf_bits
+            if i == E - 1 and lookup == sdb.LOOKUP_TABLE:
+                table_bytes_fine[0] = 4 * (1 << inf.table_bits) + 8 * inf.table_mixed
+            cov_bytes[i] = inf.device_bytes  # covering + index
+            table_mixed[i] = inf.table_mixed
             if events is not None:
                 events[i][3].record(stream)
         for i, c in enumerate(covs):
-            sdb.join_aggregate(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], sm[i], stream)
+            sdb.join_aggregate(x, y, a, c, lookup, cnt[i], sm[i], stream)
             if events is not None:
                 events[i][4].record(stream)
         covs_live.extend(covs)
@@ -320,10 +345,14 @@ def main():
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-           "config": config_of(w, N), "clocks": clk.summary(), "gpu_launches": launches}
+           "config": config_of(w, N, args.lookup, args.table_bits), "clocks": clk.summary(),
+           "gpu_launches": launches}
     res["phases_ms"] = {"build_all_eps": sweep_build_ms,
                         "index": dict(zip([str(e) for e in w.eps], index_ms)),
-                        "join_learned": dict(zip([str(e) for e in w.eps], join_ms))}
+                        "join_" + args.lookup: dict(zip([str(e) for e in w.eps], join_ms))}
+    if lookup == sdb.LOOKUP_TABLE:
+        res["table"] = {"bits": args.table_bits,
+                        "mixed_buckets": dict(zip([str(e) for e in w.eps], table_mixed))}
 
     legs = set() if args.no_extras else set(args.legs.split(","))
     # ---- join alone, learned vs binary search, per eps (not part of the step)
@@ -339,12 +368,19 @@ def main():
             lb = leaf_bits_for(inf.n_ranges)
             for bits in sorted({12, lb}):
                 variants.append((f"learned{bits}", sdb.LOOKUP_LEARNED, bits))
+            for tb in sorted({18, 20, TABLE_BITS, 24}):
+                variants.append((f"table{tb}", sdb.LOOKUP_TABLE, tb))
             for name, lk, bits in variants:
-                if bits is not None:
+                if lk == sdb.LOOKUP_LEARNED:
                     sdb.covering_build_index(c, bits, stream)
                     mw, xw = sdb.covering_index_stats(c)
                     row[name + "_window_mean"] = mw
                     row[name + "_window_max"] = xw
+                if lk == sdb.LOOKUP_TABLE:
+                    sdb.covering_build_table(c, bits, stream)
+                    ti = c.info()
+                    row[name + "_buckets"] = 1 << ti.table_bits
+                    row[name + "_mixed"] = ti.table_mixed
                 sdb.join_aggregate(x, y, a, c, lk, cnt[i], sm[i], stream)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
@@ -356,11 +392,13 @@ def main():
                 jm = e0.elapsed_time(e1) / reps
                 row[name + "_ms"] = jm
                 row[name + "_pts_per_s"] = N / (jm / 1e3)
-                if bits is not None:
+                if lk == sdb.LOOKUP_LEARNED:
                     row[name + "_fallbacks"] = sdb.covering_fallbacks(c, stream)
             row["learned_ms"] = row[f"learned{lb}_ms"]
             row["learned_pts_per_s"] = row[f"learned{lb}_pts_per_s"]
             row["leaf_bits"] = lb
+            row["table_ms"] = row[f"table{TABLE_BITS}_ms"]
+            row["table_pts_per_s"] = row[f"table{TABLE_BITS}_pts_per_s"]
             joins[str(eps)] = row
             c.free()
         res["join_only"] = joins
@@ -394,23 +432,20 @@ def main():
             e0.record(stream)
             c = sdb.build_covering(w.polygons, 24, eps, stream, flags=sdb.COVER_BOUNDARY_FLAGS)
             inf = c.info()
-            lb = leaf_bits_for(inf.n_ranges)
-            sdb.covering_build_index(c, lb, stream)
+            prepare(c)
             e1.record(stream)
             torch.cuda.synchronize()
             row = {"build_and_index_ms": e0.elapsed_time(e1), "ranges": inf.n_ranges,
-                   "plain_ranges": joins.get(str(eps), {}).get("ranges"), "leaf_bits": lb}
-            sdb.join_aggregate_range(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], bc, sm[i], bs_, ba,
-                                     stream)
+                   "plain_ranges": joins.get(str(eps), {}).get("ranges"), "lookup": args.lookup}
+            sdb.join_aggregate_range(x, y, a, c, lookup, cnt[i], bc, sm[i], bs_, ba, stream)
             torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(reps):
-                sdb.join_aggregate_range(x, y, a, c, sdb.LOOKUP_LEARNED, cnt[i], bc, sm[i], bs_,
-                                         ba, stream)
+                sdb.join_aggregate_range(x, y, a, c, lookup, cnt[i], bc, sm[i], bs_, ba, stream)
             e1.record(stream)
             torch.cuda.synchronize()
             row["range_join_ms"] = e0.elapsed_time(e1) / reps
-            row["plain_join_ms"] = joins.get(str(eps), {}).get("learned_ms")
+            row["plain_join_ms"] = join_ms[i]
             c_np = cnt[i].cpu().numpy()
             b_np = bc.cpu().numpy()
             live = c_np > 0
@@ -421,13 +456,13 @@ def main():
             # of the boundary count it drops
             e0.record(stream)
             c = sdb.build_covering(w.polygons, 24, eps, stream, flags=sdb.COVER_NONCONSERVATIVE)
-            sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
+            prepare(c)
             e1.record(stream)
             torch.cuda.synchronize()
             row["noncons_build_and_index_ms"] = e0.elapsed_time(e1)
             row["noncons_ranges"] = c.info().n_ranges
             row["noncons_join_ms"] = timed(torch, stream, lambda: sdb.join_aggregate(
-                x, y, a, c, sdb.LOOKUP_LEARNED, bs_, ba, stream), 5)
+                x, y, a, c, lookup, bs_, ba, stream), 5)
             nc_np = bs_.cpu().numpy()
             row["noncons_dropped_fraction_of_boundary"] = float(
                 (c_np - nc_np).sum() / max(1, b_np.sum()))
@@ -436,14 +471,19 @@ def main():
         res["range_estimation"] = rng_rows
     # ---- roofline of the join kernel of the finest eps inside the timed steps
     # algorithmic bytes: the point stream (x, y, attr) plus one read of the
-    # covering and its index
+    # lookup structure: the covering and its learned index, or the cell table
+    # (the covering itself is read only inside mixed buckets' windows)
     fine = str(w.eps[-1])
-    per_pt = 12 + cov_bytes[-1] / N
+    if lookup == sdb.LOOKUP_TABLE:
+        per_pt = 12 + table_bytes_fine[0] / N
+    else:
+        per_pt = 12 + cov_bytes[-1] / N
     achieved = N * per_pt / (join_ms[-1] / 1e3) / 1e9
-    T = JOIN_FINEST_TRAFFIC
-    traffic = (T["bytes"] if (N == T["points"] and w.eps[-1] == T["eps"]
-                              and fine_leaf_bits[0] == T["leaf_bits"]) else None)
-    res["roofline"] = {"kernel": "join_kernel<learned> eps=%s" % fine, "bound": "hbm",
+    T = JOIN_FINEST_TRAFFIC.get(args.lookup)
+    traffic = (T["bytes"] if (T and N == T["points"] and w.eps[-1] == T["eps"]
+                              and T.get("bits") in (None, fine_leaf_bits[0], args.table_bits))
+               else None)
+    res["roofline"] = {"kernel": "join_kernel<%s> eps=%s" % (args.lookup, fine), "bound": "hbm",
                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "peak_kind": peak_kind, "traffic": traffic,
                        "algorithmic_bytes_per_point": per_pt,
@@ -459,9 +499,9 @@ def main():
         def e2e_step():
             covs = sdb.build_coverings(w.polygons, 24, w.eps, stream)
             for c in covs:
-                sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
+                prepare(c)
             sdb.join_aggregate_host_ptrs(hx.data_ptr(), hy.data_ptr(), ha.data_ptr(), N, covs,
-                                         sdb.LOOKUP_LEARNED, hc.data_ptr(), hs.data_ptr(), stream)
+                                         lookup, hc.data_ptr(), hs.data_ptr(), stream)
             for c in covs:
                 c.free()
         for _ in range(max(1, args.warmup)):

@@ -54,7 +54,15 @@ typedef enum sdb_status {
   SDB_EBUSY = 5     /* the object is in use (e.g. a batch still running) */
 } sdb_status;
 
-enum { SDB_LOOKUP_BINARY = 0, SDB_LOOKUP_LEARNED = 1, SDB_LOOKUP_RADIX_SPLINE = 2 };
+/* Covering lookups: binary search over the range starts, the learned index
+ * (sdb_covering_build_index), the cell table (sdb_covering_build_table); and,
+ * for resident point sets only, the RadixSpline over the sorted point keys. */
+enum {
+  SDB_LOOKUP_BINARY = 0,
+  SDB_LOOKUP_LEARNED = 1,
+  SDB_LOOKUP_RADIX_SPLINE = 2,
+  SDB_LOOKUP_TABLE = 3
+};
 
 /* Polygons in host memory, read during the call only.  One simple ring per
  * polygon (no holes, no self-contact), vertices in [0, 2^grid_bits), either
@@ -101,6 +109,8 @@ typedef struct sdb_covering_info {
   uint64_t device_bytes;   /* device memory held by the covering */
   uint32_t index_leaf_bits;/* leaves = 2^index_leaf_bits, 0 = no learned index */
   uint32_t boundary_flags; /* 1 if built with SDB_COVER_BOUNDARY_FLAGS */
+  uint32_t table_bits;     /* cell table: 2^table_bits buckets (0: no table, or F = 0) */
+  uint64_t table_mixed;    /* buckets of the cell table that hold several ranges */
 } sdb_covering_info;
 
 /* Finest level for (grid_bits, eps), Sec. 2.2 (side eps/sqrt(2), so the
@@ -186,18 +196,33 @@ sdb_status sdb_covering_get_info(const sdb_covering *cov, sdb_covering_info *inf
  * SDB_EINVAL: leaf_bits outside 4..20. */
 sdb_status sdb_covering_build_index(sdb_covering *cov, uint32_t leaf_bits, void *cuda_stream);
 
+/* Build the cell table: a direct-mapped first level of a radix tree over the
+ * finest cell ids (the role of ACT's upper levels in Sec. 3, "Polygon
+ * Indexing": cells of large interior ranges are resolved at once).  With
+ * T = min(table_bits rounded down to even, 2F) the ids [0, 4^F) fall into 2^T
+ * buckets of 4^F / 2^T consecutive ids, the descendants of one cell of level
+ * T / 2 each, so a point's bucket is its cell id at that level.  A bucket that lies inside one range stores that range's
+ * polygon payload, so a point in it needs one table read; a bucket that meets
+ * several ranges stores the first and last of them, and the lookup binary
+ * searches that window of range starts.  Table: 4 bytes per bucket, plus 8
+ * bytes per mixed bucket.  Replaces a previous table.  Synchronises
+ * cuda_stream.  SDB_EINVAL: table_bits outside 8..26, or R >= 2^30 - 1. */
+sdb_status sdb_covering_build_table(sdb_covering *cov, uint32_t table_bits, void *cuda_stream);
+
 /* Index-nested-loop join fused with COUNT and SUM (Sec. 5.1): for each point i
  * with finest cell id h, the range r with start[r] <= h < start[r+1] is found
  * (lookup = SDB_LOOKUP_BINARY: binary search over the range starts;
  * SDB_LOOKUP_LEARNED: the learned index's prediction, a search bounded by the
  * stored error window, verified, with binary search as the fallback; requires
- * sdb_covering_build_index), and for every polygon j on r's list
- * d_count[j] += 1 and d_sum[j] += d_attr[i].  Both lookups give identical
- * results.  d_count and d_sum (P entries each) are zeroed by the call.
+ * sdb_covering_build_index; SDB_LOOKUP_TABLE: the cell table's bucket, then a
+ * binary search of the bucket's window if it holds several ranges; requires
+ * sdb_covering_build_table), and for every polygon j on r's list
+ * d_count[j] += 1 and d_sum[j] += d_attr[i].  All three lookups give
+ * identical results.  d_count and d_sum (P entries each) are zeroed by the call.
  * d_x, d_y, d_attr: n device values (SoA).  d_attr and d_sum may be NULL
  * (COUNT only).  n = 0 just zeroes the outputs.  Asynchronous.
  * SDB_EINVAL: null cov/d_count, n > 0 with null d_x/d_y, n > 0 with d_sum but no
- * d_attr, learned lookup without an index. */
+ * d_attr, learned lookup without an index, table lookup without a table. */
 sdb_status sdb_join_aggregate(const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
                               uint64_t n, const sdb_covering *cov, int lookup,
                               uint64_t *d_count, int64_t *d_sum, void *cuda_stream);
@@ -231,7 +256,8 @@ sdb_status sdb_join_aggregate_range(const uint32_t *d_x, const uint32_t *d_y,
  * sweep four separate joins are faster (6.4 vs 8.0 ms), so the hot path uses
  * those.  Asynchronous.
  * SDB_EINVAL: as sdb_join_aggregate, a NULL covering, coverings that differ in
- * polygon count or grid bits, n_covs = 0. */
+ * polygon count or grid bits, n_covs = 0, SDB_LOOKUP_TABLE (binary or learned
+ * lookups only). */
 sdb_status sdb_join_aggregate_multi(const uint32_t *d_x, const uint32_t *d_y,
                                     const int32_t *d_attr, uint64_t n,
                                     const sdb_covering *const *covs, uint32_t n_covs, int lookup,

@@ -21,7 +21,7 @@ OUT = os.path.join(HERE, "libsdb.so")
 BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["api.cu", "cover.cu", "sort.cu", "join.cu", "learned.cu", "noalloc.cu", "batch.cu",
            "pointindex.cu", "raster.cu",
-           "server.cu"]
+           "server.cu", "table.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

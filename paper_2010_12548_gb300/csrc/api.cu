@@ -111,8 +111,8 @@ static void free_covering(sdb_covering* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
-  void* ps[] = {c->start,  c->list_off, c->list_ids, c->pay,
-                c->sample, c->leaves,   c->knots,    c->fallbacks};
+  void* ps[] = {c->start,  c->list_off, c->list_ids, c->pay,    c->sample,
+                c->leaves, c->knots,    c->fallbacks, c->tab,   c->win};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, 0);
   cudaStreamSynchronize(0);
@@ -125,6 +125,22 @@ static sdb_status check_device(const sdb_covering* cov) {
   SDB_TRY_CUDA(cudaGetDevice(&dev));
   if (dev != cov->device) {
     set_error("covering lives on device %d, current device is %d", cov->device, dev);
+    return SDB_EINVAL;
+  }
+  return SDB_OK;
+}
+
+sdb_status check_lookup(const sdb_covering* cov, int lookup) {
+  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED && lookup != SDB_LOOKUP_TABLE) {
+    set_error("unknown lookup %d", lookup);
+    return SDB_EINVAL;
+  }
+  if (lookup == SDB_LOOKUP_LEARNED && !cov->leaves) {
+    set_error("learned lookup requested but the covering has no index");
+    return SDB_EINVAL;
+  }
+  if (lookup == SDB_LOOKUP_TABLE && !cov->tab) {
+    set_error("table lookup requested but the covering has no cell table");
     return SDB_EINVAL;
   }
   return SDB_OK;
@@ -425,8 +441,11 @@ sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* inf
   info->n_cells = cov->ncells;
   info->device_bytes =
       cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) + (4ull << cov->knot_bits) + 4 : 0);
+  if (cov->tab) info->device_bytes += (4ull << cov->tab_bits) + 8ull * cov->tab_mixed;
   info->index_leaf_bits = cov->leaf_bits;
   info->boundary_flags = cov->flagged ? 1u : 0u;
+  info->table_bits = cov->tab ? cov->tab_bits : 0u;
+  info->table_mixed = cov->tab_mixed;
   return SDB_OK;
 }
 
@@ -441,6 +460,19 @@ sdb_status sdb_covering_build_index(sdb_covering* cov, uint32_t leaf_bits, void*
   }
   SDB_TRY(check_device(cov));
   return build_learned_index(cov, leaf_bits, (cudaStream_t)cuda_stream);
+}
+
+sdb_status sdb_covering_build_table(sdb_covering* cov, uint32_t table_bits, void* cuda_stream) {
+  if (!cov) {
+    set_error("covering is NULL");
+    return SDB_EINVAL;
+  }
+  if (table_bits < 8 || table_bits > 26) {
+    set_error("table_bits %u outside 8..26", table_bits);
+    return SDB_EINVAL;
+  }
+  SDB_TRY(check_device(cov));
+  return build_cell_table(cov, table_bits, (cudaStream_t)cuda_stream);
 }
 
 sdb_status sdb_join_aggregate(const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
@@ -458,14 +490,7 @@ sdb_status sdb_join_aggregate(const uint32_t* d_x, const uint32_t* d_y, const in
     set_error("d_sum requested without d_attr");
     return SDB_EINVAL;
   }
-  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED) {
-    set_error("unknown lookup %d", lookup);
-    return SDB_EINVAL;
-  }
-  if (lookup == SDB_LOOKUP_LEARNED && !cov->leaves) {
-    set_error("learned lookup requested but the covering has no index");
-    return SDB_EINVAL;
-  }
+  SDB_TRY(check_lookup(cov, lookup));
   SDB_TRY(check_device(cov));
   return launch_join(d_x, d_y, d_attr, n, cov, lookup, d_count, d_sum, (cudaStream_t)cuda_stream,
                      true);
@@ -495,14 +520,7 @@ sdb_status sdb_join_aggregate_range(const uint32_t* d_x, const uint32_t* d_y, co
     set_error("d_sum requested without d_attr");
     return SDB_EINVAL;
   }
-  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED) {
-    set_error("unknown lookup %d", lookup);
-    return SDB_EINVAL;
-  }
-  if (lookup == SDB_LOOKUP_LEARNED && !cov->leaves) {
-    set_error("learned lookup requested but the covering has no index");
-    return SDB_EINVAL;
-  }
+  SDB_TRY(check_lookup(cov, lookup));
   SDB_TRY(check_device(cov));
   return launch_join(d_x, d_y, d_attr, n, cov, lookup, d_count, d_sum, (cudaStream_t)cuda_stream,
                      true, d_bcount, d_bsum, d_babs);
@@ -525,7 +543,7 @@ sdb_status sdb_join_aggregate_multi(const uint32_t* d_x, const uint32_t* d_y, co
     return SDB_EINVAL;
   }
   if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED) {
-    set_error("unknown lookup %d", lookup);
+    set_error("lookup %d: the multi-covering join takes the binary or learned lookup", lookup);
     return SDB_EINVAL;
   }
   for (uint32_t c = 0; c < n_covs; ++c) {
@@ -565,10 +583,7 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
       set_error("covering %u is NULL or has a different polygon count", c);
       return SDB_EINVAL;
     }
-    if (lookup == SDB_LOOKUP_LEARNED && !covs[c]->leaves) {
-      set_error("covering %u has no learned index", c);
-      return SDB_EINVAL;
-    }
+    SDB_TRY(check_lookup(covs[c], lookup));
     SDB_TRY(check_device(covs[c]));
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;

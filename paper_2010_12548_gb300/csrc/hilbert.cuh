@@ -56,18 +56,41 @@ __host__ __device__ inline void hilbert3_params(uint32_t F, uint32_t* nsteps, ui
   *st0 = ((3 * *nsteps - F) & 1u) ? 2u : 0u;
 }
 
+// One table step: the 3 top bits of xs and ys (coordinates shifted to the top
+// of the word) with the orientation st (already shifted left by 6) select a
+// table byte: 6 id bits and the next orientation.
+__device__ __forceinline__ uint32_t hilbert3_step(uint32_t& xs, uint32_t& ys, uint32_t& st,
+                                                  const uint32_t* row) {
+  const uint32_t idx = st | ((xs >> 26) & 0x38u) | (ys >> 29);
+  xs <<= 3;
+  ys <<= 3;
+  // the byte idx & 3 of the table word, upper bytes zero
+  const uint32_t e = __byte_perm(row[(idx >> 2) << 5], 0u, 0x4440u | (idx & 3u));
+  st = e & 0xc0u;
+  return e & 63u;
+}
+
 // id of cell (cx, cy) at the level the parameters were made for (cx, cy < 2^F)
 __device__ __forceinline__ uint64_t hilbert3_encode(uint32_t cx, uint32_t cy, uint32_t nsteps,
                                                     uint32_t st0, const uint32_t* tab) {
-  const uint32_t lane = threadIdx.x & 31u;
+  if (nsteps == 0) return 0;
+  const uint32_t* row = tab + (threadIdx.x & 31u);
+  const uint32_t sh = 32 - 3 * nsteps;  // nsteps <= 10: the 3 * nsteps bits at the top
+  uint32_t xs = cx << sh, ys = cy << sh, st = st0 << 6;
   uint64_t h = 0;
-  uint32_t st = st0;
-  for (int s = (int)nsteps - 1; s >= 0; --s) {
-    const uint32_t idx = (st << 6) | (((cx >> (3 * s)) & 7u) << 3) | ((cy >> (3 * s)) & 7u);
-    const uint32_t e = (tab[(idx >> 2) * 32 + lane] >> (8 * (idx & 3u))) & 255u;
-    h = (h << 6) | (e & 63u);
-    st = e >> 6;
-  }
+  for (uint32_t s = 0; s < nsteps; ++s) h = (h << 6) | hilbert3_step(xs, ys, st, row);
+  return h;
+}
+
+// the same for at most 5 table steps (ids below 2^30), in 32-bit arithmetic
+__device__ __forceinline__ uint32_t hilbert3_encode32(uint32_t cx, uint32_t cy, uint32_t nsteps,
+                                                      uint32_t st0, const uint32_t* tab) {
+  if (nsteps == 0) return 0;
+  const uint32_t* row = tab + (threadIdx.x & 31u);
+  const uint32_t sh = 32 - 3 * nsteps;
+  uint32_t xs = cx << sh, ys = cy << sh, st = st0 << 6;
+  uint32_t h = 0;
+  for (uint32_t s = 0; s < nsteps; ++s) h = (h << 6) | hilbert3_step(xs, ys, st, row);
   return h;
 }
 

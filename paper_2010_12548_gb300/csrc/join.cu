@@ -17,6 +17,10 @@
 //    prediction -> search inside the leaf's error window -> bracket verified
 //    (only the ends no probe has proven are read), binary search as the
 //    fallback (counted);
+//  * cell table: one read of the id's bucket gives the payload of most points
+//    directly; points in buckets that meet several ranges are held back in a
+//    per-warp shared-memory queue and, 32 at a time (all lanes busy), binary
+//    search their bucket's window of range starts;
 //  * aggregation: per point, its count and (split 16/16-bit, exact) attribute
 //    sum are added with shared-memory atomics to per-block accumulators
 //    (P <= SMEM_POLYS, flushed into the 64-bit outputs every few tiles), or
@@ -63,6 +67,11 @@ struct JoinArgs {
   float inv_w;
   uint32_t nleaves;
   unsigned long long* fallbacks;
+  // cell table: bucket = id of the point's cell at level txy_level, encoded
+  // with tsteps table steps from orientation tst0 (coordinates >> txy)
+  const uint32_t* tab;
+  const uint2* win;
+  uint32_t txy, tsteps, tst0;
 };
 
 // last r in [0, R) with start[r] <= h, global memory only (fallback path)
@@ -183,14 +192,20 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
   }
 }
 
-// Per-block accumulators in shared memory (P <= SMEM_POLYS): a 32-bit count and
-// the attribute sum split exactly into its low 16 bits (unsigned) and the rest
-// (signed), each in a 32-bit counter.  A block flushes them into the global
+// Per-block accumulators in shared memory (P <= SMEM_POLYS): a 32-bit count
+// and the attribute sum split exactly into its low 16 bits (unsigned) and the
+// rest (signed), each in a 32-bit counter.  A block flushes them into the global
 // 64-bit outputs at least every FLUSH_POINTS points, so none can wrap:
-// FLUSH_POINTS * 65535 < 2^32 and FLUSH_POINTS * 32768 < 2^31.
-constexpr uint32_t FLUSH_TILES = 32;
-constexpr uint32_t FLUSH_POINTS = FLUSH_TILES * THREADS * 4;
+// FLUSH_POINTS * 65535 < 2^32 and FLUSH_POINTS * 32768 < 2^31.  Points a warp
+// holds back in its queue (the cell-table lookup's mixed buckets, at most
+// QCAP - 1 per warp across a flush) count against the same bound.  (One 64-bit
+// word per polygon holding count and biased sum would need one atomic instead
+// of three, but 64-bit shared-memory atomics measured slower on GB300.)
+constexpr uint32_t FLUSH_TILES = 31;
+constexpr int QCAP = 64;  // per-warp queue of points in mixed cell-table buckets
+constexpr uint32_t FLUSH_POINTS = FLUSH_TILES * THREADS * 4 + (THREADS / 32) * (QCAP - 1);
 static_assert((uint64_t)FLUSH_POINTS * 65535u < (1ull << 32), "low-half counter could wrap");
+static_assert((uint64_t)FLUSH_POINTS * 32768u < (1ull << 31), "high-half counter could wrap");
 
 // With result-range partials, boundary points add to a second set of the same
 // counters and to a magnitude sum, split the same way (|a| <= 2^31, so its high
@@ -205,6 +220,57 @@ struct Acc {
   uint32_t* alo;
   uint32_t* ahi;
 };
+
+// shared-memory bytes of the accumulators of P polygons
+__host__ __device__ constexpr size_t acc_bytes(size_t P, bool SUM, bool RANGE) {
+  return P * ((SUM ? 12 : 4) + (RANGE ? (SUM ? 20 : 4) : 0));
+}
+
+// carve the accumulators out of shared memory at p: P words each of
+// cnt [, lo, hi] [, bcnt [, blo, bhi, alo, ahi]]
+template <bool SUM, bool RANGE>
+__device__ __forceinline__ Acc acc_at(unsigned char* p, size_t P) {
+  Acc s{};
+  uint32_t* w = reinterpret_cast<uint32_t*>(p);
+  s.cnt = w;
+  w += P;
+  if (SUM) {
+    s.lo = w;
+    s.hi = reinterpret_cast<int32_t*>(w + P);
+    w += 2 * P;
+  }
+  if (RANGE) {
+    s.bcnt = w;
+    w += P;
+    if (SUM) {
+      s.blo = w;
+      s.bhi = reinterpret_cast<int32_t*>(w + P);
+      s.alo = w + 2 * P;
+      s.ahi = w + 3 * P;
+    }
+  }
+  return s;
+}
+
+template <bool SUM, bool RANGE>
+__device__ __forceinline__ void acc_zero(const Acc& s, uint32_t P) {
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+    s.cnt[i] = 0;
+    if (SUM) {
+      s.lo[i] = 0;
+      s.hi[i] = 0;
+    }
+    if (RANGE) {
+      s.bcnt[i] = 0;
+      if (SUM) {
+        s.blo[i] = 0;
+        s.bhi[i] = 0;
+        s.alo[i] = 0;
+        s.ahi[i] = 0;
+      }
+    }
+  }
+}
 
 template <bool SMEM, bool SUM, bool RANGE>
 __device__ __forceinline__ void add_one(uint32_t p, int32_t a, uint32_t bnd, const Acc& s,
@@ -273,59 +339,77 @@ __device__ void flush_acc(const Acc& s, const JoinArgs& A) {
   }
 }
 
+// a range payload: one polygon (slot | boundary << 30), a list (2^31 | r; list
+// entries slot | boundary << 31), or none
+template <bool SMEM, bool SUM, bool RANGE>
+__device__ __forceinline__ void add_pay(uint32_t pay, int32_t a, const Acc& acc,
+                                        const JoinArgs& A) {
+  if (pay < 0x80000000u) {
+    add_one<SMEM, SUM, RANGE>(pay & 0x3fffffffu, a, (pay >> 30) & 1u, acc, A);
+  } else if (pay != NONE) {  // several polygons share the range
+    const uint32_t rr = pay & 0x7fffffffu;
+    const uint32_t b = __ldg(A.list_off + rr), e = __ldg(A.list_off + rr + 1);
+    for (uint32_t i = b; i < e; ++i) {
+      const uint32_t id = __ldg(A.list_ids + i);
+      add_one<SMEM, SUM, RANGE>(id & 0x7fffffffu, a, id >> 31, acc, A);
+    }
+  }
+}
+
+// a point held back in a warp's queue: its coordinates, mixed bucket and
+// attribute (16 bytes)
+struct QEnt {
+  uint32_t x, y, m;
+  int32_t a;
+};
+
+// the range of a point in mixed bucket m: its finest cell id, then a binary
+// search of the bucket's window of range starts
+template <bool SMEM, bool SUM, bool RANGE>
+__device__ __forceinline__ void resolve_mixed(const QEnt& E, const uint32_t* s_tab,
+                                              const Acc& acc, const JoinArgs& A) {
+  const uint64_t h = hilbert3_encode(E.x >> A.k, E.y >> A.k, A.nsteps, A.st0, s_tab);
+  const uint2 w = __ldg(A.win + E.m);
+  uint32_t lo = w.x, len = w.y - w.x + 1;
+  while (len > 1) {
+    const uint32_t half = len >> 1;
+    if (__ldg(A.start + lo + half) <= h) lo += half;
+    len -= half;
+  }
+  add_pay<SMEM, SUM, RANGE>(__ldg(A.pay + lo), E.a, acc, A);
+}
+
+// shared-memory bytes of the lookup's staging area (8-byte multiple)
+__host__ __device__ inline size_t stage_bytes(int lookup, const JoinArgs& A) {
+  if (lookup == SDB_LOOKUP_BINARY) return (size_t)A.sample_n * 8;
+  if (lookup == SDB_LOOKUP_LEARNED) return ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
+  return (size_t)(THREADS / 32) * QCAP * sizeof(QEnt);
+}
+
 template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
 __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   // the cell-id table, then the lookup staging (the binary search's sample of
-  // range starts, or the learned index's root knots), then the accumulators
+  // range starts, the learned index's root knots, or the cell-table lookup's
+  // per-warp queues), then the accumulators
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
   uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem + HILBERT3_SMEM_BYTES);
   float* s_knots = reinterpret_cast<float*>(smem + HILBERT3_SMEM_BYTES);
-  size_t off = HILBERT3_SMEM_BYTES + ((LOOKUP == SDB_LOOKUP_BINARY)
-                                          ? (size_t)A.sample_n * 8
-                                          : (((size_t)A.nknots * 4 + 7) & ~(size_t)7));
-  // accumulators: P words each of cnt [, lo, hi] [, bcnt [, blo, bhi, alo, ahi]]
-  Acc acc;
-  {
-    uint32_t* w = reinterpret_cast<uint32_t*>(smem + off);
-    const size_t P = SMEM ? A.P : 0;
-    acc.cnt = w;
-    w += P;
-    acc.lo = w;
-    acc.hi = reinterpret_cast<int32_t*>(w + (SUM ? P : 0));
-    w += SUM ? 2 * P : 0;
-    acc.bcnt = w;
-    w += RANGE ? P : 0;
-    acc.blo = w;
-    acc.bhi = reinterpret_cast<int32_t*>(w + ((RANGE && SUM) ? P : 0));
-    acc.alo = w + ((RANGE && SUM) ? 2 * P : 0);
-    acc.ahi = w + ((RANGE && SUM) ? 3 * P : 0);
-  }
+  QEnt* s_q = reinterpret_cast<QEnt*>(smem + HILBERT3_SMEM_BYTES) + (threadIdx.x >> 5) * QCAP;
+  const size_t off = HILBERT3_SMEM_BYTES + stage_bytes(LOOKUP, A);
+  const Acc acc = acc_at<SUM, RANGE>(smem + off, SMEM ? A.P : 0);
 
   hilbert3_fill(s_tab);
-  if (LOOKUP == SDB_LOOKUP_BINARY)
+  if constexpr (LOOKUP == SDB_LOOKUP_BINARY)
     for (uint32_t i = threadIdx.x; i < A.sample_n; i += THREADS) s_sample[i] = A.sample[i];
-  else
+  if constexpr (LOOKUP == SDB_LOOKUP_LEARNED)
     for (uint32_t i = threadIdx.x; i < A.nknots; i += THREADS) s_knots[i] = A.knots[i];
-  if (SMEM)
-    for (uint32_t i = threadIdx.x; i < A.P; i += THREADS) {
-      acc.cnt[i] = 0;
-      if (SUM) {
-        acc.lo[i] = 0;
-        acc.hi[i] = 0;
-      }
-      if (RANGE) {
-        acc.bcnt[i] = 0;
-        if (SUM) {
-          acc.blo[i] = 0;
-          acc.bhi[i] = 0;
-          acc.alo[i] = 0;
-          acc.ahi[i] = 0;
-        }
-      }
-    }
+  if (SMEM) acc_zero<SUM, RANGE>(acc, A.P);
   __syncthreads();
 
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t qn = 0;  // entries in this warp's queue (warp-uniform)
   const uint32_t gmask = ~((1u << A.B) - 1u);
   const uint64_t per_tile = (uint64_t)THREADS * 4;
   const uint64_t ntiles = (A.n + per_tile - 1) / per_tile;
@@ -357,34 +441,60 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
         if (SUM) as[q] = ok[q] ? A.attr[e0 + q] : 0;
       }
     }
-    uint64_t h[4];
+    if (!SUM) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      ok[q] = ok[q] && !((xs[q] | ys[q]) & gmask);
-      h[q] = ok[q] ? hilbert3_encode(xs[q] >> A.k, ys[q] >> A.k, A.nsteps, A.st0, s_tab) : 0ull;
+      for (int q = 0; q < 4; ++q) as[q] = 0;
     }
-    uint32_t r[4];
-    if (LOOKUP == SDB_LOOKUP_BINARY)
-      find_bs<4>(h, r, s_sample, A);
-    else
-      find_learned<4>(h, r, s_knots, A);
-    uint32_t pay[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) pay[q] = ok[q] ? __ldg(A.pay + r[q]) : NONE;
+    for (int q = 0; q < 4; ++q) ok[q] = ok[q] && !((xs[q] | ys[q]) & gmask);
+    if constexpr (LOOKUP == SDB_LOOKUP_TABLE) {
+      // the bucket is the id of the point's cell at the table's level (the
+      // curve's prefix property: the top bits of the finest id); only points
+      // in mixed buckets need their finest id
+      uint32_t e[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int32_t a = SUM ? as[q] : 0;
-      // single polygon: slot | boundary << 30; list entries: slot | boundary << 31
-      if (pay[q] < 0x80000000u) {
-        add_one<SMEM, SUM, RANGE>(pay[q] & 0x3fffffffu, a, (pay[q] >> 30) & 1u, acc, A);
-      } else if (pay[q] != NONE) {  // several polygons share the range
-        const uint32_t rr = pay[q] & 0x7fffffffu;
-        const uint32_t b = __ldg(A.list_off + rr), e = __ldg(A.list_off + rr + 1);
-        for (uint32_t i = b; i < e; ++i) {
-          const uint32_t id = __ldg(A.list_ids + i);
-          add_one<SMEM, SUM, RANGE>(id & 0x7fffffffu, a, id >> 31, acc, A);
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t b =
+            ok[q] ? hilbert3_encode32(xs[q] >> A.txy, ys[q] >> A.txy, A.tsteps, A.tst0, s_tab) : 0u;
+        e[q] = ok[q] ? __ldg(A.tab + b) : NONE;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool mix = e[q] >= TAB_MIXED && e[q] != NONE;
+        const uint32_t bal = __ballot_sync(FULL, mix);
+        if (mix) {
+          QEnt& E = s_q[qn + __popc(bal & lt)];
+          E.x = xs[q];
+          E.y = ys[q];
+          E.m = e[q] & ~TAB_MIXED;
+          E.a = as[q];
+        } else {
+          add_pay<SMEM, SUM, RANGE>(e[q], as[q], acc, A);
+        }
+        qn += __popc(bal);
+        if (qn >= 32) {  // a full warp of held-back points: search their windows
+          __syncwarp();
+          qn -= 32;
+          const QEnt E = s_q[qn + lane];
+          __syncwarp();
+          resolve_mixed<SMEM, SUM, RANGE>(E, s_tab, acc, A);
         }
       }
+    } else {
+      uint64_t h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        h[q] = ok[q] ? hilbert3_encode(xs[q] >> A.k, ys[q] >> A.k, A.nsteps, A.st0, s_tab) : 0ull;
+      uint32_t r[4];
+      if constexpr (LOOKUP == SDB_LOOKUP_BINARY)
+        find_bs<4>(h, r, s_sample, A);
+      else
+        find_learned<4>(h, r, s_knots, A);
+      uint32_t pay[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) pay[q] = ok[q] ? __ldg(A.pay + r[q]) : NONE;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) add_pay<SMEM, SUM, RANGE>(pay[q], as[q], acc, A);
     }
     if (SMEM && ++since_flush == FLUSH_TILES) {
       since_flush = 0;
@@ -392,6 +502,10 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
       flush_acc<SUM, RANGE>(acc, A);
       __syncthreads();
     }
+  }
+  if constexpr (LOOKUP == SDB_LOOKUP_TABLE) {  // the rest of the queue
+    __syncwarp();
+    if (lane < qn) resolve_mixed<SMEM, SUM, RANGE>(s_q[lane], s_tab, acc, A);
   }
   if (SMEM) {
     __syncthreads();
@@ -401,12 +515,8 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
 
 template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
 sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
-  size_t smem = HILBERT3_SMEM_BYTES;
-  if (SMEM) smem += (size_t)A.P * ((SUM ? 12 : 4) + (RANGE ? (SUM ? 20 : 4) : 0));
-  if (LOOKUP == SDB_LOOKUP_BINARY)
-    smem += (size_t)A.sample_n * 8;
-  else
-    smem += ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
+  size_t smem = HILBERT3_SMEM_BYTES + stage_bytes(LOOKUP, A);
+  if (SMEM) smem += acc_bytes(A.P, SUM, RANGE);
   smem = (smem + 15) & ~(size_t)15;
   auto kern = join_kernel<LOOKUP, SMEM, SUM, RANGE>;
   if (smem > 48 * 1024)
@@ -444,20 +554,15 @@ __global__ __launch_bounds__(THREADS, 4) void join_multi_kernel(MultiArgs M) {
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
   const JoinArgs& A0 = M.c[0];
   const size_t P = SMEM ? A0.P : 0;
-  const size_t per = SUM ? 3 * P : P;  // words of accumulators per covering
-  uint32_t* accw = reinterpret_cast<uint32_t*>(smem + HILBERT3_SMEM_BYTES);
+  unsigned char* accb = smem + HILBERT3_SMEM_BYTES;
   Acc acc[MULTI];
 #pragma unroll
-  for (int e = 0; e < MULTI; ++e) {
-    acc[e].cnt = accw + e * per;
-    acc[e].lo = accw + e * per + P;
-    acc[e].hi = reinterpret_cast<int32_t*>(accw + e * per + 2 * P);
-    acc[e].bcnt = acc[e].blo = acc[e].alo = acc[e].ahi = nullptr;
-    acc[e].bhi = nullptr;
-  }
+  for (int e = 0; e < MULTI; ++e) acc[e] = acc_at<SUM, false>(accb + e * acc_bytes(P, SUM, false), P);
   hilbert3_fill(s_tab);
   if (SMEM)
-    for (uint32_t i = threadIdx.x; i < M.E * per; i += THREADS) accw[i] = 0;
+#pragma unroll
+    for (int e = 0; e < MULTI; ++e)
+      if (e < (int)M.E) acc_zero<SUM, false>(acc[e], (uint32_t)P);
   __syncthreads();
 
   const uint32_t gmask = ~((1u << A0.B) - 1u);
@@ -511,17 +616,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_multi_kernel(MultiArgs M) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) pay[q] = ok[q] ? __ldg(A.pay + r[q]) : NONE;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int32_t a = SUM ? as[q] : 0;
-        if (pay[q] < 0x80000000u) {
-          add_one<SMEM, SUM, false>(pay[q] & 0x3fffffffu, a, 0u, acc[e], A);
-        } else if (pay[q] != NONE) {
-          const uint32_t rr = pay[q] & 0x7fffffffu;
-          const uint32_t b = __ldg(A.list_off + rr), en = __ldg(A.list_off + rr + 1);
-          for (uint32_t i = b; i < en; ++i)
-            add_one<SMEM, SUM, false>(__ldg(A.list_ids + i) & 0x7fffffffu, a, 0u, acc[e], A);
-        }
-      }
+      for (int q = 0; q < 4; ++q) add_pay<SMEM, SUM, false>(pay[q], SUM ? as[q] : 0, acc[e], A);
     }
     if (SMEM && ++since_flush == FLUSH_TILES) {
       since_flush = 0;
@@ -543,7 +638,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_multi_kernel(MultiArgs M) {
 template <int LOOKUP, bool SMEM, bool SUM>
 sdb_status launch_multi_t(const MultiArgs& M, cudaStream_t s) {
   size_t smem = HILBERT3_SMEM_BYTES;
-  if (SMEM) smem += (size_t)M.E * M.c[0].P * (SUM ? 12 : 4);
+  if (SMEM) smem += (size_t)M.E * acc_bytes(M.c[0].P, SUM, false);
   smem = (smem + 15) & ~(size_t)15;
   auto kern = join_multi_kernel<LOOKUP, SMEM, SUM>;
   if (smem > 48 * 1024)
@@ -567,6 +662,11 @@ sdb_status launch_pick(const JoinArgs& A, int lookup, bool has_sum, cudaStream_t
     if (smem)
       return has_sum ? launch_t<0, true, true, RANGE>(A, s) : launch_t<0, true, false, RANGE>(A, s);
     return has_sum ? launch_t<0, false, true, RANGE>(A, s) : launch_t<0, false, false, RANGE>(A, s);
+  }
+  if (lookup == SDB_LOOKUP_TABLE) {
+    if (smem)
+      return has_sum ? launch_t<3, true, true, RANGE>(A, s) : launch_t<3, true, false, RANGE>(A, s);
+    return has_sum ? launch_t<3, false, true, RANGE>(A, s) : launch_t<3, false, false, RANGE>(A, s);
   }
   if (smem)
     return has_sum ? launch_t<1, true, true, RANGE>(A, s) : launch_t<1, true, false, RANGE>(A, s);
@@ -616,6 +716,10 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.inv_w = 1.0f / (float)(1ull << cov->knot_wshift);
   A.nleaves = cov->leaf_bits ? (1u << cov->leaf_bits) : 0u;
   A.fallbacks = cov->fallbacks;
+  A.tab = cov->tab;
+  A.win = cov->win;
+  A.txy = cov->B - cov->tab_bits / 2;
+  hilbert3_params(cov->tab_bits / 2, &A.tsteps, &A.tst0);
   A.bcount = reinterpret_cast<unsigned long long*>(bcount);
   A.bsum = reinterpret_cast<unsigned long long*>(bsum);
   A.babs = reinterpret_cast<unsigned long long*>(babs);

@@ -74,14 +74,7 @@ extern "C" sdb_status sdb_join_aggregate_host_noalloc(const uint32_t* h_x, const
     set_error("h_sum requested without h_attr");
     return SDB_EINVAL;
   }
-  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED) {
-    set_error("unknown lookup %d", lookup);
-    return SDB_EINVAL;
-  }
-  if (lookup == SDB_LOOKUP_LEARNED && !cov->leaves) {
-    set_error("learned lookup requested but the covering has no index");
-    return SDB_EINVAL;
-  }
+  SDB_TRY(check_lookup(cov, lookup));
   if (cov->P > MAXP) {
     set_error("%u polygons exceed the allocation-free join's maximum of %llu", cov->P,
               (unsigned long long)MAXP);

@@ -163,6 +163,11 @@ struct sdb_covering {
   float* knots = nullptr;                  // root knots (leaf units)
   sdb::LeafRec* leaves = nullptr;          // 2^leaf_bits
   unsigned long long* fallbacks = nullptr; // device counter
+  // cell table (table.cu): 2^tab_bits buckets of 2^tab_shift ids
+  uint32_t* tab = nullptr;  // payload, or TAB_MIXED | index into win
+  uint2* win = nullptr;     // first and last range of each mixed bucket
+  uint32_t tab_bits = 0, tab_shift = 0;
+  uint64_t tab_mixed = 0;
   size_t bytes = 0;
 };
 
@@ -329,6 +334,15 @@ sdb_status polygon_bboxes(const sdb_polygons* polys, uint32_t B, std::vector<uin
 
 // learned.cu
 sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream_t s);
+
+// cell table entries: a range payload, or TAB_MIXED | m for the m-th bucket that
+// meets several ranges (m < TAB_MIXED_MAX - 1; payload values 2^31 | r need
+// r < 2^30 - 1, so the two never collide)
+constexpr uint32_t TAB_MIXED = 0xC0000000u;
+constexpr uint32_t TAB_MIXED_MAX = 0x3fffffffu;
+sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t s);
+// lookup is known and the covering has what it needs (api.cu)
+sdb_status check_lookup(const sdb_covering* cov, int lookup);
 // join.cu
 // zero = true: outputs (and the fallback counter) are cleared first;
 // zero = false: the launch adds into them (chunked joins)

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsdb.so")
 
 SDB_OK, SDB_EINVAL, SDB_ENOMEM, SDB_ECUDA, SDB_ETIMEOUT, SDB_EBUSY = range(6)
-LOOKUP_BINARY, LOOKUP_LEARNED, LOOKUP_RADIX_SPLINE = 0, 1, 2
+LOOKUP_BINARY, LOOKUP_LEARNED, LOOKUP_RADIX_SPLINE, LOOKUP_TABLE = 0, 1, 2, 3
 COVER_BOUNDARY_FLAGS, COVER_NONCONSERVATIVE = 1, 2
 
 
@@ -57,7 +57,8 @@ class CoveringInfo(C.Structure):
                 ("finest_level", C.c_uint32), ("n_polygons", C.c_uint32),
                 ("n_ranges", C.c_uint64), ("n_list_ids", C.c_uint64), ("n_cells", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("index_leaf_bits", C.c_uint32),
-                ("boundary_flags", C.c_uint32)]
+                ("boundary_flags", C.c_uint32), ("table_bits", C.c_uint32),
+                ("table_mixed", C.c_uint64)]
 
 
 class Query(C.Structure):
@@ -112,6 +113,7 @@ def lib():
             "sdb_join_aggregate_range": ([P, P, P, U64, P, I, P, P, P, P, P, P], I),
             "sdb_covering_get_info": ([P, P], I),
             "sdb_covering_build_index": ([P, U32, P], I),
+            "sdb_covering_build_table": ([P, U32, P], I),
             "sdb_join_aggregate": ([P, P, P, U64, P, I, P, P, P], I),
             "sdb_join_aggregate_host": ([P, P, P, U64, P, U32, I, P, P, P], I),
             "sdb_covering_fallbacks": ([P, P, P], I),
@@ -252,6 +254,10 @@ def build_coverings(polys, grid_bits: int, eps_list, stream=None, flags: int = 0
 
 def covering_build_index(cov: Covering, leaf_bits: int, stream=None):
     _check(lib().sdb_covering_build_index(cov.handle, leaf_bits, _stream(stream)))
+
+
+def covering_build_table(cov: Covering, table_bits: int, stream=None):
+    _check(lib().sdb_covering_build_table(cov.handle, table_bits, _stream(stream)))
 
 
 def join_aggregate(x, y, attr, cov: Covering, lookup: int, count, sum_=None, stream=None):

@@ -79,6 +79,7 @@ def test_invalid_arguments_rejected_on_host(sdblib):
                                       None) == sdblib.SDB_EINVAL
     assert L.sdb_join_aggregate(None, None, None, 0, None, 0, None, None, None) == sdblib.SDB_EINVAL
     assert L.sdb_covering_build_index(None, 12, None) == sdblib.SDB_EINVAL
+    assert L.sdb_covering_build_table(None, 20, None) == sdblib.SDB_EINVAL
     assert L.sdb_join_aggregate_host(None, None, None, 0, None, 0, 0, None, None, None) == \
         sdblib.SDB_EINVAL
     for s in range(6):

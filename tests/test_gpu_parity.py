@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Integer results, so the bar is bit-exact: canonical coverings, per-polygon
-counts and int64 sums.  The learned lookup must equal binary search.
+counts and int64 sums.  The learned and cell-table lookups must equal binary
+search.
 """
 import json
 import os
@@ -71,7 +72,8 @@ def test_handworked_golden(cuda, sdblib):
         for c in g["cases"]:
             cov = sdblib.build_covering(P, B, c["eps"])
             sdblib.covering_build_index(cov, 4)
-            for lookup in (0, 1):
+            sdblib.covering_build_table(cov, 8)
+            for lookup in (0, 1, 3):
                 cnt, sm = gpu_join(cuda, sdblib, cov, pts, lookup)
                 assert int(cnt[0]) == c[name] and int(sm[0]) == c[name], (name, c, lookup)
 
@@ -97,6 +99,11 @@ def test_covering_and_join_vs_oracle_small(cuda, sdblib, orc, B, eps, seed):
         cnt, sm = gpu_join(cuda, sdblib, cov, pts, lookup)
         assert np.array_equal(cnt, want[0]) and np.array_equal(sm, want[1]), lookup
     assert sdblib.covering_fallbacks(cov) == 0
+    for tb in (8, 12, 26):  # coarse buckets (many mixed) up to one id per bucket
+        sdblib.covering_build_table(cov, tb)
+        assert cov.info().table_bits == min(tb, 2 * oc.F)
+        cnt, sm = gpu_join(cuda, sdblib, cov, pts, sdblib.LOOKUP_TABLE)
+        assert np.array_equal(cnt, want[0]) and np.array_equal(sm, want[1]), tb
 
 
 def test_stars16_workload(cuda, sdblib, orc):
