@@ -544,6 +544,27 @@ const char *sdb_last_error(void);
  * devices, all threads).  A diagnostic counter; host only, never fails. */
 uint64_t sdb_launch_count(void);
 
+/* Device time of the library's phases (diagnostics).  While tracing is on, each
+ * traced phase records a CUDA event before and after its work on the stream it
+ * runs on: "cover.build" (a whole covering build), "cover.expand" (one level of
+ * the quadtree expansion), "cover.merge" (record sort and range merge),
+ * "sort.hist", "sort.scan", "sort.scatter" (one 8-bit pass of the record sort
+ * each), "index.build", "table.build", "join" (one join launch).  Time spent
+ * by the host between launches falls inside the enclosing phases only.
+ * sdb_trace_enable(1) drops earlier records and starts recording; (0) stops.
+ * sdb_trace_read waits for the recorded events and writes, per phase name in
+ * order of first appearance, the number of intervals and their total time in
+ * ms (at most capacity entries; *n_out = the number of names).  Host only;
+ * calls racing with traced library calls in other threads are not supported.
+ * SDB_EINVAL: n_out NULL, or out NULL with capacity > 0. */
+typedef struct sdb_trace_stat {
+  char name[32];
+  uint64_t count;
+  double total_ms;
+} sdb_trace_stat;
+sdb_status sdb_trace_enable(int on);
+sdb_status sdb_trace_read(sdb_trace_stat *out, uint32_t capacity, uint32_t *n_out);
+
 #ifdef __cplusplus
 }
 #endif

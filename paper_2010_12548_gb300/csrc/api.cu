@@ -21,6 +21,54 @@ std::atomic<unsigned long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+struct TraceRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+std::atomic<bool> g_trace_on{false};
+std::vector<TraceRec> g_trace;
+std::vector<cudaEvent_t> g_evpool;
+
+cudaEvent_t take_event() {
+  if (!g_evpool.empty()) {
+    cudaEvent_t e = g_evpool.back();
+    g_evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+TraceScope::TraceScope(const char* name, cudaStream_t st) : s(st) {
+  if (!g_trace_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  TraceRec r{name, take_event(), take_event()};
+  if (!r.a || !r.b || cudaEventRecord(r.a, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (r.a) g_evpool.push_back(r.a);
+    if (r.b) g_evpool.push_back(r.b);
+    return;
+  }
+  slot = (int)g_trace.size();
+  g_trace.push_back(r);
+}
+
+TraceScope::~TraceScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if ((size_t)slot < g_trace.size() && cudaEventRecord(g_trace[slot].b, s) != cudaSuccess) {
+    cudaGetLastError();
+    g_trace[slot].name = nullptr;
+  }
+}
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -737,5 +785,45 @@ const char* sdb_status_string(sdb_status s) {
 const char* sdb_last_error(void) { return g_err; }
 
 uint64_t sdb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+sdb_status sdb_trace_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if (on) {
+    for (TraceRec& r : g_trace) {
+      if (r.a) g_evpool.push_back(r.a);
+      if (r.b) g_evpool.push_back(r.b);
+    }
+    g_trace.clear();
+  }
+  g_trace_on.store(on != 0);
+  return SDB_OK;
+}
+
+sdb_status sdb_trace_read(sdb_trace_stat* out, uint32_t capacity, uint32_t* n_out) {
+  if (!n_out || (capacity > 0 && !out)) {
+    set_error("n_out is NULL, or out is NULL with capacity > 0");
+    return SDB_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_tmu);
+  std::vector<sdb_trace_stat> agg;
+  for (const TraceRec& r : g_trace) {
+    if (!r.name) continue;
+    SDB_TRY_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    SDB_TRY_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    size_t i = 0;
+    while (i < agg.size() && strncmp(agg[i].name, r.name, sizeof(agg[i].name) - 1) != 0) ++i;
+    if (i == agg.size()) {
+      agg.emplace_back();
+      memset(&agg[i], 0, sizeof(agg[i]));
+      strncpy(agg[i].name, r.name, sizeof(agg[i].name) - 1);
+    }
+    agg[i].count += 1;
+    agg[i].total_ms += ms;
+  }
+  for (size_t i = 0; i < agg.size() && i < capacity; ++i) out[i] = agg[i];
+  *n_out = (uint32_t)agg.size();
+  return SDB_OK;
+}
 
 }  // extern "C"

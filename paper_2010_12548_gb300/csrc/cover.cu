@@ -44,6 +44,31 @@ __device__ __forceinline__ uint32_t single_pay(uint32_t v) {
   return (v & VAL_SLOT) | ((v >> 31) << 30);
 }
 
+// Records are (key, value) pairs in two arrays, or, when the key and a short
+// value fit one 64-bit word, packed: key << (sb + 6) | flag << (sb + 5) |
+// level << sb | slot with sb slot bits (sb = 0: not packed).  The sort then
+// moves 8 bytes per record instead of 12.
+__device__ __forceinline__ void put_record(uint64_t* __restrict__ rk, uint32_t* __restrict__ rv,
+                                           uint64_t r, uint64_t key, uint32_t val, uint32_t sb) {
+  if (sb) {
+    rk[r] = (key << (sb + 6)) | ((uint64_t)(val >> 31) << (sb + 5)) |
+            ((uint64_t)val_level(val) << sb) | (uint64_t)(val & VAL_SLOT);
+  } else {
+    rk[r] = key;
+    rv[r] = val;
+  }
+}
+
+__global__ void unpack_records_kernel(const uint64_t* __restrict__ pk, uint64_t n, uint32_t sb,
+                                      uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint64_t w = pk[r];
+  key[r] = w >> (sb + 6);
+  val[r] = (uint32_t)(w & ((1ull << sb) - 1ull)) | ((uint32_t)((w >> sb) & 31u) << 26) |
+           ((uint32_t)((w >> (sb + 5)) & 1u) << 31);
+}
+
 struct Edge {
   int32_t ax, ay, bx, by;
 };
@@ -194,7 +219,7 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ edge_off,
                                   const CoverQuery* __restrict__ qs, uint32_t NP, uint32_t qshift,
                                   uint32_t bflag, bool noncons, uint32_t B, Item* __restrict__ items,
                                   uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val,
-                                  unsigned long long* __restrict__ counters) {
+                                  uint32_t sb, unsigned long long* __restrict__ counters) {
   uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (p >= NP) return;
@@ -215,8 +240,9 @@ __global__ void root_items_kernel(const uint32_t* __restrict__ edge_off,
     }
     if (lane == 0) {
       unsigned long long r = atomicAdd(&counters[2], 1ull);
-      rec_key[r] = qshift >= 64 ? 0ull : ((uint64_t)qi << qshift);
-      rec_val[r] = pair_slot[p] | bflag;  // the whole grid as one boundary cell
+      // the whole grid as one boundary cell
+      put_record(rec_key, rec_val, r, qshift >= 64 ? 0ull : ((uint64_t)qi << qshift),
+                 pair_slot[p] | bflag, sb);
     }
     return;
   }
@@ -305,8 +331,8 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
     const uint32_t* __restrict__ pair_slot, const CoverQuery* __restrict__ qs, uint32_t qshift,
     uint32_t bflag, uint32_t B, uint32_t L, Item* __restrict__ next_items,
     uint32_t* __restrict__ next_elist,
-    uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val, unsigned long long rec_base,
-    unsigned long long* __restrict__ counters) {
+    uint64_t* __restrict__ rec_key, uint32_t* __restrict__ rec_val, uint32_t sb,
+    unsigned long long rec_base, unsigned long long* __restrict__ counters) {
   const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = gt / G < n_items;
   const uint32_t t = (uint32_t)(gt / G);  // item of this lane's group
@@ -421,9 +447,8 @@ __global__ __launch_bounds__(256) void expand_level_kernel(
     bool emit = (cnt[c] > 0) ? (cl == F) : (inside != 0);
     if (emit) {
       if (gl == 0) {
-        unsigned long long r = rec_base + ro++;
-        rec_key[r] = qbits | (chid << shift);
-        rec_val[r] = slot | ((F - cl) << 26) | (cnt[c] > 0 ? bflag : 0u);
+        put_record(rec_key, rec_val, rec_base + ro++, qbits | (chid << shift),
+                   slot | ((F - cl) << 26) | (cnt[c] > 0 ? bflag : 0u), sb);
       }
       cnt[c] = 0;  // a finest boundary cell needs no edge list
     } else if (cnt[c] > 0) {
@@ -923,7 +948,8 @@ static sdb_status merge_general(uint64_t* key, uint32_t* val, uint64_t n, uint32
 // the general sweep runs
 static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const CoverSpec& spec,
                                 const CoverQuery* d_qs, uint32_t qshift, int key_bits,
-                                cudaStream_t s, CoverSet* out) {
+                                uint32_t sb, cudaStream_t s, CoverSet* out) {
+  TraceScope tr("cover.merge", s);
   Scratch sc(s);
   const uint32_t Q = spec.Q;
   if (n >= 0xffffffffull) {
@@ -933,8 +959,21 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
   uint64_t *ktmp, *sk;
   uint32_t *vtmp, *sv;
   SDB_TRY(sc.get(&ktmp, n));
-  SDB_TRY(sc.get(&vtmp, n));
-  SDB_TRY(radix_sort_pairs(key, val, ktmp, vtmp, n, key_bits, s, &sk, &sv));
+  if (sb) {
+    // packed records: sort the words on their key bits, then split them
+    uint64_t* sp;
+    SDB_TRY(radix_sort_keys(key, ktmp, n, key_bits, s, &sp, (int)sb + 6));
+    sk = sp == key ? ktmp : key;
+    SDB_TRY(sc.get(&sv, n));
+    if (n) {
+      unpack_records_kernel<<<grid_for(n, 256), 256, 0, s>>>(sp, n, sb, sk, sv);
+      note_launch();
+      SDB_TRY_CUDA(cudaGetLastError());
+    }
+  } else {
+    SDB_TRY(sc.get(&vtmp, n));
+    SDB_TRY(radix_sort_pairs(key, val, ktmp, vtmp, n, key_bits, s, &sk, &sv));
+  }
   uint32_t *flag, *gidx, *dG;
   unsigned int* nested;
   SDB_TRY(sc.get(&flag, n));
@@ -1058,7 +1097,7 @@ static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items,
                          const Edge* edges, const uint32_t* pq, const uint32_t* ps,
                          const CoverQuery* qs, uint32_t qshift, uint32_t bflag, bool noncons,
                          uint32_t B, uint32_t L,
-                         Item* nitems, uint32_t* nel, uint64_t* rkey, uint32_t* rval,
+                         Item* nitems, uint32_t* nel, uint64_t* rkey, uint32_t* rval, uint32_t sb,
                          unsigned long long rec_base, unsigned long long* ctr, cudaStream_t s) {
   const size_t threads = (size_t)n_items * G;
 #define SDB_EXPAND(g)                                                                          \
@@ -1066,11 +1105,11 @@ static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items,
     if (noncons)                                                                               \
       expand_level_kernel<g, true><<<grid_for(threads, 256), 256, 0, s>>>(                     \
           items, n_items, elist, edges, pq, ps, qs, qshift, bflag, B, L, nitems, nel, rkey,     \
-          rval, rec_base, ctr);                                                                \
+          rval, sb, rec_base, ctr);                                                            \
     else                                                                                       \
       expand_level_kernel<g, false><<<grid_for(threads, 256), 256, 0, s>>>(                    \
           items, n_items, elist, edges, pq, ps, qs, qshift, bflag, B, L, nitems, nel, rkey,     \
-          rval, rec_base, ctr);                                                                \
+          rval, sb, rec_base, ctr);                                                            \
     break;
   switch (G) {
     SDB_EXPAND(1)
@@ -1091,6 +1130,7 @@ static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items,
 
 sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStream_t s,
                            CoverSet* out) {
+  TraceScope tr("cover.build", s);
   const uint32_t P = pe.P;
   const uint32_t V = pe.V;
   const uint32_t B = spec.B, Q = spec.Q, NP = spec.NP;
@@ -1138,13 +1178,19 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
 
-  // record buffer, grown on demand
+  // record buffer, grown on demand; packed into one word per record when the
+  // key, the slot, the level and the flag fit 64 bits
+  uint32_t max_slot = 0;
+  for (uint32_t i = 0; i < NP; ++i) max_slot = spec.pair_slot[i] > max_slot ? spec.pair_slot[i] : max_slot;
+  uint32_t sb = (uint32_t)bits_for(max_slot);
+  if (sb < 1) sb = 1;
+  if (key_bits + (int)sb + 6 > 64) sb = 0;
   uint64_t rec_cap = 1 << 20, n_rec = 0;
   if (rec_cap < 8ull * NP) rec_cap = 8ull * NP;
-  uint64_t* rkey;
-  uint32_t* rval;
+  uint64_t* rkey = nullptr;
+  uint32_t* rval = nullptr;
   SDB_TRY(dalloc_n(&rkey, rec_cap, s));
-  SDB_TRY(dalloc_n(&rval, rec_cap, s));
+  if (!sb) SDB_TRY(dalloc_n(&rval, rec_cap, s));
   struct Free {
     uint64_t** k;
     uint32_t** v;
@@ -1164,7 +1210,7 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   if (NP) {
     root_items_kernel<<<grid_for((size_t)NP * 32, 256), 256, 0, s>>>(
         d_off, edges, d_pp, d_pq, d_ps, d_qs, NP, qshift, bflag, spec.noncons, B, items, rkey, rval,
-        ctr);
+        sb, ctr);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
   }
@@ -1184,16 +1230,18 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
     if (n_rec + 4 * n_items > rec_cap) {
       uint64_t nc = rec_cap;
       while (nc < n_rec + 4 * n_items) nc *= 2;
-      uint64_t* k2;
-      uint32_t* v2;
+      uint64_t* k2 = nullptr;
+      uint32_t* v2 = nullptr;
       SDB_TRY(dalloc_n(&k2, nc, s));
-      SDB_TRY(dalloc_n(&v2, nc, s));
       SDB_TRY_CUDA(cudaMemcpyAsync(k2, rkey, n_rec * 8, cudaMemcpyDeviceToDevice, s));
-      SDB_TRY_CUDA(cudaMemcpyAsync(v2, rval, n_rec * 4, cudaMemcpyDeviceToDevice, s));
       dfree(rkey, s);
-      dfree(rval, s);
       rkey = k2;
-      rval = v2;
+      if (!sb) {
+        SDB_TRY(dalloc_n(&v2, nc, s));
+        SDB_TRY_CUDA(cudaMemcpyAsync(v2, rval, n_rec * 4, cudaMemcpyDeviceToDevice, s));
+        dfree(rval, s);
+        rval = v2;
+      }
       rec_cap = nc;
     }
     if (4 * n_items > 0xffffffffull || 4 * n_edges > 0xffffffffull) {
@@ -1221,10 +1269,13 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
     uint32_t G = 1;
     if (mean >= 4)
       while (G < 32 && G < mean) G <<= 1;
-    SDB_TRY(launch_expand(G, items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift, bflag,
-                          spec.noncons, B,
-                          L, nitems, nel, rkey, rval, n_rec, ctr, s));
-    SDB_TRY_CUDA(cudaGetLastError());
+    {
+      TraceScope tr("cover.expand", s);
+      SDB_TRY(launch_expand(G, items, (uint32_t)n_items, cur_el, edges, d_pq, d_ps, d_qs, qshift,
+                            bflag, spec.noncons, B, L, nitems, nel, rkey, rval, sb, n_rec, ctr,
+                            s));
+      SDB_TRY_CUDA(cudaGetLastError());
+    }
     unsigned long long h[3];
     SDB_TRY(read_u64(ctr, h, 3, s));
     dfree(items, s);
@@ -1239,7 +1290,7 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   if (items) dfree(items, s);
   if (own_el && cur_el) dfree(cur_el, s);
   out->ncells = n_rec;
-  return merge_records(rkey, rval, n_rec, spec, d_qs, qshift, key_bits, s, out);
+  return merge_records(rkey, rval, n_rec, spec, d_qs, qshift, key_bits, sb, s, out);
 }
 
 sdb_status finish_covering(sdb_covering* cov, cudaStream_t s);

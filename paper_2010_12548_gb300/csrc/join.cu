@@ -527,6 +527,7 @@ sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
   uint64_t blocks = (uint64_t)num_sms() * per_sm;
   const uint64_t need = (A.n + 4 * THREADS - 1) / (4 * THREADS);  // tiles
   if (blocks > need) blocks = need > 0 ? need : 1;
+  TraceScope tr("join", s);
   kern<<<(unsigned)blocks, THREADS, smem, s>>>(A);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());

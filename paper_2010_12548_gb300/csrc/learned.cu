@@ -175,6 +175,7 @@ __global__ void leaf_fit_kernel(const uint64_t* __restrict__ start, uint64_t R,
 }  // namespace
 
 sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream_t s) {
+  TraceScope tr("index.build", s);
   const uint32_t L = 1u << leaf_bits;
   const uint64_t R = cov->R;
   const uint64_t top = 1ull << (2 * cov->F);

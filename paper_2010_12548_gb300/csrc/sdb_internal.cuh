@@ -74,6 +74,17 @@ int num_sms();
 // count of kernels this library has launched in the process (all devices)
 void note_launch();
 
+// Diagnostics: while tracing is on (sdb_trace_enable), a scope records a CUDA
+// event pair around its work on stream s, filed under name (a string literal).
+struct TraceScope {
+  int slot = -1;
+  cudaStream_t s;
+  TraceScope(const char* name, cudaStream_t s);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+};
+
 // ---------------------------------------------------------------- Hilbert curve
 // Quadrant-digit Hilbert curve whose order-1 visit order is (0,0), (0,1), (1,1),
 // (1,0).  Scanning levels from the top, the orientation inherited by the lower
@@ -361,8 +372,9 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
 // sort.cu: device-wide primitives
 template <class T>
 sdb_status exclusive_scan(const T* in, T* out, size_t n, T* d_total, cudaStream_t s);
+// keys-only LSD sort on bits [first_bit, first_bit + bits) (stable)
 sdb_status radix_sort_keys(uint64_t* keys, uint64_t* tmp, size_t n, int bits, cudaStream_t s,
-                           uint64_t** result);
+                           uint64_t** result, int first_bit = 0);
 sdb_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp,
                             size_t n, int bits, cudaStream_t s, uint64_t** kres, uint32_t** vres);
 // unique of a sorted array: writes out[0..m), returns m via host sync

@@ -252,7 +252,8 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
 
 template <bool VALS>
 sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp, size_t n,
-                           int bits, cudaStream_t s, uint64_t** kres, uint32_t** vres) {
+                           int bits, cudaStream_t s, uint64_t** kres, uint32_t** vres,
+                           int first_bit = 0) {
   *kres = keys;
   if (VALS) *vres = vals;
   if (n <= 1 || bits <= 0) return SDB_OK;
@@ -271,15 +272,24 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
   SDB_TRY(sc.get(&offs, (size_t)256 * nblocks));
   uint64_t *ka = keys, *kb = ktmp;
   uint32_t *va = vals, *vb = vtmp;
-  for (int shift = 0; shift < bits; shift += 8) {
-    radix_hist_kernel<<<nblocks, RS_THREADS, 0, s>>>(ka, n, shift, hist, nblocks);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
-    SDB_TRY(exclusive_scan<uint32_t>(hist, offs, (size_t)256 * nblocks, nullptr, s));
-    radix_scatter_kernel<VALS><<<nblocks, RS_THREADS, SCATTER_SMEM, s>>>(ka, va, kb, vb, n, shift,
-                                                                          offs, nblocks);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
+  for (int shift = first_bit; shift < first_bit + bits; shift += 8) {
+    {
+      TraceScope tr("sort.hist", s);
+      radix_hist_kernel<<<nblocks, RS_THREADS, 0, s>>>(ka, n, shift, hist, nblocks);
+      note_launch();
+      SDB_TRY_CUDA(cudaGetLastError());
+    }
+    {
+      TraceScope tr("sort.scan", s);
+      SDB_TRY(exclusive_scan<uint32_t>(hist, offs, (size_t)256 * nblocks, nullptr, s));
+    }
+    {
+      TraceScope tr("sort.scatter", s);
+      radix_scatter_kernel<VALS><<<nblocks, RS_THREADS, SCATTER_SMEM, s>>>(ka, va, kb, vb, n,
+                                                                            shift, offs, nblocks);
+      note_launch();
+      SDB_TRY_CUDA(cudaGetLastError());
+    }
     uint64_t* t = ka;
     ka = kb;
     kb = t;
@@ -336,9 +346,10 @@ template sdb_status exclusive_scan<uint32_t>(const uint32_t*, uint32_t*, size_t,
 template sdb_status exclusive_scan<uint64_t>(const uint64_t*, uint64_t*, size_t, uint64_t*, cudaStream_t);
 
 sdb_status radix_sort_keys(uint64_t* keys, uint64_t* tmp, size_t n, int bits, cudaStream_t s,
-                           uint64_t** result) {
+                           uint64_t** result, int first_bit) {
   uint32_t* dummy = nullptr;
-  return radix_sort_impl<false>(keys, nullptr, tmp, nullptr, n, bits, s, result, &dummy);
+  return radix_sort_impl<false>(keys, nullptr, tmp, nullptr, n, bits, s, result, &dummy,
+                                first_bit);
 }
 
 sdb_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp, size_t n,

@@ -64,6 +64,7 @@ __global__ void table_mixed_kernel(const uint64_t* __restrict__ start, uint64_t 
 }  // namespace
 
 sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t s) {
+  TraceScope tr("table.build", s);
   if (cov->R >= (uint64_t)TAB_MIXED_MAX) {
     set_error("cell table: %llu ranges, at most %u supported", (unsigned long long)cov->R,
               TAB_MIXED_MAX - 1);

@@ -114,6 +114,8 @@ def lib():
             "sdb_covering_get_info": ([P, P], I),
             "sdb_covering_build_index": ([P, U32, P], I),
             "sdb_covering_build_table": ([P, U32, P], I),
+            "sdb_trace_enable": ([C.c_int], I),
+            "sdb_trace_read": ([P, U32, P], I),
             "sdb_join_aggregate": ([P, P, P, U64, P, I, P, P, P], I),
             "sdb_join_aggregate_host": ([P, P, P, U64, P, U32, I, P, P, P], I),
             "sdb_covering_fallbacks": ([P, P, P], I),
@@ -360,6 +362,25 @@ def covering_export(cov: Covering):
     ids = np.empty(max(inf.n_list_ids, 1), np.uint32)
     _check(lib().sdb_covering_export(cov.handle, _np_ptr(start), _np_ptr(loff), _np_ptr(ids)))
     return start, loff, ids[:inf.n_list_ids]
+
+
+class _TraceStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("count", C.c_uint64), ("total_ms", C.c_double)]
+
+
+def trace_enable(on: bool = True):
+    """Start (dropping earlier records) or stop recording per-phase device time."""
+    _check(lib().sdb_trace_enable(1 if on else 0))
+
+
+def trace_read() -> dict:
+    """{phase name: (intervals, total ms)} of the recorded phases."""
+    n = C.c_uint32(0)
+    _check(lib().sdb_trace_read(None, 0, C.byref(n)))
+    buf = (_TraceStat * max(1, n.value))()
+    _check(lib().sdb_trace_read(C.cast(buf, C.c_void_p), n.value, C.byref(n)))
+    return {buf[i].name.decode(): (int(buf[i].count), float(buf[i].total_ms))
+            for i in range(min(n.value, len(buf)))}
 
 
 def launch_count() -> int:

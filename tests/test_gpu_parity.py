@@ -106,6 +106,31 @@ def test_covering_and_join_vs_oracle_small(cuda, sdblib, orc, B, eps, seed):
         assert np.array_equal(cnt, want[0]) and np.array_equal(sm, want[1]), tb
 
 
+def test_finest_grid_unpacked_records(cuda, sdblib, orc):
+    """B = 30 at eps 2 (F = 30): keys of 61 bits leave no room to pack the
+    record's value into the key word, so the builder takes the two-array
+    record path; coverings and joins still equal the oracle's."""
+    rng = np.random.default_rng(21)
+    B = 30
+    base = W.star_polygons(rng, 5, 12, nverts=(3, 9), radius=(20, 60))
+    off = np.uint32(2 ** 29 + 12345)  # small stars somewhere in the middle of the grid
+    P = W.Polygons(base.ring_off, base.x + off, base.y + off, B)
+    for eps in (2, 3, 40):
+        oc = orc.cover(P, eps)
+        cov = sdblib.build_covering(P, B, eps)
+        assert_same_covering(sdblib, cov, oc)
+        n = 30_001
+        pts = W.Points((rng.integers(0, 4096, n) + off).astype(np.uint32),
+                       (rng.integers(0, 4096, n) + off).astype(np.uint32),
+                       rng.integers(-2 ** 31, 2 ** 31, n, dtype=np.int64).astype(np.int32), B)
+        want = oc.join(pts.x, pts.y, pts.attr)
+        sdblib.covering_build_index(cov, 6)
+        sdblib.covering_build_table(cov, 20)
+        for lookup in (0, 1, 3):
+            cnt, sm = gpu_join(cuda, sdblib, cov, pts, lookup)
+            assert np.array_equal(cnt, want[0]) and np.array_equal(sm, want[1]), (eps, lookup)
+
+
 def test_stars16_workload(cuda, sdblib, orc):
     """100k uniform points, 16 overlapping star polygons, eps = 64 (F = 11)."""
     w = W.tiny_stars()
