@@ -547,7 +547,8 @@ uint64_t sdb_launch_count(void);
 /* Device time of the library's phases (diagnostics).  While tracing is on, each
  * traced phase records a CUDA event before and after its work on the stream it
  * runs on: "cover.build" (a whole covering build), "cover.expand" (one level of
- * the quadtree expansion), "cover.merge" (record sort and range merge),
+ * the quadtree expansion), "cover.merge" (record sort and range merge, made
+ * of "cover.sort", "cover.count" and "cover.emit"),
  * "sort.hist", "sort.scan", "sort.scatter" (one 8-bit pass of the record sort
  * each), "index.build", "table.build", "join" (one join launch).  Time spent
  * by the host between launches falls inside the enclosing phases only.

@@ -60,13 +60,14 @@ TraceScope::TraceScope(const char* name, cudaStream_t st) : s(st) {
   g_trace.push_back(r);
 }
 
-TraceScope::~TraceScope() {
+void TraceScope::end() {
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_tmu);
   if ((size_t)slot < g_trace.size() && cudaEventRecord(g_trace[slot].b, s) != cudaSuccess) {
     cudaGetLastError();
     g_trace[slot].name = nullptr;
   }
+  slot = -1;
 }
 
 void set_error(const char* fmt, ...) {

@@ -25,6 +25,8 @@
 // neighbours) gives the canonical ranges.
 #include "sdb_internal.cuh"
 
+#include <atomic>
+#include <utility>
 #include <vector>
 
 namespace sdb {
@@ -51,22 +53,11 @@ __device__ __forceinline__ uint32_t single_pay(uint32_t v) {
 __device__ __forceinline__ void put_record(uint64_t* __restrict__ rk, uint32_t* __restrict__ rv,
                                            uint64_t r, uint64_t key, uint32_t val, uint32_t sb) {
   if (sb) {
-    rk[r] = (key << (sb + 6)) | ((uint64_t)(val >> 31) << (sb + 5)) |
-            ((uint64_t)val_level(val) << sb) | (uint64_t)(val & VAL_SLOT);
+    rk[r] = record_pack(key, val, sb);
   } else {
     rk[r] = key;
     rv[r] = val;
   }
-}
-
-__global__ void unpack_records_kernel(const uint64_t* __restrict__ pk, uint64_t n, uint32_t sb,
-                                      uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
-  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const uint64_t w = pk[r];
-  key[r] = w >> (sb + 6);
-  val[r] = (uint32_t)(w & ((1ull << sb) - 1ull)) | ((uint32_t)((w >> sb) & 31u) << 26) |
-           ((uint32_t)((w >> (sb + 5)) & 1u) << 31);
 }
 
 struct Edge {
@@ -626,186 +617,287 @@ __global__ void sample_kernel(const uint64_t* __restrict__ start, uint32_t strid
 // between groups are empty intervals, and the canonical ranges follow by merging
 // equal neighbours.  Keys are (query << qshift) | start.
 
-__global__ void group_flags_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-                                   uint64_t n, uint32_t qshift, uint32_t* __restrict__ flag,
-                                   unsigned int* __restrict__ nested) {
-  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const uint64_t k = sk[r];
-  const uint32_t d = val_level(sv[r]);
-  flag[r] = (r == 0 || sk[r - 1] != k) ? 1u : 0u;
-  if (r + 1 < n) {
-    const uint64_t k2 = sk[r + 1];
-    if (k2 == k ? (val_level(sv[r + 1]) != d)
-                : (qof(k2, qshift) == qof(k, qshift) && k2 < k + (1ull << (2 * d))))
-      *nested = 1u;
-  }
-}
+// Two passes over the sorted records, each thread taking MR consecutive
+// records and the groups whose first record is among them (a group may reach
+// into the next threads' records; its predecessor is read backwards).  Pass 1
+// counts, per block, the ranges the groups open and the list entries of those
+// ranges, notes each query's first record and any nesting; pass 2 writes the
+// ranges at offsets from block, thread and query prefixes.
+constexpr int MT = 256;  // threads per block
+constexpr int MR = 8;    // records per thread
 
-__global__ void group_heads_kernel(const uint32_t* __restrict__ flag,
-                                   const uint32_t* __restrict__ gidx, uint64_t n,
-                                   uint32_t* __restrict__ gfirst) {
-  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n && flag[r]) gfirst[gidx[r]] = (uint32_t)r;
-}
-
-// per group: its size, and its slot ids sorted ascending (groups are small:
-// the polygons sharing one cell)
-__global__ void group_sort_kernel(uint32_t* __restrict__ sv, const uint32_t* __restrict__ gfirst,
-                                  uint32_t G, uint64_t n, uint32_t* __restrict__ gsize) {
-  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= G) return;
-  const uint32_t a = gfirst[g], b = (g + 1 < G) ? gfirst[g + 1] : (uint32_t)n;
-  const uint32_t PM = (1u << 26) - 1u;
-  for (uint32_t i = a + 1; i < b; ++i) {
-    const uint32_t v = sv[i];
-    uint32_t j = i;
-    while (j > a && (sv[j - 1] & PM) > (v & PM)) {
-      sv[j] = sv[j - 1];
-      --j;
-    }
-    sv[j] = v;
-  }
-  gsize[g] = b - a;
-}
-
-struct GroupCtx {
+struct MergeCtx {
   const uint64_t* sk;
   const uint32_t* sv;
-  const uint32_t* gfirst;
-  const uint32_t* gsize;
+  uint64_t n;
   const CoverQuery* qs;
-  uint32_t G, qshift;
+  uint32_t qshift;
   uint64_t lomask;
 };
 
-// Ranges opened by group g in its query's id order: an empty gap before it
-// (bit 0, starting at *gap_lo), the group itself unless it continues the
-// previous group of the same query with the same list (bit 1), and after the
-// query's last group the empty tail up to 4^F (bit 2).
-__device__ __forceinline__ uint32_t group_opens(const GroupCtx& c, uint32_t g, uint32_t* q_out,
-                                                uint64_t* lo_out, uint64_t* gap_lo,
-                                                uint64_t* hi_out, bool* first_out) {
-  const uint32_t a = c.gfirst[g];
+// the group starting at record a, and what it opens: an empty gap before it
+// (bit 0, from gap_lo), itself unless it continues the previous group of its
+// query with the same polygon list (bit 1), and after its query's last group
+// the empty tail up to 4^F (bit 2)
+struct GroupInfo {
+  uint64_t lo, hi, gap_lo;
+  uint32_t q, k, opens;
+  bool first, last, nested;
+};
+
+__device__ __forceinline__ bool same_list(const uint32_t* __restrict__ sv, uint64_t a, uint64_t pa,
+                                          uint32_t k) {
+  // entries are distinct within a group: equal as sets = equal sorted
+  for (uint32_t t = 0; t < k; ++t) {
+    const uint32_t e = list_entry(sv[a + t]);
+    bool found = false;
+    for (uint32_t u = 0; u < k && !found; ++u) found = list_entry(sv[pa + u]) == e;
+    if (!found) return false;
+  }
+  return true;
+}
+
+__device__ GroupInfo group_at(const MergeCtx& c, uint64_t a) {
+  GroupInfo g;
   const uint64_t key = c.sk[a];
-  const uint32_t q = (uint32_t)qof(key, c.qshift);
-  const uint64_t lo = key & c.lomask, hi = lo + (1ull << (2 * val_level(c.sv[a])));
-  const uint64_t top = 1ull << (2 * c.qs[q].F);
-  const bool first = g == 0 || qof(c.sk[c.gfirst[g - 1]], c.qshift) != q;
+  const uint32_t lev = val_level(c.sv[a]);
+  g.q = (uint32_t)qof(key, c.qshift);
+  g.lo = key & c.lomask;
+  g.hi = g.lo + (1ull << (2 * lev));
+  g.nested = false;
+  uint64_t b = a + 1;
+  while (b < c.n && c.sk[b] == key) {
+    g.nested |= val_level(c.sv[b]) != lev;  // a cell and its descendant share a start
+    ++b;
+  }
+  g.k = (uint32_t)(b - a);
+  g.first = a == 0 || qof(c.sk[a - 1], c.qshift) != g.q;
   uint32_t gap, fresh;
-  if (first) {
-    *gap_lo = 0;
-    gap = lo > 0;
+  if (g.first) {
+    g.gap_lo = 0;
+    gap = g.lo > 0;
     fresh = 1;
   } else {
-    const uint32_t pa = c.gfirst[g - 1];
-    const uint64_t phi = (c.sk[pa] & c.lomask) + (1ull << (2 * val_level(c.sv[pa])));
-    *gap_lo = phi;
-    gap = lo > phi;
-    fresh = gap || c.gsize[g] != c.gsize[g - 1];
-    for (uint32_t t = 0; !fresh && t < c.gsize[g]; ++t)
-      fresh = list_entry(c.sv[a + t]) != list_entry(c.sv[pa + t]);
+    const uint64_t pkey = c.sk[a - 1];
+    uint64_t pa = a - 1;
+    while (pa > 0 && c.sk[pa - 1] == pkey) --pa;
+    g.gap_lo = (pkey & c.lomask) + (1ull << (2 * val_level(c.sv[pa])));
+    gap = g.lo > g.gap_lo;
+    fresh = gap || (a - pa) != g.k || !same_list(c.sv, a, pa, g.k);
   }
-  const bool last = g + 1 == c.G || qof(c.sk[c.gfirst[g + 1]], c.qshift) != q;
-  const uint32_t tail = last && hi < top;
-  *q_out = q;
-  *lo_out = lo;
-  *hi_out = hi;
-  *first_out = first;
-  return gap | (fresh << 1) | (tail << 2);
+  g.last = b == c.n || qof(c.sk[b], c.qshift) != g.q;
+  // the next group of the query must start at or after this cell's end
+  if (!g.last && c.sk[b] < key + (1ull << (2 * lev))) g.nested = true;
+  const uint32_t tail = g.last && g.hi < (1ull << (2 * c.qs[g.q].F));
+  g.opens = gap | (fresh << 1) | (tail << 2);
+  return g;
 }
 
-// ranges each group opens, and each query's first and last group (one writer
-// each, since groups are sorted by query: no contended counter)
-__global__ void group_count_kernel(GroupCtx c, uint32_t* __restrict__ nopen,
-                                   uint32_t* __restrict__ qfirst, uint32_t* __restrict__ qlast) {
-  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= c.G) return;
-  uint32_t q;
-  uint64_t lo, gl, hi;
-  bool first;
-  const uint32_t o = group_opens(c, g, &q, &lo, &gl, &hi, &first);
-  nopen[g] = __popc(o);
-  if (first) qfirst[q] = g;
-  if (g + 1 == c.G || qof(c.sk[c.gfirst[g + 1]], c.qshift) != q) qlast[q] = g;
+__device__ __forceinline__ bool is_head(const MergeCtx& c, uint64_t r) {
+  return r == 0 || c.sk[r - 1] != c.sk[r];
 }
 
-// entries of query q: the ranges its groups open plus the sentinel (a query
-// without cells has one empty range)
-__global__ void query_sizes_kernel(const uint32_t* __restrict__ qfirst,
-                                   const uint32_t* __restrict__ qlast,
-                                   const uint32_t* __restrict__ gscan,
-                                   const uint32_t* __restrict__ nopen,
-                                   const uint32_t* __restrict__ gfirst, uint32_t G, uint64_t n,
-                                   uint32_t Q, uint64_t* __restrict__ qsize,
-                                   uint64_t* __restrict__ qcells) {
-  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+// block sum of a 64-bit value (MT threads)
+__device__ __forceinline__ uint64_t block_sum_u64(uint64_t v, uint64_t* s_warp) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
+  __syncthreads();
+  uint64_t t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < MT / 32; ++w) t += s_warp[w];
+  return t;
+}
+
+// block exclusive scan of a 64-bit value (MT threads)
+__device__ __forceinline__ uint64_t block_exscan_u64(uint64_t v, uint64_t* s_warp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  uint64_t pre = 0;
+  for (int ww = 0; ww < w; ++ww) pre += s_warp[ww];
+  return pre + inc - v;
+}
+
+// Records of a block: warp w takes the MR * 32 records from w * MR * 32, lane l
+// the records l, l + 32, ... of them (coalesced loads); groups are handled by
+// the lane holding their first record, in record order within the warp.
+__device__ __forceinline__ uint64_t merge_rec(uint32_t i) {
+  return (uint64_t)blockIdx.x * (MT * MR) + (threadIdx.x >> 5) * (32 * MR) + i * 32 +
+         (threadIdx.x & 31);
+}
+
+// per block: ranges opened (high 32 bits) and list entries (low 32 bits); per
+// query: its first record; any nesting
+__global__ __launch_bounds__(MT) void merge_count_kernel(MergeCtx c, uint64_t* __restrict__ bsum,
+                                                         uint32_t* __restrict__ qhead,
+                                                         unsigned int* __restrict__ nested) {
+  __shared__ uint64_t s_warp[MT / 32];
+  uint64_t acc = 0;
+  bool nest = false;
+  for (uint32_t i = 0; i < MR; ++i) {
+    const uint64_t r = merge_rec(i);
+    if (r < c.n && is_head(c, r)) {
+      const GroupInfo g = group_at(c, r);
+      acc += ((uint64_t)__popc(g.opens) << 32) + ((g.opens & 2u) ? g.k : 0u);
+      if (g.first) qhead[g.q] = (uint32_t)r;
+      nest |= g.nested;
+    }
+  }
+  if (nest) *nested = 1u;
+  const uint64_t t = block_sum_u64(acc, s_warp);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+}
+
+struct MergeOut {
+  uint64_t* start;
+  uint32_t* list_off;
+  uint32_t* list_ids;
+  uint32_t* pay;
+  uint64_t* qopen;   // per query: ranges before its first group, after its last
+  uint32_t* qlist;   // per query: list entries before its first group, after its last
+};
+
+__global__ __launch_bounds__(MT) void merge_emit_kernel(MergeCtx c, const uint64_t* __restrict__ boff,
+                                                        const uint64_t* __restrict__ extra,
+                                                        MergeOut o) {
+  __shared__ uint64_t s_warp[MT / 32];
+  const uint32_t lane = threadIdx.x & 31;
+  // per record of this lane: head flag (bit 31), opens (bits 28..30), group size
+  uint32_t code[MR];
+  uint64_t wtot = 0;
+  for (uint32_t i = 0; i < MR; ++i) {
+    const uint64_t r = merge_rec(i);
+    code[i] = 0;
+    if (r < c.n && is_head(c, r)) {
+      const GroupInfo g = group_at(c, r);
+      code[i] = 0x80000000u | (g.opens << 28) | g.k;
+      wtot += ((uint64_t)__popc(g.opens) << 32) + ((g.opens & 2u) ? g.k : 0u);
+    }
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) wtot += __shfl_xor_sync(FULL, wtot, s);
+  // the warps' totals in record order -> this warp's offset in the block
+  const uint64_t wpre = block_exscan_u64(lane == 0 ? wtot : 0ull, s_warp);
+  uint64_t run = boff[blockIdx.x] + __shfl_sync(FULL, wpre, 0);
+  for (uint32_t i = 0; i < MR; ++i) {
+    const uint32_t cd = code[i];
+    const uint32_t opens = (cd >> 28) & 7u, k = cd & 0x0fffffffu;
+    const uint64_t mine = ((uint64_t)__popc(opens) << 32) + ((opens & 2u) ? k : 0u);
+    uint64_t inc = mine;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+      const uint64_t t = __shfl_up_sync(FULL, inc, s);
+      if (lane >= (uint32_t)s) inc += t;
+    }
+    const uint64_t pre = run + inc - mine;
+    run += __shfl_sync(FULL, inc, 31);
+    if (!(cd >> 31)) continue;
+    // the group again, without the list comparison (its outcome is in opens)
+    const uint64_t r = merge_rec(i);
+    const uint64_t key = c.sk[r];
+    const uint32_t q = (uint32_t)qof(key, c.qshift);
+    const uint64_t lo = key & c.lomask, hi = lo + (1ull << (2 * val_level(c.sv[r])));
+    const bool first = r == 0 || qof(c.sk[r - 1], c.qshift) != q;
+    const bool last = r + k == c.n || qof(c.sk[r + k], c.qshift) != q;
+    uint64_t ro = pre >> 32;     // ranges before (all queries, no sentinels)
+    uint32_t L = (uint32_t)pre;  // list entries before
+    if (first) {
+      o.qopen[2 * q] = ro;
+      o.qlist[2 * q] = L;
+    }
+    uint64_t e = ro + extra[q];  // entry index: ranges plus earlier queries' extras
+    if (opens & 1u) {
+      uint64_t gap_lo = 0;
+      if (!first) {  // the end of the previous group's cell
+        const uint64_t pkey = c.sk[r - 1];
+        uint64_t pa = r - 1;
+        while (pa > 0 && c.sk[pa - 1] == pkey) --pa;
+        gap_lo = (pkey & c.lomask) + (1ull << (2 * val_level(c.sv[pa])));
+      }
+      o.start[e] = gap_lo;
+      o.list_off[e] = L;
+      o.pay[e] = NONE;
+      ++e;
+    }
+    if (opens & 2u) {
+      o.start[e] = lo;
+      o.list_off[e] = L;
+      o.pay[e] = k == 1 ? single_pay(c.sv[r]) : (0x80000000u | (uint32_t)e);
+      // the list in ascending slot order (groups are small: insertion sort)
+      uint32_t* out = o.list_ids + L;
+      for (uint32_t t = 0; t < k; ++t) {
+        const uint32_t v = list_entry(c.sv[r + t]);
+        uint32_t j = t;
+        while (j > 0 && (out[j - 1] & VAL_SLOT) > (v & VAL_SLOT)) {
+          out[j] = out[j - 1];
+          --j;
+        }
+        out[j] = v;
+      }
+      L += k;
+      ++e;
+    }
+    if (opens & 4u) {
+      o.start[e] = hi;
+      o.list_off[e] = L;
+      o.pay[e] = NONE;
+    }
+    ro += __popc(opens);
+    if (last) {
+      o.qopen[2 * q + 1] = ro;
+      o.qlist[2 * q + 1] = L;
+    }
+  }
+}
+
+// per query (one thread each): its offset and record count, its sentinel
+// (start 4^F), and the single empty range of a query without records
+struct QueryFix {
+  uint64_t extra;      // entries of earlier queries that are no ranges of groups
+  uint64_t next_head;  // first record of the next query with records (or n)
+  uint32_t prev;       // the last earlier query with records (or NONE)
+  uint32_t head;       // the query's first record (or NONE)
+};
+
+__global__ void merge_finish_kernel(const QueryFix* __restrict__ qf,
+                                    const uint64_t* __restrict__ qopen,
+                                    const uint32_t* __restrict__ qlist,
+                                    const CoverQuery* __restrict__ qs, uint32_t Q,
+                                    uint64_t* __restrict__ start, uint32_t* __restrict__ list_off,
+                                    uint32_t* __restrict__ pay, uint64_t* __restrict__ qoff,
+                                    uint64_t* __restrict__ qcells) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= Q) return;
-  const uint32_t a = qfirst[q], b = qlast[q];
-  qsize[q] = a == NONE ? 2ull : (uint64_t)(gscan[b] + nopen[b] - gscan[a]) + 1ull;
-  // the query's records: from its first group's head to the next query's
-  qcells[q] = a == NONE ? 0ull : (b + 1 < G ? (uint64_t)gfirst[b + 1] : n) - gfirst[a];
-}
-
-__global__ void group_emit_kernel(GroupCtx c, const uint32_t* __restrict__ gscan,
-                                  const uint32_t* __restrict__ qfirst,
-                                  const uint64_t* __restrict__ qoff, uint64_t* __restrict__ start,
-                                  uint32_t* __restrict__ rlen, uint32_t* __restrict__ rsrc) {
-  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= c.G) return;
-  uint32_t q;
-  uint64_t lo, gl, hi;
-  bool first;
-  const uint32_t o = group_opens(c, g, &q, &lo, &gl, &hi, &first);
-  uint64_t r = qoff[q] + (gscan[g] - gscan[qfirst[q]]);
-  if (o & 1u) {
-    start[r] = gl;
-    rlen[r] = 0;
-    rsrc[r] = 0;
-    ++r;
+  const QueryFix f = qf[q];
+  uint64_t e;
+  uint32_t L;
+  if (f.head != NONE) {
+    qoff[q] = qopen[2 * q] + f.extra;
+    e = qopen[2 * q + 1] + f.extra;
+    L = qlist[2 * q + 1];
+    qcells[q] = f.next_head - f.head;
+  } else {
+    const uint64_t ro = f.prev == NONE ? 0ull : qopen[2 * f.prev + 1];
+    L = f.prev == NONE ? 0u : qlist[2 * f.prev + 1];
+    e = ro + f.extra;
+    qoff[q] = e;
+    start[e] = 0;
+    list_off[e] = L;
+    pay[e] = NONE;
+    ++e;
+    qcells[q] = 0;
   }
-  if (o & 2u) {
-    start[r] = lo;
-    rlen[r] = c.gsize[g];
-    rsrc[r] = c.gfirst[g];
-    ++r;
-  }
-  if (o & 4u) {
-    start[r] = hi;
-    rlen[r] = 0;
-    rsrc[r] = 0;
-  }
-}
-
-// per query: the sentinel, and the single empty range of a query without cells
-__global__ void query_emit_kernel(const uint32_t* __restrict__ qfirst,
-                                  const uint64_t* __restrict__ qoff,
-                                  const CoverQuery* __restrict__ qs, uint32_t Q,
-                                  uint64_t* __restrict__ start, uint32_t* __restrict__ rlen,
-                                  uint32_t* __restrict__ rsrc) {
-  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= Q) return;
-  if (qfirst[q] == NONE) {
-    start[qoff[q]] = 0;
-    rlen[qoff[q]] = 0;
-    rsrc[qoff[q]] = 0;
-  }
-  const uint64_t e = qoff[q + 1] - 1;
   start[e] = 1ull << (2 * qs[q].F);
-  rlen[e] = 0;
-  rsrc[e] = 0;
-}
-
-__global__ void fill_lists_sv_kernel(const uint32_t* __restrict__ sv,
-                                     const uint32_t* __restrict__ rlen,
-                                     const uint32_t* __restrict__ rsrc,
-                                     const uint32_t* __restrict__ list_off, uint64_t E,
-                                     uint32_t* __restrict__ list_ids, uint32_t* __restrict__ pay) {
-  uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= E) return;
-  const uint32_t n = rlen[r], o = list_off[r], s = rsrc[r];
-  for (uint32_t t = 0; t < n; ++t) list_ids[o + t] = list_entry(sv[s + t]);
-  pay[r] = n == 0 ? NONE : (n == 1 ? single_pay(sv[s]) : (0x80000000u | (uint32_t)r));
+  list_off[e] = L;
+  pay[e] = NONE;
+  if (q == Q - 1) qoff[Q] = e + 1;
 }
 
 __global__ void set_u32_kernel(uint32_t* p, uint64_t n, uint32_t v) {
@@ -959,94 +1051,75 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
   uint64_t *ktmp, *sk;
   uint32_t *vtmp, *sv;
   SDB_TRY(sc.get(&ktmp, n));
+  TraceScope tr_sort("cover.sort", s);
   if (sb) {
     // packed records: sort the words on their key bits, then split them
-    uint64_t* sp;
-    SDB_TRY(radix_sort_keys(key, ktmp, n, key_bits, s, &sp, (int)sb + 6));
-    sk = sp == key ? ktmp : key;
+    // (the last pass writes keys and values apart)
     SDB_TRY(sc.get(&sv, n));
-    if (n) {
-      unpack_records_kernel<<<grid_for(n, 256), 256, 0, s>>>(sp, n, sb, sk, sv);
-      note_launch();
-      SDB_TRY_CUDA(cudaGetLastError());
-    }
+    SDB_TRY(radix_sort_split(key, ktmp, n, key_bits, (int)sb + 6, sb, sv, s, &sk));
   } else {
     SDB_TRY(sc.get(&vtmp, n));
     SDB_TRY(radix_sort_pairs(key, val, ktmp, vtmp, n, key_bits, s, &sk, &sv));
   }
-  uint32_t *flag, *gidx, *dG;
+  // pass 1: per block, the ranges and list entries its groups open; each
+  // query's first record; nesting
+  const uint64_t per_block = (uint64_t)MT * MR;
+  const uint64_t nb = n ? (n + per_block - 1) / per_block : 0;
+  uint64_t *bsum, *boff, *dtot;
+  uint32_t* qhead;
   unsigned int* nested;
-  SDB_TRY(sc.get(&flag, n));
-  SDB_TRY(sc.get(&gidx, n));
-  SDB_TRY(sc.get(&dG, 1));
+  SDB_TRY(sc.get(&bsum, nb ? nb : 1));
+  SDB_TRY(sc.get(&boff, nb ? nb : 1));
+  SDB_TRY(sc.get(&dtot, 1));
+  SDB_TRY(sc.get(&qhead, Q));
   SDB_TRY(sc.get(&nested, 1));
   SDB_TRY_CUDA(cudaMemsetAsync(nested, 0, sizeof(unsigned int), s));
-  if (n) {
-    group_flags_kernel<<<grid_for(n, 256), 256, 0, s>>>(sk, sv, n, qshift, flag, nested);
+  SDB_TRY_CUDA(cudaMemsetAsync(qhead, 0xff, (size_t)Q * 4, s));
+  SDB_TRY_CUDA(cudaMemsetAsync(dtot, 0, 8, s));
+  const MergeCtx mc{sk, sv, n, d_qs, qshift, qshift >= 64 ? ~0ull : ((1ull << qshift) - 1ull)};
+  tr_sort.end();
+  if (nb) {
+    TraceScope tr1("cover.count", s);
+    merge_count_kernel<<<(unsigned)nb, MT, 0, s>>>(mc, bsum, qhead, nested);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
+    SDB_TRY(exclusive_scan<uint64_t>(bsum, boff, nb, dtot, s));
   }
-  SDB_TRY(exclusive_scan<uint32_t>(flag, gidx, n, dG, s));
-  uint32_t hG[2] = {0, 0};
-  SDB_TRY_CUDA(cudaMemcpyAsync(&hG[0], dG, 4, cudaMemcpyDeviceToHost, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(&hG[1], nested, 4, cudaMemcpyDeviceToHost, s));
+  uint64_t tot = 0;
+  unsigned int hnest = 0;
+  std::vector<uint32_t> hhead(Q);
+  SDB_TRY_CUDA(cudaMemcpyAsync(&tot, dtot, 8, cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(&hnest, nested, 4, cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(hhead.data(), qhead, (size_t)Q * 4, cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  if (hG[1]) {
+  if (hnest) {
     if (Q != 1) {
       set_error("batched coverings need polygons that do not overlap within a query");
       return SDB_EINVAL;
     }
-    sc.release(flag);
-    sc.release(gidx);
     uint32_t P = 0;
     for (uint32_t i = 0; i < spec.NP; ++i) P = spec.pair_slot[i] + 1 > P ? spec.pair_slot[i] + 1 : P;
     return merge_general(sk, sv, n, spec.q[0].F, P, spec.flags, s, out);
   }
-  const uint32_t G = hG[0];
-  uint32_t *gfirst, *gsize, *nopen, *gscan, *qlast, *qfirst;
-  uint64_t *qsize, *qoff, *dE;
-  SDB_TRY(sc.get(&gfirst, G));
-  SDB_TRY(sc.get(&gsize, G));
-  SDB_TRY(sc.get(&nopen, G));
-  SDB_TRY(sc.get(&gscan, G));
-  SDB_TRY(sc.get(&qlast, Q));
-  SDB_TRY(sc.get(&qfirst, Q));
-  SDB_TRY(sc.get(&qsize, Q));
-  SDB_TRY(sc.get(&qoff, (size_t)Q + 1));
-  SDB_TRY(sc.get(&dE, 1));
-  set_u32_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, Q, NONE);
-  note_launch();
-  SDB_TRY_CUDA(cudaGetLastError());
-  GroupCtx gc{sk, sv, gfirst, gsize, d_qs, G, qshift,
-              qshift >= 64 ? ~0ull : ((1ull << qshift) - 1ull)};
-  if (G) {
-    group_heads_kernel<<<grid_for(n, 256), 256, 0, s>>>(flag, gidx, n, gfirst);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
-    group_sort_kernel<<<grid_for(G, 256), 256, 0, s>>>(sv, gfirst, G, n, gsize);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
-    group_count_kernel<<<grid_for(G, 256), 256, 0, s>>>(gc, nopen, qfirst, qlast);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
+  // entries: the groups' ranges, plus per query its sentinel, plus the empty
+  // range of a query without records
+  std::vector<QueryFix> hq(Q);
+  uint64_t extra = 0;
+  uint32_t prev = NONE;
+  for (uint32_t q = 0; q < Q; ++q) {
+    hq[q].extra = extra;
+    hq[q].head = hhead[q];
+    hq[q].prev = prev;
+    extra += hhead[q] == NONE ? 2 : 1;
+    if (hhead[q] != NONE) prev = q;
   }
-  SDB_TRY(exclusive_scan<uint32_t>(nopen, gscan, G, nullptr, s));
-  uint64_t* qcells;
-  SDB_TRY(sc.get(&qcells, Q));
-  query_sizes_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, qlast, gscan, nopen, gfirst, G, n, Q,
-                                                      qsize, qcells);
-  note_launch();
-  SDB_TRY_CUDA(cudaGetLastError());
-  SDB_TRY(exclusive_scan<uint64_t>(qsize, qoff, Q, dE, s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(qoff + Q, dE, 8, cudaMemcpyDeviceToDevice, s));
-  out->qoff.assign((size_t)Q + 1, 0);
-  out->qcells.assign(Q, 0);
-  SDB_TRY_CUDA(cudaMemcpyAsync(out->qoff.data(), qoff, ((size_t)Q + 1) * 8, cudaMemcpyDeviceToHost,
-                               s));
-  SDB_TRY_CUDA(cudaMemcpyAsync(out->qcells.data(), qcells, (size_t)Q * 8, cudaMemcpyDeviceToHost,
-                               s));
-  SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  const uint64_t E = out->qoff[Q];
+  uint64_t next = n;
+  for (uint32_t q = Q; q-- > 0;) {
+    hq[q].next_head = next;
+    if (hhead[q] != NONE) next = hhead[q];
+  }
+  const uint64_t E = (tot >> 32) + extra;
+  const uint64_t nids = tot & 0xffffffffull;
   if (E >= 0x7fffffffull) {  // entry indices travel in 31 bits of the packed payload
     set_error("covering: %llu ranges exceed the 32-bit index range", (unsigned long long)E);
     return SDB_ENOMEM;
@@ -1054,31 +1127,41 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
   SDB_TRY(dalloc_n(&out->start, E, s));
   SDB_TRY(dalloc_n(&out->list_off, E, s));
   SDB_TRY(dalloc_n(&out->pay, E, s));
-  uint32_t *rlen, *rsrc, *dN;
-  SDB_TRY(sc.get(&rlen, E));
-  SDB_TRY(sc.get(&rsrc, E));
-  SDB_TRY(sc.get(&dN, 1));
-  if (G) {
-    group_emit_kernel<<<grid_for(G, 256), 256, 0, s>>>(gc, gscan, qfirst, qoff, out->start, rlen,
-                                                        rsrc);
+  SDB_TRY(dalloc_n(&out->list_ids, nids ? nids : 1, s));
+  QueryFix* dq;
+  uint64_t *qopen, *qoff, *qcells, *dextra;
+  uint32_t* qlist;
+  SDB_TRY(sc.get(&dq, Q));
+  SDB_TRY(sc.get(&qopen, 2 * (size_t)Q));
+  SDB_TRY(sc.get(&qlist, 2 * (size_t)Q));
+  SDB_TRY(sc.get(&qoff, (size_t)Q + 1));
+  SDB_TRY(sc.get(&qcells, Q));
+  SDB_TRY(sc.get(&dextra, Q));
+  std::vector<uint64_t> hextra(Q);
+  for (uint32_t q = 0; q < Q; ++q) hextra[q] = hq[q].extra;
+  SDB_TRY_CUDA(cudaMemcpyAsync(dq, hq.data(), (size_t)Q * sizeof(QueryFix), cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(dextra, hextra.data(), (size_t)Q * 8, cudaMemcpyHostToDevice, s));
+  // pass 2: the ranges
+  if (nb) {
+    TraceScope tr2("cover.emit", s);
+    const MergeOut mo{out->start, out->list_off, out->list_ids, out->pay, qopen, qlist};
+    merge_emit_kernel<<<(unsigned)nb, MT, 0, s>>>(mc, boff, dextra, mo);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
   }
-  query_emit_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qfirst, qoff, d_qs, Q, out->start, rlen, rsrc);
+  merge_finish_kernel<<<grid_for(Q, 256), 256, 0, s>>>(dq, qopen, qlist, d_qs, Q, out->start,
+                                                       out->list_off, out->pay, qoff, qcells);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
-  SDB_TRY(exclusive_scan<uint32_t>(rlen, out->list_off, E, dN, s));
-  uint32_t nids = 0;
-  SDB_TRY_CUDA(cudaMemcpyAsync(&nids, dN, sizeof(nids), cudaMemcpyDeviceToHost, s));
+  out->qoff.assign((size_t)Q + 1, 0);
+  out->qcells.assign(Q, 0);
+  SDB_TRY_CUDA(cudaMemcpyAsync(out->qoff.data(), qoff, ((size_t)Q + 1) * 8, cudaMemcpyDeviceToHost,
+                               s));
+  SDB_TRY_CUDA(cudaMemcpyAsync(out->qcells.data(), qcells, (size_t)Q * 8, cudaMemcpyDeviceToHost,
+                               s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  SDB_TRY(dalloc_n(&out->list_ids, (size_t)nids, s));
-  fill_lists_sv_kernel<<<grid_for(E, 256), 256, 0, s>>>(sv, rlen, rsrc, out->list_off, E,
-                                                         out->list_ids, out->pay);
-  note_launch();
-  SDB_TRY_CUDA(cudaGetLastError());
   out->E = E;
   out->nids = nids;
-  SDB_TRY_CUDA(cudaStreamSynchronize(s));
   return SDB_OK;
 }
 
@@ -1128,6 +1211,25 @@ static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items,
   return SDB_OK;
 }
 
+// Capacity hints from earlier builds in this process (records, frontier cells,
+// frontier edge entries), so that a build of a size seen before allocates its
+// buffers once instead of growing them level by level (a grown buffer is a new
+// allocation plus a copy; growing pool memory is slow).  Hints only: a build
+// that needs more still grows.
+std::atomic<uint64_t> g_hint_rec{1ull << 20}, g_hint_items{1ull << 16}, g_hint_edges{1ull << 18};
+
+void raise_hint(std::atomic<uint64_t>& h, uint64_t v) {
+  uint64_t cur = h.load(std::memory_order_relaxed);
+  while (v > cur && !h.compare_exchange_weak(cur, v, std::memory_order_relaxed)) {
+  }
+}
+
+uint64_t pow2_at_least(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
 sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStream_t s,
                            CoverSet* out) {
   TraceScope tr("cover.build", s);
@@ -1151,6 +1253,7 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   }
   Scratch sc(s);
   // polygons -> device edges
+  TraceScope tr_up("cover.setup", s);
   uint32_t *d_off, *d_x, *d_y, *d_vp, *elist, *d_pp, *d_pq, *d_ps;
   CoverQuery* d_qs;
   Edge* edges;
@@ -1185,7 +1288,7 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   uint32_t sb = (uint32_t)bits_for(max_slot);
   if (sb < 1) sb = 1;
   if (key_bits + (int)sb + 6 > 64) sb = 0;
-  uint64_t rec_cap = 1 << 20, n_rec = 0;
+  uint64_t rec_cap = g_hint_rec.load(std::memory_order_relaxed), n_rec = 0;
   if (rec_cap < 8ull * NP) rec_cap = 8ull * NP;
   uint64_t* rkey = nullptr;
   uint32_t* rval = nullptr;
@@ -1205,8 +1308,33 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   unsigned long long* ctr;
   SDB_TRY(sc.get(&ctr, 3));
   SDB_TRY_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
-  Item* items = nullptr;
-  SDB_TRY(dalloc_n(&items, NP, s));
+  // frontier cells and edge lists, two buffers each (this level's, the next's)
+  struct Frontier {
+    Item* f[2] = {nullptr, nullptr};
+    uint32_t* e[2] = {nullptr, nullptr};
+    bool own_e[2] = {false, true};
+    cudaStream_t s;
+    ~Frontier() {
+      dfree(f[0], s);
+      dfree(f[1], s);
+      if (own_e[0]) dfree(e[0], s);
+      if (own_e[1]) dfree(e[1], s);
+    }
+  } fr;
+  fr.s = s;
+  Item** fbuf = fr.f;
+  uint32_t** ebuf = fr.e;
+  uint64_t fcap[2], ecap[2];
+  fcap[0] = g_hint_items.load(std::memory_order_relaxed);
+  if (fcap[0] < NP) fcap[0] = pow2_at_least(NP);
+  fcap[1] = fcap[0];
+  ecap[0] = V;  // the polygons' own edge lists (scratch)
+  ecap[1] = g_hint_edges.load(std::memory_order_relaxed);
+  SDB_TRY(dalloc_n(&fbuf[0], fcap[0], s));
+  SDB_TRY(dalloc_n(&fbuf[1], fcap[1], s));
+  SDB_TRY(dalloc_n(&ebuf[1], ecap[1], s));
+  ebuf[0] = elist;
+  Item* items = fbuf[0];
   if (NP) {
     root_items_kernel<<<grid_for((size_t)NP * 32, 256), 256, 0, s>>>(
         d_off, edges, d_pp, d_pq, d_ps, d_qs, NP, qshift, bflag, spec.noncons, B, items, rkey, rval,
@@ -1222,7 +1350,8 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
     if (spec.q[spec.pair_query[i]].F > 0)
       n_edges += pe.edge_off[spec.pair_poly[i] + 1] - pe.edge_off[spec.pair_poly[i]];
   uint32_t* cur_el = elist;
-  bool own_el = false;
+  tr_up.end();
+  TraceScope tr_lv("cover.levels", s);
   for (uint32_t L = 0; L < Fmax && n_items > 0; ++L) {
     const bool last = (L + 1 == Fmax);
     // capacity: every record and every child item comes from one of 4
@@ -1247,21 +1376,29 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
     if (4 * n_items > 0xffffffffull || 4 * n_edges > 0xffffffffull) {
       set_error("covering: level %u frontier too large (%llu cells, %llu edge entries)", L,
                 (unsigned long long)n_items, (unsigned long long)n_edges);
-      dfree(items, s);
-      if (own_el) dfree(cur_el, s);
       return SDB_ENOMEM;
     }
     Item* nitems = nullptr;
     uint32_t* nel = nullptr;
     if (!last) {
-      sdb_status st = dalloc_n(&nitems, 4 * n_items, s);
-      if (st == SDB_OK) st = dalloc_n(&nel, 4 * n_edges, s);
-      if (st != SDB_OK) {
-        dfree(items, s);
-        if (own_el) dfree(cur_el, s);
-        if (nitems) dfree(nitems, s);
-        return st;
+      // the other buffer of each pair, grown (contents are dead) when short
+      sdb_status st = SDB_OK;
+      if (fcap[1] < 4 * n_items) {
+        dfree(fbuf[1], s);
+        fbuf[1] = nullptr;
+        fcap[1] = pow2_at_least(4 * n_items);
+        st = dalloc_n(&fbuf[1], fcap[1], s);
       }
+      if (st == SDB_OK && ecap[1] < 4 * n_edges) {
+        if (fr.own_e[1]) dfree(ebuf[1], s);
+        ebuf[1] = nullptr;
+        fr.own_e[1] = true;
+        ecap[1] = pow2_at_least(4 * n_edges);
+        st = dalloc_n(&ebuf[1], ecap[1], s);
+      }
+      if (st != SDB_OK) return st;
+      nitems = fbuf[1];
+      nel = ebuf[1];
     }
     SDB_TRY_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
     // lanes per item: about the level's mean edge count, a power of two <= 32
@@ -1278,17 +1415,22 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
     }
     unsigned long long h[3];
     SDB_TRY(read_u64(ctr, h, 3, s));
-    dfree(items, s);
-    if (own_el) dfree(cur_el, s);
-    items = nitems;
-    cur_el = nel;
-    own_el = true;
+    // the next level reads what this one wrote
+    std::swap(fbuf[0], fbuf[1]);
+    std::swap(fcap[0], fcap[1]);
+    std::swap(ebuf[0], ebuf[1]);
+    std::swap(ecap[0], ecap[1]);
+    std::swap(fr.own_e[0], fr.own_e[1]);
+    items = fbuf[0];
+    cur_el = ebuf[0];
     n_items = last ? 0 : h[0];
     n_edges = h[1];
     n_rec += h[2];
+    raise_hint(g_hint_items, pow2_at_least(4 * n_items));
+    raise_hint(g_hint_edges, pow2_at_least(4 * n_edges));
   }
-  if (items) dfree(items, s);
-  if (own_el && cur_el) dfree(cur_el, s);
+  tr_lv.end();
+  raise_hint(g_hint_rec, pow2_at_least(n_rec));
   out->ncells = n_rec;
   return merge_records(rkey, rval, n_rec, spec, d_qs, qshift, key_bits, sb, s, out);
 }

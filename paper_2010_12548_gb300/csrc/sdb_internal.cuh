@@ -80,7 +80,8 @@ struct TraceScope {
   int slot = -1;
   cudaStream_t s;
   TraceScope(const char* name, cudaStream_t s);
-  ~TraceScope();
+  ~TraceScope() { end(); }
+  void end();  // records the closing event now (once)
   TraceScope(const TraceScope&) = delete;
   TraceScope& operator=(const TraceScope&) = delete;
 };
@@ -352,6 +353,18 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
 constexpr uint32_t TAB_MIXED = 0xC0000000u;
 constexpr uint32_t TAB_MIXED_MAX = 0x3fffffffu;
 sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t s);
+// A covering record's value: polygon slot (bits 0..25), level above the finest
+// (26..30), boundary flag (31).  Packed record (one 64-bit word, sb slot bits):
+// key << (sb + 6) | flag << (sb + 5) | level << sb | slot.
+__host__ __device__ inline uint64_t record_pack(uint64_t key, uint32_t val, uint32_t sb) {
+  return (key << (sb + 6)) | ((uint64_t)(val >> 31) << (sb + 5)) |
+         ((uint64_t)((val >> 26) & 31u) << sb) | (uint64_t)(val & ((1u << 26) - 1u));
+}
+__host__ __device__ inline uint32_t record_val(uint64_t w, uint32_t sb) {
+  return (uint32_t)(w & ((1ull << sb) - 1ull)) | ((uint32_t)((w >> sb) & 31u) << 26) |
+         ((uint32_t)((w >> (sb + 5)) & 1u) << 31);
+}
+
 // lookup is known and the covering has what it needs (api.cu)
 sdb_status check_lookup(const sdb_covering* cov, int lookup);
 // join.cu
@@ -372,6 +385,11 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
 // sort.cu: device-wide primitives
 template <class T>
 sdb_status exclusive_scan(const T* in, T* out, size_t n, T* d_total, cudaStream_t s);
+// keys-only LSD sort of packed covering records (record_pack) on their key
+// bits [first_bit, first_bit + bits); the result is split into keys
+// (*keys_out, one of keys / tmp) and standard values (vals_out)
+sdb_status radix_sort_split(uint64_t* keys, uint64_t* tmp, size_t n, int bits, int first_bit,
+                            uint32_t sb, uint32_t* vals_out, cudaStream_t s, uint64_t** keys_out);
 // keys-only LSD sort on bits [first_bit, first_bit + bits) (stable)
 sdb_status radix_sort_keys(uint64_t* keys, uint64_t* tmp, size_t n, int bits, cudaStream_t s,
                            uint64_t** result, int first_bit = 0);

@@ -131,11 +131,13 @@ __global__ __launch_bounds__(RS_THREADS) void radix_hist_kernel(const uint64_t* 
 // sorted by digit (stable), and writes it back so that consecutive threads
 // write consecutive slots of the same digit's output run (coalesced), starting
 // at the block's global offset for that digit.
-template <bool VALS>
+// SPLIT (keys only): the output is the packed covering record split into its
+// key (kout) and standard value (vout), sb slot bits.
+template <bool VALS, bool SPLIT = false>
 __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ offs,
-    uint32_t nblocks) {
+    uint32_t nblocks, uint32_t sb = 0) {
   extern __shared__ __align__(16) unsigned char dyn[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(dyn);                 // RS_TILE keys
   uint32_t* sv = reinterpret_cast<uint32_t*>(dyn + RS_TILE * 8);   // RS_TILE values
@@ -245,15 +247,20 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     const uint64_t key = sk[i];
     const uint32_t d = (uint32_t)((key >> shift) & 255u);
     const uint32_t pos = gbase[d] + (i - dstart[d]);
-    kout[pos] = key;
-    if (VALS) vout[pos] = sv[i];
+    if (SPLIT) {
+      kout[pos] = key >> (sb + 6);
+      vout[pos] = record_val(key, sb);
+    } else {
+      kout[pos] = key;
+      if (VALS) vout[pos] = sv[i];
+    }
   }
 }
 
 template <bool VALS>
 sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp, size_t n,
                            int bits, cudaStream_t s, uint64_t** kres, uint32_t** vres,
-                           int first_bit = 0) {
+                           int first_bit = 0, uint32_t* split_vals = nullptr, uint32_t sb = 0) {
   *kres = keys;
   if (VALS) *vres = vals;
   if (n <= 1 || bits <= 0) return SDB_OK;
@@ -266,6 +273,10 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
   SDB_TRY_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<VALS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)SCATTER_SMEM));
+  if (!VALS && split_vals)
+    SDB_TRY_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SCATTER_SMEM));
   Scratch sc(s);
   uint32_t *hist, *offs;
   SDB_TRY(sc.get(&hist, (size_t)256 * nblocks));
@@ -285,8 +296,12 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
     }
     {
       TraceScope tr("sort.scatter", s);
-      radix_scatter_kernel<VALS><<<nblocks, RS_THREADS, SCATTER_SMEM, s>>>(ka, va, kb, vb, n,
-                                                                            shift, offs, nblocks);
+      if (!VALS && split_vals && shift + 8 >= first_bit + bits)  // the last pass splits
+        radix_scatter_kernel<false, true><<<nblocks, RS_THREADS, SCATTER_SMEM, s>>>(
+            ka, nullptr, kb, split_vals, n, shift, offs, nblocks, sb);
+      else
+        radix_scatter_kernel<VALS><<<nblocks, RS_THREADS, SCATTER_SMEM, s>>>(ka, va, kb, vb, n,
+                                                                              shift, offs, nblocks);
       note_launch();
       SDB_TRY_CUDA(cudaGetLastError());
     }
@@ -350,6 +365,27 @@ sdb_status radix_sort_keys(uint64_t* keys, uint64_t* tmp, size_t n, int bits, cu
   uint32_t* dummy = nullptr;
   return radix_sort_impl<false>(keys, nullptr, tmp, nullptr, n, bits, s, result, &dummy,
                                 first_bit);
+}
+
+sdb_status radix_sort_split(uint64_t* keys, uint64_t* tmp, size_t n, int bits, int first_bit,
+                            uint32_t sb, uint32_t* vals_out, cudaStream_t s, uint64_t** keys_out) {
+  uint32_t* dummy = nullptr;
+  if (n <= 1) {  // no pass runs: split in place
+    if (n == 1) {
+      uint64_t w = 0;
+      SDB_TRY_CUDA(cudaMemcpyAsync(&w, keys, 8, cudaMemcpyDeviceToHost, s));
+      SDB_TRY_CUDA(cudaStreamSynchronize(s));
+      const uint64_t k = w >> (sb + 6);
+      const uint32_t v = record_val(w, sb);
+      SDB_TRY_CUDA(cudaMemcpyAsync(keys, &k, 8, cudaMemcpyHostToDevice, s));
+      SDB_TRY_CUDA(cudaMemcpyAsync(vals_out, &v, 4, cudaMemcpyHostToDevice, s));
+      SDB_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    *keys_out = keys;
+    return SDB_OK;
+  }
+  return radix_sort_impl<false>(keys, nullptr, tmp, nullptr, n, bits, s, keys_out, &dummy,
+                                first_bit, vals_out, sb);
 }
 
 sdb_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp, size_t n,
