@@ -201,7 +201,8 @@ sdb_status sdb_covering_build_index(sdb_covering *cov, uint32_t leaf_bits, void 
  * Indexing": cells of large interior ranges are resolved at once).  With
  * T = min(table_bits rounded down to even, 2F) the ids [0, 4^F) fall into 2^T
  * buckets of 4^F / 2^T consecutive ids, the descendants of one cell of level
- * T / 2 each, so a point's bucket is its cell id at that level.  A bucket that lies inside one range stores that range's
+ * T / 2 each.  The table lists those cells in row-major order, so a point's
+ * entry follows from its coordinates without encoding its cell id.  A bucket that lies inside one range stores that range's
  * polygon payload, so a point in it needs one table read; a bucket that meets
  * several ranges stores the first and last of them, and the lookup binary
  * searches that window of range starts.  Table: 4 bytes per bucket, plus 8

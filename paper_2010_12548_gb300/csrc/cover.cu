@@ -733,9 +733,11 @@ __device__ __forceinline__ uint64_t merge_rec(uint32_t i) {
          (threadIdx.x & 31);
 }
 
-// per block: ranges opened (high 32 bits) and list entries (low 32 bits); per
-// query: its first record; any nesting
-__global__ __launch_bounds__(MT) void merge_count_kernel(MergeCtx c, uint64_t* __restrict__ bsum,
+// per record: 0 inside a group, else head flag (bit 31), opens (bits 28..30)
+// and group size; per block: ranges opened (high 32 bits) and list entries
+// (low 32 bits); per query: its first record; any nesting
+__global__ __launch_bounds__(MT) void merge_count_kernel(MergeCtx c, uint32_t* __restrict__ code,
+                                                         uint64_t* __restrict__ bsum,
                                                          uint32_t* __restrict__ qhead,
                                                          unsigned int* __restrict__ nested) {
   __shared__ uint64_t s_warp[MT / 32];
@@ -743,12 +745,16 @@ __global__ __launch_bounds__(MT) void merge_count_kernel(MergeCtx c, uint64_t* _
   bool nest = false;
   for (uint32_t i = 0; i < MR; ++i) {
     const uint64_t r = merge_rec(i);
-    if (r < c.n && is_head(c, r)) {
+    if (r >= c.n) continue;
+    uint32_t cd = 0;
+    if (is_head(c, r)) {
       const GroupInfo g = group_at(c, r);
       acc += ((uint64_t)__popc(g.opens) << 32) + ((g.opens & 2u) ? g.k : 0u);
       if (g.first) qhead[g.q] = (uint32_t)r;
       nest |= g.nested;
+      cd = 0x80000000u | (g.opens << 28) | g.k;
     }
+    code[r] = cd;
   }
   if (nest) *nested = 1u;
   const uint64_t t = block_sum_u64(acc, s_warp);
@@ -764,7 +770,8 @@ struct MergeOut {
   uint32_t* qlist;   // per query: list entries before its first group, after its last
 };
 
-__global__ __launch_bounds__(MT) void merge_emit_kernel(MergeCtx c, const uint64_t* __restrict__ boff,
+__global__ __launch_bounds__(MT) void merge_emit_kernel(MergeCtx c, const uint32_t* __restrict__ rcode,
+                                                        const uint64_t* __restrict__ boff,
                                                         const uint64_t* __restrict__ extra,
                                                         MergeOut o) {
   __shared__ uint64_t s_warp[MT / 32];
@@ -774,12 +781,9 @@ __global__ __launch_bounds__(MT) void merge_emit_kernel(MergeCtx c, const uint64
   uint64_t wtot = 0;
   for (uint32_t i = 0; i < MR; ++i) {
     const uint64_t r = merge_rec(i);
-    code[i] = 0;
-    if (r < c.n && is_head(c, r)) {
-      const GroupInfo g = group_at(c, r);
-      code[i] = 0x80000000u | (g.opens << 28) | g.k;
-      wtot += ((uint64_t)__popc(g.opens) << 32) + ((g.opens & 2u) ? g.k : 0u);
-    }
+    code[i] = r < c.n ? rcode[r] : 0u;
+    const uint32_t opens = (code[i] >> 28) & 7u, k = code[i] & 0x0fffffffu;
+    wtot += ((uint64_t)__popc(opens) << 32) + ((opens & 2u) ? k : 0u);
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) wtot += __shfl_xor_sync(FULL, wtot, s);
@@ -1066,8 +1070,9 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
   const uint64_t per_block = (uint64_t)MT * MR;
   const uint64_t nb = n ? (n + per_block - 1) / per_block : 0;
   uint64_t *bsum, *boff, *dtot;
-  uint32_t* qhead;
+  uint32_t *qhead, *rcode;
   unsigned int* nested;
+  SDB_TRY(sc.get(&rcode, n ? n : 1));
   SDB_TRY(sc.get(&bsum, nb ? nb : 1));
   SDB_TRY(sc.get(&boff, nb ? nb : 1));
   SDB_TRY(sc.get(&dtot, 1));
@@ -1080,7 +1085,7 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
   tr_sort.end();
   if (nb) {
     TraceScope tr1("cover.count", s);
-    merge_count_kernel<<<(unsigned)nb, MT, 0, s>>>(mc, bsum, qhead, nested);
+    merge_count_kernel<<<(unsigned)nb, MT, 0, s>>>(mc, rcode, bsum, qhead, nested);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
     SDB_TRY(exclusive_scan<uint64_t>(bsum, boff, nb, dtot, s));
@@ -1145,7 +1150,7 @@ static sdb_status merge_records(uint64_t* key, uint32_t* val, uint64_t n, const 
   if (nb) {
     TraceScope tr2("cover.emit", s);
     const MergeOut mo{out->start, out->list_off, out->list_ids, out->pay, qopen, qlist};
-    merge_emit_kernel<<<(unsigned)nb, MT, 0, s>>>(mc, boff, dextra, mo);
+    merge_emit_kernel<<<(unsigned)nb, MT, 0, s>>>(mc, rcode, boff, dextra, mo);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
   }

@@ -17,10 +17,12 @@
 //    prediction -> search inside the leaf's error window -> bracket verified
 //    (only the ends no probe has proven are read), binary search as the
 //    fallback (counted);
-//  * cell table: one read of the id's bucket gives the payload of most points
-//    directly; points in buckets that meet several ranges are held back in a
-//    per-warp shared-memory queue and, 32 at a time (all lanes busy), binary
-//    search their bucket's window of range starts;
+//  * cell table: one read of the entry of the point's cell at the table's
+//    level (row-major, from the coordinates alone) gives the payload of most
+//    points directly; points in cells that meet several ranges are held back
+//    in a per-warp shared-memory queue and, 32 at a time (all lanes busy),
+//    compute their finest cell id and binary search the cell's window of
+//    range starts;
 //  * aggregation: per point, its count and (split 16/16-bit, exact) attribute
 //    sum are added with shared-memory atomics to per-block accumulators
 //    (P <= SMEM_POLYS, flushed into the 64-bit outputs every few tiles), or
@@ -67,11 +69,11 @@ struct JoinArgs {
   float inv_w;
   uint32_t nleaves;
   unsigned long long* fallbacks;
-  // cell table: bucket = id of the point's cell at level txy_level, encoded
-  // with tsteps table steps from orientation tst0 (coordinates >> txy)
+  // cell table: the entry of a point is at (y >> txy) << tlev | (x >> txy)
+  // (row-major cells of level tlev)
   const uint32_t* tab;
   const uint2* win;
-  uint32_t txy, tsteps, tst0;
+  uint32_t txy, tlev;
 };
 
 // last r in [0, R) with start[r] <= h, global memory only (fallback path)
@@ -448,16 +450,13 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) ok[q] = ok[q] && !((xs[q] | ys[q]) & gmask);
     if constexpr (LOOKUP == SDB_LOOKUP_TABLE) {
-      // the bucket is the id of the point's cell at the table's level (the
-      // curve's prefix property: the top bits of the finest id); only points
-      // in mixed buckets need their finest id
+      // the entry of the point's cell at the table's level, found from the
+      // coordinates (row-major table); only points in mixed cells need their
+      // finest cell id
       uint32_t e[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t b =
-            ok[q] ? hilbert3_encode32(xs[q] >> A.txy, ys[q] >> A.txy, A.tsteps, A.tst0, s_tab) : 0u;
-        e[q] = ok[q] ? __ldg(A.tab + b) : NONE;
-      }
+      for (int q = 0; q < 4; ++q)
+        e[q] = ok[q] ? __ldg(A.tab + (((ys[q] >> A.txy) << A.tlev) | (xs[q] >> A.txy))) : NONE;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const bool mix = e[q] >= TAB_MIXED && e[q] != NONE;
@@ -719,8 +718,8 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.fallbacks = cov->fallbacks;
   A.tab = cov->tab;
   A.win = cov->win;
-  A.txy = cov->B - cov->tab_bits / 2;
-  hilbert3_params(cov->tab_bits / 2, &A.tsteps, &A.tst0);
+  A.tlev = cov->tab_bits / 2;
+  A.txy = cov->B - A.tlev;
   A.bcount = reinterpret_cast<unsigned long long*>(bcount);
   A.bsum = reinterpret_cast<unsigned long long*>(bsum);
   A.babs = reinterpret_cast<unsigned long long*>(babs);

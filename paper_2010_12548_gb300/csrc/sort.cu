@@ -178,10 +178,13 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     const size_t g = base + (size_t)it * 32 + lane;
     const bool ok = g < n;
     const uint32_t d = ok ? (uint32_t)((k[it] >> shift) & 255u) : 256u;
+    // one lane per digit reads and advances the warp's counter (fewer
+    // shared-memory bank conflicts than every lane reading it)
     const unsigned peers = __match_any_sync(FULL, d);
-    const uint32_t before = ok ? cnt[w][d] : 0u;
-    __syncwarp();
-    if (ok && lane == __ffs(peers) - 1) cnt[w][d] = before + __popc(peers);
+    const int lead = __ffs(peers) - 1;
+    uint32_t before = (ok && lane == lead) ? cnt[w][d] : 0u;
+    before = __shfl_sync(FULL, before, lead);
+    if (ok && lane == lead) cnt[w][d] = before + __popc(peers);
     __syncwarp();
     rank[it] = before + __popc(peers & lt);
   }
