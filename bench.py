@@ -45,12 +45,17 @@ METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query late
 UNIT = "points/s"
 LEAF_BITS_RANGE = (12, 20)
 TABLE_BITS = 22  # cell table: 2^22 buckets (16 MB), fewer when 2F < 22
-# DRAM bytes (read + write) of one join_kernel launch at eps = 2^6 on the
-# default workload (100M points; 2^20 leaves or 2^22 table buckets), from one ncu
-# capture of this script's step: profiles/join_kernel_<lookup>_eps64_*.txt
+# DRAM bytes (read + write) per point of one join_kernel launch at eps = 2^6 on
+# the default workload (2^20 leaves or 2^22 table buckets), from one ncu capture
+# of this script's step: profiles/join_kernel_<lookup>_eps64_*.txt
 JOIN_FINEST_TRAFFIC = {
-    "learned": {"points": 100_000_000, "eps": 64, "bits": 20, "bytes": 1.76935e9},
+    "learned": {"eps": 64, "bits": 20, "bytes_per_point": 17.6935},
+    "table": {"eps": 64, "bits": 22, "bytes_per_point": 15.1170},
 }
+# DRAM bytes per launch (mean over the five 8-bit passes) of radix_scatter_kernel
+# in the step's record sort (117,378,603 packed records):
+# profiles/radix_scatter_kernel_sweep_zones263.txt
+SCATTER_TRAFFIC = {"records": 117_378_603, "bytes": 1.9478e9}
 
 
 def leaf_bits_for(n_ranges: int) -> int:
@@ -274,6 +279,7 @@ def main():
     stream = torch.cuda.current_stream()
     covs_live = []
     cov_bytes = [0] * E
+    ncells = [0] * E
     table_mixed = [0] * E
     table_bytes_fine = [0]
     fine_leaf_bits = [0]
@@ -299,6 +305,7 @@ def main():
                 events[i][2].record(stream)
             prepare(c)
             inf = c.info()
+            ncells[i] = inf.n_cells
             if i == E - 1:
                 fine_leaf_bits[0] = inf.index_leaf_bits
             if i == E - 1 and lookup == sdb.LOOKUP_TABLE:
@@ -324,6 +331,9 @@ def main():
     launches0 = sdb.launch_count()
     barrier(ws)
     torch.cuda.synchronize()
+    # per-phase device time of the library's launches (CUDA events around each
+    # traced launch on this stream), recorded over the timed steps
+    sdb.trace_enable(True)
     with Clocks(local) as clk:
         t0.record(stream)
         for k in range(args.steps):
@@ -331,6 +341,8 @@ def main():
         t1.record(stream)
         torch.cuda.synchronize()
     barrier(ws)
+    trace = sdb.trace_read()
+    sdb.trace_enable(False)
     launches = sdb.launch_count() - launches0
     ms = t0.elapsed_time(t1) / args.steps
     ms = max_over_ranks(ws, ms)
@@ -347,6 +359,8 @@ def main():
            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
            "config": config_of(w, N, args.lookup, args.table_bits), "clocks": clk.summary(),
            "gpu_launches": launches}
+    res["trace_per_step"] = {k: {"launches": c / args.steps, "ms": t / args.steps}
+                             for k, (c, t) in trace.items()}
     res["phases_ms"] = {"build_all_eps": sweep_build_ms,
                         "index": dict(zip([str(e) for e in w.eps], index_ms)),
                         "join_" + args.lookup: dict(zip([str(e) for e in w.eps], join_ms))}
@@ -469,10 +483,29 @@ def main():
             rng_rows[str(eps)] = row
             c.free()
         res["range_estimation"] = rng_rows
-    # ---- roofline of the join kernel of the finest eps inside the timed steps
-    # algorithmic bytes: the point stream (x, y, attr) plus one read of the
-    # lookup structure: the covering and its learned index, or the cell table
-    # (the covering itself is read only inside mixed buckets' windows)
+    # ---- rooflines from the traced launches of the timed steps (device time of
+    # each launch, CUDA events on the launching stream).
+    # The record sort's scatter, one launch per 8-bit pass over all records of
+    # the sweep: algorithmic bytes = records x (8 B read + 8 B written), and
+    # 8 B read + 12 B written in the last pass (keys and values apart)
+    recs = sum(ncells)
+    sc_n, sc_ms = trace.get("sort.scatter", (0, 0.0))
+    rooflines = {}
+    if sc_n:
+        passes = sc_n / args.steps
+        sc_bytes = recs * (16 * (passes - 1) + 20) / passes  # per launch
+        sc_avg = sc_ms / sc_n
+        ach = sc_bytes / (sc_avg / 1e3) / 1e9
+        T = SCATTER_TRAFFIC
+        rooflines["radix_scatter"] = {
+            "kernel": "radix_scatter_kernel (keys-only 8-bit pass, %d records)" % recs,
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind, "avg_launch_ms": sc_avg, "launches_per_step": passes,
+            "traffic": T["bytes"] if T and T["records"] == recs else None,
+            "algorithmic_bytes_per_launch": sc_bytes, "algorithmic_bytes_per_record": sc_bytes / recs}
+    # the join of the finest eps: the point stream (x, y, attr) plus one read of
+    # the lookup structure: the covering and its learned index, or the cell
+    # table (the covering itself is read only inside mixed cells' windows)
     fine = str(w.eps[-1])
     if lookup == sdb.LOOKUP_TABLE:
         per_pt = 12 + table_bytes_fine[0] / N
@@ -480,14 +513,23 @@ def main():
         per_pt = 12 + cov_bytes[-1] / N
     achieved = N * per_pt / (join_ms[-1] / 1e3) / 1e9
     T = JOIN_FINEST_TRAFFIC.get(args.lookup)
-    traffic = (T["bytes"] if (T and N == T["points"] and w.eps[-1] == T["eps"]
-                              and T.get("bits") in (None, fine_leaf_bits[0], args.table_bits))
+    traffic = (T["bytes_per_point"] * N if (T and w.eps[-1] == T["eps"]
+                                            and T.get("bits") in (fine_leaf_bits[0], args.table_bits))
                else None)
-    res["roofline"] = {"kernel": "join_kernel<%s> eps=%s" % (args.lookup, fine), "bound": "hbm",
-                       "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                       "peak_kind": peak_kind, "traffic": traffic,
-                       "algorithmic_bytes_per_point": per_pt,
-                       "algorithmic_bytes_per_launch": per_pt * N}
+    rooflines["join"] = {"kernel": "join_kernel<%s> eps=%s" % (args.lookup, fine), "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "avg_launch_ms": join_ms[-1],
+                         "algorithmic_bytes_per_point": per_pt,
+                         "algorithmic_bytes_per_launch": per_pt * N}
+    # the dominant kernel of the step (largest traced device time) carries the
+    # roofline; the join's is reported beside it
+    jn, jt = trace.get("join", (0, 0.0))
+    dom = "radix_scatter" if "radix_scatter" in rooflines and sc_ms >= jt else "join"
+    res["roofline"] = rooflines[dom]
+    res["roofline_join"] = rooflines["join"]
+    if "radix_scatter" in rooflines:
+        res["roofline_radix_scatter"] = rooflines["radix_scatter"]
     # ---- end to end through the host-buffer entry point
     if "e2e" in legs:
         hx = torch.from_numpy(w.points.x.view(np.int32)).pin_memory()

@@ -11,15 +11,15 @@
 // (x >> (B - L0)), with no curve encoding.  With r0 and r1 the ranges holding
 // the bucket's first and last id:
 //   r0 == r1: entry = pay[r0]               (the range's payload, as stored)
-//   r0 <  r1: entry = TAB_MIXED | m, win[m] = (r0, r1), m = rank of the cell
-//             among the mixed cells in row-major order
+//   r0 <  r1: entry = TAB_MIXED | m, win[m] = (r0, r1), m = rank of the bucket
+//             among the mixed buckets
+// r0 for every bucket comes from one pass over the ranges (each range marks the
+// first bucket starting inside it) and a prefix maximum over the buckets in
+// curve order; the entries are then written at the cells' row-major places.
 // A payload is 0xFFFFFFFF (no polygon), < 2^31 (one polygon), or 2^31 | r with
 // r < R; with R < 2^30 - 1 the values TAB_MIXED | m (m < 2^30 - 1) are disjoint
 // from all of them.  For a mixed cell the range of a point's finest id h is the
 // last r in [r0, r1] with start[r] <= h.
-#include <algorithm>
-
-#include "hilbert.cuh"
 #include "sdb_internal.cuh"
 
 namespace sdb {
@@ -38,47 +38,142 @@ __device__ __forceinline__ uint32_t last_le(const uint64_t* __restrict__ start, 
   return (uint32_t)lo;
 }
 
-// the Hilbert id at level L0 of the cell at row-major position c
-__device__ __forceinline__ uint64_t cell_bucket(uint64_t c, uint32_t L0, uint32_t nsteps,
-                                                uint32_t st0, const uint32_t* s_tab) {
-  const uint32_t cx = (uint32_t)(c & ((1ull << L0) - 1)), cy = (uint32_t)(c >> L0);
-  return hilbert3_encode(cx, cy, nsteps, st0, s_tab);
+// the row-major position of the cell of level L0 whose curve id is b: the
+// digits from the top (plain orientation there) give the transformed quadrant
+// (xt, yt) = (d >> 1, (d >> 1) ^ (d & 1)), undone by the orientation (sw, cm);
+// yt = 0 transposes, and also complements when xt = 1
+__device__ __forceinline__ uint64_t bucket_cell(uint64_t b, uint32_t L0) {
+  uint32_t sw = 0, cm = 0, cx = 0, cy = 0;
+  for (int lev = (int)L0 - 1; lev >= 0; --lev) {
+    const uint32_t d = (uint32_t)(b >> (2 * lev)) & 3u;
+    const uint32_t xt = d >> 1, yt = xt ^ (d & 1u);
+    const uint32_t u = xt ^ cm, v = yt ^ cm;
+    cx = (cx << 1) | (sw ? v : u);
+    cy = (cy << 1) | (sw ? u : v);
+    if (!yt) {
+      sw ^= 1u;
+      cm ^= xt;
+    }
+  }
+  return ((uint64_t)cy << L0) | cx;
 }
 
-__global__ void table_class_kernel(const uint64_t* __restrict__ start, uint64_t R,
-                                   const uint32_t* __restrict__ pay, uint32_t shift, uint32_t L0,
-                                   uint32_t nsteps, uint32_t st0, uint64_t nb,
-                                   uint32_t* __restrict__ tab, uint32_t* __restrict__ mixed) {
-  __shared__ uint32_t s_tab[HILBERT3_SMEM_WORDS];
-  hilbert3_fill(s_tab);
+// mark[b] = the last range r with first bucket fb(r) = b, where fb(r) is the
+// first bucket whose first id is >= start[r] (ranges are sorted: r is the last
+// one when fb(r + 1) differs, so each mark has one writer)
+__global__ void table_marks_kernel(const uint64_t* __restrict__ start, uint64_t R, uint32_t shift,
+                                   uint64_t nb, uint32_t* __restrict__ mark) {
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const uint64_t round = (1ull << shift) - 1;
+  const uint64_t b = (start[r] + round) >> shift;
+  const uint64_t bn = r + 1 < R ? (start[r + 1] + round) >> shift : nb;
+  if (b < nb && bn != b) mark[b] = (uint32_t)r;
+}
+
+// r0(b) = max(mark[0..b]): the range holding bucket b's first id.  A tile of
+// TT buckets per block: tile maxima, their exclusive max-scan, then the scan
+// within each tile.
+constexpr int TT = 2048, TB = 256;
+
+__device__ __forceinline__ uint32_t warp_incl_max(uint32_t v) {
+  const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= (uint32_t)o) v = max(v, t);
+  }
+  return v;
+}
+
+__global__ __launch_bounds__(TB) void tile_max_kernel(const uint32_t* __restrict__ mark, uint64_t nb,
+                                                      uint32_t* __restrict__ tmax) {
+  __shared__ uint32_t s[TB / 32];
+  const uint64_t b0 = (uint64_t)blockIdx.x * TT;
+  uint32_t m = 0;
+  for (uint32_t i = threadIdx.x; i < TT && b0 + i < nb; i += TB) m = max(m, mark[b0 + i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
   __syncthreads();
-  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nb;
-       c += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t b = cell_bucket(c, L0, nsteps, st0, s_tab);
-    const uint64_t lo = b << shift, hi = lo + ((1ull << shift) - 1);
-    const uint32_t r0 = last_le(start, R, lo);
-    // the bucket meets several ranges iff the next range starts inside it
-    const bool mix = start[r0 + 1] <= hi;
-    mixed[c] = mix ? 1u : 0u;
-    if (!mix) tab[c] = pay[r0];
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < TB / 32; ++w) m = max(m, s[w]);
+    tmax[blockIdx.x] = m;
+  }
+}
+
+// exclusive max-scan of the tile maxima, one block of 1024 threads
+__global__ __launch_bounds__(1024) void tile_prefix_kernel(uint32_t* __restrict__ tmax, uint32_t nt) {
+  __shared__ uint32_t s[32];
+  __shared__ uint32_t carry;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < nt; base += 1024) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < nt ? tmax[i] : 0u;
+    const uint32_t inc = warp_incl_max(v);
+    if (lane == 31) s[w] = inc;
+    __syncthreads();
+    if (w == 0) s[lane] = warp_incl_max(s[lane]);
+    __syncthreads();
+    const uint32_t wpre = w ? s[w - 1] : 0u;  // maximum over earlier warps
+    uint32_t prev = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) prev = 0;                  // maximum over earlier lanes
+    const uint32_t c = carry;
+    __syncthreads();
+    if (i < nt) tmax[i] = max(c, max(wpre, prev));
+    if (threadIdx.x == 1023) carry = max(c, max(wpre, inc));
+    __syncthreads();
+  }
+}
+
+// per bucket (curve order): r0 = max-scan of the marks; a bucket inside one
+// range stores that range's payload at its cell's row-major position, a
+// bucket that meets several ranges is flagged
+__global__ __launch_bounds__(TB) void table_fill_kernel(
+    const uint32_t* __restrict__ mark, const uint32_t* __restrict__ tpre, uint64_t nb,
+    const uint64_t* __restrict__ start, const uint32_t* __restrict__ pay, uint32_t shift,
+    uint32_t L0, uint32_t* __restrict__ tab, uint32_t* __restrict__ mixed) {
+  __shared__ uint32_t s[TB / 32];
+  __shared__ uint32_t carry;
+  const uint64_t b0 = (uint64_t)blockIdx.x * TT;
+  if (threadIdx.x == 0) carry = tpre[blockIdx.x];
+  __syncthreads();
+  for (uint32_t base = 0; base < TT && b0 + base < nb; base += TB) {
+    const uint64_t b = b0 + base + threadIdx.x;
+    const uint32_t v = b < nb ? mark[b] : 0u;
+    const uint32_t inc = warp_incl_max(v);
+    if ((threadIdx.x & 31) == 31) s[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) wpre = max(wpre, s[w]);
+    const uint32_t c = carry;
+    const uint32_t r0 = max(c, max(wpre, inc));
+    if (b < nb) {
+      const uint64_t lo = b << shift, hi = lo + ((1ull << shift) - 1);
+      // the bucket meets several ranges iff the next range starts inside it
+      const bool mix = start[r0 + 1] <= hi;
+      mixed[b] = mix ? 1u : 0u;
+      if (!mix) tab[bucket_cell(b, L0)] = pay[r0];
+    }
+    __syncthreads();
+    if (threadIdx.x == TB - 1) carry = r0;
+    __syncthreads();
   }
 }
 
 __global__ void table_mixed_kernel(const uint64_t* __restrict__ start, uint64_t R,
-                                   uint32_t shift, uint32_t L0, uint32_t nsteps, uint32_t st0,
-                                   uint64_t nb, const uint32_t* __restrict__ mixed,
+                                   uint32_t shift, uint32_t L0, uint64_t nb,
+                                   const uint32_t* __restrict__ mixed,
                                    const uint32_t* __restrict__ rank, uint32_t* __restrict__ tab,
                                    uint2* __restrict__ win) {
-  __shared__ uint32_t s_tab[HILBERT3_SMEM_WORDS];
-  hilbert3_fill(s_tab);
-  __syncthreads();
-  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nb;
-       c += (uint64_t)gridDim.x * blockDim.x) {
-    if (!mixed[c]) continue;
-    const uint64_t b = cell_bucket(c, L0, nsteps, st0, s_tab);
+  for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nb;
+       b += (uint64_t)gridDim.x * blockDim.x) {
+    if (!mixed[b]) continue;
     const uint64_t lo = b << shift, hi = lo + ((1ull << shift) - 1);
-    const uint32_t m = rank[c];
-    tab[c] = TAB_MIXED | m;
+    const uint32_t m = rank[b];
+    tab[bucket_cell(b, L0)] = TAB_MIXED | m;
     win[m] = make_uint2(last_le(start, R, lo), last_le(start, R, hi));
   }
 }
@@ -103,27 +198,37 @@ sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t
   cov->tab_bits = 0;
   cov->tab_mixed = 0;
   Scratch sc(s);
-  uint32_t *mixed, *rank, *dtot;
+  uint32_t *mixed, *rank, *dtot, *mark, *tpre;
+  const uint64_t nt = (nb + TT - 1) / TT;
   SDB_TRY(dalloc_n(&cov->tab, nb, s));
   SDB_TRY(sc.get(&mixed, nb));
   SDB_TRY(sc.get(&rank, nb));
+  SDB_TRY(sc.get(&mark, nb));
+  SDB_TRY(sc.get(&tpre, nt));
   SDB_TRY(sc.get(&dtot, 1));
-  uint32_t nsteps, st0;
-  hilbert3_params(T / 2, &nsteps, &st0);
-  // a few blocks per SM (each fills the curve table in shared memory once)
-  const unsigned grid = (unsigned)std::min<uint64_t>(grid_for(nb, 256), (uint64_t)num_sms() * 8);
-  table_class_kernel<<<grid, 256, 0, s>>>(cov->start, cov->R, cov->pay, shift, T / 2,
-                                                        nsteps, st0, nb, cov->tab, mixed);
+  SDB_TRY_CUDA(cudaMemsetAsync(mark, 0, nb * 4, s));
+  table_marks_kernel<<<grid_for(cov->R, 256), 256, 0, s>>>(cov->start, cov->R, shift, nb, mark);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
+  tile_max_kernel<<<(unsigned)nt, TB, 0, s>>>(mark, nb, tpre);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  tile_prefix_kernel<<<1, 1024, 0, s>>>(tpre, (uint32_t)nt);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  table_fill_kernel<<<(unsigned)nt, TB, 0, s>>>(mark, tpre, nb, cov->start, cov->pay, shift, T / 2,
+                                                cov->tab, mixed);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  const unsigned grid = grid_for(nb, 256);
   SDB_TRY(exclusive_scan<uint32_t>(mixed, rank, nb, dtot, s));
   uint32_t M = 0;
   SDB_TRY_CUDA(cudaMemcpyAsync(&M, dtot, 4, cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   if (M > 0) {
     SDB_TRY(dalloc_n(&cov->win, M, s));
-    table_mixed_kernel<<<grid, 256, 0, s>>>(cov->start, cov->R, shift, T / 2, nsteps,
-                                                          st0, nb, mixed, rank, cov->tab, cov->win);
+    table_mixed_kernel<<<grid, 256, 0, s>>>(cov->start, cov->R, shift, T / 2, nb, mixed, rank,
+                                            cov->tab, cov->win);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
   }
