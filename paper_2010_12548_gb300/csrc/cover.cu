@@ -25,7 +25,9 @@
 // neighbours) gives the canonical ranges.
 #include "sdb_internal.cuh"
 
+#include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -1216,17 +1218,40 @@ static sdb_status launch_expand(uint32_t G, const Item* items, uint32_t n_items,
   return SDB_OK;
 }
 
-// Capacity hints from earlier builds in this process (records, frontier cells,
-// frontier edge entries), so that a build of a size seen before allocates its
-// buffers once instead of growing them level by level (a grown buffer is a new
-// allocation plus a copy; growing pool memory is slow).  Hints only: a build
-// that needs more still grows.
-std::atomic<uint64_t> g_hint_rec{1ull << 20}, g_hint_items{1ull << 16}, g_hint_edges{1ull << 18};
-
-void raise_hint(std::atomic<uint64_t>& h, uint64_t v) {
-  uint64_t cur = h.load(std::memory_order_relaxed);
-  while (v > cur && !h.compare_exchange_weak(cur, v, std::memory_order_relaxed)) {
+// Capacity hints from earlier builds of the same shape in this process
+// (records, frontier cells, frontier edge entries), so that a repeated build
+// allocates its buffers once instead of growing them level by level (a grown
+// record buffer is a new allocation plus a copy).  Builds of other shapes (the
+// varied small builds of a serving loop) start small and grow.  Hints only: a
+// build that needs more still grows.
+struct BuildShape {
+  uint32_t B, Q, NP, V, Fmax;
+  bool operator==(const BuildShape& o) const {
+    return B == o.B && Q == o.Q && NP == o.NP && V == o.V && Fmax == o.Fmax;
   }
+};
+struct BuildHint {
+  uint64_t rec = 1ull << 20, items = 1ull << 12, edges = 1ull << 14;
+};
+std::mutex g_hint_mu;
+std::vector<std::pair<BuildShape, BuildHint>> g_hints;  // most recent last, at most 16
+
+BuildHint hint_for(const BuildShape& k) {
+  std::lock_guard<std::mutex> lk(g_hint_mu);
+  for (const auto& e : g_hints)
+    if (e.first == k) return e.second;
+  return BuildHint{};
+}
+
+void keep_hint(const BuildShape& k, const BuildHint& h) {
+  std::lock_guard<std::mutex> lk(g_hint_mu);
+  for (auto it = g_hints.begin(); it != g_hints.end(); ++it)
+    if (it->first == k) {
+      g_hints.erase(it);
+      break;
+    }
+  if (g_hints.size() >= 16) g_hints.erase(g_hints.begin());
+  g_hints.emplace_back(k, h);
 }
 
 uint64_t pow2_at_least(uint64_t v) {
@@ -1293,7 +1318,11 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   uint32_t sb = (uint32_t)bits_for(max_slot);
   if (sb < 1) sb = 1;
   if (key_bits + (int)sb + 6 > 64) sb = 0;
-  uint64_t rec_cap = g_hint_rec.load(std::memory_order_relaxed), n_rec = 0;
+  const BuildShape shape{B, Q, NP, V, Fmax};
+  const BuildHint hint = hint_for(shape);
+  BuildHint seen;
+  seen.rec = seen.items = seen.edges = 0;
+  uint64_t rec_cap = hint.rec, n_rec = 0;
   if (rec_cap < 8ull * NP) rec_cap = 8ull * NP;
   uint64_t* rkey = nullptr;
   uint32_t* rval = nullptr;
@@ -1330,11 +1359,11 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
   Item** fbuf = fr.f;
   uint32_t** ebuf = fr.e;
   uint64_t fcap[2], ecap[2];
-  fcap[0] = g_hint_items.load(std::memory_order_relaxed);
+  fcap[0] = hint.items;
   if (fcap[0] < NP) fcap[0] = pow2_at_least(NP);
   fcap[1] = fcap[0];
   ecap[0] = V;  // the polygons' own edge lists (scratch)
-  ecap[1] = g_hint_edges.load(std::memory_order_relaxed);
+  ecap[1] = hint.edges;
   SDB_TRY(dalloc_n(&fbuf[0], fcap[0], s));
   SDB_TRY(dalloc_n(&fbuf[1], fcap[1], s));
   SDB_TRY(dalloc_n(&ebuf[1], ecap[1], s));
@@ -1431,11 +1460,14 @@ sdb_status build_coverings(const PolyEdges& pe, const CoverSpec& spec, cudaStrea
     n_items = last ? 0 : h[0];
     n_edges = h[1];
     n_rec += h[2];
-    raise_hint(g_hint_items, pow2_at_least(4 * n_items));
-    raise_hint(g_hint_edges, pow2_at_least(4 * n_edges));
+    seen.items = std::max<uint64_t>(seen.items, pow2_at_least(4 * n_items));
+    seen.edges = std::max<uint64_t>(seen.edges, pow2_at_least(4 * n_edges));
   }
   tr_lv.end();
-  raise_hint(g_hint_rec, pow2_at_least(n_rec));
+  seen.rec = std::max<uint64_t>(pow2_at_least(n_rec), 1ull << 16);
+  seen.items = std::max<uint64_t>(seen.items, 1ull << 12);
+  seen.edges = std::max<uint64_t>(seen.edges, 1ull << 14);
+  keep_hint(shape, seen);
   out->ncells = n_rec;
   return merge_records(rkey, rval, n_rec, spec, d_qs, qshift, key_bits, sb, s, out);
 }
