@@ -82,16 +82,4 @@ __device__ __forceinline__ uint64_t hilbert3_encode(uint32_t cx, uint32_t cy, ui
   return h;
 }
 
-// the same for at most 5 table steps (ids below 2^30), in 32-bit arithmetic
-__device__ __forceinline__ uint32_t hilbert3_encode32(uint32_t cx, uint32_t cy, uint32_t nsteps,
-                                                      uint32_t st0, const uint32_t* tab) {
-  if (nsteps == 0) return 0;
-  const uint32_t* row = tab + (threadIdx.x & 31u);
-  const uint32_t sh = 32 - 3 * nsteps;
-  uint32_t xs = cx << sh, ys = cy << sh, st = st0 << 6;
-  uint32_t h = 0;
-  for (uint32_t s = 0; s < nsteps; ++s) h = (h << 6) | hilbert3_step(xs, ys, st, row);
-  return h;
-}
-
 }  // namespace sdb
