@@ -89,15 +89,19 @@ def parse():
     return ap.parse_args()
 
 
-def dist_init(args):
+def dist_init(args, backend: str | None = None):
+    """One process per GPU (torchrun environment); NCCL on GPUs, gloo when the
+    caller asks for it (the CPU tests of this host logic)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        backend = backend or "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -108,13 +112,21 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, v):
+    """The maximum of v over all ranks (the job's time is its slowest rank's)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(ws, units_per_rank, seconds):
+    """Whole-job throughput of weak-scaled replicas: every rank's units over the
+    slowest rank's time."""
+    return ws * units_per_rank / seconds
 
 
 class Clocks:
@@ -346,7 +358,7 @@ def main():
     launches = sdb.launch_count() - launches0
     ms = t0.elapsed_time(t1) / args.steps
     ms = max_over_ranks(ws, ms)
-    value = ws * N * E / (ms / 1e3)
+    value = job_rate(ws, N * E, ms / 1e3)
     sweep_build_ms = statistics.mean(ev[k][0][0].elapsed_time(ev[k][0][1])
                                      for k in range(args.steps))
     index_ms = [statistics.mean(ev[k][i][2].elapsed_time(ev[k][i][3]) for k in range(args.steps))
@@ -555,7 +567,7 @@ def main():
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - tt) / args.steps
         e2e_s = max_over_ranks(ws, e2e_s)
-        res["e2e"] = {"value": ws * N * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * 12,
+        res["e2e"] = {"value": job_rate(ws, N * E, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * 12,
                       "d2h_bytes_per_step": E * P * 16, "ms_per_step": e2e_s * 1e3}
         # the host join must agree with the device join
         res["e2e"]["matches_device"] = bool(np.array_equal(hc.numpy(), cnt.cpu().numpy()) and
