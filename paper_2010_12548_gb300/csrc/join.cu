@@ -179,7 +179,7 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
       }
     }
   }
-  // judge: the result must bracket h (ends not proven by a probe are read);
+  // verification: the result must bracket h (ends not proven by a probe are read);
   // otherwise plain binary search decides
 #pragma unroll
   for (int q = 0; q < G; ++q) {
