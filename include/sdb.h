@@ -246,6 +246,24 @@ sdb_status sdb_join_aggregate_range(const uint32_t *d_x, const uint32_t *d_y,
                                     uint64_t *d_bcount, int64_t *d_bsum, uint64_t *d_babs,
                                     void *cuda_stream);
 
+/* The result ranges of Sec. 6 ("the exact answer lies in [alpha - beta,
+ * alpha]") from the partials of sdb_join_aggregate_range, computed on the
+ * device: for every polygon j < n_polygons
+ *   d_count_lo[j] = d_count[j] - d_bcount[j],  d_count_hi[j] = d_count[j],
+ *   d_sum_lo[j] = d_sum[j] - (d_babs[j] + d_bsum[j]) / 2,
+ *   d_sum_hi[j] = d_sum[j] + (d_babs[j] - d_bsum[j]) / 2
+ * (exact integers: the false positives of a conservative raster are a subset
+ * of the boundary points, whose positive and negative attribute parts are the
+ * two halves).  All arrays are device memory of n_polygons entries owned by
+ * the caller; the five sum arrays are given together or all NULL (COUNT only).
+ * Asynchronous on cuda_stream.  SDB_EINVAL: a NULL count array, or only some of
+ * the sum arrays. */
+sdb_status sdb_result_bounds(const uint64_t *d_count, const int64_t *d_sum,
+                             const uint64_t *d_bcount, const int64_t *d_bsum,
+                             const uint64_t *d_babs, uint32_t n_polygons, uint64_t *d_count_lo,
+                             uint64_t *d_count_hi, int64_t *d_sum_lo, int64_t *d_sum_hi,
+                             void *cuda_stream);
+
 /* sdb_join_aggregate for n_covs coverings of the same polygons on the same grid
  * (an eps sweep) in one pass over the points: each point is read and its cell
  * id computed once, at the finest level among the coverings (a coarser id is
@@ -278,10 +296,10 @@ sdb_status sdb_join_aggregate_host(const uint32_t *h_x, const uint32_t *h_y, con
 
 /* Allocation-free variant of sdb_join_aggregate_host for one covering.  The paper
  * has no counterpart: this serves callers that cannot allocate device memory
- * while they call in -- code running while a CUDA stream capture is active
- * (allocation is not permitted during capture), services that reserve their
- * whole device-memory budget up front and forbid later allocations, and plugins
- * inside a process whose own allocator owns the device.
+ * while they call in -- services that reserve their whole device-memory budget
+ * when they start and must not allocate afterwards, and plugins inside a
+ * process whose own allocator owns the device and forbids allocations made
+ * behind its back.
  *
  * Staging buffers and per-polygon accumulators live in one file-scope device
  * array of SDB_NOALLOC_CHUNK * 12 + SDB_NOALLOC_MAX_POLYGONS * 16 bytes (13 MiB)
@@ -290,7 +308,8 @@ sdb_status sdb_join_aggregate_host(const uint32_t *h_x, const uint32_t *h_y, con
  * points SDB_NOALLOC_CHUNK at a time on cuda_stream alone and synchronises it
  * before returning (results in h_count/h_sum, P entries each).  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every
+ * that device current and keeps it; after a cudaDeviceReset of that device the
+ * kept address is stale, so the entry point must not be called again.  Every
  * call shares the array and clears the accumulators itself; calls whose GPU work
  * overlaps (other streams or threads) race on it.
  * SDB_EINVAL: more than SDB_NOALLOC_MAX_POLYGONS polygons, and the argument
@@ -544,6 +563,12 @@ const char *sdb_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far (all
  * devices, all threads).  A diagnostic counter; host only, never fails. */
 uint64_t sdb_launch_count(void);
+
+/* Device memory of the library's stream-ordered pool on the current device:
+ * bytes handed out and not yet freed (used) and bytes the pool holds from the
+ * driver (reserved; freed blocks are kept for reuse).  Diagnostics; host only.
+ * SDB_EINVAL: a NULL output. */
+sdb_status sdb_memory_stats(uint64_t *pool_used, uint64_t *pool_reserved);
 
 /* Device time of the library's phases (diagnostics).  While tracing is on, each
  * traced phase records a CUDA event before and after its work on the stream it

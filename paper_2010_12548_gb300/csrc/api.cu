@@ -575,6 +575,25 @@ sdb_status sdb_join_aggregate_range(const uint32_t* d_x, const uint32_t* d_y, co
                      true, d_bcount, d_bsum, d_babs);
 }
 
+sdb_status sdb_result_bounds(const uint64_t* d_count, const int64_t* d_sum,
+                             const uint64_t* d_bcount, const int64_t* d_bsum,
+                             const uint64_t* d_babs, uint32_t n_polygons, uint64_t* d_count_lo,
+                             uint64_t* d_count_hi, int64_t* d_sum_lo, int64_t* d_sum_hi,
+                             void* cuda_stream) {
+  if (!d_count || !d_bcount || !d_count_lo || !d_count_hi) {
+    set_error("d_count, d_bcount, d_count_lo or d_count_hi is NULL");
+    return SDB_EINVAL;
+  }
+  const bool any = d_sum || d_bsum || d_babs || d_sum_lo || d_sum_hi;
+  const bool all = d_sum && d_bsum && d_babs && d_sum_lo && d_sum_hi;
+  if (any && !all) {
+    set_error("d_sum, d_bsum, d_babs, d_sum_lo and d_sum_hi must be given together");
+    return SDB_EINVAL;
+  }
+  return launch_result_bounds(d_count, d_sum, d_bcount, d_bsum, d_babs, n_polygons, d_count_lo,
+                              d_count_hi, d_sum_lo, d_sum_hi, (cudaStream_t)cuda_stream);
+}
+
 sdb_status sdb_join_aggregate_multi(const uint32_t* d_x, const uint32_t* d_y, const int32_t* d_attr,
                                     uint64_t n, const sdb_covering* const* covs, uint32_t n_covs,
                                     int lookup, uint64_t* d_count, int64_t* d_sum,
@@ -786,6 +805,21 @@ const char* sdb_status_string(sdb_status s) {
 const char* sdb_last_error(void) { return g_err; }
 
 uint64_t sdb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+sdb_status sdb_memory_stats(uint64_t* pool_used, uint64_t* pool_reserved) {
+  if (!pool_used || !pool_reserved) {
+    set_error("pool_used or pool_reserved is NULL");
+    return SDB_EINVAL;
+  }
+  cudaMemPool_t pool;
+  SDB_TRY(get_pool(&pool));
+  unsigned long long used = 0, reserved = 0;  // the attributes are 64-bit counters
+  SDB_TRY_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  SDB_TRY_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+  *pool_used = used;
+  *pool_reserved = reserved;
+  return SDB_OK;
+}
 
 sdb_status sdb_trace_enable(int on) {
   std::lock_guard<std::mutex> lk(g_tmu);

@@ -728,6 +728,46 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
 }
 
 namespace {
+// Sec. 6: a conservative raster errs only by false positives, all of them
+// points in boundary cells, so the exact COUNT lies in [count - bcount, count]
+// and the exact SUM in [sum - pos, sum + neg] with pos = (babs + bsum) / 2 and
+// neg = (babs - bsum) / 2 the boundary points' positive and negative attribute
+// mass (both exact: babs + bsum and babs - bsum are twice a sum of magnitudes).
+__global__ void result_bounds_kernel(const uint64_t* __restrict__ count,
+                                     const int64_t* __restrict__ sum,
+                                     const uint64_t* __restrict__ bcount,
+                                     const int64_t* __restrict__ bsum,
+                                     const uint64_t* __restrict__ babs, uint32_t P,
+                                     uint64_t* __restrict__ count_lo,
+                                     uint64_t* __restrict__ count_hi, int64_t* __restrict__ sum_lo,
+                                     int64_t* __restrict__ sum_hi) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P) return;
+  const uint64_t c = count[j];
+  count_lo[j] = c - bcount[j];
+  count_hi[j] = c;
+  if (sum) {
+    const uint64_t ab = babs[j], bs = (uint64_t)bsum[j];
+    const uint64_t pos = (ab + bs) >> 1, neg = (ab - bs) >> 1;  // both < 2^63
+    sum_lo[j] = (int64_t)((uint64_t)sum[j] - pos);
+    sum_hi[j] = (int64_t)((uint64_t)sum[j] + neg);
+  }
+}
+}  // namespace
+
+sdb_status launch_result_bounds(const uint64_t* count, const int64_t* sum, const uint64_t* bcount,
+                                const int64_t* bsum, const uint64_t* babs, uint32_t P,
+                                uint64_t* count_lo, uint64_t* count_hi, int64_t* sum_lo,
+                                int64_t* sum_hi, cudaStream_t s) {
+  if (P == 0) return SDB_OK;
+  result_bounds_kernel<<<(P + 255) / 256, 256, 0, s>>>(count, sum, bcount, bsum, babs, P,
+                                                       count_lo, count_hi, sum_lo, sum_hi);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  return SDB_OK;
+}
+
+namespace {
 JoinArgs join_args(const uint32_t* x, const uint32_t* y, const int32_t* attr, uint64_t n,
                    const sdb_covering* cov, uint64_t* count, int64_t* sum) {
   JoinArgs A{};

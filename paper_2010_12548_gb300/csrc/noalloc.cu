@@ -1,18 +1,23 @@
 // Host-buffer join that allocates no device memory.
 //
 // Some callers cannot allocate device memory while they call into this
-// library: code that runs while a CUDA stream capture is active (allocation
-// calls are not permitted during capture), services that reserve their whole
-// device-memory budget up front and forbid later allocations, and plugins
-// loaded into a process whose own allocator owns the device.  For them this
-// entry point streams host points through a fixed-size staging area and keeps
-// the per-polygon accumulators in the same area: a file-scope device array
-// that every GPU which loads the library holds until the process exits.
+// library: services that reserve their whole device-memory budget when they
+// start and must not allocate afterwards (an allocation could fail or stall at
+// an arbitrary moment under load), and plugins loaded into a process whose own
+// allocator owns the device and forbids allocations made behind its back.
+// For them this entry point streams host points through a fixed-size staging
+// area and keeps the per-polygon accumulators in the same area: a file-scope
+// device array that every GPU which loads the library holds until the process
+// exits.
 //
 // Limits: at most SDB_NOALLOC_MAX_POLYGONS polygons per covering; any number of
 // points (they are processed SDB_NOALLOC_CHUNK at a time).  The array is shared
 // by every call: each call clears the accumulators before use, and calls whose
-// GPU work overlaps (on different streams or threads) race on the array.
+// GPU work overlaps (on different streams or threads) race on the array.  The
+// first call on a device looks up the array's device address with that device
+// current and keeps it for the life of the process; a process that resets the
+// device (cudaDeviceReset) reloads the module, so it must not call this entry
+// point again afterwards (the kept address would be stale).
 #include "sdb_internal.cuh"
 
 #include <mutex>

@@ -352,6 +352,11 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
 // r < 2^30 - 1, so the two never collide)
 constexpr uint32_t TAB_MIXED = 0xC0000000u;
 constexpr uint32_t TAB_MIXED_MAX = 0x3fffffffu;
+// Sec. 6 intervals from the range join's partials (join.cu)
+sdb_status launch_result_bounds(const uint64_t* count, const int64_t* sum, const uint64_t* bcount,
+                                const int64_t* bsum, const uint64_t* babs, uint32_t P,
+                                uint64_t* count_lo, uint64_t* count_hi, int64_t* sum_lo,
+                                int64_t* sum_hi, cudaStream_t s);
 sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t s);
 // A covering record's value: polygon slot (bits 0..25), level above the finest
 // (26..30), boundary flag (31).  Packed record (one 64-bit word, sb slot bits):

@@ -111,6 +111,7 @@ def lib():
             "sdb_join_aggregate_multi": ([P, P, P, U64, P, U32, I, P, P, P], I),
             "sdb_raster_join_multi": ([P, U32, U64, P, P, P, U64, U32, P, P, P], I),
             "sdb_join_aggregate_range": ([P, P, P, U64, P, I, P, P, P, P, P, P], I),
+            "sdb_result_bounds": ([P, P, P, P, P, U32, P, P, P, P, P], I),
             "sdb_covering_get_info": ([P, P], I),
             "sdb_covering_build_index": ([P, U32, P], I),
             "sdb_covering_build_table": ([P, U32, P], I),
@@ -124,6 +125,7 @@ def lib():
             "sdb_status_string": ([I], C.c_char_p),
             "sdb_last_error": ([], C.c_char_p),
             "sdb_launch_count": ([], U64),
+            "sdb_memory_stats": ([P, P], I),
             "sdb_covering_index_stats": ([P, P, P], I),
             "sdb_points_create": ([P, P, P, U64, U32, P, P], I),
             "sdb_points_free": ([P], None),
@@ -290,12 +292,20 @@ def join_aggregate_range(x, y, attr, cov: Covering, lookup: int, count, bcount, 
                                           _stream(stream)))
 
 
-def range_bounds(count, sum_, bcount, bsum, babs):
-    """Intervals holding the exact COUNT and SUM (numpy int64 arrays in, out):
-    [count - bcount, count] and [sum - (babs + bsum) / 2, sum + (babs - bsum) / 2]."""
-    count, sum_, bcount = (np.asarray(v, np.int64) for v in (count, sum_, bcount))
-    bsum, babs = np.asarray(bsum, np.int64), np.asarray(babs, np.int64)
-    return count - bcount, count, sum_ - (babs + bsum) // 2, sum_ + (babs - bsum) // 2
+def result_bounds(count, bcount, sum_=None, bsum=None, babs=None, stream=None):
+    """sdb_result_bounds on the range join's device outputs (int64 tensors of
+    P entries): returns device tensors (count_lo, count_hi, sum_lo, sum_hi), the
+    sum pair None for COUNT only."""
+    import torch
+    P = count.numel()
+    new = lambda: torch.empty(P, dtype=torch.int64, device=count.device)  # noqa: E731
+    c_lo, c_hi = new(), new()
+    s_lo, s_hi = (new(), new()) if sum_ is not None else (None, None)
+    _check(lib().sdb_result_bounds(_dptr(count, 8), _dptr(sum_, 8), _dptr(bcount, 8),
+                                   _dptr(bsum, 8), _dptr(babs, 8), P, _dptr(c_lo, 8),
+                                   _dptr(c_hi, 8), _dptr(s_lo, 8), _dptr(s_hi, 8),
+                                   _stream(stream)))
+    return c_lo, c_hi, s_lo, s_hi
 
 
 def join_aggregate_host(x, y, attr, covs, lookup: int, stream=None):
@@ -381,6 +391,14 @@ def trace_read() -> dict:
     _check(lib().sdb_trace_read(C.cast(buf, C.c_void_p), n.value, C.byref(n)))
     return {buf[i].name.decode(): (int(buf[i].count), float(buf[i].total_ms))
             for i in range(min(n.value, len(buf)))}
+
+
+def memory_stats() -> tuple[int, int]:
+    """(used, reserved) bytes of the library's device memory pool on the
+    current device."""
+    u, r = C.c_uint64(), C.c_uint64()
+    _check(lib().sdb_memory_stats(C.byref(u), C.byref(r)))
+    return int(u.value), int(r.value)
 
 
 def launch_count() -> int:

@@ -3,7 +3,9 @@
 Boundary-flagged coverings must equal the oracle's flagged coverings entry for
 entry (both merge paths), and the range join's five per-polygon outputs (count,
 sum, boundary count, boundary sum, boundary magnitude sum) must equal the
-oracle's flagged O1 join bit for bit, for both lookups.  At full size (the
+oracle's flagged O1 join bit for bit, for both lookups, and the COUNT and SUM
+intervals the library derives from them on the device must equal the
+oracle's.  At full size (the
 263-zone tiling at eps = 2^6 over 100M points) the counts and sums must equal
 the plain join's and, on a sample of points, the boundary partials must equal
 the definitional O2 test.
@@ -11,6 +13,7 @@ the definitional O2 test.
 import numpy as np
 import pytest
 
+from oracle import oracle as ORC
 from paper_2010_12548_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -34,11 +37,30 @@ def gpu_range(torch, sdb, cov, pts, lookup, with_sum=True, x=None, y=None, a=Non
     cnt, bc = out(), out()
     sm, bs, ba = (out(), out(), out()) if with_sum else (None, None, None)
     sdb.join_aggregate_range(x, y, a, cov, lookup, cnt, bc, sm, bs, ba)
+    # the Sec. 6 intervals, computed by the library from the device partials
+    bounds = sdb.result_bounds(cnt, bc, sm, bs, ba)
     torch.cuda.synchronize()
     u64 = lambda t: t.cpu().numpy().view(np.uint64)  # noqa: E731
     if not with_sum:
-        return u64(cnt), u64(bc)
-    return u64(cnt), sm.cpu().numpy(), u64(bc), bs.cpu().numpy(), u64(ba)
+        got = u64(cnt), u64(bc)
+        lo_c, hi_c = bounds[0].cpu().numpy(), bounds[1].cpu().numpy()
+        assert bounds[2] is None and bounds[3] is None
+        assert np.array_equal(lo_c, got[0].astype(np.int64) - got[1].astype(np.int64))
+        assert np.array_equal(hi_c, got[0].astype(np.int64))
+        return got
+    got = u64(cnt), sm.cpu().numpy(), u64(bc), bs.cpu().numpy(), u64(ba)
+    LAST_BOUNDS[:] = [b.cpu().numpy() for b in bounds]
+    return got
+
+
+# the device intervals of the most recent gpu_range call with sums
+LAST_BOUNDS = []
+
+
+def assert_bounds_match_oracle(orc, want):
+    """The library's intervals equal the oracle's, element by element."""
+    for g, w in zip(LAST_BOUNDS, orc.range_bounds(*want)):
+        assert np.array_equal(g, w)
 
 
 def assert_same_covering(sdb, cov, oc):
@@ -63,6 +85,7 @@ def check_range(torch, sdb, cov, oc, pts):
         got = gpu_range(torch, sdb, cov, pts, lookup)
         for g, w in zip(got, want):
             assert np.array_equal(g, w), lookup
+        assert_bounds_match_oracle(ORC, want)
         c, b = gpu_range(torch, sdb, cov, pts, lookup, with_sum=False)
         assert np.array_equal(c, want[0]) and np.array_equal(b, want[2])
         # the plain join on a flagged covering: plain results
@@ -92,7 +115,7 @@ def test_flagged_overlapping_stars(cuda, sdblib, orc, B, eps, seed):
     pts = signed_points(seed, 20_011, B)
     want = check_range(cuda, sdblib, cov, oc, pts)
     ex, exs = orc.join_exact(P, pts)
-    lo_c, hi_c, lo_s, hi_s = sdblib.range_bounds(*want)
+    lo_c, hi_c, lo_s, hi_s = LAST_BOUNDS
     assert ((lo_c <= ex) & (ex <= hi_c)).all() and ((lo_s <= exs) & (exs <= hi_s)).all()
 
 
@@ -130,6 +153,7 @@ def test_range_edge_cases(cuda, sdblib, orc):
                 got = gpu_range(torch, sdblib, cov, pts, lookup)
                 for g, w in zip(got, want):
                     assert np.array_equal(g, w), (eps, n, lookup)
+                assert_bounds_match_oracle(orc, want)
     # argument errors are caught on the host
     plain = sdblib.build_covering(P, B, 9)
     z = torch.zeros(P.n, dtype=torch.int64, device="cuda")
@@ -143,6 +167,9 @@ def test_range_edge_cases(cuda, sdblib, orc):
     assert e.value.status == sdblib.SDB_EINVAL
     with pytest.raises(sdblib.SdbError) as e:
         sdblib.build_covering(P, B, 9, flags=4)
+    assert e.value.status == sdblib.SDB_EINVAL
+    with pytest.raises(sdblib.SdbError) as e:  # sum arrays given only in part
+        sdblib.result_bounds(z, z, z, None, z)
     assert e.value.status == sdblib.SDB_EINVAL
 
 
@@ -189,6 +216,7 @@ def test_range_full_size_sampled(cuda, sdblib, orc):
     c2, s2, b2, bs2, ba2 = orc.join_o2(T, eps, sample, threads=16, boundary_sums=True)
     for u, v in zip(g, (c2, s2, b2, bs2, ba2)):
         assert np.array_equal(u, v)
+    assert_bounds_match_oracle(orc, (c2, s2, b2, bs2, ba2))
     ex, exs = orc.join_exact(T, sample, threads=16)
-    lo_c, hi_c, lo_s, hi_s = sdblib.range_bounds(*g)
+    lo_c, hi_c, lo_s, hi_s = LAST_BOUNDS
     assert ((lo_c <= ex) & (ex <= hi_c)).all() and ((lo_s <= exs) & (exs <= hi_s)).all()

@@ -1,10 +1,12 @@
 """The allocation-free host-buffer join (sdb_join_aggregate_host_noalloc).
 
-It serves callers that cannot allocate device memory while calling in (code
-inside a CUDA stream capture, services that reserve their memory budget up
-front, plugins in a process whose allocator owns the device).  Its results must
-equal the regular host-buffer entry point's, bit for bit, on consecutive calls
-that reuse the same fixed device array.  This file is collected last.
+It serves callers that cannot allocate device memory while calling in
+(services that reserve their whole memory budget when they start, plugins in a
+process whose own allocator owns the device).  Its results must equal the
+regular host-buffer entry point's, bit for bit, on consecutive calls that reuse
+the same fixed device array, for every covering lookup; and once the first call
+has set the array up, further calls must leave the device's free memory and the
+library's memory pool untouched.  This file is collected last.
 """
 import numpy as np
 import pytest
@@ -19,20 +21,35 @@ def test_noalloc_join_matches_host_join(cuda, sdblib):
     w = W.tiny_stars(2_500_003)
     cov = sdblib.build_covering(w.polygons, w.grid_bits, w.eps[0])
     sdblib.covering_build_index(cov, 8)
-    for lookup in (sdblib.LOOKUP_BINARY, sdblib.LOOKUP_LEARNED):
-        want_c, want_s = sdblib.join_aggregate_host(w.points.x, w.points.y, w.points.attr,
-                                                    [cov], lookup)
+    sdblib.covering_build_table(cov, 12)
+    lookups = (sdblib.LOOKUP_BINARY, sdblib.LOOKUP_LEARNED, sdblib.LOOKUP_TABLE)
+    half = w.points.n // 2
+    want = {}
+    for lookup in lookups:
+        c, s = sdblib.join_aggregate_host(w.points.x, w.points.y, w.points.attr, [cov], lookup)
+        ch, _ = sdblib.join_aggregate_host(w.points.x[:half], w.points.y[:half], None, [cov],
+                                           lookup)
+        want[lookup] = (c[0], s[0], ch[0])
+    # the first call on the device sets the fixed array up (and loads the
+    # kernels); after it nothing may be allocated
+    sdblib.join_aggregate_host_noalloc(w.points.x[:10], w.points.y[:10], w.points.attr[:10], cov,
+                                       sdblib.LOOKUP_BINARY)
+    cuda.cuda.synchronize()
+    free0 = cuda.cuda.mem_get_info()[0]
+    pool0 = sdblib.memory_stats()
+    for lookup in lookups:
+        want_c, want_s, want_half = want[lookup]
         for _ in range(2):  # the array keeps the previous call's contents
             got_c, got_s = sdblib.join_aggregate_host_noalloc(w.points.x, w.points.y,
                                                               w.points.attr, cov, lookup)
-            assert np.array_equal(got_c, want_c[0]) and np.array_equal(got_s, want_s[0])
+            assert np.array_equal(got_c, want_c) and np.array_equal(got_s, want_s)
         # count only, on a different number of points
-        half = w.points.n // 2
-        want_c, _ = sdblib.join_aggregate_host(w.points.x[:half], w.points.y[:half], None,
-                                               [cov], lookup)
         got_c, _ = sdblib.join_aggregate_host_noalloc(w.points.x[:half], w.points.y[:half], None,
                                                       cov, lookup)
-        assert np.array_equal(got_c, want_c[0])
+        assert np.array_equal(got_c, want_half)
+    cuda.cuda.synchronize()
+    assert cuda.cuda.mem_get_info()[0] == free0
+    assert sdblib.memory_stats() == pool0
 
 
 def test_noalloc_rejects_too_many_polygons(cuda, sdblib):
