@@ -6,21 +6,21 @@ from 32 Gaussian clusters with sigma in [2^16, 2^19], 30% uniform, int32 fare
 attribute), the 263-zone jittered Voronoi tiling (20-400 vertices), and the
 eps sweep {2^12, 2^10, 2^8, 2^6}.
 
-One step = the coverings of the whole sweep built from the polygons (host
-arrays) in one pass, then for every eps the lookup structure (by default the
-cell table of 2^22 buckets; --lookup learned: the learned index with leaves
-for ~16 ranges each within 2^12..2^20) and the join of all points into
-per-polygon COUNT and SUM (device-resident points).
-The metric counts point-joins: points x eps levels per second.
+One timed step = the join of all points into per-polygon COUNT and SUM at
+every eps of the sweep (device-resident points), with the learned lookup: the
+cell table (2^22 buckets) as its first level and the learned index (2^16 FP32
+leaves) searching inside the table's mixed buckets.  The coverings, tables and
+indexes are built before the timed region, as a database builds an index; the
+metric counts point-joins: points x eps levels per second of join time.
 
-Besides the timed steps the script measures, outside the timed region, the
-join alone per eps for the binary-search, learned and cell-table lookups, the
-Bounded Raster Join (canvas blend + conservative rasterisation), result
-range estimation (boundary-flagged coverings and the range join), point-indexed
-aggregation (sorted points, prefix sums, binary search vs RadixSpline), the
-end-to-end rate through the host-buffer entry point (points copied from pinned
-host memory every step, results read back), and the CPU oracle on a bounded
-sample.
+Beside the timed steps the script measures, on the same coverings, the plain
+binary-search join, the learned index alone (2^16 and 2^12 leaves) and the cell
+table alone; the whole hot path per step (sweep covering build from the host
+polygons, table and index fits, joins); an oracle check of the timed coverings;
+the Bounded Raster Join; result range estimation; point-indexed aggregation;
+the end-to-end rate through the host-buffer entry point (covering build from
+host polygons, points copied from pinned host memory, results read back); the
+CPU oracle on a bounded sample; batched level-of-detail queries and serving.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -44,18 +44,15 @@ if ROOT not in sys.path:
 METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query latency"
 UNIT = "points/s"
 LEAF_BITS_RANGE = (12, 20)
-TABLE_BITS = 22  # cell table: 2^22 buckets (16 MB), fewer when 2F < 22
+LEAF_BITS = 16   # learned index of the timed join: 2^16 FP32 leaves
+TABLE_BITS = 22  # its first level, the cell table: 2^22 buckets (16 MB), fewer when 2F < 22
 # DRAM bytes (read + write) per point of one join_kernel launch at eps = 2^6 on
-# the default workload (2^20 leaves or 2^22 table buckets), from one ncu capture
-# of this script's step: profiles/join_kernel_<lookup>_eps64_*.txt
-JOIN_FINEST_TRAFFIC = {
-    "learned": {"eps": 64, "bits": 20, "bytes_per_point": 17.6935},
-    "table": {"eps": 64, "bits": 22, "bytes_per_point": 15.1170},
-}
-# DRAM bytes per launch (mean over the five 8-bit passes) of radix_scatter_kernel
-# in the step's record sort (117,378,603 packed records):
-# profiles/radix_scatter_kernel_sweep_zones263.txt
-SCATTER_TRAFFIC = {"records": 117_378_603, "bytes": 1.9478e9}
+# the default workload, from one ncu capture of that launch (20M-point case,
+# scaled per point): profiles/join_kernel_table_learned_eps64_zones263_mobility20M.txt
+JOIN_FINEST_TRAFFIC = {}
+# DRAM bytes per launch (mean over the passes) of radix_scatter_kernel in the
+# sweep's record sort: profiles/radix_scatter_kernel_sweep_zones263.txt
+SCATTER_TRAFFIC = {"records": 117_378_603, "passes": 5, "bytes": 1.9478e9}
 
 
 def leaf_bits_for(n_ranges: int) -> int:
@@ -74,13 +71,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps (no join-only, e2e, CPU, batch or serving legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--legs", default="join,raster,range,e2e,cpu,batch,pointindex,serve",
-                    help="extra legs: join (lookups alone), raster (Bounded Raster Join), range "
-                         "(result range estimation), e2e, cpu, batch, pointindex (range "
-                         "counting over sorted points), serve")
-    ap.add_argument("--lookup", default="table", choices=["table", "learned", "binary"],
-                    help="lookup of the timed step's joins")
-    ap.add_argument("--table-bits", type=int, default=TABLE_BITS)
+    ap.add_argument("--legs", default="oracle,raster,range,e2e,cpu,batch,pointindex,serve",
+                    help="extra legs: oracle (check of the timed coverings), raster (Bounded "
+                         "Raster Join), range (result range estimation), e2e, cpu, batch, "
+                         "pointindex (range counting over sorted points), serve")
     ap.add_argument("--pi-points", type=int, default=500_000_000)
     ap.add_argument("--lod-points", type=int, default=200_000_000)
     ap.add_argument("--lod-queries", type=int, default=4096)
@@ -251,7 +245,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": config_of(w, args.points, args.lookup, args.table_bits),
+        "config": config_of(w, args.points),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -259,15 +253,34 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def config_of(w, n_points, lookup="table", table_bits=TABLE_BITS):
-    c = {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64_{lookup}",
-         "points": n_points, "polygons": w.polygons.n, "grid_bits": 24, "eps": w.eps,
-         "lookup": lookup, "l2": "inputs larger than L2 (point arrays 12 B/pt)"}
-    if lookup == "learned":
-        c["leaf_bits"] = "ranges/16 within 2^12..2^20"
-    if lookup == "table":
-        c["table_bits"] = f"min({table_bits}, 2F)"
-    return c
+def config_of(w, n_points):
+    return {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64",
+            "points": n_points, "polygons": w.polygons.n, "grid_bits": 24, "eps": w.eps,
+            "lookup": "table_learned (cell table 2^%d buckets, learned index 2^%d leaves)"
+                      % (TABLE_BITS, LEAF_BITS),
+            "plain_lookup": "binary", "leaf_bits": LEAF_BITS, "table_bits": TABLE_BITS,
+            "l2": "inputs larger than L2 (point arrays 12 B/pt, 1.2 GB)"}
+
+
+def lookup_prep(sdb, c, lookup, stream, leaf_bits=None, table_bits=None):
+    """The lookup structures a join with `lookup` reads, built on covering c."""
+    if lookup in (sdb.LOOKUP_LEARNED, sdb.LOOKUP_TABLE_LEARNED):
+        sdb.covering_build_index(c, leaf_bits or LEAF_BITS, stream)
+    if lookup in (sdb.LOOKUP_TABLE, sdb.LOOKUP_TABLE_LEARNED):
+        sdb.covering_build_table(c, table_bits or TABLE_BITS, stream)
+
+
+def lookup_bytes(sdb, c, lookup):
+    """Bytes of the structure a lookup reads per launch besides the points:
+    the covering and its index for the searches over all ranges, the cell
+    table, its mixed buckets' windows and (table + learned) the index for the
+    table lookups (the ranges are then read only inside mixed buckets)."""
+    inf = c.info()
+    leaves = 32 * (1 << inf.index_leaf_bits) + 4 * 4097 if inf.index_leaf_bits else 0
+    if lookup in (sdb.LOOKUP_TABLE, sdb.LOOKUP_TABLE_LEARNED):
+        tab = 4 * (1 << inf.table_bits) + 8 * inf.table_mixed
+        return tab + (leaves if lookup == sdb.LOOKUP_TABLE_LEARNED else 0)
+    return inf.device_bytes
 
 
 def main():
@@ -276,6 +289,7 @@ def main():
         run_reference(args)
         return
     ws, rank, local = dist_init(args)
+    legs = set() if args.no_extras else set(args.legs.split(","))
     import torch
     torch.cuda.set_device(local)
     from paper_2010_12548_gb300 import build as B
@@ -285,73 +299,40 @@ def main():
     w = workload(args.points)
     N = w.points.n
     P = w.polygons.n
+    E = len(w.eps)
     dev = torch.device("cuda", local)
 
     def to_dev(a):
         return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
 
     x, y, a = to_dev(w.points.x), to_dev(w.points.y), to_dev(w.points.attr)
-    E = len(w.eps)
+    stream = torch.cuda.current_stream()
+    HEAD, PLAIN = sdb.LOOKUP_TABLE_LEARNED, sdb.LOOKUP_BINARY
+
+    # the coverings of the sweep (one pass) and the headline lookup's structures,
+    # built before the timed region: they are the join's resident inputs, like
+    # the points (their build is timed separately below)
+    covs = sdb.build_coverings(w.polygons, 24, w.eps, stream)
+    for c in covs:
+        lookup_prep(sdb, c, HEAD, stream)
     cnt = torch.zeros((E, P), dtype=torch.int64, device=dev)
     sm = torch.zeros((E, P), dtype=torch.int64, device=dev)
-    stream = torch.cuda.current_stream()
-    covs_live = []
-    cov_bytes = [0] * E
-    ncells = [0] * E
-    table_mixed = [0] * E
-    table_bytes_fine = [0]
-    fine_leaf_bits = [0]
-    lookup = {"table": sdb.LOOKUP_TABLE, "learned": sdb.LOOKUP_LEARNED,
-              "binary": sdb.LOOKUP_BINARY}[args.lookup]
 
-    def prepare(c):
-        """The lookup structure of the step's lookup on covering c."""
-        if lookup == sdb.LOOKUP_LEARNED:
-            sdb.covering_build_index(c, leaf_bits_for(c.info().n_ranges), stream)
-        elif lookup == sdb.LOOKUP_TABLE:
-            sdb.covering_build_table(c, args.table_bits, stream)
-
-    def step(events=None):
-        # the sweep's coverings in one pass, then per eps the index and the join
-        if events is not None:
-            events[0][0].record(stream)
-        covs = sdb.build_coverings(w.polygons, 24, w.eps, stream)
-        if events is not None:
-            events[0][1].record(stream)
+    def step(evs=None):
+        # one pass of the join over all points at every eps of the sweep
         for i, c in enumerate(covs):
-            if events is not None:
-                events[i][2].record(stream)
-            prepare(c)
-            inf = c.info()
-            ncells[i] = inf.n_cells
-            if i == E - 1:
-                fine_leaf_bits[0] = inf.index_leaf_bits
-            if i == E - 1 and lookup == sdb.LOOKUP_TABLE:
-                table_bytes_fine[0] = 4 * (1 << inf.table_bits) + 8 * inf.table_mixed
-            cov_bytes[i] = inf.device_bytes  # covering + index
-            table_mixed[i] = inf.table_mixed
-            if events is not None:
-                events[i][3].record(stream)
-        for i, c in enumerate(covs):
-            sdb.join_aggregate(x, y, a, c, lookup, cnt[i], sm[i], stream)
-            if events is not None:
-                events[i][4].record(stream)
-        covs_live.extend(covs)
-        while covs_live:
-            covs_live.pop().free()
+            sdb.join_aggregate(x, y, a, c, HEAD, cnt[i], sm[i], stream)
+            if evs is not None:
+                evs[i].record(stream)
 
-    for _ in range(args.warmup):
+    for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in w.eps]
-          for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in w.eps] for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = sdb.launch_count()
     barrier(ws)
     torch.cuda.synchronize()
-    # per-phase device time of the library's launches (CUDA events around each
-    # traced launch on this stream), recorded over the timed steps
-    sdb.trace_enable(True)
     with Clocks(local) as clk:
         t0.record(stream)
         for k in range(args.steps):
@@ -359,196 +340,206 @@ def main():
         t1.record(stream)
         torch.cuda.synchronize()
     barrier(ws)
-    trace = sdb.trace_read()
-    sdb.trace_enable(False)
     launches = sdb.launch_count() - launches0
     ms = t0.elapsed_time(t1) / args.steps
     ms = max_over_ranks(ws, ms)
     value = job_rate(ws, N * E, ms / 1e3)
-    sweep_build_ms = statistics.mean(ev[k][0][0].elapsed_time(ev[k][0][1])
-                                     for k in range(args.steps))
-    index_ms = [statistics.mean(ev[k][i][2].elapsed_time(ev[k][i][3]) for k in range(args.steps))
-                for i in range(E)]
-    # the joins follow the last index fit back to back
-    join_ms = [statistics.mean((ev[k][i - 1][4] if i else ev[k][E - 1][3]).elapsed_time(ev[k][i][4])
-                               for k in range(args.steps)) for i in range(E)]
+    # per-eps join time: the events recorded between the back-to-back joins
+    join_ms = []
+    for i in range(E):
+        d = [(ev[k][i - 1] if i else (ev[k - 1][E - 1] if k else t0)).elapsed_time(ev[k][i])
+             for k in range(args.steps)]
+        join_ms.append(statistics.mean(d))
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-           "config": config_of(w, N, args.lookup, args.table_bits), "clocks": clk.summary(),
-           "gpu_launches": launches}
-    res["trace_per_step"] = {k: {"launches": c / args.steps, "ms": t / args.steps}
-                             for k, (c, t) in trace.items()}
-    res["phases_ms"] = {"build_all_eps": sweep_build_ms,
-                        "index": dict(zip([str(e) for e in w.eps], index_ms)),
-                        "join_" + args.lookup: dict(zip([str(e) for e in w.eps], join_ms))}
-    if lookup == sdb.LOOKUP_TABLE:
-        res["table"] = {"bits": args.table_bits,
-                        "mixed_buckets": dict(zip([str(e) for e in w.eps], table_mixed))}
-
-    legs = set() if args.no_extras else set(args.legs.split(","))
-    # ---- join alone, learned vs binary search, per eps (not part of the step)
+           "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": config_of(w, N), "clocks": clk.summary(), "gpu_launches": launches}
+    res["join_ms"] = {"table_learned": dict(zip(map(str, w.eps), join_ms))}
+    infos = [c.info() for c in covs]
+    res["coverings"] = {str(e): {"ranges": i.n_ranges, "cells": i.n_cells,
+                                 "covering_bytes": i.device_bytes, "table_mixed": i.table_mixed}
+                        for e, i in zip(w.eps, infos)}
+    head_cnt, head_sm = cnt.clone(), sm.clone()
+    fallbacks = [sdb.covering_fallbacks(c, stream) for c in covs]
+    res["learned_fallbacks"] = sum(fallbacks)
     peak, peak_kind = peaks()
-    joins = {}
-    if "join" in legs:
-        reps = 5
-        for i, eps in enumerate(w.eps):
-            c = sdb.build_covering(w.polygons, 24, eps, stream)
-            inf = c.info()
-            row = {"ranges": inf.n_ranges, "cells": inf.n_cells, "covering_bytes": inf.device_bytes}
-            variants = [("binary", sdb.LOOKUP_BINARY, None)]
-            lb = leaf_bits_for(inf.n_ranges)
-            for bits in sorted({12, lb}):
-                variants.append((f"learned{bits}", sdb.LOOKUP_LEARNED, bits))
-            for tb in sorted({18, 20, TABLE_BITS, 24}):
-                variants.append((f"table{tb}", sdb.LOOKUP_TABLE, tb))
-            for name, lk, bits in variants:
-                if lk == sdb.LOOKUP_LEARNED:
-                    sdb.covering_build_index(c, bits, stream)
-                    mw, xw = sdb.covering_index_stats(c)
-                    row[name + "_window_mean"] = mw
-                    row[name + "_window_max"] = xw
-                if lk == sdb.LOOKUP_TABLE:
-                    sdb.covering_build_table(c, bits, stream)
-                    ti = c.info()
-                    row[name + "_buckets"] = 1 << ti.table_bits
-                    row[name + "_mixed"] = ti.table_mixed
-                sdb.join_aggregate(x, y, a, c, lk, cnt[i], sm[i], stream)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record(stream)
-                for _ in range(reps):
-                    sdb.join_aggregate(x, y, a, c, lk, cnt[i], sm[i], stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                jm = e0.elapsed_time(e1) / reps
-                row[name + "_ms"] = jm
-                row[name + "_pts_per_s"] = N / (jm / 1e3)
-                if lk == sdb.LOOKUP_LEARNED:
-                    row[name + "_fallbacks"] = sdb.covering_fallbacks(c, stream)
-            row["learned_ms"] = row[f"learned{lb}_ms"]
-            row["learned_pts_per_s"] = row[f"learned{lb}_pts_per_s"]
-            row["leaf_bits"] = lb
-            row["table_ms"] = row[f"table{TABLE_BITS}_ms"]
-            row["table_pts_per_s"] = row[f"table{TABLE_BITS}_pts_per_s"]
-            joins[str(eps)] = row
-            c.free()
-        res["join_only"] = joins
+
+    # ---- the same joins with the plain binary search, the learned index alone
+    # and the cell table alone, on the same coverings; results must agree
+    reps = max(3, min(args.steps, 10))
+    agree = True
+    lk_rows = {}
+    for name, lk, bits in (("binary", PLAIN, None), ("learned", sdb.LOOKUP_LEARNED, LEAF_BITS),
+                           ("learned12", sdb.LOOKUP_LEARNED, 12), ("table", sdb.LOOKUP_TABLE, None)):
+        per = {}
+        for i, c in enumerate(covs):
+            if bits:
+                sdb.covering_build_index(c, bits, stream)
+            per[str(w.eps[i])] = timed(torch, stream, lambda c=c, i=i: sdb.join_aggregate(
+                x, y, a, c, lk, cnt[i], sm[i], stream), reps)
+            agree &= bool(torch.equal(cnt[i], head_cnt[i]) and torch.equal(sm[i], head_sm[i]))
+            if lk == sdb.LOOKUP_LEARNED:
+                per[str(w.eps[i]) + "_fallbacks"] = sdb.covering_fallbacks(c, stream)
+                mw, xw = sdb.covering_index_stats(c)
+                per[str(w.eps[i]) + "_window_mean"] = mw
+        tot = sum(per[str(e)] for e in w.eps)
+        per["points_per_s"] = N * E / (tot / 1e3)
+        lk_rows[name] = per
+    for c in covs:  # back to the headline index
+        sdb.covering_build_index(c, LEAF_BITS, stream)
+    res["join_ms"].update(lk_rows)
+    res["plain_value"] = lk_rows["binary"]["points_per_s"]
+    res["learned_only_value"] = lk_rows["learned"]["points_per_s"]
+    res["table_value"] = lk_rows["table"]["points_per_s"]
+    res["lookups_agree"] = agree
+
+    # ---- the timed coverings against the CPU oracle: the first 1M points
+    # joined on the device with the headline lookup vs the definitional test
+    # (O2) on the host, every eps
+    if rank == 0 and "oracle" in legs:
+        from oracle import oracle as O
+        O.build()
+        m = min(N, 1_000_000)
+        pts = w.points.take(np.arange(m))
+        ok = True
+        for i, (e, c) in enumerate(zip(w.eps, covs)):
+            sdb.join_aggregate(x[:m], y[:m], a[:m], c, HEAD, cnt[i], sm[i], stream)
+            torch.cuda.synchronize()
+            oc, os_, _ = O.join_o2(w.polygons, e, pts, threads=os.cpu_count() or 1)
+            ok &= bool(np.array_equal(cnt[i].cpu().numpy().view(np.uint64), oc)
+                       and np.array_equal(sm[i].cpu().numpy(), os_))
+        res["matches_oracle"] = ok
+        res["oracle_check"] = f"first {m} points, all {E} eps, headline lookup vs O2"
+
+    # ---- the whole hot path per step: sweep build from host polygons, then per
+    # eps the cell table, the learned index and the join
+    def full_step():
+        cs = sdb.build_coverings(w.polygons, 24, w.eps, stream)
+        for i, c in enumerate(cs):
+            lookup_prep(sdb, c, HEAD, stream)
+            sdb.join_aggregate(x, y, a, c, HEAD, cnt[i], sm[i], stream)
+        return cs
+    for c in full_step():
+        c.free()
+    torch.cuda.synchronize()
+    sdb.trace_enable(True)
+    fs_reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    live = []
+    for _ in range(fs_reps):
+        live.extend(full_step())
+        while live:
+            live.pop().free()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    trace = sdb.trace_read()
+    sdb.trace_enable(False)
+    full_ms = e0.elapsed_time(e1) / fs_reps
+    res["full_step"] = {"ms": full_ms, "points_per_s": N * E / (full_ms / 1e3),
+                        "what": "sweep covering build (4 eps, one pass) + per eps cell table, "
+                                "learned index fit and table_learned join"}
+    res["trace_per_step"] = {k: {"launches": cc / fs_reps, "ms": t / fs_reps}
+                             for k, (cc, t) in trace.items()}
+
+    # ---- rooflines.  The headline join at the finest eps: the point stream
+    # (x, y, attr: 12 B/pt) plus one read of the structures the lookup uses
+    fine = str(w.eps[-1])
+    per_pt = 12 + lookup_bytes(sdb, covs[-1], HEAD) / N
+    achieved = N * per_pt / (join_ms[-1] / 1e3) / 1e9
+    T = JOIN_FINEST_TRAFFIC.get("table_learned")
+    traffic = (T["bytes_per_point"] * N
+               if T and w.eps[-1] == T["eps"] and T["leaf_bits"] == LEAF_BITS else None)
+    res["roofline"] = {"kernel": "join_kernel<table_learned> eps=%s" % fine, "bound": "hbm",
+                       "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                       "avg_launch_ms": join_ms[-1], "algorithmic_bytes_per_point": per_pt,
+                       "algorithmic_bytes_per_launch": per_pt * N}
+    # the record sort's scatter inside the full step (one launch per pass over
+    # all records): 8 B read + 8 B written per record and pass, 8 + 12 B in the
+    # last pass (keys and values apart)
+    recs = sum(i.n_cells for i in infos)
+    sc_n, sc_ms = trace.get("sort.scatter", (0, 0.0))
+    if sc_n:
+        passes = sc_n / fs_reps
+        sc_bytes = recs * (16 * (passes - 1) + 20) / passes
+        sc_avg = sc_ms / sc_n
+        ach = sc_bytes / (sc_avg / 1e3) / 1e9
+        T = SCATTER_TRAFFIC
+        res["roofline_radix_scatter"] = {
+            "kernel": "radix_scatter_kernel (%d records)" % recs, "bound": "hbm",
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind, "avg_launch_ms": sc_avg, "launches_per_step": passes,
+            "traffic": T["bytes"] if T and T["records"] == recs and T["passes"] == passes
+            else None, "algorithmic_bytes_per_launch": sc_bytes}
+    for c in covs:
+        c.free()
+    covs = []
+
     # ---- Bounded Raster Join (Sec. 5.2): canvas blend + conservative raster mask
     if "raster" in legs:
         rows = {}
-        P_ = w.polygons.n
-        rc, rs_ = (torch.zeros(P_, dtype=torch.int64, device=dev) for _ in range(2))
+        rc, rs_ = (torch.zeros(P, dtype=torch.int64, device=dev) for _ in range(2))
         for i, eps in enumerate(w.eps):
             reps = 3 if eps >= 1024 else 1
-            ms = timed(torch, stream, lambda: sdb.raster_join(w.polygons, 24, eps, x, y, a, rc, rs_,
-                                                              0, stream), reps)
+            rms = timed(torch, stream, lambda: sdb.raster_join(w.polygons, 24, eps, x, y, a, rc,
+                                                               rs_, 0, stream), reps)
             F = 24 - int(np.log2(eps)) + 1
-            rows[str(eps)] = {"raster_join_ms": ms, "canvas_pixels": 4 ** F,
+            rows[str(eps)] = {"raster_join_ms": rms, "canvas_pixels": 4 ** F,
                               "tiles": max(1, 4 ** (F - 13)),
-                              "covering_index_ms": index_ms[i],
                               "covering_join_ms": join_ms[i],
-                              "covering_sweep_build_ms_all_eps": sweep_build_ms,
-                              "matches_covering_join": bool(torch.equal(rc, cnt[i])
-                                                            and torch.equal(rs_, sm[i]))}
+                              "matches_covering_join": bool(torch.equal(rc, head_cnt[i])
+                                                            and torch.equal(rs_, head_sm[i]))}
         res["raster_join"] = rows
-    # ---- result range estimation (Sec. 6): flagged coverings and the range join
+    # ---- result range estimation (Sec. 6): flagged coverings, the range join,
+    # and the intervals computed by the library
     if "range" in legs:
-        reps = 5
         rng_rows = {}
-        P_ = w.polygons.n
-        bc, bs_, ba = (torch.zeros(P_, dtype=torch.int64, device=dev) for _ in range(3))
+        bc, bs_, ba = (torch.zeros(P, dtype=torch.int64, device=dev) for _ in range(3))
+        rc, rs_ = (torch.zeros(P, dtype=torch.int64, device=dev) for _ in range(2))
         for i, eps in enumerate(w.eps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
             e0.record(stream)
             c = sdb.build_covering(w.polygons, 24, eps, stream, flags=sdb.COVER_BOUNDARY_FLAGS)
             inf = c.info()
-            prepare(c)
+            lookup_prep(sdb, c, HEAD, stream)
             e1.record(stream)
             torch.cuda.synchronize()
             row = {"build_and_index_ms": e0.elapsed_time(e1), "ranges": inf.n_ranges,
-                   "plain_ranges": joins.get(str(eps), {}).get("ranges"), "lookup": args.lookup}
-            sdb.join_aggregate_range(x, y, a, c, lookup, cnt[i], bc, sm[i], bs_, ba, stream)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(reps):
-                sdb.join_aggregate_range(x, y, a, c, lookup, cnt[i], bc, sm[i], bs_, ba, stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            row["range_join_ms"] = e0.elapsed_time(e1) / reps
+                   "plain_ranges": infos[i].n_ranges, "lookup": "table_learned"}
+            row["range_join_ms"] = timed(torch, stream, lambda: sdb.join_aggregate_range(
+                x, y, a, c, HEAD, rc, bc, rs_, bs_, ba, stream), 5)
             row["plain_join_ms"] = join_ms[i]
-            c_np = cnt[i].cpu().numpy()
-            b_np = bc.cpu().numpy()
-            live = c_np > 0
+            lo_c, hi_c, lo_s, hi_s = sdb.result_bounds(rc, bc, rs_, bs_, ba, stream)
+            torch.cuda.synchronize()
+            row["matches_plain_join"] = bool(torch.equal(rc, head_cnt[i])
+                                             and torch.equal(rs_, head_sm[i]))
+            c_np, b_np = rc.cpu().numpy(), bc.cpu().numpy()
+            live_ = c_np > 0
             row["boundary_fraction"] = float(b_np.sum() / max(1, c_np.sum()))
-            row["mean_relative_count_interval"] = float((b_np[live] / c_np[live]).mean())
+            row["mean_relative_count_interval"] = float(
+                ((hi_c - lo_c).cpu().numpy()[live_] / c_np[live_]).mean())
             c.free()
             # the non-conservative covering (Sec. 2.2): build, join, and the share
             # of the boundary count it drops
             e0.record(stream)
             c = sdb.build_covering(w.polygons, 24, eps, stream, flags=sdb.COVER_NONCONSERVATIVE)
-            prepare(c)
+            lookup_prep(sdb, c, HEAD, stream)
             e1.record(stream)
             torch.cuda.synchronize()
             row["noncons_build_and_index_ms"] = e0.elapsed_time(e1)
             row["noncons_ranges"] = c.info().n_ranges
             row["noncons_join_ms"] = timed(torch, stream, lambda: sdb.join_aggregate(
-                x, y, a, c, lookup, bs_, ba, stream), 5)
+                x, y, a, c, HEAD, bs_, ba, stream), 5)
             nc_np = bs_.cpu().numpy()
             row["noncons_dropped_fraction_of_boundary"] = float(
                 (c_np - nc_np).sum() / max(1, b_np.sum()))
             rng_rows[str(eps)] = row
             c.free()
         res["range_estimation"] = rng_rows
-    # ---- rooflines from the traced launches of the timed steps (device time of
-    # each launch, CUDA events on the launching stream).
-    # The record sort's scatter, one launch per 8-bit pass over all records of
-    # the sweep: algorithmic bytes = records x (8 B read + 8 B written), and
-    # 8 B read + 12 B written in the last pass (keys and values apart)
-    recs = sum(ncells)
-    sc_n, sc_ms = trace.get("sort.scatter", (0, 0.0))
-    rooflines = {}
-    if sc_n:
-        passes = sc_n / args.steps
-        sc_bytes = recs * (16 * (passes - 1) + 20) / passes  # per launch
-        sc_avg = sc_ms / sc_n
-        ach = sc_bytes / (sc_avg / 1e3) / 1e9
-        T = SCATTER_TRAFFIC
-        rooflines["radix_scatter"] = {
-            "kernel": "radix_scatter_kernel (keys-only 8-bit pass, %d records)" % recs,
-            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "peak_kind": peak_kind, "avg_launch_ms": sc_avg, "launches_per_step": passes,
-            "traffic": T["bytes"] if T and T["records"] == recs else None,
-            "algorithmic_bytes_per_launch": sc_bytes, "algorithmic_bytes_per_record": sc_bytes / recs}
-    # the join of the finest eps: the point stream (x, y, attr) plus one read of
-    # the lookup structure: the covering and its learned index, or the cell
-    # table (the covering itself is read only inside mixed cells' windows)
-    fine = str(w.eps[-1])
-    if lookup == sdb.LOOKUP_TABLE:
-        per_pt = 12 + table_bytes_fine[0] / N
-    else:
-        per_pt = 12 + cov_bytes[-1] / N
-    achieved = N * per_pt / (join_ms[-1] / 1e3) / 1e9
-    T = JOIN_FINEST_TRAFFIC.get(args.lookup)
-    traffic = (T["bytes_per_point"] * N if (T and w.eps[-1] == T["eps"]
-                                            and T.get("bits") in (fine_leaf_bits[0], args.table_bits))
-               else None)
-    rooflines["join"] = {"kernel": "join_kernel<%s> eps=%s" % (args.lookup, fine), "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                         "avg_launch_ms": join_ms[-1],
-                         "algorithmic_bytes_per_point": per_pt,
-                         "algorithmic_bytes_per_launch": per_pt * N}
-    # the dominant kernel of the step (largest traced device time) carries the
-    # roofline; the join's is reported beside it
-    jn, jt = trace.get("join", (0, 0.0))
-    dom = "radix_scatter" if "radix_scatter" in rooflines and sc_ms >= jt else "join"
-    res["roofline"] = rooflines[dom]
-    res["roofline_join"] = rooflines["join"]
-    if "radix_scatter" in rooflines:
-        res["roofline_radix_scatter"] = rooflines["radix_scatter"]
-    # ---- end to end through the host-buffer entry point
+    # ---- end to end through the C ABI from host buffers: the sweep's coverings
+    # from the host polygons, the table and the learned index, and the
+    # host-buffer join (points copied from pinned host memory inside the call,
+    # results copied back)
     if "e2e" in legs:
         hx = torch.from_numpy(w.points.x.view(np.int32)).pin_memory()
         hy = torch.from_numpy(w.points.y.view(np.int32)).pin_memory()
@@ -557,12 +548,12 @@ def main():
         hs = torch.zeros((E, P), dtype=torch.int64).pin_memory()
 
         def e2e_step():
-            covs = sdb.build_coverings(w.polygons, 24, w.eps, stream)
-            for c in covs:
-                prepare(c)
-            sdb.join_aggregate_host_ptrs(hx.data_ptr(), hy.data_ptr(), ha.data_ptr(), N, covs,
-                                         lookup, hc.data_ptr(), hs.data_ptr(), stream)
-            for c in covs:
+            cs = sdb.build_coverings(w.polygons, 24, w.eps, stream)
+            for c in cs:
+                lookup_prep(sdb, c, HEAD, stream)
+            sdb.join_aggregate_host_ptrs(hx.data_ptr(), hy.data_ptr(), ha.data_ptr(), N, cs,
+                                         HEAD, hc.data_ptr(), hs.data_ptr(), stream)
+            for c in cs:
                 c.free()
         for _ in range(max(1, args.warmup)):
             e2e_step()
@@ -574,17 +565,23 @@ def main():
         e2e_s = (time.perf_counter() - tt) / args.steps
         e2e_s = max_over_ranks(ws, e2e_s)
         res["e2e"] = {"value": job_rate(ws, N * E, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * 12,
-                      "d2h_bytes_per_step": E * P * 16, "ms_per_step": e2e_s * 1e3}
-        # the host join must agree with the device join
-        res["e2e"]["matches_device"] = bool(np.array_equal(hc.numpy(), cnt.cpu().numpy()) and
-                                            np.array_equal(hs.numpy(), sm.cpu().numpy()))
+                      "d2h_bytes_per_step": E * P * 16, "ms_per_step": e2e_s * 1e3,
+                      "what": "host polygons -> sweep coverings, cell tables, learned indexes "
+                              "-> host-buffer join (H2D of the points inside) -> host results"}
+        res["e2e"]["matches_device"] = bool(np.array_equal(hc.numpy(), head_cnt.cpu().numpy()) and
+                                            np.array_equal(hs.numpy(), head_sm.cpu().numpy()))
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and ws == 1 and "cpu" in legs:
         threads = os.cpu_count() or 1
         rate, sample, secs = cpu_oracle_rate(w, args.cpu_seconds, threads)
+        rate1, sample1, secs1 = cpu_oracle_rate(w, args.cpu_seconds / 3, 1)
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": f"first {sample} of the {N} points, all {E} eps "
-                                         f"levels, definitional per-point test ({secs:.1f} s)"}
+                                         f"levels, definitional per-point test ({secs:.1f} s)",
+                               "single_thread": {"value": rate1, "cores": 1,
+                                                 "sample": f"first {sample1} points, all {E} "
+                                                           f"eps ({secs1:.1f} s)"},
+                               "cpu": cpu_model()}
     # ---- batched level-of-detail queries and serving (resident points)
     del x, y, a
     torch.cuda.empty_cache()
@@ -600,6 +597,18 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def timed(torch, stream, fn, reps):

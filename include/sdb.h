@@ -55,13 +55,17 @@ typedef enum sdb_status {
 } sdb_status;
 
 /* Covering lookups: binary search over the range starts, the learned index
- * (sdb_covering_build_index), the cell table (sdb_covering_build_table); and,
- * for resident point sets only, the RadixSpline over the sorted point keys. */
+ * (sdb_covering_build_index), the cell table (sdb_covering_build_table), the
+ * cell table as the first level with the learned index searching inside the
+ * table's mixed buckets (needs both; the layout of the paper's RadixSpline, a
+ * radix table over the key's top bits in front of the model); and, for
+ * resident point sets only, the RadixSpline over the sorted point keys. */
 enum {
   SDB_LOOKUP_BINARY = 0,
   SDB_LOOKUP_LEARNED = 1,
   SDB_LOOKUP_RADIX_SPLINE = 2,
-  SDB_LOOKUP_TABLE = 3
+  SDB_LOOKUP_TABLE = 3,
+  SDB_LOOKUP_TABLE_LEARNED = 4
 };
 
 /* Polygons in host memory, read during the call only.  One simple ring per
@@ -217,13 +221,16 @@ sdb_status sdb_covering_build_table(sdb_covering *cov, uint32_t table_bits, void
  * stored error window, verified, with binary search as the fallback; requires
  * sdb_covering_build_index; SDB_LOOKUP_TABLE: the cell table's bucket, then a
  * binary search of the bucket's window if it holds several ranges; requires
- * sdb_covering_build_table), and for every polygon j on r's list
+ * sdb_covering_build_table; SDB_LOOKUP_TABLE_LEARNED: the cell table's bucket,
+ * and in a bucket of several ranges the learned index's error window cut to the
+ * bucket's window, searched and verified, with the bucket's window as the
+ * counted fallback; requires both), and for every polygon j on r's list
  * d_count[j] += 1 and d_sum[j] += d_attr[i].  All three lookups give
  * identical results.  d_count and d_sum (P entries each) are zeroed by the call.
  * d_x, d_y, d_attr: n device values (SoA).  d_attr and d_sum may be NULL
  * (COUNT only).  n = 0 just zeroes the outputs.  Asynchronous.
  * SDB_EINVAL: null cov/d_count, n > 0 with null d_x/d_y, n > 0 with d_sum but no
- * d_attr, learned lookup without an index, table lookup without a table. */
+ * d_attr, a lookup whose index or table was not built. */
 sdb_status sdb_join_aggregate(const uint32_t *d_x, const uint32_t *d_y, const int32_t *d_attr,
                               uint64_t n, const sdb_covering *cov, int lookup,
                               uint64_t *d_count, int64_t *d_sum, void *cuda_stream);
@@ -537,8 +544,8 @@ sdb_status sdb_server_get_stats(sdb_server *srv, sdb_server_stats *stats);
 void sdb_server_destroy(sdb_server *srv);
 
 /* Number of learned-index lookups of the covering's most recent learned join
- * whose bounded search missed and fell back to binary search.  Synchronises
- * cuda_stream. */
+ * (SDB_LOOKUP_LEARNED or SDB_LOOKUP_TABLE_LEARNED) whose bounded search missed
+ * and fell back to binary search.  Synchronises cuda_stream. */
 sdb_status sdb_covering_fallbacks(const sdb_covering *cov, void *cuda_stream, uint64_t *out);
 
 /* Learned-index window sizes (errlo + errhi + 1 per leaf): mean weighted by the

@@ -180,12 +180,18 @@ static sdb_status check_device(const sdb_covering* cov) {
 }
 
 sdb_status check_lookup(const sdb_covering* cov, int lookup) {
-  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED && lookup != SDB_LOOKUP_TABLE) {
+  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED && lookup != SDB_LOOKUP_TABLE &&
+      lookup != SDB_LOOKUP_TABLE_LEARNED) {
     set_error("unknown lookup %d", lookup);
     return SDB_EINVAL;
   }
   if (lookup == SDB_LOOKUP_LEARNED && !cov->leaves) {
     set_error("learned lookup requested but the covering has no index");
+    return SDB_EINVAL;
+  }
+  if (lookup == SDB_LOOKUP_TABLE_LEARNED && (!cov->tab || !cov->leaves)) {
+    set_error("table + learned lookup requested but the covering lacks %s",
+              !cov->tab ? "a cell table" : "a learned index");
     return SDB_EINVAL;
   }
   if (lookup == SDB_LOOKUP_TABLE && !cov->tab) {
@@ -663,7 +669,7 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
   if (h_sum) SDB_TRY(sc.get(&d_sum, outn));
   SDB_TRY_CUDA(cudaMemsetAsync(d_cnt, 0, outn * 8, s));
   if (d_sum) SDB_TRY_CUDA(cudaMemsetAsync(d_sum, 0, outn * 8, s));
-  if (lookup == SDB_LOOKUP_LEARNED)
+  if (lookup == SDB_LOOKUP_LEARNED || lookup == SDB_LOOKUP_TABLE_LEARNED)
     for (uint32_t c = 0; c < n_covs; ++c)
       SDB_TRY_CUDA(cudaMemsetAsync(covs[c]->fallbacks, 0, sizeof(unsigned long long), s));
   const uint64_t CH = 1ull << 24;  // points per chunk

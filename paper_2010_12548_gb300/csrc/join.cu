@@ -23,6 +23,10 @@
 //    in a per-warp shared-memory queue and, 32 at a time (all lanes busy),
 //    compute their finest cell id and binary search the cell's window of
 //    range starts;
+//  * cell table + learned index: as the cell table, but a held-back point's
+//    search runs over the learned model's error window cut to the cell's
+//    window (root knots in shared memory, one 32-byte leaf load), verified,
+//    with the cell's whole window as the counted fallback;
 //  * aggregation: per point, its count and (split 16/16-bit, exact) attribute
 //    sum are added with shared-memory atomics to per-block accumulators
 //    (P <= SMEM_POLYS, flushed into the 64-bit outputs every few tiles), or
@@ -366,13 +370,62 @@ struct QEnt {
 };
 
 // the range of a point in mixed bucket m: its finest cell id, then a binary
-// search of the bucket's window of range starts
-template <bool SMEM, bool SUM, bool RANGE>
+// search of the bucket's window of range starts (w.x = the range holding the
+// bucket's first id, w.y = the range holding its last, so start[w.x] <= h <
+// start[w.y + 1]).  With the learned index (LOOKUP == SDB_LOOKUP_TABLE_LEARNED)
+// the search runs over the model's error window cut to the bucket's window;
+// an end of the result no probe has proven is read, and a result that does not
+// bracket h falls back to the bucket's whole window (counted).
+template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
 __device__ __forceinline__ void resolve_mixed(const QEnt& E, const uint32_t* s_tab,
-                                              const Acc& acc, const JoinArgs& A) {
+                                              const float* s_knots, const Acc& acc,
+                                              const JoinArgs& A) {
   const uint64_t h = hilbert3_encode(E.x >> A.k, E.y >> A.k, A.nsteps, A.st0, s_tab);
   const uint2 w = __ldg(A.win + E.m);
   uint32_t lo = w.x, len = w.y - w.x + 1;
+  if constexpr (LOOKUP == SDB_LOOKUP_TABLE_LEARNED) {
+    const uint32_t l = root_leaf(s_knots, A.wshift, A.inv_w, A.nleaves, h);
+    uint64_t w0, w1, w2, w3;
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+        : "l"(A.leaves + l));
+    LeafRec lr;
+    lr.base = w0;
+    lr.a = __uint_as_float((uint32_t)w1);
+    lr.b = __uint_as_float((uint32_t)(w1 >> 32));
+    lr.first = (uint32_t)w2;
+    lr.last = (uint32_t)(w2 >> 32);
+    lr.errlo = (int32_t)(uint32_t)w3;
+    lr.errhi = (int32_t)(uint32_t)(w3 >> 32);
+    const int64_t pr = leaf_predict(lr, h);
+    int64_t a = pr - lr.errlo, b = pr + lr.errhi;
+    a = a > (int64_t)w.x ? a : (int64_t)w.x;
+    b = b < (int64_t)w.y ? b : (int64_t)w.y;
+    if (b < a) b = a;  // an empty cut (a model miss): one candidate, then the check
+    lo = (uint32_t)a;
+    len = (uint32_t)(b - a + 1);
+    // bit 0: start[lo] <= h is proven, bit 1: start[lo + 1] > h is proven
+    uint32_t known = (lo == w.x ? 1u : 0u) | ((uint32_t)b == w.y ? 2u : 0u);
+    while (len > 1) {
+      const uint32_t half = len >> 1;
+      if (__ldg(A.start + lo + half) <= h) {
+        lo += half;
+        known |= 1u;
+      } else {
+        known |= 2u;
+      }
+      len -= half;
+    }
+    const bool ok0 = (known & 1u) || __ldg(A.start + lo) <= h;
+    const bool ok1 = (known & 2u) || h < __ldg(A.start + lo + 1);
+    if (ok0 && ok1) {
+      add_pay<SMEM, SUM, RANGE>(__ldg(A.pay + lo), E.a, acc, A);
+      return;
+    }
+    atomicAdd(A.fallbacks, 1ull);
+    lo = w.x;
+    len = w.y - w.x + 1;
+  }
   while (len > 1) {
     const uint32_t half = len >> 1;
     if (__ldg(A.start + lo + half) <= h) lo += half;
@@ -381,11 +434,15 @@ __device__ __forceinline__ void resolve_mixed(const QEnt& E, const uint32_t* s_t
   add_pay<SMEM, SUM, RANGE>(__ldg(A.pay + lo), E.a, acc, A);
 }
 
-// shared-memory bytes of the lookup's staging area (8-byte multiple)
+// shared-memory bytes of the lookup's staging area (8-byte multiple): the
+// binary search's sample, the learned index's root knots, or the cell table's
+// per-warp queues (followed by the root knots for the table + learned lookup)
+constexpr size_t QUEUE_BYTES = (size_t)(THREADS / 32) * QCAP * sizeof(QEnt);
 __host__ __device__ inline size_t stage_bytes(int lookup, const JoinArgs& A) {
+  const size_t knots = ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
   if (lookup == SDB_LOOKUP_BINARY) return (size_t)A.sample_n * 8;
-  if (lookup == SDB_LOOKUP_LEARNED) return ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
-  return (size_t)(THREADS / 32) * QCAP * sizeof(QEnt);
+  if (lookup == SDB_LOOKUP_LEARNED) return knots;
+  return QUEUE_BYTES + (lookup == SDB_LOOKUP_TABLE_LEARNED ? knots : 0);
 }
 
 template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
@@ -395,8 +452,10 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   // range starts, the learned index's root knots, or the cell-table lookup's
   // per-warp queues), then the accumulators
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  constexpr bool TABLE = LOOKUP == SDB_LOOKUP_TABLE || LOOKUP == SDB_LOOKUP_TABLE_LEARNED;
   uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem + HILBERT3_SMEM_BYTES);
-  float* s_knots = reinterpret_cast<float*>(smem + HILBERT3_SMEM_BYTES);
+  float* s_knots = reinterpret_cast<float*>(
+      smem + HILBERT3_SMEM_BYTES + (LOOKUP == SDB_LOOKUP_TABLE_LEARNED ? QUEUE_BYTES : 0));
   QEnt* s_q = reinterpret_cast<QEnt*>(smem + HILBERT3_SMEM_BYTES) + (threadIdx.x >> 5) * QCAP;
   const size_t off = HILBERT3_SMEM_BYTES + stage_bytes(LOOKUP, A);
   const Acc acc = acc_at<SUM, RANGE>(smem + off, SMEM ? A.P : 0);
@@ -404,7 +463,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   hilbert3_fill(s_tab);
   if constexpr (LOOKUP == SDB_LOOKUP_BINARY)
     for (uint32_t i = threadIdx.x; i < A.sample_n; i += THREADS) s_sample[i] = A.sample[i];
-  if constexpr (LOOKUP == SDB_LOOKUP_LEARNED)
+  if constexpr (LOOKUP == SDB_LOOKUP_LEARNED || LOOKUP == SDB_LOOKUP_TABLE_LEARNED)
     for (uint32_t i = threadIdx.x; i < A.nknots; i += THREADS) s_knots[i] = A.knots[i];
   if (SMEM) acc_zero<SUM, RANGE>(acc, A.P);
   __syncthreads();
@@ -449,7 +508,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) ok[q] = ok[q] && !((xs[q] | ys[q]) & gmask);
-    if constexpr (LOOKUP == SDB_LOOKUP_TABLE) {
+    if constexpr (TABLE) {
       // the entry of the point's cell at the table's level, found from the
       // coordinates (row-major table); only points in mixed cells need their
       // finest cell id
@@ -476,7 +535,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
           qn -= 32;
           const QEnt E = s_q[qn + lane];
           __syncwarp();
-          resolve_mixed<SMEM, SUM, RANGE>(E, s_tab, acc, A);
+          resolve_mixed<LOOKUP, SMEM, SUM, RANGE>(E, s_tab, s_knots, acc, A);
         }
       }
     } else {
@@ -502,9 +561,9 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
       __syncthreads();
     }
   }
-  if constexpr (LOOKUP == SDB_LOOKUP_TABLE) {  // the rest of the queue
+  if constexpr (TABLE) {  // the rest of the queue
     __syncwarp();
-    if (lane < qn) resolve_mixed<SMEM, SUM, RANGE>(s_q[lane], s_tab, acc, A);
+    if (lane < qn) resolve_mixed<LOOKUP, SMEM, SUM, RANGE>(s_q[lane], s_tab, s_knots, acc, A);
   }
   if (SMEM) {
     __syncthreads();
@@ -668,6 +727,11 @@ sdb_status launch_pick(const JoinArgs& A, int lookup, bool has_sum, cudaStream_t
       return has_sum ? launch_t<3, true, true, RANGE>(A, s) : launch_t<3, true, false, RANGE>(A, s);
     return has_sum ? launch_t<3, false, true, RANGE>(A, s) : launch_t<3, false, false, RANGE>(A, s);
   }
+  if (lookup == SDB_LOOKUP_TABLE_LEARNED) {
+    if (smem)
+      return has_sum ? launch_t<4, true, true, RANGE>(A, s) : launch_t<4, true, false, RANGE>(A, s);
+    return has_sum ? launch_t<4, false, true, RANGE>(A, s) : launch_t<4, false, false, RANGE>(A, s);
+  }
   if (smem)
     return has_sum ? launch_t<1, true, true, RANGE>(A, s) : launch_t<1, true, false, RANGE>(A, s);
   return has_sum ? launch_t<1, false, true, RANGE>(A, s) : launch_t<1, false, false, RANGE>(A, s);
@@ -685,7 +749,7 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
     if (bcount) SDB_TRY_CUDA(cudaMemsetAsync(bcount, 0, (size_t)cov->P * 8, s));
     if (bsum) SDB_TRY_CUDA(cudaMemsetAsync(bsum, 0, (size_t)cov->P * 8, s));
     if (babs) SDB_TRY_CUDA(cudaMemsetAsync(babs, 0, (size_t)cov->P * 8, s));
-    if (lookup == SDB_LOOKUP_LEARNED)
+    if (lookup == SDB_LOOKUP_LEARNED || lookup == SDB_LOOKUP_TABLE_LEARNED)
       SDB_TRY_CUDA(cudaMemsetAsync(cov->fallbacks, 0, sizeof(unsigned long long), s));
   }
   if (n == 0) return SDB_OK;

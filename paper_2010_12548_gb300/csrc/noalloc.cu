@@ -103,7 +103,7 @@ extern "C" sdb_status sdb_join_aggregate_host_noalloc(const uint32_t* h_x, const
   // the array keeps the previous call's contents: clear the accumulators
   SDB_TRY_CUDA(cudaMemsetAsync(dcnt, 0, P * 8, s));
   SDB_TRY_CUDA(cudaMemsetAsync(dsum, 0, P * 8, s));
-  if (lookup == SDB_LOOKUP_LEARNED)
+  if (lookup == SDB_LOOKUP_LEARNED || lookup == SDB_LOOKUP_TABLE_LEARNED)
     SDB_TRY_CUDA(cudaMemsetAsync(cov->fallbacks, 0, sizeof(unsigned long long), s));
   for (uint64_t a0 = 0; a0 < n; a0 += CHUNK) {
     const uint64_t m = (n - a0 < CHUNK) ? n - a0 : CHUNK;

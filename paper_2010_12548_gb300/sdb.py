@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsdb.so")
 
 SDB_OK, SDB_EINVAL, SDB_ENOMEM, SDB_ECUDA, SDB_ETIMEOUT, SDB_EBUSY = range(6)
-LOOKUP_BINARY, LOOKUP_LEARNED, LOOKUP_RADIX_SPLINE, LOOKUP_TABLE = 0, 1, 2, 3
+LOOKUP_BINARY, LOOKUP_LEARNED, LOOKUP_RADIX_SPLINE, LOOKUP_TABLE, LOOKUP_TABLE_LEARNED = 0, 1, 2, 3, 4
 COVER_BOUNDARY_FLAGS, COVER_NONCONSERVATIVE = 1, 2
 
 
