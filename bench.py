@@ -64,8 +64,8 @@ def leaf_bits_for(n_ranges: int) -> int:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--points", type=int, default=100_000_000)
     ap.add_argument("--no-extras", action="store_true",
@@ -124,23 +124,68 @@ def job_rate(ws, units_per_rank, seconds):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and throttle reasons sampled during the timed region: read-only
+    NVML queries every 2 ms from a thread (the timed region can be shorter than
+    nvidia-smi's sampling interval), else nvidia-smi sampling every 50 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvml.h)
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, pci_bus_id: str | None = None):
         self.idx = gpu_index
+        self.bus = pci_bus_id
         self.rows = []
         self.proc = None
         self.t = None
+        self.nv = None
+        self.stop = threading.Event()
+        self.source = None
+
+    def _nvml(self):
+        import ctypes as C
+        nv = C.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = C.c_void_p()
+        if self.bus and nv.nvmlDeviceGetHandleByPciBusId_v2(self.bus.encode(), C.byref(h)) == 0:
+            pass
+        elif nv.nvmlDeviceGetHandleByIndex_v2(self.idx, C.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        mx = C.c_uint()
+        nv.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx))  # NVML_CLOCK_SM
+        return nv, h, mx.value
+
+    def _poll(self, nv, h, mx):
+        import ctypes as C
+        clk, rs = C.c_uint(), C.c_ulonglong()
+        while not self.stop.is_set():
+            nv.nvmlDeviceGetClockInfo(h, 1, C.byref(clk))
+            nv.nvmlDeviceGetCurrentClocksEventReasons(h, C.byref(rs))
+            self.rows.append((float(clk.value), float(mx), int(rs.value)))
+            time.sleep(0.002)
 
     def __enter__(self):
+        try:
+            nv, h, mx = self._nvml()
+            self.source = "nvml"
+            self.t = threading.Thread(target=self._poll, args=(nv, h, mx), daemon=True)
+            self.t.start()
+            t_end = time.time() + 1.0
+            while not self.rows and time.time() < t_end:
+                time.sleep(0.001)
+            self.rows.clear()
+            return self
+        except Exception:
+            self.source = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader",
                  "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
             # the sampler takes a moment to start: wait for its first sample, then
@@ -158,32 +203,42 @@ class Clocks:
             self.rows.append([c.strip() for c in line.split(",")])
 
     def __exit__(self, *a):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.t:
             self.t.join(timeout=2)
 
     def summary(self):
+        rows = list(self.rows)
+        if self.source == "nvml":
+            sm = [r[0] for r in rows if r[0] > 0]
+            reasons = sorted({n for r in rows for bit, n in self.REASONS.items() if r[2] & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None,
+                    "sm_max_mhz": max((r[1] for r in rows), default=None), "reasons": reasons,
+                    "samples": len(rows), "source": "nvml, 2 ms"}
+
         def num(s):
             try:
                 return float(s.split()[0])
             except Exception:
                 return None
-        sm = [num(r[1]) for r in self.rows if len(r) >= 9 and num(r[1])]
-        mx = [num(r[2]) for r in self.rows if len(r) >= 9 and num(r[2])]
+        sm = [num(r[1]) for r in rows if len(r) >= 9 and num(r[1])]
+        mx = [num(r[2]) for r in rows if len(r) >= 9 and num(r[2])]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for r in rows:
             if len(r) >= 9:
                 for n, v in zip(names, r[5:9]):
                     if v.strip().lower() == "active":
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(self.rows)}
+                "samples": len(rows), "source": "nvidia-smi, 50 ms"}
 
 
 def peaks():
@@ -333,7 +388,12 @@ def main():
     launches0 = sdb.launch_count()
     barrier(ws)
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
+    try:
+        p = torch.cuda.get_device_properties(local)
+        bus = "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        bus = None
+    with Clocks(local, bus) as clk:
         t0.record(stream)
         for k in range(args.steps):
             step(ev[k])

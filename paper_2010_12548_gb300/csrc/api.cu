@@ -137,6 +137,19 @@ int num_sms() {
   return g_sms[dev];
 }
 
+int carveout_pct(size_t bytes) {
+  int dev = 0, max_smem = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      max_smem <= 0) {
+    cudaGetLastError();
+    return -1;  // no preference
+  }
+  const size_t pct = (bytes * 100 + (size_t)max_smem - 1) / (size_t)max_smem;
+  return pct > 100 ? 100 : (int)pct;
+}
+
 static sdb_status finest(uint32_t B, uint64_t eps, uint32_t* k_out) {
   if (B < 1 || B > 30) {
     set_error("grid_bits %u outside 1..30", B);

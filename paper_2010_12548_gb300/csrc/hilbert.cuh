@@ -10,7 +10,8 @@
 // One table entry maps (sw, cm, 3 bits of x, 3 bits of y) to the 6 id bits of
 // those levels and the orientation after them, in one byte (256 entries).  In
 // shared memory the 64 words of the table are stored once per bank, word w of
-// lane l at [w * 32 + l], so a warp's 32 lookups never conflict (8 KB).
+// lane l at [w * 32 + l], so a warp's 32 lookups never conflict (8 KB); kernels
+// in which few points encode keep one unreplicated copy (256 bytes).
 // A level count F that is not a multiple of 3 is padded with zero levels on
 // top; each zero level transposes, so the walk starts with sw set when the
 // padding is odd and reaches the real top level in the plain orientation.
@@ -68,6 +69,37 @@ __device__ __forceinline__ uint32_t hilbert3_step(uint32_t& xs, uint32_t& ys, ui
   const uint32_t e = __byte_perm(row[(idx >> 2) << 5], 0u, 0x4440u | (idx & 3u));
   st = e & 0xc0u;
   return e & 63u;
+}
+
+// The same table once, unreplicated (64 words, 256 bytes): for kernels in which
+// only a few points encode their cell id, so bank conflicts are rare and the
+// shared memory is better left to the L1 cache.
+constexpr int HILBERT3_COMPACT_BYTES = HILBERT3_WORDS * 4;
+
+__device__ __forceinline__ void hilbert3_fill_compact(uint32_t* tab) {
+  for (int w = threadIdx.x; w < HILBERT3_WORDS; w += blockDim.x)
+    tab[w] = hilbert3_entry(4 * w) | (hilbert3_entry(4 * w + 1) << 8) |
+             (hilbert3_entry(4 * w + 2) << 16) | (hilbert3_entry(4 * w + 3) << 24);
+}
+
+// id of cell (cx, cy) at the level the parameters were made for (cx, cy < 2^F),
+// from the unreplicated table
+__device__ __forceinline__ uint64_t hilbert3_encode_compact(uint32_t cx, uint32_t cy,
+                                                            uint32_t nsteps, uint32_t st0,
+                                                            const uint32_t* tab) {
+  if (nsteps == 0) return 0;
+  const uint32_t sh = 32 - 3 * nsteps;
+  uint32_t xs = cx << sh, ys = cy << sh, st = st0 << 6;
+  uint64_t h = 0;
+  for (uint32_t s = 0; s < nsteps; ++s) {
+    const uint32_t idx = st | ((xs >> 26) & 0x38u) | (ys >> 29);
+    xs <<= 3;
+    ys <<= 3;
+    const uint32_t e = __byte_perm(tab[idx >> 2], 0u, 0x4440u | (idx & 3u));
+    st = e & 0xc0u;
+    h = (h << 6) | (e & 63u);
+  }
+  return h;
 }
 
 // id of cell (cx, cy) at the level the parameters were made for (cx, cy < 2^F)

@@ -378,13 +378,13 @@ struct QEnt {
 // bracket h falls back to the bucket's whole window (counted).
 template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
 __device__ __forceinline__ void resolve_mixed(const QEnt& E, const uint32_t* s_tab,
-                                              const float* s_knots, const Acc& acc,
-                                              const JoinArgs& A) {
-  const uint64_t h = hilbert3_encode(E.x >> A.k, E.y >> A.k, A.nsteps, A.st0, s_tab);
+                                              const Acc& acc, const JoinArgs& A) {
+  const uint64_t h = hilbert3_encode_compact(E.x >> A.k, E.y >> A.k, A.nsteps, A.st0, s_tab);
   const uint2 w = __ldg(A.win + E.m);
   uint32_t lo = w.x, len = w.y - w.x + 1;
   if constexpr (LOOKUP == SDB_LOOKUP_TABLE_LEARNED) {
-    const uint32_t l = root_leaf(s_knots, A.wshift, A.inv_w, A.nleaves, h);
+    // the root knots through the L1 cache: only points in mixed buckets read them
+    const uint32_t l = root_leaf(A.knots, A.wshift, A.inv_w, A.nleaves, h);
     uint64_t w0, w1, w2, w3;
     asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
         : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
@@ -434,15 +434,24 @@ __device__ __forceinline__ void resolve_mixed(const QEnt& E, const uint32_t* s_t
   add_pay<SMEM, SUM, RANGE>(__ldg(A.pay + lo), E.a, acc, A);
 }
 
+// shared-memory bytes of the cell-id table: replicated per bank where every
+// point encodes, one unreplicated copy for the table lookups (only points in
+// mixed buckets encode there, and shared memory left unused stays L1 cache,
+// which holds the lines of the table gathers in flight)
+__host__ __device__ constexpr size_t hilbert_bytes(int lookup) {
+  return (lookup == SDB_LOOKUP_TABLE || lookup == SDB_LOOKUP_TABLE_LEARNED)
+             ? (size_t)HILBERT3_COMPACT_BYTES
+             : (size_t)HILBERT3_SMEM_BYTES;
+}
+
 // shared-memory bytes of the lookup's staging area (8-byte multiple): the
 // binary search's sample, the learned index's root knots, or the cell table's
-// per-warp queues (followed by the root knots for the table + learned lookup)
+// per-warp queues
 constexpr size_t QUEUE_BYTES = (size_t)(THREADS / 32) * QCAP * sizeof(QEnt);
 __host__ __device__ inline size_t stage_bytes(int lookup, const JoinArgs& A) {
-  const size_t knots = ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
   if (lookup == SDB_LOOKUP_BINARY) return (size_t)A.sample_n * 8;
-  if (lookup == SDB_LOOKUP_LEARNED) return knots;
-  return QUEUE_BYTES + (lookup == SDB_LOOKUP_TABLE_LEARNED ? knots : 0);
+  if (lookup == SDB_LOOKUP_LEARNED) return ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
+  return QUEUE_BYTES;
 }
 
 template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
@@ -453,17 +462,20 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   // per-warp queues), then the accumulators
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
   constexpr bool TABLE = LOOKUP == SDB_LOOKUP_TABLE || LOOKUP == SDB_LOOKUP_TABLE_LEARNED;
-  uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem + HILBERT3_SMEM_BYTES);
-  float* s_knots = reinterpret_cast<float*>(
-      smem + HILBERT3_SMEM_BYTES + (LOOKUP == SDB_LOOKUP_TABLE_LEARNED ? QUEUE_BYTES : 0));
-  QEnt* s_q = reinterpret_cast<QEnt*>(smem + HILBERT3_SMEM_BYTES) + (threadIdx.x >> 5) * QCAP;
-  const size_t off = HILBERT3_SMEM_BYTES + stage_bytes(LOOKUP, A);
+  constexpr size_t HB = hilbert_bytes(LOOKUP);
+  uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem + HB);
+  float* s_knots = reinterpret_cast<float*>(smem + HB);
+  QEnt* s_q = reinterpret_cast<QEnt*>(smem + HB) + (threadIdx.x >> 5) * QCAP;
+  const size_t off = HB + stage_bytes(LOOKUP, A);
   const Acc acc = acc_at<SUM, RANGE>(smem + off, SMEM ? A.P : 0);
 
-  hilbert3_fill(s_tab);
+  if constexpr (TABLE)
+    hilbert3_fill_compact(s_tab);
+  else
+    hilbert3_fill(s_tab);
   if constexpr (LOOKUP == SDB_LOOKUP_BINARY)
     for (uint32_t i = threadIdx.x; i < A.sample_n; i += THREADS) s_sample[i] = A.sample[i];
-  if constexpr (LOOKUP == SDB_LOOKUP_LEARNED || LOOKUP == SDB_LOOKUP_TABLE_LEARNED)
+  if constexpr (LOOKUP == SDB_LOOKUP_LEARNED)
     for (uint32_t i = threadIdx.x; i < A.nknots; i += THREADS) s_knots[i] = A.knots[i];
   if (SMEM) acc_zero<SUM, RANGE>(acc, A.P);
   __syncthreads();
@@ -535,7 +547,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
           qn -= 32;
           const QEnt E = s_q[qn + lane];
           __syncwarp();
-          resolve_mixed<LOOKUP, SMEM, SUM, RANGE>(E, s_tab, s_knots, acc, A);
+          resolve_mixed<LOOKUP, SMEM, SUM, RANGE>(E, s_tab, acc, A);
         }
       }
     } else {
@@ -563,7 +575,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   }
   if constexpr (TABLE) {  // the rest of the queue
     __syncwarp();
-    if (lane < qn) resolve_mixed<LOOKUP, SMEM, SUM, RANGE>(s_q[lane], s_tab, s_knots, acc, A);
+    if (lane < qn) resolve_mixed<LOOKUP, SMEM, SUM, RANGE>(s_q[lane], s_tab, acc, A);
   }
   if (SMEM) {
     __syncthreads();
@@ -573,7 +585,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
 
 template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
 sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
-  size_t smem = HILBERT3_SMEM_BYTES + stage_bytes(LOOKUP, A);
+  size_t smem = hilbert_bytes(LOOKUP) + stage_bytes(LOOKUP, A);
   if (SMEM) smem += acc_bytes(A.P, SUM, RANGE);
   smem = (smem + 15) & ~(size_t)15;
   auto kern = join_kernel<LOOKUP, SMEM, SUM, RANGE>;
@@ -582,6 +594,11 @@ sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
   int per_sm = 0;
   SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
   if (per_sm < 1) per_sm = 1;
+  // ask for no more shared memory than the resident blocks use (plus the 1 KB
+  // the system reserves per block): the rest of the SM's unified memory stays
+  // L1 cache, whose lines hold the lookups' gathers in flight
+  SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    carveout_pct((size_t)per_sm * (smem + 1024))));
   uint64_t blocks = (uint64_t)num_sms() * per_sm;
   const uint64_t need = (A.n + 4 * THREADS - 1) / (4 * THREADS);  // tiles
   if (blocks > need) blocks = need > 0 ? need : 1;

@@ -69,6 +69,9 @@ struct Scratch {
   }
 };
 
+// shared-memory carveout (percent of the SM's maximum shared memory, rounded up)
+// that holds the given bytes of resident blocks' shared memory
+int carveout_pct(size_t bytes);
 int num_sms();
 
 // count of kernels this library has launched in the process (all devices)
