@@ -71,15 +71,18 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps (no join-only, e2e, CPU, batch or serving legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--legs", default="oracle,raster,range,e2e,cpu,batch,pointindex,serve",
+    ap.add_argument("--legs",
+                    default="oracle,raster,range,e2e,cpu,config3,batch,pointindex,serve",
                     help="extra legs: oracle (check of the timed coverings), raster (Bounded "
-                         "Raster Join), range (result range estimation), e2e, cpu, batch, "
-                         "pointindex (range counting over sorted points), serve")
+                         "Raster Join), range (result range estimation), e2e, cpu, config3 "
+                         "(1B points, 40k tiling, learned vs plain), batch, pointindex (range "
+                         "counting over sorted points), serve")
     ap.add_argument("--pi-points", type=int, default=500_000_000)
     ap.add_argument("--lod-points", type=int, default=200_000_000)
     ap.add_argument("--lod-queries", type=int, default=4096)
     ap.add_argument("--serve-points", type=int, default=500_000_000)
     ap.add_argument("--serve-rates", default="1000,10000,50000")
+    ap.add_argument("--c3-points", type=int, default=1_000_000_000)
     return ap.parse_args()
 
 
@@ -273,6 +276,36 @@ def cpu_oracle_rate(w, seconds: float, threads: int, max_points: int | None = No
         n = int(n * min(8.0, max(2.0, seconds / max(spent, 1e-3) / 2)))
         n = min(n, w.points.n)
     return pts.n * len(w.eps) / spent, pts.n, spent
+
+
+def oracle_forms(w, threads: int):
+    """Both oracle forms timed on the host: O1 (recursive quadtree covering,
+    ordered map of ranges, per-point ordered lookup; single thread) and O2 (the
+    definitional per-point test; one thread and all cores), on the 16-star
+    100k-point workload at eps 64 and on the zone workload at eps 2^12."""
+    from oracle import oracle as O
+    from paper_2010_12548_gb300 import workloads as W
+    out = {}
+    t1 = W.tiny_stars(100_000)
+    for name, polys, eps, pts in (("stars16_100k_eps64", t1.polygons, t1.eps[0], t1.points),
+                                  ("zones263_eps4096", w.polygons, 4096,
+                                   w.points.take(np.arange(min(w.points.n, 2_000_000))))):
+        t = time.perf_counter()
+        oc = O.cover(polys, eps)
+        build_s = time.perf_counter() - t
+        t = time.perf_counter()
+        oc.join(pts.x, pts.y, pts.attr)
+        join_s = time.perf_counter() - t
+        oc.free()
+        row = {"points": pts.n, "o1_build_s": build_s, "o1_points_per_s": pts.n / join_s}
+        for th in (1, threads):
+            m = pts.n if th > 1 else min(pts.n, 200_000)
+            sp = pts.take(np.arange(m))
+            t = time.perf_counter()
+            O.join_o2(polys, eps, sp, threads=th)
+            row[f"o2_points_per_s_{th}t"] = m / (time.perf_counter() - t)
+        out[name] = row
+    return out
 
 
 def run_reference(args):
@@ -641,17 +674,18 @@ def main():
                                "single_thread": {"value": rate1, "cores": 1,
                                                  "sample": f"first {sample1} points, all {E} "
                                                            f"eps ({secs1:.1f} s)"},
-                               "cpu": cpu_model()}
+                               "cpu": cpu_model(), "oracle_forms": oracle_forms(w, threads)}
     # ---- batched level-of-detail queries and serving (resident points)
     del x, y, a
     torch.cuda.empty_cache()
-    if "batch" in legs or "serve" in legs or "pointindex" in legs:
+    if legs & {"batch", "serve", "pointindex", "config3"}:
         res.update(resident_legs(args, legs, sdb, torch, dev, stream))
-    if "serving" in res and res["serving"].get("batched"):
-        nominal = [r for r in res["serving"]["batched"] if r["rate"] == 10000] or \
-            res["serving"]["batched"]
+    if "serving" in res and res["serving"].get("batched_learned"):
+        nominal = [r for r in res["serving"]["batched_learned"] if r["rate"] == 10000] or \
+            res["serving"]["batched_learned"]
         res["p50_ms"] = nominal[0]["p50_ms"]
         res["p99_ms"] = nominal[0]["p99_ms"]
+        res["latency_note"] = "learned, batched serving at %d queries/s" % nominal[0]["rate"]
     if rank == 0:
         print(json.dumps(res), flush=True)
     if ws > 1:
@@ -764,6 +798,101 @@ def point_index_leg(args, sdb, torch, dev, stream, T, pts, resident):
     return out
 
 
+C3_EPS_SWEEP = (2 ** 12, 2 ** 11, 2 ** 10, 2 ** 9)
+
+
+def config3_leg(args, sdb, torch, dev, stream, T, pts):
+    """The large learned index (1B points on [0,2^28)^2, 64-cluster mix, the
+    40,000-cell tiling).  Range and record counts of single covering builds
+    against eps (they grow as 1/eps: the finest feasible eps is the finest whose
+    records, frontier edge entries and ranges stay inside the builder's 32-bit
+    limits); at the finest eps of the sweep, the join of all points with binary
+    search, the learned index alone (2^16 leaves), the cell table and the
+    table + learned lookup on the same covering; results must agree and match
+    the oracle's definitional test on a 2M-point sample."""
+    from oracle import oracle as O
+    n = min(args.c3_points, pts.n)
+    P = T.n
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    xs = torch.from_numpy(pts.x[:n].view(np.int32)).to(dev)
+    ys = torch.from_numpy(pts.y[:n].view(np.int32)).to(dev)
+    at = torch.from_numpy(pts.attr[:n]).to(dev)
+    out = {"workload": f"tracts40k_pts{n // 1_000_000}M_g28", "points": n, "polygons": P,
+           "sweep": {}}
+    cov = None
+    for eps in C3_EPS_SWEEP:
+        if cov is not None:
+            cov.free()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cov = sdb.build_covering(T, 28, eps, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        inf = cov.info()
+        out["sweep"][str(eps)] = {"ranges": inf.n_ranges, "cells": inf.n_cells,
+                                  "covering_bytes": inf.device_bytes, "finest_level": inf.finest_level,
+                                  "build_ms": e0.elapsed_time(e1)}
+    eps = C3_EPS_SWEEP[-1]
+    cells = out["sweep"][str(eps)]["cells"]
+    out["eps"] = eps
+    out["eps_2^5_estimate"] = {
+        "cells": cells * eps // 32, "why_not_built": "records grow as 1/eps: about %.1e records "
+        "at eps = 2^5, beyond the builder's 32-bit record and edge-entry ranges and, as a "
+        "covering of ~24 B per range, beyond device memory" % (cells * eps / 32)}
+    e0.record(stream)
+    sdb.covering_build_table(cov, TABLE_BITS, stream)
+    sdb.covering_build_index(cov, LEAF_BITS, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["table_and_index_ms"] = e0.elapsed_time(e1)
+    cnt = torch.zeros(P, dtype=torch.int64, device=dev)
+    sm = torch.zeros(P, dtype=torch.int64, device=dev)
+    ref = None
+    agree = True
+    rows = {}
+    for name, lk in (("table_learned", sdb.LOOKUP_TABLE_LEARNED), ("binary", sdb.LOOKUP_BINARY),
+                     ("learned", sdb.LOOKUP_LEARNED), ("table", sdb.LOOKUP_TABLE)):
+        ms = timed(torch, stream, lambda lk=lk: sdb.join_aggregate(xs, ys, at, cov, lk, cnt, sm,
+                                                                    stream), 3)
+        rows[name] = {"ms": ms, "points_per_s": n / (ms / 1e3)}
+        if lk in (sdb.LOOKUP_LEARNED, sdb.LOOKUP_TABLE_LEARNED):
+            rows[name]["fallbacks"] = sdb.covering_fallbacks(cov, stream)
+        got = (cnt.clone(), sm.clone())
+        if ref is None:
+            ref = got
+        agree &= bool(torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]))
+    out["joins"] = rows
+    out["lookups_agree"] = agree
+    out["value"] = rows["table_learned"]["points_per_s"]
+    out["plain_value"] = rows["binary"]["points_per_s"]
+    inf = cov.info()
+    out["table_mixed"] = inf.table_mixed
+    mw, xw = sdb.covering_index_stats(cov)
+    out["learned_window_mean"] = mw
+    peak, peak_kind = peaks()
+    per_pt = 12 + lookup_bytes(sdb, cov, sdb.LOOKUP_TABLE_LEARNED) / n
+    ach = n * per_pt / (rows["table_learned"]["ms"] / 1e3) / 1e9
+    out["roofline"] = {"kernel": "join_kernel<table_learned> eps=%d" % eps, "bound": "hbm",
+                       "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "peak_kind": peak_kind, "algorithmic_bytes_per_point": per_pt}
+    # the oracle's definitional test on a fixed 2M-point sample
+    O.build()
+    idx = np.arange(0, n, max(1, n // 2_000_000))[:2_000_000]
+    sp = pts.take(idx)
+    ti = torch.from_numpy(idx.astype(np.int64)).to(dev)
+    sdb.join_aggregate(xs[ti].contiguous(), ys[ti].contiguous(), at[ti].contiguous(), cov,
+                       sdb.LOOKUP_TABLE_LEARNED, cnt, sm, stream)
+    torch.cuda.synchronize()
+    oc, os_, _ = O.join_o2(T, eps, sp, threads=os.cpu_count() or 1)
+    out["matches_oracle"] = bool(np.array_equal(cnt.cpu().numpy().view(np.uint64), oc)
+                                 and np.array_equal(sm.cpu().numpy(), os_))
+    out["oracle_check"] = f"{len(idx)} points (every {max(1, n // 2_000_000)}th), O2"
+    cov.free()
+    del xs, ys, at, cnt, sm
+    torch.cuda.empty_cache()
+    return out
+
+
 def resident_legs(args, legs, sdb, torch, dev, stream):
     """Batched level-of-detail queries (4,096 queries over 200M resident points)
     and serving (Poisson arrivals of zoom-session queries over 500M points)."""
@@ -772,8 +901,9 @@ def resident_legs(args, legs, sdb, torch, dev, stream):
     T = W.tracts40k_tiling()
     n_all = max(args.lod_points if "batch" in legs else 0,
                 args.serve_points if "serve" in legs else 0,
-                args.pi_points if "pointindex" in legs else 0)
-    pts = W.resident_points(n_all)
+                args.pi_points if "pointindex" in legs else 0,
+                args.c3_points if "config3" in legs else 0)
+    pts = W.resident_points(n_all)  # a shorter set is a prefix of a longer one
 
     def resident(n):
         xs = torch.from_numpy(pts.x[:n].view(np.int32)).to(dev)
@@ -799,6 +929,16 @@ def resident_legs(args, legs, sdb, torch, dev, stream):
         with torch.cuda.stream(side):
             ms = {m: timed(torch, side, lambda m=m: sdb.batch_run(b, m, cnt, sm, side), 5)
                   for m in (sdb.BATCH_PERSISTENT, sdb.BATCH_GRAPH, sdb.BATCH_PER_QUERY)}
+        ref_c, ref_s = cnt.clone(), sm.clone()
+        t = time.perf_counter()
+        sdb.batch_set_lookup(b, sdb.LOOKUP_LEARNED, stream)
+        index_s = time.perf_counter() - t
+        linf = b.info()
+        with torch.cuda.stream(side):
+            lms = {m: timed(torch, side, lambda m=m: sdb.batch_run(b, m, cnt, sm, side), 5)
+                   for m in (sdb.BATCH_PERSISTENT, sdb.BATCH_GRAPH, sdb.BATCH_PER_QUERY)}
+        learned_same = bool(torch.equal(cnt, ref_c) and torch.equal(sm, ref_s))
+        learned_fb = sdb.batch_fallbacks(b, stream)
         out["batched"] = {
             "workload": f"lod{args.lod_queries}_tracts40k_pts{args.lod_points // 1_000_000}M_g28",
             "queries": inf.n_queries, "pairs": inf.n_pairs, "ranges": inf.n_ranges,
@@ -807,11 +947,19 @@ def resident_legs(args, legs, sdb, torch, dev, stream):
             "persistent_ms": ms[sdb.BATCH_PERSISTENT], "graph_ms": ms[sdb.BATCH_GRAPH],
             "per_query_launches_ms": ms[sdb.BATCH_PER_QUERY],
             "queries_per_s_graph": inf.n_queries / (ms[sdb.BATCH_GRAPH] / 1e3),
-            "candidate_points_per_s_graph": inf.candidates / (ms[sdb.BATCH_GRAPH] / 1e3)}
+            "candidate_points_per_s_graph": inf.candidates / (ms[sdb.BATCH_GRAPH] / 1e3),
+            "learned": {"index_build_s": index_s, "indexed_queries": linf.indexed_queries,
+                        "leaves": linf.n_leaves, "persistent_ms": lms[sdb.BATCH_PERSISTENT],
+                        "graph_ms": lms[sdb.BATCH_GRAPH],
+                        "per_query_launches_ms": lms[sdb.BATCH_PER_QUERY],
+                        "queries_per_s_graph": inf.n_queries / (lms[sdb.BATCH_GRAPH] / 1e3),
+                        "same_as_binary": learned_same, "fallbacks": learned_fb}}
         b.free()
         p.free()
         del cnt, sm
         torch.cuda.empty_cache()
+    if "config3" in legs:
+        out["config3"] = config3_leg(args, sdb, torch, dev, stream, T, pts)
     if "pointindex" in legs:
         out["point_index"] = point_index_leg(args, sdb, torch, dev, stream, T, pts, resident)
     if "serve" in legs:
@@ -820,11 +968,18 @@ def resident_legs(args, legs, sdb, torch, dev, stream):
         p = resident(args.serve_points)
         rates = [int(r) for r in args.serve_rates.split(",") if r]
         serving = {"workload": f"zoom512sessions_tracts40k_pts{args.serve_points // 1_000_000}M_g28",
-                   "queries_in_pool": len(queries), "batched": [], "plain": []}
-        for kind, cfg in (("batched", dict(workers=4, max_batch=256, cache_bytes=40 << 30)),
+                   "queries_in_pool": len(queries), "batched_learned": [], "batched": [],
+                   "plain": [],
+                   "plain_note": "one query per launch, binary search, no covering cache: it "
+                                 "sustains under 1k queries/s, so at higher rates its queue "
+                                 "grows for the whole run (600 queries) and the percentiles "
+                                 "measure that backlog"}
+        for kind, cfg in (("batched_learned", dict(workers=4, max_batch=256, cache_bytes=40 << 30,
+                                                   lookup=sdb.LOOKUP_LEARNED)),
+                          ("batched", dict(workers=4, max_batch=256, cache_bytes=40 << 30)),
                           ("plain", dict(workers=1, max_batch=1, use_cache=False,
                                          per_query=True))):
-            for rate in (rates if kind == "batched" else rates[:1]):
+            for rate in rates:
                 srv = sdb.server_create(p, T, **cfg)
                 n = int(min(4000, max(400, rate * 2)))
                 if kind == "plain":

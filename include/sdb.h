@@ -442,6 +442,9 @@ typedef struct sdb_batch_info {
   uint64_t n_tiles;        /* work items of the persistent launch */
   uint32_t tile;           /* points per work item */
   uint32_t points_per_thread;
+  uint32_t lookup;         /* SDB_LOOKUP_BINARY or SDB_LOOKUP_LEARNED */
+  uint32_t indexed_queries;/* queries searched through their learned index */
+  uint64_t n_leaves;       /* learned leaves over all queries */
 } sdb_batch_info;
 
 enum { SDB_BATCH_PERSISTENT = 0, SDB_BATCH_PER_QUERY = 1, SDB_BATCH_GRAPH = 2 };
@@ -473,6 +476,25 @@ sdb_status sdb_batch_query_ranges(const sdb_batch *b, uint32_t *h_ranges);
 sdb_status sdb_batch_run(sdb_batch *b, int mode, uint64_t *d_count, int64_t *d_sum,
                          void *cuda_stream);
 
+/* Lookup of later runs (sdb_batch_run, sdb_batch_autotune).  SDB_LOOKUP_BINARY
+ * (the default): binary search over each query's ranges.  SDB_LOOKUP_LEARNED
+ * (Sec. 3, learned index): every query covering of at least
+ * SDB_BATCH_LEARNED_MIN_RANGES ranges gets a two-level model fitted on the
+ * device -- a linear root over the span of its range starts picking one of up
+ * to 2^16 leaves (about SDB_BATCH_RANGES_PER_LEAF ranges each), each leaf an
+ * FP32 least-squares line with the largest prediction errors below and above
+ * measured by the lookup's own arithmetic; a point searches its leaf's error
+ * window, the result is verified and binary search over the query's ranges is
+ * the counted fallback, so results are identical to binary search.  Smaller
+ * coverings keep binary search.  Synchronises cuda_stream.  SDB_EINVAL: another
+ * lookup. */
+#define SDB_BATCH_LEARNED_MIN_RANGES 64u
+#define SDB_BATCH_RANGES_PER_LEAF 8u
+sdb_status sdb_batch_set_lookup(sdb_batch *b, int lookup, void *cuda_stream);
+/* Learned searches of the most recent run that fell back to binary search.
+ * Synchronises cuda_stream. */
+sdb_status sdb_batch_fallbacks(const sdb_batch *b, void *cuda_stream, uint64_t *out);
+
 /* Autotuner: times the persistent launch on this batch for tiles of 1024,
  * 4096, 16384 points and 1, 2, 4 points per thread, keeps the fastest.
  * Synchronises cuda_stream. */
@@ -494,7 +516,9 @@ void sdb_batch_free(sdb_batch *b);
  * batches are pinned) or is built with the batch's other missing queries in one
  * pass; a worker takes new work only while the coverings of running batches fit
  * cache_bytes.  Each batch's join is one persistent launch, or one launch per
- * query in the plain form (per_query = 1).  Results are the same as the batch
+ * query in the plain form (per_query = 1), searching each query's ranges by
+ * binary search or, with lookup = SDB_LOOKUP_LEARNED, through a learned index
+ * fitted to the batch's coverings (sdb_batch_set_lookup).  Results are the same as the batch
  * API's for the same query, alone or in any mix.
  * ------------------------------------------------------------------------- */
 typedef struct sdb_server sdb_server;
@@ -507,6 +531,8 @@ typedef struct sdb_server_config {
   uint32_t per_query;         /* 1: one launch per query instead of one per batch */
   uint32_t tile;              /* points per work item, 0 = default */
   uint32_t points_per_thread; /* 1, 2, 4, or 0 = default */
+  uint32_t lookup;            /* SDB_LOOKUP_BINARY (0) or SDB_LOOKUP_LEARNED: each batch
+                                 fits the learned index of sdb_batch_set_lookup */
 } sdb_server_config;
 
 typedef struct sdb_ticket_info {

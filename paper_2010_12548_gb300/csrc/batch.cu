@@ -19,6 +19,14 @@
 //    the query's finest level, binary search in the query's ranges, and
 //    per-slot COUNT/SUM in the query's output slice.  Alternatively one launch
 //    per query, or the persistent launch replayed as a captured CUDA graph.
+//  * Learned lookup (Sec. 3, learned index): each query covering with enough
+//    ranges gets a two-level model, a linear root over the span of its range
+//    starts (leaf = (h - lo) >> shift) and FP32 linear leaves fitted by least
+//    squares with their maximum errors measured by the lookup's own arithmetic;
+//    a point searches only its leaf's error window, the result is verified, and
+//    binary search over the slice is the counted fallback.  The points of a
+//    work item are Hilbert-ordered, so neighbouring lanes read the same leaf and
+//    window lines.
 //  * An autotuner picks the tile size and points per thread by timing the
 //    candidates on the batch itself.
 #include "hilbert.cuh"
@@ -179,7 +187,67 @@ struct BatchArgs {
   const ChunkDev* chunks;
   unsigned long long* count;
   unsigned long long* sum;
+  const LeafRec* leaves;          // per-query learned leaves (queries with nleaves > 0)
+  unsigned long long* fallbacks;  // learned searches that missed
 };
+
+// last r in [0, R) with st[r] <= h (st[R] is the slice's sentinel, above all ids)
+__device__ __forceinline__ uint32_t slice_bs(const uint64_t* __restrict__ st, uint32_t R,
+                                             uint64_t h) {
+  uint32_t lo = 0;
+  for (uint32_t len = R + 1; len > 1;) {
+    const uint32_t half = len >> 1;
+    if (__ldg(st + lo + half) <= h) lo += half;
+    len -= half;
+  }
+  return lo;
+}
+
+// the range of id h in a query slice through its learned index: ids outside
+// the leaves' span are the first or last range; else the leaf's prediction,
+// a search of its error window (an end no probe has proven is read back), and
+// binary search over the slice when the window does not bracket h (counted)
+__device__ __forceinline__ uint32_t slice_learned(const uint64_t* __restrict__ st,
+                                                  const QueryDev& Q, const LeafRec* leaves,
+                                                  unsigned long long* fallbacks, uint64_t h) {
+  if (h < Q.llo) return 0;
+  if (h >= Q.lhi) return Q.R - 1;
+  uint64_t l = (h - Q.llo) >> Q.lwshift;
+  if (l >= Q.nleaves) l = Q.nleaves - 1;
+  uint64_t w0, w1, w2, w3;
+  asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+      : "l"(leaves + Q.loff + l));
+  LeafRec lr;
+  lr.base = w0;
+  lr.a = __uint_as_float((uint32_t)w1);
+  lr.b = __uint_as_float((uint32_t)(w1 >> 32));
+  lr.first = (uint32_t)w2;
+  lr.last = (uint32_t)(w2 >> 32);
+  lr.errlo = (int32_t)(uint32_t)w3;
+  lr.errhi = (int32_t)(uint32_t)(w3 >> 32);
+  const int64_t pr = leaf_predict(lr, h);
+  int64_t a = pr - lr.errlo, b = pr + lr.errhi;
+  if (a < (int64_t)lr.first) a = lr.first;
+  if (b > (int64_t)lr.last) b = lr.last;
+  if (b < a) b = a;
+  uint32_t lo = (uint32_t)a, len = (uint32_t)(b - a + 1), known = 0;
+  while (len > 1) {
+    const uint32_t half = len >> 1;
+    if (__ldg(st + lo + half) <= h) {
+      lo += half;
+      known |= 1u;
+    } else {
+      known |= 2u;
+    }
+    len -= half;
+  }
+  const bool ok0 = (known & 1u) || __ldg(st + lo) <= h;
+  const bool ok1 = (known & 2u) || h < __ldg(st + lo + 1);
+  if (ok0 && ok1) return lo;
+  atomicAdd(fallbacks, 1ull);
+  return slice_bs(st, Q.R, h);
+}
 
 __device__ __forceinline__ void add_slot(const BatchArgs& A, uint32_t out, uint32_t p, int32_t a,
                                          bool sum) {
@@ -221,15 +289,21 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
       uint32_t lo[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) lo[g] = 0;
-      for (uint32_t len = Q.R + 1; len > 1;) {
-        const uint32_t half = len >> 1;
-        uint64_t v[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) v[g] = __ldg(C.start + Q.sbase + lo[g] + half);
+      if (Q.nleaves) {  // block-uniform: every point of the work item is in query Q
 #pragma unroll
         for (int g = 0; g < G; ++g)
-          if (v[g] <= h[g]) lo[g] += half;
-        len -= half;
+          if (ok[g]) lo[g] = slice_learned(C.start + Q.sbase, Q, A.leaves, A.fallbacks, h[g]);
+      } else {
+        for (uint32_t len = Q.R + 1; len > 1;) {
+          const uint32_t half = len >> 1;
+          uint64_t v[G];
+#pragma unroll
+          for (int g = 0; g < G; ++g) v[g] = __ldg(C.start + Q.sbase + lo[g] + half);
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (v[g] <= h[g]) lo[g] += half;
+          len -= half;
+        }
       }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
@@ -246,6 +320,105 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
       }
     }
   }
+}
+
+// ---------------------------------------------------------------- learned index
+// per query with leaves: the span [llo, lhi) of ids between its second range
+// start and one past its last range start
+__global__ void slice_span_kernel(const QueryDev* __restrict__ qd, uint32_t Q,
+                                  const ChunkDev* __restrict__ chunks, uint32_t min_ranges,
+                                  uint64_t* __restrict__ span) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const QueryDev d = qd[q];
+  if (d.R < 2 || d.R < min_ranges) {
+    span[2 * q] = span[2 * q + 1] = 0;
+    return;
+  }
+  const uint64_t* st = chunks[d.chunk].start + d.sbase;
+  span[2 * q] = st[1];
+  span[2 * q + 1] = st[d.R - 1] + 1;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
+  return v;
+}
+
+// one warp per leaf: leaf l of query q receives the ids [base, end), base =
+// llo + (l << shift), end = base + 2^shift (the last leaf ends at lhi); its
+// ranges are first .. last (local indices: the ranges holding base and end - 1).
+// Least squares of the local index on the leaf-relative start (FP32, centred),
+// then the largest prediction errors below and above over every id the leaf
+// receives, from the lookup's own arithmetic at the two ends of each range's
+// part of the leaf (the prediction is monotone in h).
+__global__ void batch_leaf_fit_kernel(const QueryDev* __restrict__ qd,
+                                      const ChunkDev* __restrict__ chunks,
+                                      const uint32_t* __restrict__ leaf_q, uint64_t total,
+                                      LeafRec* __restrict__ leaves) {
+  const uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= total) return;
+  const QueryDev Q = qd[leaf_q[g]];
+  const uint64_t l = g - Q.loff;
+  const uint64_t* st = chunks[Q.chunk].start + Q.sbase;
+  const uint64_t b0 = Q.llo + (l << Q.lwshift);
+  uint64_t b1 = l + 1 == Q.nleaves ? Q.lhi : b0 + (1ull << Q.lwshift);
+  if (b1 > Q.lhi) b1 = Q.lhi;
+  const uint32_t first = slice_bs(st, Q.R, b0), last = slice_bs(st, Q.R, b1 - 1);
+  LeafRec lr;
+  lr.base = b0;
+  lr.first = first;
+  lr.last = last;
+  const uint32_t n = last - first + 1;
+  float sx = 0.f, sy = 0.f;
+  for (uint32_t i = first + lane; i <= last; i += 32) {
+    const uint64_t v = st[i] > b0 ? st[i] : b0;
+    sx += __ull2float_rn(v - b0);
+    sy += (float)(i - first);
+  }
+  const float inv_n = 1.0f / (float)n;
+  const float mx = warp_sum_f(sx) * inv_n, my = warp_sum_f(sy) * inv_n;
+  float sxx = 0.f, sxy = 0.f;
+  for (uint32_t i = first + lane; i <= last; i += 32) {
+    const uint64_t v = st[i] > b0 ? st[i] : b0;
+    const float dx = __ull2float_rn(v - b0) - mx, dy = (float)(i - first) - my;
+    sxx = fmaf(dx, dx, sxx);
+    sxy = fmaf(dx, dy, sxy);
+  }
+  sxx = warp_sum_f(sxx);
+  sxy = warp_sum_f(sxy);
+  const float slope = (sxx > 0.f && sxy > 0.f) ? sxy / sxx : 0.f;
+  lr.a = slope;
+  lr.b = my - slope * mx;
+  lr.errlo = 0;
+  lr.errhi = 0;
+  long long ehi = 0, elo = 0;
+  for (uint32_t i = first + lane; i <= last; i += 32) {
+    const uint64_t lo_h = st[i] > b0 ? st[i] : b0;
+    const uint64_t hi_h = (st[i + 1] < b1 ? st[i + 1] : b1) - 1;
+    const long long plo = (long long)leaf_predict(lr, lo_h);
+    const long long phi = (long long)leaf_predict(lr, hi_h);
+    const long long up = (long long)i - plo, dn = phi - (long long)i;
+    ehi = up > ehi ? up : ehi;
+    elo = dn > elo ? dn : elo;
+  }
+  ehi = warp_max_ll(ehi);
+  elo = warp_max_ll(elo);
+  const long long CAP = 1ll << 30;
+  lr.errhi = (int32_t)(ehi > CAP ? CAP : ehi);
+  lr.errlo = (int32_t)(elo > CAP ? CAP : elo);
+  if (lane == 0) leaves[g] = lr;
 }
 
 }  // namespace
@@ -302,6 +475,10 @@ sdb_status status_of(cudaError_t e, const char* what) {
 }  // namespace
 
 void BatchCore::release(cudaStream_t s) {
+  dfree(leaves, s);
+  dfree(fallbacks, s);
+  leaves = nullptr;
+  fallbacks = nullptr;
   dfree(dq, s);
   dfree(dchunks, s);
   dfree(cand, s);
@@ -399,8 +576,88 @@ sdb_status batch_core_prepare(BatchCore* c, cudaStream_t s) {
   return SDB_OK;
 }
 
+sdb_status batch_core_index(BatchCore* c, uint32_t min_ranges, uint32_t ranges_per_leaf,
+                            cudaStream_t s) {
+  const uint32_t Q = c->Q;
+  dfree(c->leaves, s);
+  c->leaves = nullptr;
+  c->nleaves = 0;
+  c->indexed = 0;
+  c->learned = min_ranges > 0;
+  for (auto& d : c->hq) d.nleaves = d.loff = d.lwshift = 0, d.llo = d.lhi = 0;
+  if (c->learned) {
+    if (ranges_per_leaf == 0) ranges_per_leaf = 1;
+    Scratch sc(s);
+    uint64_t* dspan;
+    SDB_TRY(sc.get(&dspan, (size_t)Q * 2));
+    slice_span_kernel<<<grid_for(Q, 128), 128, 0, s>>>(c->dq, Q, c->dchunks, min_ranges, dspan);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    std::vector<uint64_t> span((size_t)Q * 2);
+    SDB_TRY_CUDA(cudaMemcpyAsync(span.data(), dspan, span.size() * 8, cudaMemcpyDeviceToHost, s));
+    SDB_TRY_CUDA(cudaStreamSynchronize(s));
+    std::vector<uint32_t> leaf_q;
+    uint64_t total = 0;
+    for (uint32_t q = 0; q < Q; ++q) {
+      BatchQueryDev& d = c->hq[q];
+      const uint64_t lo = span[2 * q], hi = span[2 * q + 1];
+      if (hi <= lo) continue;  // too few ranges: binary search
+      // leaves for about ranges_per_leaf ranges each, a power of two in 16 .. 2^16
+      uint64_t want = 16;
+      while (want < 65536 && want * ranges_per_leaf < d.R) want *= 2;
+      const uint64_t sp = hi - lo;
+      uint32_t ws = 0;
+      while (((sp + (1ull << ws) - 1) >> ws) > want) ++ws;
+      const uint64_t L = (sp + (1ull << ws) - 1) >> ws;
+      d.nleaves = (uint32_t)L;
+      d.lwshift = ws;
+      d.loff = (uint32_t)total;
+      d.llo = lo;
+      d.lhi = hi;
+      total += L;
+      if (total >= 0xffffffffull) {
+        set_error("batch learned index: %llu leaves exceed the 32-bit range",
+                  (unsigned long long)total);
+        return SDB_EINVAL;
+      }
+      leaf_q.insert(leaf_q.end(), (size_t)L, q);
+      ++c->indexed;
+    }
+    if (total) {
+      uint32_t* dlq;
+      SDB_TRY(sc.get(&dlq, total));
+      SDB_TRY(dalloc_n(&c->leaves, total, s));
+      if (reinterpret_cast<uintptr_t>(c->leaves) & 31u) {  // leaves are read 32 bytes at once
+        set_error("batch learned index: leaf records not 32-byte aligned");
+        return SDB_ECUDA;
+      }
+      SDB_TRY_CUDA(cudaMemcpyAsync(dlq, leaf_q.data(), total * 4, cudaMemcpyHostToDevice, s));
+      SDB_TRY_CUDA(cudaMemcpyAsync(c->dq, c->hq.data(), Q * sizeof(BatchQueryDev),
+                                   cudaMemcpyHostToDevice, s));
+      batch_leaf_fit_kernel<<<grid_for(total * 32, 256), 256, 0, s>>>(c->dq, c->dchunks, dlq,
+                                                                      total, c->leaves);
+      note_launch();
+      SDB_TRY_CUDA(cudaGetLastError());
+      SDB_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    c->nleaves = total;
+    if (!c->fallbacks) {
+      SDB_TRY(dalloc_n(&c->fallbacks, 1, s));
+      SDB_TRY_CUDA(cudaMemsetAsync(c->fallbacks, 0, sizeof(unsigned long long), s));
+    }
+  }
+  SDB_TRY_CUDA(cudaMemcpyAsync(c->dq, c->hq.data(), Q * sizeof(BatchQueryDev),
+                               cudaMemcpyHostToDevice, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  return SDB_OK;
+}
+
 sdb_status batch_core_run(BatchCore* c, int mode, uint64_t* count, int64_t* sum, cudaStream_t s) {
   BatchArgs A;
+  A.leaves = c->leaves;
+  A.fallbacks = c->fallbacks;
+  if (c->fallbacks)
+    SDB_TRY_CUDA(cudaMemsetAsync(c->fallbacks, 0, sizeof(unsigned long long), s));
   A.x = c->pts->x;
   A.y = c->pts->y;
   A.attr = c->pts->attr;
@@ -726,6 +983,39 @@ sdb_status sdb_batch_get_info(const sdb_batch* b, sdb_batch_info* info) {
   info->n_tiles = b->core.ntiles;
   info->tile = b->core.tile;
   info->points_per_thread = b->core.ppt;
+  info->lookup = b->core.learned ? SDB_LOOKUP_LEARNED : SDB_LOOKUP_BINARY;
+  info->indexed_queries = b->core.indexed;
+  info->n_leaves = b->core.nleaves;
+  return SDB_OK;
+}
+
+sdb_status sdb_batch_set_lookup(sdb_batch* b, int lookup, void* cuda_stream) {
+  if (!b || (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED)) {
+    set_error("batch NULL, or a lookup other than binary search and the learned index");
+    return SDB_EINVAL;
+  }
+  if (!valid_device(b->device)) {
+    set_error("batch lives on another device");
+    return SDB_EINVAL;
+  }
+  if (b->graph) {  // the captured launch refers to the old lookup structures
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return batch_core_index(&b->core, lookup == SDB_LOOKUP_LEARNED ? SDB_BATCH_LEARNED_MIN_RANGES : 0,
+                          SDB_BATCH_RANGES_PER_LEAF, (cudaStream_t)cuda_stream);
+}
+
+sdb_status sdb_batch_fallbacks(const sdb_batch* b, void* cuda_stream, uint64_t* out) {
+  if (!b || !out) {
+    set_error("batch or output is NULL");
+    return SDB_EINVAL;
+  }
+  *out = 0;
+  if (!b->core.fallbacks) return SDB_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  SDB_TRY_CUDA(cudaMemcpyAsync(out, b->core.fallbacks, 8, cudaMemcpyDeviceToHost, s));
+  SDB_TRY_CUDA(cudaStreamSynchronize(s));
   return SDB_OK;
 }
 

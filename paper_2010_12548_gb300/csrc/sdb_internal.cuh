@@ -295,6 +295,11 @@ struct BatchQueryDev {
   uint32_t k, nsteps, st0;
   uint32_t x0, y0, x1, y1;
   uint32_t out_off;
+  // learned index of the slice (nleaves = 0: binary search): ids below llo lie
+  // in range 0, ids from lhi on in range R - 1; between them leaf
+  // min(nleaves - 1, (h - llo) >> lwshift) of the batch's leaf array, from loff
+  uint32_t nleaves, loff, lwshift, pad;
+  uint64_t llo, lhi;
 };
 struct BatchChunkDev {
   const uint64_t* start;
@@ -308,6 +313,12 @@ struct BatchTile {
 // Everything a batched join needs besides the coverings themselves.
 struct BatchCore {
   const sdb_points* pts = nullptr;
+  // learned lookup (batch_core_index): per-query leaves, fallback counter
+  bool learned = false;
+  LeafRec* leaves = nullptr;
+  uint64_t nleaves = 0;
+  uint32_t indexed = 0;  // queries with leaves
+  unsigned long long* fallbacks = nullptr;
   uint32_t Q = 0;
   uint64_t out_len = 0, candidates = 0;
   std::vector<BatchQueryDev> hq;
@@ -330,6 +341,10 @@ sdb_status batch_query_dev(uint32_t B, const sdb_query& q, uint64_t out_off, Bat
 sdb_status batch_core_prepare(BatchCore* c, cudaStream_t s);
 sdb_status batch_core_tiles(BatchCore* c, uint32_t T, cudaStream_t s);
 // mode SDB_BATCH_PERSISTENT or SDB_BATCH_PER_QUERY; outputs cleared first
+// fit the per-query learned index of every query with at least min_ranges
+// ranges (about ranges_per_leaf ranges per leaf, at most 2^16 leaves a query)
+sdb_status batch_core_index(BatchCore* c, uint32_t min_ranges, uint32_t ranges_per_leaf,
+                            cudaStream_t s);
 sdb_status batch_core_run(BatchCore* c, int mode, uint64_t* count, int64_t* sum, cudaStream_t s);
 // coverings for queries cq (pairs in query order), chunked; fills sbase/R/chunk
 // of hq with chunk indices starting at chunk_base

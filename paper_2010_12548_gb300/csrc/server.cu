@@ -272,6 +272,8 @@ sdb_status process(sdb_server* S, std::vector<std::shared_ptr<Ticket>>& batch, c
     uint64_t* d_cnt = nullptr;
     int64_t* d_sum = nullptr;
     rc = sdb::batch_core_prepare(&core, s);
+    if (rc == SDB_OK && S->cfg.lookup == SDB_LOOKUP_LEARNED)
+      rc = sdb::batch_core_index(&core, SDB_BATCH_LEARNED_MIN_RANGES, SDB_BATCH_RANGES_PER_LEAF, s);
     if (rc == SDB_OK) rc = sdb::dalloc_n(&d_cnt, out_off, s);
     if (rc == SDB_OK) rc = sdb::dalloc_n(&d_sum, out_off, s);
     if (rc == SDB_OK)
@@ -377,6 +379,10 @@ sdb_status sdb_server_create(const sdb_points* pts, const sdb_polygons* polys,
   if (cfg->points_per_thread && !(cfg->points_per_thread == 1 || cfg->points_per_thread == 2 ||
                                   cfg->points_per_thread == 4)) {
     set_error("points per thread must be 1, 2 or 4");
+    return SDB_EINVAL;
+  }
+  if (cfg->lookup != SDB_LOOKUP_BINARY && cfg->lookup != SDB_LOOKUP_LEARNED) {
+    set_error("server lookup must be binary search or the learned index");
     return SDB_EINVAL;
   }
   int dev = -1;

@@ -70,7 +70,8 @@ class BatchInfo(C.Structure):
     _fields_ = [("n_queries", C.c_uint32), ("n_pairs", C.c_uint32), ("out_len", C.c_uint64),
                 ("n_ranges", C.c_uint64), ("max_ranges", C.c_uint64), ("n_cells", C.c_uint64),
                 ("candidates", C.c_uint64), ("n_tiles", C.c_uint64), ("tile", C.c_uint32),
-                ("points_per_thread", C.c_uint32)]
+                ("points_per_thread", C.c_uint32), ("lookup", C.c_uint32),
+                ("indexed_queries", C.c_uint32), ("n_leaves", C.c_uint64)]
 
 
 BATCH_PERSISTENT, BATCH_PER_QUERY, BATCH_GRAPH = 0, 1, 2
@@ -79,7 +80,7 @@ BATCH_PERSISTENT, BATCH_PER_QUERY, BATCH_GRAPH = 0, 1, 2
 class ServerConfig(C.Structure):
     _fields_ = [("workers", C.c_uint32), ("max_batch", C.c_uint32), ("cache_bytes", C.c_uint64),
                 ("use_cache", C.c_uint32), ("per_query", C.c_uint32), ("tile", C.c_uint32),
-                ("points_per_thread", C.c_uint32)]
+                ("points_per_thread", C.c_uint32), ("lookup", C.c_uint32)]
 
 
 class TicketInfo(C.Structure):
@@ -139,6 +140,8 @@ def lib():
             "sdb_batch_run": ([P, I, P, P, P], I),
             "sdb_batch_autotune": ([P, P, P, P], I),
             "sdb_batch_set_tuning": ([P, U32, U32, P], I),
+            "sdb_batch_set_lookup": ([P, I, P], I),
+            "sdb_batch_fallbacks": ([P, P, P], I),
             "sdb_batch_free": ([P], None),
             "sdb_server_create": ([P, P, P, P], I),
             "sdb_server_submit": ([P, P, P, P], I),
@@ -519,6 +522,17 @@ def batch_set_tuning(batch: Batch, tile: int, points_per_thread: int, stream=Non
     _check(lib().sdb_batch_set_tuning(batch.handle, tile, points_per_thread, _stream(stream)))
 
 
+def batch_set_lookup(batch: Batch, lookup: int, stream=None):
+    """sdb_batch_set_lookup: LOOKUP_BINARY or LOOKUP_LEARNED for later runs."""
+    _check(lib().sdb_batch_set_lookup(batch.handle, lookup, _stream(stream)))
+
+
+def batch_fallbacks(batch: Batch, stream=None) -> int:
+    v = C.c_uint64()
+    _check(lib().sdb_batch_fallbacks(batch.handle, _stream(stream), C.byref(v)))
+    return int(v.value)
+
+
 class Server:
     """Continuous-batching query server (owns the library handle)."""
 
@@ -564,13 +578,14 @@ class Server:
 
 
 def server_create(points: Points, polys, *, workers=4, max_batch=256, cache_bytes=40 << 30,
-                  use_cache=True, per_query=False, tile=0, points_per_thread=0) -> Server:
+                  use_cache=True, per_query=False, tile=0, points_per_thread=0,
+                  lookup=LOOKUP_BINARY) -> Server:
     off = np.ascontiguousarray(polys.ring_off, np.uint32)
     x = np.ascontiguousarray(polys.x, np.uint32)
     y = np.ascontiguousarray(polys.y, np.uint32)
     sp = _Polys(len(off) - 1, _np_ptr(off), _np_ptr(x), _np_ptr(y))
     cfg = ServerConfig(workers, max_batch, cache_bytes, int(use_cache), int(per_query), tile,
-                       points_per_thread)
+                       points_per_thread, lookup)
     out = C.c_void_p()
     _check(lib().sdb_server_create(points.handle, C.byref(sp), C.byref(cfg), C.byref(out)))
     return Server(out.value, points, len(off) - 1)

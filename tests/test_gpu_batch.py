@@ -2,7 +2,8 @@
 
 Each query's slice must equal the oracle's definitional join of the query's
 polygon subset at its eps over the points inside its viewport, bit for bit, in
-every launch mode, alone or in the mix.
+every launch mode, alone or in the mix, with binary search or with the
+per-query learned index (which must report no fallback).
 """
 import numpy as np
 import pytest
@@ -155,3 +156,56 @@ def test_lod_workload_full_size_sampled(cuda, sdblib, orc):
     sample = set(order[:3].tolist()) | set(order[-3:].tolist()) | set(
         rng.choice(len(rows), 10, replace=False).tolist())
     check_all(orc, T, pts, rows, qb.subset_ids, cnt, sm, which=sample)
+
+
+def test_learned_batch_vs_oracle(cuda, sdblib, orc, small):
+    """The per-query learned index: the same results as binary search in every
+    mode, after tuning changes, and equal to the oracle; no fallback; switching
+    back to binary search gives the same results again."""
+    torch = cuda
+    T, pts, rows, ids, b = small
+    ref = run_batch(torch, sdblib, b, sdblib.BATCH_PERSISTENT)
+    sdblib.batch_set_lookup(b, sdblib.LOOKUP_LEARNED)
+    inf = b.info()
+    assert inf.lookup == sdblib.LOOKUP_LEARNED and inf.indexed_queries > 0 and inf.n_leaves > 0
+    got = run_batch(torch, sdblib, b, sdblib.BATCH_PERSISTENT)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    assert sdblib.batch_fallbacks(b) == 0
+    check_all(orc, T, pts, rows, ids, got[0], got[1])
+    s = torch.cuda.Stream()
+    for mode in (sdblib.BATCH_PER_QUERY, sdblib.BATCH_GRAPH, sdblib.BATCH_GRAPH):
+        with torch.cuda.stream(s):
+            c2, s2 = run_batch(torch, sdblib, b, mode, stream=s)
+        assert np.array_equal(c2, ref[0]) and np.array_equal(s2, ref[1]), mode
+        assert sdblib.batch_fallbacks(b, s) == 0
+    for tile, ppt in ((1, 1), (37, 2), (4096, 4)):
+        sdblib.batch_set_tuning(b, tile, ppt)
+        got = run_batch(torch, sdblib, b, sdblib.BATCH_PERSISTENT)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), (tile, ppt)
+    sdblib.batch_set_lookup(b, sdblib.LOOKUP_BINARY)
+    assert b.info().lookup == sdblib.LOOKUP_BINARY and b.info().n_leaves == 0
+    got = run_batch(torch, sdblib, b, sdblib.BATCH_PERSISTENT)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    with pytest.raises(sdblib.SdbError) as e:
+        sdblib.batch_set_lookup(b, sdblib.LOOKUP_TABLE)
+    assert e.value.status == sdblib.SDB_EINVAL
+
+
+def test_learned_lod_full_size(cuda, sdblib, orc):
+    """The 4,096-query level-of-detail batch over 200M points: learned equals
+    binary search for every query, no fallback, sampled queries vs the oracle."""
+    torch = cuda
+    T, pts, qb = W.lod_workload()
+    rows = [tuple(r) for r in qb.queries]
+    p = sdblib.points_create(dev(torch, pts.x), dev(torch, pts.y), dev(torch, pts.attr), 28)
+    b = sdblib.batch_create(p, T, rows, qb.subset_ids)
+    ref = run_batch(torch, sdblib, b, sdblib.BATCH_PERSISTENT)
+    sdblib.batch_set_lookup(b, sdblib.LOOKUP_LEARNED)
+    assert b.info().indexed_queries > 0
+    got = run_batch(torch, sdblib, b, sdblib.BATCH_PERSISTENT)
+    assert sdblib.batch_fallbacks(b) == 0
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    ranges = b.query_ranges()
+    order = np.argsort(ranges)
+    check_all(orc, T, pts, rows, qb.subset_ids, got[0], got[1],
+              which=set(order[-4:].tolist()))

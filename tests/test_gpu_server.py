@@ -1,6 +1,7 @@
 """Continuous-batching server: every result equals the batch API's answer for
 the same query alone (and the oracle's), whatever batch it ran in, with or
-without the covering cache, batched or one launch per query."""
+without the covering cache, batched or one launch per query, with binary
+search or the learned index."""
 import threading
 import time
 
@@ -61,7 +62,9 @@ def serve(sdblib, T, p, queries, order, gap_s=0.0, **cfg):
 @pytest.mark.parametrize("cfg", [dict(workers=4, max_batch=16),
                                  dict(workers=2, max_batch=64, use_cache=False),
                                  dict(workers=1, max_batch=1, use_cache=False, per_query=True),
-                                 dict(workers=3, max_batch=8, cache_bytes=1 << 20)])
+                                 dict(workers=3, max_batch=8, cache_bytes=1 << 20),
+                                 dict(workers=4, max_batch=16, lookup=1),
+                                 dict(workers=2, max_batch=64, use_cache=False, lookup=1)])
 def test_server_matches_alone(cuda, sdblib, env, cfg):
     T, pts, p, queries, ref = env
     rng = np.random.default_rng(4)
@@ -102,3 +105,6 @@ def test_server_tickets_and_timeouts(cuda, sdblib, env):
         srv.submit((0, 0, 2 ** 21, 10, 64, 0, 1), np.array([0], np.uint32))  # outside the grid
     assert e.value.status == sdblib.SDB_EINVAL
     srv.destroy()
+    with pytest.raises(sdblib.SdbError) as e:  # the table lookup has no batched form
+        sdblib.server_create(p, T, lookup=sdblib.LOOKUP_TABLE)
+    assert e.value.status == sdblib.SDB_EINVAL
