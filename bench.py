@@ -367,6 +367,8 @@ def lookup_bytes(sdb, c, lookup):
     leaves = 32 * (1 << inf.index_leaf_bits) + 4 * 4097 if inf.index_leaf_bits else 0
     if lookup in (sdb.LOOKUP_TABLE, sdb.LOOKUP_TABLE_LEARNED):
         tab = 4 * (1 << inf.table_bits) + 8 * inf.table_mixed
+        if inf.table_sub_bits:
+            tab += 4 * (1 << (2 * inf.table_sub_bits)) * inf.table_mixed + 8 * inf.table_sub_mixed
         return tab + (leaves if lookup == sdb.LOOKUP_TABLE_LEARNED else 0)
     return inf.device_bytes
 
@@ -450,7 +452,8 @@ def main():
     res["join_ms"] = {"table_learned": dict(zip(map(str, w.eps), join_ms))}
     infos = [c.info() for c in covs]
     res["coverings"] = {str(e): {"ranges": i.n_ranges, "cells": i.n_cells,
-                                 "covering_bytes": i.device_bytes, "table_mixed": i.table_mixed}
+                                 "covering_bytes": i.device_bytes, "table_mixed": i.table_mixed,
+                                 "table_sub_mixed": i.table_sub_mixed}
                         for e, i in zip(w.eps, infos)}
     head_cnt, head_sm = cnt.clone(), sm.clone()
     fallbacks = [sdb.covering_fallbacks(c, stream) for c in covs]
@@ -867,6 +870,7 @@ def config3_leg(args, sdb, torch, dev, stream, T, pts):
     out["plain_value"] = rows["binary"]["points_per_s"]
     inf = cov.info()
     out["table_mixed"] = inf.table_mixed
+    out["table_sub_mixed"] = inf.table_sub_mixed
     mw, xw = sdb.covering_index_stats(cov)
     out["learned_window_mean"] = mw
     peak, peak_kind = peaks()

@@ -115,6 +115,8 @@ typedef struct sdb_covering_info {
   uint32_t boundary_flags; /* 1 if built with SDB_COVER_BOUNDARY_FLAGS */
   uint32_t table_bits;     /* cell table: 2^table_bits buckets (0: no table, or F = 0) */
   uint64_t table_mixed;    /* buckets of the cell table that hold several ranges */
+  uint32_t table_sub_bits; /* second level: 2^s x 2^s sub-cells per mixed bucket (0: none) */
+  uint64_t table_sub_mixed;/* sub-cells that hold several ranges */
 } sdb_covering_info;
 
 /* Finest level for (grid_bits, eps), Sec. 2.2 (side eps/sqrt(2), so the
@@ -209,8 +211,12 @@ sdb_status sdb_covering_build_index(sdb_covering *cov, uint32_t leaf_bits, void 
  * entry follows from its coordinates without encoding its cell id.  A bucket that lies inside one range stores that range's
  * polygon payload, so a point in it needs one table read; a bucket that meets
  * several ranges stores the first and last of them, and the lookup binary
- * searches that window of range starts.  Table: 4 bytes per bucket, plus 8
- * bytes per mixed bucket.  Replaces a previous table.  Synchronises
+ * searches that window of range starts.  A second level (the tree's next
+ * levels) splits every mixed bucket into s x s sub-cells, s = 2^min(3, F - T/2),
+ * stored the same way, so a point in a mixed bucket makes one more read and
+ * searches only inside a sub-cell that meets several ranges.  Table: 4 bytes
+ * per bucket, 8 per mixed bucket, 4 s^2 per mixed bucket for the second level
+ * and 8 per mixed sub-cell.  Replaces a previous table.  Synchronises
  * cuda_stream.  SDB_EINVAL: table_bits outside 8..26, or R >= 2^30 - 1. */
 sdb_status sdb_covering_build_table(sdb_covering *cov, uint32_t table_bits, void *cuda_stream);
 

@@ -174,7 +174,8 @@ static void free_covering(sdb_covering* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   void* ps[] = {c->start,  c->list_off, c->list_ids, c->pay,    c->sample,
-                c->leaves, c->knots,    c->fallbacks, c->tab,   c->win};
+                c->leaves, c->knots,    c->fallbacks, c->tab,   c->win,
+                c->sub,    c->win2};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, 0);
   cudaStreamSynchronize(0);
@@ -509,11 +510,16 @@ sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* inf
   info->n_cells = cov->ncells;
   info->device_bytes =
       cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) + (4ull << cov->knot_bits) + 4 : 0);
-  if (cov->tab) info->device_bytes += (4ull << cov->tab_bits) + 8ull * cov->tab_mixed;
+  if (cov->tab)
+    info->device_bytes += (4ull << cov->tab_bits) + 8ull * cov->tab_mixed +
+                          (4ull << (2 * cov->sub_bits)) * (cov->sub ? cov->tab_mixed : 0) +
+                          8ull * cov->sub_mixed;
   info->index_leaf_bits = cov->leaf_bits;
   info->boundary_flags = cov->flagged ? 1u : 0u;
   info->table_bits = cov->tab ? cov->tab_bits : 0u;
   info->table_mixed = cov->tab_mixed;
+  info->table_sub_bits = cov->sub ? cov->sub_bits : 0u;
+  info->table_sub_mixed = cov->sub_mixed;
   return SDB_OK;
 }
 

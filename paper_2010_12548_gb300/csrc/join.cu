@@ -76,8 +76,12 @@ struct JoinArgs {
   // cell table: the entry of a point is at (y >> txy) << tlev | (x >> txy)
   // (row-major cells of level tlev)
   const uint32_t* tab;
-  const uint2* win;
+  const uint2* win;  // windows of the mixed cells of the last table level
   uint32_t txy, tlev;
+  // second table level (sub == nullptr: none): sub-cell of a point in mixed
+  // bucket m at sub[m << 2 s2 | ((y >> txy2) & S-1) << s2 | ((x >> txy2) & S-1)]
+  const uint32_t* sub;
+  uint32_t s2, txy2;
 };
 
 // last r in [0, R) with start[r] <= h, global memory only (fallback path)
@@ -369,10 +373,10 @@ struct QEnt {
   int32_t a;
 };
 
-// the range of a point in mixed bucket m: its finest cell id, then a binary
-// search of the bucket's window of range starts (w.x = the range holding the
-// bucket's first id, w.y = the range holding its last, so start[w.x] <= h <
-// start[w.y + 1]).  With the learned index (LOOKUP == SDB_LOOKUP_TABLE_LEARNED)
+// the range of a point in mixed cell m of the table's last level (a bucket, or
+// a sub-cell of the second level): its finest cell id, then a binary search of
+// the cell's window of range starts (w.x = the range holding the cell's first
+// id, w.y = the range holding its last, so start[w.x] <= h < start[w.y + 1]).  With the learned index (LOOKUP == SDB_LOOKUP_TABLE_LEARNED)
 // the search runs over the model's error window cut to the bucket's window;
 // an end of the result no probe has proven is read, and a result that does not
 // bracket h falls back to the bucket's whole window (counted).
@@ -528,6 +532,15 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         e[q] = ok[q] ? __ldg(A.tab + (((ys[q] >> A.txy) << A.tlev) | (xs[q] >> A.txy))) : NONE;
+      if (A.sub) {  // a point in a mixed bucket reads its sub-cell's entry
+        const uint32_t smask = (1u << A.s2) - 1u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (e[q] >= TAB_MIXED && e[q] != NONE)
+            e[q] = __ldg(A.sub + (((uint64_t)(e[q] & ~TAB_MIXED) << (2 * A.s2)) |
+                                  (((ys[q] >> A.txy2) & smask) << A.s2) |
+                                  ((xs[q] >> A.txy2) & smask)));
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const bool mix = e[q] >= TAB_MIXED && e[q] != NONE;
@@ -798,9 +811,12 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.nleaves = cov->leaf_bits ? (1u << cov->leaf_bits) : 0u;
   A.fallbacks = cov->fallbacks;
   A.tab = cov->tab;
-  A.win = cov->win;
+  A.win = cov->sub ? cov->win2 : cov->win;
   A.tlev = cov->tab_bits / 2;
   A.txy = cov->B - A.tlev;
+  A.sub = cov->sub;
+  A.s2 = cov->sub_bits;
+  A.txy2 = A.txy - cov->sub_bits;
   A.bcount = reinterpret_cast<unsigned long long*>(bcount);
   A.bsum = reinterpret_cast<unsigned long long*>(bsum);
   A.babs = reinterpret_cast<unsigned long long*>(babs);

@@ -183,6 +183,13 @@ struct sdb_covering {
   uint2* win = nullptr;     // first and last range of each mixed bucket
   uint32_t tab_bits = 0, tab_shift = 0;
   uint64_t tab_mixed = 0;
+  // the table's second level: every mixed bucket split into 2^sub_bits x
+  // 2^sub_bits sub-cells (row-major), each a payload or TAB_MIXED | index into
+  // win2 (sub_bits = 0: no second level)
+  uint32_t* sub = nullptr;
+  uint2* win2 = nullptr;
+  uint32_t sub_bits = 0;
+  uint64_t sub_mixed = 0;
   size_t bytes = 0;
 };
 

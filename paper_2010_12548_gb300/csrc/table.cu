@@ -20,6 +20,11 @@
 // r < R; with R < 2^30 - 1 the values TAB_MIXED | m (m < 2^30 - 1) are disjoint
 // from all of them.  For a mixed cell the range of a point's finest id h is the
 // last r in [r0, r1] with start[r] <= h.
+//
+// A second level (the next levels of the same tree) splits each mixed bucket
+// into up to 8 x 8 sub-cells, stored row-major per bucket with the same entry
+// encoding (TAB_MIXED | m2 indexing win2), so a point in a mixed bucket makes
+// one more read and searches only when its sub-cell meets several ranges.
 #include "sdb_internal.cuh"
 
 namespace sdb {
@@ -167,14 +172,68 @@ __global__ void table_mixed_kernel(const uint64_t* __restrict__ start, uint64_t 
                                    uint32_t shift, uint32_t L0, uint64_t nb,
                                    const uint32_t* __restrict__ mixed,
                                    const uint32_t* __restrict__ rank, uint32_t* __restrict__ tab,
-                                   uint2* __restrict__ win) {
+                                   uint2* __restrict__ win, uint32_t* __restrict__ mpos) {
   for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nb;
        b += (uint64_t)gridDim.x * blockDim.x) {
     if (!mixed[b]) continue;
     const uint64_t lo = b << shift, hi = lo + ((1ull << shift) - 1);
     const uint32_t m = rank[b];
-    tab[bucket_cell(b, L0)] = TAB_MIXED | m;
+    const uint64_t pos = bucket_cell(b, L0);
+    tab[pos] = TAB_MIXED | m;
     win[m] = make_uint2(last_le(start, R, lo), last_le(start, R, hi));
+    mpos[m] = (uint32_t)pos;
+  }
+}
+
+// last r in [a, b] with start[r] <= h (start[a] <= h)
+__device__ __forceinline__ uint32_t last_le_in(const uint64_t* __restrict__ start, uint32_t a,
+                                               uint32_t b, uint64_t h) {
+  uint32_t lo = a, len = b - a + 1;
+  while (len > 1) {
+    const uint32_t half = len >> 1;
+    if (__ldg(start + lo + half) <= h) lo += half;
+    len -= half;
+  }
+  return lo;
+}
+
+// The second level.  Mixed bucket m (row-major cell pos = mpos[m] of level L0)
+// splits into S x S sub-cells of level L1 = L0 + s2 (S = 2^s2), stored
+// row-major within the bucket at sub[m * S^2 + (sy << s2 | sx)].  A sub-cell is
+// again a quadtree cell, so its finest ids are one contiguous block
+// [hs << 2 (F - L1), (hs + 1) << 2 (F - L1)), hs its curve id at level L1; the
+// ranges holding the block's first and last id lie in the bucket's window.
+// Pass 1 (write = false) flags the sub-cells that meet several ranges and
+// stores the payload of the others; pass 2 writes TAB_MIXED | m2 and the
+// window of the m2-th flagged sub-cell.
+__global__ void table_sub_kernel(const uint64_t* __restrict__ start, const uint32_t* __restrict__ pay,
+                                 const uint2* __restrict__ win, const uint32_t* __restrict__ mpos,
+                                 uint64_t M, uint32_t L0, uint32_t s2, uint32_t F,
+                                 uint32_t* __restrict__ sub, uint32_t* __restrict__ flag,
+                                 const uint32_t* __restrict__ rank2, uint2* __restrict__ win2,
+                                 bool write) {
+  const uint64_t per = 1ull << (2 * s2);
+  const uint32_t L1 = L0 + s2, sh = 2 * (F - L1);
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < M * per;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t m = t >> (2 * s2);
+    const uint32_t j = (uint32_t)(t & (per - 1));
+    if (write && !flag[t]) continue;
+    const uint32_t pos = mpos[m];
+    const uint32_t cx = pos & ((1u << L0) - 1u), cy = pos >> L0;
+    const uint32_t sx = j & ((1u << s2) - 1u), sy = j >> s2;
+    const uint64_t hs = hilbert_id((cx << s2) | sx, (cy << s2) | sy, L1);
+    const uint64_t lo = hs << sh, hi = lo + ((1ull << sh) - 1);
+    const uint2 w = win[m];
+    const uint32_t r0 = last_le_in(start, w.x, w.y, lo), r1 = last_le_in(start, r0, w.y, hi);
+    if (!write) {
+      flag[t] = r0 != r1 ? 1u : 0u;
+      if (r0 == r1) sub[t] = pay[r0];
+    } else {
+      const uint32_t m2 = rank2[t];
+      sub[t] = TAB_MIXED | m2;
+      win2[m2] = make_uint2(r0, r1);
+    }
   }
 }
 
@@ -193,10 +252,16 @@ sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t
   const uint64_t nb = 1ull << T;
   if (cov->tab) dfree(cov->tab, s);
   if (cov->win) dfree(cov->win, s);
+  if (cov->sub) dfree(cov->sub, s);
+  if (cov->win2) dfree(cov->win2, s);
   cov->tab = nullptr;
   cov->win = nullptr;
+  cov->sub = nullptr;
+  cov->win2 = nullptr;
   cov->tab_bits = 0;
   cov->tab_mixed = 0;
+  cov->sub_bits = 0;
+  cov->sub_mixed = 0;
   Scratch sc(s);
   uint32_t *mixed, *rank, *dtot, *mark, *tpre;
   const uint64_t nt = (nb + TT - 1) / TT;
@@ -225,17 +290,51 @@ sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t
   uint32_t M = 0;
   SDB_TRY_CUDA(cudaMemcpyAsync(&M, dtot, 4, cudaMemcpyDeviceToHost, s));
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
+  // second level: sub-cells of 2^s2 x 2^s2 per mixed bucket, s2 <= 3 whole
+  // levels above the finest, while the sub-cell count keeps indices in range
+  const uint32_t L0 = T / 2;
+  uint32_t s2 = cov->F - L0 < 3 ? cov->F - L0 : 3;
+  while (s2 > 0 && (uint64_t)M << (2 * s2) >= (uint64_t)TAB_MIXED_MAX) --s2;
+  uint64_t M2 = 0;
   if (M > 0) {
+    uint32_t* mpos;
+    SDB_TRY(sc.get(&mpos, M));
     SDB_TRY(dalloc_n(&cov->win, M, s));
-    table_mixed_kernel<<<grid, 256, 0, s>>>(cov->start, cov->R, shift, T / 2, nb, mixed, rank,
-                                            cov->tab, cov->win);
+    table_mixed_kernel<<<grid, 256, 0, s>>>(cov->start, cov->R, shift, L0, nb, mixed, rank,
+                                            cov->tab, cov->win, mpos);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
+    if (s2 > 0) {
+      const uint64_t ns = M << (2 * s2);
+      uint32_t *flag2, *rank2;
+      SDB_TRY(dalloc_n(&cov->sub, ns, s));
+      SDB_TRY(sc.get(&flag2, ns));
+      SDB_TRY(sc.get(&rank2, ns));
+      const unsigned g2 = grid_for(ns, 256);
+      table_sub_kernel<<<g2, 256, 0, s>>>(cov->start, cov->pay, cov->win, mpos, M, L0, s2,
+                                          cov->F, cov->sub, flag2, nullptr, nullptr, false);
+      note_launch();
+      SDB_TRY_CUDA(cudaGetLastError());
+      SDB_TRY(exclusive_scan<uint32_t>(flag2, rank2, ns, dtot, s));
+      uint32_t m2 = 0;
+      SDB_TRY_CUDA(cudaMemcpyAsync(&m2, dtot, 4, cudaMemcpyDeviceToHost, s));
+      SDB_TRY_CUDA(cudaStreamSynchronize(s));
+      M2 = m2;
+      if (M2 > 0) {
+        SDB_TRY(dalloc_n(&cov->win2, M2, s));
+        table_sub_kernel<<<g2, 256, 0, s>>>(cov->start, cov->pay, cov->win, mpos, M, L0, s2,
+                                            cov->F, cov->sub, flag2, rank2, cov->win2, true);
+        note_launch();
+        SDB_TRY_CUDA(cudaGetLastError());
+      }
+    }
   }
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   cov->tab_bits = T;
   cov->tab_shift = shift;
   cov->tab_mixed = M;
+  cov->sub_bits = cov->sub ? s2 : 0;
+  cov->sub_mixed = M2;
   return SDB_OK;
 }
 

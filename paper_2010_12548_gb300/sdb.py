@@ -58,7 +58,8 @@ class CoveringInfo(C.Structure):
                 ("n_ranges", C.c_uint64), ("n_list_ids", C.c_uint64), ("n_cells", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("index_leaf_bits", C.c_uint32),
                 ("boundary_flags", C.c_uint32), ("table_bits", C.c_uint32),
-                ("table_mixed", C.c_uint64)]
+                ("table_mixed", C.c_uint64), ("table_sub_bits", C.c_uint32),
+                ("table_sub_mixed", C.c_uint64)]
 
 
 class Query(C.Structure):
