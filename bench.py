@@ -892,8 +892,101 @@ def config3_leg(args, sdb, torch, dev, stream, T, pts):
                                  and np.array_equal(sm.cpu().numpy(), os_))
     out["oracle_check"] = f"{len(idx)} points (every {max(1, n // 2_000_000)}th), O2"
     cov.free()
-    del xs, ys, at, cnt, sm
+    del cnt, sm
     torch.cuda.empty_cache()
+    # eps = 2^5 itself, tiled: the grid's 32 x 32 level-5 quadtree cells as
+    # viewport queries over the resident (Hilbert-ordered) points, 32 tiles a
+    # batch; per polygon the tiles' answers add up to the whole grid's
+    out["tiled"] = config3_tiled(sdb, torch, dev, stream, T, xs, ys, at, pts, n, idx)
+    del xs, ys, at
+    torch.cuda.empty_cache()
+    return out
+
+
+C3_TILE_LEVEL, C3_TILED_EPS, C3_TILES_PER_BATCH = 5, 2 ** 5, 32
+
+
+def tiled_join(sdb, torch, dev, stream, T, p, qb, lookups, timing=True):
+    """Per polygon COUNT and SUM over all tiles for each lookup (device tensors),
+    with the build and join times."""
+    from paper_2010_12548_gb300 import workloads as W  # noqa: F401
+    P = T.n
+    rows = [tuple(int(v) for v in r) for r in qb.queries]
+    tot = {lk: (torch.zeros(P, dtype=torch.int64, device=dev),
+                torch.zeros(P, dtype=torch.int64, device=dev)) for lk in lookups}
+    build_s, join_ms = 0.0, {lk: 0.0 for lk in lookups}
+    cells = ranges = max_ranges = 0
+    fallbacks = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for g0 in range(0, len(rows), C3_TILES_PER_BATCH):
+        grp = rows[g0:g0 + C3_TILES_PER_BATCH]
+        base = grp[0][5]
+        end = grp[-1][5] + grp[-1][6]
+        ids = qb.subset_ids[base:end]
+        grp = [r[:5] + (r[5] - base, r[6]) for r in grp]
+        t = time.perf_counter()
+        b = sdb.batch_create(p, T, grp, ids, stream)
+        build_s += time.perf_counter() - t
+        inf = b.info()
+        cells += inf.n_cells
+        ranges += inf.n_ranges
+        max_ranges = max(max_ranges, inf.max_ranges)
+        idt = torch.from_numpy(ids.astype(np.int64)).to(dev)
+        cnt = torch.zeros(max(1, inf.out_len), dtype=torch.int64, device=dev)
+        sm = torch.zeros(max(1, inf.out_len), dtype=torch.int64, device=dev)
+        for lk in lookups:
+            sdb.batch_set_lookup(b, lk, stream)
+            if timing:
+                sdb.batch_run(b, sdb.BATCH_PERSISTENT, cnt, sm, stream)  # warm
+            e0.record(stream)
+            sdb.batch_run(b, sdb.BATCH_PERSISTENT, cnt, sm, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            join_ms[lk] += e0.elapsed_time(e1)
+            if lk == sdb.LOOKUP_LEARNED:
+                fallbacks += sdb.batch_fallbacks(b, stream)
+            tot[lk][0].index_add_(0, idt, cnt[:inf.out_len])
+            tot[lk][1].index_add_(0, idt, sm[:inf.out_len])
+        b.free()
+        del cnt, sm, idt
+    return tot, {"build_s": build_s, "join_ms": join_ms, "cells": cells, "ranges": ranges,
+                 "max_ranges_per_tile": max_ranges, "fallbacks": fallbacks}
+
+
+def config3_tiled(sdb, torch, dev, stream, T, xs, ys, at, pts, n, idx):
+    from oracle import oracle as O
+    from paper_2010_12548_gb300 import workloads as W
+    qb = W.tile_queries(T, 28, C3_TILE_LEVEL, C3_TILED_EPS)
+    t = time.perf_counter()
+    p = sdb.points_create(xs, ys, at, 28, stream)
+    torch.cuda.synchronize()
+    resident_s = time.perf_counter() - t
+    lks = (sdb.LOOKUP_LEARNED, sdb.LOOKUP_BINARY)
+    tot, st = tiled_join(sdb, torch, dev, stream, T, p, qb, lks)
+    p.free()
+    out = {"eps": C3_TILED_EPS, "tiles": len(qb.queries), "tile_level": C3_TILE_LEVEL,
+           "tiles_per_batch": C3_TILES_PER_BATCH, "resident_set_s": resident_s,
+           "covering_build_s": st["build_s"], "cells": st["cells"], "ranges": st["ranges"],
+           "max_ranges_per_tile": st["max_ranges_per_tile"], "learned_fallbacks": st["fallbacks"],
+           "learned_join_ms": st["join_ms"][sdb.LOOKUP_LEARNED],
+           "binary_join_ms": st["join_ms"][sdb.LOOKUP_BINARY]}
+    out["learned_points_per_s"] = n / (out["learned_join_ms"] / 1e3)
+    out["binary_points_per_s"] = n / (out["binary_join_ms"] / 1e3)
+    a, b = tot[sdb.LOOKUP_LEARNED], tot[sdb.LOOKUP_BINARY]
+    out["lookups_agree"] = bool(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]))
+    out["every_point_counted"] = bool(int(a[0].sum().item()) >= n)
+    # the sample, tiled the same way, against the definitional test at eps 2^5
+    ti = torch.from_numpy(idx.astype(np.int64)).to(dev)
+    sp = sdb.points_create(xs[ti].contiguous(), ys[ti].contiguous(), at[ti].contiguous(), 28,
+                           stream)
+    stot, _ = tiled_join(sdb, torch, dev, stream, T, sp, qb, (sdb.LOOKUP_LEARNED,), timing=False)
+    sp.free()
+    sample = pts.take(idx)
+    oc, os_, _ = O.join_o2(T, C3_TILED_EPS, sample, threads=os.cpu_count() or 1)
+    c, s_ = stot[sdb.LOOKUP_LEARNED]
+    out["matches_oracle"] = bool(np.array_equal(c.cpu().numpy().view(np.uint64), oc)
+                                 and np.array_equal(s_.cpu().numpy(), os_))
+    out["oracle_check"] = f"{len(idx)} sampled points tiled the same way vs O2 at eps 2^5"
     return out
 
 

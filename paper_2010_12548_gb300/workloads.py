@@ -601,6 +601,30 @@ def lod_queries(seed: int, n: int, polys: Polygons, side=(2 ** 14, 2 ** 24),
                       np.concatenate(ids) if ids else np.zeros(0, np.uint32))
 
 
+def tile_queries(polys: Polygons, grid_bits: int, tile_level: int, eps: int,
+                 margin: int = 1 << 12) -> QueryBatch:
+    """The grid cut into 4^tile_level square tiles (quadtree cells of level
+    tile_level, row-major), one viewport query per tile at eps, its subset the
+    polygons whose bounding box, grown by ``margin`` grid units, meets the tile
+    (a superset of the polygons that can reach it for any finest side up to the
+    margin).  The queries of all tiles together partition the grid, so the
+    per-polygon sums of their answers are the whole grid's answer."""
+    side = 1 << (grid_bits - tile_level)
+    bb = polygon_bboxes(polys)
+    rows, ids, off = [], [], 0
+    n = 1 << tile_level
+    for ty in range(n):
+        for tx in range(n):
+            x0, y0 = tx * side, ty * side
+            x1, y1 = x0 + side, y0 + side
+            hit = np.nonzero((bb[:, 0] - margin < x1) & (bb[:, 2] + margin >= x0) &
+                             (bb[:, 1] - margin < y1) & (bb[:, 3] + margin >= y0))[0]
+            rows.append((x0, y0, x1, y1, eps, off, len(hit)))
+            ids.append(hit.astype(np.uint32))
+            off += len(hit)
+    return QueryBatch(np.asarray(rows, np.int64), np.concatenate(ids))
+
+
 def resident_points(n_points: int) -> Points:
     """Points on [0,2^28)^2 for the level-of-detail and serving workloads: 70%
     from 64 Gaussian clusters (sigma in [2^20, 2^23], clipped), 30% uniform.
