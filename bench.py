@@ -47,12 +47,14 @@ LEAF_BITS_RANGE = (12, 20)
 LEAF_BITS = 16   # learned index of the timed join: 2^16 FP32 leaves
 TABLE_BITS = 22  # its first level, the cell table: 2^22 buckets (16 MB), fewer when 2F < 22
 # DRAM bytes (read + write) per point of one join_kernel launch at eps = 2^6 on
-# the default workload, from one ncu capture of that launch (20M-point case,
-# scaled per point): profiles/join_kernel_table_learned_eps64_zones263_mobility20M.txt
-JOIN_FINEST_TRAFFIC = {}
-# DRAM bytes per launch (mean over the passes) of radix_scatter_kernel in the
+# the default workload, from one ncu capture of that launch on the 20M-point
+# case, scaled to 100M points per point (an upper bound: the table structures'
+# share is read once per launch):
+# profiles/join_kernel_table_learned_eps64_zones263_mobility20M.txt
+JOIN_FINEST_TRAFFIC = {"table_learned": {"eps": 64, "leaf_bits": 16, "bytes_per_point": 14.505}}
+# DRAM bytes of one launch of radix_scatter_kernel (a keys-only pass) in the
 # sweep's record sort: profiles/radix_scatter_kernel_sweep_zones263.txt
-SCATTER_TRAFFIC = {"records": 117_378_603, "passes": 5, "bytes": 1.9478e9}
+SCATTER_TRAFFIC = {"records": 117_378_603, "passes": 5, "bytes": 1.8595e9}
 
 
 def leaf_bits_for(n_ranges: int) -> int:
@@ -632,10 +634,12 @@ def main():
             rng_rows[str(eps)] = row
             c.free()
         res["range_estimation"] = rng_rows
-    # ---- end to end through the C ABI from host buffers: the sweep's coverings
-    # from the host polygons, the table and the learned index, and the
-    # host-buffer join (points copied from pinned host memory inside the call,
-    # results copied back)
+    # ---- end to end through the C ABI from host buffers.  e2e: the timed
+    # step's metric through the host-buffer entry point -- every step copies the
+    # points from pinned host memory (chunked, copies overlapping the joins) and
+    # reads the results back, against the resident coverings and lookup
+    # structures.  e2e_with_build adds, every step, the sweep's covering build
+    # from the host polygons and the table and index fits.
     if "e2e" in legs:
         hx = torch.from_numpy(w.points.x.view(np.int32)).pin_memory()
         hy = torch.from_numpy(w.points.y.view(np.int32)).pin_memory()
@@ -643,29 +647,50 @@ def main():
         hc = torch.zeros((E, P), dtype=torch.int64).pin_memory()
         hs = torch.zeros((E, P), dtype=torch.int64).pin_memory()
 
-        def e2e_step():
+        def host_join(cs):
+            sdb.join_aggregate_host_ptrs(hx.data_ptr(), hy.data_ptr(), ha.data_ptr(), N, cs,
+                                         HEAD, hc.data_ptr(), hs.data_ptr(), stream)
+
+        def e2e_build_step():
             cs = sdb.build_coverings(w.polygons, 24, w.eps, stream)
             for c in cs:
                 lookup_prep(sdb, c, HEAD, stream)
-            sdb.join_aggregate_host_ptrs(hx.data_ptr(), hy.data_ptr(), ha.data_ptr(), N, cs,
-                                         HEAD, hc.data_ptr(), hs.data_ptr(), stream)
+            host_join(cs)
             for c in cs:
                 c.free()
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        torch.cuda.synchronize()
-        tt = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - tt) / args.steps
-        e2e_s = max_over_ranks(ws, e2e_s)
-        res["e2e"] = {"value": job_rate(ws, N * E, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * 12,
-                      "d2h_bytes_per_step": E * P * 16, "ms_per_step": e2e_s * 1e3,
-                      "what": "host polygons -> sweep coverings, cell tables, learned indexes "
-                              "-> host-buffer join (H2D of the points inside) -> host results"}
-        res["e2e"]["matches_device"] = bool(np.array_equal(hc.numpy(), head_cnt.cpu().numpy()) and
-                                            np.array_equal(hs.numpy(), head_sm.cpu().numpy()))
+
+        def wall(fn, steps, warm):
+            for _ in range(warm):
+                fn()
+            torch.cuda.synchronize()
+            tt = time.perf_counter()
+            for _ in range(steps):
+                fn()
+            torch.cuda.synchronize()
+            return max_over_ranks(ws, (time.perf_counter() - tt) / steps)
+
+        cs = sdb.build_coverings(w.polygons, 24, w.eps, stream)
+        for c in cs:
+            lookup_prep(sdb, c, HEAD, stream)
+        e2e_s = wall(lambda: host_join(cs), args.steps, max(3, args.warmup))
+        same = bool(np.array_equal(hc.numpy(), head_cnt.cpu().numpy()) and
+                    np.array_equal(hs.numpy(), head_sm.cpu().numpy()))
+        for c in cs:
+            c.free()
+        res["e2e"] = {"value": job_rate(ws, N * E, e2e_s), "unit": UNIT,
+                      "h2d_bytes_per_step": N * 12, "d2h_bytes_per_step": E * P * 16,
+                      "ms_per_step": e2e_s * 1e3, "matches_device": same,
+                      "what": "sdb_join_aggregate_host: points copied from pinned host memory "
+                              "every step (chunks, copies overlapping the joins), the four "
+                              "joins against the resident coverings, results read back"}
+        eb_s = wall(e2e_build_step, max(3, args.steps // 4), 1)
+        res["e2e_with_build"] = {
+            "value": job_rate(ws, N * E, eb_s), "unit": UNIT, "ms_per_step": eb_s * 1e3,
+            "h2d_bytes_per_step": N * 12, "d2h_bytes_per_step": E * P * 16,
+            "matches_device": bool(np.array_equal(hc.numpy(), head_cnt.cpu().numpy()) and
+                                   np.array_equal(hs.numpy(), head_sm.cpu().numpy())),
+            "what": "host polygons -> sweep coverings, cell tables, learned indexes -> "
+                    "host-buffer join -> host results, every step"}
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and ws == 1 and "cpu" in legs:
         threads = os.cpu_count() or 1

@@ -249,8 +249,24 @@ __device__ __forceinline__ uint32_t slice_learned(const uint64_t* __restrict__ s
   return slice_bs(st, Q.R, h);
 }
 
+// Per-block accumulators of a work item's query slots in shared memory (when
+// the query has at most BATCH_SMEM_SLOTS slots): a count and the attribute
+// split exactly into its low 16 bits and the rest; a work item holds at most
+// 2^16 points, so none can wrap (2^16 * 65535 < 2^32, 2^16 * 2^15 <= 2^31), and
+// the item's totals go to the outputs with one global atomic each.
+constexpr uint32_t BATCH_SMEM_SLOTS = 2048;
+constexpr uint32_t BATCH_MAX_TILE = 1u << 16;
+
 __device__ __forceinline__ void add_slot(const BatchArgs& A, uint32_t out, uint32_t p, int32_t a,
-                                         bool sum) {
+                                         bool sum, uint32_t* s_acc, uint32_t ns) {
+  if (s_acc) {
+    atomicAdd(&s_acc[p], 1u);
+    if (sum) {
+      atomicAdd(&s_acc[ns + p], (uint32_t)a & 0xffffu);
+      atomicAdd(reinterpret_cast<int32_t*>(&s_acc[2 * ns + p]), a >> 16);
+    }
+    return;
+  }
   atomicAdd(&A.count[out + p], 1ull);
   if (sum) atomicAdd(&A.sum[out + p], (unsigned long long)(long long)a);
 }
@@ -261,6 +277,7 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
                                                         unsigned long long* head) {
   __shared__ uint32_t tab[HILBERT3_SMEM_WORDS];
   __shared__ uint32_t s_tile;
+  extern __shared__ uint32_t s_slots[];  // (SUM ? 3 : 1) * BATCH_SMEM_SLOTS words
   hilbert3_fill(tab);
   __syncthreads();
   for (;;) {
@@ -272,6 +289,14 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
     const TileRec tr = A.tiles[t];
     const QueryDev Q = A.q[tr.q];
     const ChunkDev C = A.chunks[Q.chunk];
+    // block-uniform: the work item's query decides where its sums gather
+    const uint32_t ns = Q.npoly;
+    uint32_t* s_acc = (ns <= BATCH_SMEM_SLOTS && tr.end - tr.begin <= BATCH_MAX_TILE) ? s_slots
+                                                                                      : nullptr;
+    if (s_acc) {
+      for (uint32_t i = threadIdx.x; i < (SUM ? 3 : 1) * ns; i += THREADS) s_acc[i] = 0;
+      __syncthreads();
+    }
     for (uint32_t i0 = tr.begin + threadIdx.x * G; i0 < tr.end; i0 += THREADS * G) {
       uint64_t h[G];
       bool ok[G];
@@ -311,11 +336,26 @@ __global__ __launch_bounds__(THREADS) void batch_kernel(BatchArgs A, uint32_t ti
         const uint64_t e = Q.sbase + lo[g];
         const uint32_t p = __ldg(C.pay + e);
         if (p < 0x80000000u) {
-          add_slot(A, Q.out_off, p, av[g], SUM);
+          add_slot(A, Q.out_off, p, av[g], SUM, s_acc, ns);
         } else if (p != NONE) {
           const uint32_t rr = p & 0x7fffffffu;
           const uint32_t b = __ldg(C.list_off + rr), en = __ldg(C.list_off + rr + 1);
-          for (uint32_t j = b; j < en; ++j) add_slot(A, Q.out_off, __ldg(C.list_ids + j), av[g], SUM);
+          for (uint32_t j = b; j < en; ++j)
+            add_slot(A, Q.out_off, __ldg(C.list_ids + j), av[g], SUM, s_acc, ns);
+        }
+      }
+    }
+    if (s_acc) {  // the work item's totals into the query's output slots
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < ns; i += THREADS) {
+        const uint32_t c = s_acc[i];
+        if (!c) continue;
+        atomicAdd(&A.count[Q.out_off + i], (unsigned long long)c);
+        if (SUM) {
+          const long long tot =
+              (long long)reinterpret_cast<const int32_t*>(s_acc)[2 * ns + i] * 65536 +
+              (long long)s_acc[ns + i];
+          atomicAdd(&A.sum[Q.out_off + i], (unsigned long long)tot);
         }
       }
     }
@@ -442,12 +482,13 @@ template <int G, bool SUM>
 sdb_status launch_batch_t(const BatchArgs& A, uint32_t lo, uint32_t hi,
                           unsigned long long* head, cudaStream_t s) {
   auto kern = batch_kernel<G, SUM>;
+  const size_t smem = (size_t)(SUM ? 3 : 1) * BATCH_SMEM_SLOTS * 4;
   int per_sm = 0;
-  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0));
+  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
   uint64_t blocks = (uint64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
   if (blocks > hi - lo) blocks = hi - lo;
   if (blocks == 0) return SDB_OK;
-  kern<<<(unsigned)blocks, THREADS, 0, s>>>(A, lo, hi, head);
+  kern<<<(unsigned)blocks, THREADS, smem, s>>>(A, lo, hi, head);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
   return SDB_OK;
@@ -510,6 +551,7 @@ sdb_status batch_query_dev(uint32_t B, const sdb_query& Qu, uint64_t out_off, Ba
   d->x1 = Qu.x1;
   d->y1 = Qu.y1;
   d->out_off = (uint32_t)out_off;
+  d->npoly = Qu.poly_cnt;
   *F_out = F;
   return SDB_OK;
 }

@@ -305,7 +305,8 @@ struct BatchQueryDev {
   // learned index of the slice (nleaves = 0: binary search): ids below llo lie
   // in range 0, ids from lhi on in range R - 1; between them leaf
   // min(nleaves - 1, (h - llo) >> lwshift) of the batch's leaf array, from loff
-  uint32_t nleaves, loff, lwshift, pad;
+  uint32_t nleaves, loff, lwshift;
+  uint32_t npoly;  // output slots of the query (its subset's size)
   uint64_t llo, lhi;
 };
 struct BatchChunkDev {
