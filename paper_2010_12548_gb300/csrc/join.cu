@@ -458,22 +458,8 @@ __host__ __device__ inline size_t stage_bytes(int lookup, const JoinArgs& A) {
   return QUEUE_BYTES;
 }
 
-// resident blocks per SM the compiler is asked to fit (registers) for the
-// table lookups and for the searching lookups
-#ifndef SDB_JOIN_TABLE_MINB
-#define SDB_JOIN_TABLE_MINB 4
-#endif
-// 1: in the table lookups, lanes of a warp whose points share a single-polygon
-// payload add their count and attribute sum once (warp match + reductions)
-#ifndef SDB_JOIN_WARP_AGG
-#define SDB_JOIN_WARP_AGG 0
-#endif
-
 template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
-__global__ __launch_bounds__(THREADS, (LOOKUP == SDB_LOOKUP_TABLE ||
-                                       LOOKUP == SDB_LOOKUP_TABLE_LEARNED)
-                                          ? SDB_JOIN_TABLE_MINB
-                                          : 4) void join_kernel(JoinArgs A) {
+__global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   // the cell-id table, then the lookup staging (the binary search's sample of
   // range starts, the learned index's root knots, or the cell-table lookup's
@@ -565,33 +551,9 @@ __global__ __launch_bounds__(THREADS, (LOOKUP == SDB_LOOKUP_TABLE ||
           E.y = ys[q];
           E.m = e[q] & ~TAB_MIXED;
           E.a = as[q];
-        } else if (!(SDB_JOIN_WARP_AGG && SMEM && !RANGE && e[q] < 0x80000000u)) {
+        } else {
           add_pay<SMEM, SUM, RANGE>(e[q], as[q], acc, A);
         }
-#if SDB_JOIN_WARP_AGG
-        if constexpr (SMEM && !RANGE) {
-          // lanes holding the same single-polygon payload form one group; its
-          // first lane adds the group's count and attribute parts
-          const bool single = !mix && e[q] < 0x80000000u;
-          const unsigned g = __match_any_sync(FULL, single ? e[q] : 0x80000000u + lane);
-          if (single) {
-            uint32_t lo = 0;
-            int32_t hi = 0;
-            if (SUM) {
-              lo = __reduce_add_sync(g, (uint32_t)as[q] & 0xffffu);
-              hi = __reduce_add_sync(g, as[q] >> 16);
-            }
-            if (lane == (uint32_t)(__ffs(g) - 1)) {
-              const uint32_t p = e[q] & 0x3fffffffu;
-              atomicAdd(&acc.cnt[p], (uint32_t)__popc(g));
-              if (SUM) {
-                atomicAdd(&acc.lo[p], lo);
-                atomicAdd(&acc.hi[p], hi);
-              }
-            }
-          }
-        }
-#endif
         qn += __popc(bal);
         if (qn >= 32) {  // a full warp of held-back points: search their windows
           __syncwarp();
