@@ -82,6 +82,10 @@ struct JoinArgs {
   // bucket m at sub[m << 2 s2 | ((y >> txy2) & S-1) << s2 | ((x >> txy2) & S-1)]
   const uint32_t* sub;
   uint32_t s2, txy2;
+  // the tree's top level, staged in shared memory (top == nullptr: none): the
+  // entry of a point is at (y >> top_xy) << top_lev | (x >> top_xy)
+  const uint16_t* top;
+  uint32_t top_xy, top_lev;
 };
 
 // last r in [0, R) with start[r] <= h, global memory only (fallback path)
@@ -316,7 +320,7 @@ __device__ __forceinline__ void add_one(uint32_t p, int32_t a, uint32_t bnd, con
 
 template <bool SUM, bool RANGE>
 __device__ void flush_acc(const Acc& s, const JoinArgs& A) {
-  for (uint32_t i = threadIdx.x; i < A.P; i += THREADS) {
+  for (uint32_t i = threadIdx.x; i < A.P; i += blockDim.x) {
     const uint32_t c = s.cnt[i];
     if (c) {
       atomicAdd(&A.count[i], (unsigned long long)c);
@@ -450,37 +454,63 @@ __host__ __device__ constexpr size_t hilbert_bytes(int lookup) {
 
 // shared-memory bytes of the lookup's staging area (8-byte multiple): the
 // binary search's sample, the learned index's root knots, or the cell table's
-// per-warp queues
-constexpr size_t QUEUE_BYTES = (size_t)(THREADS / 32) * QCAP * sizeof(QEnt);
-__host__ __device__ inline size_t stage_bytes(int lookup, const JoinArgs& A) {
+// per-warp queues (blocks of tpb threads)
+__host__ __device__ inline size_t stage_bytes(int lookup, const JoinArgs& A, int tpb) {
   if (lookup == SDB_LOOKUP_BINARY) return (size_t)A.sample_n * 8;
   if (lookup == SDB_LOOKUP_LEARNED) return ((size_t)A.nknots * 4 + 7) & ~(size_t)7;
-  return QUEUE_BYTES;
+  return (size_t)(tpb / 32) * QCAP * sizeof(QEnt);
 }
 
-template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
-__global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
+// The table lookups with the tree's top level in shared memory run one block
+// of TOP_THREADS per SM (the level takes 128 KB); their accumulators are
+// flushed every TOP_FLUSH_TILES tiles, which keeps the same no-wrap bound.
+constexpr int TOP_THREADS = 1024;
+constexpr uint32_t TOP_FLUSH_TILES = 15;
+static_assert((uint64_t)(TOP_FLUSH_TILES * TOP_THREADS * 4 + (TOP_THREADS / 32) * (QCAP - 1)) *
+                      65535u < (1ull << 32),
+              "low-half counter could wrap");
+static_assert((uint64_t)(TOP_FLUSH_TILES * TOP_THREADS * 4 + (TOP_THREADS / 32) * (QCAP - 1)) *
+                      32768u < (1ull << 31),
+              "high-half counter could wrap");
+
+__host__ __device__ inline size_t top_bytes(const JoinArgs& A) {
+  return (size_t)2 << (2 * A.top_lev);
+}
+
+template <int LOOKUP, bool SMEM, bool SUM, bool RANGE, bool TOP = false>
+__global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? 1 : 4) void join_kernel(JoinArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int TPB = TOP ? TOP_THREADS : THREADS;
+  constexpr uint32_t FT = TOP ? TOP_FLUSH_TILES : FLUSH_TILES;
   // the cell-id table, then the lookup staging (the binary search's sample of
   // range starts, the learned index's root knots, or the cell-table lookup's
-  // per-warp queues), then the accumulators
+  // per-warp queues), then the accumulators, then (TOP) the tree's top level
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
   constexpr bool TABLE = LOOKUP == SDB_LOOKUP_TABLE || LOOKUP == SDB_LOOKUP_TABLE_LEARNED;
+  static_assert(!TOP || TABLE, "the top level belongs to the table lookups");
   constexpr size_t HB = hilbert_bytes(LOOKUP);
   uint64_t* s_sample = reinterpret_cast<uint64_t*>(smem + HB);
   float* s_knots = reinterpret_cast<float*>(smem + HB);
   QEnt* s_q = reinterpret_cast<QEnt*>(smem + HB) + (threadIdx.x >> 5) * QCAP;
-  const size_t off = HB + stage_bytes(LOOKUP, A);
+  const size_t off = HB + stage_bytes(LOOKUP, A, TPB);
   const Acc acc = acc_at<SUM, RANGE>(smem + off, SMEM ? A.P : 0);
+  const uint16_t* s_top =
+      reinterpret_cast<const uint16_t*>(smem + ((off + acc_bytes(SMEM ? A.P : 0, SUM, RANGE) +
+                                                 15) & ~(size_t)15));
 
   if constexpr (TABLE)
     hilbert3_fill_compact(s_tab);
   else
     hilbert3_fill(s_tab);
   if constexpr (LOOKUP == SDB_LOOKUP_BINARY)
-    for (uint32_t i = threadIdx.x; i < A.sample_n; i += THREADS) s_sample[i] = A.sample[i];
+    for (uint32_t i = threadIdx.x; i < A.sample_n; i += TPB) s_sample[i] = A.sample[i];
   if constexpr (LOOKUP == SDB_LOOKUP_LEARNED)
-    for (uint32_t i = threadIdx.x; i < A.nknots; i += THREADS) s_knots[i] = A.knots[i];
+    for (uint32_t i = threadIdx.x; i < A.nknots; i += TPB) s_knots[i] = A.knots[i];
+  if constexpr (TOP) {  // 16-byte copies of the top level (a multiple of 16 bytes)
+    const uint4* src = reinterpret_cast<const uint4*>(A.top);
+    uint4* dst = reinterpret_cast<uint4*>(const_cast<uint16_t*>(s_top));
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(top_bytes(A) / 16); i += TPB) dst[i] = __ldg(src + i);
+  }
   if (SMEM) acc_zero<SUM, RANGE>(acc, A.P);
   __syncthreads();
 
@@ -488,10 +518,10 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t qn = 0;  // entries in this warp's queue (warp-uniform)
   const uint32_t gmask = ~((1u << A.B) - 1u);
-  const uint64_t per_tile = (uint64_t)THREADS * 4;
+  const uint64_t per_tile = (uint64_t)TPB * 4;
   const uint64_t ntiles = (A.n + per_tile - 1) / per_tile;
   uint32_t since_flush = 0;
-  // block-uniform loop over tiles of 1024 consecutive points; thread t takes
+  // block-uniform loop over tiles of 4 TPB consecutive points; thread t takes
   // points 4t..4t+3 of the tile (a warp reads 512 contiguous bytes per array)
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t e0 = t * per_tile + (uint64_t)threadIdx.x * 4;
@@ -529,9 +559,25 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
       // coordinates (row-major table); only points in mixed cells need their
       // finest cell id
       uint32_t e[4];
+      if constexpr (TOP) {
+        // the top level answers points whose top cell lies in one range; the
+        // others read the table as below
+        bool ask[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        e[q] = ok[q] ? __ldg(A.tab + (((ys[q] >> A.txy) << A.tlev) | (xs[q] >> A.txy))) : NONE;
+        for (int q = 0; q < 4; ++q) {
+          const uint16_t v =
+              ok[q] ? s_top[((ys[q] >> A.top_xy) << A.top_lev) | (xs[q] >> A.top_xy)] : TOP_NONE;
+          ask[q] = v == TOP_ASK;
+          e[q] = v == TOP_NONE ? NONE : (uint32_t)v;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (ask[q]) e[q] = __ldg(A.tab + (((ys[q] >> A.txy) << A.tlev) | (xs[q] >> A.txy)));
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          e[q] = ok[q] ? __ldg(A.tab + (((ys[q] >> A.txy) << A.tlev) | (xs[q] >> A.txy))) : NONE;
+      }
       if (A.sub) {  // a point in a mixed bucket reads its sub-cell's entry
         const uint32_t smask = (1u << A.s2) - 1u;
 #pragma unroll
@@ -579,7 +625,7 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) add_pay<SMEM, SUM, RANGE>(pay[q], as[q], acc, A);
     }
-    if (SMEM && ++since_flush == FLUSH_TILES) {
+    if (SMEM && ++since_flush == FT) {
       since_flush = 0;
       __syncthreads();
       flush_acc<SUM, RANGE>(acc, A);
@@ -596,16 +642,18 @@ __global__ __launch_bounds__(THREADS, 4) void join_kernel(JoinArgs A) {
   }
 }
 
-template <int LOOKUP, bool SMEM, bool SUM, bool RANGE>
+template <int LOOKUP, bool SMEM, bool SUM, bool RANGE, bool TOP = false>
 sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
-  size_t smem = hilbert_bytes(LOOKUP) + stage_bytes(LOOKUP, A);
+  constexpr int TPB = TOP ? TOP_THREADS : THREADS;
+  size_t smem = hilbert_bytes(LOOKUP) + stage_bytes(LOOKUP, A, TPB);
   if (SMEM) smem += acc_bytes(A.P, SUM, RANGE);
   smem = (smem + 15) & ~(size_t)15;
-  auto kern = join_kernel<LOOKUP, SMEM, SUM, RANGE>;
+  if (TOP) smem += top_bytes(A);
+  auto kern = join_kernel<LOOKUP, SMEM, SUM, RANGE, TOP>;
   if (smem > 48 * 1024)
     SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
+  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, smem));
   if (per_sm < 1) per_sm = 1;
   // ask for no more shared memory than the resident blocks use (plus the 1 KB
   // the system reserves per block): the rest of the SM's unified memory stays
@@ -613,10 +661,10 @@ sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
   SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     carveout_pct((size_t)per_sm * (smem + 1024))));
   uint64_t blocks = (uint64_t)num_sms() * per_sm;
-  const uint64_t need = (A.n + 4 * THREADS - 1) / (4 * THREADS);  // tiles
+  const uint64_t need = (A.n + 4 * TPB - 1) / (4 * TPB);  // tiles
   if (blocks > need) blocks = need > 0 ? need : 1;
   TraceScope tr("join", s);
-  kern<<<(unsigned)blocks, THREADS, smem, s>>>(A);
+  kern<<<(unsigned)blocks, TPB, smem, s>>>(A);
   note_launch();
   SDB_TRY_CUDA(cudaGetLastError());
   return SDB_OK;
@@ -752,6 +800,22 @@ sdb_status launch_pick(const JoinArgs& A, int lookup, bool has_sum, cudaStream_t
       return has_sum ? launch_t<0, true, true, RANGE>(A, s) : launch_t<0, true, false, RANGE>(A, s);
     return has_sum ? launch_t<0, false, true, RANGE>(A, s) : launch_t<0, false, false, RANGE>(A, s);
   }
+  if constexpr (!RANGE) {  // the table lookups with the top level in shared memory
+    if (A.top && lookup == SDB_LOOKUP_TABLE) {
+      if (smem)
+        return has_sum ? launch_t<3, true, true, false, true>(A, s)
+                       : launch_t<3, true, false, false, true>(A, s);
+      return has_sum ? launch_t<3, false, true, false, true>(A, s)
+                     : launch_t<3, false, false, false, true>(A, s);
+    }
+    if (A.top && lookup == SDB_LOOKUP_TABLE_LEARNED) {
+      if (smem)
+        return has_sum ? launch_t<4, true, true, false, true>(A, s)
+                       : launch_t<4, true, false, false, true>(A, s);
+      return has_sum ? launch_t<4, false, true, false, true>(A, s)
+                     : launch_t<4, false, false, false, true>(A, s);
+    }
+  }
   if (lookup == SDB_LOOKUP_TABLE) {
     if (smem)
       return has_sum ? launch_t<3, true, true, RANGE>(A, s) : launch_t<3, true, false, RANGE>(A, s);
@@ -817,6 +881,9 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.sub = cov->sub;
   A.s2 = cov->sub_bits;
   A.txy2 = A.txy - cov->sub_bits;
+  A.top = cov->top;
+  A.top_lev = cov->top_level;
+  A.top_xy = cov->B - cov->top_level;
   A.bcount = reinterpret_cast<unsigned long long*>(bcount);
   A.bsum = reinterpret_cast<unsigned long long*>(bsum);
   A.babs = reinterpret_cast<unsigned long long*>(babs);

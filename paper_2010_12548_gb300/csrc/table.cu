@@ -237,6 +237,36 @@ __global__ void table_sub_kernel(const uint64_t* __restrict__ start, const uint3
   }
 }
 
+// The top level: cell (tx, ty) of level Lt covers the 2^d x 2^d cells of the
+// table's level L0 = Lt + d below it.  When all of them hold the same
+// single-polygon payload p (no mixed cell, no list, no boundary flag, p below
+// TOP_NONE) the whole cell lies in one range -- its ids are contiguous and the
+// canonical covering merges equal neighbours, so cells with equal payloads
+// side by side belong to one range -- and the entry is p; all empty gives
+// TOP_NONE; anything else TOP_ASK (the table decides).
+__global__ void table_top_kernel(const uint32_t* __restrict__ tab, uint32_t L0, uint32_t Lt,
+                                 uint16_t* __restrict__ top) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (1u << (2 * Lt))) return;
+  const uint32_t d = L0 - Lt, tx = c & ((1u << Lt) - 1u), ty = c >> Lt;
+  const uint32_t first = tab[((size_t)(ty << d) << L0) | (tx << d)];
+  bool same = true;
+  for (uint32_t j = 0; j < (1u << d) && same; ++j)
+    for (uint32_t i = 0; i < (1u << d); ++i)
+      if (tab[((size_t)((ty << d) + j) << L0) | ((tx << d) + i)] != first) {
+        same = false;
+        break;
+      }
+  uint16_t v = TOP_ASK;
+  if (same) {
+    if (first == 0xFFFFFFFFu)
+      v = TOP_NONE;
+    else if (first < (uint32_t)TOP_NONE)
+      v = (uint16_t)first;
+  }
+  top[c] = v;
+}
+
 }  // namespace
 
 sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t s) {
@@ -254,10 +284,13 @@ sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t
   if (cov->win) dfree(cov->win, s);
   if (cov->sub) dfree(cov->sub, s);
   if (cov->win2) dfree(cov->win2, s);
+  if (cov->top) dfree(cov->top, s);
   cov->tab = nullptr;
   cov->win = nullptr;
   cov->sub = nullptr;
   cov->win2 = nullptr;
+  cov->top = nullptr;
+  cov->top_level = 0;
   cov->tab_bits = 0;
   cov->tab_mixed = 0;
   cov->sub_bits = 0;
@@ -328,6 +361,16 @@ sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t
         SDB_TRY_CUDA(cudaGetLastError());
       }
     }
+  }
+  // the top level for shared memory (levels 4 .. TOP_MAX_LEVEL)
+  if (L0 >= 4) {
+    const uint32_t Lt = L0 < TOP_MAX_LEVEL ? L0 : TOP_MAX_LEVEL;
+    const uint32_t nt = 1u << (2 * Lt);
+    SDB_TRY(dalloc_n(&cov->top, nt, s));
+    table_top_kernel<<<(nt + 255) / 256, 256, 0, s>>>(cov->tab, L0, Lt, cov->top);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    cov->top_level = Lt;
   }
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
   cov->tab_bits = T;
