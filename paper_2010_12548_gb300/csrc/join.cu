@@ -42,6 +42,12 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t NONE = 0xffffffffu;
 constexpr int THREADS = 256;
 constexpr uint32_t SMEM_POLYS = 2048;
+#ifndef SDB_JOIN_PREFETCH
+#define SDB_JOIN_PREFETCH 1
+#endif
+#ifndef SDB_JOIN_HISKIP
+#define SDB_JOIN_HISKIP 1
+#endif
 constexpr uint32_t SMEM_POLYS_RANGE = 1024;  // 32 bytes of accumulators per polygon
 
 struct JoinArgs {
@@ -294,7 +300,11 @@ __device__ __forceinline__ void add_one(uint32_t p, int32_t a, uint32_t bnd, con
     atomicAdd(&s.cnt[p], 1u);
     if (SUM) {
       atomicAdd(&s.lo[p], (uint32_t)a & 0xffffu);
+#if SDB_JOIN_HISKIP
       if (a >> 16) atomicAdd(&s.hi[p], a >> 16);  // zero for attributes in [0, 2^16)
+#else
+      atomicAdd(&s.hi[p], a >> 16);
+#endif
     }
     if (RANGE && bnd) {
       atomicAdd(&s.bcnt[p], 1u);
@@ -536,7 +546,7 @@ __global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? 1 : 4) void join
     if (A.vec && e0 + 3 < A.n) {
       uint4 xv, yv;
       int4 av = make_int4(0, 0, 0, 0);
-      if (TABLE && have) {
+      if (TABLE && SDB_JOIN_PREFETCH && have) {
         xv = nx;
         yv = ny;
         av = na;
@@ -545,7 +555,7 @@ __global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? 1 : 4) void join
         yv = __ldcs(reinterpret_cast<const uint4*>(A.y + e0));
         if (SUM) av = __ldcs(reinterpret_cast<const int4*>(A.attr + e0));
       }
-      if constexpr (TABLE) {
+      if constexpr (TABLE && SDB_JOIN_PREFETCH) {
         const uint64_t e1 = e0 + (uint64_t)gridDim.x * per_tile;
         have = e1 + 3 < A.n;
         if (have) {

@@ -168,6 +168,13 @@ __global__ void digit_base_kernel(const unsigned long long* __restrict__ counts,
 constexpr unsigned long long LB_AGG = 1ull << 62, LB_INC = 2ull << 62;
 constexpr unsigned long long LB_VAL = (1ull << 62) - 1;
 constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;  // waits on one predecessor before giving up
+#ifndef SDB_SORT_LB_WINDOW
+#define SDB_SORT_LB_WINDOW 8
+#endif
+constexpr int LB_WINDOW = SDB_SORT_LB_WINDOW;  // predecessor words read per round
+#ifndef SDB_SORT_LOOKBACK
+#define SDB_SORT_LOOKBACK 1
+#endif
 
 __device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
   unsigned long long v;
@@ -270,23 +277,37 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
         lb_store(mine, LB_INC | total);
       } else {
         lb_store(mine, LB_AGG | total);
+        // predecessors' words LB_WINDOW at a time (independent loads), taken in
+        // order until an inclusive count; an unpublished word stops the round
         long long j = (long long)tile - 1;
         uint32_t spins = 0;
         while (j >= 0) {
-          const unsigned long long v = lb_load(lb_state + (size_t)j * 256 + d);
-          const unsigned long long f = v & ~LB_VAL;
-          if (f == 0) {
+          unsigned long long v[LB_WINDOW];
+#pragma unroll
+          for (int i = 0; i < LB_WINDOW; ++i)
+            v[i] = j - i >= 0 ? lb_load(lb_state + (size_t)(j - i) * 256 + d) : LB_INC;
+          int used = 0;
+          bool done = false;
+#pragma unroll
+          for (int i = 0; i < LB_WINDOW; ++i) {
+            if (done || used < i) break;
+            const unsigned long long f = v[i] & ~LB_VAL;
+            if (f == 0) break;
+            excl += v[i] & LB_VAL;
+            ++used;
+            done = f == LB_INC;
+          }
+          if (done) break;
+          j -= used;
+          if (used == 0) {
             if (++spins > LB_SPIN_LIMIT) {
               atomicExch(err, 1u);
               break;
             }
             __nanosleep(32);
-            continue;
+          } else {
+            spins = 0;
           }
-          spins = 0;
-          excl += v & LB_VAL;
-          if (f == LB_INC) break;
-          --j;
         }
         lb_store(mine, LB_INC | (excl + total));
       }
@@ -439,7 +460,7 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
   uint32_t nblocks = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
   constexpr size_t SCATTER_SMEM = (size_t)RS_TILE * (VALS ? 16 : 12);
   const int npass = (bits + 7) / 8;
-  if (npass <= HIST_ALL_MAX_PASSES) {
+  if (SDB_SORT_LOOKBACK && npass <= HIST_ALL_MAX_PASSES) {
     SDB_TRY(radix_sort_lookback<VALS>(keys, vals, ktmp, vtmp, n, bits, s, kres, vres, first_bit,
                                       split_vals, sb));
     return SDB_OK;
