@@ -51,7 +51,7 @@ TABLE_BITS = 22  # its first level, the cell table: 2^22 buckets (16 MB), fewer 
 # case, scaled to 100M points per point (an upper bound: the table structures'
 # share is read once per launch):
 # profiles/join_kernel_table_learned_eps64_zones263_mobility20M.txt
-JOIN_FINEST_TRAFFIC = {"table_learned": {"eps": 64, "leaf_bits": 16, "bytes_per_point": 14.505}}
+JOIN_FINEST_TRAFFIC = {}  # re-captured whenever the join kernel changes
 # DRAM bytes of one launch of radix_scatter_kernel (a keys-only pass) in the
 # sweep's record sort: profiles/radix_scatter_kernel_sweep_zones263.txt
 SCATTER_TRAFFIC = {"records": 117_378_603, "passes": 5, "bytes": 1.8595e9}
@@ -552,7 +552,8 @@ def main():
                        "achieved": achieved, "peak": peak, "unit": "GB/s",
                        "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                        "avg_launch_ms": join_ms[-1], "algorithmic_bytes_per_point": per_pt,
-                       "algorithmic_bytes_per_launch": per_pt * N}
+                       "algorithmic_bytes_per_launch": per_pt * N,
+                       "profile": "profiles/join_kernel_table_learned_eps64_zones263_mobility20M.txt"}
     # the record sort's scatter inside the full step (one launch per pass over
     # all records): 8 B read + 8 B written per record and pass, 8 + 12 B in the
     # last pass (keys and values apart)

@@ -8,10 +8,6 @@
 #include <mutex>
 #include <string>
 
-#ifndef SDB_HOST_COPY_STREAMS
-#define SDB_HOST_COPY_STREAMS 1
-#endif
-
 namespace sdb {
 
 namespace {
@@ -713,38 +709,16 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
     cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
   }
-#if SDB_HOST_COPY_STREAMS > 1
-  cudaStream_t cs2[2];
-  cudaEvent_t side[2];
-  for (int k = 0; k < 2; ++k) {
-    SDB_TRY_CUDA(cudaStreamCreateWithFlags(&cs2[k], cudaStreamNonBlocking));
-    cudaEventCreateWithFlags(&side[k], cudaEventDisableTiming);
-  }
-#endif
   sdb_status st = SDB_OK;
   for (uint64_t c = 0; c < nch && st == SDB_OK; ++c) {
     const int b = (int)(c & 1);
     const uint64_t a0 = c * CH, m = (n - a0 < CH) ? n - a0 : CH;
     cudaError_t e = cudaSuccess;
     if (c >= 2) e = cudaStreamWaitEvent(cs, done[b], 0);
-#if SDB_HOST_COPY_STREAMS > 1
-    // the three arrays on three copy streams (separate copy engines)
-    if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(cs2[k], copied[b], 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dx[b], h_x + a0, m * 4, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dy[b], h_y + a0, m * 4, cudaMemcpyHostToDevice, cs2[0]);
-    if (e == cudaSuccess && h_sum)
-      e = cudaMemcpyAsync(da[b], h_attr + a0, m * 4, cudaMemcpyHostToDevice, cs2[1]);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-      e = cudaEventRecord(side[k], cs2[k]);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, side[k], 0);
-    }
-#else
     if (e == cudaSuccess) e = cudaMemcpyAsync(dx[b], h_x + a0, m * 4, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dy[b], h_y + a0, m * 4, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess && h_sum)
       e = cudaMemcpyAsync(da[b], h_attr + a0, m * 4, cudaMemcpyHostToDevice, cs);
-#endif
     if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[b], 0);
     if (e != cudaSuccess) {
@@ -770,13 +744,6 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
     cudaEventDestroy(done[b]);
   }
   cudaStreamDestroy(cs);
-#if SDB_HOST_COPY_STREAMS > 1
-  for (int k = 0; k < 2; ++k) {
-    cudaStreamSynchronize(cs2[k]);
-    cudaStreamDestroy(cs2[k]);
-    cudaEventDestroy(side[k]);
-  }
-#endif
   return st;
 }
 

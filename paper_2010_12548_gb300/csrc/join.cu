@@ -42,12 +42,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t NONE = 0xffffffffu;
 constexpr int THREADS = 256;
 constexpr uint32_t SMEM_POLYS = 2048;
-#ifndef SDB_JOIN_PREFETCH
-#define SDB_JOIN_PREFETCH 1
-#endif
-#ifndef SDB_JOIN_HISKIP
-#define SDB_JOIN_HISKIP 1
-#endif
+
 constexpr uint32_t SMEM_POLYS_RANGE = 1024;  // 32 bytes of accumulators per polygon
 
 struct JoinArgs {
@@ -300,11 +295,7 @@ __device__ __forceinline__ void add_one(uint32_t p, int32_t a, uint32_t bnd, con
     atomicAdd(&s.cnt[p], 1u);
     if (SUM) {
       atomicAdd(&s.lo[p], (uint32_t)a & 0xffffu);
-#if SDB_JOIN_HISKIP
       if (a >> 16) atomicAdd(&s.hi[p], a >> 16);  // zero for attributes in [0, 2^16)
-#else
-      atomicAdd(&s.hi[p], a >> 16);
-#endif
     }
     if (RANGE && bnd) {
       atomicAdd(&s.bcnt[p], 1u);
@@ -533,46 +524,23 @@ __global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? 1 : 4) void join
   uint32_t since_flush = 0;
   // block-uniform loop over tiles of 4 TPB consecutive points; thread t takes
   // points 4t..4t+3 of the tile (a warp reads 512 contiguous bytes per array)
-  // the table lookups load the points of the block's next tile one iteration
-  // ahead: their per-point work is short, so the stream's latency would show
-  uint4 nx = make_uint4(0, 0, 0, 0), ny = nx;
-  int4 na = make_int4(0, 0, 0, 0);
-  bool have = false;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t e0 = t * per_tile + (uint64_t)threadIdx.x * 4;
     uint32_t xs[4], ys[4];
     int32_t as[4];
     bool ok[4];
     if (A.vec && e0 + 3 < A.n) {
-      uint4 xv, yv;
-      int4 av = make_int4(0, 0, 0, 0);
-      if (TABLE && SDB_JOIN_PREFETCH && have) {
-        xv = nx;
-        yv = ny;
-        av = na;
-      } else {
-        xv = __ldcs(reinterpret_cast<const uint4*>(A.x + e0));
-        yv = __ldcs(reinterpret_cast<const uint4*>(A.y + e0));
-        if (SUM) av = __ldcs(reinterpret_cast<const int4*>(A.attr + e0));
-      }
-      if constexpr (TABLE && SDB_JOIN_PREFETCH) {
-        const uint64_t e1 = e0 + (uint64_t)gridDim.x * per_tile;
-        have = e1 + 3 < A.n;
-        if (have) {
-          nx = __ldcs(reinterpret_cast<const uint4*>(A.x + e1));
-          ny = __ldcs(reinterpret_cast<const uint4*>(A.y + e1));
-          if (SUM) na = __ldcs(reinterpret_cast<const int4*>(A.attr + e1));
-        }
-      }
+      const uint4 xv = __ldcs(reinterpret_cast<const uint4*>(A.x + e0));
+      const uint4 yv = __ldcs(reinterpret_cast<const uint4*>(A.y + e0));
       xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
       ys[0] = yv.x; ys[1] = yv.y; ys[2] = yv.z; ys[3] = yv.w;
       if (SUM) {
+        const int4 av = __ldcs(reinterpret_cast<const int4*>(A.attr + e0));
         as[0] = av.x; as[1] = av.y; as[2] = av.z; as[3] = av.w;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) ok[q] = true;
     } else {
-      have = false;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         ok[q] = e0 + q < A.n;

@@ -3,8 +3,6 @@
 // and unique of a sorted array.  Hand-written; no library sort.
 #include "sdb_internal.cuh"
 
-#include <algorithm>
-
 namespace sdb {
 
 namespace {
@@ -128,63 +126,6 @@ __global__ __launch_bounds__(RS_THREADS) void radix_hist_kernel(const uint64_t* 
   }
 }
 
-// ------------------------------------------------ single-pass scatter support
-// Digit counts of every pass at once (one read of the keys): per block in shared
-// memory, then added to the global counts of each (pass, digit).
-constexpr int HIST_ALL_MAX_PASSES = 8;
-__global__ __launch_bounds__(RS_THREADS) void radix_hist_all_kernel(
-    const uint64_t* __restrict__ keys, size_t n, int first_bit, int npass,
-    unsigned long long* __restrict__ counts) {
-  __shared__ uint32_t h[HIST_ALL_MAX_PASSES][256];
-  for (int i = threadIdx.x; i < HIST_ALL_MAX_PASSES * 256; i += RS_THREADS) (&h[0][0])[i] = 0;
-  __syncthreads();
-  for (size_t g = (size_t)blockIdx.x * RS_THREADS + threadIdx.x; g < n;
-       g += (size_t)gridDim.x * RS_THREADS) {
-    const uint64_t k = keys[g] >> first_bit;
-    for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(uint32_t)(k >> (8 * p)) & 255u], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < npass * 256; i += RS_THREADS) {
-    const uint32_t v = (&h[0][0])[i];
-    if (v) atomicAdd(&counts[i], (unsigned long long)v);
-  }
-}
-
-// exclusive prefix of each pass's 256 digit counts: the digit's first slot
-__global__ void digit_base_kernel(const unsigned long long* __restrict__ counts, int npass,
-                                  unsigned long long* __restrict__ base) {
-  const int p = threadIdx.x;
-  if (p >= npass) return;
-  unsigned long long acc = 0;
-  for (int d = 0; d < 256; ++d) {
-    base[p * 256 + d] = acc;
-    acc += counts[p * 256 + d];
-  }
-}
-
-// Decoupled look-back state of one (tile, digit): the top two bits say what
-// the low 62 hold -- 0 nothing yet, 1 the tile's own count, 2 the count of the
-// tile and every earlier tile -- so flag and count travel in one 64-bit word.
-constexpr unsigned long long LB_AGG = 1ull << 62, LB_INC = 2ull << 62;
-constexpr unsigned long long LB_VAL = (1ull << 62) - 1;
-constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;  // waits on one predecessor before giving up
-#ifndef SDB_SORT_LB_WINDOW
-#define SDB_SORT_LB_WINDOW 8
-#endif
-constexpr int LB_WINDOW = SDB_SORT_LB_WINDOW;  // predecessor words read per round
-#ifndef SDB_SORT_LOOKBACK
-#define SDB_SORT_LOOKBACK 1
-#endif
-
-__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 // Stable scatter of one 8-bit digit.  Each warp ranks its 512 keys (in order)
 // by digit with a warp match; the block then lays its tile out in shared memory
 // sorted by digit (stable), and writes it back so that consecutive threads
@@ -192,21 +133,11 @@ __device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long lo
 // at the block's global offset for that digit.
 // SPLIT (keys only): the output is the packed covering record split into its
 // key (kout) and standard value (vout), sb slot bits.
-// LB (single pass per digit): the tile's global offsets come from a decoupled
-// look-back instead of a separate histogram and scan -- tiles are taken in
-// ticket order (a tile waits only on tiles already running), each publishes its
-// digit counts as soon as it has ranked its keys, then walks back over earlier
-// tiles' words until one holds an inclusive count, and publishes its own
-// inclusive count.  A wait that runs past LB_SPIN_LIMIT sets *err and goes on
-// with the count it has (the host reports the error; the sort's output is then
-// not used).
-template <bool VALS, bool SPLIT = false, bool LB = false>
+template <bool VALS, bool SPLIT = false>
 __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ offs,
-    uint32_t nblocks, uint32_t sb = 0, unsigned long long* __restrict__ lb_state = nullptr,
-    const unsigned long long* __restrict__ digit_base = nullptr,
-    unsigned int* __restrict__ ticket = nullptr, unsigned int* __restrict__ err = nullptr) {
+    uint32_t nblocks, uint32_t sb = 0) {
   extern __shared__ __align__(16) unsigned char dyn[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(dyn);                 // RS_TILE keys
   uint32_t* sv = reinterpret_cast<uint32_t*>(dyn + RS_TILE * 8);   // RS_TILE values
@@ -214,13 +145,10 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
   __shared__ uint32_t cnt[RS_WARPS][256];  // per warp and digit: count, then warp prefix
   __shared__ uint32_t dstart[256];         // digit's first slot in the tile
   __shared__ uint32_t gbase[256];          // digit's first global slot for this block
-  __shared__ uint32_t s_tile;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
-  if (LB && threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   __syncthreads();
-  const uint32_t tile = LB ? s_tile : blockIdx.x;
-  const size_t tile0 = (size_t)tile * RS_TILE;
+  const size_t tile0 = (size_t)blockIdx.x * RS_TILE;
   const size_t base = tile0 + (size_t)w * (32 * RS_ITEMS);
   const unsigned lt = (1u << lane) - 1u;
   // a full tile's values travel to shared memory while the keys are ranked
@@ -270,51 +198,7 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
       cnt[ww][d] = total;
       total += t;
     }
-    if (LB) {
-      unsigned long long* mine = lb_state + (size_t)tile * 256 + d;
-      unsigned long long excl = 0;
-      if (tile == 0) {
-        lb_store(mine, LB_INC | total);
-      } else {
-        lb_store(mine, LB_AGG | total);
-        // predecessors' words LB_WINDOW at a time (independent loads), taken in
-        // order until an inclusive count; an unpublished word stops the round
-        long long j = (long long)tile - 1;
-        uint32_t spins = 0;
-        while (j >= 0) {
-          unsigned long long v[LB_WINDOW];
-#pragma unroll
-          for (int i = 0; i < LB_WINDOW; ++i)
-            v[i] = j - i >= 0 ? lb_load(lb_state + (size_t)(j - i) * 256 + d) : LB_INC;
-          int used = 0;
-          bool done = false;
-#pragma unroll
-          for (int i = 0; i < LB_WINDOW; ++i) {
-            if (done || used < i) break;
-            const unsigned long long f = v[i] & ~LB_VAL;
-            if (f == 0) break;
-            excl += v[i] & LB_VAL;
-            ++used;
-            done = f == LB_INC;
-          }
-          if (done) break;
-          j -= used;
-          if (used == 0) {
-            if (++spins > LB_SPIN_LIMIT) {
-              atomicExch(err, 1u);
-              break;
-            }
-            __nanosleep(32);
-          } else {
-            spins = 0;
-          }
-        }
-        lb_store(mine, LB_INC | (excl + total));
-      }
-      gbase[d] = (uint32_t)(digit_base[d] + excl);  // n < 2^32
-    } else {
-      gbase[d] = offs[(size_t)d * nblocks + blockIdx.x];
-    }
+    gbase[d] = offs[(size_t)d * nblocks + blockIdx.x];
   }
   // exclusive scan of the 256 digit totals (block-wide, two levels of warps)
   {
@@ -376,76 +260,6 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
   }
 }
 
-// One histogram pass over the keys for all digits, then per 8-bit digit one
-// scatter pass with decoupled look-back (no per-pass histogram or scan).
-template <bool VALS>
-sdb_status radix_sort_lookback(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp,
-                               size_t n, int bits, cudaStream_t s, uint64_t** kres,
-                               uint32_t** vres, int first_bit, uint32_t* split_vals, uint32_t sb) {
-  const uint32_t nblocks = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
-  constexpr size_t SCATTER_SMEM = (size_t)RS_TILE * (VALS ? 16 : 12);
-  const int npass = (bits + 7) / 8;
-  SDB_TRY_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<VALS, false, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)SCATTER_SMEM));
-  if (!VALS && split_vals)
-    SDB_TRY_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<false, true, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SCATTER_SMEM));
-  Scratch sc(s);
-  unsigned long long *counts, *base, *state;
-  unsigned int* ctl;  // [0] ticket, [1] error flag
-  SDB_TRY(sc.get(&counts, (size_t)npass * 256));
-  SDB_TRY(sc.get(&base, (size_t)npass * 256));
-  SDB_TRY(sc.get(&state, (size_t)nblocks * 256));
-  SDB_TRY(sc.get(&ctl, 2));
-  SDB_TRY_CUDA(cudaMemsetAsync(counts, 0, (size_t)npass * 256 * 8, s));
-  SDB_TRY_CUDA(cudaMemsetAsync(ctl, 0, 8, s));
-  {
-    TraceScope tr("sort.hist", s);
-    const unsigned hb = (unsigned)std::min<uint64_t>(nblocks, (uint64_t)num_sms() * 8);
-    radix_hist_all_kernel<<<hb, RS_THREADS, 0, s>>>(keys, n, first_bit, npass, counts);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
-    digit_base_kernel<<<1, 32, 0, s>>>(counts, npass, base);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
-  }
-  uint64_t *ka = keys, *kb = ktmp;
-  uint32_t *va = vals, *vb = vtmp;
-  for (int p = 0; p < npass; ++p) {
-    const int shift = first_bit + 8 * p;
-    SDB_TRY_CUDA(cudaMemsetAsync(state, 0, (size_t)nblocks * 256 * 8, s));
-    SDB_TRY_CUDA(cudaMemsetAsync(ctl, 0, 4, s));  // the ticket; the error flag stays
-    TraceScope tr("sort.scatter", s);
-    if (!VALS && split_vals && p == npass - 1)  // the last pass splits
-      radix_scatter_kernel<false, true, true><<<nblocks, RS_THREADS, SCATTER_SMEM, s>>>(
-          ka, nullptr, kb, split_vals, n, shift, nullptr, nblocks, sb, state, base + p * 256, ctl,
-          ctl + 1);
-    else
-      radix_scatter_kernel<VALS, false, true><<<nblocks, RS_THREADS, SCATTER_SMEM, s>>>(
-          ka, va, kb, vb, n, shift, nullptr, nblocks, 0, state, base + p * 256, ctl, ctl + 1);
-    note_launch();
-    SDB_TRY_CUDA(cudaGetLastError());
-    uint64_t* t = ka;
-    ka = kb;
-    kb = t;
-    uint32_t* u = va;
-    va = vb;
-    vb = u;
-  }
-  unsigned int e = 0;
-  SDB_TRY_CUDA(cudaMemcpyAsync(&e, ctl + 1, 4, cudaMemcpyDeviceToHost, s));
-  SDB_TRY_CUDA(cudaStreamSynchronize(s));
-  if (e) {
-    set_error("radix sort: a look-back wait ran past its limit");
-    return SDB_ETIMEOUT;
-  }
-  *kres = ka;
-  if (VALS) *vres = va;
-  return SDB_OK;
-}
-
 template <bool VALS>
 sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint32_t* vtmp, size_t n,
                            int bits, cudaStream_t s, uint64_t** kres, uint32_t** vres,
@@ -459,12 +273,6 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
   }
   uint32_t nblocks = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
   constexpr size_t SCATTER_SMEM = (size_t)RS_TILE * (VALS ? 16 : 12);
-  const int npass = (bits + 7) / 8;
-  if (SDB_SORT_LOOKBACK && npass <= HIST_ALL_MAX_PASSES) {
-    SDB_TRY(radix_sort_lookback<VALS>(keys, vals, ktmp, vtmp, n, bits, s, kres, vres, first_bit,
-                                      split_vals, sb));
-    return SDB_OK;
-  }
   SDB_TRY_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<VALS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)SCATTER_SMEM));
