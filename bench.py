@@ -678,7 +678,17 @@ def main():
                     np.array_equal(hs.numpy(), head_sm.cpu().numpy()))
         for c in cs:
             c.free()
+        # the host -> device link: one pinned copy of the point arrays
+        dbuf = torch.empty(N * 3, dtype=torch.int32, device=dev)
+        def link_copy():
+            dbuf[:N].copy_(hx, non_blocking=True)
+            dbuf[N:2 * N].copy_(hy, non_blocking=True)
+            dbuf[2 * N:].copy_(ha, non_blocking=True)
+        link_s = wall(link_copy, 5, 2)
+        del dbuf
         res["e2e"] = {"value": job_rate(ws, N * E, e2e_s), "unit": UNIT,
+                      "h2d_link_GB_per_s": N * 12 / link_s / 1e9,
+                      "frac_of_link": (N * 12 / e2e_s) / (N * 12 / link_s),
                       "h2d_bytes_per_step": N * 12, "d2h_bytes_per_step": E * P * 16,
                       "ms_per_step": e2e_s * 1e3, "matches_device": same,
                       "what": "sdb_join_aggregate_host: points copied from pinned host memory "
