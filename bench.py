@@ -945,7 +945,6 @@ C3_TILE_LEVEL, C3_TILED_EPS, C3_TILES_PER_BATCH = 5, 2 ** 5, 32
 def tiled_join(sdb, torch, dev, stream, T, p, qb, lookups, timing=True):
     """Per polygon COUNT and SUM over all tiles for each lookup (device tensors),
     with the build and join times."""
-    from paper_2010_12548_gb300 import workloads as W  # noqa: F401
     P = T.n
     rows = [tuple(int(v) for v in r) for r in qb.queries]
     tot = {lk: (torch.zeros(P, dtype=torch.int64, device=dev),
