@@ -175,7 +175,7 @@ static void free_covering(sdb_covering* c) {
   cudaDeviceSynchronize();
   void* ps[] = {c->start,  c->list_off, c->list_ids, c->pay,    c->sample,
                 c->leaves, c->knots,    c->fallbacks, c->tab,   c->win,
-                c->sub,    c->win2,     c->top};
+                c->sub,    c->win2,     c->top,       c->top_pal};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, 0);
   cudaStreamSynchronize(0);
@@ -512,7 +512,7 @@ sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* inf
       cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) + (4ull << cov->knot_bits) + 4 : 0);
   if (cov->tab)
     info->device_bytes += (4ull << cov->tab_bits) + 8ull * cov->tab_mixed +
-                          (cov->top ? 2ull << (2 * cov->top_level) : 0) +
+                          (cov->top ? (1ull << (2 * cov->top_level)) + 4 * TOP_PALETTE : 0) +
                           (4ull << (2 * cov->sub_bits)) * (cov->sub ? cov->tab_mixed : 0) +
                           8ull * cov->sub_mixed;
   info->index_leaf_bits = cov->leaf_bits;

@@ -84,8 +84,10 @@ struct JoinArgs {
   const uint32_t* sub;
   uint32_t s2, txy2;
   // the tree's top level, staged in shared memory (top == nullptr: none): the
-  // entry of a point is at (y >> top_xy) << top_lev | (x >> top_xy)
-  const uint16_t* top;
+  // byte of a point is at (y >> top_xy) << top_lev | (x >> top_xy), an index
+  // into the palette of payloads top_pal, TOP_NONE or TOP_ASK
+  const uint8_t* top;
+  const uint32_t* top_pal;
   uint32_t top_xy, top_lev;
 };
 
@@ -462,11 +464,13 @@ __host__ __device__ inline size_t stage_bytes(int lookup, const JoinArgs& A, int
   return (size_t)(tpb / 32) * QCAP * sizeof(QEnt);
 }
 
-// The table lookups with the tree's top level in shared memory run one block
-// of TOP_THREADS per SM (the level takes 128 KB); their accumulators are
-// flushed every TOP_FLUSH_TILES tiles, which keeps the same no-wrap bound.
-constexpr int TOP_THREADS = 1024;
-constexpr uint32_t TOP_FLUSH_TILES = 15;
+// The table lookups with the tree's top level in shared memory run two blocks
+// of TOP_THREADS per SM (the level and its palette take 65 KB per block, and
+// the kernel fits 40 registers); their accumulators are flushed every
+// TOP_FLUSH_TILES tiles, which keeps the same no-wrap bound.
+constexpr int TOP_THREADS = 768;
+constexpr int TOP_BLOCKS = 2;
+constexpr uint32_t TOP_FLUSH_TILES = 20;
 static_assert((uint64_t)(TOP_FLUSH_TILES * TOP_THREADS * 4 + (TOP_THREADS / 32) * (QCAP - 1)) *
                       65535u < (1ull << 32),
               "low-half counter could wrap");
@@ -474,12 +478,13 @@ static_assert((uint64_t)(TOP_FLUSH_TILES * TOP_THREADS * 4 + (TOP_THREADS / 32) 
                       32768u < (1ull << 31),
               "high-half counter could wrap");
 
+// the top level's bytes (a multiple of 16 from level 2 on) and its palette
 __host__ __device__ inline size_t top_bytes(const JoinArgs& A) {
-  return (size_t)2 << (2 * A.top_lev);
+  return ((size_t)1 << (2 * A.top_lev)) + 4 * TOP_PALETTE;
 }
 
 template <int LOOKUP, bool SMEM, bool SUM, bool RANGE, bool TOP = false>
-__global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? 1 : 4) void join_kernel(JoinArgs A) {
+__global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? TOP_BLOCKS : 4) void join_kernel(JoinArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int TPB = TOP ? TOP_THREADS : THREADS;
   constexpr uint32_t FT = TOP ? TOP_FLUSH_TILES : FLUSH_TILES;
@@ -495,9 +500,9 @@ __global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? 1 : 4) void join
   QEnt* s_q = reinterpret_cast<QEnt*>(smem + HB) + (threadIdx.x >> 5) * QCAP;
   const size_t off = HB + stage_bytes(LOOKUP, A, TPB);
   const Acc acc = acc_at<SUM, RANGE>(smem + off, SMEM ? A.P : 0);
-  const uint16_t* s_top =
-      reinterpret_cast<const uint16_t*>(smem + ((off + acc_bytes(SMEM ? A.P : 0, SUM, RANGE) +
-                                                 15) & ~(size_t)15));
+  uint8_t* s_top =
+      smem + ((off + acc_bytes(SMEM ? A.P : 0, SUM, RANGE) + 15) & ~(size_t)15);
+  uint32_t* s_pal = reinterpret_cast<uint32_t*>(s_top + ((size_t)1 << (2 * A.top_lev)));
 
   if constexpr (TABLE)
     hilbert3_fill_compact(s_tab);
@@ -507,10 +512,11 @@ __global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? 1 : 4) void join
     for (uint32_t i = threadIdx.x; i < A.sample_n; i += TPB) s_sample[i] = A.sample[i];
   if constexpr (LOOKUP == SDB_LOOKUP_LEARNED)
     for (uint32_t i = threadIdx.x; i < A.nknots; i += TPB) s_knots[i] = A.knots[i];
-  if constexpr (TOP) {  // 16-byte copies of the top level (a multiple of 16 bytes)
+  if constexpr (TOP) {  // 16-byte copies of the top level, then its palette
     const uint4* src = reinterpret_cast<const uint4*>(A.top);
-    uint4* dst = reinterpret_cast<uint4*>(const_cast<uint16_t*>(s_top));
-    for (uint32_t i = threadIdx.x; i < (uint32_t)(top_bytes(A) / 16); i += TPB) dst[i] = __ldg(src + i);
+    uint4* dst = reinterpret_cast<uint4*>(s_top);
+    for (uint32_t i = threadIdx.x; i < (1u << (2 * A.top_lev)) / 16; i += TPB) dst[i] = __ldg(src + i);
+    for (uint32_t i = threadIdx.x; i < TOP_PALETTE; i += TPB) s_pal[i] = __ldg(A.top_pal + i);
   }
   if (SMEM) acc_zero<SUM, RANGE>(acc, A.P);
   __syncthreads();
@@ -566,10 +572,10 @@ __global__ __launch_bounds__(TOP ? TOP_THREADS : THREADS, TOP ? 1 : 4) void join
         bool ask[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const uint16_t v =
+          const uint8_t v =
               ok[q] ? s_top[((ys[q] >> A.top_xy) << A.top_lev) | (xs[q] >> A.top_xy)] : TOP_NONE;
           ask[q] = v == TOP_ASK;
-          e[q] = v == TOP_NONE ? NONE : (uint32_t)v;
+          e[q] = v >= TOP_NONE ? NONE : s_pal[v];
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -883,6 +889,7 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   A.s2 = cov->sub_bits;
   A.txy2 = A.txy - cov->sub_bits;
   A.top = cov->top;
+  A.top_pal = cov->top_pal;
   A.top_lev = cov->top_level;
   A.top_xy = cov->B - cov->top_level;
   A.bcount = reinterpret_cast<unsigned long long*>(bcount);

@@ -191,9 +191,12 @@ struct sdb_covering {
   uint32_t sub_bits = 0;
   uint64_t sub_mixed = 0;
   // the tree's top level, small enough for shared memory: 4^top_level cells of
-  // level top_level, row-major, 2 bytes each (TOP_ASK: consult the table,
-  // TOP_NONE: no polygon, else the single polygon); top == nullptr: none
-  uint16_t* top = nullptr;
+  // level top_level, row-major, 1 byte each (TOP_ASK: consult the table,
+  // TOP_NONE: no polygon, else an index into top_pal, the single-polygon
+  // payloads of the level's cells, at most TOP_PALETTE of them, the most
+  // frequent first); top == nullptr: none
+  uint8_t* top = nullptr;
+  uint32_t* top_pal = nullptr;
   uint32_t top_level = 0;
   size_t bytes = 0;
 };
@@ -382,10 +385,11 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream
 // meets several ranges (m < TAB_MIXED_MAX - 1; payload values 2^31 | r need
 // r < 2^30 - 1, so the two never collide)
 constexpr uint32_t TAB_MIXED = 0xC0000000u;
-// top-level entries: a single-polygon payload below TOP_NONE, or one of these
-constexpr uint16_t TOP_ASK = 0xFFFFu;
-constexpr uint16_t TOP_NONE = 0xFFFEu;
-constexpr uint32_t TOP_MAX_LEVEL = 8;  // 4^8 cells, 128 KB of shared memory
+// top-level entries: an index into the level's palette of payloads, or one of these
+constexpr uint8_t TOP_ASK = 0xFFu;
+constexpr uint8_t TOP_NONE = 0xFEu;
+constexpr uint32_t TOP_PALETTE = 254;  // palette slots (indices 0 .. 253)
+constexpr uint32_t TOP_MAX_LEVEL = 8;  // 4^8 cells, 64 KB of shared memory
 constexpr uint32_t TAB_MIXED_MAX = 0x3fffffffu;
 // Sec. 6 intervals from the range join's partials (join.cu)
 sdb_status launch_result_bounds(const uint64_t* count, const int64_t* sum, const uint64_t* bcount,

@@ -27,6 +27,9 @@
 // one more read and searches only when its sub-cell meets several ranges.
 #include "sdb_internal.cuh"
 
+#include <algorithm>
+#include <vector>
+
 namespace sdb {
 
 namespace {
@@ -239,13 +242,16 @@ __global__ void table_sub_kernel(const uint64_t* __restrict__ start, const uint3
 
 // The top level: cell (tx, ty) of level Lt covers the 2^d x 2^d cells of the
 // table's level L0 = Lt + d below it.  When all of them hold the same
-// single-polygon payload p (no mixed cell, no list, no boundary flag, p below
-// TOP_NONE) the whole cell lies in one range -- its ids are contiguous and the
-// canonical covering merges equal neighbours, so cells with equal payloads
-// side by side belong to one range -- and the entry is p; all empty gives
-// TOP_NONE; anything else TOP_ASK (the table decides).
+// single-polygon payload p (no mixed cell, no list, no boundary flag) the whole
+// cell lies in one range -- its ids are contiguous and the canonical covering
+// merges equal neighbours, so cells with equal payloads side by side belong to
+// one range -- and the cell's word is p; all empty gives TOP_WORD_NONE;
+// anything else TOP_WORD_ASK (the table decides).  The host then turns the
+// words into one byte each through a palette of the most frequent payloads.
+constexpr uint32_t TOP_WORD_ASK = 0xFFFFFFFEu, TOP_WORD_NONE = 0xFFFFFFFFu;
+
 __global__ void table_top_kernel(const uint32_t* __restrict__ tab, uint32_t L0, uint32_t Lt,
-                                 uint16_t* __restrict__ top) {
+                                 uint32_t* __restrict__ word) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= (1u << (2 * Lt))) return;
   const uint32_t d = L0 - Lt, tx = c & ((1u << Lt) - 1u), ty = c >> Lt;
@@ -257,14 +263,14 @@ __global__ void table_top_kernel(const uint32_t* __restrict__ tab, uint32_t L0, 
         same = false;
         break;
       }
-  uint16_t v = TOP_ASK;
+  uint32_t v = TOP_WORD_ASK;
   if (same) {
     if (first == 0xFFFFFFFFu)
-      v = TOP_NONE;
-    else if (first < (uint32_t)TOP_NONE)
-      v = (uint16_t)first;
+      v = TOP_WORD_NONE;
+    else if (first < 0x40000000u)  // one polygon, no boundary flag
+      v = first;
   }
-  top[c] = v;
+  word[c] = v;
 }
 
 }  // namespace
@@ -285,6 +291,8 @@ sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t
   if (cov->sub) dfree(cov->sub, s);
   if (cov->win2) dfree(cov->win2, s);
   if (cov->top) dfree(cov->top, s);
+  if (cov->top_pal) dfree(cov->top_pal, s);
+  cov->top_pal = nullptr;
   cov->tab = nullptr;
   cov->win = nullptr;
   cov->sub = nullptr;
@@ -362,14 +370,60 @@ sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t
       }
     }
   }
-  // the top level for shared memory (levels 4 .. TOP_MAX_LEVEL)
+  // the top level for shared memory (levels 4 .. TOP_MAX_LEVEL): the cells'
+  // words on the device, the palette and the byte per cell on the host
   if (L0 >= 4) {
     const uint32_t Lt = L0 < TOP_MAX_LEVEL ? L0 : TOP_MAX_LEVEL;
     const uint32_t nt = 1u << (2 * Lt);
-    SDB_TRY(dalloc_n(&cov->top, nt, s));
-    table_top_kernel<<<(nt + 255) / 256, 256, 0, s>>>(cov->tab, L0, Lt, cov->top);
+    uint32_t* word;
+    SDB_TRY(sc.get(&word, nt));
+    table_top_kernel<<<(nt + 255) / 256, 256, 0, s>>>(cov->tab, L0, Lt, word);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
+    std::vector<uint32_t> hw(nt);
+    SDB_TRY_CUDA(cudaMemcpyAsync(hw.data(), word, (size_t)nt * 4, cudaMemcpyDeviceToHost, s));
+    SDB_TRY_CUDA(cudaStreamSynchronize(s));
+    // the payloads by frequency (ties by value): the palette holds the first
+    // TOP_PALETTE; cells of other payloads ask the table
+    std::vector<uint32_t> pv;
+    for (uint32_t v : hw)
+      if (v < TOP_WORD_ASK) pv.push_back(v);
+    std::sort(pv.begin(), pv.end());
+    std::vector<std::pair<uint32_t, uint32_t>> freq;  // (count, payload)
+    for (size_t i = 0; i < pv.size();) {
+      size_t j = i;
+      while (j < pv.size() && pv[j] == pv[i]) ++j;
+      freq.emplace_back((uint32_t)(j - i), pv[i]);
+      i = j;
+    }
+    std::sort(freq.begin(), freq.end(), [](const std::pair<uint32_t, uint32_t>& a,
+                                           const std::pair<uint32_t, uint32_t>& b) {
+      return a.first != b.first ? a.first > b.first : a.second < b.second;
+    });
+    std::vector<uint32_t> pal(TOP_PALETTE, 0xFFFFFFFFu);
+    std::vector<std::pair<uint32_t, uint32_t>> slot;  // (payload, palette index)
+    for (uint32_t i = 0; i < freq.size() && i < TOP_PALETTE; ++i) {
+      pal[i] = freq[i].second;
+      slot.emplace_back(freq[i].second, i);
+    }
+    std::sort(slot.begin(), slot.end());
+    std::vector<uint8_t> hb(nt);
+    for (uint32_t c = 0; c < nt; ++c) {
+      const uint32_t v = hw[c];
+      uint8_t b = TOP_ASK;
+      if (v == TOP_WORD_NONE) {
+        b = TOP_NONE;
+      } else if (v != TOP_WORD_ASK) {
+        auto it = std::lower_bound(slot.begin(), slot.end(), std::make_pair(v, 0u));
+        if (it != slot.end() && it->first == v) b = (uint8_t)it->second;
+      }
+      hb[c] = b;
+    }
+    SDB_TRY(dalloc_n(&cov->top, nt, s));
+    SDB_TRY(dalloc_n(&cov->top_pal, TOP_PALETTE, s));
+    SDB_TRY_CUDA(cudaMemcpyAsync(cov->top, hb.data(), nt, cudaMemcpyHostToDevice, s));
+    SDB_TRY_CUDA(cudaMemcpyAsync(cov->top_pal, pal.data(), TOP_PALETTE * 4,
+                                 cudaMemcpyHostToDevice, s));
     cov->top_level = Lt;
   }
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
