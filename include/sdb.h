@@ -228,9 +228,10 @@ sdb_status sdb_covering_build_table(sdb_covering *cov, uint32_t table_bits, void
  * sdb_covering_build_index; SDB_LOOKUP_TABLE: the cell table's bucket, then a
  * binary search of the bucket's window if it holds several ranges; requires
  * sdb_covering_build_table; SDB_LOOKUP_TABLE_LEARNED: the cell table's bucket,
- * and in a bucket of several ranges the learned index's error window cut to the
- * bucket's window, searched and verified, with the bucket's window as the
- * counted fallback; requires both), and for every polygon j on r's list
+ * and in a bucket of several ranges -- when its window holds more than 64 of
+ * them -- the learned index's error window cut to the bucket's window, searched
+ * and verified, with the bucket's window as the counted fallback; requires
+ * both), and for every polygon j on r's list
  * d_count[j] += 1 and d_sum[j] += d_attr[i].  All three lookups give
  * identical results.  d_count and d_sum (P entries each) are zeroed by the call.
  * d_x, d_y, d_attr: n device values (SoA).  d_attr and d_sum may be NULL

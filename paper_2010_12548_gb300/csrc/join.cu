@@ -42,6 +42,9 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t NONE = 0xffffffffu;
 constexpr int THREADS = 256;
 constexpr uint32_t SMEM_POLYS = 2048;
+// windows of the table's mixed cells longer than this are searched through the
+// learned model (table + learned lookup), shorter ones directly
+constexpr uint32_t LEARNED_MIN_WINDOW = 64;
 
 constexpr uint32_t SMEM_POLYS_RANGE = 1024;  // 32 bytes of accumulators per polygon
 
@@ -393,7 +396,9 @@ __device__ __forceinline__ void resolve_mixed(const QEnt& E, const uint32_t* s_t
   const uint64_t h = hilbert3_encode_compact(E.x >> A.k, E.y >> A.k, A.nsteps, A.st0, s_tab);
   const uint2 w = __ldg(A.win + E.m);
   uint32_t lo = w.x, len = w.y - w.x + 1;
-  if constexpr (LOOKUP == SDB_LOOKUP_TABLE_LEARNED) {
+  // the model replaces the search where the window is long; a short window
+  // costs fewer probes than the model's root, leaf and verification reads
+  if (LOOKUP == SDB_LOOKUP_TABLE_LEARNED && len > LEARNED_MIN_WINDOW) {
     // the root knots through the L1 cache: only points in mixed buckets read them
     const uint32_t l = root_leaf(A.knots, A.wshift, A.inv_w, A.nleaves, h);
     uint64_t w0, w1, w2, w3;
