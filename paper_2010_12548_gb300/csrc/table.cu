@@ -246,8 +246,8 @@ __global__ void table_sub_kernel(const uint64_t* __restrict__ start, const uint3
 // cell lies in one range -- its ids are contiguous and the canonical covering
 // merges equal neighbours, so cells with equal payloads side by side belong to
 // one range -- and the cell's word is p; all empty gives TOP_WORD_NONE;
-// anything else TOP_WORD_ASK (the table decides).  The host then turns the
-// words into one byte each through a palette of the most frequent payloads.
+// anything else TOP_WORD_ASK (the table decides).  The words then become one
+// byte each through a palette of the most frequent payloads.
 constexpr uint32_t TOP_WORD_ASK = 0xFFFFFFFEu, TOP_WORD_NONE = 0xFFFFFFFFu;
 
 __global__ void table_top_kernel(const uint32_t* __restrict__ tab, uint32_t L0, uint32_t Lt,
@@ -267,10 +267,26 @@ __global__ void table_top_kernel(const uint32_t* __restrict__ tab, uint32_t L0, 
   if (same) {
     if (first == 0xFFFFFFFFu)
       v = TOP_WORD_NONE;
-    else if (first < 0x40000000u)  // one polygon, no boundary flag
+    else if (first < 0x40000000u)  // one polygon (its slot), no boundary flag
       v = first;
   }
   word[c] = v;
+}
+
+// occurrences of each single-polygon payload among the top level's cells
+__global__ void top_count_kernel(const uint32_t* __restrict__ word, uint32_t nt,
+                                 uint32_t* __restrict__ count) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nt && word[c] < TOP_WORD_ASK) atomicAdd(&count[word[c]], 1u);
+}
+
+// the byte of each cell: its payload's palette index (map), or TOP_NONE / TOP_ASK
+__global__ void top_byte_kernel(const uint32_t* __restrict__ word, uint32_t nt,
+                                const uint8_t* __restrict__ map, uint8_t* __restrict__ top) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nt) return;
+  const uint32_t v = word[c];
+  top[c] = v == TOP_WORD_NONE ? TOP_NONE : (v == TOP_WORD_ASK ? TOP_ASK : map[v]);
 }
 
 }  // namespace
@@ -380,50 +396,41 @@ sdb_status build_cell_table(sdb_covering* cov, uint32_t table_bits, cudaStream_t
     table_top_kernel<<<(nt + 255) / 256, 256, 0, s>>>(cov->tab, L0, Lt, word);
     note_launch();
     SDB_TRY_CUDA(cudaGetLastError());
-    std::vector<uint32_t> hw(nt);
-    SDB_TRY_CUDA(cudaMemcpyAsync(hw.data(), word, (size_t)nt * 4, cudaMemcpyDeviceToHost, s));
+    // payloads are polygon slots (< P): count them on the device, pick the
+    // palette on the host from P counts, map the cells on the device
+    const uint32_t P = cov->P;
+    uint32_t* cnt;
+    uint8_t* dmap;
+    SDB_TRY(sc.get(&cnt, P));
+    SDB_TRY(sc.get(&dmap, P));
+    SDB_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)P * 4, s));
+    top_count_kernel<<<(nt + 255) / 256, 256, 0, s>>>(word, nt, cnt);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
+    std::vector<uint32_t> hc(P);
+    SDB_TRY_CUDA(cudaMemcpyAsync(hc.data(), cnt, (size_t)P * 4, cudaMemcpyDeviceToHost, s));
     SDB_TRY_CUDA(cudaStreamSynchronize(s));
-    // the payloads by frequency (ties by value): the palette holds the first
-    // TOP_PALETTE; cells of other payloads ask the table
-    std::vector<uint32_t> pv;
-    for (uint32_t v : hw)
-      if (v < TOP_WORD_ASK) pv.push_back(v);
-    std::sort(pv.begin(), pv.end());
-    std::vector<std::pair<uint32_t, uint32_t>> freq;  // (count, payload)
-    for (size_t i = 0; i < pv.size();) {
-      size_t j = i;
-      while (j < pv.size() && pv[j] == pv[i]) ++j;
-      freq.emplace_back((uint32_t)(j - i), pv[i]);
-      i = j;
-    }
-    std::sort(freq.begin(), freq.end(), [](const std::pair<uint32_t, uint32_t>& a,
-                                           const std::pair<uint32_t, uint32_t>& b) {
-      return a.first != b.first ? a.first > b.first : a.second < b.second;
-    });
+    // the most frequent payloads (ties by slot) take the palette's slots
+    std::vector<uint32_t> order;
+    for (uint32_t j = 0; j < P; ++j)
+      if (hc[j]) order.push_back(j);
+    const size_t keep = std::min<size_t>(order.size(), TOP_PALETTE);
+    auto more = [&](uint32_t a, uint32_t b) { return hc[a] != hc[b] ? hc[a] > hc[b] : a < b; };
+    std::partial_sort(order.begin(), order.begin() + keep, order.end(), more);
     std::vector<uint32_t> pal(TOP_PALETTE, 0xFFFFFFFFu);
-    std::vector<std::pair<uint32_t, uint32_t>> slot;  // (payload, palette index)
-    for (uint32_t i = 0; i < freq.size() && i < TOP_PALETTE; ++i) {
-      pal[i] = freq[i].second;
-      slot.emplace_back(freq[i].second, i);
-    }
-    std::sort(slot.begin(), slot.end());
-    std::vector<uint8_t> hb(nt);
-    for (uint32_t c = 0; c < nt; ++c) {
-      const uint32_t v = hw[c];
-      uint8_t b = TOP_ASK;
-      if (v == TOP_WORD_NONE) {
-        b = TOP_NONE;
-      } else if (v != TOP_WORD_ASK) {
-        auto it = std::lower_bound(slot.begin(), slot.end(), std::make_pair(v, 0u));
-        if (it != slot.end() && it->first == v) b = (uint8_t)it->second;
-      }
-      hb[c] = b;
+    std::vector<uint8_t> map(P, TOP_ASK);
+    for (size_t i = 0; i < keep; ++i) {
+      pal[i] = order[i];
+      map[order[i]] = (uint8_t)i;
     }
     SDB_TRY(dalloc_n(&cov->top, nt, s));
     SDB_TRY(dalloc_n(&cov->top_pal, TOP_PALETTE, s));
-    SDB_TRY_CUDA(cudaMemcpyAsync(cov->top, hb.data(), nt, cudaMemcpyHostToDevice, s));
+    SDB_TRY_CUDA(cudaMemcpyAsync(dmap, map.data(), P, cudaMemcpyHostToDevice, s));
     SDB_TRY_CUDA(cudaMemcpyAsync(cov->top_pal, pal.data(), TOP_PALETTE * 4,
                                  cudaMemcpyHostToDevice, s));
+    top_byte_kernel<<<(nt + 255) / 256, 256, 0, s>>>(word, nt, dmap, cov->top);
+    note_launch();
+    SDB_TRY_CUDA(cudaGetLastError());
     cov->top_level = Lt;
   }
   SDB_TRY_CUDA(cudaStreamSynchronize(s));
