@@ -279,18 +279,20 @@ sdb_status sdb_result_bounds(const uint64_t *d_count, const int64_t *d_sum,
                              void *cuda_stream);
 
 /* sdb_join_aggregate for n_covs coverings of the same polygons on the same grid
- * (an eps sweep) in one pass over the points: each point is read and its cell
- * id computed once, at the finest level among the coverings (a coarser id is
- * its prefix), then looked up in every covering.  d_count and d_sum hold
- * n_covs rows of P entries (row c for covs[c]), zeroed by the call; results
- * equal n_covs separate sdb_join_aggregate calls.  It saves the repeated reads
- * and encodings of the points, but its lookups read the coverings' root models
- * through the L1 cache instead of shared memory; on GB300 with the 263-zone
- * sweep four separate joins are faster (6.4 vs 8.0 ms), so the hot path uses
- * those.  Asynchronous.
+ * (an eps sweep) in one pass over the points: each point is read once.  With
+ * the binary or learned lookup its cell id is computed once, at the finest
+ * level among the coverings (a coarser id is its prefix), then looked up in
+ * every covering.  With the table lookups (SDB_LOOKUP_TABLE,
+ * SDB_LOOKUP_TABLE_LEARNED; every covering needs its cell table, and the
+ * learned one its index) a combined top level -- the cells whose payload is
+ * the same single polygon in every covering -- answers a point for all
+ * coverings with one shared-memory read, and the other points go through each
+ * covering's table in turn.  d_count and d_sum hold n_covs rows of P entries
+ * (row c for covs[c]), zeroed by the call; results equal n_covs separate
+ * sdb_join_aggregate calls.  Asynchronous.
  * SDB_EINVAL: as sdb_join_aggregate, a NULL covering, coverings that differ in
- * polygon count or grid bits, n_covs = 0, SDB_LOOKUP_TABLE (binary or learned
- * lookups only). */
+ * polygon count or grid bits, n_covs = 0, a covering without the table or
+ * index its lookup needs. */
 sdb_status sdb_join_aggregate_multi(const uint32_t *d_x, const uint32_t *d_y,
                                     const int32_t *d_attr, uint64_t n,
                                     const sdb_covering *const *covs, uint32_t n_covs, int lookup,

@@ -636,19 +636,12 @@ sdb_status sdb_join_aggregate_multi(const uint32_t* d_x, const uint32_t* d_y, co
     set_error("d_sum requested without d_attr");
     return SDB_EINVAL;
   }
-  if (lookup != SDB_LOOKUP_BINARY && lookup != SDB_LOOKUP_LEARNED) {
-    set_error("lookup %d: the multi-covering join takes the binary or learned lookup", lookup);
-    return SDB_EINVAL;
-  }
   for (uint32_t c = 0; c < n_covs; ++c) {
     if (!covs[c] || covs[c]->P != covs[0]->P || covs[c]->B != covs[0]->B) {
       set_error("covering %u is NULL or differs in polygon count or grid bits", c);
       return SDB_EINVAL;
     }
-    if (lookup == SDB_LOOKUP_LEARNED && !covs[c]->leaves) {
-      set_error("learned lookup requested but covering %u has no index", c);
-      return SDB_EINVAL;
-    }
+    SDB_TRY(check_lookup(covs[c], lookup));
     SDB_TRY(check_device(covs[c]));
   }
   return launch_join_multi(d_x, d_y, d_attr, n, covs, n_covs, lookup, d_count, d_sum,

@@ -804,6 +804,186 @@ sdb_status launch_multi_t(const MultiArgs& M, cudaStream_t s) {
   return SDB_OK;
 }
 
+// ------------------------------------------------ an eps sweep through the tables
+// One pass over the points for up to MULTI coverings of the same polygons with
+// cell tables (an eps sweep): each point is read once; a combined top level in
+// shared memory -- a top cell whose payload is the same single polygon in
+// every covering -- answers it for all coverings at once; otherwise each
+// covering's table, second level and (for a mixed cell) window search answer it
+// in turn, per lane.
+struct SweepArgs {
+  JoinArgs c[MULTI];       // per covering: its table, lookup and outputs
+  uint32_t E;
+  const uint8_t* top;      // combined top level (nullptr: every point asks the tables)
+  const uint32_t* pal;     // its palette (the first covering's)
+  uint32_t top_xy, top_lev;
+};
+
+struct TopSet {
+  const uint8_t* top[MULTI];
+  const uint32_t* pal[MULTI];
+  uint32_t E;
+};
+
+// combined top level: the first covering's byte where every covering's cell
+// holds the same single polygon (or all hold none), TOP_ASK elsewhere
+__global__ void sweep_top_kernel(TopSet t, uint32_t nt, uint8_t* __restrict__ out) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nt) return;
+  const uint8_t b0 = t.top[0][c];
+  uint8_t v = b0;
+  if (b0 != TOP_ASK) {
+    const uint32_t p0 = b0 < TOP_NONE ? t.pal[0][b0] : 0xFFFFFFFFu;
+    for (uint32_t e = 1; e < t.E; ++e) {
+      const uint8_t b = t.top[e][c];
+      const uint32_t p = b < TOP_NONE ? t.pal[e][b] : (b == TOP_NONE ? 0xFFFFFFFFu : 0xFFFFFFFEu);
+      if (p != p0) v = TOP_ASK;
+    }
+  }
+  out[c] = v;
+}
+
+// one covering's answer for a point that the combined top level did not give:
+// its table entry, its second-level entry in a mixed bucket, a window search in
+// a mixed sub-cell
+template <int LOOKUP, bool SMEM, bool SUM>
+__device__ __forceinline__ void sweep_one(uint32_t x, uint32_t y, int32_t a,
+                                          const uint32_t* s_tab, const Acc& acc,
+                                          const JoinArgs& A) {
+  uint32_t e = __ldg(A.tab + (((y >> A.txy) << A.tlev) | (x >> A.txy)));
+  if (A.sub && e >= TAB_MIXED && e != NONE) {
+    const uint32_t smask = (1u << A.s2) - 1u;
+    e = __ldg(A.sub + (((uint64_t)(e & ~TAB_MIXED) << (2 * A.s2)) |
+                       (((y >> A.txy2) & smask) << A.s2) | ((x >> A.txy2) & smask)));
+  }
+  if (e >= TAB_MIXED && e != NONE) {
+    QEnt E;
+    E.x = x;
+    E.y = y;
+    E.m = e & ~TAB_MIXED;
+    E.a = a;
+    resolve_mixed<LOOKUP, SMEM, SUM, false>(E, s_tab, acc, A);
+  } else {
+    add_pay<SMEM, SUM, false>(e, a, acc, A);
+  }
+}
+
+template <int LOOKUP, bool SMEM, bool SUM>
+__global__ __launch_bounds__(TOP_THREADS, TOP_BLOCKS) void sweep_kernel(SweepArgs S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int TPB = TOP_THREADS;
+  const JoinArgs& A0 = S.c[0];
+  const size_t P = SMEM ? A0.P : 0;
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  unsigned char* accb = smem + HILBERT3_COMPACT_BYTES;
+  Acc acc[MULTI];
+#pragma unroll
+  for (int e = 0; e < MULTI; ++e) acc[e] = acc_at<SUM, false>(accb + e * acc_bytes(P, SUM, false), P);
+  uint8_t* s_top = accb + ((MULTI * acc_bytes(P, SUM, false) + 15) & ~(size_t)15);
+  uint32_t* s_pal = reinterpret_cast<uint32_t*>(s_top + ((size_t)1 << (2 * S.top_lev)));
+  hilbert3_fill_compact(s_tab);
+  if (S.top) {
+    const uint4* src = reinterpret_cast<const uint4*>(S.top);
+    uint4* dst = reinterpret_cast<uint4*>(s_top);
+    for (uint32_t i = threadIdx.x; i < (1u << (2 * S.top_lev)) / 16; i += TPB) dst[i] = __ldg(src + i);
+    for (uint32_t i = threadIdx.x; i < TOP_PALETTE; i += TPB) s_pal[i] = __ldg(S.pal + i);
+  }
+  if (SMEM)
+#pragma unroll
+    for (int e = 0; e < MULTI; ++e)
+      if (e < (int)S.E) acc_zero<SUM, false>(acc[e], (uint32_t)P);
+  __syncthreads();
+
+  const uint32_t gmask = ~((1u << A0.B) - 1u);
+  const uint64_t per_tile = (uint64_t)TPB * 4;
+  const uint64_t ntiles = (A0.n + per_tile - 1) / per_tile;
+  uint32_t since_flush = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t e0 = t * per_tile + (uint64_t)threadIdx.x * 4;
+    uint32_t xs[4], ys[4];
+    int32_t as[4];
+    bool ok[4];
+    if (A0.vec && e0 + 3 < A0.n) {
+      const uint4 xv = __ldcs(reinterpret_cast<const uint4*>(A0.x + e0));
+      const uint4 yv = __ldcs(reinterpret_cast<const uint4*>(A0.y + e0));
+      xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
+      ys[0] = yv.x; ys[1] = yv.y; ys[2] = yv.z; ys[3] = yv.w;
+      if (SUM) {
+        const int4 av = __ldcs(reinterpret_cast<const int4*>(A0.attr + e0));
+        as[0] = av.x; as[1] = av.y; as[2] = av.z; as[3] = av.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ok[q] = true;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ok[q] = e0 + q < A0.n;
+        xs[q] = ok[q] ? A0.x[e0 + q] : 0u;
+        ys[q] = ok[q] ? A0.y[e0 + q] : 0u;
+        as[q] = (SUM && ok[q]) ? A0.attr[e0 + q] : 0;
+      }
+    }
+    if (!SUM) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) as[q] = 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!ok[q] || ((xs[q] | ys[q]) & gmask)) continue;
+      const uint8_t v =
+          S.top ? s_top[((ys[q] >> S.top_xy) << S.top_lev) | (xs[q] >> S.top_xy)] : TOP_ASK;
+      if (v < TOP_NONE) {  // the same single polygon in every covering
+        const uint32_t p = s_pal[v];
+#pragma unroll
+        for (int e = 0; e < MULTI; ++e)
+          if (e < (int)S.E) add_pay<SMEM, SUM, false>(p, as[q], acc[e], S.c[e]);
+      } else if (v == TOP_ASK) {
+#pragma unroll
+        for (int e = 0; e < MULTI; ++e)
+          if (e < (int)S.E) sweep_one<LOOKUP, SMEM, SUM>(xs[q], ys[q], as[q], s_tab, acc[e], S.c[e]);
+      }
+    }
+    if (SMEM && ++since_flush == TOP_FLUSH_TILES) {
+      since_flush = 0;
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < MULTI; ++e)
+        if (e < (int)S.E) flush_acc<SUM, false>(acc[e], S.c[e]);
+      __syncthreads();
+    }
+  }
+  if (SMEM) {
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < MULTI; ++e)
+      if (e < (int)S.E) flush_acc<SUM, false>(acc[e], S.c[e]);
+  }
+}
+
+template <int LOOKUP, bool SMEM, bool SUM>
+sdb_status launch_sweep_t(const SweepArgs& S, cudaStream_t s) {
+  size_t smem = HILBERT3_COMPACT_BYTES;
+  if (SMEM) smem += ((size_t)MULTI * acc_bytes(S.c[0].P, SUM, false) + 15) & ~(size_t)15;
+  if (S.top) smem += ((size_t)1 << (2 * S.top_lev)) + 4 * TOP_PALETTE;
+  smem = (smem + 15) & ~(size_t)15;
+  auto kern = sweep_kernel<LOOKUP, SMEM, SUM>;
+  if (smem > 48 * 1024)
+    SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TOP_THREADS, smem));
+  if (per_sm < 1) per_sm = 1;
+  SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    carveout_pct((size_t)per_sm * (smem + 1024))));
+  uint64_t blocks = (uint64_t)num_sms() * per_sm;
+  const uint64_t need = (S.c[0].n + 4 * TOP_THREADS - 1) / (4 * TOP_THREADS);
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  TraceScope tr("join", s);
+  kern<<<(unsigned)blocks, TOP_THREADS, smem, s>>>(S);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
+  return SDB_OK;
+}
+
 template <bool RANGE>
 sdb_status launch_pick(const JoinArgs& A, int lookup, bool has_sum, cudaStream_t s) {
   const bool smem = A.P <= (RANGE ? SMEM_POLYS_RANGE : SMEM_POLYS);
@@ -974,6 +1154,13 @@ JoinArgs join_args(const uint32_t* x, const uint32_t* y, const int32_t* attr, ui
   A.inv_w = 1.0f / (float)(1ull << cov->knot_wshift);
   A.nleaves = cov->leaf_bits ? (1u << cov->leaf_bits) : 0u;
   A.fallbacks = cov->fallbacks;
+  A.tab = cov->tab;
+  A.win = cov->sub ? cov->win2 : cov->win;
+  A.tlev = cov->tab_bits / 2;
+  A.txy = cov->B - A.tlev;
+  A.sub = cov->sub;
+  A.s2 = cov->sub_bits;
+  A.txy2 = A.txy - cov->sub_bits;
   return A;
 }
 }  // namespace
@@ -994,12 +1181,54 @@ sdb_status launch_join_multi(const uint32_t* x, const uint32_t* y, const int32_t
       if (zero) {
         SDB_TRY_CUDA(cudaMemsetAsync(count + (size_t)(e0 + e) * P, 0, (size_t)P * 8, s));
         if (sum) SDB_TRY_CUDA(cudaMemsetAsync(sum + (size_t)(e0 + e) * P, 0, (size_t)P * 8, s));
-        if (lookup == SDB_LOOKUP_LEARNED)
+        if (lookup == SDB_LOOKUP_LEARNED || lookup == SDB_LOOKUP_TABLE_LEARNED)
           SDB_TRY_CUDA(cudaMemsetAsync(c->fallbacks, 0, sizeof(unsigned long long), s));
       }
       M.c[e] = join_args(x, y, attr, n, c, count + (size_t)(e0 + e) * P,
                          sum ? sum + (size_t)(e0 + e) * P : nullptr);
       M.shift[e] = 2 * (covs[e0 + finest]->F - c->F);
+    }
+    if (lookup == SDB_LOOKUP_TABLE || lookup == SDB_LOOKUP_TABLE_LEARNED) {
+      if (n == 0) continue;
+      SweepArgs S{};
+      S.E = m;
+      for (uint32_t e = 0; e < m; ++e) S.c[e] = M.c[e];
+      // the combined top level when every covering has one of the same level
+      Scratch sc(s);
+      bool tops = true;
+      for (uint32_t e = 0; e < m; ++e)
+        tops = tops && covs[e0 + e]->top && covs[e0 + e]->top_level == covs[e0]->top_level;
+      if (tops) {
+        const uint32_t Lt = covs[e0]->top_level, nt = 1u << (2 * Lt);
+        uint8_t* ctop;
+        SDB_TRY(sc.get(&ctop, nt));
+        TopSet ts{};
+        ts.E = m;
+        for (uint32_t e = 0; e < m; ++e) {
+          ts.top[e] = covs[e0 + e]->top;
+          ts.pal[e] = covs[e0 + e]->top_pal;
+        }
+        sweep_top_kernel<<<(nt + 255) / 256, 256, 0, s>>>(ts, nt, ctop);
+        note_launch();
+        SDB_TRY_CUDA(cudaGetLastError());
+        S.top = ctop;
+        S.pal = covs[e0]->top_pal;
+        S.top_lev = Lt;
+        S.top_xy = covs[e0]->B - Lt;
+      }
+      const bool smem = (uint64_t)MULTI * P <= SMEM_POLYS;
+      const bool has_sum = sum != nullptr;
+      sdb_status st;
+      if (lookup == SDB_LOOKUP_TABLE)
+        st = smem ? (has_sum ? launch_sweep_t<3, true, true>(S, s) : launch_sweep_t<3, true, false>(S, s))
+                  : (has_sum ? launch_sweep_t<3, false, true>(S, s)
+                             : launch_sweep_t<3, false, false>(S, s));
+      else
+        st = smem ? (has_sum ? launch_sweep_t<4, true, true>(S, s) : launch_sweep_t<4, true, false>(S, s))
+                  : (has_sum ? launch_sweep_t<4, false, true>(S, s)
+                             : launch_sweep_t<4, false, false>(S, s));
+      SDB_TRY(st);
+      continue;
     }
     // the encoding parameters of the finest covering go with c[0]
     const JoinArgs& Af = M.c[finest];

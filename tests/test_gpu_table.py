@@ -179,7 +179,9 @@ def test_table_edge_cases_and_errors(cuda, sdblib, orc, lookup):
                  lambda: sdblib.covering_build_table(fresh, 7),
                  lambda: sdblib.covering_build_table(fresh, 27),
                  lambda: sdblib.join_aggregate(x, y, None, cov, 5, z),
-                 lambda: sdblib.join_aggregate_multi(x, y, None, [cov], TABLE, z[None, :])):
+                 lambda: sdblib.join_aggregate_multi(x, y, None, [cov, fresh], TABLE,
+                                                     torch.zeros((2, P.n), dtype=torch.int64,
+                                                                 device="cuda"))):
         with pytest.raises(sdblib.SdbError) as e:
             call()
         assert e.value.status == sdblib.SDB_EINVAL
@@ -236,3 +238,48 @@ def test_table_full_size(cuda, sdblib):
                 assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), (eps,
                                                                                           tb)
                 no_fallback(sdblib, cov, lookup)
+
+
+@pytest.mark.parametrize("lookup", LOOKUPS)
+def test_table_sweep_join_equals_separate(cuda, sdblib, orc, lookup):
+    """One pass over the points for several coverings through their tables (the
+    combined top level where every covering holds the same polygon, each table
+    elsewhere) equals one join per covering and the oracle; more coverings than
+    one pass takes, coverings without a common top level, ragged n, COUNT only."""
+    torch = cuda
+    T = W.zones263_tiling()
+    pts = W.mobility_points(W.BASE_SEED + 12, 300_007, 24, 32)
+    eps_list = [1024, 2 ** 14, 64, 4096, 256]
+    covs = [sdblib.build_covering(T, 24, e) for e in eps_list]
+    for c in covs:
+        build_table(sdblib, c, 22, lookup, leaf_bits=14)
+    x, y, a = dev(torch, pts.x), dev(torch, pts.y), dev(torch, pts.attr)
+    E, P = len(covs), T.n
+    for n in (pts.n, 1001, 0):
+        cnt = torch.full((E, P), 7, dtype=torch.int64, device="cuda")
+        sm = torch.full((E, P), 7, dtype=torch.int64, device="cuda")
+        sdblib.join_aggregate_multi(x[:n], y[:n], a[:n], covs, lookup, cnt, sm)
+        torch.cuda.synchronize()
+        for e, c in enumerate(covs):
+            want = join(torch, sdblib, c, pts, lookup, x=x[:n], y=y[:n], a=a[:n])
+            assert np.array_equal(cnt[e].cpu().numpy().view(np.uint64), want[0]), (n, e)
+            assert np.array_equal(sm[e].cpu().numpy(), want[1]), (n, e)
+            no_fallback(sdblib, c, lookup)
+    want = orc.cover(T, 64).join(pts.x, pts.y, pts.attr)
+    cnt = torch.zeros((E, P), dtype=torch.int64, device="cuda")
+    sdblib.join_aggregate_multi(x, y, None, covs, lookup, cnt)
+    torch.cuda.synchronize()
+    assert np.array_equal(cnt[2].cpu().numpy().view(np.uint64), want[0])
+    # top levels of different levels (a 2^8-bucket table has its top at level 4):
+    # no combined level, every point asks the tables
+    small = sdblib.build_covering(T, 24, 2 ** 13)
+    build_table(sdblib, small, 8, lookup, leaf_bits=6)
+    pair = [small, covs[2]]
+    cnt = torch.zeros((2, P), dtype=torch.int64, device="cuda")
+    sm = torch.zeros((2, P), dtype=torch.int64, device="cuda")
+    sdblib.join_aggregate_multi(x, y, a, pair, lookup, cnt, sm)
+    torch.cuda.synchronize()
+    for e, c in enumerate(pair):
+        want = join(torch, sdblib, c, pts, lookup, x=x, y=y, a=a)
+        assert np.array_equal(cnt[e].cpu().numpy().view(np.uint64), want[0]), e
+        assert np.array_equal(sm[e].cpu().numpy(), want[1]), e
