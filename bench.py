@@ -490,6 +490,15 @@ def main():
     res["learned_only_value"] = lk_rows["learned"]["points_per_s"]
     res["table_value"] = lk_rows["table"]["points_per_s"]
     res["lookups_agree"] = agree
+    # the sweep in one pass over the points (sdb_join_aggregate_multi through the
+    # tables: the points read once, a combined top level for all four coverings)
+    sw_ms = timed(torch, stream, lambda: sdb.join_aggregate_multi(x, y, a, covs, HEAD, cnt, sm,
+                                                                  stream), reps)
+    res["sweep_fused"] = {"ms": sw_ms, "points_per_s": N * E / (sw_ms / 1e3),
+                          "same_as_separate_joins": bool(torch.equal(cnt, head_cnt)
+                                                         and torch.equal(sm, head_sm)),
+                          "what": "one pass over the points for all four coverings "
+                                  "(table + learned lookup)"}
 
     # ---- the timed coverings against the CPU oracle: the first 1M points
     # joined on the device with the headline lookup vs the definitional test
