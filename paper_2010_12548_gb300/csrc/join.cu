@@ -843,31 +843,6 @@ __global__ void sweep_top_kernel(TopSet t, uint32_t nt, uint8_t* __restrict__ ou
   out[c] = v;
 }
 
-// one covering's answer for a point that the combined top level did not give:
-// its table entry, its second-level entry in a mixed bucket, a window search in
-// a mixed sub-cell
-template <int LOOKUP, bool SMEM, bool SUM>
-__device__ __forceinline__ void sweep_one(uint32_t x, uint32_t y, int32_t a,
-                                          const uint32_t* s_tab, const Acc& acc,
-                                          const JoinArgs& A) {
-  uint32_t e = __ldg(A.tab + (((y >> A.txy) << A.tlev) | (x >> A.txy)));
-  if (A.sub && e >= TAB_MIXED && e != NONE) {
-    const uint32_t smask = (1u << A.s2) - 1u;
-    e = __ldg(A.sub + (((uint64_t)(e & ~TAB_MIXED) << (2 * A.s2)) |
-                       (((y >> A.txy2) & smask) << A.s2) | ((x >> A.txy2) & smask)));
-  }
-  if (e >= TAB_MIXED && e != NONE) {
-    QEnt E;
-    E.x = x;
-    E.y = y;
-    E.m = e & ~TAB_MIXED;
-    E.a = a;
-    resolve_mixed<LOOKUP, SMEM, SUM, false>(E, s_tab, acc, A);
-  } else {
-    add_pay<SMEM, SUM, false>(e, a, acc, A);
-  }
-}
-
 template <int LOOKUP, bool SMEM, bool SUM>
 __global__ __launch_bounds__(TOP_THREADS, TOP_BLOCKS) void sweep_kernel(SweepArgs S) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -927,20 +902,52 @@ __global__ __launch_bounds__(TOP_THREADS, TOP_BLOCKS) void sweep_kernel(SweepArg
 #pragma unroll
       for (int q = 0; q < 4; ++q) as[q] = 0;
     }
+    // the combined top level first; then, covering by covering, the table
+    // entries of the points it did not answer, all four gathers in flight
+    bool ask[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
+      ask[q] = false;
       if (!ok[q] || ((xs[q] | ys[q]) & gmask)) continue;
       const uint8_t v =
           S.top ? s_top[((ys[q] >> S.top_xy) << S.top_lev) | (xs[q] >> S.top_xy)] : TOP_ASK;
+      ask[q] = v == TOP_ASK;
       if (v < TOP_NONE) {  // the same single polygon in every covering
         const uint32_t p = s_pal[v];
 #pragma unroll
         for (int e = 0; e < MULTI; ++e)
           if (e < (int)S.E) add_pay<SMEM, SUM, false>(p, as[q], acc[e], S.c[e]);
-      } else if (v == TOP_ASK) {
+      }
+    }
 #pragma unroll
-        for (int e = 0; e < MULTI; ++e)
-          if (e < (int)S.E) sweep_one<LOOKUP, SMEM, SUM>(xs[q], ys[q], as[q], s_tab, acc[e], S.c[e]);
+    for (int e = 0; e < MULTI; ++e) {
+      if (e >= (int)S.E) break;
+      const JoinArgs& A = S.c[e];
+      uint32_t en[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        en[q] = ask[q] ? __ldg(A.tab + (((ys[q] >> A.txy) << A.tlev) | (xs[q] >> A.txy))) : NONE;
+      if (A.sub) {
+        const uint32_t smask = (1u << A.s2) - 1u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (en[q] >= TAB_MIXED && en[q] != NONE)
+            en[q] = __ldg(A.sub + (((uint64_t)(en[q] & ~TAB_MIXED) << (2 * A.s2)) |
+                                   (((ys[q] >> A.txy2) & smask) << A.s2) |
+                                   ((xs[q] >> A.txy2) & smask)));
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (en[q] >= TAB_MIXED && en[q] != NONE) {
+          QEnt Q;
+          Q.x = xs[q];
+          Q.y = ys[q];
+          Q.m = en[q] & ~TAB_MIXED;
+          Q.a = as[q];
+          resolve_mixed<LOOKUP, SMEM, SUM, false>(Q, s_tab, acc[e], A);
+        } else {
+          add_pay<SMEM, SUM, false>(en[q], as[q], acc[e], A);
+        }
       }
     }
     if (SMEM && ++since_flush == TOP_FLUSH_TILES) {
