@@ -265,11 +265,11 @@ def test_table_sweep_join_equals_separate(cuda, sdblib, orc, lookup):
             assert np.array_equal(cnt[e].cpu().numpy().view(np.uint64), want[0]), (n, e)
             assert np.array_equal(sm[e].cpu().numpy(), want[1]), (n, e)
             no_fallback(sdblib, c, lookup)
-    want = orc.cover(T, 64).join(pts.x, pts.y, pts.attr)
+    want = orc.cover(T, 4096).join(pts.x, pts.y, pts.attr)
     cnt = torch.zeros((E, P), dtype=torch.int64, device="cuda")
     sdblib.join_aggregate_multi(x, y, None, covs, lookup, cnt)
     torch.cuda.synchronize()
-    assert np.array_equal(cnt[2].cpu().numpy().view(np.uint64), want[0])
+    assert np.array_equal(cnt[3].cpu().numpy().view(np.uint64), want[0])
     # top levels of different levels (a 2^8-bucket table has its top at level 4):
     # no combined level, every point asks the tables
     small = sdblib.build_covering(T, 24, 2 ** 13)
