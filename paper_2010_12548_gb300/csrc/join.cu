@@ -809,8 +809,12 @@ sdb_status launch_multi_t(const MultiArgs& M, cudaStream_t s) {
 // cell tables (an eps sweep): each point is read once; a combined top level in
 // shared memory -- a top cell whose payload is the same single polygon in
 // every covering -- answers it for all coverings at once; otherwise each
-// covering's table, second level and (for a mixed cell) window search answer it
-// in turn, per lane.
+// covering's table and second level answer it in turn.  Points in mixed cells
+// of any covering wait in one per-warp queue (the covering's number in the top
+// two bits of the queued cell index) and are searched 32 at a time, so the
+// kernel holds one copy of the window search per queue drain, not one per
+// covering and point (an unrolled form spent two thirds of its cycles waiting
+// for instructions).
 struct SweepArgs {
   JoinArgs c[MULTI];       // per covering: its table, lookup and outputs
   uint32_t E;
@@ -843,20 +847,55 @@ __global__ void sweep_top_kernel(TopSet t, uint32_t nt, uint8_t* __restrict__ ou
   out[c] = v;
 }
 
+// queued cell indices carry the covering in their top two bits (mixed cell
+// indices stay below TAB_MIXED_MAX < 2^30)
+constexpr uint32_t SWEEP_E_SHIFT = 30;
+static_assert(MULTI <= 4 && TAB_MIXED_MAX < (1u << SWEEP_E_SHIFT), "covering bits");
+
+// shared-memory layout of the sweep: the compact cell-id table, the per-warp
+// queues, MULTI accumulator sets, then (with a combined top level) its bytes
+// and palette
+__host__ __device__ constexpr size_t sweep_queue_off() { return HILBERT3_COMPACT_BYTES; }
+__host__ __device__ constexpr size_t sweep_acc_off() {
+  return sweep_queue_off() + (size_t)(TOP_THREADS / 32) * QCAP * sizeof(QEnt);
+}
+__host__ __device__ constexpr size_t sweep_top_off(size_t P, bool SUM) {
+  return (sweep_acc_off() + MULTI * acc_bytes(P, SUM, false) + 15) & ~(size_t)15;
+}
+
 template <int LOOKUP, bool SMEM, bool SUM>
-__global__ __launch_bounds__(TOP_THREADS, TOP_BLOCKS) void sweep_kernel(SweepArgs S) {
+__device__ __forceinline__ void sweep_resolve(QEnt Q, const uint32_t* s_tab,
+                                              unsigned char* accb, size_t ab, size_t P,
+                                              const JoinArgs* s_args) {
+  const uint32_t e = Q.m >> SWEEP_E_SHIFT;
+  Q.m &= (1u << SWEEP_E_SHIFT) - 1u;
+  resolve_mixed<LOOKUP, SMEM, SUM, false>(Q, s_tab, acc_at<SUM, false>(accb + e * ab, P),
+                                          s_args[e]);
+}
+
+template <int LOOKUP, bool SMEM, bool SUM>
+__global__ __launch_bounds__(TOP_THREADS, TOP_BLOCKS) void sweep_kernel(
+    const __grid_constant__ SweepArgs S) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // the coverings' arguments, read with a covering index known only at run time
+  __shared__ JoinArgs s_args[MULTI];
   constexpr int TPB = TOP_THREADS;
   const JoinArgs& A0 = S.c[0];
+  const uint32_t E = S.E;
   const size_t P = SMEM ? A0.P : 0;
+  const size_t ab = acc_bytes(P, SUM, false);
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
-  unsigned char* accb = smem + HILBERT3_COMPACT_BYTES;
-  Acc acc[MULTI];
-#pragma unroll
-  for (int e = 0; e < MULTI; ++e) acc[e] = acc_at<SUM, false>(accb + e * acc_bytes(P, SUM, false), P);
-  uint8_t* s_top = accb + ((MULTI * acc_bytes(P, SUM, false) + 15) & ~(size_t)15);
+  QEnt* s_q = reinterpret_cast<QEnt*>(smem + sweep_queue_off()) + (threadIdx.x >> 5) * QCAP;
+  unsigned char* accb = smem + sweep_acc_off();
+  uint8_t* s_top = smem + sweep_top_off(P, SUM);
   uint32_t* s_pal = reinterpret_cast<uint32_t*>(s_top + ((size_t)1 << (2 * S.top_lev)));
   hilbert3_fill_compact(s_tab);
+  {
+    static_assert(sizeof(JoinArgs) % 4 == 0, "word copy");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(S.c);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_args);
+    for (uint32_t i = threadIdx.x; i < E * (sizeof(JoinArgs) / 4); i += TPB) dst[i] = src[i];
+  }
   if (S.top) {
     const uint4* src = reinterpret_cast<const uint4*>(S.top);
     uint4* dst = reinterpret_cast<uint4*>(s_top);
@@ -864,11 +903,12 @@ __global__ __launch_bounds__(TOP_THREADS, TOP_BLOCKS) void sweep_kernel(SweepArg
     for (uint32_t i = threadIdx.x; i < TOP_PALETTE; i += TPB) s_pal[i] = __ldg(S.pal + i);
   }
   if (SMEM)
-#pragma unroll
-    for (int e = 0; e < MULTI; ++e)
-      if (e < (int)S.E) acc_zero<SUM, false>(acc[e], (uint32_t)P);
+    for (uint32_t e = 0; e < E; ++e) acc_zero<SUM, false>(acc_at<SUM, false>(accb + e * ab, P), (uint32_t)P);
   __syncthreads();
 
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t qn = 0;  // entries in this warp's queue (warp-uniform)
   const uint32_t gmask = ~((1u << A0.B) - 1u);
   const uint64_t per_tile = (uint64_t)TPB * 4;
   const uint64_t ntiles = (A0.n + per_tile - 1) / per_tile;
@@ -902,75 +942,79 @@ __global__ __launch_bounds__(TOP_THREADS, TOP_BLOCKS) void sweep_kernel(SweepArg
 #pragma unroll
       for (int q = 0; q < 4; ++q) as[q] = 0;
     }
-    // the combined top level first; then, covering by covering, the table
-    // entries of the points it did not answer, all four gathers in flight
+    // the combined top level: a payload shared by every covering, NONE, or ask
     bool ask[4];
+    uint32_t pc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      ask[q] = false;
-      if (!ok[q] || ((xs[q] | ys[q]) & gmask)) continue;
-      const uint8_t v =
-          S.top ? s_top[((ys[q] >> S.top_xy) << S.top_lev) | (xs[q] >> S.top_xy)] : TOP_ASK;
+      const bool in = ok[q] && !((xs[q] | ys[q]) & gmask);
+      const uint8_t v = !in ? TOP_NONE
+                            : (S.top ? s_top[((ys[q] >> S.top_xy) << S.top_lev) | (xs[q] >> S.top_xy)]
+                                     : TOP_ASK);
       ask[q] = v == TOP_ASK;
-      if (v < TOP_NONE) {  // the same single polygon in every covering
-        const uint32_t p = s_pal[v];
-#pragma unroll
-        for (int e = 0; e < MULTI; ++e)
-          if (e < (int)S.E) add_pay<SMEM, SUM, false>(p, as[q], acc[e], S.c[e]);
-      }
+      pc[q] = v < TOP_NONE ? s_pal[v] : NONE;
     }
-#pragma unroll
-    for (int e = 0; e < MULTI; ++e) {
-      if (e >= (int)S.E) break;
-      const JoinArgs& A = S.c[e];
+    // covering by covering (a loop the compiler keeps rolled): the table
+    // entries of the points the top level did not answer, all four gathers in
+    // flight, then the second level; mixed cells go to the queue
+#pragma unroll 1
+    for (uint32_t e = 0; e < E; ++e) {
+      const JoinArgs& A = s_args[e];
+      const Acc acc = acc_at<SUM, false>(accb + e * ab, P);
       uint32_t en[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        en[q] = ask[q] ? __ldg(A.tab + (((ys[q] >> A.txy) << A.tlev) | (xs[q] >> A.txy))) : NONE;
+        en[q] = ask[q] ? __ldg(A.tab + (((ys[q] >> A.txy) << A.tlev) | (xs[q] >> A.txy))) : pc[q];
       if (A.sub) {
         const uint32_t smask = (1u << A.s2) - 1u;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (en[q] >= TAB_MIXED && en[q] != NONE)
+          if (ask[q] && en[q] >= TAB_MIXED && en[q] != NONE)
             en[q] = __ldg(A.sub + (((uint64_t)(en[q] & ~TAB_MIXED) << (2 * A.s2)) |
                                    (((ys[q] >> A.txy2) & smask) << A.s2) |
                                    ((xs[q] >> A.txy2) & smask)));
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (en[q] >= TAB_MIXED && en[q] != NONE) {
-          QEnt Q;
+        const bool mix = ask[q] && en[q] >= TAB_MIXED && en[q] != NONE;
+        const uint32_t bal = __ballot_sync(FULL, mix);
+        if (mix) {
+          QEnt& Q = s_q[qn + __popc(bal & lt)];
           Q.x = xs[q];
           Q.y = ys[q];
-          Q.m = en[q] & ~TAB_MIXED;
+          Q.m = (en[q] & ~TAB_MIXED) | (e << SWEEP_E_SHIFT);
           Q.a = as[q];
-          resolve_mixed<LOOKUP, SMEM, SUM, false>(Q, s_tab, acc[e], A);
         } else {
-          add_pay<SMEM, SUM, false>(en[q], as[q], acc[e], A);
+          add_pay<SMEM, SUM, false>(en[q], as[q], acc, A);
+        }
+        qn += __popc(bal);
+        if (qn >= 32) {  // a full warp of held-back points: search their windows
+          __syncwarp();
+          qn -= 32;
+          const QEnt Q = s_q[qn + lane];
+          __syncwarp();
+          sweep_resolve<LOOKUP, SMEM, SUM>(Q, s_tab, accb, ab, P, s_args);
         }
       }
     }
     if (SMEM && ++since_flush == TOP_FLUSH_TILES) {
       since_flush = 0;
       __syncthreads();
-#pragma unroll
-      for (int e = 0; e < MULTI; ++e)
-        if (e < (int)S.E) flush_acc<SUM, false>(acc[e], S.c[e]);
+      for (uint32_t e = 0; e < E; ++e) flush_acc<SUM, false>(acc_at<SUM, false>(accb + e * ab, P), s_args[e]);
       __syncthreads();
     }
   }
+  __syncwarp();  // the rest of the queue
+  if (lane < qn) sweep_resolve<LOOKUP, SMEM, SUM>(s_q[lane], s_tab, accb, ab, P, s_args);
   if (SMEM) {
     __syncthreads();
-#pragma unroll
-    for (int e = 0; e < MULTI; ++e)
-      if (e < (int)S.E) flush_acc<SUM, false>(acc[e], S.c[e]);
+    for (uint32_t e = 0; e < E; ++e) flush_acc<SUM, false>(acc_at<SUM, false>(accb + e * ab, P), s_args[e]);
   }
 }
 
 template <int LOOKUP, bool SMEM, bool SUM>
 sdb_status launch_sweep_t(const SweepArgs& S, cudaStream_t s) {
-  size_t smem = HILBERT3_COMPACT_BYTES;
-  if (SMEM) smem += ((size_t)MULTI * acc_bytes(S.c[0].P, SUM, false) + 15) & ~(size_t)15;
+  size_t smem = sweep_top_off(SMEM ? S.c[0].P : 0, SUM);
   if (S.top) smem += ((size_t)1 << (2 * S.top_lev)) + 4 * TOP_PALETTE;
   smem = (smem + 15) & ~(size_t)15;
   auto kern = sweep_kernel<LOOKUP, SMEM, SUM>;
@@ -980,7 +1024,7 @@ sdb_status launch_sweep_t(const SweepArgs& S, cudaStream_t s) {
   SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TOP_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                    carveout_pct((size_t)per_sm * (smem + 1024))));
+                                    carveout_pct((size_t)per_sm * (smem + sizeof(SweepArgs::c) + 1024))));
   uint64_t blocks = (uint64_t)num_sms() * per_sm;
   const uint64_t need = (S.c[0].n + 4 * TOP_THREADS - 1) / (4 * TOP_THREADS);
   if (blocks > need) blocks = need > 0 ? need : 1;
