@@ -322,11 +322,10 @@ sdb_status sdb_join_aggregate_host(const uint32_t *h_x, const uint32_t *h_y, con
  * that every GPU which loads the library holds until the process exits.  The
  * call makes no cudaMalloc/cudaFree or other allocating call; it streams the
  * points SDB_NOALLOC_CHUNK at a time on cuda_stream alone and synchronises it
- * before returning (results in h_count/h_sum, P entries each).  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current and keeps it; after a cudaDeviceReset of that device the
- * kept address is stale, so the entry point must not be called again.  Every
- * call shares the array and clears the accumulators itself; calls whose GPU work
+ * before returning (results in h_count/h_sum, P entries each).  Each call
+ * looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, which allocates nothing), so calls after a
+ * cudaDeviceReset find the reloaded array.  Every call shares the array and clears the accumulators itself; calls whose GPU work
  * overlaps (other streams or threads) race on it.
  * SDB_EINVAL: more than SDB_NOALLOC_MAX_POLYGONS polygons, and the argument
  * errors of sdb_join_aggregate_host. */

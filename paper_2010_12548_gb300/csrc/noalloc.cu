@@ -13,14 +13,10 @@
 // Limits: at most SDB_NOALLOC_MAX_POLYGONS polygons per covering; any number of
 // points (they are processed SDB_NOALLOC_CHUNK at a time).  The array is shared
 // by every call: each call clears the accumulators before use, and calls whose
-// GPU work overlaps (on different streams or threads) race on the array.  The
-// first call on a device looks up the array's device address with that device
-// current and keeps it for the life of the process; a process that resets the
-// device (cudaDeviceReset) reloads the module, so it must not call this entry
-// point again afterwards (the kept address would be stale).
+// GPU work overlaps (on different streams or threads) race on the array.  Each
+// call looks up the array's device address in the current context, so calls
+// made after a device reset (which reloads the module) find it afresh.
 #include "sdb_internal.cuh"
-
-#include <mutex>
 
 namespace sdb {
 
@@ -33,26 +29,15 @@ constexpr size_t SCRATCH_BYTES = CHUNK * 12 + MAXP * 16;
 // staging: x[CHUNK] | y[CHUNK] | attr[CHUNK] | count[MAXP] | sum[MAXP]
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
-std::mutex g_mu;
-void* g_addr[64];
-
-// Device address of the array for the current device, looked up once per
-// device (host code only sees a host-side stand-in for the symbol).
+// Device address of the array in the current context (host code only sees a
+// host-side stand-in for the symbol).  Looked up on every call -- the lookup
+// allocates nothing -- so a context recreated after a device reset never sees
+// a stale address.
 sdb_status scratch_address(unsigned char** out) {
-  int dev = 0;
-  SDB_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("device %d out of range", dev);
-    return SDB_EINVAL;
-  }
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
-    g_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_addr[dev]);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+  *out = static_cast<unsigned char*>(p);
   return SDB_OK;
 }
 
