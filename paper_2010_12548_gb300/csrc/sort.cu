@@ -130,11 +130,17 @@ __global__ __launch_bounds__(RS_THREADS) void radix_hist_kernel(const uint64_t* 
 // by digit with a warp match; the block then lays its tile out in shared memory
 // sorted by digit (stable), and writes it back so that consecutive threads
 // write consecutive slots of the same digit's output run (coalesced), starting
-// at the block's global offset for that digit.
+// at the block's global offset for that digit.  Only the ranks stay in
+// registers across the block's digit prefix: the keys are read again (from L2,
+// four at a time) to lay the tile out, which keeps the keys-only form at five
+// resident blocks per SM instead of three.
 // SPLIT (keys only): the output is the packed covering record split into its
 // key (kout) and standard value (vout), sb slot bits.
+template <bool VALS>
+constexpr int scatter_blocks() { return VALS ? 3 : 5; }
+
 template <bool VALS, bool SPLIT = false>
-__global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
+__global__ __launch_bounds__(RS_THREADS, scatter_blocks<VALS>()) void radix_scatter_kernel(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ offs,
     uint32_t nblocks, uint32_t sb = 0) {
@@ -164,20 +170,25 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  // keys stay in registers through the ranking; values are read only when
-  // the tile's layout is known (fewer live registers, more resident warps)
-  uint64_t k[RS_ITEMS];
-  uint32_t rank[RS_ITEMS];
-#pragma unroll
-  for (int it = 0; it < RS_ITEMS; ++it) {  // all loads in flight before the ranking
-    const size_t g = base + (size_t)it * 32 + lane;
-    k[it] = g < n ? kin[g] : 0ull;
-  }
+  // the keys are loaded for their digits only (each dies once ranked), half
+  // of them in flight at a time; values are read only when the tile's layout
+  // is known.  Ranks, later tile slots (< RS_TILE), go two to a register.
+  uint32_t rank[RS_ITEMS / 2] = {};
+  static_assert(RS_TILE <= 65536, "16-bit slots");
+  constexpr int RS_HALF = RS_ITEMS / 2;
+  uint64_t k[RS_HALF];
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
+    if (it % RS_HALF == 0) {
+#pragma unroll
+      for (int j = 0; j < RS_HALF; ++j) {
+        const size_t g = base + (size_t)(it + j) * 32 + lane;
+        k[j] = g < n ? kin[g] : 0ull;
+      }
+    }
     const size_t g = base + (size_t)it * 32 + lane;
     const bool ok = g < n;
-    const uint32_t d = ok ? (uint32_t)((k[it] >> shift) & 255u) : 256u;
+    const uint32_t d = ok ? (uint32_t)((k[it % RS_HALF] >> shift) & 255u) : 256u;
     // one lane per digit reads and advances the warp's counter (fewer
     // shared-memory bank conflicts than every lane reading it)
     const unsigned peers = __match_any_sync(FULL, d);
@@ -186,7 +197,7 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     before = __shfl_sync(FULL, before, lead);
     if (ok && lane == lead) cnt[w][d] = before + __popc(peers);
     __syncwarp();
-    rank[it] = before + __popc(peers & lt);
+    rank[it >> 1] |= (before + __popc(peers & lt)) << (16 * (it & 1));
   }
   __syncthreads();
   // digit totals of the tile -> warp prefixes; thread d owns digit d
@@ -216,14 +227,26 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     dstart[threadIdx.x] = wpre + inc - total;
   }
   __syncthreads();
-  // stable layout of the tile by digit in shared memory (rank becomes the slot)
+  // stable layout of the tile by digit in shared memory (rank becomes the
+  // slot); the keys come back from L2 four at a time
 #pragma unroll
-  for (int it = 0; it < RS_ITEMS; ++it) {
-    const size_t g = base + (size_t)it * 32 + lane;
-    if (g < n) {
-      const uint32_t d = (uint32_t)((k[it] >> shift) & 255u);
-      rank[it] += dstart[d] + cnt[w][d];
-      sk[rank[it]] = k[it];
+  for (int it0 = 0; it0 < RS_ITEMS; it0 += 4) {
+    uint64_t kk[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const size_t g = base + (size_t)(it0 + j) * 32 + lane;
+      kk[j] = g < n ? __ldcg(kin + g) : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const size_t g = base + (size_t)(it0 + j) * 32 + lane;
+      if (g < n) {
+        const uint32_t d = (uint32_t)((kk[j] >> shift) & 255u);
+        const int it = it0 + j;
+        const uint32_t slot = ((rank[it >> 1] >> (16 * (it & 1))) & 0xffffu) + dstart[d] + cnt[w][d];
+        rank[it >> 1] += (slot - ((rank[it >> 1] >> (16 * (it & 1))) & 0xffffu)) << (16 * (it & 1));
+        sk[slot] = kk[j];
+      }
     }
   }
   if (VALS) {
@@ -242,7 +265,7 @@ __global__ __launch_bounds__(RS_THREADS, 3) void radix_scatter_kernel(
     }
 #pragma unroll
     for (int it = 0; it < RS_ITEMS; ++it)
-      if (base + (size_t)it * 32 + lane < n) sv[rank[it]] = v[it];
+      if (base + (size_t)it * 32 + lane < n) sv[(rank[it >> 1] >> (16 * (it & 1))) & 0xffffu] = v[it];
   }
   __syncthreads();
   const uint32_t tile_n = (uint32_t)min((size_t)RS_TILE, n - tile0);
@@ -272,7 +295,8 @@ sdb_status radix_sort_impl(uint64_t* keys, uint32_t* vals, uint64_t* ktmp, uint3
     return SDB_EINVAL;
   }
   uint32_t nblocks = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
-  constexpr size_t SCATTER_SMEM = (size_t)RS_TILE * (VALS ? 16 : 12);
+  // keys (8 B each), and with values the values' slots and their staging
+  constexpr size_t SCATTER_SMEM = (size_t)RS_TILE * (VALS ? 16 : 8);
   SDB_TRY_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<VALS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)SCATTER_SMEM));
