@@ -772,11 +772,16 @@ def timed(torch, stream, fn, reps):
 
 def poisson_serve(sdb, srv, queries, rate, n, seed):
     """Submit n queries at Poisson arrival times (rate per second) from a
-    submitter thread; returns per-query latencies and the wall time."""
+    submitter thread; returns per-query latencies, batch sizes, cache hits, the
+    wall time and how late each submit came against its arrival time (the
+    queries are marshalled before the clock starts, so the submitter keeps
+    pace with the arrivals)."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, size=n)
     order = rng.integers(0, len(queries), size=n)
+    preps = [srv.prepare(*queries[order[k]]) for k in range(n)]
     tickets = [None] * n
+    sub_t = np.zeros(n)
     t0 = time.perf_counter()
     due = t0 + np.cumsum(gaps)
 
@@ -788,8 +793,8 @@ def poisson_serve(sdb, srv, queries, rate, n, seed):
                     break
                 if due[k] - now > 2e-4:
                     time.sleep(min(1e-3, due[k] - now - 1e-4))
-            row, ids = queries[order[k]]
-            tickets[k] = srv.submit(row, ids)
+            tickets[k] = srv.submit_prepared(preps[k])
+            sub_t[k] = time.perf_counter()
     th = threading.Thread(target=submitter)
     th.start()
     lat, batch, hits = [], [], 0
@@ -800,7 +805,7 @@ def poisson_serve(sdb, srv, queries, rate, n, seed):
         batch.append(info.batch_size)
         hits += info.cache_hit
     wall = time.perf_counter() - t0
-    return np.asarray(lat), np.asarray(batch), hits, wall
+    return np.asarray(lat), np.asarray(batch), hits, wall, (sub_t - due) * 1e3
 
 
 def point_index_leg(args, sdb, torch, dev, stream, T, pts, resident):
@@ -1144,13 +1149,15 @@ def resident_legs(args, legs, sdb, torch, dev, stream):
                 n = int(min(4000, max(400, rate * 2)))
                 if kind == "plain":
                     n = min(n, 600)
-                lat, bs, hits, wall = poisson_serve(sdb, srv, queries, rate, n, seed=rate)
+                lat, bs, hits, wall, lag = poisson_serve(sdb, srv, queries, rate, n, seed=rate)
                 st = srv.stats()
                 srv.destroy()
                 serving[kind].append({
                     "rate": rate, "queries": n, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                    "throughput_qps": n / wall, "mean_batch": float(bs.mean()),
+                    "throughput_qps": n / wall, "wall_s": float(wall),
+                    "submit_lag_p99_ms": float(np.percentile(lag, 99)),
+                    "submit_lag_max_ms": float(lag.max()), "mean_batch": float(bs.mean()),
                     "cache_hit_rate": hits / n, "batches": int(st.batches),
                     "cache_bytes": int(st.peak_bytes)})
         out["serving"] = serving

@@ -542,15 +542,25 @@ class Server:
         self.points = points
         self.n_polygons = P
 
-    def submit(self, query, subset_ids) -> int:
-        """Queue (x0, y0, x1, y1, eps, _, poly_cnt) with its subset ids; returns a ticket."""
+    @staticmethod
+    def prepare(query, subset_ids):
+        """The marshalled arguments of one submit (the query record and its
+        subset ids), for callers that submit at high rates."""
         ids = np.ascontiguousarray(subset_ids, np.uint32)
         q = Query(*[int(v) for v in query])
         q.poly_off = 0
         q.poly_cnt = len(ids)
+        return (q, ids, C.byref(q), _np_ptr(ids))
+
+    def submit_prepared(self, prep) -> int:
+        """Queue a query marshalled by prepare(); returns a ticket."""
         t = C.c_uint64()
-        _check(lib().sdb_server_submit(self._h, C.byref(q), _np_ptr(ids), C.byref(t)))
+        _check(lib().sdb_server_submit(self._h, prep[2], prep[3], C.byref(t)))
         return t.value
+
+    def submit(self, query, subset_ids) -> int:
+        """Queue (x0, y0, x1, y1, eps, _, poly_cnt) with its subset ids; returns a ticket."""
+        return self.submit_prepared(self.prepare(query, subset_ids))
 
     def wait(self, ticket: int, poly_cnt: int, timeout_ms: int = 60_000):
         """(count, sum, TicketInfo) of a ticket; raises SdbError(SDB_ETIMEOUT) on timeout."""
