@@ -54,7 +54,7 @@ TABLE_BITS = 22  # its first level, the cell table: 2^22 buckets (16 MB), fewer 
 JOIN_FINEST_TRAFFIC = {"table_learned": {"eps": 64, "leaf_bits": 16, "bytes_per_point": 13.929}}
 # DRAM bytes of one launch of radix_scatter_kernel (a keys-only pass) in the
 # sweep's record sort: profiles/radix_scatter_kernel_sweep_zones263.txt
-SCATTER_TRAFFIC = {"records": 117_378_603, "passes": 5, "bytes": 1.8595e9}
+SCATTER_TRAFFIC = {"records": 117_378_603, "passes": 5, "bytes": 1.8926e9}
 
 
 def leaf_bits_for(n_ranges: int) -> int:
@@ -467,16 +467,22 @@ def main():
     reps = max(3, min(args.steps, 10))
     agree = True
     lk_rows = {}
-    for name, lk, bits in (("binary", PLAIN, None), ("learned", sdb.LOOKUP_LEARNED, LEAF_BITS),
-                           ("learned12", sdb.LOOKUP_LEARNED, 12), ("table", sdb.LOOKUP_TABLE, None)):
+    # (the "_line_root" rows fit the index with its root as one line over the
+    # id space, the plain two-level model, instead of 2^12 root segments)
+    for name, lk, bits, root in (("binary", PLAIN, None, None),
+                                 ("learned", sdb.LOOKUP_LEARNED, LEAF_BITS, None),
+                                 ("learned12", sdb.LOOKUP_LEARNED, 12, None),
+                                 ("learned_line_root", sdb.LOOKUP_LEARNED, LEAF_BITS, 0),
+                                 ("table_learned_line_root", HEAD, LEAF_BITS, 0),
+                                 ("table", sdb.LOOKUP_TABLE, None, None)):
         per = {}
         for i, c in enumerate(covs):
             if bits:
-                sdb.covering_build_index(c, bits, stream)
+                sdb.covering_build_index(c, bits, stream, root_bits=root)
             per[str(w.eps[i])] = timed(torch, stream, lambda c=c, i=i: sdb.join_aggregate(
                 x, y, a, c, lk, cnt[i], sm[i], stream), reps)
             agree &= bool(torch.equal(cnt[i], head_cnt[i]) and torch.equal(sm[i], head_sm[i]))
-            if lk == sdb.LOOKUP_LEARNED:
+            if lk in (sdb.LOOKUP_LEARNED, sdb.LOOKUP_TABLE_LEARNED):
                 per[str(w.eps[i]) + "_fallbacks"] = sdb.covering_fallbacks(c, stream)
                 mw, xw = sdb.covering_index_stats(c)
                 per[str(w.eps[i]) + "_window_mean"] = mw
@@ -805,7 +811,12 @@ def poisson_serve(sdb, srv, queries, rate, n, seed):
         batch.append(info.batch_size)
         hits += info.cache_hit
     wall = time.perf_counter() - t0
-    return np.asarray(lat), np.asarray(batch), hits, wall, (sub_t - due) * 1e3
+    lat = np.asarray(lat)
+    # the last completion: each query's submit time plus the latency the server
+    # measured for it (the ticket collection above runs after the arrivals and
+    # is not part of the service)
+    span = float((sub_t + lat / 1e3).max() - t0)
+    return lat, np.asarray(batch), hits, wall, span, float(gaps.sum()), (sub_t - due) * 1e3
 
 
 def point_index_leg(args, sdb, torch, dev, stream, T, pts, resident):
@@ -1149,13 +1160,16 @@ def resident_legs(args, legs, sdb, torch, dev, stream):
                 n = int(min(4000, max(400, rate * 2)))
                 if kind == "plain":
                     n = min(n, 600)
-                lat, bs, hits, wall, lag = poisson_serve(sdb, srv, queries, rate, n, seed=rate)
+                lat, bs, hits, wall, span, offered, lag = poisson_serve(sdb, srv, queries,
+                                                                        rate, n, seed=rate)
                 st = srv.stats()
                 srv.destroy()
                 serving[kind].append({
                     "rate": rate, "queries": n, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                    "throughput_qps": n / wall, "wall_s": float(wall),
+                    "throughput_qps": n / span, "span_s": span,
+                    "offered_qps": n / offered,
+                    "wall_s_with_collection": float(wall),
                     "submit_lag_p99_ms": float(np.percentile(lag, 99)),
                     "submit_lag_max_ms": float(lag.max()), "mean_batch": float(bs.mean()),
                     "cache_hit_rate": hits / n, "batches": int(st.batches),

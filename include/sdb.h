@@ -117,6 +117,7 @@ typedef struct sdb_covering_info {
   uint64_t table_mixed;    /* buckets of the cell table that hold several ranges */
   uint32_t table_sub_bits; /* second level: 2^s x 2^s sub-cells per mixed bucket (0: none) */
   uint64_t table_sub_mixed;/* sub-cells that hold several ranges */
+  uint32_t index_root_bits;/* learned index root: 2^index_root_bits segments (0: one line) */
 } sdb_covering_info;
 
 /* Finest level for (grid_bits, eps), Sec. 2.2 (side eps/sqrt(2), so the
@@ -194,13 +195,22 @@ sdb_status sdb_covering_get_info(const sdb_covering *cov, sdb_covering_info *inf
 
 /* Fit the learned range index (Sec. 3, "Point Indexing": a learned model
  * predicts a key's position in the sorted array, after RadixSpline): a root
- * linear model maps a cell id to one of 2^leaf_bits leaves, each leaf a linear
- * model in FP32 on leaf-relative ids, plus the leaf's maximum prediction error
- * below and above, measured with the same FP32 arithmetic the lookup uses over
- * every id the root sends to that leaf.  The fit (least squares per leaf) runs
- * on the device.  Replaces a previous index.  Synchronises cuda_stream.
- * SDB_EINVAL: leaf_bits outside 4..20. */
+ * maps a cell id to one of 2^leaf_bits leaves, each leaf a linear model in FP32
+ * on leaf-relative ids, plus the leaf's maximum prediction error below and
+ * above, measured with the same FP32 arithmetic the lookup uses over every id
+ * the root sends to that leaf.  The root is piecewise linear in FP32 over
+ * 2^root_bits equal segments of [0, 4^F): at each segment end it takes the
+ * fraction of range starts below that id (the starts' cumulative distribution,
+ * so leaves receive about equal numbers of ranges); root_bits = 0 is a single
+ * root line from 0 to 4^F (the plain two-level model).  The fit (least squares
+ * per leaf) runs on the device.  Replaces a previous index.  Synchronises
+ * cuda_stream.  sdb_covering_build_index uses SDB_INDEX_ROOT_BITS_DEFAULT.
+ * SDB_EINVAL: leaf_bits outside 4..20, root_bits above SDB_INDEX_ROOT_BITS_MAX. */
+#define SDB_INDEX_ROOT_BITS_DEFAULT 12u
+#define SDB_INDEX_ROOT_BITS_MAX 12u
 sdb_status sdb_covering_build_index(sdb_covering *cov, uint32_t leaf_bits, void *cuda_stream);
+sdb_status sdb_covering_build_index_ex(sdb_covering *cov, uint32_t leaf_bits, uint32_t root_bits,
+                                       void *cuda_stream);
 
 /* Build the cell table: a direct-mapped first level of a radix tree over the
  * finest cell ids (the role of ACT's upper levels in Sec. 3, "Polygon

@@ -516,6 +516,7 @@ sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* inf
                           (4ull << (2 * cov->sub_bits)) * (cov->sub ? cov->tab_mixed : 0) +
                           8ull * cov->sub_mixed;
   info->index_leaf_bits = cov->leaf_bits;
+  info->index_root_bits = cov->leaf_bits ? cov->knot_bits : 0u;
   info->boundary_flags = cov->flagged ? 1u : 0u;
   info->table_bits = cov->tab ? cov->tab_bits : 0u;
   info->table_mixed = cov->tab_mixed;
@@ -524,7 +525,8 @@ sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* inf
   return SDB_OK;
 }
 
-sdb_status sdb_covering_build_index(sdb_covering* cov, uint32_t leaf_bits, void* cuda_stream) {
+sdb_status sdb_covering_build_index_ex(sdb_covering* cov, uint32_t leaf_bits, uint32_t root_bits,
+                                       void* cuda_stream) {
   if (!cov) {
     set_error("covering is NULL");
     return SDB_EINVAL;
@@ -533,8 +535,16 @@ sdb_status sdb_covering_build_index(sdb_covering* cov, uint32_t leaf_bits, void*
     set_error("leaf_bits %u outside 4..20", leaf_bits);
     return SDB_EINVAL;
   }
+  if (root_bits > SDB_INDEX_ROOT_BITS_MAX) {
+    set_error("root_bits %u above %u", root_bits, SDB_INDEX_ROOT_BITS_MAX);
+    return SDB_EINVAL;
+  }
   SDB_TRY(check_device(cov));
-  return build_learned_index(cov, leaf_bits, (cudaStream_t)cuda_stream);
+  return build_learned_index(cov, leaf_bits, root_bits, (cudaStream_t)cuda_stream);
+}
+
+sdb_status sdb_covering_build_index(sdb_covering* cov, uint32_t leaf_bits, void* cuda_stream) {
+  return sdb_covering_build_index_ex(cov, leaf_bits, SDB_INDEX_ROOT_BITS_DEFAULT, cuda_stream);
 }
 
 sdb_status sdb_covering_build_table(sdb_covering* cov, uint32_t table_bits, void* cuda_stream) {

@@ -5,7 +5,8 @@
 //
 //   root:  leaf(h) = clamp(floor(knot_j + (knot_{j+1} - knot_j) * frac), 0, L-1)  (FP32)
 //          with j = h >> wshift, frac = (h - (j << wshift)) / 2^wshift and
-//          knot_j = L * #{i : start_i < j << wshift} / R  (2^12 uniform knots)
+//          knot_j = L * #{i : start_i < j << wshift} / R  (2^K uniform knots,
+//          K = 12 by default; K = 0 is a single root line over [0, 4^F))
 //   leaf:  pred(h) = first + floor(fma(a, float(h - base), b))         (FP32)
 //
 // Both maps are monotone in h.  The root is the piecewise-linear interpolant of
@@ -174,12 +175,13 @@ __global__ void leaf_fit_kernel(const uint64_t* __restrict__ start, uint64_t R,
 
 }  // namespace
 
-sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream_t s) {
+sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, uint32_t root_bits,
+                               cudaStream_t s) {
   TraceScope tr("index.build", s);
   const uint32_t L = 1u << leaf_bits;
   const uint64_t R = cov->R;
   const uint64_t top = 1ull << (2 * cov->F);
-  const uint32_t kbits = 2 * cov->F < 12 ? 2 * cov->F : 12;
+  const uint32_t kbits = 2 * cov->F < root_bits ? 2 * cov->F : root_bits;
   const uint32_t K = 1u << kbits;
   const uint32_t wshift = 2 * cov->F - kbits;
   const float inv_w = 1.0f / (float)(1ull << wshift);  // exact: a power of two

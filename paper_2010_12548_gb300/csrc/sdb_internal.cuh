@@ -379,7 +379,8 @@ void viewport_pairs(const std::vector<uint32_t>& bb, uint32_t q, const sdb_query
 sdb_status polygon_bboxes(const sdb_polygons* polys, uint32_t B, std::vector<uint32_t>* bb);
 
 // learned.cu
-sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, cudaStream_t s);
+sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, uint32_t root_bits,
+                               cudaStream_t s);
 
 // cell table entries: a range payload, or TAB_MIXED | m for the m-th bucket that
 // meets several ranges (m < TAB_MIXED_MAX - 1; payload values 2^31 | r need

@@ -59,7 +59,7 @@ class CoveringInfo(C.Structure):
                 ("device_bytes", C.c_uint64), ("index_leaf_bits", C.c_uint32),
                 ("boundary_flags", C.c_uint32), ("table_bits", C.c_uint32),
                 ("table_mixed", C.c_uint64), ("table_sub_bits", C.c_uint32),
-                ("table_sub_mixed", C.c_uint64)]
+                ("table_sub_mixed", C.c_uint64), ("index_root_bits", C.c_uint32)]
 
 
 class Query(C.Structure):
@@ -116,6 +116,7 @@ def lib():
             "sdb_result_bounds": ([P, P, P, P, P, U32, P, P, P, P, P], I),
             "sdb_covering_get_info": ([P, P], I),
             "sdb_covering_build_index": ([P, U32, P], I),
+            "sdb_covering_build_index_ex": ([P, U32, U32, P], I),
             "sdb_covering_build_table": ([P, U32, P], I),
             "sdb_trace_enable": ([C.c_int], I),
             "sdb_trace_read": ([P, U32, P], I),
@@ -260,8 +261,12 @@ def build_coverings(polys, grid_bits: int, eps_list, stream=None, flags: int = 0
     return [Covering(o) for o in outs]
 
 
-def covering_build_index(cov: Covering, leaf_bits: int, stream=None):
-    _check(lib().sdb_covering_build_index(cov.handle, leaf_bits, _stream(stream)))
+def covering_build_index(cov: Covering, leaf_bits: int, stream=None, root_bits=None):
+    if root_bits is None:
+        _check(lib().sdb_covering_build_index(cov.handle, leaf_bits, _stream(stream)))
+    else:
+        _check(lib().sdb_covering_build_index_ex(cov.handle, leaf_bits, root_bits,
+                                                 _stream(stream)))
 
 
 def covering_build_table(cov: Covering, table_bits: int, stream=None):

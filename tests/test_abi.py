@@ -79,6 +79,7 @@ def test_invalid_arguments_rejected_on_host(sdblib):
                                       None) == sdblib.SDB_EINVAL
     assert L.sdb_join_aggregate(None, None, None, 0, None, 0, None, None, None) == sdblib.SDB_EINVAL
     assert L.sdb_covering_build_index(None, 12, None) == sdblib.SDB_EINVAL
+    assert L.sdb_covering_build_index_ex(None, 12, 0, None) == sdblib.SDB_EINVAL
     assert L.sdb_covering_build_table(None, 20, None) == sdblib.SDB_EINVAL
     assert L.sdb_trace_read(None, 0, None) == sdblib.SDB_EINVAL
     # tracing with nothing recorded needs no device

@@ -146,6 +146,13 @@ def test_stars16_workload(cuda, sdblib, orc):
             cnt, sm = gpu_join(cuda, sdblib, cov, w.points, lookup)
             assert np.array_equal(cnt, o1[0]) and np.array_equal(sm, o1[1])
         assert sdblib.covering_fallbacks(cov) == 0
+    # the root as one line (the plain two-level model) and as 2^6 segments
+    for root_bits in (0, 6):
+        sdblib.covering_build_index(cov, 8, root_bits=root_bits)
+        assert cov.info().index_root_bits == root_bits
+        cnt, sm = gpu_join(cuda, sdblib, cov, w.points, 1)
+        assert np.array_equal(cnt, o1[0]) and np.array_equal(sm, o1[1])
+        assert sdblib.covering_fallbacks(cov) == 0
 
 
 def test_zones_tiling_coarse_eps(cuda, sdblib, orc):
@@ -159,9 +166,14 @@ def test_zones_tiling_coarse_eps(cuda, sdblib, orc):
         want = oc.join(pts.x, pts.y, pts.attr)
         assert int(want[0].sum()) >= pts.n  # tiling: every point in >= 1 polygon
         sdblib.covering_build_index(cov, 12)
+        assert cov.info().index_root_bits == 12
         for lookup in (0, 1):
             cnt, sm = gpu_join(cuda, sdblib, cov, pts, lookup)
             assert np.array_equal(cnt, want[0]) and np.array_equal(sm, want[1])
+        assert sdblib.covering_fallbacks(cov) == 0
+        sdblib.covering_build_index(cov, 12, root_bits=0)  # one root line
+        cnt, sm = gpu_join(cuda, sdblib, cov, pts, 1)
+        assert np.array_equal(cnt, want[0]) and np.array_equal(sm, want[1])
         assert sdblib.covering_fallbacks(cov) == 0
 
 
