@@ -45,13 +45,18 @@ METRIC = "ε-bounded join points/s (learned vs plain lookup); p50/p99 query late
 UNIT = "points/s"
 LEAF_BITS_RANGE = (12, 20)
 LEAF_BITS = 16   # learned index of the timed join: 2^16 FP32 leaves
+# its root: one line over the id space (the plain two-level model); a root of
+# 2^12 segments along the range starts' distribution measured no faster on these
+# coverings (windows 1.6x narrower, same join time) and is timed beside it
+LEAF_ROOT_BITS = 0
 TABLE_BITS = 22  # its first level, the cell table: 2^22 buckets (16 MB), fewer when 2F < 22
 # DRAM bytes (read + write) per point of one join_kernel launch at eps = 2^6 on
 # the default workload, from one ncu capture of that launch on the 20M-point
 # case, scaled to 100M points per point (an upper bound: the table structures'
 # share is read once per launch):
 # profiles/join_kernel_table_learned_eps64_zones263_mobility20M.txt
-JOIN_FINEST_TRAFFIC = {"table_learned": {"eps": 64, "leaf_bits": 16, "bytes_per_point": 13.929}}
+JOIN_FINEST_TRAFFIC = {"table_learned": {"eps": 64, "leaf_bits": 16, "root_bits": 12,
+                                         "bytes_per_point": 13.929}}
 # DRAM bytes of one launch of radix_scatter_kernel (a keys-only pass) in the
 # sweep's record sort: profiles/radix_scatter_kernel_sweep_zones263.txt
 SCATTER_TRAFFIC = {"records": 117_378_603, "passes": 5, "bytes": 1.8926e9}
@@ -346,16 +351,17 @@ def run_reference(args):
 def config_of(w, n_points):
     return {"workload": f"zones263_mobility{n_points // 1_000_000}M_g24_eps4096-64",
             "points": n_points, "polygons": w.polygons.n, "grid_bits": 24, "eps": w.eps,
-            "lookup": "table_learned (cell table 2^%d buckets, learned index 2^%d leaves)"
-                      % (TABLE_BITS, LEAF_BITS),
-            "plain_lookup": "binary", "leaf_bits": LEAF_BITS, "table_bits": TABLE_BITS,
+            "lookup": "table_learned (cell table 2^%d buckets, learned index 2^%d leaves under "
+                      "one root line)" % (TABLE_BITS, LEAF_BITS),
+            "plain_lookup": "binary", "leaf_bits": LEAF_BITS, "root_bits": LEAF_ROOT_BITS,
+            "table_bits": TABLE_BITS,
             "l2": "inputs larger than L2 (point arrays 12 B/pt, 1.2 GB)"}
 
 
 def lookup_prep(sdb, c, lookup, stream, leaf_bits=None, table_bits=None):
     """The lookup structures a join with `lookup` reads, built on covering c."""
     if lookup in (sdb.LOOKUP_LEARNED, sdb.LOOKUP_TABLE_LEARNED):
-        sdb.covering_build_index(c, leaf_bits or LEAF_BITS, stream)
+        sdb.covering_build_index(c, leaf_bits or LEAF_BITS, stream, root_bits=LEAF_ROOT_BITS)
     if lookup in (sdb.LOOKUP_TABLE, sdb.LOOKUP_TABLE_LEARNED):
         sdb.covering_build_table(c, table_bits or TABLE_BITS, stream)
 
@@ -467,13 +473,13 @@ def main():
     reps = max(3, min(args.steps, 10))
     agree = True
     lk_rows = {}
-    # (the "_line_root" rows fit the index with its root as one line over the
-    # id space, the plain two-level model, instead of 2^12 root segments)
+    # (the "_knot_root" rows fit the index with a root of 2^12 segments along
+    # the range starts' distribution instead of one root line)
     for name, lk, bits, root in (("binary", PLAIN, None, None),
-                                 ("learned", sdb.LOOKUP_LEARNED, LEAF_BITS, None),
-                                 ("learned12", sdb.LOOKUP_LEARNED, 12, None),
-                                 ("learned_line_root", sdb.LOOKUP_LEARNED, LEAF_BITS, 0),
-                                 ("table_learned_line_root", HEAD, LEAF_BITS, 0),
+                                 ("learned", sdb.LOOKUP_LEARNED, LEAF_BITS, LEAF_ROOT_BITS),
+                                 ("learned12", sdb.LOOKUP_LEARNED, 12, LEAF_ROOT_BITS),
+                                 ("learned_knot_root", sdb.LOOKUP_LEARNED, LEAF_BITS, 12),
+                                 ("table_learned_knot_root", HEAD, LEAF_BITS, 12),
                                  ("table", sdb.LOOKUP_TABLE, None, None)):
         per = {}
         for i, c in enumerate(covs):
@@ -490,7 +496,7 @@ def main():
         per["points_per_s"] = N * E / (tot / 1e3)
         lk_rows[name] = per
     for c in covs:  # back to the headline index
-        sdb.covering_build_index(c, LEAF_BITS, stream)
+        sdb.covering_build_index(c, LEAF_BITS, stream, root_bits=LEAF_ROOT_BITS)
     res["join_ms"].update(lk_rows)
     res["plain_value"] = lk_rows["binary"]["points_per_s"]
     res["learned_only_value"] = lk_rows["learned"]["points_per_s"]
@@ -562,7 +568,8 @@ def main():
     achieved = N * per_pt / (join_ms[-1] / 1e3) / 1e9
     T = JOIN_FINEST_TRAFFIC.get("table_learned")
     traffic = (T["bytes_per_point"] * N
-               if T and w.eps[-1] == T["eps"] and T["leaf_bits"] == LEAF_BITS else None)
+               if T and w.eps[-1] == T["eps"] and T["leaf_bits"] == LEAF_BITS
+               and T["root_bits"] == LEAF_ROOT_BITS else None)
     res["roofline"] = {"kernel": "join_kernel<table_learned> eps=%s" % fine, "bound": "hbm",
                        "achieved": achieved, "peak": peak, "unit": "GB/s",
                        "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
@@ -910,7 +917,7 @@ def config3_leg(args, sdb, torch, dev, stream, T, pts):
         "covering of ~24 B per range, beyond device memory" % (cells * eps / 32)}
     e0.record(stream)
     sdb.covering_build_table(cov, TABLE_BITS, stream)
-    sdb.covering_build_index(cov, LEAF_BITS, stream)
+    sdb.covering_build_index(cov, LEAF_BITS, stream, root_bits=LEAF_ROOT_BITS)
     e1.record(stream)
     torch.cuda.synchronize()
     out["table_and_index_ms"] = e0.elapsed_time(e1)

@@ -4,7 +4,7 @@ The benchmark builds the 263-zone tiling's coverings for the whole eps sweep
 {2^12, 2^10, 2^8, 2^6} in one pass (sdb_build_coverings: four queries, about
 117M packed records, 40-bit keys) and joins 100M mobility points against each
 with the learned lookup (cell table of 2^22 buckets in front of a learned
-index of 2^16 leaves).  Here, on exactly those inputs and in exactly those
+index of 2^16 leaves under one root line).  Here, on exactly those inputs and in exactly those
 launches:
 
 * every swept covering equals the covering built for its eps alone, entry for
@@ -41,7 +41,7 @@ def timed(cuda, sdblib):
     covs = sdblib.build_coverings(w.polygons, 24, w.eps)
     for c in covs:
         sdblib.covering_build_table(c, bench.TABLE_BITS)
-        sdblib.covering_build_index(c, bench.LEAF_BITS)
+        sdblib.covering_build_index(c, bench.LEAF_BITS, root_bits=bench.LEAF_ROOT_BITS)
     return w, covs
 
 

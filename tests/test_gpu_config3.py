@@ -6,7 +6,7 @@ single covering build reaches on it (2^9: about 2.1e9 raster cells and 5.3e8
 ranges; eps = 2^5 would need about 3.4e10).  In the launches the benchmark
 times (all 1B points at once):
 
-* binary search, the learned index alone (2^16 leaves), the cell table and the
+* binary search, the learned index alone (2^16 leaves under one root line), the cell table and the
   table + learned lookup give identical per-polygon COUNT and SUM, with no
   learned fallback;
 * every point is counted at least once (the polygons tile the whole grid);
@@ -56,7 +56,7 @@ def test_config3_full_size(cuda, sdblib, orc):
     inf = cov.info()
     assert inf.n_cells > 2_000_000_000 and inf.n_ranges > 500_000_000
     sdblib.covering_build_table(cov, bench.TABLE_BITS)
-    sdblib.covering_build_index(cov, bench.LEAF_BITS)
+    sdblib.covering_build_index(cov, bench.LEAF_BITS, root_bits=bench.LEAF_ROOT_BITS)
     ref = join(torch, sdblib, cov, x, y, a, sdblib.LOOKUP_BINARY, P)
     assert int(ref[0].sum()) >= N
     for lookup in (sdblib.LOOKUP_LEARNED, sdblib.LOOKUP_TABLE, sdblib.LOOKUP_TABLE_LEARNED):
