@@ -55,8 +55,8 @@ TABLE_BITS = 22  # its first level, the cell table: 2^22 buckets (16 MB), fewer 
 # case, scaled to 100M points per point (an upper bound: the table structures'
 # share is read once per launch):
 # profiles/join_kernel_table_learned_eps64_zones263_mobility20M.txt
-JOIN_FINEST_TRAFFIC = {"table_learned": {"eps": 64, "leaf_bits": 16, "root_bits": 12,
-                                         "bytes_per_point": 13.929}}
+JOIN_FINEST_TRAFFIC = {"table_learned": {"eps": 64, "leaf_bits": 16, "root_bits": 0,
+                                         "bytes_per_point": 13.934}}
 # DRAM bytes of one launch of radix_scatter_kernel (a keys-only pass) in the
 # sweep's record sort: profiles/radix_scatter_kernel_sweep_zones263.txt
 SCATTER_TRAFFIC = {"records": 117_378_603, "passes": 5, "bytes": 1.8926e9}

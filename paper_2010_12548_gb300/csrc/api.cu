@@ -137,6 +137,17 @@ int num_sms() {
   return g_sms[dev];
 }
 
+sdb_status occupancy(const void* kern, int threads, size_t smem, int* per_sm) {
+  // the occupancy calculator honours the kernel's preferred carveout, which
+  // the previous launch may have set for a smaller footprint: ask with the
+  // whole unified memory available to shared memory
+  SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared));
+  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, threads, smem));
+  if (*per_sm < 1) *per_sm = 1;
+  return SDB_OK;
+}
+
 int carveout_pct(size_t bytes) {
   int dev = 0, max_smem = 0;
   cudaGetDevice(&dev);

@@ -665,8 +665,7 @@ sdb_status launch_t(const JoinArgs& A, cudaStream_t s) {
   if (smem > 48 * 1024)
     SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, smem));
-  if (per_sm < 1) per_sm = 1;
+  SDB_TRY(occupancy(reinterpret_cast<const void*>(kern), TPB, smem, &per_sm));
   // ask for no more shared memory than the resident blocks use (plus the 1 KB
   // the system reserves per block): the rest of the SM's unified memory stays
   // L1 cache, whose lines hold the lookups' gathers in flight
@@ -1021,8 +1020,7 @@ sdb_status launch_sweep_t(const SweepArgs& S, cudaStream_t s) {
   if (smem > 48 * 1024)
     SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  SDB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TOP_THREADS, smem));
-  if (per_sm < 1) per_sm = 1;
+  SDB_TRY(occupancy(reinterpret_cast<const void*>(kern), TOP_THREADS, smem, &per_sm));
   SDB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                     carveout_pct((size_t)per_sm * (smem + sizeof(SweepArgs::c) + 1024))));
   uint64_t blocks = (uint64_t)num_sms() * per_sm;

@@ -72,6 +72,9 @@ struct Scratch {
 // shared-memory carveout (percent of the SM's maximum shared memory, rounded up)
 // that holds the given bytes of resident blocks' shared memory
 int carveout_pct(size_t bytes);
+// resident blocks per SM of kernel kern (at least 1) with the given threads and
+// dynamic shared memory, independent of the carveout a previous launch chose
+sdb_status occupancy(const void* kern, int threads, size_t smem, int* per_sm);
 int num_sms();
 
 // count of kernels this library has launched in the process (all devices)
