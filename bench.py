@@ -372,7 +372,8 @@ def lookup_bytes(sdb, c, lookup):
     table, its mixed buckets' windows and (table + learned) the index for the
     table lookups (the ranges are then read only inside mixed buckets)."""
     inf = c.info()
-    leaves = 32 * (1 << inf.index_leaf_bits) + 4 * 4097 if inf.index_leaf_bits else 0
+    leaves = (32 * (1 << inf.index_leaf_bits) + 4 * ((1 << inf.index_root_bits) + 1)
+              if inf.index_leaf_bits else 0)
     if lookup in (sdb.LOOKUP_TABLE, sdb.LOOKUP_TABLE_LEARNED):
         tab = 4 * (1 << inf.table_bits) + 8 * inf.table_mixed
         if inf.table_sub_bits:

@@ -198,7 +198,8 @@ sdb_status sdb_covering_get_info(const sdb_covering *cov, sdb_covering_info *inf
  * maps a cell id to one of 2^leaf_bits leaves, each leaf a linear model in FP32
  * on leaf-relative ids, plus the leaf's maximum prediction error below and
  * above, measured with the same FP32 arithmetic the lookup uses over every id
- * the root sends to that leaf.  The root is piecewise linear in FP32 over
+ * the root sends to that leaf, and the fences of the range starts (every 16th
+ * start, which the lookup searches before the starts).  The root is piecewise linear in FP32 over
  * 2^root_bits equal segments of [0, 4^F): at each segment end it takes the
  * fraction of range starts below that id (the starts' cumulative distribution,
  * so leaves receive about equal numbers of ranges); root_bits = 0 is a single
@@ -234,8 +235,9 @@ sdb_status sdb_covering_build_table(sdb_covering *cov, uint32_t table_bits, void
  * with finest cell id h, the range r with start[r] <= h < start[r+1] is found
  * (lookup = SDB_LOOKUP_BINARY: binary search over the range starts;
  * SDB_LOOKUP_LEARNED: the learned index's prediction, a search bounded by the
- * stored error window, verified, with binary search as the fallback; requires
- * sdb_covering_build_index; SDB_LOOKUP_TABLE: the cell table's bucket, then a
+ * stored error window (first over the index's fences, every 16th range start,
+ * then inside one fence's block), verified, with binary search as the fallback;
+ * requires sdb_covering_build_index; SDB_LOOKUP_TABLE: the cell table's bucket, then a
  * binary search of the bucket's window if it holds several ranges; requires
  * sdb_covering_build_table; SDB_LOOKUP_TABLE_LEARNED: the cell table's bucket,
  * and in a bucket of several ranges -- when its window holds more than 64 of

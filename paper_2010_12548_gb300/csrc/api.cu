@@ -186,7 +186,7 @@ static void free_covering(sdb_covering* c) {
   cudaDeviceSynchronize();
   void* ps[] = {c->start,  c->list_off, c->list_ids, c->pay,    c->sample,
                 c->leaves, c->knots,    c->fallbacks, c->tab,   c->win,
-                c->sub,    c->win2,     c->top,       c->top_pal};
+                c->sub,    c->win2,     c->top,       c->top_pal, c->fence};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, 0);
   cudaStreamSynchronize(0);
@@ -520,7 +520,9 @@ sdb_status sdb_covering_get_info(const sdb_covering* cov, sdb_covering_info* inf
   info->n_list_ids = cov->nids;
   info->n_cells = cov->ncells;
   info->device_bytes =
-      cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) + (4ull << cov->knot_bits) + 4 : 0);
+      cov->bytes + (cov->leaf_bits ? (32ull << cov->leaf_bits) + (4ull << cov->knot_bits) + 4 +
+                                         8ull * ((cov->R >> FENCE_SHIFT) + 1)
+                                   : 0);
   if (cov->tab)
     info->device_bytes += (4ull << cov->tab_bits) + 8ull * cov->tab_mixed +
                           (cov->top ? (1ull << (2 * cov->top_level)) + 4 * TOP_PALETTE : 0) +

@@ -70,8 +70,9 @@ struct JoinArgs {
   uint64_t R;
   uint32_t sample_n, stride;
   uint32_t B, k, nsteps, st0, P;
-  // learned index
+  // learned index, and its fences (start[j << FENCE_SHIFT])
   const LeafRec* leaves;
+  const uint64_t* fence;
   const float* knots;
   uint32_t nknots, wshift;
   float inv_w;
@@ -142,8 +143,10 @@ __device__ __forceinline__ void find_bs(const uint64_t (&h)[G], uint32_t (&r)[G]
 template <int G>
 __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&r)[G],
                                              const float* s_knots, const JoinArgs& A) {
-  uint64_t lo[G];
-  uint32_t len[G];
+  // the model's window [a, b] of each point, then the last fence in it at or
+  // below h (fences stay cache-resident), then the window cut to that fence's
+  // block of 2^FENCE_SHIFT starts (one 128-byte line) searched to the end
+  uint32_t lo[G], b[G], jlo[G], jlen[G];  // range indices are below 2^32
   uint32_t maxlen = 1;
 #pragma unroll
   for (int q = 0; q < G; ++q) {
@@ -162,23 +165,45 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
     lr.errlo = (int32_t)(uint32_t)w3;
     lr.errhi = (int32_t)(uint32_t)(w3 >> 32);
     const int64_t pr = leaf_predict(lr, h[q]);
-    int64_t a = pr - lr.errlo, b = pr + lr.errhi;
-    if (a < (int64_t)lr.first) a = lr.first;
-    if (b > (int64_t)lr.last) b = lr.last;
-    if (b < a) b = a;
-    lo[q] = (uint64_t)a;
-    len[q] = (uint32_t)(b - a + 1);
+    int64_t wa = pr - lr.errlo, wb = pr + lr.errhi;
+    if (wa < (int64_t)lr.first) wa = lr.first;
+    if (wb > (int64_t)lr.last) wb = lr.last;
+    if (wb < wa) wb = wa;
+    lo[q] = (uint32_t)wa;
+    b[q] = (uint32_t)wb;
+    jlo[q] = lo[q] >> FENCE_SHIFT;
+    jlen[q] = ((uint32_t)wb >> FENCE_SHIFT) - jlo[q] + 1;
+    maxlen = max(maxlen, jlen[q]);
+  }
+  // the same number of halving steps for the whole warp; finished lanes idle
+  maxlen = __reduce_max_sync(FULL, maxlen);
+  for (int st = 32 - __clz(maxlen - 1); st > 0; --st) {
+    uint64_t v[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+      if (jlen[q] > 1) v[q] = __ldg(A.fence + jlo[q] + (jlen[q] >> 1));
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      if (jlen[q] > 1) {
+        const uint32_t half = jlen[q] >> 1;
+        if (v[q] <= h[q]) jlo[q] += half;
+        jlen[q] -= half;
+      }
+    }
+  }
+  uint32_t len[G];
+  maxlen = 1;
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    const uint32_t blk = jlo[q] << FENCE_SHIFT;
+    const uint32_t s0 = lo[q] > blk ? lo[q] : blk;
+    const uint32_t e0 = blk + ((1u << FENCE_SHIFT) - 1) < b[q] ? blk + ((1u << FENCE_SHIFT) - 1) : b[q];
+    lo[q] = s0;
+    len[q] = e0 - s0 + 1;
     maxlen = max(maxlen, len[q]);
   }
-  // the same number of halving steps for the whole warp; finished lanes idle.
-  // A probe <= h proves start[lo] <= h for the final lo (bit 0), a probe > h
-  // proves start[lo + 1] > h (bit 1: the result is the window's last start <= h)
   maxlen = __reduce_max_sync(FULL, maxlen);
-  const int steps = 32 - __clz(maxlen - 1);
-  uint32_t known[G];
-#pragma unroll
-  for (int q = 0; q < G; ++q) known[q] = 0;
-  for (int st = 0; st < steps; ++st) {
+  for (int st = 32 - __clz(maxlen - 1); st > 0; --st) {
     uint64_t v[G];
 #pragma unroll
     for (int q = 0; q < G; ++q)
@@ -187,24 +212,22 @@ __device__ __forceinline__ void find_learned(const uint64_t (&h)[G], uint32_t (&
     for (int q = 0; q < G; ++q) {
       if (len[q] > 1) {
         const uint32_t half = len[q] >> 1;
-        if (v[q] <= h[q]) {
-          lo[q] += half;
-          known[q] |= 1u;
-        } else {
-          known[q] |= 2u;
-        }
+        if (v[q] <= h[q]) lo[q] += half;
         len[q] -= half;
       }
     }
   }
-  // verification: the result must bracket h (ends not proven by a probe are read);
+  // verification: the result must bracket h (start[lo] from the line just
+  // searched, start[lo + 1] from it or, at the line's end, from the next fence);
   // otherwise plain binary search decides
 #pragma unroll
   for (int q = 0; q < G; ++q) {
-    const uint64_t s0 = (known[q] & 1u) ? 0ull : __ldg(A.start + lo[q]);
-    const uint64_t s1 = (known[q] & 2u) ? ~0ull : __ldg(A.start + lo[q] + 1);
+    const uint32_t nx = lo[q] + 1;
+    const uint64_t s0 = __ldg(A.start + lo[q]);
+    const uint64_t s1 = (nx & ((1u << FENCE_SHIFT) - 1)) ? __ldg(A.start + nx)
+                                                         : __ldg(A.fence + (nx >> FENCE_SHIFT));
     if (s0 <= h[q] && h[q] < s1) {
-      r[q] = (uint32_t)lo[q];
+      r[q] = lo[q];
     } else {
       atomicAdd(A.fallbacks, 1ull);
       r[q] = bs_global(A.start, A.R, h[q]);
@@ -1109,6 +1132,7 @@ sdb_status launch_join(const uint32_t* x, const uint32_t* y, const int32_t* attr
   hilbert3_params(cov->F, &A.nsteps, &A.st0);
   A.P = cov->P;
   A.leaves = cov->leaves;
+  A.fence = cov->fence;
   A.knots = cov->knots;
   A.nknots = cov->leaf_bits ? (1u << cov->knot_bits) + 1 : 0;
   A.wshift = cov->knot_wshift;
@@ -1197,6 +1221,7 @@ JoinArgs join_args(const uint32_t* x, const uint32_t* y, const int32_t* attr, ui
   hilbert3_params(cov->F, &A.nsteps, &A.st0);
   A.P = cov->P;
   A.leaves = cov->leaves;
+  A.fence = cov->fence;
   A.knots = cov->knots;
   A.nknots = cov->leaf_bits ? (1u << cov->knot_bits) + 1 : 0;
   A.wshift = cov->knot_wshift;

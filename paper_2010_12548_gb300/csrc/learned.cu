@@ -75,6 +75,13 @@ __global__ void leaf_base_kernel(const float* __restrict__ knot, uint32_t wshift
   base[l] = lo;
 }
 
+// fence j: the range start of index j << FENCE_SHIFT (j <= R >> FENCE_SHIFT)
+__global__ void fence_kernel(const uint64_t* __restrict__ start, uint64_t nf,
+                             uint64_t* __restrict__ fence) {
+  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nf) fence[j] = start[j << FENCE_SHIFT];
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -188,8 +195,15 @@ sdb_status build_learned_index(sdb_covering* cov, uint32_t leaf_bits, uint32_t r
   Scratch sc(s);
   if (cov->leaves) dfree(cov->leaves, s);
   if (cov->knots) dfree(cov->knots, s);
+  if (cov->fence) dfree(cov->fence, s);
   cov->leaves = nullptr;
   cov->knots = nullptr;
+  cov->fence = nullptr;
+  const uint64_t nf = (R >> FENCE_SHIFT) + 1;
+  SDB_TRY(dalloc_n(&cov->fence, nf, s));
+  fence_kernel<<<grid_for(nf, 256), 256, 0, s>>>(cov->start, nf, cov->fence);
+  note_launch();
+  SDB_TRY_CUDA(cudaGetLastError());
   SDB_TRY(dalloc_n(&cov->leaves, L, s));
   if (reinterpret_cast<uintptr_t>(cov->leaves) & 31u) {  // the lookup reads 32 bytes at once
     set_error("learned index: leaf records not 32-byte aligned");

@@ -160,6 +160,11 @@ __device__ __forceinline__ uint32_t root_leaf(const float* knot, uint32_t wshift
   return (uint32_t)v >= nleaves ? nleaves - 1 : (uint32_t)v;
 }
 
+// Fences of the learned index: every 2^FENCE_SHIFT-th range start, so that a
+// window search first narrows the window to one 128-byte line of starts
+// through the (cache-resident) fences.
+constexpr uint32_t FENCE_SHIFT = 4;
+
 }  // namespace sdb
 
 struct sdb_covering {
@@ -180,6 +185,7 @@ struct sdb_covering {
   uint32_t knot_bits = 0, knot_wshift = 0; // root: 2^knot_bits + 1 knots, spacing 2^knot_wshift ids
   float* knots = nullptr;                  // root knots (leaf units)
   sdb::LeafRec* leaves = nullptr;          // 2^leaf_bits
+  uint64_t* fence = nullptr;               // start[j << FENCE_SHIFT], j = 0 .. R >> FENCE_SHIFT
   unsigned long long* fallbacks = nullptr; // device counter
   // cell table (table.cu): 2^tab_bits buckets of 2^tab_shift ids
   uint32_t* tab = nullptr;  // payload, or TAB_MIXED | index into win
