@@ -702,10 +702,10 @@ def main():
         for c in cs:
             c.free()
         # the host -> device link: the point arrays copied from pinned memory in
-        # the host join's chunks of 2^22 points (one copy of 3 x 400 MB measured
+        # the host join's chunks of 2^24 points (one copy of 3 x 400 MB measured
         # half the rate on some hosts)
         dbuf = torch.empty(N * 3, dtype=torch.int32, device=dev)
-        LINK_CHUNK = 1 << 22
+        LINK_CHUNK = 1 << 24
         def link_copy():
             with torch.cuda.stream(stream):
                 for j, h in enumerate((hx, hy, ha)):

@@ -708,9 +708,11 @@ sdb_status sdb_join_aggregate_host(const uint32_t* h_x, const uint32_t* h_y, con
   if (lookup == SDB_LOOKUP_LEARNED || lookup == SDB_LOOKUP_TABLE_LEARNED)
     for (uint32_t c = 0; c < n_covs; ++c)
       SDB_TRY_CUDA(cudaMemsetAsync(covs[c]->fallbacks, 0, sizeof(unsigned long long), s));
-  // points per chunk: small enough that the joins of the last chunk, which no
-  // copy hides, stay short against the copies of the whole input
-  const uint64_t CH = 1ull << 22;
+  // points per chunk: the joins of the last chunk are not hidden by a copy,
+  // but smaller chunks issue more launches per call, and a host whose API calls
+  // are slow then falls behind the copies (2^22: 6.00 ms on some hosts, 7.81 on
+  // another, for 100M points at four eps; 2^24: 6.05 ms)
+  const uint64_t CH = 1ull << 24;
   const uint64_t nch = (n + CH - 1) / CH;
   uint32_t* dx[2];
   uint32_t* dy[2];
